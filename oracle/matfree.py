@@ -1,0 +1,446 @@
+"""O2: matrix-free FP64 oracle on nodal arrays -- test infrastructure only.
+
+Same mathematics as ``oracle.dense`` (O1), applied without global matrices so that
+it reaches the mesh sizes of the benchmark workloads.  Vectors live on the global
+GLL grid as nodal arrays u[g3, g2, g1]; a condensed vector is a nodal array that
+is zero at element-interior nodes and on the Dirichlet boundary.
+
+Operators follow the definitions directly and make no attempt at the paper's
+O(p^3) factorisations except where the paper prescribes them (Algorithm 1):
+  * element operator: eq. helmholtzop applied in tensor-product form, O(p^4);
+  * condensed element operator (Sec. 2.2): Hhat_e u_B =
+        (H_e [u_B; 0])_B - (H_e [0; H_II^{-1} (H_e [u_B; 0])_I])_B,
+    with H_II^{-1} by 3D fast diagonalisation of the element interior block
+    (eq. fast_diagonalization for one element);
+  * smoother: Algorithm 2 around Algorithm 1 on every vertex star;
+  * transfers: per-element 3D embedded interpolation and its exact transpose;
+  * coarse solve: exact sparse direct solve of the full coarse system with the
+    embedded right-hand side (F_hat, 0) (Sec. 3.1, eq. star_right_hand_side_full
+    argument applied to the whole domain);
+  * Algorithms 3 and 4 literally.
+"""
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+from numpy.lib.stride_tricks import as_strided
+
+from . import dense
+from .gll import gll, interp_matrix, standard_matrices, weight_poly
+
+
+# --------------------------------------------------------------------------
+# element blocks of a nodal array
+# --------------------------------------------------------------------------
+
+def elem_view(u, mesh):
+    """Overlapping view (n3, n2, n1, p+1, p+1, p+1) of the element blocks of a nodal array."""
+    p = mesh.p
+    n1, n2, n3 = mesh.n
+    s3, s2, s1 = u.strides
+    return as_strided(u, shape=(n3, n2, n1, p + 1, p + 1, p + 1),
+                      strides=(p * s3, p * s2, p * s1, s3, s2, s1), writeable=False)
+
+
+def elem_blocks(u, mesh):
+    return np.array(elem_view(np.ascontiguousarray(u, dtype=float), mesh))
+
+
+def assemble_blocks(blocks, mesh):
+    """Sum element blocks into a nodal array (direct stiffness summation)."""
+    out = np.zeros(mesh.shape)
+    p = mesh.p
+    n1, n2, n3 = mesh.n
+    s3, s2, s1 = out.strides
+    view = as_strided(out, shape=(n3, n2, n1, p + 1, p + 1, p + 1),
+                      strides=(p * s3, p * s2, p * s1, s3, s2, s1), writeable=True)
+    # elements of one parity class share no node, so each class is one vectorised add
+    for q3 in (0, 1):
+        for q2 in (0, 1):
+            for q1 in (0, 1):
+                view[q3::2, q2::2, q1::2] += blocks[q3::2, q2::2, q1::2]
+    return out
+
+
+def masks(mesh):
+    """Boolean nodal masks: skeleton (element boundaries) and free (not Dirichlet)."""
+    p = mesh.p
+    G = np.meshgrid(np.arange(mesh.N[2]), np.arange(mesh.N[1]), np.arange(mesh.N[0]), indexing="ij")
+    g3, g2, g1 = G
+    skel = (g1 % p == 0) | (g2 % p == 0) | (g3 % p == 0)
+    free = ((g1 > 0) & (g1 < mesh.N[0] - 1) & (g2 > 0) & (g2 < mesh.N[1] - 1)
+            & (g3 > 0) & (g3 < mesh.N[2] - 1))
+    return skel, free
+
+
+def condensed_mask(mesh):
+    skel, free = masks(mesh)
+    return skel & free
+
+
+def elem_coeffs(mesh):
+    """d_e = h1 h2 h3 / 8 (lambda, 4/h1^2, 4/h2^2, 4/h3^2) for every element (Sec. 2.1)."""
+    h3, h2, h1 = np.meshgrid(mesh.h[2], mesh.h[1], mesh.h[0], indexing="ij")
+    vol = h1 * h2 * h3 / 8.0
+    return np.stack([vol * mesh.lam, vol * 4.0 / h1**2, vol * 4.0 / h2**2, vol * 4.0 / h3**2], axis=-1)
+
+
+def apply_elem_op(X, d, p):
+    """eq. helmholtzop on element blocks X[..., i3, i2, i1] with coefficients d[..., 4]."""
+    M, L = standard_matrices(p)
+    w = np.diag(M)
+    W3, W2, W1 = w[:, None, None], w[None, :, None], w[None, None, :]
+    t0 = X * (W3 * W2 * W1)
+    t1 = np.einsum("...ijk,ck->...ijc", X, L) * (W3 * W2)
+    t2 = np.einsum("...ijk,bj->...ibk", X, L) * (W3 * W1)
+    t3 = np.einsum("...ijk,ai->...ajk", X, L) * (W2 * W1)
+    e = (Ellipsis, None, None, None)
+    return d[..., 0][e] * t0 + d[..., 1][e] * t1 + d[..., 2][e] * t2 + d[..., 3][e] * t3
+
+
+def interior_eigen(p):
+    """Reference interior generalized eigenpairs S^T L_II S = Lambda, S^T M_II S = I (Sec. 3.2)."""
+    M, L = standard_matrices(p)
+    lam, S = sla.eigh(L[1:p, 1:p], M[1:p, 1:p])
+    return S, lam
+
+
+def hii_inv(Y, d, p):
+    """H_II^{-1} on interior blocks Y[..., m, m, m] by fast diagonalisation (eq. fast_diagonalization)."""
+    S, lam = interior_eigen(p)
+    Z = np.einsum("...ijk,ia,jb,kc->...abc", Y, S, S, S, optimize=True)
+    D = (d[..., 0][..., None, None, None]
+         + d[..., 3][..., None, None, None] * lam[:, None, None]
+         + d[..., 2][..., None, None, None] * lam[None, :, None]
+         + d[..., 1][..., None, None, None] * lam[None, None, :])
+    Z = Z / D
+    return np.einsum("...abc,ia,jb,kc->...ijk", Z, S, S, S, optimize=True)
+
+
+def _interior(X):
+    return X[..., 1:-1, 1:-1, 1:-1]
+
+
+def _zero_interior(X):
+    Y = X.copy()
+    Y[..., 1:-1, 1:-1, 1:-1] = 0.0
+    return Y
+
+
+def _only_interior(Xi, p):
+    shp = Xi.shape[:-3] + (p + 1, p + 1, p + 1)
+    Y = np.zeros(shp)
+    Y[..., 1:-1, 1:-1, 1:-1] = Xi
+    return Y
+
+
+# --------------------------------------------------------------------------
+# condensed operator, condensation, recovery (Sec. 2.2; Algorithm 4 first/last lines)
+# --------------------------------------------------------------------------
+
+def apply_condensed(mesh, u, chunk=512):
+    """y = Hhat u for a condensed nodal array u (element by element, then assembled)."""
+    p = mesh.p
+    u = np.where(condensed_mask(mesh), u, 0.0)
+    blocks = elem_blocks(u, mesh)
+    d = elem_coeffs(mesh)
+    n1, n2, n3 = mesh.n
+    bflat = blocks.reshape(-1, p + 1, p + 1, p + 1)
+    dflat = d.reshape(-1, 4)
+    out = np.empty_like(bflat)
+    for s in range(0, bflat.shape[0], chunk):
+        X = bflat[s:s + chunk]
+        dd = dflat[s:s + chunk]
+        t = apply_elem_op(X, dd, p)
+        if p > 1:
+            xi = hii_inv(_interior(t), dd, p)
+            t = t - apply_elem_op(_only_interior(xi, p), dd, p)
+        out[s:s + chunk] = _zero_interior(t)
+    y = assemble_blocks(out.reshape(n3, n2, n1, p + 1, p + 1, p + 1), mesh)
+    return np.where(condensed_mask(mesh), y, 0.0)
+
+
+def mass_diag(mesh):
+    """Assembled diagonal GLL mass: element mass (h1 h2 h3 / 8) M (x) M (x) M summed (Sec. 2.1)."""
+    _, w = gll(mesh.p)
+    W = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    h3, h2, h1 = np.meshgrid(mesh.h[2], mesh.h[1], mesh.h[0], indexing="ij")
+    blocks = (h1 * h2 * h3 / 8.0)[..., None, None, None] * W
+    return assemble_blocks(blocks, mesh)
+
+
+def condense_rhs(mesh, f, chunk=512):
+    """F = M f;  Fhat = F_B - sum_e H_BI H_II^{-1} F_I (Algorithm 4, condensation step)."""
+    p = mesh.p
+    F = mass_diag(mesh) * np.asarray(f, float)
+    Fh = np.where(condensed_mask(mesh), F, 0.0)
+    if p == 1:
+        return Fh
+    d = elem_coeffs(mesh)
+    blocks = elem_blocks(F, mesh)
+    n1, n2, n3 = mesh.n
+    bflat = blocks.reshape(-1, p + 1, p + 1, p + 1)
+    dflat = d.reshape(-1, 4)
+    out = np.empty_like(bflat)
+    for s in range(0, bflat.shape[0], chunk):
+        dd = dflat[s:s + chunk]
+        xi = hii_inv(_interior(bflat[s:s + chunk]), dd, p)
+        out[s:s + chunk] = _zero_interior(apply_elem_op(_only_interior(xi, p), dd, p))
+    Z = assemble_blocks(out.reshape(n3, n2, n1, p + 1, p + 1, p + 1), mesh)
+    return np.where(condensed_mask(mesh), Fh - Z, 0.0)
+
+
+def recover(mesh, f, uhat, chunk=512):
+    """Nodal u: skeleton values from uhat, u_I = H_II^{-1} (F_I - H_IB u_B) per element."""
+    p = mesh.p
+    u = np.where(condensed_mask(mesh), uhat, 0.0)
+    if p == 1:
+        return u
+    F = mass_diag(mesh) * np.asarray(f, float)
+    d = elem_coeffs(mesh)
+    ub = elem_blocks(u, mesh).reshape(-1, p + 1, p + 1, p + 1)
+    fb = elem_blocks(F, mesh).reshape(-1, p + 1, p + 1, p + 1)
+    dflat = d.reshape(-1, 4)
+    n1, n2, n3 = mesh.n
+    ui = np.empty((ub.shape[0], p - 1, p - 1, p - 1))
+    for s in range(0, ub.shape[0], chunk):
+        dd = dflat[s:s + chunk]
+        t = apply_elem_op(ub[s:s + chunk], dd, p)
+        ui[s:s + chunk] = hii_inv(_interior(fb[s:s + chunk]) - _interior(t), dd, p)
+    out = u.copy()
+    ui = ui.reshape(n3, n2, n1, p - 1, p - 1, p - 1)
+    for a3 in range(n3):
+        for a2 in range(n2):
+            for a1 in range(n1):
+                out[a3 * p + 1:(a3 + 1) * p, a2 * p + 1:(a2 + 1) * p, a1 * p + 1:(a1 + 1) * p] = ui[a3, a2, a1]
+    return out
+
+
+# --------------------------------------------------------------------------
+# star smoother (Algorithm 2 around Algorithm 1)
+# --------------------------------------------------------------------------
+
+class StarTables:
+    """Per vertex line eigen-tables (Sec. 3.2, 3.3) and 1D weight vectors of one level."""
+
+    def __init__(self, mesh):
+        self.mesh = mesh
+        p = mesh.p
+        m = p - 1
+        self.S, self.Lam, self.act, self.wl = [], [], [], []
+        x = mesh.node_coords()
+        j = np.arange(-m, m + 1)
+        for d in range(3):
+            Sd, Ld, Ad, Wd = [], [], [], []
+            for c in range(mesh.n[d] + 1):
+                S, lam, act = dense.star_line_table(mesh, d, c)
+                Sd.append(S)
+                Ld.append(lam)
+                Ad.append(act)
+                g = c * p + j
+                wv = np.zeros(len(j))
+                for k, gg in enumerate(g):
+                    if 0 <= gg < mesh.N[d]:
+                        dist = x[d][gg] - mesh.X[d][c]
+                        if dist == 0.0:
+                            wv[k] = 1.0
+                            continue
+                        side = c if dist > 0 else c - 1
+                        wv[k] = weight_poly(abs(dist) / mesh.h[d][side])
+                Wd.append(wv)
+            self.S.append(np.array(Sd))
+            self.Lam.append(np.array(Ld))
+            self.act.append(np.array(Ad))
+            self.wl.append(np.array(Wd))
+
+
+def smooth(mesh, r, tables=None, chunk=128):
+    """Delta u = Smoother(r) (Algorithm 2), each star inverted by Algorithm 1.
+
+    Star outputs are combined as W_i times the solution; a node stored on
+    several planes of one star contributes the mean of its plane values.
+    """
+    p = mesh.p
+    m = p - 1
+    nS = 2 * m + 1
+    if tables is None:
+        tables = StarTables(mesh)
+    r = np.where(condensed_mask(mesh), r, 0.0)
+    P = p  # padding so every star plane slice is in range
+    rp = np.pad(r, P)
+    dup = np.zeros_like(rp)
+    verts = np.array(dense.star_vertices(mesh))
+    j = np.arange(-m, m + 1)
+    z = (j == 0)
+    mult = 1.0 + z[:, None] + z[None, :]
+    lam = mesh.lam
+    for s in range(0, len(verts), chunk):
+        V = verts[s:s + chunk]
+        c1, c2, c3 = V[:, 0], V[:, 1], V[:, 2]
+        o1 = (c1 * p + P)[:, None, None]
+        o2 = (c2 * p + P)[:, None, None]
+        o3 = (c3 * p + P)[:, None, None]
+        jj = j[None, :, None]
+        kk = j[None, None, :]
+        # plane gathers: F1[j2, j3], F2[j1, j3], F3[j1, j2]
+        i1 = (o3 + kk, o2 + jj, o1 + 0 * jj)
+        i2 = (o3 + kk, o2 + 0 * jj, o1 + jj)
+        i3 = (o3 + 0 * jj, o2 + kk, o1 + jj)
+        F1 = rp[i1] / mult
+        F2 = rp[i2] / mult
+        F3 = rp[i3] / mult
+        S1, S2, S3 = tables.S[0][c1], tables.S[1][c2], tables.S[2][c3]
+        L1, L2, L3 = tables.Lam[0][c1], tables.Lam[1][c2], tables.Lam[2][c3]
+        s1, s2, s3 = S1[:, m, :], S2[:, m, :], S3[:, m, :]
+        A1 = np.einsum("zjb,zjk,zkc->zbc", S2, F1, S3, optimize=True)
+        A2 = np.einsum("zja,zjk,zkc->zac", S1, F2, S3, optimize=True)
+        A3 = np.einsum("zja,zjk,zkb->zab", S1, F3, S2, optimize=True)
+        E = (s1[:, :, None, None] * A1[:, None, :, :]
+             + s2[:, None, :, None] * A2[:, :, None, :]
+             + s3[:, None, None, :] * A3[:, :, :, None])
+        D = lam + L1[:, :, None, None] + L2[:, None, :, None] + L3[:, None, None, :]
+        Vv = E / D
+        B1 = np.einsum("za,zabc->zbc", s1, Vv)
+        B2 = np.einsum("zb,zabc->zac", s2, Vv)
+        B3 = np.einsum("zc,zabc->zab", s3, Vv)
+        O1 = np.einsum("zjb,zbc,zkc->zjk", S2, B1, S3, optimize=True)
+        O2 = np.einsum("zja,zac,zkc->zjk", S1, B2, S3, optimize=True)
+        O3 = np.einsum("zja,zab,zkb->zjk", S1, B3, S2, optimize=True)
+        w1, w2, w3 = tables.wl[0][c1], tables.wl[1][c2], tables.wl[2][c3]
+        a1, a2, a3 = tables.act[0][c1], tables.act[1][c2], tables.act[2][c3]
+        # W/mult on each plane; masked where the node is not a star node
+        W1 = (w2[:, :, None] * w3[:, None, :]) * (a1[:, m][:, None, None] & a2[:, :, None] & a3[:, None, :])
+        W2 = (w1[:, :, None] * w3[:, None, :]) * (a2[:, m][:, None, None] & a1[:, :, None] & a3[:, None, :])
+        W3 = (w1[:, :, None] * w2[:, None, :]) * (a3[:, m][:, None, None] & a1[:, :, None] & a2[:, None, :])
+        np.add.at(dup, i1, W1 * O1 / mult)
+        np.add.at(dup, i2, W2 * O2 / mult)
+        np.add.at(dup, i3, W3 * O3 / mult)
+    du = dup[P:-P, P:-P, P:-P]
+    return np.where(condensed_mask(mesh), du, 0.0)
+
+
+# --------------------------------------------------------------------------
+# transfers (Sec. 4.1)
+# --------------------------------------------------------------------------
+
+def _interp(mesh_c, mesh_f):
+    xc, _ = gll(mesh_c.p)
+    xf, _ = gll(mesh_f.p)
+    return interp_matrix(xc, xf)
+
+
+def prolong(mesh_c, mesh_f, uc):
+    """Fine condensed nodal array J uc: per-element (J (x) J (x) J) on the coarse skeleton values."""
+    J = _interp(mesh_c, mesh_f)
+    uc = np.where(condensed_mask(mesh_c), uc, 0.0)
+    Xc = elem_blocks(uc, mesh_c)
+    Xf = np.einsum("ai,bj,ck,...ijk->...abc", J, J, J, Xc, optimize=True)
+    out = np.zeros(mesh_f.shape)
+    pf = mesh_f.p
+    n1, n2, n3 = mesh_f.n
+    for a3 in range(n3):
+        for a2 in range(n2):
+            for a1 in range(n1):
+                out[a3 * pf:(a3 + 1) * pf + 1, a2 * pf:(a2 + 1) * pf + 1, a1 * pf:(a1 + 1) * pf + 1] = Xf[a3, a2, a1]
+    return np.where(condensed_mask(mesh_f), out, 0.0)
+
+
+def multiplicity(mesh):
+    """Number of elements sharing each node."""
+    one = np.ones((mesh.n[2], mesh.n[1], mesh.n[0], mesh.p + 1, mesh.p + 1, mesh.p + 1))
+    return assemble_blocks(one, mesh)
+
+
+def restrict(mesh_f, mesh_c, rf):
+    """Exact transpose of ``prolong`` on condensed vectors."""
+    J = _interp(mesh_c, mesh_f)
+    rf = np.where(condensed_mask(mesh_f), rf, 0.0) / multiplicity(mesh_f)
+    Xf = elem_blocks(rf, mesh_f)
+    Xc = np.einsum("ai,bj,ck,...abc->...ijk", J, J, J, Xf, optimize=True)
+    out = assemble_blocks(Xc, mesh_c)
+    return np.where(condensed_mask(mesh_c), out, 0.0)
+
+
+# --------------------------------------------------------------------------
+# coarse solve, V-cycle, solver
+# --------------------------------------------------------------------------
+
+class CoarseSolver:
+    """Exact coarse solve: full system at p0 with embedded right-hand side (F_hat, 0)."""
+
+    def __init__(self, mesh):
+        self.mesh = mesh
+        H = dense.assemble_H(mesh)
+        sets = dense.index_sets(mesh)
+        self.free = sets["free"]
+        self.lu = spla.splu(H[self.free][:, self.free].tocsc())
+
+    def solve(self, Fh):
+        rhs = np.where(condensed_mask(self.mesh), Fh, 0.0).ravel()[self.free]
+        u = np.zeros(int(np.prod(self.mesh.N)))
+        u[self.free] = self.lu.solve(rhs)
+        return np.where(condensed_mask(self.mesh), u.reshape(self.mesh.shape), 0.0)
+
+
+class MG:
+    """p-multigrid hierarchy (Sec. 4.1) on nodal condensed arrays."""
+
+    def __init__(self, mesh, p0=1, nu_pre=1, nu_post=1):
+        self.degs = dense.level_degrees(mesh.p, p0)
+        self.meshes = [mesh.with_degree(q) for q in self.degs]
+        self.tables = [StarTables(m) if m.p > 1 or True else None for m in self.meshes]
+        self.coarse = CoarseSolver(self.meshes[0])
+        self.nu_pre, self.nu_post = nu_pre, nu_post
+
+    @property
+    def L(self):
+        return len(self.degs) - 1
+
+    def op(self, l, u):
+        return apply_condensed(self.meshes[l], u)
+
+    def smooth(self, l, r):
+        return smooth(self.meshes[l], r, self.tables[l])
+
+
+def vcycle(mg, u, F):
+    """Algorithm 3, literally, on nodal condensed arrays."""
+    L = mg.L
+    ul = [None] * (L + 1)
+    Fl = [None] * (L + 1)
+    ul[L] = np.array(u, float, copy=True)
+    Fl[L] = np.asarray(F, float)
+    for l in range(L, 0, -1):
+        if l != L:
+            ul[l] = np.zeros_like(Fl[l])
+        for _ in range(mg.nu_pre):
+            ul[l] = ul[l] + mg.smooth(l, Fl[l] - mg.op(l, ul[l]))
+        Fl[l - 1] = restrict(mg.meshes[l], mg.meshes[l - 1], Fl[l] - mg.op(l, ul[l]))
+    ul[0] = mg.coarse.solve(Fl[0])
+    for l in range(1, L + 1):
+        ul[l] = ul[l] + prolong(mg.meshes[l - 1], mg.meshes[l], ul[l - 1])
+        for _ in range(mg.nu_post):
+            ul[l] = ul[l] + mg.smooth(l, Fl[l] - mg.op(l, ul[l]))
+    return ul[L]
+
+
+def mg_solve(mg, Fhat, rtol=1e-10, maxit=50):
+    """Algorithm 4: condensed V-cycle iteration to ||r|| <= rtol ||r_0||; returns (u, n, history)."""
+    u = np.zeros_like(Fhat)
+    r = Fhat - mg.op(mg.L, u)
+    n0 = np.linalg.norm(r)
+    hist = [n0]
+    it = 0
+    while hist[-1] > rtol * n0 and it < maxit:
+        u = vcycle(mg, u, Fhat)
+        r = Fhat - mg.op(mg.L, u)
+        hist.append(np.linalg.norm(r))
+        it += 1
+    return u, it, np.array(hist)
+
+
+def solve(mesh, f, p0=1, rtol=1e-10, maxit=50):
+    """Whole solver: condense, Algorithm 4, recover.  Returns (u_nodal, iterations, history)."""
+    mg = MG(mesh, p0)
+    Fh = condense_rhs(mesh, f)
+    uh, it, hist = mg_solve(mg, Fh, rtol, maxit)
+    return recover(mesh, f, uh), it, hist
