@@ -1,0 +1,234 @@
+/*
+ * semmg -- p-multigrid for the statically condensed spectral-element Helmholtz
+ * problem on one GPU (sm_103a).  C ABI.
+ *
+ * Method: Huismann, Stiller, Froehlich, "Scaling to the stars -- a linearly
+ * scaling elliptic solver for p-multigrid", arXiv:1808.03595.
+ *
+ * Problem (Sec. 2.1, eq. helmholtz_equation): lambda u - Laplace u = f on a box
+ * meshed by a tensor product of cuboidal elements (per-axis widths h_d[a]),
+ * GLL nodal basis of degree p, homogeneous Dirichlet conditions on all six
+ * faces (Sec. 3.3).  The element operator is eq. helmholtzop with coefficients
+ * d_e = h1 h2 h3 / 8 (lambda, 4/h1^2, 4/h2^2, 4/h3^2), the rightmost Kronecker
+ * factor acting along x1.
+ *
+ * ------------------------------------------------------------------ layouts
+ * Nodal arrays: the global GLL grid of a level, N_d = n_d p + 1 points per
+ * axis, FP64, C order u[g3][g2][g1] (x1 fastest), Dirichlet boundary included.
+ *
+ * Condensed ("hat") vectors: values on the element skeleton (element-boundary
+ * nodes, Sec. 2.2), one slot per unique node, grouped by entity, with m = p-1,
+ * nv_d = n_d + 1 vertex planes per axis.  Entities on the domain boundary are
+ * stored too and always hold 0 (homogeneous Dirichlet); no entry point writes
+ * a non-zero there.  Group order and index formulas (c = vertex-plane index,
+ * a = element index, i = 0..m-1 interior node index, the last index fastest):
+ *   F1 faces normal to x1 [a3][a2][c1][i3][i2]   n3 n2 nv1 m^2
+ *   F2 faces normal to x2 [a3][c2][a1][i3][i1]   n3 nv2 n1 m^2
+ *   F3 faces normal to x3 [c3][a2][a1][i2][i1]   nv3 n2 n1 m^2
+ *   E1 edges along x1     [c3][c2][a1][i1]       nv3 nv2 n1 m
+ *   E2 edges along x2     [c3][a2][c1][i2]       nv3 n2 nv1 m
+ *   E3 edges along x3     [a3][c2][c1][i3]       n3 nv2 nv1 m
+ *   V  vertices           [c3][c2][c1]           nv3 nv2 nv1
+ * Levels are numbered 0 (coarsest, degree p0) .. L (finest, degree p); the
+ * degrees are p_l = p0 2^l for l < L and p_L = p (Sec. 4.1).
+ *
+ * ------------------------------------------------------------------ ownership
+ * Every vector argument is a DEVICE pointer owned by the caller, except in
+ * semmg_solve_host, whose f/u are HOST pointers.  The library allocates its
+ * tables and work buffers in semmg_setup (cudaMalloc) and frees them in
+ * semmg_destroy.  Every call is ordered on `stream` (a cudaStream_t, NULL =
+ * legacy default stream) and asynchronous unless stated otherwise.  A context
+ * is not thread-safe: calls on one context must not overlap in time on the
+ * host, and calls on one context enqueued on different streams race on its
+ * work buffers.
+ *
+ * ------------------------------------------------------------------ errors
+ * Every function returns SEMMG_OK (0) or a negative SEMMG_ERR_* code and never
+ * aborts the process.  semmg_last_error() gives a message for the last failure
+ * on a context (including the CUDA error string for SEMMG_ERR_CUDA).
+ */
+#ifndef SEMMG_H
+#define SEMMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct semmg_ctx semmg_ctx;
+
+enum {
+  SEMMG_OK = 0,
+  SEMMG_ERR_INVALID_ARG = -1,   /* null pointer, bad size, level out of range */
+  SEMMG_ERR_UNSUPPORTED = -2,   /* p < 1, p > SEMMG_MAX_DEGREE, p0 > p, ... */
+  SEMMG_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  SEMMG_ERR_NOT_CONVERGED = -4, /* max_iter cycles without reaching rtol; info filled */
+  SEMMG_ERR_NONFINITE = -5,     /* NaN or Inf in a residual norm */
+  SEMMG_ERR_TIMEOUT = -6,       /* a bounded device wait ran out (batched form) */
+  SEMMG_ERR_NOMEM = -7          /* device or host allocation failed */
+};
+
+#define SEMMG_MAX_DEGREE 48
+
+/* precision of the V-cycle (the outer iteration, its residual, norms and
+ * update, the coarse solve, condensation and recovery are always FP64) */
+enum { SEMMG_FP64 = 0, SEMMG_MIXED = 1 };
+/* element type of a vector argument of smooth / restrict / prolong_add */
+enum { SEMMG_F64 = 0, SEMMG_F32 = 1 };
+
+typedef struct {
+  int n[3];              /* elements per axis, each >= 1 */
+  const double* h[3];    /* HOST arrays: n[d] element widths along axis d, > 0 */
+} semmg_mesh;
+
+typedef struct {
+  int p0;          /* coarse degree, 1 <= p0 <= p (default 2, Sec. 4.1) */
+  int nu_pre;      /* pre-smoothing steps per level (default 1, Algorithm 3) */
+  int nu_post;     /* post-smoothing steps per level (default 1) */
+  int precision;   /* SEMMG_FP64 (default) or SEMMG_MIXED */
+  int max_iter;    /* V-cycle cap of semmg_solve (default 50) */
+} semmg_opts;
+
+typedef struct {
+  int iters;          /* V-cycles performed (n_10 when rtol = 1e-10) */
+  double res0;        /* ||r_0||_2 over the condensed unknowns */
+  double res_final;   /* ||r_iters||_2 */
+  double rho;         /* (res_final / res0)^(1/iters), Sec. 5.2 */
+  int status;         /* return code of the solve */
+} semmg_info;
+
+/* Fill *opts with the defaults listed above. */
+void semmg_default_opts(semmg_opts* opts);
+
+/* Build the level hierarchy of Sec. 4.1 for the mesh, degree p and lambda >= 0:
+ * 1D GLL tables, element interior eigenpairs, per-vertex-line star eigen-tables
+ * with identity padding at the Dirichlet boundary (Sec. 3.2-3.3), smoother
+ * weights (degree 7, Sec. 3.2), interpolation matrices and the coarse
+ * fast-diagonalisation tables; uploads them and allocates work buffers.
+ * opts may be NULL (defaults).  Synchronises the device once at the end.
+ * On success *out owns everything; release it with semmg_destroy. */
+int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* opts,
+                void* stream, semmg_ctx** out);
+
+/* Free all device and host memory of ctx (NULL is ignored).  Synchronises. */
+void semmg_destroy(semmg_ctx* ctx);
+
+/* Number of levels L+1 and the degree of a level. */
+int semmg_num_levels(const semmg_ctx* ctx, int* nlevels);
+int semmg_level_degree(const semmg_ctx* ctx, int level, int* p);
+
+/* Length of a condensed vector (skeleton slots, boundary ones included) and of
+ * a nodal array, at a level. */
+int semmg_condensed_size(const semmg_ctx* ctx, int level, int64_t* n);
+int semmg_nodal_size(const semmg_ctx* ctx, int level, int64_t* n);
+
+/* Condensed <-> nodal copies at a level (FP64).  pack reads the skeleton nodes
+ * of u_nodal (zero written on the Dirichlet boundary); unpack writes the
+ * skeleton nodes of u_nodal and leaves element-interior nodes untouched. */
+int semmg_pack(semmg_ctx* ctx, int level, const double* u_nodal, double* u_hat, void* stream);
+int semmg_unpack(semmg_ctx* ctx, int level, const double* u_hat, double* u_nodal, void* stream);
+
+/* y_hat = Hhat u_hat, Hhat = H_BB - H_BI H_II^{-1} H_IB the condensed operator
+ * (Sec. 2.2) applied matrix-free in O(p^3) per element, FP64.  y_hat must not
+ * alias u_hat. */
+int semmg_apply_condensed(semmg_ctx* ctx, int level, const double* u_hat, double* y_hat, void* stream);
+
+/* r_hat = f_hat - Hhat u_hat (Sec. 2.3, residual), FP64.  r_hat may alias f_hat. */
+int semmg_residual(semmg_ctx* ctx, int level, const double* f_hat, const double* u_hat,
+                   double* r_hat, void* stream);
+
+/* du_hat = Smoother(r_hat): Algorithm 2 around Algorithm 1 on the stars of all
+ * (n1+1)(n2+1)(n3+1) vertices of the level (Sec. 3.2), level >= 1.  dtype
+ * SEMMG_F64 or SEMMG_F32 gives the element type of both vectors and the
+ * arithmetic.  Overwrites du_hat (zero on the Dirichlet boundary). */
+int semmg_smooth(semmg_ctx* ctx, int level, int dtype, const void* r_hat, void* du_hat, void* stream);
+
+/* coarse = J^T fine: restriction from level `level` (>= 1) to level-1, the exact
+ * transpose of the embedded interpolation (Sec. 4.1).  Overwrites coarse. */
+int semmg_restrict(semmg_ctx* ctx, int level, int dtype, const void* fine, void* coarse, void* stream);
+
+/* fine += J coarse: prolongation from level-1 to level `level` (>= 1), the
+ * embedded 1D interpolation tensor product restricted to the skeleton. */
+int semmg_prolong_add(semmg_ctx* ctx, int level, int dtype, const void* coarse, void* fine, void* stream);
+
+/* u_hat0 = Hhat_0^{-1} f_hat0 on level 0, exact, FP64: the full degree-p0
+ * system with right-hand side (f_hat0 on the skeleton, 0 in the element
+ * interiors) solved by global fast diagonalisation; its skeleton part is the
+ * condensed solution (Sec. 3.1 embedding argument). */
+int semmg_coarse_solve(semmg_ctx* ctx, const double* f_hat0, double* u_hat0, void* stream);
+
+/* One V-cycle of Algorithm 3 on the finest level: u_hat <- MultigridCycle(u_hat, f_hat),
+ * computed as u_hat + MultigridCycle(0, f_hat - Hhat u_hat) (equal in exact
+ * arithmetic); the inner cycle runs in the context's precision. */
+int semmg_vcycle(semmg_ctx* ctx, double* u_hat, const double* f_hat, void* stream);
+
+/* f_hat = F_B - H_BI H_II^{-1} F_I with F = M f, M the assembled GLL mass and
+ * f_nodal the right-hand side at every GLL node (Algorithm 4, condensation). */
+int semmg_condense_rhs(semmg_ctx* ctx, const double* f_nodal, double* f_hat, void* stream);
+
+/* u_nodal = (u_hat, H_II^{-1}(F_I - H_IB u_hat)) (Algorithm 4, recovery); writes
+ * every node of u_nodal (0 on the Dirichlet boundary). */
+int semmg_recover(semmg_ctx* ctx, const double* f_nodal, const double* u_hat, double* u_nodal,
+                  void* stream);
+
+/* Algorithm 4: condense, V-cycles from u_hat = 0 until ||r|| <= rtol ||r_0||
+ * (Euclidean norm over the condensed unknowns, checked on the host after each
+ * cycle: one 8-byte device-to-host copy per cycle), recover.  f_nodal and
+ * u_nodal are device nodal arrays of the finest level.  info may be NULL.
+ * Returns SEMMG_ERR_NOT_CONVERGED after max_iter cycles (u_nodal still holds
+ * the last iterate), SEMMG_ERR_NONFINITE on a NaN/Inf residual norm. */
+int semmg_solve(semmg_ctx* ctx, const double* f_nodal, double* u_nodal, double rtol,
+                semmg_info* info, void* stream);
+
+/* semmg_solve with HOST nodal arrays: copies f to the device, solves, copies u
+ * back, and synchronises `stream` before returning. */
+int semmg_solve_host(semmg_ctx* ctx, const double* f_host, double* u_host, double rtol,
+                     semmg_info* info, void* stream);
+
+/* ------------------------------------------------------------------ timing
+ * Per-kernel-class timing with CUDA events recorded on the caller's stream
+ * around every launch the context makes (off by default; a few microseconds
+ * of host time per launch when on).  Each class also accumulates the
+ * algorithmic work of its launches: SEMMG_K_STAR counts 37 n_S^3 flops per
+ * star (Sec. 3.2 operation count of Algorithm 1); SEMMG_K_ELEM_SCHUR 73 m^3
+ * per element, m = p-1 (six 2D transforms each way, expansion and
+ * contraction); SEMMG_K_CONDENSE and SEMMG_K_RECOVER 12 p^4 + 25 p^3 per
+ * element (Sec. 4.2); bytes are the compulsory reads and writes of each
+ * launch's inputs and outputs. */
+enum {
+  SEMMG_K_STAR = 0,        /* Algorithm 1 on every star of a level */
+  SEMMG_K_STAR_GATHER,     /* weighted star outputs summed per skeleton node */
+  SEMMG_K_ELEM_SCHUR,      /* H_BI H_II^{-1} H_IB per element */
+  SEMMG_K_ASSEMBLE,        /* H_BB line sums + element terms per skeleton node */
+  SEMMG_K_TRANSFER,        /* restriction and prolongation */
+  SEMMG_K_COARSE,          /* coarse fast diagonalisation */
+  SEMMG_K_CONDENSE,        /* right-hand side condensation */
+  SEMMG_K_RECOVER,         /* interior recovery */
+  SEMMG_K_VECTOR,          /* copies, updates and norms */
+  SEMMG_K_COUNT
+};
+
+typedef struct {
+  double ms;         /* summed device time between the events around the launches */
+  int64_t launches;  /* kernel launches of this class */
+  double flops;      /* algorithmic flops of those launches */
+  double bytes;      /* compulsory bytes of those launches */
+} semmg_kstat;
+
+/* Switch timing on (1) or off (0); switching resets the statistics. */
+int semmg_set_timing(semmg_ctx* ctx, int enable);
+/* Statistics of one class since the last reset; synchronises the device
+ * with the last recorded event. */
+int semmg_get_kstat(semmg_ctx* ctx, int kind, semmg_kstat* out);
+int semmg_reset_kstats(semmg_ctx* ctx);
+
+/* Static message for an error code / last error message of a context. */
+const char* semmg_strerror(int code);
+const char* semmg_last_error(const semmg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEMMG_H */

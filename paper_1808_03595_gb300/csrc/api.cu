@@ -1,0 +1,790 @@
+// C ABI of the semmg library: context setup (level hierarchy of Sec. 4.1),
+// buffer management and the orchestration of Algorithms 2-4 on one stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "semmg_internal.h"
+#include "setup_host.h"
+
+namespace semmg {
+int set_elem_smem_limits();
+int set_star_smem_limits();
+int set_transfer_smem_limits();
+int64_t restrict_face_buffer(const Geo& Gf, int pc);
+int64_t restrict_edge_buffer(const Geo& Gf, int pc);
+}  // namespace semmg
+
+using namespace semmg;
+
+namespace {
+
+struct DevLevel {
+  Tabs<double> td{};
+  Tabs<float> tf{};
+  void* Fw = nullptr;  // V-cycle vectors in the working precision
+  void* Uw = nullptr;
+  void* Rw = nullptr;
+  LaunchCfg schur64, schur32, star64, star32;
+};
+
+Geo make_geo(const int n[3], int p, double lam) {
+  Geo g{};
+  g.p = p;
+  g.m = p - 1;
+  g.nS = 2 * p - 1;
+  g.n1 = n[0]; g.n2 = n[1]; g.n3 = n[2];
+  g.nv1 = n[0] + 1; g.nv2 = n[1] + 1; g.nv3 = n[2] + 1;
+  const int64_t m = g.m, mm = m * m;
+  g.oF1 = 0;
+  g.oF2 = g.oF1 + (int64_t)g.n3 * g.n2 * g.nv1 * mm;
+  g.oF3 = g.oF2 + (int64_t)g.n3 * g.nv2 * g.n1 * mm;
+  g.oE1 = g.oF3 + (int64_t)g.nv3 * g.n2 * g.n1 * mm;
+  g.oE2 = g.oE1 + (int64_t)g.nv3 * g.nv2 * g.n1 * m;
+  g.oE3 = g.oE2 + (int64_t)g.nv3 * g.n2 * g.nv1 * m;
+  g.oV = g.oE3 + (int64_t)g.n3 * g.nv2 * g.nv1 * m;
+  g.size = g.oV + (int64_t)g.nv1 * g.nv2 * g.nv3;
+  g.nelem = (int64_t)g.n1 * g.n2 * g.n3;
+  g.nstar = (int64_t)g.nv1 * g.nv2 * g.nv3;
+  g.pinv = ((1ull << 32) + (uint64_t)p - 1) / (uint64_t)p;
+  g.lam = lam;
+  return g;
+}
+
+}  // namespace
+
+struct semmg_ctx {
+  semmg_opts opts{};
+  double lam = 0;
+  int nsm = 0;
+  std::vector<double> h[3];
+  std::vector<Geo> geo;
+  std::vector<HostLevel> hl;
+  std::vector<DevLevel> dl;
+  HostCoarse hc;
+  CoarseTabs ct{};
+  std::vector<void*> allocs;
+  // shared scratch (sized in doubles for the largest level)
+  void* Zs = nullptr;
+  void* Obs = nullptr;
+  void* FBs = nullptr;
+  void* EBs = nullptr;
+  void* wss = nullptr;
+  LaunchCfg fdm;
+  // FP64 outer iteration
+  double* Fh = nullptr;
+  double* Uh = nullptr;
+  double* Rh = nullptr;
+  // coarse solve
+  double* cX = nullptr;
+  double* cY = nullptr;
+  double* F0d = nullptr;
+  double* U0d = nullptr;
+  // norms
+  double* part = nullptr;
+  int npart = 0;
+  double* dnorm = nullptr;
+  double* hnorm = nullptr;  // pinned
+  // host-buffer solve
+  double* fnod = nullptr;
+  double* unod = nullptr;
+  std::string err;
+  // timing
+  int timing = 0;
+  struct Pending { int kind; int ev; double flops, bytes; int64_t launches; };
+  std::vector<cudaEvent_t> events;
+  std::vector<Pending> pending;
+  int ev_used = 0;
+  semmg_kstat ks[SEMMG_K_COUNT] = {};
+
+  int L() const { return (int)geo.size() - 1; }
+
+  ~semmg_ctx() {
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+    for (void* p : allocs) cudaFree(p);
+    if (hnorm) cudaFreeHost(hnorm);
+    cudaGetLastError();
+  }
+};
+
+namespace {
+
+int fail(semmg_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+int check_cuda(semmg_ctx* c, const char* where) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, SEMMG_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+  return SEMMG_OK;
+}
+
+void* dalloc(semmg_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  c->allocs.push_back(p);
+  return p;
+}
+
+template <typename T>
+const T* upload(semmg_ctx* c, const std::vector<double>& v, bool* ok) {
+  std::vector<T> tmp(v.begin(), v.end());
+  T* d = (T*)dalloc(c, tmp.size() * sizeof(T));
+  if (!d) {
+    *ok = false;
+    return nullptr;
+  }
+  if (!tmp.empty() && cudaMemcpy(d, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    *ok = false;
+  return d;
+}
+
+const unsigned char* upload_u8(semmg_ctx* c, const std::vector<unsigned char>& v, bool* ok) {
+  unsigned char* d = (unsigned char*)dalloc(c, v.size());
+  if (!d) {
+    *ok = false;
+    return nullptr;
+  }
+  if (!v.empty() && cudaMemcpy(d, v.data(), v.size(), cudaMemcpyHostToDevice) != cudaSuccess) *ok = false;
+  return d;
+}
+
+template <typename T>
+Tabs<T> upload_tabs(semmg_ctx* c, const HostLevel& H, const std::vector<double>* h, bool* ok) {
+  Tabs<T> t{};
+  t.w = upload<T>(c, H.w, ok);
+  t.Ls = upload<T>(c, H.Ls, ok);
+  t.Sh = upload<T>(c, H.Sh, ok);
+  t.Sref = upload<T>(c, H.Sref, ok);
+  t.a0 = upload<T>(c, H.a0, ok);
+  t.ap = upload<T>(c, H.ap, ok);
+  t.lamI = upload<T>(c, H.lamI, ok);
+  for (int d = 0; d < 3; ++d) {
+    t.h[d] = upload<T>(c, h[d], ok);
+    t.starS[d] = upload<T>(c, H.starS[d], ok);
+    t.starLam[d] = upload<T>(c, H.starLam[d], ok);
+    t.act[d] = upload_u8(c, H.act[d], ok);
+  }
+  t.w1d = upload<T>(c, H.w1d, ok);
+  t.J = H.J.empty() ? nullptr : upload<T>(c, H.J, ok);
+  t.pc = H.pc;
+  return t;
+}
+
+int g_limits_done = 0;
+
+template <typename T> const Tabs<T>& tabs(const semmg_ctx* c, int l);
+template <> const Tabs<double>& tabs<double>(const semmg_ctx* c, int l) { return c->dl[l].td; }
+template <> const Tabs<float>& tabs<float>(const semmg_ctx* c, int l) { return c->dl[l].tf; }
+template <typename T> const LaunchCfg& schur_cfg(const semmg_ctx* c, int l);
+template <> const LaunchCfg& schur_cfg<double>(const semmg_ctx* c, int l) { return c->dl[l].schur64; }
+template <> const LaunchCfg& schur_cfg<float>(const semmg_ctx* c, int l) { return c->dl[l].schur32; }
+template <typename T> const LaunchCfg& star_cfg(const semmg_ctx* c, int l);
+template <> const LaunchCfg& star_cfg<double>(const semmg_ctx* c, int l) { return c->dl[l].star64; }
+template <> const LaunchCfg& star_cfg<float>(const semmg_ctx* c, int l) { return c->dl[l].star32; }
+
+struct Tic;
+int ev_get(semmg_ctx* c);
+
+// Algorithmic work per launch (see semmg.h, timing).
+double star_flops(const Geo& G) { return 37.0 * G.nS * (double)G.nS * G.nS * (double)G.nstar; }
+double schur_flops(const Geo& G) { return 73.0 * G.m * (double)G.m * G.m * (double)G.nelem; }
+double fdm_flops(const Geo& G) {
+  const double p = G.p;
+  return (12.0 * p * p * p * p + 25.0 * p * p * p) * (double)G.nelem;
+}
+
+}  // namespace
+namespace {
+
+bool valid_level(const semmg_ctx* c, int level) { return c && level >= 0 && level <= c->L(); }
+
+// ---- timing: an event pair around each launch group of one kernel class
+int ev_get(semmg_ctx* c) {
+  if (c->ev_used == (int)c->events.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    c->events.push_back(e);
+  }
+  return c->ev_used++;
+}
+
+struct Tic {
+  semmg_ctx* c;
+  int kind;
+  int ev = -1;
+  cudaStream_t st;
+  Tic(semmg_ctx* c_, int kind_, cudaStream_t st_) : c(c_), kind(kind_), st(st_) {
+    if (c->timing) {
+      ev = ev_get(c);
+      if (ev >= 0) cudaEventRecord(c->events[ev], st);
+    }
+  }
+  void toc(double flops, double bytes, int64_t launches = 1) {
+    if (!c->timing || ev < 0) return;
+    const int e1 = ev_get(c);
+    if (e1 < 0) return;
+    cudaEventRecord(c->events[e1], st);
+    c->pending.push_back({kind, ev, flops, bytes, launches});
+  }
+};
+
+void collect_timing(semmg_ctx* c) {
+  if (c->pending.empty()) return;
+  cudaEventSynchronize(c->events[c->ev_used - 1]);
+  for (const auto& p : c->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->events[p.ev], c->events[p.ev + 1]);
+    semmg_kstat& k = c->ks[p.kind];
+    k.ms += ms;
+    k.launches += p.launches;
+    k.flops += p.flops;
+    k.bytes += p.bytes;
+  }
+  c->pending.clear();
+  c->ev_used = 0;
+}
+
+// out = F - Hhat u (mode 0) or Hhat u (mode 1) on level l
+template <typename T>
+void op_residual(semmg_ctx* c, int l, const T* F, const T* u, T* out, int mode, cudaStream_t st) {
+  const Geo& G = c->geo[l];
+  const double vec = (double)G.size * sizeof(T);
+  const double zb = (double)G.nelem * 6 * G.m * G.m * sizeof(T);
+  {
+    Tic t(c, SEMMG_K_ELEM_SCHUR, st);
+    launch_elem_schur<T>(G, tabs<T>(c, l), u, (T*)c->Zs, (T*)c->wss, schur_cfg<T>(c, l), st);
+    t.toc(schur_flops(G), zb * 2, G.m > 0 ? 1 : 0);
+  }
+  Tic t(c, SEMMG_K_ASSEMBLE, st);
+  launch_assemble<T>(G, tabs<T>(c, l), F, u, (T*)c->Zs, out, mode, st);
+  t.toc(0.0, vec * (mode == 0 ? 3 : 2) + zb);
+}
+
+// du = Smoother(r) (accumulate: du += Smoother(r)) on level l >= 1
+template <typename T>
+void op_smooth(semmg_ctx* c, int l, const T* r, T* du, int accumulate, cudaStream_t st) {
+  const Geo& G = c->geo[l];
+  const double vec = (double)G.size * sizeof(T);
+  const double ob = (double)G.nstar * 3 * G.nS * G.nS * sizeof(T);
+  {
+    Tic t(c, SEMMG_K_STAR, st);
+    launch_star<T>(G, tabs<T>(c, l), r, (T*)c->Obs, (T*)c->wss, star_cfg<T>(c, l), st);
+    t.toc(star_flops(G), vec + ob);
+  }
+  Tic t(c, SEMMG_K_STAR_GATHER, st);
+  launch_star_gather<T>(G, (const T*)c->Obs, du, accumulate, st);
+  t.toc(0.0, ob + vec * (accumulate ? 2 : 1));
+}
+
+template <typename T>
+void op_restrict(semmg_ctx* c, int l, const T* fine, T* coarse, cudaStream_t st) {
+  Tic t(c, SEMMG_K_TRANSFER, st);
+  launch_restrict<T>(c->geo[l], c->geo[l - 1], tabs<T>(c, l), fine, coarse, (T*)c->FBs, (T*)c->EBs, st);
+  t.toc(0.0, (double)(c->geo[l].size + c->geo[l - 1].size) * sizeof(T), 3);
+}
+
+template <typename T>
+void op_prolong_add(semmg_ctx* c, int l, const T* coarse, T* fine, cudaStream_t st) {
+  Tic t(c, SEMMG_K_TRANSFER, st);
+  launch_prolong_add<T>(c->geo[l - 1], c->geo[l], tabs<T>(c, l), coarse, fine, st);
+  t.toc(0.0, (double)(2 * c->geo[l].size + c->geo[l - 1].size) * sizeof(T), 3);
+}
+
+template <typename T> void op_coarse(semmg_ctx* c, const T* F0, T* U0, cudaStream_t st);
+template <>
+void op_coarse<double>(semmg_ctx* c, const double* F0, double* U0, cudaStream_t st) {
+  Tic t(c, SEMMG_K_COARSE, st);
+  launch_coarse_solve(c->geo[0], c->ct, F0, U0, c->cX, c->cY, st);
+  t.toc(0.0, 2.0 * c->geo[0].size * sizeof(double), 8);
+}
+template <>
+void op_coarse<float>(semmg_ctx* c, const float* F0, float* U0, cudaStream_t st) {
+  const int64_t n = c->geo[0].size;
+  Tic t(c, SEMMG_K_COARSE, st);
+  launch_copy<double, float>(c->F0d, F0, n, st);
+  launch_coarse_solve(c->geo[0], c->ct, c->F0d, c->U0d, c->cX, c->cY, st);
+  launch_copy<float, double>(U0, c->U0d, n, st);
+  t.toc(0.0, 2.0 * n * sizeof(float), 10);
+}
+
+// Algorithm 3 with u_L = 0 on the residual held in Fw[L]: Uw[L] <- MultigridCycle(0, Fw[L]).
+template <typename T>
+void vcycle0(semmg_ctx* c, cudaStream_t st) {
+  const int L = c->L();
+  for (int l = L; l >= 1; --l) {
+    T* F = (T*)c->dl[l].Fw;
+    T* U = (T*)c->dl[l].Uw;
+    T* R = (T*)c->dl[l].Rw;
+    const int64_t n = c->geo[l].size;
+    if (c->opts.nu_pre >= 1) {
+      op_smooth<T>(c, l, F, U, 0, st);  // u_l = 0 + Smoother(F_l - H_l 0)
+      for (int i = 1; i < c->opts.nu_pre; ++i) {
+        op_residual<T>(c, l, F, U, R, 0, st);
+        op_smooth<T>(c, l, R, U, 1, st);
+      }
+    } else {
+      cudaMemsetAsync(U, 0, n * sizeof(T), st);
+    }
+    op_residual<T>(c, l, F, U, R, 0, st);
+    op_restrict<T>(c, l, R, (T*)c->dl[l - 1].Fw, st);
+  }
+  op_coarse<T>(c, (const T*)c->dl[0].Fw, (T*)c->dl[0].Uw, st);
+  for (int l = 1; l <= L; ++l) {
+    T* F = (T*)c->dl[l].Fw;
+    T* U = (T*)c->dl[l].Uw;
+    T* R = (T*)c->dl[l].Rw;
+    op_prolong_add<T>(c, l, (const T*)c->dl[l - 1].Uw, U, st);
+    for (int i = 0; i < c->opts.nu_post; ++i) {
+      op_residual<T>(c, l, F, U, R, 0, st);
+      op_smooth<T>(c, l, R, U, 1, st);
+    }
+  }
+}
+
+// u += MultigridCycle(0, r) with r in Rh (FP64); the cycle runs in the context precision.
+void correction(semmg_ctx* c, double* u, const double* r, cudaStream_t st) {
+  const int L = c->L();
+  const int64_t n = c->geo[L].size;
+  const size_t es = c->opts.precision == SEMMG_MIXED ? sizeof(float) : sizeof(double);
+  {
+    Tic t(c, SEMMG_K_VECTOR, st);
+    if (c->opts.precision == SEMMG_MIXED)
+      launch_copy<float, double>((float*)c->dl[L].Fw, r, n, st);
+    else
+      launch_copy<double, double>((double*)c->dl[L].Fw, r, n, st);
+    t.toc(0.0, (double)n * (8 + es));
+  }
+  if (c->opts.precision == SEMMG_MIXED)
+    vcycle0<float>(c, st);
+  else
+    vcycle0<double>(c, st);
+  Tic t(c, SEMMG_K_VECTOR, st);
+  if (c->opts.precision == SEMMG_MIXED)
+    launch_axpy<double, float>(u, (const float*)c->dl[L].Uw, 1.0, n, st);
+  else
+    launch_axpy<double, double>(u, (const double*)c->dl[L].Uw, 1.0, n, st);
+  t.toc(0.0, (double)n * (16 + es));
+}
+
+int norm2_sync(semmg_ctx* c, const double* x, int64_t n, cudaStream_t st, double* out) {
+  Tic t(c, SEMMG_K_VECTOR, st);
+  launch_norm2<double>(x, n, c->part, c->npart, c->dnorm, st);
+  t.toc(2.0 * n, 8.0 * n, 2);
+  cudaMemcpyAsync(c->hnorm, c->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return check_cuda(c, "norm");
+  *out = std::sqrt(*c->hnorm);
+  return check_cuda(c, "norm");
+}
+
+int set_limits(semmg_ctx* c) {
+  if (g_limits_done) return SEMMG_OK;
+  if (set_elem_smem_limits() | set_star_smem_limits() | set_transfer_smem_limits())
+    return fail(c, SEMMG_ERR_CUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
+  g_limits_done = 1;
+  return SEMMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void semmg_default_opts(semmg_opts* o) {
+  if (!o) return;
+  o->p0 = 2;
+  o->nu_pre = 1;
+  o->nu_post = 1;
+  o->precision = SEMMG_FP64;
+  o->max_iter = 50;
+}
+
+int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* opts, void* stream,
+                semmg_ctx** out) {
+  if (!out) return SEMMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!mesh) return SEMMG_ERR_INVALID_ARG;
+  semmg_opts o;
+  semmg_default_opts(&o);
+  if (opts) o = *opts;
+  if (p < 1 || p > SEMMG_MAX_DEGREE) return SEMMG_ERR_UNSUPPORTED;
+  if (o.p0 < 1 || o.p0 > p) return SEMMG_ERR_UNSUPPORTED;
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) return SEMMG_ERR_INVALID_ARG;
+  if (o.nu_pre < 0 || o.nu_post < 0 || o.max_iter < 1) return SEMMG_ERR_INVALID_ARG;
+  if (o.precision != SEMMG_FP64 && o.precision != SEMMG_MIXED) return SEMMG_ERR_INVALID_ARG;
+  for (int d = 0; d < 3; ++d) {
+    if (mesh->n[d] < 1 || !mesh->h[d]) return SEMMG_ERR_INVALID_ARG;
+    if ((int64_t)mesh->n[d] * p + 1 >= (1 << 20)) return SEMMG_ERR_UNSUPPORTED;
+    for (int a = 0; a < mesh->n[d]; ++a)
+      if (!(mesh->h[d][a] > 0.0) || !std::isfinite(mesh->h[d][a])) return SEMMG_ERR_INVALID_ARG;
+  }
+  std::unique_ptr<semmg_ctx> c(new (std::nothrow) semmg_ctx());
+  if (!c) return SEMMG_ERR_NOMEM;
+  c->opts = o;
+  c->lam = lambda;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SEMMG_ERR_CUDA;
+  }
+  if (set_limits(c.get()) != SEMMG_OK) return SEMMG_ERR_CUDA;
+  for (int d = 0; d < 3; ++d) c->h[d].assign(mesh->h[d], mesh->h[d] + mesh->n[d]);
+  // level degrees (Sec. 4.1): p0 2^l while below p, then p
+  std::vector<int> degs{o.p0};
+  while (degs.back() * 2 < p) degs.push_back(degs.back() * 2);
+  if (degs.back() != p) degs.push_back(p);
+  const int nl = (int)degs.size();
+  c->geo.resize(nl);
+  c->hl.resize(nl);
+  c->dl.resize(nl);
+  for (int l = 0; l < nl; ++l) {
+    c->geo[l] = make_geo(mesh->n, degs[l], lambda);
+    c->hl[l].p = degs[l];
+    build_level_tables(c->hl[l], c->h);
+    if (l > 0) {
+      lagrange_interp(c->hl[l - 1].x, c->hl[l].x, c->hl[l].J);
+      c->hl[l].pc = degs[l - 1];
+    }
+  }
+  build_coarse_tables(degs[0], c->h, c->hc);
+  bool ok = true;
+  for (int l = 0; l < nl; ++l) {
+    c->dl[l].td = upload_tabs<double>(c.get(), c->hl[l], c->h, &ok);
+    c->dl[l].tf = upload_tabs<float>(c.get(), c->hl[l], c->h, &ok);
+  }
+  for (int d = 0; d < 3; ++d) {
+    c->ct.K[d] = c->hc.K[d];
+    c->ct.S[d] = upload<double>(c.get(), c->hc.S[d], &ok);
+    c->ct.lam[d] = upload<double>(c.get(), c->hc.lam[d], &ok);
+  }
+  if (!ok) return SEMMG_ERR_NOMEM;
+  // launch plans and scratch sizes
+  size_t zs = 0, obs = 0, fbs = 0, ebs = 0, wsb = 0;
+  for (int l = 0; l < nl; ++l) {
+    const Geo& G = c->geo[l];
+    DevLevel& D = c->dl[l];
+    D.schur64 = plan_elem_schur<double>(G, c->nsm);
+    D.schur32 = plan_elem_schur<float>(G, c->nsm);
+    wsb = std::max(wsb, D.schur64.ws_elems() * sizeof(double));
+    wsb = std::max(wsb, D.schur32.ws_elems() * sizeof(float));
+    zs = std::max(zs, (size_t)(G.nelem * 6 * (int64_t)G.m * G.m));
+    if (l >= 1) {
+      D.star64 = plan_star<double>(G, c->nsm);
+      D.star32 = plan_star<float>(G, c->nsm);
+      wsb = std::max(wsb, D.star64.ws_elems() * sizeof(double));
+      wsb = std::max(wsb, D.star32.ws_elems() * sizeof(float));
+      obs = std::max(obs, (size_t)(G.nstar * 3 * (int64_t)G.nS * G.nS));
+      fbs = std::max(fbs, (size_t)restrict_face_buffer(G, degs[l - 1]));
+      ebs = std::max(ebs, (size_t)restrict_edge_buffer(G, degs[l - 1]));
+    }
+  }
+  c->fdm = plan_elem_fdm(c->geo[nl - 1], c->nsm);
+  for (int l = 0; l < nl; ++l) {
+    const DevLevel& D = c->dl[l];
+    if (!D.schur64.ok || !D.schur32.ok || (l >= 1 && (!D.star64.ok || !D.star32.ok)))
+      return SEMMG_ERR_UNSUPPORTED;
+  }
+  if (!c->fdm.ok) return SEMMG_ERR_UNSUPPORTED;
+  wsb = std::max(wsb, c->fdm.ws_elems() * sizeof(double));
+  c->Zs = dalloc(c.get(), zs * sizeof(double));
+  c->Obs = dalloc(c.get(), obs * sizeof(double));
+  c->FBs = dalloc(c.get(), fbs * sizeof(double));
+  c->EBs = dalloc(c.get(), ebs * sizeof(double));
+  c->wss = dalloc(c.get(), wsb);
+  const size_t esz = o.precision == SEMMG_MIXED ? sizeof(float) : sizeof(double);
+  for (int l = 0; l < nl; ++l) {
+    const size_t n = (size_t)c->geo[l].size;
+    c->dl[l].Fw = dalloc(c.get(), n * esz);
+    c->dl[l].Uw = dalloc(c.get(), n * esz);
+    c->dl[l].Rw = dalloc(c.get(), n * esz);
+    if (!c->dl[l].Fw || !c->dl[l].Uw || !c->dl[l].Rw) return SEMMG_ERR_NOMEM;
+  }
+  const size_t nL = (size_t)c->geo[nl - 1].size;
+  c->Fh = (double*)dalloc(c.get(), nL * sizeof(double));
+  c->Uh = (double*)dalloc(c.get(), nL * sizeof(double));
+  c->Rh = (double*)dalloc(c.get(), nL * sizeof(double));
+  const size_t nK = (size_t)c->ct.K[0] * c->ct.K[1] * c->ct.K[2];
+  c->cX = (double*)dalloc(c.get(), nK * sizeof(double));
+  c->cY = (double*)dalloc(c.get(), nK * sizeof(double));
+  c->F0d = (double*)dalloc(c.get(), (size_t)c->geo[0].size * sizeof(double));
+  c->U0d = (double*)dalloc(c.get(), (size_t)c->geo[0].size * sizeof(double));
+  c->npart = 512;
+  c->part = (double*)dalloc(c.get(), c->npart * sizeof(double));
+  c->dnorm = (double*)dalloc(c.get(), sizeof(double));
+  if (!c->Zs || !c->Obs || !c->FBs || !c->EBs || !c->wss || !c->Fh || !c->Uh || !c->Rh || !c->cX || !c->cY ||
+      !c->F0d || !c->U0d || !c->part || !c->dnorm)
+    return SEMMG_ERR_NOMEM;
+  if (cudaMallocHost((void**)&c->hnorm, sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    c->hnorm = nullptr;
+    return SEMMG_ERR_NOMEM;
+  }
+  *c->hnorm = 0.0;
+  for (int l = 0; l < nl; ++l) {
+    const size_t n = (size_t)c->geo[l].size;
+    cudaMemsetAsync(c->dl[l].Fw, 0, n * esz, st);
+    cudaMemsetAsync(c->dl[l].Uw, 0, n * esz, st);
+    cudaMemsetAsync(c->dl[l].Rw, 0, n * esz, st);
+  }
+  cudaMemsetAsync(c->Fh, 0, nL * sizeof(double), st);
+  cudaMemsetAsync(c->Uh, 0, nL * sizeof(double), st);
+  cudaMemsetAsync(c->Rh, 0, nL * sizeof(double), st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return SEMMG_ERR_CUDA;
+  }
+  *out = c.release();
+  return SEMMG_OK;
+}
+
+void semmg_destroy(semmg_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  delete c;
+}
+
+int semmg_num_levels(const semmg_ctx* c, int* nl) {
+  if (!c || !nl) return SEMMG_ERR_INVALID_ARG;
+  *nl = (int)c->geo.size();
+  return SEMMG_OK;
+}
+
+int semmg_level_degree(const semmg_ctx* c, int level, int* p) {
+  if (!valid_level(c, level) || !p) return SEMMG_ERR_INVALID_ARG;
+  *p = c->geo[level].p;
+  return SEMMG_OK;
+}
+
+int semmg_condensed_size(const semmg_ctx* c, int level, int64_t* n) {
+  if (!valid_level(c, level) || !n) return SEMMG_ERR_INVALID_ARG;
+  *n = c->geo[level].size;
+  return SEMMG_OK;
+}
+
+int semmg_nodal_size(const semmg_ctx* c, int level, int64_t* n) {
+  if (!valid_level(c, level) || !n) return SEMMG_ERR_INVALID_ARG;
+  const Geo& G = c->geo[level];
+  *n = (int64_t)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
+  return SEMMG_OK;
+}
+
+int semmg_pack(semmg_ctx* c, int level, const double* u_nodal, double* u_hat, void* stream) {
+  if (!valid_level(c, level) || !u_nodal || !u_hat) return SEMMG_ERR_INVALID_ARG;
+  launch_pack(c->geo[level], u_nodal, u_hat, (cudaStream_t)stream);
+  return check_cuda(c, "pack");
+}
+
+int semmg_unpack(semmg_ctx* c, int level, const double* u_hat, double* u_nodal, void* stream) {
+  if (!valid_level(c, level) || !u_nodal || !u_hat) return SEMMG_ERR_INVALID_ARG;
+  launch_unpack(c->geo[level], u_hat, u_nodal, (cudaStream_t)stream);
+  return check_cuda(c, "unpack");
+}
+
+int semmg_apply_condensed(semmg_ctx* c, int level, const double* u, double* y, void* stream) {
+  if (!valid_level(c, level) || !u || !y || u == y) return SEMMG_ERR_INVALID_ARG;
+  op_residual<double>(c, level, nullptr, u, y, 1, (cudaStream_t)stream);
+  return check_cuda(c, "apply_condensed");
+}
+
+int semmg_residual(semmg_ctx* c, int level, const double* f, const double* u, double* r, void* stream) {
+  if (!valid_level(c, level) || !f || !u || !r || u == r) return SEMMG_ERR_INVALID_ARG;
+  op_residual<double>(c, level, f, u, r, 0, (cudaStream_t)stream);
+  return check_cuda(c, "residual");
+}
+
+int semmg_smooth(semmg_ctx* c, int level, int dtype, const void* r, void* du, void* stream) {
+  if (!valid_level(c, level) || level < 1 || !r || !du || r == du) return SEMMG_ERR_INVALID_ARG;
+  if (dtype == SEMMG_F64)
+    op_smooth<double>(c, level, (const double*)r, (double*)du, 0, (cudaStream_t)stream);
+  else if (dtype == SEMMG_F32)
+    op_smooth<float>(c, level, (const float*)r, (float*)du, 0, (cudaStream_t)stream);
+  else
+    return SEMMG_ERR_INVALID_ARG;
+  return check_cuda(c, "smooth");
+}
+
+int semmg_restrict(semmg_ctx* c, int level, int dtype, const void* fine, void* coarse, void* stream) {
+  if (!valid_level(c, level) || level < 1 || !fine || !coarse) return SEMMG_ERR_INVALID_ARG;
+  if (dtype == SEMMG_F64)
+    op_restrict<double>(c, level, (const double*)fine, (double*)coarse, (cudaStream_t)stream);
+  else if (dtype == SEMMG_F32)
+    op_restrict<float>(c, level, (const float*)fine, (float*)coarse, (cudaStream_t)stream);
+  else
+    return SEMMG_ERR_INVALID_ARG;
+  return check_cuda(c, "restrict");
+}
+
+int semmg_prolong_add(semmg_ctx* c, int level, int dtype, const void* coarse, void* fine, void* stream) {
+  if (!valid_level(c, level) || level < 1 || !fine || !coarse) return SEMMG_ERR_INVALID_ARG;
+  if (dtype == SEMMG_F64)
+    op_prolong_add<double>(c, level, (const double*)coarse, (double*)fine, (cudaStream_t)stream);
+  else if (dtype == SEMMG_F32)
+    op_prolong_add<float>(c, level, (const float*)coarse, (float*)fine, (cudaStream_t)stream);
+  else
+    return SEMMG_ERR_INVALID_ARG;
+  return check_cuda(c, "prolong_add");
+}
+
+int semmg_coarse_solve(semmg_ctx* c, const double* f0, double* u0, void* stream) {
+  if (!c || !f0 || !u0 || f0 == u0) return SEMMG_ERR_INVALID_ARG;
+  op_coarse<double>(c, f0, u0, (cudaStream_t)stream);
+  return check_cuda(c, "coarse_solve");
+}
+
+int semmg_vcycle(semmg_ctx* c, double* u, const double* f, void* stream) {
+  if (!c || !u || !f) return SEMMG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = c->L();
+  op_residual<double>(c, L, f, u, c->Rh, 0, st);
+  correction(c, u, c->Rh, st);
+  return check_cuda(c, "vcycle");
+}
+
+int semmg_condense_rhs(semmg_ctx* c, const double* f, double* fh, void* stream) {
+  if (!c || !f || !fh) return SEMMG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = c->L();
+  const Geo& G = c->geo[L];
+  const double nn = (double)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
+  Tic t(c, SEMMG_K_CONDENSE, st);
+  launch_elem_condense(G, c->dl[L].td, f, (double*)c->Zs, (double*)c->wss, c->fdm, st);
+  launch_assemble_rhs(G, c->dl[L].td, f, (const double*)c->Zs, fh, st);
+  t.toc(G.m > 0 ? fdm_flops(G) : 0.0, 8.0 * (nn + G.size), 2);
+  return check_cuda(c, "condense_rhs");
+}
+
+int semmg_recover(semmg_ctx* c, const double* f, const double* uh, double* u, void* stream) {
+  if (!c || !f || !uh || !u) return SEMMG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = c->L();
+  const Geo& G = c->geo[L];
+  const double nn = (double)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
+  Tic t(c, SEMMG_K_RECOVER, st);
+  launch_unpack(G, uh, u, st);
+  launch_elem_recover(G, c->dl[L].td, f, uh, u, (double*)c->wss, c->fdm, st);
+  t.toc(G.m > 0 ? fdm_flops(G) : 0.0, 8.0 * (2 * nn + G.size), 2);
+  return check_cuda(c, "recover");
+}
+
+int semmg_solve(semmg_ctx* c, const double* f, double* u, double rtol, semmg_info* info, void* stream) {
+  if (!c || !f || !u || !(rtol > 0.0)) return SEMMG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = c->L();
+  const int64_t n = c->geo[L].size;
+  int rc = semmg_condense_rhs(c, f, c->Fh, stream);
+  if (rc) return rc;
+  cudaMemsetAsync(c->Uh, 0, n * sizeof(double), st);
+  double r0 = 0.0, rn = 0.0;
+  rc = norm2_sync(c, c->Fh, n, st, &r0);  // r_0 = Fhat - Hhat 0
+  if (rc) return rc;
+  int it = 0;
+  int status = SEMMG_OK;
+  if (!std::isfinite(r0)) status = SEMMG_ERR_NONFINITE;
+  rn = r0;
+  const double* r = c->Fh;
+  while (status == SEMMG_OK && rn > rtol * r0 && it < c->opts.max_iter) {
+    correction(c, c->Uh, r, st);
+    op_residual<double>(c, L, c->Fh, c->Uh, c->Rh, 0, st);
+    r = c->Rh;
+    rc = norm2_sync(c, c->Rh, n, st, &rn);
+    if (rc) return rc;
+    ++it;
+    if (!std::isfinite(rn)) status = SEMMG_ERR_NONFINITE;
+  }
+  if (status == SEMMG_OK && rn > rtol * r0) status = SEMMG_ERR_NOT_CONVERGED;
+  rc = semmg_recover(c, f, c->Uh, u, stream);
+  if (rc) return rc;
+  if (info) {
+    info->iters = it;
+    info->res0 = r0;
+    info->res_final = rn;
+    info->rho = (it > 0 && r0 > 0) ? std::pow(rn / r0, 1.0 / it) : 0.0;
+    info->status = status;
+  }
+  if (status != SEMMG_OK) fail(c, status, "solve: %s after %d cycles", semmg_strerror(status), it);
+  return status;
+}
+
+int semmg_solve_host(semmg_ctx* c, const double* f_host, double* u_host, double rtol, semmg_info* info,
+                     void* stream) {
+  if (!c || !f_host || !u_host) return SEMMG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t nn = 0;
+  semmg_nodal_size(c, c->L(), &nn);
+  if (!c->fnod) {
+    c->fnod = (double*)dalloc(c, nn * sizeof(double));
+    c->unod = (double*)dalloc(c, nn * sizeof(double));
+    if (!c->fnod || !c->unod) return fail(c, SEMMG_ERR_NOMEM, "solve_host: device buffers");
+  }
+  cudaMemcpyAsync(c->fnod, f_host, nn * sizeof(double), cudaMemcpyHostToDevice, st);
+  const int rc = semmg_solve(c, c->fnod, c->unod, rtol, info, stream);
+  if (rc != SEMMG_OK && rc != SEMMG_ERR_NOT_CONVERGED && rc != SEMMG_ERR_NONFINITE) return rc;
+  cudaMemcpyAsync(u_host, c->unod, nn * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return check_cuda(c, "solve_host");
+  return rc;
+}
+
+const char* semmg_strerror(int code) {
+  switch (code) {
+    case SEMMG_OK: return "success";
+    case SEMMG_ERR_INVALID_ARG: return "invalid argument";
+    case SEMMG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case SEMMG_ERR_CUDA: return "CUDA error";
+    case SEMMG_ERR_NOT_CONVERGED: return "not converged";
+    case SEMMG_ERR_NONFINITE: return "non-finite residual";
+    case SEMMG_ERR_TIMEOUT: return "device wait timed out";
+    case SEMMG_ERR_NOMEM: return "out of memory";
+    default: return "unknown error";
+  }
+}
+
+const char* semmg_last_error(const semmg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"
+
+extern "C" {
+
+int semmg_set_timing(semmg_ctx* c, int enable) {
+  if (!c) return SEMMG_ERR_INVALID_ARG;
+  collect_timing(c);
+  c->timing = enable ? 1 : 0;
+  for (auto& k : c->ks) k = semmg_kstat{};
+  return check_cuda(c, "set_timing");
+}
+
+int semmg_get_kstat(semmg_ctx* c, int kind, semmg_kstat* out) {
+  if (!c || !out || kind < 0 || kind >= SEMMG_K_COUNT) return SEMMG_ERR_INVALID_ARG;
+  collect_timing(c);
+  *out = c->ks[kind];
+  return check_cuda(c, "get_kstat");
+}
+
+int semmg_reset_kstats(semmg_ctx* c) {
+  if (!c) return SEMMG_ERR_INVALID_ARG;
+  collect_timing(c);
+  for (auto& k : c->ks) k = semmg_kstat{};
+  return check_cuda(c, "reset_kstats");
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+// Internal declarations of the semmg CUDA library: level geometry, device
+// tables, skeleton indexing and kernel launchers.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "semmg.h"
+
+namespace semmg {
+
+#define SEMMG_HD __host__ __device__ __forceinline__
+
+// ---------------------------------------------------------------- geometry
+// One level of the hierarchy on the tensor-product mesh: degree p, m = p-1
+// interior nodes per element edge, n_S = 2p-1 star points per direction
+// (Sec. 2.3), and the offsets of the entity groups of a condensed vector
+// (layout documented in semmg.h).
+struct Geo {
+  int p, m, nS;
+  int n1, n2, n3;
+  int nv1, nv2, nv3;
+  int64_t oF1, oF2, oF3, oE1, oE2, oE3, oV, size;
+  int64_t nelem, nstar;
+  uint64_t pinv;  // ceil(2^32 / p): exact division g / p for 0 <= g < 2^20
+  double lam;
+};
+
+enum EntityType { ENT_F1 = 0, ENT_F2, ENT_F3, ENT_E1, ENT_E2, ENT_E3, ENT_V, ENT_NONE };
+
+SEMMG_HD int divp(const Geo& G, int g) {
+  return (int)(((unsigned long long)(unsigned)g * G.pinv) >> 32);
+}
+
+// Skeleton slot of the global GLL node (g1, g2, g3), or -1 for an element
+// interior node.  `type` receives the entity group.
+SEMMG_HD int64_t skel_index(const Geo& G, int g1, int g2, int g3, int* type = nullptr) {
+  const int a1 = divp(G, g1), a2 = divp(G, g2), a3 = divp(G, g3);
+  const int q1 = g1 - a1 * G.p, q2 = g2 - a2 * G.p, q3 = g3 - a3 * G.p;
+  const int m = G.m;
+  const int64_t mm = (int64_t)m * m;
+  const int v1 = (q1 == 0), v2 = (q2 == 0), v3 = (q3 == 0);
+  const int cnt = v1 + v2 + v3;
+  int t = ENT_NONE;
+  int64_t s = -1;
+  if (cnt == 3) {
+    t = ENT_V;
+    s = G.oV + ((int64_t)a3 * G.nv2 + a2) * G.nv1 + a1;
+  } else if (cnt == 2) {
+    if (!v1) {
+      t = ENT_E1;
+      s = G.oE1 + (((int64_t)a3 * G.nv2 + a2) * G.n1 + a1) * m + (q1 - 1);
+    } else if (!v2) {
+      t = ENT_E2;
+      s = G.oE2 + (((int64_t)a3 * G.n2 + a2) * G.nv1 + a1) * m + (q2 - 1);
+    } else {
+      t = ENT_E3;
+      s = G.oE3 + (((int64_t)a3 * G.nv2 + a2) * G.nv1 + a1) * m + (q3 - 1);
+    }
+  } else if (cnt == 1) {
+    if (v1) {
+      t = ENT_F1;
+      s = G.oF1 + (((int64_t)a3 * G.n2 + a2) * G.nv1 + a1) * mm + (int64_t)(q3 - 1) * m + (q2 - 1);
+    } else if (v2) {
+      t = ENT_F2;
+      s = G.oF2 + (((int64_t)a3 * G.nv2 + a2) * G.n1 + a1) * mm + (int64_t)(q3 - 1) * m + (q1 - 1);
+    } else {
+      t = ENT_F3;
+      s = G.oF3 + (((int64_t)a3 * G.n2 + a2) * G.n1 + a1) * mm + (int64_t)(q2 - 1) * m + (q1 - 1);
+    }
+  }
+  if (type) *type = t;
+  return s;
+}
+
+// Index stride of a run of nodes along axis d (0-based) inside one entity.
+SEMMG_HD int run_stride(const Geo& G, int type, int d) {
+  switch (type) {
+    case ENT_F1: return d == 1 ? 1 : G.m;
+    case ENT_F2: return d == 0 ? 1 : G.m;
+    case ENT_F3: return d == 0 ? 1 : G.m;
+    default: return 1;
+  }
+}
+
+// Decode a skeleton slot into its global node coordinates; returns the entity
+// type and whether the node lies on the Dirichlet boundary.
+SEMMG_HD int skel_decode(const Geo& G, int64_t s, int* g, bool* bdry) {
+  const int p = G.p, m = G.m;
+  const int64_t mm = (int64_t)m * m;
+  int t;
+  int c1 = 0, c2 = 0, c3 = 0;  // plane / element coordinates
+  if (s < G.oF2) {
+    t = ENT_F1;
+    int64_t r = s - G.oF1;
+    const int64_t f = r / mm, w = r - f * mm;
+    const int i3 = (int)(w / m), i2 = (int)(w - (int64_t)i3 * m);
+    c1 = (int)(f % G.nv1);
+    const int64_t f2 = f / G.nv1;
+    const int a2 = (int)(f2 % G.n2), a3 = (int)(f2 / G.n2);
+    g[0] = c1 * p; g[1] = a2 * p + i2 + 1; g[2] = a3 * p + i3 + 1;
+    *bdry = (c1 == 0 || c1 == G.n1);
+  } else if (s < G.oF3) {
+    t = ENT_F2;
+    int64_t r = s - G.oF2;
+    const int64_t f = r / mm, w = r - f * mm;
+    const int i3 = (int)(w / m), i1 = (int)(w - (int64_t)i3 * m);
+    const int a1 = (int)(f % G.n1);
+    const int64_t f2 = f / G.n1;
+    c2 = (int)(f2 % G.nv2);
+    const int a3 = (int)(f2 / G.nv2);
+    g[0] = a1 * p + i1 + 1; g[1] = c2 * p; g[2] = a3 * p + i3 + 1;
+    *bdry = (c2 == 0 || c2 == G.n2);
+  } else if (s < G.oE1) {
+    t = ENT_F3;
+    int64_t r = s - G.oF3;
+    const int64_t f = r / mm, w = r - f * mm;
+    const int i2 = (int)(w / m), i1 = (int)(w - (int64_t)i2 * m);
+    const int a1 = (int)(f % G.n1);
+    const int64_t f2 = f / G.n1;
+    const int a2 = (int)(f2 % G.n2);
+    c3 = (int)(f2 / G.n2);
+    g[0] = a1 * p + i1 + 1; g[1] = a2 * p + i2 + 1; g[2] = c3 * p;
+    *bdry = (c3 == 0 || c3 == G.n3);
+  } else if (s < G.oE2) {
+    t = ENT_E1;
+    int64_t r = s - G.oE1;
+    const int64_t e = r / m;
+    const int i1 = (int)(r - e * m);
+    const int a1 = (int)(e % G.n1);
+    const int64_t e2 = e / G.n1;
+    c2 = (int)(e2 % G.nv2);
+    c3 = (int)(e2 / G.nv2);
+    g[0] = a1 * p + i1 + 1; g[1] = c2 * p; g[2] = c3 * p;
+    *bdry = (c2 == 0 || c2 == G.n2 || c3 == 0 || c3 == G.n3);
+  } else if (s < G.oE3) {
+    t = ENT_E2;
+    int64_t r = s - G.oE2;
+    const int64_t e = r / m;
+    const int i2 = (int)(r - e * m);
+    c1 = (int)(e % G.nv1);
+    const int64_t e2 = e / G.nv1;
+    const int a2 = (int)(e2 % G.n2);
+    c3 = (int)(e2 / G.n2);
+    g[0] = c1 * p; g[1] = a2 * p + i2 + 1; g[2] = c3 * p;
+    *bdry = (c1 == 0 || c1 == G.n1 || c3 == 0 || c3 == G.n3);
+  } else if (s < G.oV) {
+    t = ENT_E3;
+    int64_t r = s - G.oE3;
+    const int64_t e = r / m;
+    const int i3 = (int)(r - e * m);
+    c1 = (int)(e % G.nv1);
+    const int64_t e2 = e / G.nv1;
+    c2 = (int)(e2 % G.nv2);
+    const int a3 = (int)(e2 / G.nv2);
+    g[0] = c1 * p; g[1] = c2 * p; g[2] = a3 * p + i3 + 1;
+    *bdry = (c1 == 0 || c1 == G.n1 || c2 == 0 || c2 == G.n2);
+  } else {
+    t = ENT_V;
+    int64_t r = s - G.oV;
+    c1 = (int)(r % G.nv1);
+    const int64_t r2 = r / G.nv1;
+    c2 = (int)(r2 % G.nv2);
+    c3 = (int)(r2 / G.nv2);
+    g[0] = c1 * p; g[1] = c2 * p; g[2] = c3 * p;
+    *bdry = (c1 == 0 || c1 == G.n1 || c2 == 0 || c2 == G.n2 || c3 == 0 || c3 == G.n3);
+  }
+  return t;
+}
+
+// Base slot of a face of element (a1,a2,a3); f = 2d + side, side 0 at local
+// index 0, side 1 at local index p along axis d.
+SEMMG_HD int64_t elem_face_base(const Geo& G, int a1, int a2, int a3, int f) {
+  const int64_t mm = (int64_t)G.m * G.m;
+  const int side = f & 1;
+  switch (f >> 1) {
+    case 0: return G.oF1 + (((int64_t)a3 * G.n2 + a2) * G.nv1 + a1 + side) * mm;
+    case 1: return G.oF2 + (((int64_t)a3 * G.nv2 + a2 + side) * G.n1 + a1) * mm;
+    default: return G.oF3 + (((int64_t)(a3 + side) * G.n2 + a2) * G.n1 + a1) * mm;
+  }
+}
+
+// ---------------------------------------------------------------- tables
+// Device tables of one level in one precision.
+template <typename T>
+struct Tabs {
+  const T* w;      // GLL weights, p+1
+  const T* Ls;     // standard-element stiffness, (p+1)^2 row-major
+  const T* Sh;     // m x m: Sh[i][k] = w[i+1] Sref[i][k]
+  const T* Sref;   // m x m: interior generalised eigenvectors, Sref^T M_II Sref = I
+  const T* a0;     // m: sum_i Sref[i][k] Ls[i+1][0]
+  const T* ap;     // m: sum_i Sref[i][k] Ls[i+1][p]
+  const T* lamI;   // m: interior eigenvalues
+  const T* h[3];   // element widths per axis
+  const T* starS[3];    // per axis: nv_d blocks of nS x nS, S[j][k], row j <-> offset j-m
+  const T* starLam[3];  // per axis: nv_d x nS
+  const unsigned char* act[3];  // per axis: nv_d x nS active flags
+  const T* w1d;    // m+1: smoother weight at offset |j| (Sec. 3.2, weights)
+  const T* J;      // (p+1) x (pc+1) interpolation from level-1, row-major; null on level 0
+  int pc;
+};
+
+// Coarse fast-diagonalisation tables (level 0, FP64): K_d = n_d p0 - 1
+// interior grid points per axis.
+struct CoarseTabs {
+  int K[3];
+  const double* S[3];    // K_d x K_d, S[g][k]
+  const double* lam[3];  // K_d
+};
+
+// ---------------------------------------------------------------- launchers
+// Per-CTA working arrays of a kernel, each placed in shared memory when it
+// fits under the cap (in the given priority order) and otherwise in a
+// per-CTA slice of a global workspace (L2-resident for the sizes used).
+constexpr int kMaxRegions = 6;
+struct WsPlan {
+  int64_t off[kMaxRegions];      // offset in elements of T (smem base or CTA slice)
+  int in_smem[kMaxRegions];
+  int64_t gstride;               // elements of T per CTA in the global workspace
+};
+
+struct LaunchCfg {
+  int grid = 0;
+  int block = 256;
+  size_t smem = 0;               // dynamic shared memory bytes
+  WsPlan ws{};
+  bool ok = false;               // plan_ok() passed
+  size_t ws_elems() const { return (size_t)ws.gstride * (size_t)grid; }
+};
+
+// Greedy placement: regions visited in `order` (all regions when order is
+// null), placed in shared memory while the running total stays under
+// cap_bytes, otherwise in the per-CTA global slice.  sizes are in elements of
+// `esize` bytes.  Every region gets a disjoint range; plan_ok() re-checks that.
+inline WsPlan plan_regions(const size_t* sizes, int n, size_t esize, size_t cap_bytes, size_t* smem_bytes,
+                           const int* order = nullptr) {
+  WsPlan w{};
+  size_t sm = 0, gl = 0;
+  for (int k = 0; k < n; ++k) {
+    const int i = order ? order[k] : k;
+    const size_t sz = (sizes[i] + 3) & ~size_t(3);  // keep 32-byte alignment for doubles
+    if ((sm + sz) * esize <= cap_bytes) {
+      w.in_smem[i] = 1;
+      w.off[i] = (int64_t)sm;
+      sm += sz;
+    } else {
+      w.in_smem[i] = 0;
+      w.off[i] = (int64_t)gl;
+      gl += sz;
+    }
+  }
+  w.gstride = (int64_t)((gl + 31) & ~size_t(31));
+  *smem_bytes = sm * esize;
+  return w;
+}
+
+// Host check that the regions are pairwise disjoint and inside their memory.
+inline bool plan_ok(const WsPlan& w, const size_t* sizes, int n, size_t esize, size_t smem_bytes) {
+  for (int i = 0; i < n; ++i) {
+    const int64_t lim = w.in_smem[i] ? (int64_t)(smem_bytes / esize) : w.gstride;
+    if (w.off[i] < 0 || w.off[i] + (int64_t)sizes[i] > lim) return false;
+    for (int j = 0; j < i; ++j) {
+      if (w.in_smem[i] != w.in_smem[j]) continue;
+      const bool disjoint = w.off[i] + (int64_t)sizes[i] <= w.off[j] || w.off[j] + (int64_t)sizes[j] <= w.off[i];
+      if (!disjoint) return false;
+    }
+  }
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T* ws_ptr(const WsPlan& w, int i, unsigned char* smem, T* gws) {
+  return w.in_smem[i] ? reinterpret_cast<T*>(smem) + w.off[i]
+                      : gws + (int64_t)blockIdx.x * w.gstride + w.off[i];
+}
+
+inline int blocks_per_sm(size_t smem) {
+  int b = (int)((228 * 1024) / (smem + 1024));
+  if (b > 8) b = 8;
+  if (b < 1) b = 1;
+  return b;
+}
+
+template <typename T> LaunchCfg plan_elem_schur(const Geo& G, int nsm);
+template <typename T> void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws,
+                                             const LaunchCfg& c, cudaStream_t st);
+LaunchCfg plan_elem_fdm(const Geo& G, int nsm);
+void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f_nodal, double* Z,
+                          double* ws, const LaunchCfg& c, cudaStream_t st);
+void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f_nodal, const double* uhat,
+                         double* u_nodal, double* ws, const LaunchCfg& c, cudaStream_t st);
+template <typename T> void launch_assemble(const Geo& G, const Tabs<T>& t, const T* F, const T* u,
+                                           const T* Z, T* out, int mode, cudaStream_t st);
+void launch_assemble_rhs(const Geo& G, const Tabs<double>& t, const double* f_nodal, const double* Z,
+                         double* Fhat, cudaStream_t st);
+void launch_pack(const Geo& G, const double* nodal, double* hat, cudaStream_t st);
+void launch_unpack(const Geo& G, const double* hat, double* nodal, cudaStream_t st);
+template <typename T> LaunchCfg plan_star(const Geo& G, int nsm);
+template <typename T> void launch_star(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws,
+                                       const LaunchCfg& c, cudaStream_t st);
+template <typename T> void launch_star_gather(const Geo& G, const T* Ob, T* du, int accumulate,
+                                              cudaStream_t st);
+template <typename T> void launch_prolong_add(const Geo& Gc, const Geo& Gf, const Tabs<T>& tf,
+                                              const T* uc, T* uf, cudaStream_t st);
+template <typename T> void launch_restrict(const Geo& Gf, const Geo& Gc, const Tabs<T>& tf, const T* rf,
+                                           T* rc, T* FB, T* EB, cudaStream_t st);
+void launch_coarse_solve(const Geo& G0, const CoarseTabs& ct, const double* F0, double* U0, double* X,
+                         double* Y, cudaStream_t st);
+template <typename T> void launch_norm2(const T* x, int64_t n, double* partial, int npart, double* out,
+                                        cudaStream_t st);
+template <typename TY, typename TX> void launch_axpy(TY* y, const TX* x, double a, int64_t n,
+                                                     cudaStream_t st);
+template <typename TO, typename TI> void launch_copy(TO* y, const TI* x, int64_t n, cudaStream_t st);
+
+int set_kernel_smem_limits();
+
+}  // namespace semmg

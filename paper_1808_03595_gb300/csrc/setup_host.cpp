@@ -1,0 +1,276 @@
+// Host-side FP64 setup numerics: GLL basis, 1D operators, symmetric eigen-
+// solver, and the per-level tables of Sec. 2-4.  Runs once per semmg_setup.
+#include "setup_host.h"
+
+#include <algorithm>
+#include <cmath>
+#include <stdexcept>
+
+namespace semmg {
+
+// Legendre P_n(x) and P_n'(x) by the three-term recurrence.
+static void legendre(int n, double x, double* P, double* dP) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) {
+    *P = 1.0;
+    *dP = 0.0;
+    return;
+  }
+  for (int k = 2; k <= n; ++k) {
+    const double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    p0 = p1;
+    p1 = pk;
+  }
+  *P = p1;
+  // P_n'(x) = n (x P_n - P_{n-1}) / (x^2 - 1); only used for |x| < 1
+  *dP = (std::fabs(x) < 1.0) ? n * (x * p1 - p0) / (x * x - 1.0) : 0.0;
+}
+
+void gll_host(int p, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(p + 1, 0.0);
+  w.assign(p + 1, 0.0);
+  x[0] = -1.0;
+  x[p] = 1.0;
+  // interior nodes: roots of P_p', Newton from the Chebyshev-Lobatto points;
+  // with q = P_p', q' = (2 x P_p' - p (p+1) P_p) / (1 - x^2) (Legendre ODE)
+  for (int i = 1; i < p; ++i) {
+    double t = -std::cos(M_PI * i / p);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(p, t, &P, &dP);
+      const double d2P = (2.0 * t * dP - p * (p + 1.0) * P) / (1.0 - t * t);
+      const double dt = dP / d2P;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    x[i] = t;
+  }
+  std::sort(x.begin(), x.end());
+  for (int i = 0; i <= p; ++i) {
+    double P, dP;
+    legendre(p, x[i], &P, &dP);
+    w[i] = 2.0 / (p * (p + 1.0) * P * P);
+  }
+}
+
+// D[i][j] = l_j'(x_i) through the Legendre form of the GLL cardinal functions.
+void deriv_matrix(int p, const std::vector<double>& x, std::vector<double>& D) {
+  D.assign((p + 1) * (p + 1), 0.0);
+  std::vector<double> P(p + 1);
+  for (int i = 0; i <= p; ++i) {
+    double dP;
+    legendre(p, x[i], &P[i], &dP);
+  }
+  for (int i = 0; i <= p; ++i)
+    for (int j = 0; j <= p; ++j) {
+      if (i != j)
+        D[i * (p + 1) + j] = P[i] / (P[j] * (x[i] - x[j]));
+      else if (i == 0)
+        D[0] = -0.25 * p * (p + 1.0);
+      else if (i == p)
+        D[p * (p + 1) + p] = 0.25 * p * (p + 1.0);
+    }
+}
+
+void stiffness(int p, const std::vector<double>& x, const std::vector<double>& w, std::vector<double>& L) {
+  std::vector<double> D;
+  deriv_matrix(p, x, D);
+  const int P1 = p + 1;
+  L.assign(P1 * P1, 0.0);
+  for (int i = 0; i < P1; ++i)
+    for (int j = 0; j < P1; ++j) {
+      double s = 0.0;
+      for (int q = 0; q < P1; ++q) s += w[q] * D[q * P1 + i] * D[q * P1 + j];
+      L[i * P1 + j] = s;
+    }
+  for (int i = 0; i < P1; ++i)
+    for (int j = i + 1; j < P1; ++j) {
+      const double a = 0.5 * (L[i * P1 + j] + L[j * P1 + i]);
+      L[i * P1 + j] = L[j * P1 + i] = a;
+    }
+}
+
+// J[I][i] = prod_{k != i} (xf_I - xc_k) / (xc_i - xc_k)
+void lagrange_interp(const std::vector<double>& xc, const std::vector<double>& xf, std::vector<double>& J) {
+  const int nc = (int)xc.size(), nf = (int)xf.size();
+  J.assign(nf * nc, 0.0);
+  for (int I = 0; I < nf; ++I)
+    for (int i = 0; i < nc; ++i) {
+      double v = 1.0;
+      for (int k = 0; k < nc; ++k)
+        if (k != i) v *= (xf[I] - xc[k]) / (xc[i] - xc[k]);
+      J[I * nc + i] = v;
+    }
+}
+
+// Cyclic Jacobi rotations for a symmetric matrix A (n x n, row-major):
+// A = V diag(ev) V^T, V orthogonal (columns are eigenvectors).
+void jacobi_eig(int n, std::vector<double> A, std::vector<double>& ev, std::vector<double>& V) {
+  V.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+  double scale = 0.0;
+  for (double a : A) scale = std::max(scale, std::fabs(a));
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+    if (off == 0.0 || off <= 1e-36 * scale * scale) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (std::fabs(apq) <= 1e-19 * (std::fabs(A[p * n + p]) + std::fabs(A[q * n + q]))) {
+          A[p * n + q] = A[q * n + p] = 0.0;
+          continue;
+        }
+        const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  ev.resize(n);
+  for (int i = 0; i < n; ++i) ev[i] = A[i * n + i];
+}
+
+// Generalised problem L S = M S Lam with diagonal M > 0: S^T M S = I, S^T L S = Lam.
+void gen_eig_diag_mass(int n, const std::vector<double>& L, const std::vector<double>& Md, std::vector<double>& S,
+                       std::vector<double>& lam) {
+  std::vector<double> A(n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) A[i * n + j] = L[i * n + j] / std::sqrt(Md[i] * Md[j]);
+  std::vector<double> Q;
+  jacobi_eig(n, A, lam, Q);
+  S.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) S[i * n + k] = Q[i * n + k] / std::sqrt(Md[i]);
+}
+
+double weight_poly(double t) {
+  const double t2 = t * t, t4 = t2 * t2;
+  return 1.0 - 35.0 * t4 + 84.0 * t4 * t - 70.0 * t4 * t2 + 20.0 * t4 * t2 * t;
+}
+
+void build_level_tables(HostLevel& L, const std::vector<double>* h) {
+  const int p = L.p, m = p - 1, P1 = p + 1, nS = 2 * m + 1;
+  gll_host(p, L.x, L.w);
+  stiffness(p, L.x, L.w, L.Ls);
+  // interior reference eigenpairs (Sec. 3.2 applied to one element's interior)
+  L.Sref.clear();
+  L.Sh.clear();
+  L.a0.clear();
+  L.ap.clear();
+  L.lamI.clear();
+  if (m > 0) {
+    std::vector<double> Lii(m * m), Mii(m);
+    for (int i = 0; i < m; ++i) {
+      Mii[i] = L.w[i + 1];
+      for (int j = 0; j < m; ++j) Lii[i * m + j] = L.Ls[(i + 1) * P1 + (j + 1)];
+    }
+    gen_eig_diag_mass(m, Lii, Mii, L.Sref, L.lamI);
+    L.Sh.resize(m * m);
+    L.a0.assign(m, 0.0);
+    L.ap.assign(m, 0.0);
+    for (int i = 0; i < m; ++i)
+      for (int k = 0; k < m; ++k) {
+        L.Sh[i * m + k] = L.w[i + 1] * L.Sref[i * m + k];
+        L.a0[k] += L.Sref[i * m + k] * L.Ls[(i + 1) * P1 + 0];
+        L.ap[k] += L.Sref[i * m + k] * L.Ls[(i + 1) * P1 + p];
+      }
+  }
+  // star tables per axis and vertex line (Sec. 3.2, 3.3)
+  for (int d = 0; d < 3; ++d) {
+    const int nd = (int)h[d].size();
+    const int Nd = nd * p + 1;
+    L.starS[d].assign((size_t)(nd + 1) * nS * nS, 0.0);
+    L.starLam[d].assign((size_t)(nd + 1) * nS, 1.0);
+    L.act[d].assign((size_t)(nd + 1) * nS, 0);
+    for (int c = 0; c <= nd; ++c) {
+      std::vector<double> Mb(nS, 0.0), Lb(nS * nS, 0.0);
+      for (int a = c - 1; a <= c; ++a) {
+        if (a < 0 || a >= nd) continue;
+        const double ha = h[d][a];
+        for (int i = 0; i <= p; ++i) {
+          const int ji = a * p + i - c * p;
+          if (ji < -m || ji > m) continue;
+          Mb[ji + m] += 0.5 * ha * L.w[i];
+          for (int k = 0; k <= p; ++k) {
+            const int jk = a * p + k - c * p;
+            if (jk < -m || jk > m) continue;
+            Lb[(ji + m) * nS + (jk + m)] += 2.0 / ha * L.Ls[i * P1 + k];
+          }
+        }
+      }
+      std::vector<int> act;
+      for (int j = -m; j <= m; ++j) {
+        const int g = c * p + j;
+        if (g >= 1 && g <= Nd - 2) act.push_back(j + m);
+      }
+      double* S = &L.starS[d][(size_t)c * nS * nS];
+      double* lam = &L.starLam[d][(size_t)c * nS];
+      unsigned char* ac = &L.act[d][(size_t)c * nS];
+      for (int i = 0; i < nS; ++i) S[i * nS + i] = 1.0;  // identity padding
+      const int na = (int)act.size();
+      if (na > 0) {
+        std::vector<double> La(na * na), Ma(na), Sa, la;
+        for (int i = 0; i < na; ++i) {
+          Ma[i] = Mb[act[i]];
+          for (int j = 0; j < na; ++j) La[i * na + j] = Lb[act[i] * nS + act[j]];
+        }
+        gen_eig_diag_mass(na, La, Ma, Sa, la);
+        for (int i = 0; i < na; ++i) {
+          S[act[i] * nS + act[i]] = 0.0;
+          ac[act[i]] = 1;
+          lam[act[i]] = la[i];
+        }
+        for (int i = 0; i < na; ++i)
+          for (int k = 0; k < na; ++k) S[act[i] * nS + act[k]] = Sa[i * na + k];
+      }
+    }
+  }
+  // smoother weights at star offset |j| (Sec. 3.2): t = (1 + xi_|j|) / 2
+  L.w1d.assign(m + 1, 0.0);
+  for (int k = 0; k <= m; ++k) L.w1d[k] = weight_poly(0.5 * (1.0 + L.x[k]));
+}
+
+void build_coarse_tables(int p0, const std::vector<double>* h, HostCoarse& C) {
+  std::vector<double> x, w, Ls;
+  gll_host(p0, x, w);
+  stiffness(p0, x, w, Ls);
+  const int P1 = p0 + 1;
+  for (int d = 0; d < 3; ++d) {
+    const int nd = (int)h[d].size();
+    const int N = nd * p0 + 1, K = N - 2;
+    C.K[d] = K > 0 ? K : 0;
+    C.S[d].clear();
+    C.lam[d].clear();
+    if (K <= 0) continue;
+    std::vector<double> Mg(N, 0.0), Lg((size_t)N * N, 0.0);
+    for (int a = 0; a < nd; ++a)
+      for (int i = 0; i <= p0; ++i) {
+        Mg[a * p0 + i] += 0.5 * h[d][a] * w[i];
+        for (int k = 0; k <= p0; ++k) Lg[(size_t)(a * p0 + i) * N + (a * p0 + k)] += 2.0 / h[d][a] * Ls[i * P1 + k];
+      }
+    std::vector<double> Li((size_t)K * K), Mi(K);
+    for (int i = 0; i < K; ++i) {
+      Mi[i] = Mg[i + 1];
+      for (int j = 0; j < K; ++j) Li[(size_t)i * K + j] = Lg[(size_t)(i + 1) * N + (j + 1)];
+    }
+    gen_eig_diag_mass(K, Li, Mi, C.S[d], C.lam[d]);
+  }
+}
+
+}  // namespace semmg

@@ -1,0 +1,36 @@
+// Host-side FP64 setup numerics (no CUDA): GLL basis, 1D operators, the
+// symmetric eigen-solver and the per-level tables.
+#pragma once
+
+#include <vector>
+
+namespace semmg {
+
+struct HostLevel {
+  int p = 0;
+  std::vector<double> x, w, Ls;                    // GLL nodes, weights, standard stiffness
+  std::vector<double> Sref, Sh, a0, ap, lamI;      // interior eigen-tables
+  std::vector<double> starS[3], starLam[3];        // per axis: (n_d+1) blocks
+  std::vector<unsigned char> act[3];
+  std::vector<double> w1d;                         // smoother weights at |offset|
+  std::vector<double> J;                           // interpolation from the next coarser level
+  int pc = 0;
+};
+
+struct HostCoarse {
+  int K[3] = {0, 0, 0};
+  std::vector<double> S[3], lam[3];
+};
+
+void gll_host(int p, std::vector<double>& x, std::vector<double>& w);
+void deriv_matrix(int p, const std::vector<double>& x, std::vector<double>& D);
+void stiffness(int p, const std::vector<double>& x, const std::vector<double>& w, std::vector<double>& L);
+void lagrange_interp(const std::vector<double>& xc, const std::vector<double>& xf, std::vector<double>& J);
+void jacobi_eig(int n, std::vector<double> A, std::vector<double>& ev, std::vector<double>& V);
+void gen_eig_diag_mass(int n, const std::vector<double>& L, const std::vector<double>& Md, std::vector<double>& S,
+                       std::vector<double>& lam);
+double weight_poly(double t);
+void build_level_tables(HostLevel& L, const std::vector<double>* h);
+void build_coarse_tables(int p0, const std::vector<double>* h, HostCoarse& C);
+
+}  // namespace semmg

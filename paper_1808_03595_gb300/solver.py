@@ -1,0 +1,203 @@
+"""Python binding of the semmg C ABI: argument marshalling for torch CUDA tensors.
+
+Every computation happens inside libsemmg.so; this module only passes device
+pointers, sizes and the current CUDA stream.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+class SemmgError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{L.ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """A semmg context: mesh (per-axis element widths), degree p, lambda >= 0, options."""
+
+    def __init__(self, h, p, lam, p0=2, nu_pre=1, nu_post=1, precision="fp64", max_iter=50, stream=None):
+        self._lib = L.load()
+        self._ctx = ctypes.c_void_p()
+        self.h = [np.ascontiguousarray(np.asarray(hd, dtype=np.float64)) for hd in h]
+        self.n = [len(hd) for hd in self.h]
+        self.p = int(p)
+        self.lam = float(lam)
+        mesh = L.semmg_mesh()
+        for d in range(3):
+            mesh.n[d] = self.n[d]
+            mesh.h[d] = self.h[d].ctypes.data_as(L.P_double)
+        opts = L.semmg_opts()
+        self._lib.semmg_default_opts(ctypes.byref(opts))
+        opts.p0 = p0
+        opts.nu_pre = nu_pre
+        opts.nu_post = nu_post
+        opts.precision = {"fp64": L.SEMMG_FP64, "mixed": L.SEMMG_MIXED}[precision]
+        opts.max_iter = max_iter
+        self.precision = precision
+        rc = self._lib.semmg_setup(ctypes.byref(mesh), self.p, self.lam, ctypes.byref(opts), _stream(stream),
+                                   ctypes.byref(self._ctx))
+        if rc != 0:
+            raise SemmgError(rc, "setup")
+        nl = ctypes.c_int()
+        self._check(self._lib.semmg_num_levels(self._ctx, ctypes.byref(nl)))
+        self.nlevels = nl.value
+        self.degrees = []
+        for lv in range(self.nlevels):
+            q = ctypes.c_int()
+            self._check(self._lib.semmg_level_degree(self._ctx, lv, ctypes.byref(q)))
+            self.degrees.append(q.value)
+
+    # ------------------------------------------------------------ helpers
+    def _check(self, rc, allow=()):
+        if rc != 0 and rc not in allow:
+            msg = self._lib.semmg_last_error(self._ctx).decode() if self._ctx else ""
+            raise SemmgError(rc, msg)
+        return rc
+
+    def close(self):
+        if self._ctx:
+            self._lib.semmg_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def L(self):
+        return self.nlevels - 1
+
+    def condensed_size(self, level=None):
+        n = ctypes.c_int64()
+        self._check(self._lib.semmg_condensed_size(self._ctx, self.L if level is None else level, ctypes.byref(n)))
+        return n.value
+
+    def nodal_size(self, level=None):
+        n = ctypes.c_int64()
+        self._check(self._lib.semmg_nodal_size(self._ctx, self.L if level is None else level, ctypes.byref(n)))
+        return n.value
+
+    def nodal_shape(self, level=None):
+        q = self.degrees[self.L if level is None else level]
+        return (self.n[2] * q + 1, self.n[1] * q + 1, self.n[0] * q + 1)
+
+    def _hat(self, level, dtype=torch.float64):
+        return torch.zeros(self.condensed_size(level), dtype=dtype, device="cuda")
+
+    # ------------------------------------------------------------ entry points
+    def pack(self, level, u_nodal, out=None):
+        out = self._hat(level) if out is None else out
+        self._check(self._lib.semmg_pack(self._ctx, level, _ptr(u_nodal), _ptr(out), _stream()))
+        return out
+
+    def unpack(self, level, u_hat, out=None):
+        out = torch.zeros(self.nodal_shape(level), dtype=torch.float64, device="cuda") if out is None else out
+        self._check(self._lib.semmg_unpack(self._ctx, level, _ptr(u_hat), _ptr(out), _stream()))
+        return out
+
+    def apply_condensed(self, level, u, out=None):
+        out = self._hat(level) if out is None else out
+        self._check(self._lib.semmg_apply_condensed(self._ctx, level, _ptr(u), _ptr(out), _stream()))
+        return out
+
+    def residual(self, level, f, u, out=None):
+        out = self._hat(level) if out is None else out
+        self._check(self._lib.semmg_residual(self._ctx, level, _ptr(f), _ptr(u), _ptr(out), _stream()))
+        return out
+
+    @staticmethod
+    def _dtype_code(t):
+        if t.dtype == torch.float64:
+            return L.SEMMG_F64
+        if t.dtype == torch.float32:
+            return L.SEMMG_F32
+        raise TypeError("float32 or float64 tensors only")
+
+    def smooth(self, level, r, out=None):
+        out = self._hat(level, r.dtype) if out is None else out
+        self._check(self._lib.semmg_smooth(self._ctx, level, self._dtype_code(r), _ptr(r), _ptr(out), _stream()))
+        return out
+
+    def restrict(self, level, fine, out=None):
+        out = self._hat(level - 1, fine.dtype) if out is None else out
+        self._check(self._lib.semmg_restrict(self._ctx, level, self._dtype_code(fine), _ptr(fine), _ptr(out),
+                                             _stream()))
+        return out
+
+    def prolong_add(self, level, coarse, fine):
+        self._check(self._lib.semmg_prolong_add(self._ctx, level, self._dtype_code(coarse), _ptr(coarse),
+                                                _ptr(fine), _stream()))
+        return fine
+
+    def coarse_solve(self, f0, out=None):
+        out = self._hat(0) if out is None else out
+        self._check(self._lib.semmg_coarse_solve(self._ctx, _ptr(f0), _ptr(out), _stream()))
+        return out
+
+    def vcycle(self, u, f):
+        self._check(self._lib.semmg_vcycle(self._ctx, _ptr(u), _ptr(f), _stream()))
+        return u
+
+    def condense_rhs(self, f_nodal, out=None):
+        out = self._hat(self.L) if out is None else out
+        self._check(self._lib.semmg_condense_rhs(self._ctx, _ptr(f_nodal), _ptr(out), _stream()))
+        return out
+
+    def recover(self, f_nodal, u_hat, out=None):
+        out = torch.zeros(self.nodal_shape(), dtype=torch.float64, device="cuda") if out is None else out
+        self._check(self._lib.semmg_recover(self._ctx, _ptr(f_nodal), _ptr(u_hat), _ptr(out), _stream()))
+        return out
+
+    def solve(self, f_nodal, rtol=1e-10, out=None, allow_not_converged=False):
+        out = torch.empty(self.nodal_shape(), dtype=torch.float64, device="cuda") if out is None else out
+        info = L.semmg_info()
+        allow = (L.SEMMG_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        self._check(self._lib.semmg_solve(self._ctx, _ptr(f_nodal), _ptr(out), rtol, ctypes.byref(info), _stream()),
+                    allow)
+        return out, info
+
+    def solve_host(self, f_host, u_host, rtol=1e-10, allow_not_converged=False):
+        """f_host, u_host: contiguous float64 CPU tensors (pinned for asynchronous copies)."""
+        info = L.semmg_info()
+        allow = (L.SEMMG_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        self._check(self._lib.semmg_solve_host(self._ctx, _ptr(f_host), _ptr(u_host), rtol, ctypes.byref(info),
+                                               _stream()), allow)
+        return u_host, info
+
+    # ------------------------------------------------------------ timing
+    def set_timing(self, enable=True):
+        self._check(self._lib.semmg_set_timing(self._ctx, 1 if enable else 0))
+
+    def reset_kstats(self):
+        self._check(self._lib.semmg_reset_kstats(self._ctx))
+
+    def kstats(self):
+        """Per kernel class: dict(ms, launches, flops, bytes) accumulated since the last reset."""
+        out = {}
+        for i, name in enumerate(L.KSTAT_KINDS):
+            k = L.semmg_kstat()
+            self._check(self._lib.semmg_get_kstat(self._ctx, i, ctypes.byref(k)))
+            out[name] = {"ms": k.ms, "launches": k.launches, "flops": k.flops, "bytes": k.bytes}
+        return out
