@@ -1,0 +1,339 @@
+"""Benchmark: unknowns/s per solve to a 1e-10 relative residual reduction.
+
+Workload (default): Helmholtz lambda = 1 on the unit cube, 8x8x8 uniform
+elements, degree sweep p in {4, 8, 16, 32}, f = manufactured solution plus
+seeded N(0, 1e-2) noise at the GLL nodes, plain FP64 GPU form, coarse degree
+p0 = 2.  One step solves all four degrees (condensation, V-cycles to 1e-10,
+interior recovery); unknowns = sum of (8p+1)^3.  The mixed-precision form
+(FP32 V-cycle inside FP64 iterative refinement) is timed on the same workload
+and reported under "mixed".
+
+Timing: CUDA events on the solving stream around each solve, L2 flushed
+(256 MiB write) before every solve, W untimed warm-up steps, then K timed
+steps; max over ranks.  "e2e" repeats the timed steps through the host-buffer
+entry point (pinned host f in, u out, copies inside the timed region).
+Multi-GPU runs are replicas (the path has no exchange step on one mesh).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+SWEEP = [4, 8, 16, 32]
+WORKLOAD = "helmholtz_8x8x8_p4-8-16-32"
+METRIC = "unknowns/s per solve to 1e-10 residual (FP64 vs mixed); smoother HBM GB/s"
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 entry in the peaks file)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, value):
+    if pg is None:
+        return value
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- reference arm: the oracle on the host
+
+def oracle_sample(p=8):
+    """One O2 (oracle) solve of the 8x8x8 Helmholtz workload at degree p; returns (unknowns, seconds, iters)."""
+    from oracle import dense, matfree
+    h, p, lam, f, p0 = workloads.config(f"helmholtz_8x8x8_p{p}")
+    mesh = dense.Mesh(h, p, lam)
+    t0 = time.perf_counter()
+    _, it, _ = matfree.solve(mesh, f, p0=p0)
+    dt = time.perf_counter() - t0
+    return (8 * p + 1) ** 3, dt, it
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return 0
+    sample_p = args.cpu_sample_p
+    for _ in range(args.warmup):
+        oracle_sample(sample_p)
+    tot_n, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        n, dt, _ = oracle_sample(sample_p)
+        tot_n += n
+        tot_t += dt
+    v = tot_n / tot_t
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"p={sample_p} solve per step", "parallelism": "none"},
+        "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one matrix-free oracle (numpy FP64) solve of helmholtz_8x8x8 at p={sample_p} "
+                                   f"({(8 * sample_p + 1) ** 3} unknowns) per step"},
+        "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_semmg(args, world, rank, local, pg):
+    import torch
+    from paper_1808_03595_gb300 import Context
+    from paper_1808_03595_gb300 import build as _build
+    _build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    degrees = [int(x) for x in args.degrees.split(",")]
+
+    cases = []
+    for p in degrees:
+        h, p, lam, f, p0 = workloads.config(f"helmholtz_8x8x8_p{p}")
+        fd = torch.as_tensor(f, dtype=torch.float64, device=dev)
+        ctx64 = Context(h, p, lam, p0=p0, precision="fp64")
+        ctx32 = Context(h, p, lam, p0=p0, precision="mixed")
+        ud = torch.empty_like(fd)
+        fh = torch.as_tensor(f, dtype=torch.float64).pin_memory()
+        uh = torch.empty_like(fh).pin_memory()
+        cases.append({"p": p, "n": int(fd.numel()), "f": fd, "u": ud, "fh": fh, "uh": uh, "fp64": ctx64,
+                      "mixed": ctx32})
+    torch.cuda.synchronize()
+
+    def solve_all(form, timed, host=False):
+        ms, iters = 0.0, {}
+        for c in cases:
+            ctx = c[form]
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if host:
+                _, info = ctx.solve_host(c["fh"], c["uh"], rtol=1e-10)
+            else:
+                _, info = ctx.solve(c["f"], rtol=1e-10, out=c["u"])
+            e1.record(stream)
+            e1.synchronize()
+            if timed:
+                ms += e0.elapsed_time(e1)
+            iters[c["p"]] = info.iters
+            assert info.res_final <= 1e-10 * info.res0, (form, c["p"], info.res_final, info.res0)
+        return ms, iters
+
+    for form in ("fp64", "mixed"):
+        for _ in range(args.warmup):
+            solve_all(form, False)
+    # timed region (device-resident inputs)
+    for c in cases:
+        c["fp64"].set_timing(True)
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t64, it64 = 0.0, {}
+    for _ in range(args.steps):
+        ms, it64 = solve_all("fp64", True)
+        t64 += ms
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(pg)
+    kst = {}
+    for c in cases:
+        for k, v in c["fp64"].kstats().items():
+            acc = kst.setdefault(k, {"ms": 0.0, "launches": 0, "flops": 0.0, "bytes": 0.0})
+            for kk in acc:
+                acc[kk] += v[kk]
+        c["fp64"].set_timing(False)
+    t32, it32 = 0.0, {}
+    for _ in range(args.steps):
+        ms, it32 = solve_all("mixed", True)
+        t32 += ms
+    # end to end through the host-buffer entry point
+    for _ in range(1):
+        solve_all("fp64", False, host=True)
+    te2e = 0.0
+    for _ in range(args.steps):
+        ms, _ = solve_all("fp64", True, host=True)
+        te2e += ms
+    torch.cuda.synchronize()
+
+    t64 = max_over_ranks(pg, t64)
+    t32 = max_over_ranks(pg, t32)
+    te2e = max_over_ranks(pg, te2e)
+    unknowns = sum(c["n"] for c in cases)
+    value = world * unknowns * args.steps / (t64 / 1e3)
+    value32 = world * unknowns * args.steps / (t32 / 1e3)
+    e2e = world * unknowns * args.steps / (te2e / 1e3)
+
+    # roofline of the dominant kernel (FP64 form): FP64-ALU bound
+    dom = max(kst, key=lambda k: kst[k]["ms"])
+    d = kst[dom]
+    total_ms = sum(v["ms"] for v in kst.values())
+    launches = sum(v["launches"] for v in kst.values())
+    peaks = load_peaks()
+    if d["flops"] > 0:
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (2 FP64 FMA/clk/SM x 152 SMs at 2.07 GHz)",
+                "launches": d["launches"], "share_of_kernel_time": d["ms"] / total_ms,
+                "hbm_gbs": d["bytes"] / (d["ms"] / 1e3) / 1e9}
+    else:
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        pk = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
+                "traffic": None, "kernel": dom, "launches": d["launches"]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t64 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "degrees": degrees, "elements": [8, 8, 8], "lambda": 1.0, "p0": 2,
+                   "rtol": 1e-10, "l2": "flushed (256 MiB write) before every solve",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "iterations": {"fp64": it64, "mixed": it32},
+        "mixed": {"value": value32, "unit": "unknowns/s", "dtype": "f64+f32", "ms_per_step": t32 / args.steps,
+                  "speedup_vs_fp64": value32 / value},
+        "e2e": {"value": e2e, "unit": "unknowns/s", "h2d_bytes_per_step": 8 * unknowns,
+                "d2h_bytes_per_step": 8 * unknowns},
+        "gpu_launches": int(launches // max(1, args.steps)) * args.steps,
+        "kernels_fp64": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
+                         for k, v in kst.items()},
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        n, dt, _ = oracle_sample(args.cpu_sample_p)
+        line["cpu_baseline"] = {"value": n / dt, "unit": "unknowns/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"one matrix-free oracle (numpy FP64) solve of helmholtz_8x8x8 at "
+                                          f"p={args.cpu_sample_p} ({n} unknowns), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for c in cases:
+        c["fp64"].close()
+        c["mixed"].close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="semmg", choices=["semmg", "reference"])
+    ap.add_argument("--degrees", default=",".join(str(p) for p in SWEEP))
+    ap.add_argument("--cpu-sample-p", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank, pg)
+    else:
+        rc = run_semmg(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())
