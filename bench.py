@@ -218,7 +218,8 @@ def run_semmg(args, world, rank, local, pg):
             assert info.res_final <= 1e-10 * info.res0, (form, c["p"], info.res_final, info.res0)
         return ms, iters
 
-    for form in ("fp64", "mixed"):
+    forms = args.forms.split(",")
+    for form in forms:
         for _ in range(args.warmup):
             solve_all(form, False)
     # timed region (device-resident inputs)
@@ -242,17 +243,19 @@ def run_semmg(args, world, rank, local, pg):
             for kk in acc:
                 acc[kk] += v[kk]
         c["fp64"].set_timing(False)
-    t32, it32 = 0.0, {}
-    for _ in range(args.steps):
-        ms, it32 = solve_all("mixed", True)
-        t32 += ms
-    # end to end through the host-buffer entry point
-    for _ in range(1):
+    t32, it32, te2e = float("nan"), {}, float("nan")
+    if "mixed" in forms:
+        t32 = 0.0
+        for _ in range(args.steps):
+            ms, it32 = solve_all("mixed", True)
+            t32 += ms
+    if not args.no_e2e:
+        # end to end through the host-buffer entry point
         solve_all("fp64", False, host=True)
-    te2e = 0.0
-    for _ in range(args.steps):
-        ms, _ = solve_all("fp64", True, host=True)
-        te2e += ms
+        te2e = 0.0
+        for _ in range(args.steps):
+            ms, _ = solve_all("fp64", True, host=True)
+            te2e += ms
     torch.cuda.synchronize()
 
     t64 = max_over_ranks(pg, t64)
@@ -322,6 +325,8 @@ def main():
     ap.add_argument("--degrees", default=",".join(str(p) for p in SWEEP))
     ap.add_argument("--cpu-sample-p", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", default="fp64,mixed", help="forms to run: fp64 (timed headline) and/or mixed")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
