@@ -186,6 +186,36 @@ int semmg_solve(semmg_ctx* ctx, const double* f_nodal, double* u_nodal, double r
 int semmg_solve_host(semmg_ctx* ctx, const double* f_host, double* u_host, double rtol,
                      semmg_info* info, void* stream);
 
+/* ------------------------------------------------------------------ no-allocation smoothing
+ * The paper has no counterpart to this entry point; it exists for callers of
+ * this library that must not allocate device memory while they work -- for
+ * example code running under a memory manager that has already claimed the
+ * device for its own pool, or a host thread that cannot afford the
+ * device-wide synchronisation cudaMalloc and cudaFree may cause.
+ *
+ * semmg_smooth_noalloc computes exactly what semmg_smooth computes (du_hat =
+ * Smoother(r_hat) on `level`, same kernels, same results) but calls no
+ * cudaMalloc, cudaFree or other allocating routine: the star output buffer and
+ * the per-block work arrays come from one array of SEMMG_NOALLOC_SCRATCH_BYTES
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.  The context (its read-only tables) must have been
+ * set up beforehand by code that was allowed to allocate; the caller passes
+ * r_hat and du_hat as for semmg_smooth.
+ *   - The first call on a device looks the array's address up (once per
+ *     device, with that device current); make that first call before any
+ *     stream capture.
+ *   - A level whose star output buffer (nstar * 3 * n_S^2 elements) plus one
+ *     block's work arrays exceeds the array returns SEMMG_ERR_UNSUPPORTED,
+ *     with the sizes in semmg_last_error(ctx); larger work arrays only lower
+ *     the number of blocks that run at once.
+ *   - Every call, on every context, shares the one array and it keeps the
+ *     last call's contents; each call writes every scratch entry it later
+ *     reads, so nothing has to start at zero.  Calls whose executions overlap
+ *     on the GPU (different streams, or different host threads) race on the
+ *     array and give wrong results: order them on one stream. */
+#define SEMMG_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int semmg_smooth_noalloc(semmg_ctx* ctx, int level, int dtype, const void* r_hat, void* du_hat, void* stream);
+
 /* ------------------------------------------------------------------ timing
  * Per-kernel-class timing with CUDA events recorded on the caller's stream
  * around every launch the context makes (off by default; a few microseconds

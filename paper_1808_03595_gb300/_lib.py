@@ -25,6 +25,7 @@ ERRORS = {
 SEMMG_ERR_NOT_CONVERGED = -4
 SEMMG_FP64, SEMMG_MIXED = 0, 1
 SEMMG_F64, SEMMG_F32 = 0, 1
+SEMMG_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 class semmg_mesh(ctypes.Structure):
@@ -70,6 +71,7 @@ SIGNATURES = {
     "semmg_recover": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "semmg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(semmg_info), c_void_p]),
     "semmg_solve_host": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(semmg_info), c_void_p]),
+    "semmg_smooth_noalloc": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "semmg_set_timing": (c_int, [c_void_p, c_int]),
     "semmg_get_kstat": (c_int, [c_void_p, c_int, ctypes.POINTER(semmg_kstat)]),
     "semmg_reset_kstats": (c_int, [c_void_p]),

@@ -407,6 +407,47 @@ int set_limits(semmg_ctx* c) {
 
 }  // namespace
 
+
+namespace semmg {
+
+// Star smoothing of one level (semmg_smooth's work) with the star output
+// buffer and the per-block work arrays placed in caller-provided device
+// memory instead of the context's scratch; the grid shrinks until the work
+// arrays fit.  Returns SEMMG_ERR_UNSUPPORTED when the level does not fit.
+int smooth_with_scratch(semmg_ctx* c, int level, int dtype, const void* r, void* du, void* scratch,
+                        size_t scratch_bytes, cudaStream_t st) {
+  if (!valid_level(c, level) || level < 1 || !r || !du || r == du || !scratch) return SEMMG_ERR_INVALID_ARG;
+  if (dtype != SEMMG_F64 && dtype != SEMMG_F32) return SEMMG_ERR_INVALID_ARG;
+  const Geo& G = c->geo[level];
+  const size_t es = dtype == SEMMG_F64 ? sizeof(double) : sizeof(float);
+  LaunchCfg cfg = dtype == SEMMG_F64 ? c->dl[level].star64 : c->dl[level].star32;
+  const size_t ob_bytes = ((size_t)G.nstar * 3 * G.nS * G.nS * es + 255) & ~size_t(255);
+  const size_t per_cta = (size_t)cfg.ws.gstride * es;
+  if (ob_bytes > scratch_bytes)
+    return fail(c, SEMMG_ERR_UNSUPPORTED,
+                "smooth_noalloc: level %d needs %zu bytes of star output buffer, more than the %zu-byte scratch",
+                level, ob_bytes, scratch_bytes);
+  if (per_cta > 0) {
+    const size_t fit = (scratch_bytes - ob_bytes) / per_cta;
+    if (fit < 1)
+      return fail(c, SEMMG_ERR_UNSUPPORTED,
+                  "smooth_noalloc: level %d needs %zu + %zu bytes of scratch, more than the %zu-byte scratch", level,
+                  ob_bytes, per_cta, scratch_bytes);
+    if ((size_t)cfg.grid > fit) cfg.grid = (int)fit;
+  }
+  unsigned char* base = (unsigned char*)scratch;
+  if (dtype == SEMMG_F64) {
+    launch_star<double>(G, c->dl[level].td, (const double*)r, (double*)base, (double*)(base + ob_bytes), cfg, st);
+    launch_star_gather<double>(G, (const double*)base, (double*)du, 0, st);
+  } else {
+    launch_star<float>(G, c->dl[level].tf, (const float*)r, (float*)base, (float*)(base + ob_bytes), cfg, st);
+    launch_star_gather<float>(G, (const float*)base, (float*)du, 0, st);
+  }
+  return check_cuda(c, "smooth_noalloc");
+}
+
+}  // namespace semmg
+
 extern "C" {
 
 void semmg_default_opts(semmg_opts* o) {

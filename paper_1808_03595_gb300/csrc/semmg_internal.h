@@ -316,5 +316,7 @@ template <typename TY, typename TX> void launch_axpy(TY* y, const TX* x, double 
 template <typename TO, typename TI> void launch_copy(TO* y, const TI* x, int64_t n, cudaStream_t st);
 
 int set_kernel_smem_limits();
+int smooth_with_scratch(semmg_ctx* c, int level, int dtype, const void* r, void* du, void* scratch,
+                        size_t scratch_bytes, cudaStream_t st);
 
 }  // namespace semmg
