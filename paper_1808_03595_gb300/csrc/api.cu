@@ -90,6 +90,7 @@ struct semmg_ctx {
   int npart = 0;
   double* dnorm = nullptr;
   double* hnorm = nullptr;  // pinned
+  int* star_counter = nullptr;  // work counter of the star kernel (self-resetting)
   // host-buffer solve
   double* fnod = nullptr;
   double* unod = nullptr;
@@ -182,6 +183,15 @@ Tabs<T> upload_tabs(semmg_ctx* c, const HostLevel& H, const std::vector<double>*
     t.starLam[d] = upload<T>(c, H.starLam[d], ok);
     t.act[d] = upload_u8(c, H.act[d], ok);
   }
+  for (int d = 0; d < 3; ++d) {
+    t.starSym[d] = upload_u8(c, H.sym[d], ok);
+    std::vector<int> ci(H.cls[d].begin(), H.cls[d].end());
+    int* dci = (int*)dalloc(c, ci.size() * sizeof(int));
+    if (!dci || cudaMemcpy(dci, ci.data(), ci.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) *ok = false;
+    t.starCls[d] = dci;
+    t.ncls[d] = (int)H.rep[d].size();
+  }
+  t.Rtab = H.Rtab.empty() ? nullptr : upload<T>(c, H.Rtab, ok);
   t.w1d = upload<T>(c, H.w1d, ok);
   t.J = H.J.empty() ? nullptr : upload<T>(c, H.J, ok);
   t.pc = H.pc;
@@ -289,7 +299,7 @@ void op_smooth(semmg_ctx* c, int l, const T* r, T* du, int accumulate, cudaStrea
   const double ob = (double)G.nstar * 3 * G.nS * G.nS * sizeof(T);
   {
     Tic t(c, SEMMG_K_STAR, st);
-    launch_star<T>(G, tabs<T>(c, l), r, (T*)c->Obs, (T*)c->wss, star_cfg<T>(c, l), st);
+    launch_star<T>(G, tabs<T>(c, l), r, (T*)c->Obs, (T*)c->wss, star_cfg<T>(c, l), c->star_counter, st);
     t.toc(star_flops(G), vec + ob);
   }
   Tic t(c, SEMMG_K_STAR_GATHER, st);
@@ -437,10 +447,12 @@ int smooth_with_scratch(semmg_ctx* c, int level, int dtype, const void* r, void*
   }
   unsigned char* base = (unsigned char*)scratch;
   if (dtype == SEMMG_F64) {
-    launch_star<double>(G, c->dl[level].td, (const double*)r, (double*)base, (double*)(base + ob_bytes), cfg, st);
+    launch_star<double>(G, c->dl[level].td, (const double*)r, (double*)base, (double*)(base + ob_bytes), cfg,
+                        nullptr, st);
     launch_star_gather<double>(G, (const double*)base, (double*)du, 0, st);
   } else {
-    launch_star<float>(G, c->dl[level].tf, (const float*)r, (float*)base, (float*)(base + ob_bytes), cfg, st);
+    launch_star<float>(G, c->dl[level].tf, (const float*)r, (float*)base, (float*)(base + ob_bytes), cfg, nullptr,
+                       st);
     launch_star_gather<float>(G, (const float*)base, (float*)du, 0, st);
   }
   return check_cuda(c, "smooth_noalloc");
@@ -502,6 +514,7 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   for (int l = 0; l < nl; ++l) {
     c->geo[l] = make_geo(mesh->n, degs[l], lambda);
     c->hl[l].p = degs[l];
+    c->hl[l].lam = lambda;
     build_level_tables(c->hl[l], c->h);
     if (l > 0) {
       lagrange_interp(c->hl[l - 1].x, c->hl[l].x, c->hl[l].J);
@@ -573,6 +586,8 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   c->npart = 512;
   c->part = (double*)dalloc(c.get(), c->npart * sizeof(double));
   c->dnorm = (double*)dalloc(c.get(), sizeof(double));
+  c->star_counter = (int*)dalloc(c.get(), 4 * sizeof(int));
+  if (!c->star_counter || cudaMemset(c->star_counter, 0, 4 * sizeof(int)) != cudaSuccess) return SEMMG_ERR_NOMEM;
   if (!c->Zs || !c->Obs || !c->FBs || !c->EBs || !c->wss || !c->Fh || !c->Uh || !c->Rh || !c->cX || !c->cY ||
       !c->F0d || !c->U0d || !c->part || !c->dnorm)
     return SEMMG_ERR_NOMEM;

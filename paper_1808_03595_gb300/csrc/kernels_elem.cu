@@ -375,10 +375,10 @@ template void launch_elem_schur<float>(const Geo&, const Tabs<float>&, const flo
 
 int set_elem_smem_limits() {
   int bad = 0;
-  bad |= cudaFuncSetAttribute(k_elem_schur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_schur<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_condense, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_recover, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_condense, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_recover, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return bad;
 }
 

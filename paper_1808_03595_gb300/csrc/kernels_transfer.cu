@@ -356,10 +356,10 @@ template void launch_restrict<float>(const Geo&, const Geo&, const Tabs<float>&,
 
 int set_transfer_smem_limits() {
   int bad = 0;
-  bad |= cudaFuncSetAttribute(k_prolong_faces<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  bad |= cudaFuncSetAttribute(k_prolong_faces<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  bad |= cudaFuncSetAttribute(k_restrict_faces<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  bad |= cudaFuncSetAttribute(k_restrict_faces<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  bad |= cudaFuncSetAttribute(k_prolong_faces<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_prolong_faces<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_restrict_faces<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_restrict_faces<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return bad;
 }
 

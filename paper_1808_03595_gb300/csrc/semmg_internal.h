@@ -198,6 +198,10 @@ struct Tabs {
   const T* starS[3];    // per axis: nv_d blocks of nS x nS, S[j][k], row j <-> offset j-m
   const T* starLam[3];  // per axis: nv_d x nS
   const unsigned char* act[3];  // per axis: nv_d x nS active flags
+  const unsigned char* starSym[3];  // per axis: nv_d flags, centrosymmetric line (columns: even, then odd)
+  const int* starCls[3];           // per axis: nv_d line classes
+  int ncls[3];                     // classes per axis
+  const T* Rtab;   // per star class (c1*ncls2 + c2)*ncls3 + c3: nS^3 values 1/(lam+Lam1+Lam2+Lam3), or null
   const T* w1d;    // m+1: smoother weight at offset |j| (Sec. 3.2, weights)
   const T* J;      // (p+1) x (pc+1) interpolation from level-1, row-major; null on level 0
   int pc;
@@ -300,7 +304,7 @@ void launch_pack(const Geo& G, const double* nodal, double* hat, cudaStream_t st
 void launch_unpack(const Geo& G, const double* hat, double* nodal, cudaStream_t st);
 template <typename T> LaunchCfg plan_star(const Geo& G, int nsm);
 template <typename T> void launch_star(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws,
-                                       const LaunchCfg& c, cudaStream_t st);
+                                       const LaunchCfg& c, int* counter, cudaStream_t st);
 template <typename T> void launch_star_gather(const Geo& G, const T* Ob, T* du, int accumulate,
                                               cudaStream_t st);
 template <typename T> void launch_prolong_add(const Geo& Gc, const Geo& Gf, const Tabs<T>& tf,

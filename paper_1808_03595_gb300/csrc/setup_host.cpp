@@ -51,6 +51,14 @@ void gll_host(int p, std::vector<double>& x, std::vector<double>& w) {
     legendre(p, x[i], &P, &dP);
     w[i] = 2.0 / (p * (p + 1.0) * P * P);
   }
+  // the rule is symmetric about 0; make it exactly so (x_i = -x_{p-i}, w_i = w_{p-i})
+  for (int i = 0; i <= p / 2; ++i) {
+    const double xs = 0.5 * (x[p - i] - x[i]), ws = 0.5 * (w[i] + w[p - i]);
+    x[i] = -xs;
+    x[p - i] = xs;
+    w[i] = w[p - i] = ws;
+  }
+  if (p % 2 == 0) x[p / 2] = 0.0;
 }
 
 // D[i][j] = l_j'(x_i) through the Legendre form of the GLL cardinal functions.
@@ -87,6 +95,15 @@ void stiffness(int p, const std::vector<double>& x, const std::vector<double>& w
     for (int j = i + 1; j < P1; ++j) {
       const double a = 0.5 * (L[i * P1 + j] + L[j * P1 + i]);
       L[i * P1 + j] = L[j * P1 + i] = a;
+    }
+  // centrosymmetric: L[i][j] = L[p-i][p-j]
+  for (int i = 0; i < P1; ++i)
+    for (int j = 0; j < P1; ++j) {
+      const int i2 = p - i, j2 = p - j;
+      if (i * P1 + j < i2 * P1 + j2) {
+        const double a = 0.5 * (L[i * P1 + j] + L[i2 * P1 + j2]);
+        L[i * P1 + j] = L[i2 * P1 + j2] = a;
+      }
     }
 }
 
@@ -159,6 +176,69 @@ void gen_eig_diag_mass(int n, const std::vector<double>& L, const std::vector<do
     for (int k = 0; k < n; ++k) S[i * n + k] = Q[i * n + k] / std::sqrt(Md[i]);
 }
 
+// Centrosymmetric generalised problem (L, diag M) on n = 2m+1 points around
+// the centre m: eigenvectors split into even (v[m+j] = v[m-j]) and odd
+// (v[m+j] = -v[m-j], v[m] = 0) ones, computed separately in the folded bases
+// e_0 = d_m, e_j = (d_{m+j} + d_{m-j})/sqrt2 and o_j = (d_{m+j} - d_{m-j})/sqrt2.
+// Columns of S: the m+1 even eigenvectors first, then the m odd ones.
+void gen_eig_centrosym(int n, const std::vector<double>& L, const std::vector<double>& Md, std::vector<double>& S,
+                       std::vector<double>& lam) {
+  const int m = (n - 1) / 2;
+  std::vector<double> A(n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) A[i * n + j] = L[i * n + j] / std::sqrt(Md[i] * Md[j]);
+  const double r2 = 1.0 / std::sqrt(2.0);
+  // basis vectors as coefficient lists (index, coefficient)
+  auto even_vec = [&](int j, std::vector<double>& v) {
+    v.assign(n, 0.0);
+    if (j == 0) v[m] = 1.0;
+    else { v[m + j] = r2; v[m - j] = r2; }
+  };
+  auto odd_vec = [&](int j, std::vector<double>& v) {
+    v.assign(n, 0.0);
+    v[m + j] = r2;
+    v[m - j] = -r2;
+  };
+  std::vector<std::vector<double>> E(m + 1), O(m);
+  for (int j = 0; j <= m; ++j) even_vec(j, E[j]);
+  for (int j = 1; j <= m; ++j) odd_vec(j, O[j - 1]);
+  auto project = [&](const std::vector<std::vector<double>>& B, std::vector<double>& P) {
+    const int k = (int)B.size();
+    P.assign(k * k, 0.0);
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) {
+          if (B[a][i] == 0.0) continue;
+          for (int j = 0; j < n; ++j) s += B[a][i] * A[i * n + j] * B[b][j];
+        }
+        P[a * k + b] = s;
+      }
+    for (int a = 0; a < k; ++a)
+      for (int b = a + 1; b < k; ++b) P[a * k + b] = P[b * k + a] = 0.5 * (P[a * k + b] + P[b * k + a]);
+  };
+  std::vector<double> Ae, Ao, Qe, Qo, le, lo;
+  project(E, Ae);
+  project(O, Ao);
+  jacobi_eig(m + 1, Ae, le, Qe);
+  if (m > 0) jacobi_eig(m, Ao, lo, Qo);
+  S.assign(n * n, 0.0);
+  lam.assign(n, 0.0);
+  for (int k = 0; k <= m; ++k) {
+    lam[k] = le[k];
+    for (int a = 0; a <= m; ++a)
+      for (int i = 0; i < n; ++i) S[i * n + k] += E[a][i] * Qe[a * (m + 1) + k];
+  }
+  for (int k = 0; k < m; ++k) {
+    lam[m + 1 + k] = lo[k];
+    for (int a = 0; a < m; ++a)
+      for (int i = 0; i < n; ++i) S[i * n + (m + 1 + k)] += O[a][i] * Qo[a * m + k];
+  }
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) S[i * n + k] /= std::sqrt(Md[i]);
+  for (int k = m + 1; k < n; ++k) S[m * n + k] = 0.0;  // odd vectors vanish at the centre
+}
+
 double weight_poly(double t) {
   const double t2 = t * t, t4 = t2 * t2;
   return 1.0 - 35.0 * t4 + 84.0 * t4 * t - 70.0 * t4 * t2 + 20.0 * t4 * t2 * t;
@@ -198,6 +278,7 @@ void build_level_tables(HostLevel& L, const std::vector<double>* h) {
     L.starS[d].assign((size_t)(nd + 1) * nS * nS, 0.0);
     L.starLam[d].assign((size_t)(nd + 1) * nS, 1.0);
     L.act[d].assign((size_t)(nd + 1) * nS, 0);
+    L.sym[d].assign(nd + 1, 0);
     for (int c = 0; c <= nd; ++c) {
       std::vector<double> Mb(nS, 0.0), Lb(nS * nS, 0.0);
       for (int a = c - 1; a <= c; ++a) {
@@ -224,7 +305,17 @@ void build_level_tables(HostLevel& L, const std::vector<double>* h) {
       unsigned char* ac = &L.act[d][(size_t)c * nS];
       for (int i = 0; i < nS; ++i) S[i * nS + i] = 1.0;  // identity padding
       const int na = (int)act.size();
-      if (na > 0) {
+      const bool sym = (c >= 1 && c <= nd - 1 && na == nS && h[d][c - 1] == h[d][c]);
+      L.sym[d][c] = sym ? 1 : 0;
+      if (sym) {
+        std::vector<double> Ss, ls;
+        gen_eig_centrosym(nS, Lb, Mb, Ss, ls);
+        for (int i = 0; i < nS; ++i) {
+          ac[i] = 1;
+          lam[i] = ls[i];
+          for (int k = 0; k < nS; ++k) S[i * nS + k] = Ss[i * nS + k];
+        }
+      } else if (na > 0) {
         std::vector<double> La(na * na), Ma(na), Sa, la;
         for (int i = 0; i < na; ++i) {
           Ma[i] = Mb[act[i]];
@@ -239,6 +330,49 @@ void build_level_tables(HostLevel& L, const std::vector<double>* h) {
         for (int i = 0; i < na; ++i)
           for (int k = 0; k < na; ++k) S[act[i] * nS + act[k]] = Sa[i * na + k];
       }
+    }
+  }
+  // vertex lines with identical tables share a class (uniform meshes: the two
+  // boundary lines and one interior class per axis)
+  for (int d = 0; d < 3; ++d) {
+    const int nl = (int)h[d].size() + 1;
+    L.cls[d].assign(nl, -1);
+    L.rep[d].clear();
+    for (int c = 0; c < nl; ++c) {
+      for (int r = 0; r < (int)L.rep[d].size() && L.cls[d][c] < 0; ++r) {
+        const int c2 = L.rep[d][r];
+        bool same = L.sym[d][c] == L.sym[d][c2];
+        for (int i = 0; same && i < nS * nS; ++i)
+          same = L.starS[d][(size_t)c * nS * nS + i] == L.starS[d][(size_t)c2 * nS * nS + i];
+        for (int i = 0; same && i < nS; ++i)
+          same = L.starLam[d][(size_t)c * nS + i] == L.starLam[d][(size_t)c2 * nS + i] &&
+                 L.act[d][(size_t)c * nS + i] == L.act[d][(size_t)c2 * nS + i];
+        if (same) L.cls[d][c] = r;
+      }
+      if (L.cls[d][c] < 0) {
+        L.cls[d][c] = (int)L.rep[d].size();
+        L.rep[d].push_back(c);
+      }
+    }
+  }
+  // inverse 3D eigenvalues 1/(lam + Lam1 + Lam2 + Lam3) per star class, when small enough
+  {
+    const size_t n3 = (size_t)nS * nS * nS;
+    const size_t ncls = L.rep[0].size() * L.rep[1].size() * L.rep[2].size();
+    L.Rtab.clear();
+    if (ncls * n3 <= kMaxRtabEntries) {
+      L.Rtab.resize(ncls * n3);
+      size_t o = 0;
+      for (size_t r1 = 0; r1 < L.rep[0].size(); ++r1)
+        for (size_t r2 = 0; r2 < L.rep[1].size(); ++r2)
+          for (size_t r3 = 0; r3 < L.rep[2].size(); ++r3) {
+            const double* l1 = &L.starLam[0][(size_t)L.rep[0][r1] * nS];
+            const double* l2 = &L.starLam[1][(size_t)L.rep[1][r2] * nS];
+            const double* l3 = &L.starLam[2][(size_t)L.rep[2][r3] * nS];
+            for (int k3 = 0; k3 < nS; ++k3)
+              for (int k2 = 0; k2 < nS; ++k2)
+                for (int k1 = 0; k1 < nS; ++k1) L.Rtab[o++] = 1.0 / (L.lam + l1[k1] + l2[k2] + l3[k3]);
+          }
     }
   }
   // smoother weights at star offset |j| (Sec. 3.2): t = (1 + xi_|j|) / 2

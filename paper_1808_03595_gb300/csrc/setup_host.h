@@ -6,12 +6,19 @@
 
 namespace semmg {
 
+// Largest number of inverse-eigenvalue entries precomputed per level.
+constexpr size_t kMaxRtabEntries = size_t(1) << 25;
+
 struct HostLevel {
   int p = 0;
+  double lam = 0.0;
   std::vector<double> x, w, Ls;                    // GLL nodes, weights, standard stiffness
   std::vector<double> Sref, Sh, a0, ap, lamI;      // interior eigen-tables
   std::vector<double> starS[3], starLam[3];        // per axis: (n_d+1) blocks
   std::vector<unsigned char> act[3];
+  std::vector<unsigned char> sym[3];               // per vertex line: centrosymmetric (folded) tables
+  std::vector<int> cls[3], rep[3];                 // line class per vertex line, representative line per class
+  std::vector<double> Rtab;                        // per star class [k3][k2][k1]: 1/(lam + Lam1 + Lam2 + Lam3)
   std::vector<double> w1d;                         // smoother weights at |offset|
   std::vector<double> J;                           // interpolation from the next coarser level
   int pc = 0;
@@ -28,6 +35,8 @@ void stiffness(int p, const std::vector<double>& x, const std::vector<double>& w
 void lagrange_interp(const std::vector<double>& xc, const std::vector<double>& xf, std::vector<double>& J);
 void jacobi_eig(int n, std::vector<double> A, std::vector<double>& ev, std::vector<double>& V);
 void gen_eig_diag_mass(int n, const std::vector<double>& L, const std::vector<double>& Md, std::vector<double>& S,
+                       std::vector<double>& lam);
+void gen_eig_centrosym(int n, const std::vector<double>& L, const std::vector<double>& Md, std::vector<double>& S,
                        std::vector<double>& lam);
 double weight_poly(double t);
 void build_level_tables(HostLevel& L, const std::vector<double>* h);
