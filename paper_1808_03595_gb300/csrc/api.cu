@@ -192,6 +192,14 @@ Tabs<T> upload_tabs(semmg_ctx* c, const HostLevel& H, const std::vector<double>*
     t.ncls[d] = (int)H.rep[d].size();
   }
   t.Rtab = H.Rtab.empty() ? nullptr : upload<T>(c, H.Rtab, ok);
+  for (int d = 0; d < 3; ++d) {
+    const std::vector<int>& hc = H.hcls[d];
+    int* dhc = (int*)dalloc(c, hc.size() * sizeof(int));
+    if (!dhc || cudaMemcpy(dhc, hc.data(), hc.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) *ok = false;
+    t.hcls[d] = dhc;
+    t.nhcls[d] = (int)H.hval[d].size();
+  }
+  t.Relem = H.Relem.empty() ? nullptr : upload<T>(c, H.Relem, ok);
   t.w1d = upload<T>(c, H.w1d, ok);
   t.J = H.J.empty() ? nullptr : upload<T>(c, H.J, ok);
   t.pc = H.pc;

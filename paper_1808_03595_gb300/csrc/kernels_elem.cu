@@ -14,6 +14,13 @@
 // alpha_d = (2/h_d)^{3/2}, c_f = sqrt(h_a h_b)/2, Sh = diag(w_I) Sref,
 // a_s[k] = sum_i Sref[i][k] L_S[i][s].  H_BI is the transpose.  This gives the
 // O(p^3) Schur complement term H_BI H_II^{-1} H_IB on the six faces.
+//
+// The interior block is centrosymmetric, so Sref splits into even and odd
+// eigenvectors (columns 0..ne-1 even, ne..m-1 odd, ne = (m+1)/2): every 1D
+// transform folds a line about its middle and multiplies half-size blocks,
+// and a_p[k] = +a_0[k] (even k) / -a_0[k] (odd k), so the two faces of one
+// axis enter as their sum (even k_d) and difference (odd k_d).  1/D comes from
+// a table per distinct width triple when one was built.
 #include "semmg_internal.h"
 
 namespace semmg {
@@ -22,124 +29,236 @@ namespace {
 
 template <typename T>
 struct ElemScal {
-  T sf[6];      // c_f alpha_d for the six faces
+  T sf[3];      // c_f alpha_d for the two faces of axis d
   T e[3];       // 4 / h_d^2
+  int64_t cls;  // width-class triple of the element (for the 1/D table)
 };
 
 template <typename T>
 __device__ __forceinline__ ElemScal<T> elem_scalars(const Tabs<T>& t, int a1, int a2, int a3) {
   ElemScal<T> s;
   const double h1 = (double)t.h[0][a1], h2 = (double)t.h[1][a2], h3 = (double)t.h[2][a3];
-  const double c1 = 0.5 * sqrt(h2 * h3), c2 = 0.5 * sqrt(h1 * h3), c3 = 0.5 * sqrt(h1 * h2);
-  const double al1 = pow(2.0 / h1, 1.5), al2 = pow(2.0 / h2, 1.5), al3 = pow(2.0 / h3, 1.5);
-  s.sf[0] = s.sf[1] = (T)(c1 * al1);
-  s.sf[2] = s.sf[3] = (T)(c2 * al2);
-  s.sf[4] = s.sf[5] = (T)(c3 * al3);
+  s.sf[0] = (T)(0.5 * sqrt(h2 * h3) * pow(2.0 / h1, 1.5));
+  s.sf[1] = (T)(0.5 * sqrt(h1 * h3) * pow(2.0 / h2, 1.5));
+  s.sf[2] = (T)(0.5 * sqrt(h1 * h2) * pow(2.0 / h3, 1.5));
   s.e[0] = (T)(4.0 / (h1 * h1));
   s.e[1] = (T)(4.0 / (h2 * h2));
   s.e[2] = (T)(4.0 / (h3 * h3));
+  s.cls = ((int64_t)t.hcls[0][a1] * t.nhcls[1] + t.hcls[1][a2]) * t.nhcls[2] + t.hcls[2][a3];
   return s;
 }
 
-// Forward 2D transform of the six face interiors held in X[f][ib][ia]:
-// X[f][kb][ka] <- sf[f] * sum Sh[ib][kb] Sh[ia][ka] X[f][ib][ia].
-template <typename T>
-__device__ void faces_forward(int m, const T* __restrict__ Sh, T* X, T* Tt, const ElemScal<T>& sc) {
-  const int mm = m * m;
-  for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
-    const int f = idx / mm, r = idx - f * mm, ib = r / m, ka = r - ib * m;
-    const T* x = X + f * mm + ib * m;
-    T s = 0;
-    for (int ia = 0; ia < m; ++ia) s += x[ia] * Sh[ia * m + ka];
-    Tt[idx] = s;
+// ---------------------------------------------------------------- folded line transforms
+// Arrays are [D2][D1][D0] (D0 fastest); a line runs along axis ax (0: D0, 1:
+// D1, 2: D2) and has n = m points.  Folded coordinates of a line: even
+// position j < ne pairs points h+j and n-1-(h+j) (h = n/2), odd position
+// q >= ne pairs points q and n-1-q.
+
+struct Lines {
+  int n, h, ne, D0, D1, total;
+  __device__ __forceinline__ int stride(int ax) const { return ax == 0 ? 1 : (ax == 1 ? D0 : D0 * D1); }
+  __device__ __forceinline__ int pos(int idx, int ax) const {
+    return ax == 0 ? idx % D0 : (ax == 1 ? (idx / D0) % D1 : idx / (D0 * D1));
   }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
-    const int f = idx / mm, r = idx - f * mm, kb = r / m, ka = r - kb * m;
-    const T* tt = Tt + f * mm + ka;
+};
+
+template <typename T>
+__device__ void fold_lines(const Lines& L, int ax, const T* X, T* Y) {
+  const int str = L.stride(ax);
+  for (int idx = threadIdx.x; idx < L.total; idx += blockDim.x) {
+    const int j = L.pos(idx, ax);
+    const int base = idx - j * str;
+    T v;
+    if (j < L.ne) {
+      const int i = L.h + j, mi = L.n - 1 - i;
+      v = (i == mi) ? X[base + i * str] : X[base + i * str] + X[base + mi * str];
+    } else {
+      v = X[base + j * str] - X[base + (L.n - 1 - j) * str];
+    }
+    Y[idx] = v;
+  }
+}
+
+// out[k] = scale * sum_i S[i][k] x[i], from folded x.
+template <typename T>
+__device__ void tx_lines(const Lines& L, int ax, const T* __restrict__ S, const T* Y, T* Z, T scale) {
+  const int str = L.stride(ax), n = L.n;
+  for (int idx = threadIdx.x; idx < L.total; idx += blockDim.x) {
+    const int k = L.pos(idx, ax);
+    const T* y = Y + (idx - k * str);
     T s = 0;
-    for (int ib = 0; ib < m; ++ib) s += Sh[ib * m + kb] * tt[ib * m];
-    X[idx] = sc.sf[f] * s;
+    if (k < L.ne) {
+      for (int j = 0; j < L.ne; ++j) s += S[(L.h + j) * n + k] * y[j * str];
+    } else {
+      for (int q = L.ne; q < n; ++q) s += S[q * n + k] * y[q * str];
+    }
+    Z[idx] = scale * s;
+  }
+}
+
+// Transposed transform into folded form: position j < ne gets
+// E_j = sum_{k even} S[h+j][k] b[k], position q >= ne gets O_q = sum_{k odd} S[q][k] b[k].
+template <typename T>
+__device__ void txT_lines(const Lines& L, int ax, const T* __restrict__ S, const T* B, T* Y) {
+  const int str = L.stride(ax), n = L.n;
+  for (int idx = threadIdx.x; idx < L.total; idx += blockDim.x) {
+    const int j = L.pos(idx, ax);
+    const T* b = B + (idx - j * str);
+    T s = 0;
+    if (j < L.ne) {
+      const T* sr = S + (L.h + j) * n;
+      for (int k = 0; k < L.ne; ++k) s += sr[k] * b[k * str];
+    } else {
+      const T* sr = S + j * n;
+      for (int k = L.ne; k < n; ++k) s += sr[k] * b[k * str];
+    }
+    Y[idx] = s;
+  }
+}
+
+// Natural-order value at element idx from folded E/O data.
+template <typename T>
+__device__ __forceinline__ T unfold_at(const Lines& L, int ax, const T* Y, int idx) {
+  const int str = L.stride(ax);
+  const int i = L.pos(idx, ax);
+  const int base = idx - i * str;
+  const int mi = L.n - 1 - i;
+  if (i == mi) return Y[base + (i - L.h) * str];
+  if (i > mi) return Y[base + (i - L.h) * str] + Y[base + i * str];
+  return Y[base + (mi - L.h) * str] - Y[base + mi * str];
+}
+
+template <typename T>
+__device__ void unfold_lines(const Lines& L, int ax, const T* Y, T* X) {
+  for (int idx = threadIdx.x; idx < L.total; idx += blockDim.x) X[idx] = unfold_at(L, ax, Y, idx);
+}
+
+// ---------------------------------------------------------------- face helpers
+// Six faces X[f][ib][ia] (f = 2d + side) -> pair sums and differences
+// X[2d] = X[2d] + X[2d+1], X[2d+1] = X[2d] - X[2d+1].
+template <typename T>
+__device__ void face_pairs(int mm, T* X) {
+  for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
+    const int d = idx / mm, r = idx - d * mm;
+    const T a = X[(2 * d) * mm + r], b = X[(2 * d + 1) * mm + r];
+    X[(2 * d) * mm + r] = a + b;
+    X[(2 * d + 1) * mm + r] = a - b;
+  }
+}
+
+// forward 2D transform of the six face arrays, scaled by c_f alpha_d
+template <typename T>
+__device__ void faces_forward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc) {
+  fold_lines(F, 0, X, Tt);
+  __syncthreads();
+  tx_lines(F, 0, Sh, Tt, X, (T)1);
+  __syncthreads();
+  fold_lines(F, 1, X, Tt);
+  __syncthreads();
+  const int mm = F.D0 * F.D1;
+  const int str = F.stride(1), n = F.n;
+  for (int idx = threadIdx.x; idx < F.total; idx += blockDim.x) {  // tx along slow index with per-face scale
+    const int k = F.pos(idx, 1);
+    const T* y = Tt + (idx - k * str);
+    T s = 0;
+    if (k < F.ne) {
+      for (int j = 0; j < F.ne; ++j) s += Sh[(F.h + j) * n + k] * y[j * str];
+    } else {
+      for (int q = F.ne; q < n; ++q) s += Sh[q * n + k] * y[q * str];
+    }
+    X[idx] = sc.sf[(idx / mm) >> 1] * s;
   }
   __syncthreads();
 }
 
-// Backward 2D transform: out[f][ib][ia] = sf[f] * sum Sh[ib][kb] Sh[ia][ka] X[f][kb][ka].
+// Back transform of the six reduced arrays (pairs: even / odd parts of axis d)
+// and store of both faces: Z[2d] = sf (Ye + Yo), Z[2d+1] = sf (Ye - Yo).
 template <typename T, typename Store>
-__device__ void faces_backward(int m, const T* __restrict__ Sh, const T* X, T* Tt, const ElemScal<T>& sc,
-                               Store store) {
-  const int mm = m * m;
-  for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
-    const int f = idx / mm, r = idx - f * mm, kb = r / m, ia = r - kb * m;
-    const T* x = X + f * mm + kb * m;
-    T s = 0;
-    for (int ka = 0; ka < m; ++ka) s += x[ka] * Sh[ia * m + ka];
-    Tt[idx] = s;
-  }
+__device__ void faces_backward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc, Store store) {
+  txT_lines(F, 0, Sh, X, Tt);
   __syncthreads();
-  for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
-    const int f = idx / mm, r = idx - f * mm, ib = r / m, ia = r - ib * m;
-    const T* tt = Tt + f * mm + ia;
-    T s = 0;
-    for (int kb = 0; kb < m; ++kb) s += Sh[ib * m + kb] * tt[kb * m];
-    store(idx, sc.sf[f] * s);
+  unfold_lines(F, 0, Tt, X);
+  __syncthreads();
+  txT_lines(F, 1, Sh, X, Tt);
+  __syncthreads();
+  const int mm = F.D0 * F.D1;
+  for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
+    const int d = idx / mm, r = idx - d * mm;
+    const T ye = unfold_at(F, 1, Tt, (2 * d) * mm + r);
+    const T yo = unfold_at(F, 1, Tt, (2 * d + 1) * mm + r);
+    store((2 * d) * mm + r, sc.sf[d] * (ye + yo));
+    store((2 * d + 1) * mm + r, sc.sf[d] * (ye - yo));
   }
 }
 
-// Sum of the six face contributions at eigen-point k (face data in X).
+// Face contribution at eigen-point k from the pair sums (even k_d) / differences (odd k_d).
 template <typename T>
-__device__ __forceinline__ T face_expand(int m, const T* a0, const T* ap, const T* X, int k1, int k2, int k3) {
+__device__ __forceinline__ T face_expand(int m, int ne, const T* a0, const T* X, int k1, int k2, int k3) {
   const int mm = m * m;
-  return a0[k1] * X[0 * mm + k3 * m + k2] + ap[k1] * X[1 * mm + k3 * m + k2]
-       + a0[k2] * X[2 * mm + k3 * m + k1] + ap[k2] * X[3 * mm + k3 * m + k1]
-       + a0[k3] * X[4 * mm + k2 * m + k1] + ap[k3] * X[5 * mm + k2 * m + k1];
+  return a0[k1] * X[(k1 < ne ? 0 : 1) * mm + k3 * m + k2] + a0[k2] * X[(k2 < ne ? 2 : 3) * mm + k3 * m + k1] +
+         a0[k3] * X[(k3 < ne ? 4 : 5) * mm + k2 * m + k1];
 }
 
-// X[f][kb][ka] <- sum_{k_d} a_side[k_d] W(k) for the six faces.
+// X[2d + parity][kb][ka] <- sum over k_d of that parity of a0[k_d] W(k)
 template <typename T>
-__device__ void faces_reduce(int m, const T* a0, const T* ap, const T* W, T* X) {
+__device__ void faces_reduce(int m, int ne, const T* a0, const T* W, T* X) {
   const int mm = m * m;
   for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
     const int f = idx / mm, r = idx - f * mm, kb = r / m, ka = r - kb * m;
-    const T* a = (f & 1) ? ap : a0;
+    const int k0 = (f & 1) ? ne : 0, k1 = (f & 1) ? m : ne;
     T s = 0;
     switch (f >> 1) {
-      case 0: { const T* w = W + (kb * m + ka) * m; for (int k = 0; k < m; ++k) s += a[k] * w[k]; } break;
-      case 1: { const T* w = W + kb * mm + ka; for (int k = 0; k < m; ++k) s += a[k] * w[k * m]; } break;
-      default: { const T* w = W + kb * m + ka; for (int k = 0; k < m; ++k) s += a[k] * w[k * mm]; } break;
+      case 0: { const T* w = W + (kb * m + ka) * m; for (int k = k0; k < k1; ++k) s += a0[k] * w[k]; } break;
+      case 1: { const T* w = W + kb * mm + ka; for (int k = k0; k < k1; ++k) s += a0[k] * w[k * m]; } break;
+      default: { const T* w = W + kb * m + ka; for (int k = k0; k < k1; ++k) s += a0[k] * w[k * mm]; } break;
     }
     X[idx] = s;
   }
 }
 
 template <typename T>
-__device__ void load_tables(int m, const Tabs<T>& t, T* Sh, T* a0, T* ap, T* lI) {
+__device__ __forceinline__ T inv_d(const Tabs<T>& t, const ElemScal<T>& sc, const T* lI, T lam, int64_t idx, int k1,
+                                   int k2, int k3, int64_t n3) {
+  if (t.Relem) return t.Relem[sc.cls * n3 + idx];
+  return (T)1 / (lam + sc.e[0] * lI[k1] + sc.e[1] * lI[k2] + sc.e[2] * lI[k3]);
+}
+
+template <typename T>
+__device__ void load_tables(int m, const Tabs<T>& t, T* Sh, T* a0, T* lI) {
   for (int i = threadIdx.x; i < m * m; i += blockDim.x) Sh[i] = t.Sh[i];
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     a0[i] = t.a0[i];
-    ap[i] = t.ap[i];
     lI[i] = t.lamI[i];
   }
 }
 
+__device__ __forceinline__ void elem_coords(const Geo& G, int64_t e, int* a1, int* a2, int* a3) {
+  *a1 = (int)(e % G.n1);
+  *a2 = (int)((e / G.n1) % G.n2);
+  *a3 = (int)(e / ((int64_t)G.n1 * G.n2));
+}
+
 // y_e = H_BI H_II^{-1} H_IB u on the six faces of every element -> Z[e][f][.]
-// Work regions: 0 tables (Sh, a0, ap, Lam), 1 X (6 m^2), 2 Tt (6 m^2), 3 W (m^3).
+// Work regions: 0 tables (Sh, a0, Lam), 1 X (6 m^2), 2 Tt (6 m^2), 3 W (m^3).
 template <typename T>
 __global__ void __launch_bounds__(256) k_elem_schur(Geo G, Tabs<T> t, const T* __restrict__ u, T* __restrict__ Z,
                                                      T* ws, WsPlan wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = G.m, mm = m * m;
+  const int64_t n3 = (int64_t)mm * m;
   T* Sh = ws_ptr<T>(wp, 0, smem_raw, ws);
   T* a0 = Sh + mm;
-  T* ap = a0 + m;
-  T* lI = ap + m;
+  T* lI = a0 + m;
   T* X = ws_ptr<T>(wp, 1, smem_raw, ws);
   T* Tt = ws_ptr<T>(wp, 2, smem_raw, ws);
   T* W = ws_ptr<T>(wp, 3, smem_raw, ws);
-  load_tables(m, t, Sh, a0, ap, lI);
+  load_tables(m, t, Sh, a0, lI);
+  const Lines F{m, m / 2, (m + 1) / 2, m, m, 6 * mm};
+  const int ne = F.ne;
   const T lam = (T)G.lam;
   for (int64_t e = blockIdx.x; e < G.nelem; e += gridDim.x) {
-    const int a1 = (int)(e % G.n1), a2 = (int)((e / G.n1) % G.n2), a3 = (int)(e / ((int64_t)G.n1 * G.n2));
+    int a1, a2, a3;
+    elem_coords(G, e, &a1, &a2, &a3);
     const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
     __syncthreads();
     for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
@@ -147,90 +266,65 @@ __global__ void __launch_bounds__(256) k_elem_schur(Geo G, Tabs<T> t, const T* _
       X[idx] = u[elem_face_base(G, a1, a2, a3, f) + (idx - f * mm)];
     }
     __syncthreads();
-    faces_forward(m, Sh, X, Tt, sc);
-    for (int idx = threadIdx.x; idx < m * mm; idx += blockDim.x) {
-      const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
-      const T D = lam + sc.e[0] * lI[k1] + sc.e[1] * lI[k2] + sc.e[2] * lI[k3];
-      W[idx] = face_expand(m, a0, ap, X, k1, k2, k3) / D;
+    face_pairs(mm, X);
+    __syncthreads();
+    faces_forward(F, Sh, X, Tt, sc);
+    for (int64_t idx = threadIdx.x; idx < n3; idx += blockDim.x) {
+      const int k1 = (int)(idx % m), k2 = (int)((idx / m) % m), k3 = (int)(idx / mm);
+      W[idx] = face_expand(m, ne, a0, X, k1, k2, k3) * inv_d(t, sc, lI, lam, idx, k1, k2, k3, n3);
     }
     __syncthreads();
-    faces_reduce(m, a0, ap, W, X);
+    faces_reduce(m, ne, a0, W, X);
     __syncthreads();
     T* Ze = Z + e * 6 * mm;
-    faces_backward(m, Sh, X, Tt, sc, [&](int idx, T v) { Ze[idx] = v; });
+    faces_backward(F, Sh, X, Tt, sc, [&](int idx, T v) { Ze[idx] = v; });
   }
 }
 
-// Interior 3D transforms with the reference eigenvectors (scale applied by the caller).
-// forward: B[k3][k2][k1] = sum Sref[i1][k1] Sref[i2][k2] Sref[i3][k3] A[i3][i2][i1]; A is clobbered.
-__device__ void interior_forward(int m, const double* Sr, double* A, double* B) {
-  const int mm = m * m, mmm = mm * m;
-  for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {  // along x1
-    const int k1 = idx % m, r = idx - k1;
-    double s = 0;
-    for (int i = 0; i < m; ++i) s += A[r + i] * Sr[i * m + k1];
-    B[idx] = s;
-  }
+// Interior 3D transforms with the folded reference eigenvectors.
+// forward: A <- scale * (Sref^T (x) Sref^T (x) Sref^T) A, B is scratch.
+__device__ void interior_forward(const Lines& I, const double* Sr, double* A, double* B, double scale) {
+  fold_lines(I, 0, A, B);
   __syncthreads();
-  for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {  // along x2
-    const int k1 = idx % m, k2 = (idx / m) % m, i3 = idx / mm;
-    const double* b = B + i3 * mm + k1;
-    double s = 0;
-    for (int i = 0; i < m; ++i) s += Sr[i * m + k2] * b[i * m];
-    A[idx] = s;
-  }
+  tx_lines(I, 0, Sr, B, A, 1.0);
   __syncthreads();
-  for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {  // along x3
-    const int r = idx % mm, k3 = idx / mm;
-    const double* a = A + r;
-    double s = 0;
-    for (int i = 0; i < m; ++i) s += Sr[i * m + k3] * a[i * mm];
-    B[idx] = s;
-  }
+  fold_lines(I, 1, A, B);
+  __syncthreads();
+  tx_lines(I, 1, Sr, B, A, 1.0);
+  __syncthreads();
+  fold_lines(I, 2, A, B);
+  __syncthreads();
+  tx_lines(I, 2, Sr, B, A, scale);
   __syncthreads();
 }
 
-// backward: A[i3][i2][i1] = sum Sref[i1][k1] Sref[i2][k2] Sref[i3][k3] B[k3][k2][k1]; B is clobbered.
-__device__ void interior_backward(int m, const double* Sr, double* B, double* A) {
-  const int mm = m * m, mmm = mm * m;
-  for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {  // along x3
-    const int r = idx % mm, i3 = idx / mm;
-    const double* b = B + r;
-    double s = 0;
-    for (int k = 0; k < m; ++k) s += Sr[i3 * m + k] * b[k * mm];
-    A[idx] = s;
-  }
+// backward along x3 and x2 (natural order in A afterwards), then the x1
+// transposed transform into B; the caller unfolds B along x1.
+__device__ void interior_backward(const Lines& I, const double* Sr, double* A, double* B) {
+  txT_lines(I, 2, Sr, A, B);
   __syncthreads();
-  for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {  // along x2
-    const int k1 = idx % m, i2 = (idx / m) % m, i3 = idx / mm;
-    const double* a = A + i3 * mm + k1;
-    double s = 0;
-    for (int k = 0; k < m; ++k) s += Sr[i2 * m + k] * a[k * m];
-    B[idx] = s;
-  }
+  unfold_lines(I, 2, B, A);
   __syncthreads();
-  for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {  // along x1
-    const int i1 = idx % m, r = idx - i1;
-    double s = 0;
-    for (int k = 0; k < m; ++k) s += B[r + k] * Sr[i1 * m + k];
-    A[idx] = s;
-  }
+  txT_lines(I, 1, Sr, A, B);
+  __syncthreads();
+  unfold_lines(I, 1, B, A);
+  __syncthreads();
+  txT_lines(I, 0, Sr, A, B);
   __syncthreads();
 }
 
 struct FdmSmem {
-  double *Sh, *Sr, *a0, *ap, *lI, *X, *Tt, *A, *B;
+  double *Sh, *Sr, *a0, *lI, *X, *Tt, *A, *B;
 };
 
-// Work regions: 0 tables (Sh, Sref, a0, ap, Lam), 1 X (6 m^2), 2 Tt (6 m^2), 3 A+B (2 m^3).
+// Work regions: 0 tables (Sh, Sref, a0, Lam), 1 X (6 m^2), 2 Tt (6 m^2), 3 A+B (2 m^3).
 __device__ FdmSmem fdm_layout(int m, unsigned char* smem, double* ws, const WsPlan& wp) {
   const int mm = m * m;
   FdmSmem s;
   s.Sh = ws_ptr<double>(wp, 0, smem, ws);
   s.Sr = s.Sh + mm;
   s.a0 = s.Sr + mm;
-  s.ap = s.a0 + m;
-  s.lI = s.ap + m;
+  s.lI = s.a0 + m;
   s.X = ws_ptr<double>(wp, 1, smem, ws);
   s.Tt = ws_ptr<double>(wp, 2, smem, ws);
   s.A = ws_ptr<double>(wp, 3, smem, ws);
@@ -238,17 +332,26 @@ __device__ FdmSmem fdm_layout(int m, unsigned char* smem, double* ws, const WsPl
   return s;
 }
 
+__device__ __forceinline__ int64_t interior_node(const Geo& G, int a1, int a2, int a3, int idx) {
+  const int m = G.m, p = G.p;
+  const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / (m * m);
+  const int64_t N1 = (int64_t)G.n1 * p + 1, N2 = (int64_t)G.n2 * p + 1;
+  return ((int64_t)(a3 * p + i3 + 1) * N2 + (a2 * p + i2 + 1)) * N1 + (a1 * p + i1 + 1);
+}
+
 // Z[e][f] = (H_BI H_II^{-1} F_I) on the faces, F_I = (M f)_I element-local.
 __global__ void __launch_bounds__(256) k_elem_condense(Geo G, Tabs<double> t, const double* __restrict__ f,
                                                         double* __restrict__ Z, double* ws, WsPlan wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = G.m, mm = m * m, mmm = mm * m, p = G.p;
+  const int m = G.m, mm = m * m, mmm = mm * m;
   FdmSmem s = fdm_layout(m, smem_raw, ws, wp);
-  load_tables(m, t, s.Sh, s.a0, s.ap, s.lI);
+  load_tables(m, t, s.Sh, s.a0, s.lI);
   for (int i = threadIdx.x; i < mm; i += blockDim.x) s.Sr[i] = t.Sref[i];
-  const int N1 = G.n1 * p + 1, N2 = G.n2 * p + 1;
+  const Lines F{m, m / 2, (m + 1) / 2, m, m, 6 * mm};
+  const Lines I{m, m / 2, (m + 1) / 2, m, m, mmm};
   for (int64_t e = blockIdx.x; e < G.nelem; e += gridDim.x) {
-    const int a1 = (int)(e % G.n1), a2 = (int)((e / G.n1) % G.n2), a3 = (int)(e / ((int64_t)G.n1 * G.n2));
+    int a1, a2, a3;
+    elem_coords(G, e, &a1, &a2, &a3);
     const ElemScal<double> sc = elem_scalars(t, a1, a2, a3);
     const double h1 = t.h[0][a1], h2 = t.h[1][a2], h3 = t.h[2][a3];
     const double vol = h1 * h2 * h3 / 8.0;
@@ -256,21 +359,19 @@ __global__ void __launch_bounds__(256) k_elem_condense(Geo G, Tabs<double> t, co
     __syncthreads();
     for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
       const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / mm;
-      const int64_t g = ((int64_t)(a3 * p + i3 + 1) * N2 + (a2 * p + i2 + 1)) * N1 + (a1 * p + i1 + 1);
-      s.A[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] * f[g];
+      s.A[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] * f[interior_node(G, a1, a2, a3, idx)];
     }
     __syncthreads();
-    interior_forward(m, s.Sr, s.A, s.B);
+    interior_forward(I, s.Sr, s.A, s.B, sig);
     for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
       const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
-      const double D = G.lam + sc.e[0] * s.lI[k1] + sc.e[1] * s.lI[k2] + sc.e[2] * s.lI[k3];
-      s.B[idx] = sig * s.B[idx] / D;
+      s.A[idx] *= inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
     }
     __syncthreads();
-    faces_reduce(m, s.a0, s.ap, s.B, s.X);
+    faces_reduce(m, F.ne, s.a0, s.A, s.X);
     __syncthreads();
     double* Ze = Z + e * 6 * mm;
-    faces_backward(m, s.Sh, s.X, s.Tt, sc, [&](int idx, double v) { Ze[idx] = v; });
+    faces_backward(F, s.Sh, s.X, s.Tt, sc, [&](int idx, double v) { Ze[idx] = v; });
   }
 }
 
@@ -279,13 +380,15 @@ __global__ void __launch_bounds__(256) k_elem_recover(Geo G, Tabs<double> t, con
                                                        const double* __restrict__ uh, double* __restrict__ un,
                                                        double* ws, WsPlan wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = G.m, mm = m * m, mmm = mm * m, p = G.p;
+  const int m = G.m, mm = m * m, mmm = mm * m;
   FdmSmem s = fdm_layout(m, smem_raw, ws, wp);
-  load_tables(m, t, s.Sh, s.a0, s.ap, s.lI);
+  load_tables(m, t, s.Sh, s.a0, s.lI);
   for (int i = threadIdx.x; i < mm; i += blockDim.x) s.Sr[i] = t.Sref[i];
-  const int N1 = G.n1 * p + 1, N2 = G.n2 * p + 1;
+  const Lines F{m, m / 2, (m + 1) / 2, m, m, 6 * mm};
+  const Lines I{m, m / 2, (m + 1) / 2, m, m, mmm};
   for (int64_t e = blockIdx.x; e < G.nelem; e += gridDim.x) {
-    const int a1 = (int)(e % G.n1), a2 = (int)((e / G.n1) % G.n2), a3 = (int)(e / ((int64_t)G.n1 * G.n2));
+    int a1, a2, a3;
+    elem_coords(G, e, &a1, &a2, &a3);
     const ElemScal<double> sc = elem_scalars(t, a1, a2, a3);
     const double h1 = t.h[0][a1], h2 = t.h[1][a2], h3 = t.h[2][a3];
     const double vol = h1 * h2 * h3 / 8.0;
@@ -293,28 +396,26 @@ __global__ void __launch_bounds__(256) k_elem_recover(Geo G, Tabs<double> t, con
     __syncthreads();
     for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
       const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / mm;
-      const int64_t g = ((int64_t)(a3 * p + i3 + 1) * N2 + (a2 * p + i2 + 1)) * N1 + (a1 * p + i1 + 1);
-      s.A[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] * f[g];
+      s.A[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] * f[interior_node(G, a1, a2, a3, idx)];
     }
     for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
       const int fc = idx / mm;
       s.X[idx] = uh[elem_face_base(G, a1, a2, a3, fc) + (idx - fc * mm)];
     }
     __syncthreads();
-    interior_forward(m, s.Sr, s.A, s.B);
-    faces_forward(m, s.Sh, s.X, s.Tt, sc);
+    interior_forward(I, s.Sr, s.A, s.B, sig);
+    face_pairs(mm, s.X);
+    __syncthreads();
+    faces_forward(F, s.Sh, s.X, s.Tt, sc);
     for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
       const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
-      const double D = G.lam + sc.e[0] * s.lI[k1] + sc.e[1] * s.lI[k2] + sc.e[2] * s.lI[k3];
-      s.B[idx] = (sig * s.B[idx] - face_expand(m, s.a0, s.ap, s.X, k1, k2, k3)) / D;
+      s.A[idx] = (s.A[idx] - face_expand(m, F.ne, s.a0, s.X, k1, k2, k3)) *
+                 inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
     }
     __syncthreads();
-    interior_backward(m, s.Sr, s.B, s.A);
-    for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
-      const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / mm;
-      const int64_t g = ((int64_t)(a3 * p + i3 + 1) * N2 + (a2 * p + i2 + 1)) * N1 + (a1 * p + i1 + 1);
-      un[g] = sig * s.A[idx];
-    }
+    interior_backward(I, s.Sr, s.A, s.B);
+    for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x)
+      un[interior_node(G, a1, a2, a3, idx)] = sig * unfold_at(I, 0, s.B, idx);
   }
 }
 
@@ -326,7 +427,7 @@ template <typename T>
 LaunchCfg plan_elem_schur(const Geo& G, int nsm) {
   LaunchCfg c;
   const size_t m = G.m, mm = m * m;
-  const size_t sizes[4] = {mm + 3 * m, 6 * mm, 6 * mm, mm * m};
+  const size_t sizes[4] = {mm + 2 * m, 6 * mm, 6 * mm, mm * m};
   c.ws = plan_regions(sizes, 4, sizeof(T), kSmemCap, &c.smem);
   c.ok = plan_ok(c.ws, sizes, 4, sizeof(T), c.smem);
   const int64_t grid = (int64_t)nsm * blocks_per_sm(c.smem);
@@ -345,7 +446,7 @@ void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, 
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm) {
   LaunchCfg c;
   const size_t m = G.m, mm = m * m;
-  const size_t sizes[4] = {2 * mm + 3 * m, 6 * mm, 6 * mm, 2 * mm * m};
+  const size_t sizes[4] = {2 * mm + 2 * m, 6 * mm, 6 * mm, 2 * mm * m};
   c.ws = plan_regions(sizes, 4, sizeof(double), kSmemCap, &c.smem);
   c.ok = plan_ok(c.ws, sizes, 4, sizeof(double), c.smem);
   const int64_t grid = (int64_t)nsm * blocks_per_sm(c.smem);

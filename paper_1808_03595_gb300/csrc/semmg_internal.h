@@ -190,10 +190,13 @@ struct Tabs {
   const T* w;      // GLL weights, p+1
   const T* Ls;     // standard-element stiffness, (p+1)^2 row-major
   const T* Sh;     // m x m: Sh[i][k] = w[i+1] Sref[i][k]
-  const T* Sref;   // m x m: interior generalised eigenvectors, Sref^T M_II Sref = I
+  const T* Sref;   // m x m: interior generalised eigenvectors, Sref^T M_II Sref = I, columns even then odd
   const T* a0;     // m: sum_i Sref[i][k] Ls[i+1][0]
   const T* ap;     // m: sum_i Sref[i][k] Ls[i+1][p]
   const T* lamI;   // m: interior eigenvalues
+  const int* hcls[3];  // per axis: width class of every element
+  int nhcls[3];        // width classes per axis
+  const T* Relem;      // per width-class triple: m^3 values 1/(lam + sum 4/h^2 Lam), or null
   const T* h[3];   // element widths per axis
   const T* starS[3];    // per axis: nv_d blocks of nS x nS, S[j][k], row j <-> offset j-m
   const T* starLam[3];  // per axis: nv_d x nS

@@ -176,43 +176,42 @@ void gen_eig_diag_mass(int n, const std::vector<double>& L, const std::vector<do
     for (int k = 0; k < n; ++k) S[i * n + k] = Q[i * n + k] / std::sqrt(Md[i]);
 }
 
-// Centrosymmetric generalised problem (L, diag M) on n = 2m+1 points around
-// the centre m: eigenvectors split into even (v[m+j] = v[m-j]) and odd
-// (v[m+j] = -v[m-j], v[m] = 0) ones, computed separately in the folded bases
-// e_0 = d_m, e_j = (d_{m+j} + d_{m-j})/sqrt2 and o_j = (d_{m+j} - d_{m-j})/sqrt2.
-// Columns of S: the m+1 even eigenvectors first, then the m odd ones.
+// Centrosymmetric generalised problem (L, diag M) on n points (L[i][j] =
+// L[n-1-i][n-1-j], M likewise): eigenvectors split into even (v[i] =
+// v[n-1-i]) and odd (v[i] = -v[n-1-i]) ones, computed separately in the
+// folded bases.  With h = n/2 (rounded down) and ne = (n+1)/2, the columns of
+// S hold the ne even eigenvectors first, then the n - ne odd ones.  The
+// folded coordinates are: even position j < ne pairs rows h+j and n-1-(h+j)
+// (the centre alone when they coincide); odd position q >= ne pairs rows q
+// and n-1-q.
 void gen_eig_centrosym(int n, const std::vector<double>& L, const std::vector<double>& Md, std::vector<double>& S,
                        std::vector<double>& lam) {
-  const int m = (n - 1) / 2;
+  const int h = n / 2, ne = (n + 1) / 2, no = n - ne;
   std::vector<double> A(n * n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) A[i * n + j] = L[i * n + j] / std::sqrt(Md[i] * Md[j]);
   const double r2 = 1.0 / std::sqrt(2.0);
-  // basis vectors as coefficient lists (index, coefficient)
-  auto even_vec = [&](int j, std::vector<double>& v) {
-    v.assign(n, 0.0);
-    if (j == 0) v[m] = 1.0;
-    else { v[m + j] = r2; v[m - j] = r2; }
-  };
-  auto odd_vec = [&](int j, std::vector<double>& v) {
-    v.assign(n, 0.0);
-    v[m + j] = r2;
-    v[m - j] = -r2;
-  };
-  std::vector<std::vector<double>> E(m + 1), O(m);
-  for (int j = 0; j <= m; ++j) even_vec(j, E[j]);
-  for (int j = 1; j <= m; ++j) odd_vec(j, O[j - 1]);
+  std::vector<std::vector<double>> E(ne, std::vector<double>(n, 0.0)), O(no, std::vector<double>(n, 0.0));
+  for (int j = 0; j < ne; ++j) {
+    const int i = h + j, mi = n - 1 - i;
+    if (i == mi) E[j][i] = 1.0;
+    else { E[j][i] = r2; E[j][mi] = r2; }
+  }
+  for (int q = ne; q < n; ++q) {
+    O[q - ne][q] = r2;
+    O[q - ne][n - 1 - q] = -r2;
+  }
   auto project = [&](const std::vector<std::vector<double>>& B, std::vector<double>& P) {
     const int k = (int)B.size();
     P.assign(k * k, 0.0);
     for (int a = 0; a < k; ++a)
       for (int b = 0; b < k; ++b) {
-        double s = 0.0;
+        double sum = 0.0;
         for (int i = 0; i < n; ++i) {
           if (B[a][i] == 0.0) continue;
-          for (int j = 0; j < n; ++j) s += B[a][i] * A[i * n + j] * B[b][j];
+          for (int j = 0; j < n; ++j) sum += B[a][i] * A[i * n + j] * B[b][j];
         }
-        P[a * k + b] = s;
+        P[a * k + b] = sum;
       }
     for (int a = 0; a < k; ++a)
       for (int b = a + 1; b < k; ++b) P[a * k + b] = P[b * k + a] = 0.5 * (P[a * k + b] + P[b * k + a]);
@@ -220,23 +219,35 @@ void gen_eig_centrosym(int n, const std::vector<double>& L, const std::vector<do
   std::vector<double> Ae, Ao, Qe, Qo, le, lo;
   project(E, Ae);
   project(O, Ao);
-  jacobi_eig(m + 1, Ae, le, Qe);
-  if (m > 0) jacobi_eig(m, Ao, lo, Qo);
+  jacobi_eig(ne, Ae, le, Qe);
+  if (no > 0) jacobi_eig(no, Ao, lo, Qo);
   S.assign(n * n, 0.0);
   lam.assign(n, 0.0);
-  for (int k = 0; k <= m; ++k) {
+  for (int k = 0; k < ne; ++k) {
     lam[k] = le[k];
-    for (int a = 0; a <= m; ++a)
-      for (int i = 0; i < n; ++i) S[i * n + k] += E[a][i] * Qe[a * (m + 1) + k];
+    for (int a = 0; a < ne; ++a)
+      for (int i = 0; i < n; ++i) S[i * n + k] += E[a][i] * Qe[a * ne + k];
   }
-  for (int k = 0; k < m; ++k) {
-    lam[m + 1 + k] = lo[k];
-    for (int a = 0; a < m; ++a)
-      for (int i = 0; i < n; ++i) S[i * n + (m + 1 + k)] += O[a][i] * Qo[a * m + k];
+  for (int k = 0; k < no; ++k) {
+    lam[ne + k] = lo[k];
+    for (int a = 0; a < no; ++a)
+      for (int i = 0; i < n; ++i) S[i * n + (ne + k)] += O[a][i] * Qo[a * no + k];
   }
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) S[i * n + k] /= std::sqrt(Md[i]);
-  for (int k = m + 1; k < n; ++k) S[m * n + k] = 0.0;  // odd vectors vanish at the centre
+  // exact parity: odd vectors vanish at a centre node, mirrored rows are equal up to sign
+  for (int i = 0; i < n; ++i) {
+    const int mi = n - 1 - i;
+    if (mi < i) continue;
+    for (int k = 0; k < n; ++k) {
+      if (mi == i) {
+        if (k >= ne) S[i * n + k] = 0.0;
+      } else {
+        const double v = S[mi * n + k];
+        S[i * n + k] = k < ne ? v : -v;
+      }
+    }
+  }
 }
 
 double weight_poly(double t) {
@@ -260,7 +271,7 @@ void build_level_tables(HostLevel& L, const std::vector<double>* h) {
       Mii[i] = L.w[i + 1];
       for (int j = 0; j < m; ++j) Lii[i * m + j] = L.Ls[(i + 1) * P1 + (j + 1)];
     }
-    gen_eig_diag_mass(m, Lii, Mii, L.Sref, L.lamI);
+    gen_eig_centrosym(m, Lii, Mii, L.Sref, L.lamI);
     L.Sh.resize(m * m);
     L.a0.assign(m, 0.0);
     L.ap.assign(m, 0.0);
@@ -372,6 +383,40 @@ void build_level_tables(HostLevel& L, const std::vector<double>* h) {
             for (int k3 = 0; k3 < nS; ++k3)
               for (int k2 = 0; k2 < nS; ++k2)
                 for (int k1 = 0; k1 < nS; ++k1) L.Rtab[o++] = 1.0 / (L.lam + l1[k1] + l2[k2] + l3[k3]);
+          }
+    }
+  }
+  // element classes: elements with equal widths share their interior eigen-tables,
+  // so 1/(lam + sum_d 4/h_d^2 Lam[k_d]) is tabulated per distinct width triple
+  for (int d = 0; d < 3; ++d) {
+    L.hval[d].clear();
+    L.hcls[d].assign(h[d].size(), 0);
+    for (size_t a = 0; a < h[d].size(); ++a) {
+      int found = -1;
+      for (size_t r = 0; r < L.hval[d].size(); ++r)
+        if (L.hval[d][r] == h[d][a]) found = (int)r;
+      if (found < 0) {
+        found = (int)L.hval[d].size();
+        L.hval[d].push_back(h[d][a]);
+      }
+      L.hcls[d][a] = found;
+    }
+  }
+  L.Relem.clear();
+  if (m > 0) {
+    const size_t n3 = (size_t)m * m * m;
+    const size_t ncls = L.hval[0].size() * L.hval[1].size() * L.hval[2].size();
+    if (ncls * n3 <= kMaxRtabEntries) {
+      L.Relem.resize(ncls * n3);
+      size_t o = 0;
+      for (double h1 : L.hval[0])
+        for (double h2 : L.hval[1])
+          for (double h3 : L.hval[2]) {
+            const double e1 = 4.0 / (h1 * h1), e2 = 4.0 / (h2 * h2), e3 = 4.0 / (h3 * h3);
+            for (int k3 = 0; k3 < m; ++k3)
+              for (int k2 = 0; k2 < m; ++k2)
+                for (int k1 = 0; k1 < m; ++k1)
+                  L.Relem[o++] = 1.0 / (L.lam + e1 * L.lamI[k1] + e2 * L.lamI[k2] + e3 * L.lamI[k3]);
           }
     }
   }

@@ -13,7 +13,10 @@ struct HostLevel {
   int p = 0;
   double lam = 0.0;
   std::vector<double> x, w, Ls;                    // GLL nodes, weights, standard stiffness
-  std::vector<double> Sref, Sh, a0, ap, lamI;      // interior eigen-tables
+  std::vector<double> Sref, Sh, a0, ap, lamI;      // interior eigen-tables (columns: even, then odd eigenvectors)
+  std::vector<double> hval[3];                     // distinct element widths per axis
+  std::vector<int> hcls[3];                        // width class of every element per axis
+  std::vector<double> Relem;                       // per width-class triple [k3][k2][k1]: 1/(lam + sum 4/h^2 Lam)
   std::vector<double> starS[3], starLam[3];        // per axis: (n_d+1) blocks
   std::vector<unsigned char> act[3];
   std::vector<unsigned char> sym[3];               // per vertex line: centrosymmetric (folded) tables
