@@ -303,6 +303,8 @@ def run_semmg(args, world, rank, local, pg):
         "roofline": roof,
         "clocks": clk,
     }
+    if args.batch and rank == 0:
+        line["batched"] = run_batch(args, dev, stream, flush)
     if rank == 0 and not args.no_cpu_baseline:
         n, dt, _ = oracle_sample(args.cpu_sample_p)
         line["cpu_baseline"] = {"value": n / dt, "unit": "unknowns/s", "cores": os.cpu_count(), "kind": "oracle",
@@ -316,6 +318,47 @@ def run_semmg(args, world, rank, local, pg):
     return 0
 
 
+def run_batch(args, dev, stream, flush):
+    """64 independent Helmholtz solves (n ~ U{2..12}, p ~ U{4..24}, lambda = 10^U(-2,3), mixed form) in one
+    CUDA graph launch; throughput = total unknowns / graph time."""
+    import torch
+    from paper_1808_03595_gb300 import Batch, Context
+    cases = workloads.batch64()
+    ctxs, fs, us = [], [], []
+    for h, p, lam, f in cases:
+        ctxs.append(Context(h, p, lam, p0=2, precision="mixed"))
+        fs.append(torch.as_tensor(f, dtype=torch.float64, device=dev))
+        us.append(torch.empty_like(fs[-1]))
+    t0 = time.perf_counter()
+    b = Batch(ctxs, fs, us)
+    t_capture = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        b.solve()
+    ms = 0.0
+    iters = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, infos = b.solve()
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        assert rc == 0 and all(i.res_final <= 1e-10 * i.res0 for i in infos)
+        iters = [i.iters for i in infos]
+    unknowns = sum(int(f.numel()) for f in fs)
+    out = {"workload": "batch64 (n~U{2..12}, p~U{4..24}, lambda=10^U(-2,3), f~U(-1,1), seed 1808035955)",
+           "value": unknowns * args.steps / (ms / 1e3), "unit": "unknowns/s", "dtype": "f64+f32",
+           "solves": len(cases), "unknowns": unknowns, "ms_per_batch": ms / args.steps,
+           "graph_nodes": b.graph_nodes(), "capture_s": t_capture,
+           "iterations": {"min": min(iters), "max": max(iters), "mean": sum(iters) / len(iters)}}
+    b.close()
+    for c in ctxs:
+        c.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,6 +370,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--forms", default="fp64,mixed", help="forms to run: fp64 (timed headline) and/or mixed")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing (profiling runs)")
+    ap.add_argument("--batch", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the 64-solve batched graph workload")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -186,6 +186,32 @@ int semmg_solve(semmg_ctx* ctx, const double* f_nodal, double* u_nodal, double r
 int semmg_solve_host(semmg_ctx* ctx, const double* f_host, double* u_host, double rtol,
                      semmg_info* info, void* stream);
 
+/* ------------------------------------------------------------------ batched form
+ * Many independent solves (each its own context: any mesh, p, lambda,
+ * precision) captured once into one CUDA graph and launched with one call.
+ * Each solve is a branch of the graph: condensation, then a device-side loop
+ * (a conditional WHILE node) of V-cycle, FP64 residual and norm, whose check
+ * kernel ends the loop when ||r|| <= rtol ||r_0|| or after max_iter cycles,
+ * then interior recovery.  Branches are independent, so solves run
+ * concurrently; no host round trip happens between cycles (Algorithm 4 with
+ * the stopping test of Sec. 5.2 evaluated on the device).
+ *
+ * semmg_batch_create captures the graph: f[i] and u[i] are device nodal
+ * arrays of context i that the graph keeps using (refill f[i] in place to
+ * solve again).  The contexts must stay alive and must not be used by other
+ * calls while a batch launch runs.  Allocates a small control block.
+ * semmg_batch_solve launches the graph on `stream`, waits for it, and fills
+ * infos[0..nb-1] (NULL allowed); it returns SEMMG_OK when every solve
+ * converged, else the first non-zero status.
+ * semmg_batch_graph_nodes reports the node count of the captured top-level
+ * graph (kernel and memset nodes plus one conditional node per solve). */
+typedef struct semmg_batch semmg_batch;
+int semmg_batch_create(semmg_ctx* const* ctxs, int nb, const double* const* f_nodal, double* const* u_nodal,
+                       double rtol, void* stream, semmg_batch** out);
+int semmg_batch_solve(semmg_batch* batch, semmg_info* infos, void* stream);
+int semmg_batch_graph_nodes(const semmg_batch* batch, int64_t* nodes);
+void semmg_batch_destroy(semmg_batch* batch);
+
 /* ------------------------------------------------------------------ no-allocation smoothing
  * The paper has no counterpart to this entry point; it exists for callers of
  * this library that must not allocate device memory while they work -- for

@@ -7,13 +7,16 @@ tensors.  Nothing is imported eagerly so that the build step can run without
 a GPU.
 """
 
-__all__ = ["Context", "build"]
+__all__ = ["Context", "Batch", "build"]
 
 
 def __getattr__(name):
     if name == "Context":
         from .solver import Context
         return Context
+    if name == "Batch":
+        from .solver import Batch
+        return Batch
     if name == "build":
         from .build import build
         return build

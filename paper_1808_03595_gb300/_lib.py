@@ -72,6 +72,11 @@ SIGNATURES = {
     "semmg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(semmg_info), c_void_p]),
     "semmg_solve_host": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(semmg_info), c_void_p]),
     "semmg_smooth_noalloc": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "semmg_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_void_p),
+                                   ctypes.POINTER(c_void_p), c_double, c_void_p, ctypes.POINTER(c_void_p)]),
+    "semmg_batch_solve": (c_int, [c_void_p, ctypes.POINTER(semmg_info), c_void_p]),
+    "semmg_batch_graph_nodes": (c_int, [c_void_p, ctypes.POINTER(c_int64)]),
+    "semmg_batch_destroy": (None, [c_void_p]),
     "semmg_set_timing": (c_int, [c_void_p, c_int]),
     "semmg_get_kstat": (c_int, [c_void_p, c_int, ctypes.POINTER(semmg_kstat)]),
     "semmg_reset_kstats": (c_int, [c_void_p]),

@@ -852,3 +852,237 @@ int semmg_reset_kstats(semmg_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- batched form (one CUDA graph)
+
+namespace {
+
+struct BatchCtl {
+  double res0sq;
+  double ressq;
+  double rtol;
+  int iters;
+  int maxit;
+  int status;
+  int pad;
+};
+
+// r_0 known: start the loop unless the right-hand side is zero or not finite.
+__global__ void k_batch_init(BatchCtl* ctl, const double* dnorm, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double r0 = *dnorm;
+  ctl->res0sq = r0;
+  ctl->ressq = r0;
+  ctl->iters = 0;
+  const bool finite = isfinite(r0);
+  ctl->status = finite ? SEMMG_OK : SEMMG_ERR_NONFINITE;
+  cudaGraphSetConditional(h, (finite && r0 > 0.0 && ctl->maxit > 0) ? 1u : 0u);
+}
+
+// after a cycle: continue while ||r||^2 > rtol^2 ||r_0||^2 and below the cycle cap
+__global__ void k_batch_check(BatchCtl* ctl, const double* dnorm, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double r = *dnorm;
+  ctl->ressq = r;
+  ctl->iters += 1;
+  unsigned cont = 1u;
+  if (!isfinite(r)) {
+    ctl->status = SEMMG_ERR_NONFINITE;
+    cont = 0u;
+  } else if (r <= ctl->rtol * ctl->rtol * ctl->res0sq) {
+    ctl->status = SEMMG_OK;
+    cont = 0u;
+  } else if (ctl->iters >= ctl->maxit) {
+    ctl->status = SEMMG_ERR_NOT_CONVERGED;
+    cont = 0u;
+  }
+  cudaGraphSetConditional(h, cont);
+}
+
+}  // namespace
+
+struct semmg_batch {
+  std::vector<semmg_ctx*> ctxs;
+  BatchCtl* dctl = nullptr;
+  BatchCtl* hctl = nullptr;  // pinned
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t nodes = 0;
+  ~semmg_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (dctl) cudaFree(dctl);
+    if (hctl) cudaFreeHost(hctl);
+    cudaGetLastError();
+  }
+};
+
+namespace {
+
+// Enqueue one solve of context c (device nodal f -> u) into the capturing stream s.
+int capture_solve(semmg_ctx* c, const double* f, double* u, BatchCtl* ctl, cudaStream_t s, cudaStream_t sb) {
+  const int L = c->L();
+  const int64_t n = c->geo[L].size;
+  semmg_condense_rhs(c, f, c->Fh, s);
+  cudaMemsetAsync(c->Uh, 0, n * sizeof(double), s);
+  launch_copy<double, double>(c->Rh, c->Fh, n, s);
+  launch_norm2<double>(c->Fh, n, c->part, c->npart, c->dnorm, s);
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g) != cudaSuccess || cs != cudaStreamCaptureStatusActive)
+    return fail(c, SEMMG_ERR_CUDA, "batch: stream is not capturing");
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+    return check_cuda(c, "batch: conditional handle");
+  k_batch_init<<<1, 32, 0, s>>>(ctl, c->dnorm, h);
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &ndeps) != cudaSuccess)
+    return check_cuda(c, "batch: capture info");
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  if (cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp) != cudaSuccess) return check_cuda(c, "batch: while node");
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return check_cuda(c, "batch: body capture");
+  correction(c, c->Uh, c->Rh, sb);
+  op_residual<double>(c, L, c->Fh, c->Uh, c->Rh, 0, sb);
+  launch_norm2<double>(c->Rh, n, c->part, c->npart, c->dnorm, sb);
+  k_batch_check<<<1, 32, 0, sb>>>(ctl, c->dnorm, h);
+  cudaGraph_t got = nullptr;
+  if (cudaStreamEndCapture(sb, &got) != cudaSuccess) return check_cuda(c, "batch: body end");
+  if (cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+    return check_cuda(c, "batch: dependencies");
+  semmg_recover(c, f, c->Uh, u, s);
+  return check_cuda(c, "batch: capture");
+}
+
+}  // namespace
+
+extern "C" {
+
+int semmg_batch_create(semmg_ctx* const* ctxs, int nb, const double* const* f, double* const* u, double rtol,
+                       void* stream, semmg_batch** out) {
+  if (!out) return SEMMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!ctxs || !f || !u || nb < 1 || !(rtol > 0.0)) return SEMMG_ERR_INVALID_ARG;
+  for (int i = 0; i < nb; ++i) {
+    if (!ctxs[i] || !f[i] || !u[i]) return SEMMG_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return SEMMG_ERR_INVALID_ARG;  // one context per branch: its buffers are not shared
+  }
+  std::unique_ptr<semmg_batch> b(new (std::nothrow) semmg_batch());
+  if (!b) return SEMMG_ERR_NOMEM;
+  b->ctxs.assign(ctxs, ctxs + nb);
+  if (cudaMalloc((void**)&b->dctl, nb * sizeof(BatchCtl)) != cudaSuccess ||
+      cudaMallocHost((void**)&b->hctl, nb * sizeof(BatchCtl)) != cudaSuccess) {
+    cudaGetLastError();
+    return SEMMG_ERR_NOMEM;
+  }
+  for (int i = 0; i < nb; ++i) {
+    b->hctl[i] = BatchCtl{0.0, 0.0, rtol, 0, ctxs[i]->opts.max_iter, 0, 0};
+  }
+  if (cudaMemcpy(b->dctl, b->hctl, nb * sizeof(BatchCtl), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return SEMMG_ERR_CUDA;
+  }
+  // timing events cannot be recorded inside the captured graph
+  std::vector<int> timing(nb);
+  for (int i = 0; i < nb; ++i) {
+    timing[i] = ctxs[i]->timing;
+    collect_timing(ctxs[i]);
+    ctxs[i]->timing = 0;
+  }
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> s(nb, nullptr), sb(nb, nullptr);
+  std::vector<cudaEvent_t> ev(nb + 1, nullptr);
+  int rc = SEMMG_OK;
+  auto cleanup = [&]() {
+    for (int i = 0; i < nb; ++i) {
+      if (s[i]) cudaStreamDestroy(s[i]);
+      if (sb[i]) cudaStreamDestroy(sb[i]);
+      ctxs[i]->timing = timing[i];
+    }
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+    if (cap) cudaStreamDestroy(cap);
+  };
+  bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; ok && i < nb; ++i)
+    ok = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&sb[i], cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; ok && i <= nb; ++i) ok = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    cleanup();
+    return SEMMG_ERR_CUDA;
+  }
+  cudaStreamSynchronize((cudaStream_t)stream);
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return SEMMG_ERR_CUDA;
+  }
+  cudaEventRecord(ev[nb], cap);
+  for (int i = 0; i < nb && rc == SEMMG_OK; ++i) {
+    cudaStreamWaitEvent(s[i], ev[nb], 0);
+    rc = capture_solve(ctxs[i], f[i], u[i], b->dctl + i, s[i], sb[i]);
+    cudaEventRecord(ev[i], s[i]);
+    cudaStreamWaitEvent(cap, ev[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(cap, &g);
+  if (rc == SEMMG_OK && (ee != cudaSuccess || !g)) rc = SEMMG_ERR_CUDA;
+  if (rc == SEMMG_OK) {
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    b->nodes = (int64_t)nn;
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) rc = SEMMG_ERR_CUDA;
+  }
+  b->graph = g;
+  cudaGetLastError();
+  cleanup();
+  if (rc != SEMMG_OK) return rc;
+  *out = b.release();
+  return SEMMG_OK;
+}
+
+int semmg_batch_solve(semmg_batch* b, semmg_info* infos, void* stream) {
+  if (!b || !b->exec) return SEMMG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nb = (int)b->ctxs.size();
+  if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return check_cuda(b->ctxs[0], "batch_solve: launch");
+  cudaMemcpyAsync(b->hctl, b->dctl, nb * sizeof(BatchCtl), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return check_cuda(b->ctxs[0], "batch_solve");
+  int first = SEMMG_OK;
+  for (int i = 0; i < nb; ++i) {
+    const BatchCtl& k = b->hctl[i];
+    if (infos) {
+      infos[i].iters = k.iters;
+      infos[i].res0 = std::sqrt(k.res0sq);
+      infos[i].res_final = std::sqrt(k.ressq);
+      infos[i].rho = (k.iters > 0 && k.res0sq > 0) ? std::pow(std::sqrt(k.ressq / k.res0sq), 1.0 / k.iters) : 0.0;
+      infos[i].status = k.status;
+    }
+    if (first == SEMMG_OK && k.status != SEMMG_OK) first = k.status;
+  }
+  return first;
+}
+
+int semmg_batch_graph_nodes(const semmg_batch* b, int64_t* nodes) {
+  if (!b || !nodes) return SEMMG_ERR_INVALID_ARG;
+  *nodes = b->nodes;
+  return SEMMG_OK;
+}
+
+void semmg_batch_destroy(semmg_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  delete b;
+}
+
+}  // extern "C"

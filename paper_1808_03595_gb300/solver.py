@@ -201,3 +201,48 @@ class Context:
             self._check(self._lib.semmg_get_kstat(self._ctx, i, ctypes.byref(k)))
             out[name] = {"ms": k.ms, "launches": k.launches, "flops": k.flops, "bytes": k.bytes}
         return out
+
+
+class Batch:
+    """Independent solves of several contexts captured into one CUDA graph (semmg_batch_*).
+
+    f_list / u_list are device nodal tensors that the graph keeps using; refill
+    the f tensors in place and call solve() again to solve new right-hand sides.
+    """
+
+    def __init__(self, ctxs, f_list, u_list, rtol=1e-10, stream=None):
+        self._lib = L.load()
+        self._b = ctypes.c_void_p()
+        self.ctxs, self.f, self.u = list(ctxs), list(f_list), list(u_list)
+        nb = len(self.ctxs)
+        arr = (ctypes.c_void_p * nb)
+        rc = self._lib.semmg_batch_create(arr(*[c._ctx.value for c in self.ctxs]), nb,
+                                          arr(*[t.data_ptr() for t in self.f]), arr(*[t.data_ptr() for t in self.u]),
+                                          rtol, _stream(stream), ctypes.byref(self._b))
+        if rc != 0:
+            raise SemmgError(rc, "batch_create")
+
+    def solve(self, stream=None):
+        """Launch the graph, wait, and return (status, [info per solve])."""
+        nb = len(self.ctxs)
+        infos = (L.semmg_info * nb)()
+        rc = self._lib.semmg_batch_solve(self._b, infos, _stream(stream))
+        if rc not in (0, L.SEMMG_ERR_NOT_CONVERGED, -5):
+            raise SemmgError(rc, "batch_solve")
+        return rc, list(infos)
+
+    def graph_nodes(self):
+        n = ctypes.c_int64()
+        self._lib.semmg_batch_graph_nodes(self._b, ctypes.byref(n))
+        return n.value
+
+    def close(self):
+        if self._b:
+            self._lib.semmg_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
