@@ -198,6 +198,8 @@ def run_semmg(args, world, rank, local, pg):
                       "mixed": ctx32})
     torch.cuda.synchronize()
 
+    per_p_ms = {"fp64": {}, "mixed": {}}
+
     def solve_all(form, timed, host=False):
         ms, iters = 0.0, {}
         for c in cases:
@@ -213,7 +215,10 @@ def run_semmg(args, world, rank, local, pg):
             e1.record(stream)
             e1.synchronize()
             if timed:
-                ms += e0.elapsed_time(e1)
+                dt = e0.elapsed_time(e1)
+                ms += dt
+                if not host:
+                    per_p_ms[form][c["p"]] = per_p_ms[form].get(c["p"], 0.0) + dt / args.steps
             iters[c["p"]] = info.iters
             assert info.res_final <= 1e-10 * info.res0, (form, c["p"], info.res_final, info.res0)
         return ms, iters
@@ -244,11 +249,20 @@ def run_semmg(args, world, rank, local, pg):
                 acc[kk] += v[kk]
         c["fp64"].set_timing(False)
     t32, it32, te2e = float("nan"), {}, float("nan")
+    kst32 = {}
     if "mixed" in forms:
+        for c in cases:
+            c["mixed"].set_timing(True)
         t32 = 0.0
         for _ in range(args.steps):
             ms, it32 = solve_all("mixed", True)
             t32 += ms
+        for c in cases:
+            for k, v in c["mixed"].kstats().items():
+                acc = kst32.setdefault(k, {"ms": 0.0, "launches": 0})
+                acc["ms"] += v["ms"]
+                acc["launches"] += v["launches"]
+            c["mixed"].set_timing(False)
     if not args.no_e2e:
         # end to end through the host-buffer entry point
         solve_all("fp64", False, host=True)
@@ -300,6 +314,9 @@ def run_semmg(args, world, rank, local, pg):
         "gpu_launches": int(launches // max(1, args.steps)) * args.steps,
         "kernels_fp64": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
                          for k, v in kst.items()},
+        "kernels_mixed": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
+                          for k, v in kst32.items()},
+        "ms_per_degree": per_p_ms,
         "roofline": roof,
         "clocks": clk,
     }

@@ -63,7 +63,7 @@ struct Lines {
 };
 
 template <typename T>
-__device__ void fold_lines(const Lines& L, int ax, const T* X, T* Y) {
+__device__ __forceinline__ void fold_lines(const Lines& L, int ax, const T* X, T* Y) {
   const int str = L.stride(ax);
   for (int idx = threadIdx.x; idx < L.total; idx += blockDim.x) {
     const int j = L.pos(idx, ax);
@@ -81,7 +81,7 @@ __device__ void fold_lines(const Lines& L, int ax, const T* X, T* Y) {
 
 // out[k] = scale * sum_i S[i][k] x[i], from folded x.
 template <typename T>
-__device__ void tx_lines(const Lines& L, int ax, const T* __restrict__ S, const T* Y, T* Z, T scale) {
+__device__ __forceinline__ void tx_lines(const Lines& L, int ax, const T* __restrict__ S, const T* Y, T* Z, T scale) {
   const int str = L.stride(ax), n = L.n;
   for (int idx = threadIdx.x; idx < L.total; idx += blockDim.x) {
     const int k = L.pos(idx, ax);
@@ -99,7 +99,7 @@ __device__ void tx_lines(const Lines& L, int ax, const T* __restrict__ S, const 
 // Transposed transform into folded form: position j < ne gets
 // E_j = sum_{k even} S[h+j][k] b[k], position q >= ne gets O_q = sum_{k odd} S[q][k] b[k].
 template <typename T>
-__device__ void txT_lines(const Lines& L, int ax, const T* __restrict__ S, const T* B, T* Y) {
+__device__ __forceinline__ void txT_lines(const Lines& L, int ax, const T* __restrict__ S, const T* B, T* Y) {
   const int str = L.stride(ax), n = L.n;
   for (int idx = threadIdx.x; idx < L.total; idx += blockDim.x) {
     const int j = L.pos(idx, ax);
@@ -129,7 +129,7 @@ __device__ __forceinline__ T unfold_at(const Lines& L, int ax, const T* Y, int i
 }
 
 template <typename T>
-__device__ void unfold_lines(const Lines& L, int ax, const T* Y, T* X) {
+__device__ __forceinline__ void unfold_lines(const Lines& L, int ax, const T* Y, T* X) {
   for (int idx = threadIdx.x; idx < L.total; idx += blockDim.x) X[idx] = unfold_at(L, ax, Y, idx);
 }
 
@@ -137,7 +137,7 @@ __device__ void unfold_lines(const Lines& L, int ax, const T* Y, T* X) {
 // Six faces X[f][ib][ia] (f = 2d + side) -> pair sums and differences
 // X[2d] = X[2d] + X[2d+1], X[2d+1] = X[2d] - X[2d+1].
 template <typename T>
-__device__ void face_pairs(int mm, T* X) {
+__device__ __forceinline__ void face_pairs(int mm, T* X) {
   for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
     const int d = idx / mm, r = idx - d * mm;
     const T a = X[(2 * d) * mm + r], b = X[(2 * d + 1) * mm + r];
@@ -148,7 +148,7 @@ __device__ void face_pairs(int mm, T* X) {
 
 // forward 2D transform of the six face arrays, scaled by c_f alpha_d
 template <typename T>
-__device__ void faces_forward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc) {
+__device__ __forceinline__ void faces_forward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc) {
   fold_lines(F, 0, X, Tt);
   __syncthreads();
   tx_lines(F, 0, Sh, Tt, X, (T)1);
@@ -174,7 +174,7 @@ __device__ void faces_forward(const Lines& F, const T* Sh, T* X, T* Tt, const El
 // Back transform of the six reduced arrays (pairs: even / odd parts of axis d)
 // and store of both faces: Z[2d] = sf (Ye + Yo), Z[2d+1] = sf (Ye - Yo).
 template <typename T, typename Store>
-__device__ void faces_backward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc, Store store) {
+__device__ __forceinline__ void faces_backward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc, Store store) {
   txT_lines(F, 0, Sh, X, Tt);
   __syncthreads();
   unfold_lines(F, 0, Tt, X);
@@ -201,7 +201,7 @@ __device__ __forceinline__ T face_expand(int m, int ne, const T* a0, const T* X,
 
 // X[2d + parity][kb][ka] <- sum over k_d of that parity of a0[k_d] W(k)
 template <typename T>
-__device__ void faces_reduce(int m, int ne, const T* a0, const T* W, T* X) {
+__device__ __forceinline__ void faces_reduce(int m, int ne, const T* a0, const T* W, T* X) {
   const int mm = m * m;
   for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
     const int f = idx / mm, r = idx - f * mm, kb = r / m, ka = r - kb * m;
@@ -216,15 +216,20 @@ __device__ void faces_reduce(int m, int ne, const T* a0, const T* W, T* X) {
   }
 }
 
-template <typename T>
-__device__ __forceinline__ T inv_d(const Tabs<T>& t, const ElemScal<T>& sc, const T* lI, T lam, int64_t idx, int k1,
-                                   int k2, int k3, int64_t n3) {
+__device__ __forceinline__ double inv_d(const Tabs<double>& t, const ElemScal<double>& sc, const double* lI,
+                                        double lam, int64_t idx, int k1, int k2, int k3, int64_t n3) {
   if (t.Relem) return t.Relem[sc.cls * n3 + idx];
-  return (T)1 / (lam + sc.e[0] * lI[k1] + sc.e[1] * lI[k2] + sc.e[2] * lI[k3]);
+  return 1.0 / (lam + sc.e[0] * lI[k1] + sc.e[1] * lI[k2] + sc.e[2] * lI[k3]);
+}
+
+// FP32 (inside FP64 iterative refinement): approximate reciprocal, no table read
+__device__ __forceinline__ float inv_d(const Tabs<float>&, const ElemScal<float>& sc, const float* lI, float lam,
+                                       int64_t, int k1, int k2, int k3, int64_t) {
+  return __fdividef(1.0f, lam + sc.e[0] * lI[k1] + sc.e[1] * lI[k2] + sc.e[2] * lI[k3]);
 }
 
 template <typename T>
-__device__ void load_tables(int m, const Tabs<T>& t, T* Sh, T* a0, T* lI) {
+__device__ __forceinline__ void load_tables(int m, const Tabs<T>& t, T* Sh, T* a0, T* lI) {
   for (int i = threadIdx.x; i < m * m; i += blockDim.x) Sh[i] = t.Sh[i];
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     a0[i] = t.a0[i];
@@ -240,11 +245,12 @@ __device__ __forceinline__ void elem_coords(const Geo& G, int64_t e, int* a1, in
 
 // y_e = H_BI H_II^{-1} H_IB u on the six faces of every element -> Z[e][f][.]
 // Work regions: 0 tables (Sh, a0, Lam), 1 X (6 m^2), 2 Tt (6 m^2), 3 W (m^3).
-template <typename T>
-__global__ void __launch_bounds__(256) k_elem_schur(Geo G, Tabs<T> t, const T* __restrict__ u, T* __restrict__ Z,
+// PC > 0 compiles the kernel for degree PC (constant extents); PC = 0 reads it from G.
+template <typename T, int PC>
+__global__ void __launch_bounds__(512) k_elem_schur(Geo G, Tabs<T> t, const T* __restrict__ u, T* __restrict__ Z,
                                                      T* ws, WsPlan wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = G.m, mm = m * m;
+  const int m = PC ? PC - 1 : G.m, mm = m * m;
   const int64_t n3 = (int64_t)mm * m;
   T* Sh = ws_ptr<T>(wp, 0, smem_raw, ws);
   T* a0 = Sh + mm;
@@ -283,7 +289,7 @@ __global__ void __launch_bounds__(256) k_elem_schur(Geo G, Tabs<T> t, const T* _
 
 // Interior 3D transforms with the folded reference eigenvectors.
 // forward: A <- scale * (Sref^T (x) Sref^T (x) Sref^T) A, B is scratch.
-__device__ void interior_forward(const Lines& I, const double* Sr, double* A, double* B, double scale) {
+__device__ __forceinline__ void interior_forward(const Lines& I, const double* Sr, double* A, double* B, double scale) {
   fold_lines(I, 0, A, B);
   __syncthreads();
   tx_lines(I, 0, Sr, B, A, 1.0);
@@ -300,7 +306,7 @@ __device__ void interior_forward(const Lines& I, const double* Sr, double* A, do
 
 // backward along x3 and x2 (natural order in A afterwards), then the x1
 // transposed transform into B; the caller unfolds B along x1.
-__device__ void interior_backward(const Lines& I, const double* Sr, double* A, double* B) {
+__device__ __forceinline__ void interior_backward(const Lines& I, const double* Sr, double* A, double* B) {
   txT_lines(I, 2, Sr, A, B);
   __syncthreads();
   unfold_lines(I, 2, B, A);
@@ -340,10 +346,11 @@ __device__ __forceinline__ int64_t interior_node(const Geo& G, int a1, int a2, i
 }
 
 // Z[e][f] = (H_BI H_II^{-1} F_I) on the faces, F_I = (M f)_I element-local.
+template <int PC>
 __global__ void __launch_bounds__(256) k_elem_condense(Geo G, Tabs<double> t, const double* __restrict__ f,
                                                         double* __restrict__ Z, double* ws, WsPlan wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = G.m, mm = m * m, mmm = mm * m;
+  const int m = PC ? PC - 1 : G.m, mm = m * m, mmm = mm * m;
   FdmSmem s = fdm_layout(m, smem_raw, ws, wp);
   load_tables(m, t, s.Sh, s.a0, s.lI);
   for (int i = threadIdx.x; i < mm; i += blockDim.x) s.Sr[i] = t.Sref[i];
@@ -376,11 +383,12 @@ __global__ void __launch_bounds__(256) k_elem_condense(Geo G, Tabs<double> t, co
 }
 
 // u_I = H_II^{-1} (F_I - H_IB uhat) written into the nodal array.
+template <int PC>
 __global__ void __launch_bounds__(256) k_elem_recover(Geo G, Tabs<double> t, const double* __restrict__ f,
                                                        const double* __restrict__ uh, double* __restrict__ un,
                                                        double* ws, WsPlan wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = G.m, mm = m * m, mmm = mm * m;
+  const int m = PC ? PC - 1 : G.m, mm = m * m, mmm = mm * m;
   FdmSmem s = fdm_layout(m, smem_raw, ws, wp);
   load_tables(m, t, s.Sh, s.a0, s.lI);
   for (int i = threadIdx.x; i < mm; i += blockDim.x) s.Sr[i] = t.Sref[i];
@@ -420,6 +428,7 @@ __global__ void __launch_bounds__(256) k_elem_recover(Geo G, Tabs<double> t, con
 }
 
 constexpr size_t kSmemCap = 112 * 1024;
+constexpr size_t kSchurSmemCap = 200 * 1024;
 
 }  // namespace
 
@@ -428,8 +437,9 @@ LaunchCfg plan_elem_schur(const Geo& G, int nsm) {
   LaunchCfg c;
   const size_t m = G.m, mm = m * m;
   const size_t sizes[4] = {mm + 2 * m, 6 * mm, 6 * mm, mm * m};
-  c.ws = plan_regions(sizes, 4, sizeof(T), kSmemCap, &c.smem);
+  c.ws = plan_regions(sizes, 4, sizeof(T), kSchurSmemCap, &c.smem);
   c.ok = plan_ok(c.ws, sizes, 4, sizeof(T), c.smem);
+  c.block = c.smem > 100 * 1024 ? 512 : 256;
   const int64_t grid = (int64_t)nsm * blocks_per_sm(c.smem);
   c.grid = (int)(G.nelem < grid ? G.nelem : grid);
   if (c.grid < 1) c.grid = 1;
@@ -440,7 +450,14 @@ template <typename T>
 void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, const LaunchCfg& c,
                        cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
-  k_elem_schur<T><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws);
+  switch (G.p) {
+    case 2: k_elem_schur<T, 2><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 4: k_elem_schur<T, 4><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 8: k_elem_schur<T, 8><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 16: k_elem_schur<T, 16><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 32: k_elem_schur<T, 32><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    default: k_elem_schur<T, 0><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+  }
 }
 
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm) {
@@ -458,13 +475,21 @@ LaunchCfg plan_elem_fdm(const Geo& G, int nsm) {
 void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f, double* Z, double* ws,
                           const LaunchCfg& c, cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
-  k_elem_condense<<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, ws, c.ws);
+  switch (G.p) {
+    case 16: k_elem_condense<16><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, ws, c.ws); break;
+    case 32: k_elem_condense<32><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, ws, c.ws); break;
+    default: k_elem_condense<0><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, ws, c.ws); break;
+  }
 }
 
 void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f, const double* uh, double* un,
                          double* ws, const LaunchCfg& c, cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
-  k_elem_recover<<<c.grid, c.block, c.smem, st>>>(G, t, f, uh, un, ws, c.ws);
+  switch (G.p) {
+    case 16: k_elem_recover<16><<<c.grid, c.block, c.smem, st>>>(G, t, f, uh, un, ws, c.ws); break;
+    case 32: k_elem_recover<32><<<c.grid, c.block, c.smem, st>>>(G, t, f, uh, un, ws, c.ws); break;
+    default: k_elem_recover<0><<<c.grid, c.block, c.smem, st>>>(G, t, f, uh, un, ws, c.ws); break;
+  }
 }
 
 template LaunchCfg plan_elem_schur<double>(const Geo&, int);
@@ -474,12 +499,26 @@ template void launch_elem_schur<double>(const Geo&, const Tabs<double>&, const d
 template void launch_elem_schur<float>(const Geo&, const Tabs<float>&, const float*, float*, float*,
                                        const LaunchCfg&, cudaStream_t);
 
-int set_elem_smem_limits() {
+template <typename T>
+static int schur_attrs() {
   int bad = 0;
-  bad |= cudaFuncSetAttribute(k_elem_schur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_schur<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_condense, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_recover, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return bad;
+}
+
+int set_elem_smem_limits() {
+  int bad = schur_attrs<double>() | schur_attrs<float>();
+  bad |= cudaFuncSetAttribute(k_elem_condense<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_condense<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_condense<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_recover<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_recover<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_recover<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return bad;
 }
 

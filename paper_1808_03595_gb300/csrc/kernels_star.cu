@@ -23,7 +23,7 @@ namespace semmg {
 namespace {
 
 // Work regions: 0 S tables (3 nS^2; optional), 1 P (3 nS^2), 2 Tt (3 nS^2),
-// 3 V (nS^3), 4 Lam + act (3 nS each, as T).
+// 3 V slab (ts nS^2), 4 Lam + act (3 nS each, as T).
 //
 // Plane dd (normal to axis dd) is stored [jb][ja] with a = the lower and b
 // the higher of the two in-plane axes.  Centrosymmetric lines (every interior
@@ -33,13 +33,21 @@ namespace {
 // multiply-adds.  Odd eigenvectors vanish at the vertex (s_d[k] = 0 for
 // k > m), so the contractions along the normals run over the even half only.
 
+// a / b: IEEE division in FP64, the hardware approximate quotient (about 2 ulp)
+// in FP32, where the smoother sits inside FP64 iterative refinement.
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+
+// k3-planes of the eigenspace held at once.
+__host__ __device__ __forceinline__ int slab_thickness(int nS) { return nS <= 16 ? 8 : (nS <= 32 ? 4 : 2); }
+
 // Plane pass helpers: axis index of the fast (a) and slow (b) in-plane axes.
 __device__ __forceinline__ int ax_fast(int dd) { return dd == 0 ? 1 : 0; }
 __device__ __forceinline__ int ax_slow(int dd) { return dd == 2 ? 1 : 2; }
 
 // Fold (sym) or copy a 3-plane array along the fast (along=0) or slow (along=1) index.
 template <typename T>
-__device__ void fold_pass(int nS, int m, const int* sym, int along, const T* X, T* Y) {
+__device__ __forceinline__ void fold_pass(int nS, int m, const int* sym, int along, const T* X, T* Y) {
   const int n2 = nS * nS;
   for (int idx = threadIdx.x; idx < 3 * n2; idx += blockDim.x) {
     const int dd = idx / n2, rr = idx - dd * n2, row = rr / nS, col = rr - row * nS;
@@ -64,7 +72,7 @@ __device__ void fold_pass(int nS, int m, const int* sym, int along, const T* X, 
 // Forward 1D transform of folded data along the fast (along=0) / slow (along=1)
 // index: out[k] = sum_j S[j][k] x[j] (folded sums on symmetric lines).
 template <typename T>
-__device__ void tx_pass(int nS, int m, const int* sym, const T* const* S, int along, const T* Y, T* Z) {
+__device__ __forceinline__ void tx_pass(int nS, int m, const int* sym, const T* const* S, int along, const T* Y, T* Z) {
   const int n2 = nS * nS;
   for (int idx = threadIdx.x; idx < 3 * n2; idx += blockDim.x) {
     const int dd = idx / n2, rr = idx - dd * n2, row = rr / nS, col = rr - row * nS;
@@ -89,7 +97,7 @@ __device__ void tx_pass(int nS, int m, const int* sym, const T* const* S, int al
 // Transposed 1D transform into folded form: symmetric lines give E_j (j <= m)
 // and O_j (stored at m+j); others give x[j] = sum_k S[j][k] b[k].
 template <typename T>
-__device__ void txT_pass(int nS, int m, const int* sym, const T* const* S, int along, const T* B, T* Y) {
+__device__ __forceinline__ void txT_pass(int nS, int m, const int* sym, const T* const* S, int along, const T* B, T* Y) {
   const int n2 = nS * nS;
   for (int idx = threadIdx.x; idx < 3 * n2; idx += blockDim.x) {
     const int dd = idx / n2, rr = idx - dd * n2, row = rr / nS, col = rr - row * nS;
@@ -114,6 +122,116 @@ __device__ void txT_pass(int nS, int m, const int* sym, const T* const* S, int a
   }
 }
 
+
+// ---- grouped passes: each thread computes kG outputs of one line that share
+// the input loads (kG independent multiply-add chains per thread).
+constexpr int kG = 4;
+
+// Output block of group g on a line: [k0, k1) and the input range of that block.
+struct Block {
+  int k0, k1;   // outputs
+  int j0, j1;   // folded inputs
+  int even;     // 1: even block (inputs j use row m + j), 0: odd block or unfolded (row j)
+};
+
+__device__ __forceinline__ int groups_per_line(int nS, int m, int symax) {
+  return symax ? (m + 1 + kG - 1) / kG + (m + kG - 1) / kG : (nS + kG - 1) / kG;
+}
+
+__device__ __forceinline__ Block block_of(int nS, int m, int symax, int g) {
+  Block b;
+  if (!symax) {
+    b.k0 = g * kG; b.k1 = min(b.k0 + kG, nS); b.j0 = 0; b.j1 = nS; b.even = 0;
+  } else {
+    const int ge = (m + 1 + kG - 1) / kG;
+    if (g < ge) {
+      b.k0 = g * kG; b.k1 = min(b.k0 + kG, m + 1); b.j0 = 0; b.j1 = m + 1; b.even = 1;
+    } else {
+      b.k0 = m + 1 + (g - ge) * kG; b.k1 = min(b.k0 + kG, nS); b.j0 = m + 1; b.j1 = nS; b.even = 0;
+    }
+  }
+  return b;
+}
+
+// Z = forward transform of folded Y along `along` (0: fast index, 1: slow index), grouped.
+template <typename T>
+__device__ __forceinline__ void tx_pass_g(int nS, int m, const int* sym, const T* const* S, int along, const T* Y,
+                                          T* Z) {
+  const int n2 = nS * nS;
+  int gpl[3], acc[4];
+  acc[0] = 0;
+  for (int dd = 0; dd < 3; ++dd) {
+    const int ax = along == 0 ? ax_fast(dd) : ax_slow(dd);
+    gpl[dd] = groups_per_line(nS, m, sym[ax]);
+    acc[dd + 1] = acc[dd] + nS * gpl[dd];
+  }
+  for (int it = threadIdx.x; it < acc[3]; it += blockDim.x) {
+    const int dd = it < acc[1] ? 0 : (it < acc[2] ? 1 : 2);
+    const int r = it - acc[dd], line = r / gpl[dd], g = r - line * gpl[dd];
+    const int ax = along == 0 ? ax_fast(dd) : ax_slow(dd);
+    const Block b = block_of(nS, m, sym[ax], g);
+    const T* Sa = S[ax];
+    const T* y = Y + dd * n2 + (along == 0 ? line * nS : line);
+    const int ys = along == 0 ? 1 : nS;
+    T a[kG];
+#pragma unroll
+    for (int q = 0; q < kG; ++q) a[q] = 0;
+    for (int j = b.j0; j < b.j1; ++j) {
+      const T yv = y[j * ys];
+      const T* sr = Sa + (b.even ? m + j : j) * nS + b.k0;
+#pragma unroll
+      for (int q = 0; q < kG; ++q)
+        if (b.k0 + q < b.k1) a[q] += sr[q] * yv;
+    }
+    T* z = Z + dd * n2;
+#pragma unroll
+    for (int q = 0; q < kG; ++q)
+      if (b.k0 + q < b.k1) z[along == 0 ? line * nS + b.k0 + q : (b.k0 + q) * nS + line] = a[q];
+  }
+}
+
+// Y = transposed transform into folded form (E_j / O_j), grouped over outputs j.
+template <typename T>
+__device__ __forceinline__ void txT_pass_g(int nS, int m, const int* sym, const T* const* S, int along, const T* B,
+                                           T* Y) {
+  const int n2 = nS * nS;
+  int gpl[3], acc[4];
+  acc[0] = 0;
+  for (int dd = 0; dd < 3; ++dd) {
+    const int ax = along == 0 ? ax_fast(dd) : ax_slow(dd);
+    gpl[dd] = groups_per_line(nS, m, sym[ax]);
+    acc[dd + 1] = acc[dd] + nS * gpl[dd];
+  }
+  for (int it = threadIdx.x; it < acc[3]; it += blockDim.x) {
+    const int dd = it < acc[1] ? 0 : (it < acc[2] ? 1 : 2);
+    const int r = it - acc[dd], line = r / gpl[dd], g = r - line * gpl[dd];
+    const int ax = along == 0 ? ax_fast(dd) : ax_slow(dd);
+    // the group's outputs are folded positions [k0, k1); their sums run over the
+    // eigen-index block of the same parity, [j0, j1) (same ranges as the forward pass)
+    const Block blk = block_of(nS, m, sym[ax], g);
+    const T* Sa = S[ax];
+    const T* bb = B + dd * n2 + (along == 0 ? line * nS : line);
+    const int bs = along == 0 ? 1 : nS;
+    T a[kG];
+    const T* sr[kG];
+#pragma unroll
+    for (int q = 0; q < kG; ++q) {
+      a[q] = 0;
+      const int jo = min(blk.k0 + q, blk.k1 - 1);
+      sr[q] = Sa + (blk.even ? m + jo : jo) * nS;
+    }
+    for (int k = blk.j0; k < blk.j1; ++k) {
+      const T bv = bb[k * bs];
+#pragma unroll
+      for (int q = 0; q < kG; ++q) a[q] += sr[q][k] * bv;
+    }
+    T* yv = Y + dd * n2;
+#pragma unroll
+    for (int q = 0; q < kG; ++q)
+      if (blk.k0 + q < blk.k1) yv[along == 0 ? line * nS + blk.k0 + q : (blk.k0 + q) * nS + line] = a[q];
+  }
+}
+
 // Unfold E/O pairs (or copy) back to natural order along the fast / slow index.
 template <typename T>
 __device__ __forceinline__ T unfold_value(int nS, int m, const int* sym, int along, const T* Y, int dd, int row,
@@ -130,13 +248,15 @@ __device__ __forceinline__ T unfold_value(int nS, int m, const int* sym, int alo
   return j > m ? y[ie] + y[io] : y[ie] - y[io];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_star(Geo G, Tabs<T> t, const T* __restrict__ r, T* __restrict__ Ob,
+// PC > 0 compiles the kernel for degree PC (constant extents, unrolled loops);
+// PC = 0 takes the degree from G.
+template <typename T, int PC>
+__global__ void __launch_bounds__(512) k_star(Geo G, Tabs<T> t, const T* __restrict__ r, T* __restrict__ Ob,
                                                T* ws, WsPlan wp, int S_copy, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_next;
   __shared__ int s_sym[3];
-  const int p = G.p, m = G.m, nS = G.nS, n2 = nS * nS;
+  const int p = PC ? PC : G.p, m = p - 1, nS = 2 * p - 1, n2 = nS * nS;
   T* Sbuf = ws_ptr<T>(wp, 0, smem_raw, ws);
   T* P = ws_ptr<T>(wp, 1, smem_raw, ws);
   T* Tt = ws_ptr<T>(wp, 2, smem_raw, ws);
@@ -184,61 +304,97 @@ __global__ void __launch_bounds__(256) k_star(Geo G, Tabs<T> t, const T* __restr
     // 2a. in-plane transforms A = S_b^T P S_a (fold, transform; fast then slow index)
     fold_pass(nS, m, sym, 0, P, Tt);
     __syncthreads();
-    tx_pass(nS, m, sym, S, 0, Tt, P);
+    tx_pass_g(nS, m, sym, S, 0, Tt, P);
     __syncthreads();
     fold_pass(nS, m, sym, 1, P, Tt);
     __syncthreads();
-    tx_pass(nS, m, sym, S, 1, Tt, P);
+    tx_pass_g(nS, m, sym, S, 1, Tt, P);
     __syncthreads();
-    // 2b + 3. expansion along the normals with the vertex rows, times 1/D
+    // 2b + 3 + 4a. expansion along the normals with the vertex rows, times 1/D,
+    // and the contractions back along the normals, in slabs of `ts` k3-planes
+    // held in shared memory: B1[k3][k2] = sum_k1 s1 V and B2[k3][k1] = sum_k2 s2 V
+    // per slab, B3[k2][k1] = sum_k3 s3 V accumulated over the slabs.
+    // Odd eigenvectors vanish at the vertex, so on symmetric axes the sums run
+    // over the even half only.  Results land in Tt (B1, B2, B3).
     const T* s1 = S[0] + m * nS;
     const T* s2 = S[1] + m * nS;
     const T* s3 = S[2] + m * nS;
     const int64_t n3 = (int64_t)n2 * nS;
     const T* R = nullptr;
-    if (t.Rtab) {
+    if (t.Rtab && sizeof(T) == sizeof(double)) {
       const int64_t cls = ((int64_t)t.starCls[0][c[0]] * t.ncls[1] + t.starCls[1][c[1]]) * t.ncls[2] + t.starCls[2][c[2]];
       R = t.Rtab + cls * n3;
     }
-    for (int64_t idx = threadIdx.x; idx < n3; idx += blockDim.x) {
-      const int k1 = (int)(idx % nS), k2 = (int)((idx / nS) % nS), k3 = (int)(idx / n2);
-      const T E = s1[k1] * P[k3 * nS + k2] + s2[k2] * P[n2 + k3 * nS + k1] + s3[k3] * P[2 * n2 + k2 * nS + k1];
-      V[idx] = R ? E * R[idx] : E / (lam + Lm[k1] + Lm[nS + k2] + Lm[2 * nS + k3]);
-    }
-    __syncthreads();
-    // 4a. contraction along the normals: B1[k3][k2], B2[k3][k1], B3[k2][k1]
-    for (int idx = threadIdx.x; idx < 3 * n2; idx += blockDim.x) {
-      const int dd = idx / n2, rr = idx - dd * n2, kb = rr / nS, ka = rr % nS;
-      const int nz = sym[dd] ? m + 1 : nS;  // odd eigenvectors vanish at the vertex
-      T s = 0;
-      if (dd == 0) {
-        const T* v = V + (int64_t)(kb * nS + ka) * nS;
-        for (int k = 0; k < nz; ++k) s += s1[k] * v[k];
-      } else if (dd == 1) {
-        const T* v = V + (int64_t)kb * n2 + ka;
-        for (int k = 0; k < nz; ++k) s += s2[k] * v[k * nS];
-      } else {
-        const T* v = V + (int64_t)kb * nS + ka;
-        for (int k = 0; k < nz; ++k) s += s3[k] * v[(int64_t)k * n2];
+    const int nz1 = sym[0] ? m + 1 : nS, nz2 = sym[1] ? m + 1 : nS, nz3 = sym[2] ? m + 1 : nS;
+    const int ts = slab_thickness(nS);
+    T* B1 = Tt;
+    T* B2 = Tt + n2;
+    T* B3 = Tt + 2 * n2;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) B3[i] = 0;
+    for (int k3s = 0; k3s < nS; k3s += ts) {
+      const int tn = nS - k3s < ts ? nS - k3s : ts;
+      __syncthreads();
+      for (int pr = threadIdx.x; pr < n2; pr += blockDim.x) {
+        const int k1 = pr % nS, k2 = pr / nS;
+        const T a3 = P[2 * n2 + k2 * nS + k1];
+        T b3 = 0;
+        for (int kk = 0; kk < tn; ++kk) {
+          const int k3 = k3s + kk;
+          const T E = s1[k1] * P[k3 * nS + k2] + s2[k2] * P[n2 + k3 * nS + k1] + s3[k3] * a3;
+          const int64_t pt = (int64_t)k3 * n2 + pr;
+          const T v = R ? E * R[pt] : fast_div(E, lam + Lm[k1] + Lm[nS + k2] + Lm[2 * nS + k3]);
+          V[kk * n2 + pr] = v;
+          if (k3 < nz3) b3 += s3[k3] * v;
+        }
+        B3[pr] += b3;
       }
-      P[idx] = s;
+      __syncthreads();
+      for (int o = threadIdx.x; o < 2 * tn * nS; o += blockDim.x) {
+        const int which = o / (tn * nS), rr = o - which * tn * nS, kk = rr / nS, kx = rr % nS;
+        const T* vs = V + kk * n2;
+        T s = 0;
+        T s_1 = 0, s_2 = 0, s_3 = 0;  // four independent partial sums
+        if (which == 0) {  // B1[k3][k2 = kx] = sum over k1
+          const T* v = vs + kx * nS;
+          int k = 0;
+          for (; k + 3 < nz1; k += 4) {
+            s += s1[k] * v[k];
+            s_1 += s1[k + 1] * v[k + 1];
+            s_2 += s1[k + 2] * v[k + 2];
+            s_3 += s1[k + 3] * v[k + 3];
+          }
+          for (; k < nz1; ++k) s += s1[k] * v[k];
+          B1[(k3s + kk) * nS + kx] = (s + s_1) + (s_2 + s_3);
+        } else {           // B2[k3][k1 = kx] = sum over k2
+          const T* v = vs + kx;
+          int k = 0;
+          for (; k + 3 < nz2; k += 4) {
+            s += s2[k] * v[k * nS];
+            s_1 += s2[k + 1] * v[(k + 1) * nS];
+            s_2 += s2[k + 2] * v[(k + 2) * nS];
+            s_3 += s2[k + 3] * v[(k + 3) * nS];
+          }
+          for (; k < nz2; ++k) s += s2[k] * v[k * nS];
+          B2[(k3s + kk) * nS + kx] = (s + s_1) + (s_2 + s_3);
+        }
+      }
     }
     __syncthreads();
     // 4b. back to the planes: O = S_b B S_a^T (slow index first, then fast)
-    txT_pass(nS, m, sym, S, 1, P, Tt);
+    txT_pass_g(nS, m, sym, S, 1, Tt, P);
     __syncthreads();
     for (int idx = threadIdx.x; idx < 3 * n2; idx += blockDim.x) {
       const int dd = idx / n2, rr = idx - dd * n2, row = rr / nS, col = rr - row * nS;
-      P[idx] = unfold_value(nS, m, sym, 1, Tt, dd, row, col);
+      Tt[idx] = unfold_value(nS, m, sym, 1, P, dd, row, col);
     }
     __syncthreads();
-    txT_pass(nS, m, sym, S, 0, P, Tt);
+    txT_pass_g(nS, m, sym, S, 0, Tt, P);
     __syncthreads();
     T* ob = Ob + st * 3 * (int64_t)n2;
     for (int idx = threadIdx.x; idx < 3 * n2; idx += blockDim.x) {
       const int dd = idx / n2, rr = idx - dd * n2, jb = rr / nS, ja = rr % nS;
       const int ax_a = ax_fast(dd), ax_b = ax_slow(dd);
-      const T s = unfold_value(nS, m, sym, 0, Tt, dd, jb, ja);
+      const T s = unfold_value(nS, m, sym, 0, P, dd, jb, ja);
       const bool active = Ac[dd * nS + m] != (T)0 && Ac[ax_a * nS + ja] != (T)0 && Ac[ax_b * nS + jb] != (T)0;
       const int oa = ja - m, obb = jb - m;
       const T wgt = t.w1d[oa < 0 ? -oa : oa] * t.w1d[obb < 0 ? -obb : obb];
@@ -270,7 +426,7 @@ __global__ void __launch_bounds__(256) k_star(Geo G, Tabs<T> t, const T* __restr
   }
 }
 
-constexpr size_t kStarSmemCap = 112 * 1024;
+constexpr size_t kStarSmemCap = 200 * 1024;
 
 }  // namespace
 
@@ -278,11 +434,12 @@ template <typename T>
 LaunchCfg plan_star(const Geo& G, int nsm) {
   LaunchCfg c;
   const size_t nS = G.nS, n2 = nS * nS;
-  const size_t sizes[5] = {3 * n2, 3 * n2, 3 * n2, n2 * nS, 6 * nS};
-  // priority: small tables, planes, transform temp, S tables, eigenspace
-  const int order[5] = {4, 1, 2, 0, 3};
+  const size_t sizes[5] = {3 * n2, 3 * n2, 3 * n2, (size_t)slab_thickness((int)nS) * n2, 6 * nS};
+  // priority: small tables, planes, transform temp, eigenspace slab, S tables
+  const int order[5] = {4, 1, 2, 3, 0};
   c.ws = plan_regions(sizes, 5, sizeof(T), kStarSmemCap, &c.smem, order);
   c.ok = plan_ok(c.ws, sizes, 5, sizeof(T), c.smem);
+  c.block = c.smem > 100 * 1024 ? 512 : 256;  // a block that owns the SM brings more warps
   const int64_t grid = (int64_t)nsm * blocks_per_sm(c.smem);
   c.grid = (int)(G.nstar < grid ? G.nstar : grid);
   if (c.grid < 1) c.grid = 1;
@@ -295,7 +452,14 @@ void launch_star(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws, const
   if (G.nstar == 0 || !c.ok) return;
   // copy the S tables into the CTA's work memory only when that is shared memory
   const int S_copy = c.ws.in_smem[0];
-  k_star<T><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter);
+  switch (G.p) {
+    case 2: k_star<T, 2><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
+    case 4: k_star<T, 4><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
+    case 8: k_star<T, 8><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
+    case 16: k_star<T, 16><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
+    case 32: k_star<T, 32><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
+    default: k_star<T, 0><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
+  }
 }
 
 template LaunchCfg plan_star<double>(const Geo&, int);
@@ -305,11 +469,18 @@ template void launch_star<double>(const Geo&, const Tabs<double>&, const double*
 template void launch_star<float>(const Geo&, const Tabs<float>&, const float*, float*, float*, const LaunchCfg&, int*,
                                  cudaStream_t);
 
-int set_star_smem_limits() {
+template <typename T>
+static int star_attrs() {
   int bad = 0;
-  bad |= cudaFuncSetAttribute(k_star<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_star<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_star<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_star<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_star<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_star<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_star<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_star<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return bad;
 }
+
+int set_star_smem_limits() { return star_attrs<double>() | star_attrs<float>(); }
 
 }  // namespace semmg
