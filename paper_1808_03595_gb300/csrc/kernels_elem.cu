@@ -116,6 +116,110 @@ __device__ __forceinline__ void txT_lines(const Lines& L, int ax, const T* __res
   }
 }
 
+
+// ---- grouped line transforms: each thread computes kG outputs of one line
+// that share the input loads (independent multiply-add chains).
+constexpr int kG = 4;
+
+__device__ __forceinline__ int nlines(const Lines& L) { return L.total / L.n; }
+
+// First element and stride of line l along axis ax.
+__device__ __forceinline__ void line_of(const Lines& L, int ax, int l, int* base, int* str, int* i2) {
+  if (ax == 0) {
+    *base = l * L.D0;
+    *str = 1;
+    *i2 = l / L.D1;
+  } else if (ax == 1) {
+    const int a2 = l / L.D0, a0 = l - a2 * L.D0;
+    *base = a2 * L.D1 * L.D0 + a0;
+    *str = L.D0;
+    *i2 = a2;
+  } else {
+    *base = l;
+    *str = L.D0 * L.D1;
+    *i2 = 0;
+  }
+}
+
+__device__ __forceinline__ int line_groups(const Lines& L) {
+  return (L.ne + kG - 1) / kG + (L.n - L.ne + kG - 1) / kG;
+}
+
+// Outputs [k0, k1) of group g and the folded input range [j0, j1); even: inputs use row h + j.
+__device__ __forceinline__ void line_block(const Lines& L, int g, int* k0, int* k1, int* j0, int* j1, int* even) {
+  const int ge = (L.ne + kG - 1) / kG;
+  if (g < ge) {
+    *k0 = g * kG;
+    *k1 = min(*k0 + kG, L.ne);
+    *j0 = 0;
+    *j1 = L.ne;
+    *even = 1;
+  } else {
+    *k0 = L.ne + (g - ge) * kG;
+    *k1 = min(*k0 + kG, L.n);
+    *j0 = L.ne;
+    *j1 = L.n;
+    *even = 0;
+  }
+}
+
+// Z = (scale or sc2[i2]) * forward transform of folded Y along ax.
+template <typename T>
+__device__ __forceinline__ void tx_lines_g(const Lines& L, int ax, const T* __restrict__ S, const T* Y, T* Z,
+                                           T scale, const T* sc2) {
+  const int G = line_groups(L), n = L.n;
+  const int items = nlines(L) * G;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int l = it / G, g = it - l * G;
+    int base, str, i2, k0, k1, j0, j1, even;
+    line_of(L, ax, l, &base, &str, &i2);
+    line_block(L, g, &k0, &k1, &j0, &j1, &even);
+    T a[kG];
+#pragma unroll
+    for (int q = 0; q < kG; ++q) a[q] = 0;
+    for (int j = j0; j < j1; ++j) {
+      const T yv = Y[base + j * str];
+      const T* sr = S + (even ? L.h + j : j) * n + k0;
+#pragma unroll
+      for (int q = 0; q < kG; ++q)
+        if (k0 + q < k1) a[q] += sr[q] * yv;
+    }
+    const T s = sc2 ? sc2[i2] : scale;
+#pragma unroll
+    for (int q = 0; q < kG; ++q)
+      if (k0 + q < k1) Z[base + (k0 + q) * str] = s * a[q];
+  }
+}
+
+// Y = transposed transform of B along ax into folded form (E_j, O_q).
+template <typename T>
+__device__ __forceinline__ void txT_lines_g(const Lines& L, int ax, const T* __restrict__ S, const T* B, T* Y) {
+  const int G = line_groups(L), n = L.n;
+  const int items = nlines(L) * G;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int l = it / G, g = it - l * G;
+    int base, str, i2, k0, k1, j0, j1, even;
+    line_of(L, ax, l, &base, &str, &i2);
+    line_block(L, g, &k0, &k1, &j0, &j1, &even);
+    T a[kG];
+    const T* sr[kG];
+#pragma unroll
+    for (int q = 0; q < kG; ++q) {
+      a[q] = 0;
+      const int jo = min(k0 + q, k1 - 1);
+      sr[q] = S + (even ? L.h + jo : jo) * n;
+    }
+    for (int k = j0; k < j1; ++k) {
+      const T bv = B[base + k * str];
+#pragma unroll
+      for (int q = 0; q < kG; ++q) a[q] += sr[q][k] * bv;
+    }
+#pragma unroll
+    for (int q = 0; q < kG; ++q)
+      if (k0 + q < k1) Y[base + (k0 + q) * str] = a[q];
+  }
+}
+
 // Natural-order value at element idx from folded E/O data.
 template <typename T>
 __device__ __forceinline__ T unfold_at(const Lines& L, int ax, const T* Y, int idx) {
@@ -149,25 +253,15 @@ __device__ __forceinline__ void face_pairs(int mm, T* X) {
 // forward 2D transform of the six face arrays, scaled by c_f alpha_d
 template <typename T>
 __device__ __forceinline__ void faces_forward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc) {
+  __shared__ T sc6[6];
+  if (threadIdx.x < 6) sc6[threadIdx.x] = sc.sf[threadIdx.x >> 1];
   fold_lines(F, 0, X, Tt);
   __syncthreads();
-  tx_lines(F, 0, Sh, Tt, X, (T)1);
+  tx_lines_g(F, 0, Sh, Tt, X, (T)1, (const T*)nullptr);
   __syncthreads();
   fold_lines(F, 1, X, Tt);
   __syncthreads();
-  const int mm = F.D0 * F.D1;
-  const int str = F.stride(1), n = F.n;
-  for (int idx = threadIdx.x; idx < F.total; idx += blockDim.x) {  // tx along slow index with per-face scale
-    const int k = F.pos(idx, 1);
-    const T* y = Tt + (idx - k * str);
-    T s = 0;
-    if (k < F.ne) {
-      for (int j = 0; j < F.ne; ++j) s += Sh[(F.h + j) * n + k] * y[j * str];
-    } else {
-      for (int q = F.ne; q < n; ++q) s += Sh[q * n + k] * y[q * str];
-    }
-    X[idx] = sc.sf[(idx / mm) >> 1] * s;
-  }
+  tx_lines_g(F, 1, Sh, Tt, X, (T)1, (const T*)sc6);
   __syncthreads();
 }
 
@@ -175,11 +269,11 @@ __device__ __forceinline__ void faces_forward(const Lines& F, const T* Sh, T* X,
 // and store of both faces: Z[2d] = sf (Ye + Yo), Z[2d+1] = sf (Ye - Yo).
 template <typename T, typename Store>
 __device__ __forceinline__ void faces_backward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc, Store store) {
-  txT_lines(F, 0, Sh, X, Tt);
+  txT_lines_g(F, 0, Sh, X, Tt);
   __syncthreads();
   unfold_lines(F, 0, Tt, X);
   __syncthreads();
-  txT_lines(F, 1, Sh, X, Tt);
+  txT_lines_g(F, 1, Sh, X, Tt);
   __syncthreads();
   const int mm = F.D0 * F.D1;
   for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
@@ -206,13 +300,21 @@ __device__ __forceinline__ void faces_reduce(int m, int ne, const T* a0, const T
   for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
     const int f = idx / mm, r = idx - f * mm, kb = r / m, ka = r - kb * m;
     const int k0 = (f & 1) ? ne : 0, k1 = (f & 1) ? m : ne;
-    T s = 0;
+    const T* w;
+    int ws;
     switch (f >> 1) {
-      case 0: { const T* w = W + (kb * m + ka) * m; for (int k = k0; k < k1; ++k) s += a0[k] * w[k]; } break;
-      case 1: { const T* w = W + kb * mm + ka; for (int k = k0; k < k1; ++k) s += a0[k] * w[k * m]; } break;
-      default: { const T* w = W + kb * m + ka; for (int k = k0; k < k1; ++k) s += a0[k] * w[k * mm]; } break;
+      case 0: w = W + (kb * m + ka) * m; ws = 1; break;
+      case 1: w = W + kb * mm + ka; ws = m; break;
+      default: w = W + kb * m + ka; ws = mm; break;
     }
-    X[idx] = s;
+    T s0 = 0, s1 = 0;  // two independent partial sums
+    int k = k0;
+    for (; k + 1 < k1; k += 2) {
+      s0 += a0[k] * w[k * ws];
+      s1 += a0[k + 1] * w[(k + 1) * ws];
+    }
+    if (k < k1) s0 += a0[k] * w[k * ws];
+    X[idx] = s0 + s1;
   }
 }
 
@@ -292,30 +394,30 @@ __global__ void __launch_bounds__(512) k_elem_schur(Geo G, Tabs<T> t, const T* _
 __device__ __forceinline__ void interior_forward(const Lines& I, const double* Sr, double* A, double* B, double scale) {
   fold_lines(I, 0, A, B);
   __syncthreads();
-  tx_lines(I, 0, Sr, B, A, 1.0);
+  tx_lines_g(I, 0, Sr, B, A, 1.0, (const double*)nullptr);
   __syncthreads();
   fold_lines(I, 1, A, B);
   __syncthreads();
-  tx_lines(I, 1, Sr, B, A, 1.0);
+  tx_lines_g(I, 1, Sr, B, A, 1.0, (const double*)nullptr);
   __syncthreads();
   fold_lines(I, 2, A, B);
   __syncthreads();
-  tx_lines(I, 2, Sr, B, A, scale);
+  tx_lines_g(I, 2, Sr, B, A, scale, (const double*)nullptr);
   __syncthreads();
 }
 
 // backward along x3 and x2 (natural order in A afterwards), then the x1
 // transposed transform into B; the caller unfolds B along x1.
 __device__ __forceinline__ void interior_backward(const Lines& I, const double* Sr, double* A, double* B) {
-  txT_lines(I, 2, Sr, A, B);
+  txT_lines_g(I, 2, Sr, A, B);
   __syncthreads();
   unfold_lines(I, 2, B, A);
   __syncthreads();
-  txT_lines(I, 1, Sr, A, B);
+  txT_lines_g(I, 1, Sr, A, B);
   __syncthreads();
   unfold_lines(I, 1, B, A);
   __syncthreads();
-  txT_lines(I, 0, Sr, A, B);
+  txT_lines_g(I, 0, Sr, A, B);
   __syncthreads();
 }
 
