@@ -212,6 +212,20 @@ int semmg_batch_solve(semmg_batch* batch, semmg_info* infos, void* stream);
 int semmg_batch_graph_nodes(const semmg_batch* batch, int64_t* nodes);
 void semmg_batch_destroy(semmg_batch* batch);
 
+/* ------------------------------------------------------------------ launch autotuning
+ * For every level of the context, times a few launch shapes of the star
+ * smoother and of the element Schur kernel -- the shared-memory budget per
+ * block (which decides which work arrays stay on chip and how many blocks
+ * share an SM) and the threads per block -- on the context's own buffers and
+ * keeps the fastest.  Every shape computes bitwise the same result; only the
+ * time changes.  Choices are cached per process by (kernel, element size,
+ * degree) and reused by later contexts without timing.  Synchronises the
+ * stream; call it before capturing a batch. */
+int semmg_autotune(semmg_ctx* ctx, void* stream);
+/* Launch shape in use for `kernel` (0 = star smoother, 1 = element Schur
+ * kernel) at `level` in element type dtype (SEMMG_F64 / SEMMG_F32). */
+int semmg_get_launch(const semmg_ctx* ctx, int level, int kernel, int dtype, int* block, int* smem_bytes, int* grid);
+
 /* ------------------------------------------------------------------ no-allocation smoothing
  * The paper has no counterpart to this entry point; it exists for callers of
  * this library that must not allocate device memory while they work -- for

@@ -77,6 +77,9 @@ SIGNATURES = {
     "semmg_batch_solve": (c_int, [c_void_p, ctypes.POINTER(semmg_info), c_void_p]),
     "semmg_batch_graph_nodes": (c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "semmg_batch_destroy": (None, [c_void_p]),
+    "semmg_autotune": (c_int, [c_void_p, c_void_p]),
+    "semmg_get_launch": (c_int, [c_void_p, c_int, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                 ctypes.POINTER(c_int)]),
     "semmg_set_timing": (c_int, [c_void_p, c_int]),
     "semmg_get_kstat": (c_int, [c_void_p, c_int, ctypes.POINTER(semmg_kstat)]),
     "semmg_reset_kstats": (c_int, [c_void_p]),

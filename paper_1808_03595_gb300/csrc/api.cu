@@ -4,7 +4,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -75,6 +78,7 @@ struct semmg_ctx {
   void* FBs = nullptr;
   void* EBs = nullptr;
   void* wss = nullptr;
+  size_t ws_bytes = 0;
   LaunchCfg fdm;
   // FP64 outer iteration
   double* Fh = nullptr;
@@ -574,6 +578,7 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   c->FBs = dalloc(c.get(), fbs * sizeof(double));
   c->EBs = dalloc(c.get(), ebs * sizeof(double));
   c->wss = dalloc(c.get(), wsb);
+  c->ws_bytes = wsb;
   const size_t esz = o.precision == SEMMG_MIXED ? sizeof(float) : sizeof(double);
   for (int l = 0; l < nl; ++l) {
     const size_t n = (size_t)c->geo[l].size;
@@ -1086,3 +1091,118 @@ void semmg_batch_destroy(semmg_batch* b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- launch autotuning
+
+namespace {
+
+struct TuneChoice {
+  size_t cap;
+  int block;
+};
+std::mutex g_tune_lock;
+std::map<std::tuple<int, int, int>, TuneChoice> g_tune;  // (kernel, element size, degree) -> choice
+
+const size_t kTuneCaps[3] = {48 * 1024, 100 * 1024, 200 * 1024};
+const int kTuneBlocks[2] = {256, 512};
+
+template <typename T>
+float time_launch(semmg_ctx* c, int l, int kernel, const LaunchCfg& cfg, const T* in, T* out, cudaStream_t st) {
+  const Geo& G = c->geo[l];
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto run = [&]() {
+    if (kernel == 0)
+      launch_star<T>(G, tabs<T>(c, l), in, (T*)c->Obs, (T*)c->wss, cfg, c->star_counter, st);
+    else
+      launch_elem_schur<T>(G, tabs<T>(c, l), in, (T*)c->Zs, (T*)c->wss, cfg, st);
+  };
+  run();
+  cudaEventRecord(e0, st);
+  const int reps = 3;
+  for (int i = 0; i < reps; ++i) run();
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  (void)out;
+  return ms / reps;
+}
+
+template <typename T>
+void tune_one(semmg_ctx* c, int l, int kernel, LaunchCfg& slot, const T* in, cudaStream_t st) {
+  const Geo& G = c->geo[l];
+  const auto key = std::make_tuple(kernel, (int)sizeof(T), G.p);
+  {
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      LaunchCfg cf = kernel == 0 ? plan_star<T>(G, c->nsm, it->second.cap, it->second.block)
+                                 : plan_elem_schur<T>(G, c->nsm, it->second.cap, it->second.block);
+      if (cf.ok && cf.ws_elems() * sizeof(T) <= c->ws_bytes) slot = cf;
+      return;
+    }
+  }
+  float best = 1e30f;
+  TuneChoice bc{0, 0};
+  LaunchCfg bcfg = slot;
+  for (size_t cap : kTuneCaps)
+    for (int blk : kTuneBlocks) {
+      LaunchCfg cf = kernel == 0 ? plan_star<T>(G, c->nsm, cap, blk) : plan_elem_schur<T>(G, c->nsm, cap, blk);
+      if (!cf.ok || cf.ws_elems() * sizeof(T) > c->ws_bytes) continue;
+      const float ms = time_launch<T>(c, l, kernel, cf, in, nullptr, st);
+      if (ms < best) {
+        best = ms;
+        bc = TuneChoice{cap, blk};
+        bcfg = cf;
+      }
+    }
+  if (best < 1e30f) {
+    slot = bcfg;
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    g_tune[key] = bc;
+  }
+}
+
+}  // namespace
+
+extern "C" int semmg_autotune(semmg_ctx* c, void* stream) {
+  if (!c) return SEMMG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  collect_timing(c);
+  const int saved = c->timing;
+  c->timing = 0;
+  const int L = c->L();
+  const bool mixed = c->opts.precision == SEMMG_MIXED;
+  for (int l = 0; l <= L; ++l) {
+    if (mixed) {
+      const float* in = (const float*)c->dl[l].Fw;
+      if (l >= 1) tune_one<float>(c, l, 0, c->dl[l].star32, in, st);
+      if (c->geo[l].m > 0) tune_one<float>(c, l, 1, c->dl[l].schur32, in, st);
+    } else {
+      const double* in = (const double*)c->dl[l].Fw;
+      if (l >= 1) tune_one<double>(c, l, 0, c->dl[l].star64, in, st);
+      if (c->geo[l].m > 0) tune_one<double>(c, l, 1, c->dl[l].schur64, in, st);
+    }
+  }
+  if (mixed && c->geo[L].m > 0) tune_one<double>(c, L, 1, c->dl[L].schur64, c->Uh, st);
+  c->timing = saved;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return check_cuda(c, "autotune");
+  return check_cuda(c, "autotune");
+}
+
+extern "C" int semmg_get_launch(const semmg_ctx* c, int level, int kernel, int dtype, int* block, int* smem,
+                                int* grid) {
+  if (!valid_level(c, level) || !block || !smem || !grid || (kernel != 0 && kernel != 1)) return SEMMG_ERR_INVALID_ARG;
+  const DevLevel& D = c->dl[level];
+  const LaunchCfg* cf;
+  if (kernel == 0) cf = dtype == SEMMG_F32 ? &D.star32 : &D.star64;
+  else cf = dtype == SEMMG_F32 ? &D.schur32 : &D.schur64;
+  *block = cf->block;
+  *smem = (int)cf->smem;
+  *grid = cf->grid;
+  return SEMMG_OK;
+}

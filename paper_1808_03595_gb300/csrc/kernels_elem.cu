@@ -535,14 +535,17 @@ constexpr size_t kSchurSmemCap = 200 * 1024;
 }  // namespace
 
 template <typename T>
-LaunchCfg plan_elem_schur(const Geo& G, int nsm) {
+LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap, int block) {
   LaunchCfg c;
+  if (cap == 0) cap = kSchurSmemCap;
   const size_t m = G.m, mm = m * m;
   const size_t sizes[4] = {mm + 2 * m, 6 * mm, 6 * mm, mm * m};
-  c.ws = plan_regions(sizes, 4, sizeof(T), kSchurSmemCap, &c.smem);
+  c.ws = plan_regions(sizes, 4, sizeof(T), cap, &c.smem);
   c.ok = plan_ok(c.ws, sizes, 4, sizeof(T), c.smem);
-  c.block = c.smem > 100 * 1024 ? 512 : 256;
-  const int64_t grid = (int64_t)nsm * blocks_per_sm(c.smem);
+  c.block = block ? block : (c.smem > 100 * 1024 ? 512 : 256);
+  int bps = blocks_per_sm(c.smem);
+  if (bps * c.block > 2048) bps = 2048 / c.block;
+  const int64_t grid = (int64_t)nsm * bps;
   c.grid = (int)(G.nelem < grid ? G.nelem : grid);
   if (c.grid < 1) c.grid = 1;
   return c;
@@ -594,8 +597,8 @@ void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f, c
   }
 }
 
-template LaunchCfg plan_elem_schur<double>(const Geo&, int);
-template LaunchCfg plan_elem_schur<float>(const Geo&, int);
+template LaunchCfg plan_elem_schur<double>(const Geo&, int, size_t, int);
+template LaunchCfg plan_elem_schur<float>(const Geo&, int, size_t, int);
 template void launch_elem_schur<double>(const Geo&, const Tabs<double>&, const double*, double*, double*,
                                         const LaunchCfg&, cudaStream_t);
 template void launch_elem_schur<float>(const Geo&, const Tabs<float>&, const float*, float*, float*,

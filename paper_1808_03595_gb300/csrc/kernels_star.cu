@@ -431,16 +431,19 @@ constexpr size_t kStarSmemCap = 200 * 1024;
 }  // namespace
 
 template <typename T>
-LaunchCfg plan_star(const Geo& G, int nsm) {
+LaunchCfg plan_star(const Geo& G, int nsm, size_t cap, int block) {
   LaunchCfg c;
+  if (cap == 0) cap = kStarSmemCap;
   const size_t nS = G.nS, n2 = nS * nS;
   const size_t sizes[5] = {3 * n2, 3 * n2, 3 * n2, (size_t)slab_thickness((int)nS) * n2, 6 * nS};
   // priority: small tables, planes, transform temp, eigenspace slab, S tables
   const int order[5] = {4, 1, 2, 3, 0};
-  c.ws = plan_regions(sizes, 5, sizeof(T), kStarSmemCap, &c.smem, order);
+  c.ws = plan_regions(sizes, 5, sizeof(T), cap, &c.smem, order);
   c.ok = plan_ok(c.ws, sizes, 5, sizeof(T), c.smem);
-  c.block = c.smem > 100 * 1024 ? 512 : 256;  // a block that owns the SM brings more warps
-  const int64_t grid = (int64_t)nsm * blocks_per_sm(c.smem);
+  c.block = block ? block : (c.smem > 100 * 1024 ? 512 : 256);  // a block that owns the SM brings more warps
+  int bps = blocks_per_sm(c.smem);
+  if (bps * c.block > 2048) bps = 2048 / c.block;
+  const int64_t grid = (int64_t)nsm * bps;
   c.grid = (int)(G.nstar < grid ? G.nstar : grid);
   if (c.grid < 1) c.grid = 1;
   return c;
@@ -462,8 +465,8 @@ void launch_star(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws, const
   }
 }
 
-template LaunchCfg plan_star<double>(const Geo&, int);
-template LaunchCfg plan_star<float>(const Geo&, int);
+template LaunchCfg plan_star<double>(const Geo&, int, size_t, int);
+template LaunchCfg plan_star<float>(const Geo&, int, size_t, int);
 template void launch_star<double>(const Geo&, const Tabs<double>&, const double*, double*, double*,
                                   const LaunchCfg&, int*, cudaStream_t);
 template void launch_star<float>(const Geo&, const Tabs<float>&, const float*, float*, float*, const LaunchCfg&, int*,

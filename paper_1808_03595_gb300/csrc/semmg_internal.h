@@ -291,7 +291,7 @@ inline int blocks_per_sm(size_t smem) {
   return b;
 }
 
-template <typename T> LaunchCfg plan_elem_schur(const Geo& G, int nsm);
+template <typename T> LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap = 0, int block = 0);
 template <typename T> void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws,
                                              const LaunchCfg& c, cudaStream_t st);
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm);
@@ -305,7 +305,7 @@ void launch_assemble_rhs(const Geo& G, const Tabs<double>& t, const double* f_no
                          double* Fhat, cudaStream_t st);
 void launch_pack(const Geo& G, const double* nodal, double* hat, cudaStream_t st);
 void launch_unpack(const Geo& G, const double* hat, double* nodal, cudaStream_t st);
-template <typename T> LaunchCfg plan_star(const Geo& G, int nsm);
+template <typename T> LaunchCfg plan_star(const Geo& G, int nsm, size_t cap = 0, int block = 0);
 template <typename T> void launch_star(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws,
                                        const LaunchCfg& c, int* counter, cudaStream_t st);
 template <typename T> void launch_star_gather(const Geo& G, const T* Ob, T* du, int accumulate,

@@ -186,6 +186,19 @@ class Context:
                                                _stream()), allow)
         return u_host, info
 
+    # ------------------------------------------------------------ launch tuning
+    def autotune(self):
+        """Pick the fastest launch shape per level for the star and element kernels (semmg_autotune)."""
+        self._check(self._lib.semmg_autotune(self._ctx, _stream()))
+
+    def launch_shape(self, level, kernel, dtype=torch.float64):
+        """(block, shared-memory bytes, grid) of kernel 'star' or 'schur' at a level."""
+        b, s, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.semmg_get_launch(self._ctx, level, {"star": 0, "schur": 1}[kernel],
+                                               L.SEMMG_F32 if dtype == torch.float32 else L.SEMMG_F64,
+                                               ctypes.byref(b), ctypes.byref(s), ctypes.byref(g)))
+        return b.value, s.value, g.value
+
     # ------------------------------------------------------------ timing
     def set_timing(self, enable=True):
         self._check(self._lib.semmg_set_timing(self._ctx, 1 if enable else 0))
