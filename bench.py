@@ -35,6 +35,12 @@ SWEEP = [4, 8, 16, 32]
 WORKLOAD = "helmholtz_8x8x8_p4-8-16-32"
 METRIC = "unknowns/s per solve to 1e-10 residual (FP64 vs mixed); smoother HBM GB/s"
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 entry in the peaks file)
+# DRAM bytes (read + write) per k_star<double> launch, averaged over every launch of
+# `bench.py --forms fp64 --no-e2e --no-batch --no-cpu-baseline --steps 1 --warmup 3` under
+# ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (profiles/k_star_f64_dram_helmholtz_8x8x8.md);
+# valid only for the star-kernel source it was measured on.
+STAR_TRAFFIC_BYTES = 20.70e6
+STAR_TRAFFIC_SOURCE = "6788e2e1dafe5fd0"
 
 
 def load_peaks():
@@ -295,10 +301,17 @@ def run_semmg(args, world, rank, local, pg):
     total_ms = sum(v["ms"] for v in kst.values())
     launches = sum(v["launches"] for v in kst.values())
     peaks = load_peaks()
+    traffic = None
+    if dom == "star":
+        import hashlib
+        src = os.path.join(ROOT, "paper_1808_03595_gb300", "csrc", "kernels_star.cu")
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == STAR_TRAFFIC_SOURCE:
+            traffic = STAR_TRAFFIC_BYTES
     if d["flops"] > 0:
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
+                "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
                 "peak_source": "nominal FP64 1.25 TFLOP/s (2 FP64 FMA/clk/SM x 152 SMs at 2.07 GHz)",
                 "launches": d["launches"], "share_of_kernel_time": d["ms"] / total_ms,
                 "hbm_gbs": d["bytes"] / (d["ms"] / 1e3) / 1e9}
