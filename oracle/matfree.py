@@ -17,7 +17,9 @@ O(p^3) factorisations except where the paper prescribes them (Algorithm 1):
   * coarse solve: exact sparse direct solve of the full coarse system with the
     embedded right-hand side (F_hat, 0) (Sec. 3.1, eq. star_right_hand_side_full
     argument applied to the whole domain);
-  * Algorithms 3 and 4 literally.
+  * Algorithms 3 and 4 literally; Algorithm 5 (Krylov acceleration) with the
+    V-cycle as preconditioner; optionally the varied smoothing counts
+    nu_l = 2^(L-l) of Sec. 4.1.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -384,16 +386,21 @@ class CoarseSolver:
 class MG:
     """p-multigrid hierarchy (Sec. 4.1) on nodal condensed arrays."""
 
-    def __init__(self, mesh, p0=1, nu_pre=1, nu_post=1):
+    def __init__(self, mesh, p0=1, nu_pre=1, nu_post=1, nu_vary=False):
         self.degs = dense.level_degrees(mesh.p, p0)
         self.meshes = [mesh.with_degree(q) for q in self.degs]
-        self.tables = [StarTables(m) if m.p > 1 or True else None for m in self.meshes]
+        self.tables = [StarTables(m) for m in self.meshes]
         self.coarse = CoarseSolver(self.meshes[0])
         self.nu_pre, self.nu_post = nu_pre, nu_post
+        self.nu_vary = nu_vary
 
     @property
     def L(self):
         return len(self.degs) - 1
+
+    def nu(self, l, base):
+        """Smoothing steps on level l (Sec. 4.1): the base count, or base * 2^(L-l) when varied."""
+        return base * 2 ** (self.L - l) if self.nu_vary else base
 
     def op(self, l, u):
         return apply_condensed(self.meshes[l], u)
@@ -412,13 +419,13 @@ def vcycle(mg, u, F):
     for l in range(L, 0, -1):
         if l != L:
             ul[l] = np.zeros_like(Fl[l])
-        for _ in range(mg.nu_pre):
+        for _ in range(mg.nu(l, mg.nu_pre)):
             ul[l] = ul[l] + mg.smooth(l, Fl[l] - mg.op(l, ul[l]))
         Fl[l - 1] = restrict(mg.meshes[l], mg.meshes[l - 1], Fl[l] - mg.op(l, ul[l]))
     ul[0] = mg.coarse.solve(Fl[0])
     for l in range(1, L + 1):
         ul[l] = ul[l] + prolong(mg.meshes[l - 1], mg.meshes[l], ul[l - 1])
-        for _ in range(mg.nu_post):
+        for _ in range(mg.nu(l, mg.nu_post)):
             ul[l] = ul[l] + mg.smooth(l, Fl[l] - mg.op(l, ul[l]))
     return ul[L]
 
@@ -436,6 +443,46 @@ def mg_solve(mg, Fhat, rtol=1e-10, maxit=50):
         hist.append(np.linalg.norm(r))
         it += 1
     return u, it, np.array(hist)
+
+
+def ipcg(op, precond, b, rtol=1e-10, maxit=50):
+    """Algorithm 5's iteration: inexact preconditioned CG from u = 0.
+
+    op(v) applies the SPD operator, precond(r) the (possibly non-symmetric or
+    varying) preconditioner.  beta uses the difference of the new and the old
+    residual against z, so the method tolerates preconditioners that are not
+    symmetric (the weighted smoother makes the V-cycle one).  Stops at
+    ||r|| <= rtol ||r_0|| with the recursively updated residual.
+    Returns (u, iterations, residual-norm history).
+    """
+    u = np.zeros_like(b)
+    r = b - op(u)
+    s = r.copy()          # makes beta = 0 in the first iteration
+    p = np.zeros_like(b)
+    delta = 1.0
+    n0 = np.linalg.norm(r)
+    hist = [n0]
+    it = 0
+    while hist[-1] > rtol * n0 and it < maxit:
+        z = precond(r)
+        gamma = float(np.vdot(z, r))
+        gamma0 = float(np.vdot(z, s))
+        beta = (gamma - gamma0) / delta
+        delta = gamma
+        p = beta * p + z
+        q = op(p)
+        alpha = gamma / float(np.vdot(q, p))
+        s = r.copy()
+        u = u + alpha * p
+        r = r - alpha * q
+        hist.append(np.linalg.norm(r))
+        it += 1
+    return u, it, np.array(hist)
+
+
+def kmg_solve(mg, Fhat, rtol=1e-10, maxit=50):
+    """Algorithm 5: Krylov-accelerated multigrid, the V-cycle MultigridCycle(0, r) as preconditioner."""
+    return ipcg(lambda v: mg.op(mg.L, v), lambda r: vcycle(mg, np.zeros_like(r), r), Fhat, rtol, maxit)
 
 
 def solve(mesh, f, p0=1, rtol=1e-10, maxit=50):

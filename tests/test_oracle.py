@@ -310,27 +310,95 @@ def test_mg_solve_matches_direct_solve():
 
 def _golden_iterations():
     rows = []
-    with open(os.path.join(GOLDEN, "paper_iterations.txt")) as fh:
+    with open(os.path.join(GOLDEN, "paper_iterations_stretched.txt")) as fh:
         for line in fh:
             line = line.strip()
             if line and not line.startswith("#"):
-                p, n = line.split()
-                rows.append((int(p), int(n)))
+                alpha, solver, p, n = line.split()
+                rows.append((float(alpha), solver, int(p), int(n)))
     return rows
 
 
-@pytest.mark.parametrize("p,n10", [r for r in _golden_iterations() if r[0] <= 8])
-def test_iterations_match_paper_table(p, n10):
-    # Sec. 5.2 / Table (alpha = 1, MG): 8^3 elements on (0, 2 pi)^3, Poisson,
-    # pseudo-random input data, p0 = 2; the paper's runs used inhomogeneous
-    # Dirichlet data, these use homogeneous ones, so one iteration of slack.
-    mesh = dense.Mesh([np.full(8, 2 * np.pi / 8)] * 3, p, 0.0)
+@pytest.mark.parametrize("alpha,solver,p,n10", [r for r in _golden_iterations() if r[2] <= 8])
+def test_iterations_match_paper_table(alpha, solver, p, n10):
+    # Sec. 5.4, table of iterations on stretched grids: 8^3 elements on
+    # (0, 2 pi)^3, widths in geometric progression (factor alpha), Poisson,
+    # pseudo-random input data (Sec. 5.2), p0 = 2.  The paper's runs used
+    # inhomogeneous Dirichlet data, these use homogeneous ones: one iteration
+    # of slack.  Covers Algorithm 4 (MG), Algorithm 5 (kMG) and Algorithm 5
+    # with the varied smoothing counts of Sec. 4.1 (kvMG).
+    import workloads
+    mesh = dense.Mesh(workloads.expansion_widths(8, alpha), p, 0.0)
     f = _rng(1808).uniform(-1, 1, mesh.shape)
-    mg = matfree.MG(mesh, p0=2)
+    mg = matfree.MG(mesh, p0=2, nu_vary=(solver == "kvMG"))
     Fh = matfree.condense_rhs(mesh, f)
-    _, it, hist = matfree.mg_solve(mg, Fh)
+    if solver == "MG":
+        _, it, hist = matfree.mg_solve(mg, Fh, maxit=60)
+    else:
+        _, it, hist = matfree.kmg_solve(mg, Fh, maxit=60)
+    assert hist[-1] <= 1e-10 * hist[0]
     assert abs(it - n10) <= 1, (it, n10)
-    # Sec. 5.2: MG convergence rate about 1e-4 per cycle for p >= 8
+    # Sec. 5.2: MG convergence rate about 1e-4 per cycle for p >= 8 on the uniform mesh
     rho = (hist[-1] / hist[0]) ** (1.0 / it)
-    if p >= 8:
+    if alpha == 1.0 and p >= 8:
         assert rho < 1e-3
+
+
+def test_ipcg_identity_preconditioner_is_textbook_cg():
+    # With z = r the old-residual term z^T s vanishes in exact arithmetic
+    # (successive CG residuals are orthogonal), so Algorithm 5's iteration is
+    # plain CG: its iterates must follow scipy's CG step by step.
+    import scipy.sparse.linalg as spla
+    rng = _rng(21)
+    n = 40
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    A = Q @ np.diag(np.linspace(1.0, 30.0, n)) @ Q.T
+    b = rng.standard_normal(n)
+    xs = []
+    spla.cg(A, b, rtol=1e-300, atol=0.0, maxiter=12, callback=lambda xk: xs.append(xk.copy()))
+    for k in range(1, 13):
+        u, it, _ = matfree.ipcg(lambda v: A @ v, lambda r: r.copy(), b, rtol=1e-300, maxit=k)
+        assert it == k
+        assert np.linalg.norm(u - xs[k - 1]) <= 1e-10 * np.linalg.norm(xs[k - 1])
+
+
+def test_ipcg_exact_preconditioner_one_step_and_nonsymmetric():
+    rng = _rng(22)
+    n = 30
+    B = rng.standard_normal((n, n))
+    A = B @ B.T + n * np.eye(n)
+    b = rng.standard_normal(n)
+    x = np.linalg.solve(A, b)
+    # exact inverse as preconditioner: p = z = A^{-1} r_0 and alpha = 1, done in one step
+    u, it, hist = matfree.ipcg(lambda v: A @ v, lambda r: np.linalg.solve(A, r), b, rtol=1e-12)
+    assert it == 1 and np.linalg.norm(u - x) <= 1e-12 * np.linalg.norm(x)
+    # a non-symmetric preconditioner (a perturbed inverse) still converges; ipCG's beta is
+    # meant for this case (Sec. 4.1: the weighted smoother makes the V-cycle non-symmetric)
+    P = np.linalg.inv(A) @ (np.eye(n) + 0.3 * rng.standard_normal((n, n)) / np.sqrt(n))
+    u, it, hist = matfree.ipcg(lambda v: A @ v, lambda r: P @ r, b, rtol=1e-10, maxit=200)
+    assert hist[-1] <= 1e-10 * hist[0]
+    assert np.linalg.norm(u - x) <= 1e-8 * np.linalg.norm(x)
+
+
+def test_kmg_solve_matches_direct_solve():
+    # Algorithm 5 with the V-cycle preconditioner reaches the dense direct solution
+    mesh = _mesh_small(p=5, lam=0.0)
+    cond = dense.Condensed(mesh)
+    f = _rng(11).uniform(-1, 1, mesh.shape)
+    uex = cond.full_solve(cond.load(f))
+    Fh = matfree.condense_rhs(mesh, f)
+    for nu_vary in (False, True):
+        mg = matfree.MG(mesh, p0=1, nu_vary=nu_vary)
+        uh, it, hist = matfree.kmg_solve(mg, Fh)
+        assert hist[-1] <= 1e-10 * hist[0] and it <= 6
+        u = matfree.recover(mesh, f, uh)
+        assert np.abs(u - uex).max() < 1e-8 * np.abs(uex).max()
+
+
+def test_varied_smoothing_counts():
+    # Sec. 4.1: nu_pre,l = nu_post,l = 2^(L-l); the finest level keeps one step
+    mesh = dense.Mesh([np.full(2, 0.5)] * 3, 8, 1.0)
+    mg = matfree.MG(mesh, p0=1, nu_vary=True)
+    assert mg.degs == [1, 2, 4, 8]
+    assert [mg.nu(l, 1) for l in range(1, 4)] == [4, 2, 1]
+    assert [matfree.MG(mesh, p0=1).nu(l, 1) for l in range(1, 4)] == [1, 1, 1]

@@ -13,6 +13,9 @@ Workloads (names used by bench.py and the tests):
   poisson_6x6x6_p48_stretched
                           lambda = 0, per-axis widths exp(U(0, ln 8)) normalised to 1 (seed 1808035954),
                           manufactured f
+  expansion_widths(n, alpha)
+                          per-axis widths in geometric progression on (0, 2 pi), the stretched
+                          meshes of the paper's iteration-count table (Sec. 5.4)
   batch64                 64 solves, n ~ U{2..12}, p ~ U{4..24}, lambda = 10^U(-2, 3), f ~ U(-1, 1),
                           seed 1808035955
 """
@@ -66,6 +69,13 @@ def stretched_widths(n, seed=SEED_CFG4, ratio=8.0):
         w = np.exp(rng.uniform(0.0, math.log(ratio), size=n))
         out.append(w / w.sum())
     return out
+
+
+def expansion_widths(n, alpha, length=2 * math.pi):
+    """Per-axis widths growing by the constant factor alpha from one end of each axis to the other
+    (the paper's stretched test meshes, Sec. 5.4: largest over smallest width alpha^(n-1))."""
+    w = alpha ** np.arange(n, dtype=float)
+    return [length * w / w.sum() for _ in range(3)]
 
 
 def sinsinsin(h, p):
