@@ -5,8 +5,11 @@ elements, degree sweep p in {4, 8, 16, 32}, f = manufactured solution plus
 seeded N(0, 1e-2) noise at the GLL nodes, plain FP64 GPU form, coarse degree
 p0 = 2.  One step solves all four degrees (condensation, V-cycles to 1e-10,
 interior recovery); unknowns = sum of (8p+1)^3.  The mixed-precision form
-(FP32 V-cycle inside FP64 iterative refinement) is timed on the same workload
-and reported under "mixed".
+(FP32 smoother and transfers, FP64 residual arithmetic, inside FP64 iterative
+refinement) is timed on the same workload and reported under "mixed"; "forms"
+adds the all-FP32 V-cycle and the Krylov-accelerated iteration (Algorithm 5)
+in FP64 and mixed precision, and "batched" 64 independent solves in one CUDA
+graph.
 
 Timing: CUDA events on the solving stream around each solve, L2 flushed
 (256 MiB write) before every solve, W untimed warm-up steps, then K timed
@@ -34,6 +37,10 @@ import workloads  # noqa: E402
 SWEEP = [4, 8, 16, 32]
 WORKLOAD = "helmholtz_8x8x8_p4-8-16-32"
 METRIC = "unknowns/s per solve to 1e-10 residual (FP64 vs mixed); smoother HBM GB/s"
+# timed forms: name -> (precision, outer iteration).  "fp64" is the headline value,
+# "mixed" the mixed-precision line (FP32 smoother and transfers, FP64 residuals).
+FORMS = {"fp64": ("fp64", "mg"), "mixed": ("mixed", "mg"), "mixed_fp32": ("mixed_fp32", "mg"),
+         "kmg_fp64": ("fp64", "kmg"), "kmg_mixed": ("mixed", "kmg")}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 entry in the peaks file)
 # DRAM bytes (read + write) per k_star<double> launch, averaged over every launch of
 # `bench.py --forms fp64 --no-e2e --no-batch --no-cpu-baseline --steps 1 --warmup 3` under
@@ -41,6 +48,20 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 entry in th
 # valid only for the star-kernel source it was measured on.
 STAR_TRAFFIC_BYTES = 20.70e6
 STAR_TRAFFIC_SOURCE = "6788e2e1dafe5fd0"
+STAR_SOURCES = ("star_kernel.cuh", "kernels_star_f64.cu")
+
+
+def star_source_hash():
+    """First 16 hex digits of the SHA-256 of the FP64 star-kernel sources (None if one is missing)."""
+    import hashlib
+    hsh = hashlib.sha256()
+    for name in STAR_SOURCES:
+        path = os.path.join(ROOT, "paper_1808_03595_gb300", "csrc", name)
+        if not os.path.exists(path):
+            return None
+        with open(path, "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:16]
 
 
 def load_peaks():
@@ -191,29 +212,37 @@ def run_semmg(args, world, rank, local, pg):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     degrees = [int(x) for x in args.degrees.split(",")]
 
+    forms = args.forms.split(",")
+    if "fp64" not in forms:
+        forms = ["fp64"] + forms
+    for form in forms:
+        if form not in FORMS:
+            raise SystemExit(f"unknown form {form}; choose from {sorted(FORMS)}")
     cases = []
     for p in degrees:
         h, p, lam, f, p0 = workloads.config(f"helmholtz_8x8x8_p{p}")
         fd = torch.as_tensor(f, dtype=torch.float64, device=dev)
-        ctx64 = Context(h, p, lam, p0=p0, precision="fp64")
-        ctx32 = Context(h, p, lam, p0=p0, precision="mixed")
         ud = torch.empty_like(fd)
         fh = torch.as_tensor(f, dtype=torch.float64).pin_memory()
         uh = torch.empty_like(fh).pin_memory()
-        cases.append({"p": p, "n": int(fd.numel()), "f": fd, "u": ud, "fh": fh, "uh": uh, "fp64": ctx64,
-                      "mixed": ctx32})
+        c = {"p": p, "n": int(fd.numel()), "f": fd, "u": ud, "fh": fh, "uh": uh}
+        for form in forms:
+            prec, solver = FORMS[form]
+            c[form] = Context(h, p, lam, p0=p0, precision=prec, solver=solver)
+        cases.append(c)
     tuned = {}
     if args.autotune:
         for c in cases:
-            for form in ("fp64", "mixed"):
+            for form in forms:
                 ctx = c[form]
                 ctx.autotune()
-                dt = torch.float32 if form == "mixed" else torch.float64
+                dts = torch.float32 if FORMS[form][0] == "mixed_fp32" else torch.float64
+                dt = torch.float64 if FORMS[form][0] == "fp64" else torch.float32
                 tuned.setdefault(form, {})[c["p"]] = {
-                    "star": ctx.launch_shape(ctx.L, "star", dt), "schur": ctx.launch_shape(ctx.L, "schur", dt)}
+                    "star": ctx.launch_shape(ctx.L, "star", dt), "schur": ctx.launch_shape(ctx.L, "schur", dts)}
     torch.cuda.synchronize()
 
-    per_p_ms = {"fp64": {}, "mixed": {}}
+    per_p_ms = {form: {} for form in forms}
 
     def solve_all(form, timed, host=False):
         ms, iters = 0.0, {}
@@ -238,7 +267,6 @@ def run_semmg(args, world, rank, local, pg):
             assert info.res_final <= 1e-10 * info.res0, (form, c["p"], info.res_final, info.res0)
         return ms, iters
 
-    forms = args.forms.split(",")
     for form in forms:
         for _ in range(args.warmup):
             solve_all(form, False)
@@ -263,21 +291,28 @@ def run_semmg(args, world, rank, local, pg):
             for kk in acc:
                 acc[kk] += v[kk]
         c["fp64"].set_timing(False)
-    t32, it32, te2e = float("nan"), {}, float("nan")
-    kst32 = {}
-    if "mixed" in forms:
+    te2e = float("nan")
+    tform, itform, kstform = {}, {}, {}
+    for form in forms:
+        if form == "fp64":
+            continue
         for c in cases:
-            c["mixed"].set_timing(True)
-        t32 = 0.0
+            c[form].set_timing(True)
+        tf = 0.0
         for _ in range(args.steps):
-            ms, it32 = solve_all("mixed", True)
-            t32 += ms
+            ms, itform[form] = solve_all(form, True)
+            tf += ms
+        tform[form] = tf
+        kk = kstform.setdefault(form, {})
         for c in cases:
-            for k, v in c["mixed"].kstats().items():
-                acc = kst32.setdefault(k, {"ms": 0.0, "launches": 0})
+            for k, v in c[form].kstats().items():
+                acc = kk.setdefault(k, {"ms": 0.0, "launches": 0})
                 acc["ms"] += v["ms"]
                 acc["launches"] += v["launches"]
-            c["mixed"].set_timing(False)
+            c[form].set_timing(False)
+    t32 = tform.get("mixed", float("nan"))
+    it32 = itform.get("mixed", {})
+    kst32 = kstform.get("mixed", {})
     if not args.no_e2e:
         # end to end through the host-buffer entry point
         solve_all("fp64", False, host=True)
@@ -290,10 +325,20 @@ def run_semmg(args, world, rank, local, pg):
     t64 = max_over_ranks(pg, t64)
     t32 = max_over_ranks(pg, t32)
     te2e = max_over_ranks(pg, te2e)
+    tform = {k: max_over_ranks(pg, v) for k, v in tform.items()}
     unknowns = sum(c["n"] for c in cases)
     value = world * unknowns * args.steps / (t64 / 1e3)
     value32 = world * unknowns * args.steps / (t32 / 1e3)
     e2e = world * unknowns * args.steps / (te2e / 1e3)
+    forms_out = {"fp64": {"precision": "fp64", "solver": "mg", "value": value, "ms_per_step": t64 / args.steps,
+                          "iterations": it64}}
+    for form, tf in tform.items():
+        v = world * unknowns * args.steps / (tf / 1e3)
+        forms_out[form] = {"precision": FORMS[form][0], "solver": FORMS[form][1], "value": v,
+                           "ms_per_step": tf / args.steps, "iterations": itform[form], "speedup_vs_fp64": v / value,
+                           "kernels": {k: {"ms_per_step": x["ms"] / args.steps,
+                                           "launches_per_step": x["launches"] / args.steps}
+                                       for k, x in kstform[form].items()}}
 
     # roofline of the dominant kernel (FP64 form): FP64-ALU bound
     dom = max(kst, key=lambda k: kst[k]["ms"])
@@ -303,9 +348,7 @@ def run_semmg(args, world, rank, local, pg):
     peaks = load_peaks()
     traffic = None
     if dom == "star":
-        import hashlib
-        src = os.path.join(ROOT, "paper_1808_03595_gb300", "csrc", "kernels_star.cu")
-        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == STAR_TRAFFIC_SOURCE:
+        if star_source_hash() == STAR_TRAFFIC_SOURCE:
             traffic = STAR_TRAFFIC_BYTES
     if d["flops"] > 0:
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
@@ -338,6 +381,7 @@ def run_semmg(args, world, rank, local, pg):
                          for k, v in kst.items()},
         "kernels_mixed": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
                           for k, v in kst32.items()},
+        "forms": forms_out,
         "ms_per_degree": per_p_ms,
         "launch_shapes_finest_level": tuned,
         "roofline": roof,
@@ -353,8 +397,8 @@ def run_semmg(args, world, rank, local, pg):
     if rank == 0:
         print(json.dumps(line), flush=True)
     for c in cases:
-        c["fp64"].close()
-        c["mixed"].close()
+        for form in forms:
+            c[form].close()
     return 0
 
 
@@ -413,7 +457,8 @@ def main():
     ap.add_argument("--degrees", default=",".join(str(p) for p in SWEEP))
     ap.add_argument("--cpu-sample-p", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="fp64,mixed", help="forms to run: fp64 (timed headline) and/or mixed")
+    ap.add_argument("--forms", default=",".join(FORMS),
+                    help="forms to time, from " + ", ".join(FORMS) + " (fp64 is always timed: the headline)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing (profiling runs)")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="tune launch shapes per degree before the warm-up (outside the timed region)")

@@ -71,9 +71,16 @@ enum {
 
 #define SEMMG_MAX_DEGREE 48
 
-/* precision of the V-cycle (the outer iteration, its residual, norms and
- * update, the coarse solve, condensation and recovery are always FP64) */
-enum { SEMMG_FP64 = 0, SEMMG_MIXED = 1 };
+/* precision of the V-cycle; the outer iteration (its residual, norms and
+ * update), the coarse solve, condensation and recovery are always FP64.
+ *   SEMMG_FP64        everything FP64;
+ *   SEMMG_MIXED       FP32 vectors, smoother and transfers in the V-cycle; its
+ *                     level residuals F - Hhat u in FP64 arithmetic on the FP32
+ *                     values (rounded once to FP32);
+ *   SEMMG_MIXED_FP32  the whole V-cycle in FP32, level residuals included. */
+enum { SEMMG_FP64 = 0, SEMMG_MIXED = 1, SEMMG_MIXED_FP32 = 2 };
+/* outer iteration of semmg_solve and of the batched form */
+enum { SEMMG_SOLVER_MG = 0, SEMMG_SOLVER_KMG = 1 };
 /* element type of a vector argument of smooth / restrict / prolong_add */
 enum { SEMMG_F64 = 0, SEMMG_F32 = 1 };
 
@@ -86,8 +93,11 @@ typedef struct {
   int p0;          /* coarse degree, 1 <= p0 <= p (default 2, Sec. 4.1) */
   int nu_pre;      /* pre-smoothing steps per level (default 1, Algorithm 3) */
   int nu_post;     /* post-smoothing steps per level (default 1) */
-  int precision;   /* SEMMG_FP64 (default) or SEMMG_MIXED */
-  int max_iter;    /* V-cycle cap of semmg_solve (default 50) */
+  int precision;   /* SEMMG_FP64 (default), SEMMG_MIXED or SEMMG_MIXED_FP32 */
+  int max_iter;    /* iteration cap of semmg_solve (default 50) */
+  int solver;      /* SEMMG_SOLVER_MG (Algorithm 4, default) or SEMMG_SOLVER_KMG (Algorithm 5) */
+  int nu_vary;     /* 0 (default): nu_pre / nu_post steps on every level; 1: nu_pre 2^(L-l) and
+                      nu_post 2^(L-l) steps on level l (Sec. 4.1, "kvMG" with SEMMG_SOLVER_KMG) */
 } semmg_opts;
 
 typedef struct {
@@ -172,12 +182,21 @@ int semmg_condense_rhs(semmg_ctx* ctx, const double* f_nodal, double* f_hat, voi
 int semmg_recover(semmg_ctx* ctx, const double* f_nodal, const double* u_hat, double* u_nodal,
                   void* stream);
 
-/* Algorithm 4: condense, V-cycles from u_hat = 0 until ||r|| <= rtol ||r_0||
- * (Euclidean norm over the condensed unknowns, checked on the host after each
- * cycle: one 8-byte device-to-host copy per cycle), recover.  f_nodal and
- * u_nodal are device nodal arrays of the finest level.  info may be NULL.
- * Returns SEMMG_ERR_NOT_CONVERGED after max_iter cycles (u_nodal still holds
- * the last iterate), SEMMG_ERR_NONFINITE on a NaN/Inf residual norm. */
+/* Algorithm 4 (opts.solver = SEMMG_SOLVER_MG): condense, V-cycles from
+ * u_hat = 0 until ||r|| <= rtol ||r_0|| (Euclidean norm over the condensed
+ * unknowns, checked on the host after each cycle: one 8-byte device-to-host
+ * copy per cycle), recover.
+ * Algorithm 5 (opts.solver = SEMMG_SOLVER_KMG): the same with the inexact
+ * preconditioned CG iteration of Sec. 4.1 in place of the plain cycle loop:
+ * z = MultigridCycle(0, r), gamma = z.r, gamma0 = z.s, beta = (gamma -
+ * gamma0) / delta, p = beta p + z, q = Hhat p, alpha = gamma / q.p, s = r,
+ * u += alpha p, r -= alpha q; the stopping test uses this updated residual.
+ * All of it in FP64 except the V-cycle in the mixed form; one Hhat
+ * application per iteration, as in Algorithm 4.
+ * f_nodal and u_nodal are device nodal arrays of the finest level.  info may
+ * be NULL; info->iters counts iterations (V-cycles).  Returns
+ * SEMMG_ERR_NOT_CONVERGED after max_iter iterations (u_nodal still holds the
+ * last iterate), SEMMG_ERR_NONFINITE on a NaN/Inf residual norm. */
 int semmg_solve(semmg_ctx* ctx, const double* f_nodal, double* u_nodal, double rtol,
                 semmg_info* info, void* stream);
 
@@ -190,8 +209,9 @@ int semmg_solve_host(semmg_ctx* ctx, const double* f_host, double* u_host, doubl
  * Many independent solves (each its own context: any mesh, p, lambda,
  * precision) captured once into one CUDA graph and launched with one call.
  * Each solve is a branch of the graph: condensation, then a device-side loop
- * (a conditional WHILE node) of V-cycle, FP64 residual and norm, whose check
- * kernel ends the loop when ||r|| <= rtol ||r_0|| or after max_iter cycles,
+ * (a conditional WHILE node) of V-cycle, FP64 residual and norm (or one
+ * Algorithm 5 iteration, per the context's opts.solver), whose check kernel
+ * ends the loop when ||r|| <= rtol ||r_0|| or after max_iter iterations,
  * then interior recovery.  Branches are independent, so solves run
  * concurrently; no host round trip happens between cycles (Algorithm 4 with
  * the stopping test of Sec. 5.2 evaluated on the device).
@@ -216,15 +236,27 @@ void semmg_batch_destroy(semmg_batch* batch);
  * For every level of the context, times a few launch shapes of the star
  * smoother and of the element Schur kernel -- the shared-memory budget per
  * block (which decides which work arrays stay on chip and how many blocks
- * share an SM) and the threads per block -- on the context's own buffers and
+ * share an SM), the threads per block and the register budget per thread
+ * (64 or 128, two builds of each kernel) -- on the context's own buffers and
  * keeps the fastest.  Every shape computes bitwise the same result; only the
  * time changes.  Choices are cached per process by (kernel, element size,
  * degree) and reused by later contexts without timing.  Synchronises the
  * stream; call it before capturing a batch. */
 int semmg_autotune(semmg_ctx* ctx, void* stream);
 /* Launch shape in use for `kernel` (0 = star smoother, 1 = element Schur
- * kernel) at `level` in element type dtype (SEMMG_F64 / SEMMG_F32). */
-int semmg_get_launch(const semmg_ctx* ctx, int level, int kernel, int dtype, int* block, int* smem_bytes, int* grid);
+ * kernel) at `level` in element type dtype (SEMMG_F64 / SEMMG_F32):
+ * threads per block, dynamic shared memory, blocks, and the register budget
+ * per thread of the kernel build that runs (64 or 128). */
+int semmg_get_launch(const semmg_ctx* ctx, int level, int kernel, int dtype, int* block, int* smem_bytes, int* grid,
+                     int* max_regs);
+/* Pin the launch shape of `kernel` at `level` in dtype: a shared-memory budget
+ * per block (work arrays that do not fit go to the context's global work
+ * memory), threads per block (256 or 512) and registers per thread (64 or
+ * 128); the blocks per launch follow from those.  For reproducing a tuned
+ * configuration without timing, and for tests.  SEMMG_ERR_INVALID_ARG on a
+ * bad value, SEMMG_ERR_UNSUPPORTED when the shape does not fit the context's
+ * work memory (the shape in use is then unchanged). */
+int semmg_set_launch(semmg_ctx* ctx, int level, int kernel, int dtype, int smem_cap_bytes, int block, int max_regs);
 
 /* ------------------------------------------------------------------ no-allocation smoothing
  * The paper has no counterpart to this entry point; it exists for callers of

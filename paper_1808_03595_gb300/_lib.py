@@ -23,7 +23,8 @@ ERRORS = {
     -7: "SEMMG_ERR_NOMEM",
 }
 SEMMG_ERR_NOT_CONVERGED = -4
-SEMMG_FP64, SEMMG_MIXED = 0, 1
+SEMMG_FP64, SEMMG_MIXED, SEMMG_MIXED_FP32 = 0, 1, 2
+SEMMG_SOLVER_MG, SEMMG_SOLVER_KMG = 0, 1
 SEMMG_F64, SEMMG_F32 = 0, 1
 SEMMG_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -33,7 +34,8 @@ class semmg_mesh(ctypes.Structure):
 
 
 class semmg_opts(ctypes.Structure):
-    _fields_ = [("p0", c_int), ("nu_pre", c_int), ("nu_post", c_int), ("precision", c_int), ("max_iter", c_int)]
+    _fields_ = [("p0", c_int), ("nu_pre", c_int), ("nu_post", c_int), ("precision", c_int), ("max_iter", c_int),
+                ("solver", c_int), ("nu_vary", c_int)]
 
 
 class semmg_kstat(ctypes.Structure):
@@ -79,7 +81,8 @@ SIGNATURES = {
     "semmg_batch_destroy": (None, [c_void_p]),
     "semmg_autotune": (c_int, [c_void_p, c_void_p]),
     "semmg_get_launch": (c_int, [c_void_p, c_int, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
-                                 ctypes.POINTER(c_int)]),
+                                 ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    "semmg_set_launch": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int]),
     "semmg_set_timing": (c_int, [c_void_p, c_int]),
     "semmg_get_kstat": (c_int, [c_void_p, c_int, ctypes.POINTER(semmg_kstat)]),
     "semmg_reset_kstats": (c_int, [c_void_p]),

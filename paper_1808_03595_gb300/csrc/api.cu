@@ -8,6 +8,7 @@
 #include <memory>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <new>
 #include <string>
 #include <vector>
@@ -84,6 +85,11 @@ struct semmg_ctx {
   double* Fh = nullptr;
   double* Uh = nullptr;
   double* Rh = nullptr;
+  // Algorithm 5 vectors (old residual s, search direction p, q = Hhat p) and scalars
+  double* kS = nullptr;
+  double* kP = nullptr;
+  double* kQ = nullptr;
+  KrylovScal* kscal = nullptr;
   // coarse solve
   double* cX = nullptr;
   double* cY = nullptr;
@@ -183,6 +189,17 @@ Tabs<T> upload_tabs(semmg_ctx* c, const HostLevel& H, const std::vector<double>*
   t.lamI = upload<T>(c, H.lamI, ok);
   for (int d = 0; d < 3; ++d) {
     t.h[d] = upload<T>(c, h[d], ok);
+    std::vector<double> hx(6 * h[d].size());
+    for (size_t a = 0; a < h[d].size(); ++a) {
+      const double ha = h[d][a];
+      hx[6 * a + 0] = ha;
+      hx[6 * a + 1] = 2.0 / ha;
+      hx[6 * a + 2] = 4.0 / (ha * ha);
+      hx[6 * a + 3] = std::sqrt(ha);
+      hx[6 * a + 4] = std::pow(2.0 / ha, 1.5);
+      hx[6 * a + 5] = std::sqrt(2.0 / ha);
+    }
+    t.hx[d] = upload<T>(c, hx, ok);
     t.starS[d] = upload<T>(c, H.starS[d], ok);
     t.starLam[d] = upload<T>(c, H.starLam[d], ok);
     t.act[d] = upload_u8(c, H.act[d], ok);
@@ -287,12 +304,30 @@ void collect_timing(semmg_ctx* c) {
   c->ev_used = 0;
 }
 
-// out = F - Hhat u (mode 0) or Hhat u (mode 1) on level l
+// V-cycle in FP32 (both mixed forms)
+bool cycle32(const semmg_ctx* c) { return c->opts.precision != SEMMG_FP64; }
+
+// out = F - Hhat u (mode 0) or Hhat u (mode 1) on level l.  FP32 vectors of
+// the SEMMG_MIXED form get FP64 arithmetic (FP64 face terms Z, FP64 sums).
 template <typename T>
 void op_residual(semmg_ctx* c, int l, const T* F, const T* u, T* out, int mode, cudaStream_t st) {
   const Geo& G = c->geo[l];
   const double vec = (double)G.size * sizeof(T);
   const double zb = (double)G.nelem * 6 * G.m * G.m * sizeof(T);
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->opts.precision == SEMMG_MIXED) {
+      const double zb64 = (double)G.nelem * 6 * G.m * G.m * sizeof(double);
+      {
+        Tic t(c, SEMMG_K_ELEM_SCHUR, st);
+        launch_elem_schur_mixed(G, c->dl[l].td, u, (double*)c->Zs, (double*)c->wss, c->dl[l].schur64, st);
+        t.toc(schur_flops(G), zb64 + zb / 2, G.m > 0 ? 1 : 0);
+      }
+      Tic t(c, SEMMG_K_ASSEMBLE, st);
+      launch_assemble_mixed(G, c->dl[l].td, F, u, (const double*)c->Zs, out, mode, st);
+      t.toc(0.0, vec * (mode == 0 ? 3 : 2) + zb64);
+      return;
+    }
+  }
   {
     Tic t(c, SEMMG_K_ELEM_SCHUR, st);
     launch_elem_schur<T>(G, tabs<T>(c, l), u, (T*)c->Zs, (T*)c->wss, schur_cfg<T>(c, l), st);
@@ -350,6 +385,9 @@ void op_coarse<float>(semmg_ctx* c, const float* F0, float* U0, cudaStream_t st)
   t.toc(0.0, 2.0 * n * sizeof(float), 10);
 }
 
+// Smoothing steps on level l: the base count, or base 2^(L-l) when varied (Sec. 4.1).
+int nu_at(const semmg_ctx* c, int l, int base) { return c->opts.nu_vary ? base << (c->L() - l) : base; }
+
 // Algorithm 3 with u_L = 0 on the residual held in Fw[L]: Uw[L] <- MultigridCycle(0, Fw[L]).
 template <typename T>
 void vcycle0(semmg_ctx* c, cudaStream_t st) {
@@ -359,9 +397,10 @@ void vcycle0(semmg_ctx* c, cudaStream_t st) {
     T* U = (T*)c->dl[l].Uw;
     T* R = (T*)c->dl[l].Rw;
     const int64_t n = c->geo[l].size;
-    if (c->opts.nu_pre >= 1) {
+    const int nu_pre = nu_at(c, l, c->opts.nu_pre);
+    if (nu_pre >= 1) {
       op_smooth<T>(c, l, F, U, 0, st);  // u_l = 0 + Smoother(F_l - H_l 0)
-      for (int i = 1; i < c->opts.nu_pre; ++i) {
+      for (int i = 1; i < nu_pre; ++i) {
         op_residual<T>(c, l, F, U, R, 0, st);
         op_smooth<T>(c, l, R, U, 1, st);
       }
@@ -377,42 +416,99 @@ void vcycle0(semmg_ctx* c, cudaStream_t st) {
     T* U = (T*)c->dl[l].Uw;
     T* R = (T*)c->dl[l].Rw;
     op_prolong_add<T>(c, l, (const T*)c->dl[l - 1].Uw, U, st);
-    for (int i = 0; i < c->opts.nu_post; ++i) {
+    const int nu_post = nu_at(c, l, c->opts.nu_post);
+    for (int i = 0; i < nu_post; ++i) {
       op_residual<T>(c, l, F, U, R, 0, st);
       op_smooth<T>(c, l, R, U, 1, st);
     }
   }
 }
 
-// u += MultigridCycle(0, r) with r in Rh (FP64); the cycle runs in the context precision.
-void correction(semmg_ctx* c, double* u, const double* r, cudaStream_t st) {
+// z = MultigridCycle(0, r) into Uw[L] for r in FP64; the cycle runs in the context precision.
+void precondition(semmg_ctx* c, const double* r, cudaStream_t st) {
   const int L = c->L();
   const int64_t n = c->geo[L].size;
-  const size_t es = c->opts.precision == SEMMG_MIXED ? sizeof(float) : sizeof(double);
+  const size_t es = cycle32(c) ? sizeof(float) : sizeof(double);
   {
     Tic t(c, SEMMG_K_VECTOR, st);
-    if (c->opts.precision == SEMMG_MIXED)
+    if (cycle32(c))
       launch_copy<float, double>((float*)c->dl[L].Fw, r, n, st);
     else
       launch_copy<double, double>((double*)c->dl[L].Fw, r, n, st);
     t.toc(0.0, (double)n * (8 + es));
   }
-  if (c->opts.precision == SEMMG_MIXED)
+  if (cycle32(c))
     vcycle0<float>(c, st);
   else
     vcycle0<double>(c, st);
+}
+
+// u += MultigridCycle(0, r) with r in FP64.
+void correction(semmg_ctx* c, double* u, const double* r, cudaStream_t st) {
+  const int L = c->L();
+  const int64_t n = c->geo[L].size;
+  const size_t es = cycle32(c) ? sizeof(float) : sizeof(double);
+  precondition(c, r, st);
   Tic t(c, SEMMG_K_VECTOR, st);
-  if (c->opts.precision == SEMMG_MIXED)
+  if (cycle32(c))
     launch_axpy<double, float>(u, (const float*)c->dl[L].Uw, 1.0, n, st);
   else
     launch_axpy<double, double>(u, (const double*)c->dl[L].Uw, 1.0, n, st);
   t.toc(0.0, (double)n * (16 + es));
 }
 
-int norm2_sync(semmg_ctx* c, const double* x, int64_t n, cudaStream_t st, double* out) {
+// Start of the outer iteration from u_hat = 0: r = F_hat, ||r||^2 into dnorm,
+// and for Algorithm 5 s = r, p = 0, delta = 1.
+void iter_start(semmg_ctx* c, cudaStream_t st) {
+  const int L = c->L();
+  const int64_t n = c->geo[L].size;
   Tic t(c, SEMMG_K_VECTOR, st);
-  launch_norm2<double>(x, n, c->part, c->npart, c->dnorm, st);
-  t.toc(2.0 * n, 8.0 * n, 2);
+  cudaMemsetAsync(c->Uh, 0, n * sizeof(double), st);
+  launch_copy<double, double>(c->Rh, c->Fh, n, st);
+  launch_norm2<double>(c->Fh, n, c->part, c->npart, c->dnorm, st);
+  if (c->opts.solver == SEMMG_SOLVER_KMG) {
+    launch_copy<double, double>(c->kS, c->Rh, n, st);
+    cudaMemsetAsync(c->kP, 0, n * sizeof(double), st);
+    launch_krylov_init(c->kscal, st);
+  }
+  t.toc(2.0 * n, 8.0 * n * (c->opts.solver == SEMMG_SOLVER_KMG ? 6 : 3), 3);
+}
+
+// One outer iteration, ||r||^2 into dnorm.  Algorithm 4: u += MultigridCycle(0, r),
+// r = F - Hhat u.  Algorithm 5: z = MultigridCycle(0, r), beta, p = beta p + z,
+// q = Hhat p, alpha, s = r, u += alpha p, r -= alpha q.
+void iter_step(semmg_ctx* c, cudaStream_t st) {
+  const int L = c->L();
+  const int64_t n = c->geo[L].size;
+  if (c->opts.solver == SEMMG_SOLVER_MG) {
+    correction(c, c->Uh, c->Rh, st);
+    op_residual<double>(c, L, c->Fh, c->Uh, c->Rh, 0, st);
+    Tic t(c, SEMMG_K_VECTOR, st);
+    launch_norm2<double>(c->Rh, n, c->part, c->npart, c->dnorm, st);
+    t.toc(2.0 * n, 8.0 * n, 2);
+    return;
+  }
+  precondition(c, c->Rh, st);
+  const bool mixed = cycle32(c);
+  {
+    Tic t(c, SEMMG_K_VECTOR, st);
+    if (mixed)
+      launch_krylov_beta_dir<float>((const float*)c->dl[L].Uw, c->Rh, c->kS, c->kP, n, c->part, c->npart, c->kscal,
+                                    st);
+    else
+      launch_krylov_beta_dir<double>((const double*)c->dl[L].Uw, c->Rh, c->kS, c->kP, n, c->part, c->npart,
+                                     c->kscal, st);
+    t.toc(6.0 * n, n * (mixed ? 4.0 + 8 + 8 + 4 + 16 : 8.0 * 6), 3);
+  }
+  op_residual<double>(c, L, c->Fh, c->kP, c->kQ, 1, st);  // q = Hhat p
+  Tic t(c, SEMMG_K_VECTOR, st);
+  launch_krylov_alpha(c->kQ, c->kP, n, c->part, c->npart, c->kscal, st);
+  launch_krylov_update(c->Uh, c->Rh, c->kS, c->kP, c->kQ, n, c->part, c->npart, c->kscal, c->dnorm, st);
+  t.toc(8.0 * n, 8.0 * n * 9, 4);
+}
+
+// sqrt of the squared norm left in dnorm by the last iteration (one 8-byte copy + sync)
+int dnorm_sync(semmg_ctx* c, cudaStream_t st, double* out) {
   cudaMemcpyAsync(c->hnorm, c->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return check_cuda(c, "norm");
   *out = std::sqrt(*c->hnorm);
@@ -481,6 +577,8 @@ void semmg_default_opts(semmg_opts* o) {
   o->nu_post = 1;
   o->precision = SEMMG_FP64;
   o->max_iter = 50;
+  o->solver = SEMMG_SOLVER_MG;
+  o->nu_vary = 0;
 }
 
 int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* opts, void* stream,
@@ -495,7 +593,10 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   if (o.p0 < 1 || o.p0 > p) return SEMMG_ERR_UNSUPPORTED;
   if (!(lambda >= 0.0) || !std::isfinite(lambda)) return SEMMG_ERR_INVALID_ARG;
   if (o.nu_pre < 0 || o.nu_post < 0 || o.max_iter < 1) return SEMMG_ERR_INVALID_ARG;
-  if (o.precision != SEMMG_FP64 && o.precision != SEMMG_MIXED) return SEMMG_ERR_INVALID_ARG;
+  if (o.precision != SEMMG_FP64 && o.precision != SEMMG_MIXED && o.precision != SEMMG_MIXED_FP32)
+    return SEMMG_ERR_INVALID_ARG;
+  if (o.solver != SEMMG_SOLVER_MG && o.solver != SEMMG_SOLVER_KMG) return SEMMG_ERR_INVALID_ARG;
+  if (o.nu_vary != 0 && o.nu_vary != 1) return SEMMG_ERR_INVALID_ARG;
   for (int d = 0; d < 3; ++d) {
     if (mesh->n[d] < 1 || !mesh->h[d]) return SEMMG_ERR_INVALID_ARG;
     if ((int64_t)mesh->n[d] * p + 1 >= (1 << 20)) return SEMMG_ERR_UNSUPPORTED;
@@ -579,7 +680,7 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   c->EBs = dalloc(c.get(), ebs * sizeof(double));
   c->wss = dalloc(c.get(), wsb);
   c->ws_bytes = wsb;
-  const size_t esz = o.precision == SEMMG_MIXED ? sizeof(float) : sizeof(double);
+  const size_t esz = o.precision != SEMMG_FP64 ? sizeof(float) : sizeof(double);
   for (int l = 0; l < nl; ++l) {
     const size_t n = (size_t)c->geo[l].size;
     c->dl[l].Fw = dalloc(c.get(), n * esz);
@@ -591,13 +692,20 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   c->Fh = (double*)dalloc(c.get(), nL * sizeof(double));
   c->Uh = (double*)dalloc(c.get(), nL * sizeof(double));
   c->Rh = (double*)dalloc(c.get(), nL * sizeof(double));
+  if (o.solver == SEMMG_SOLVER_KMG) {
+    c->kS = (double*)dalloc(c.get(), nL * sizeof(double));
+    c->kP = (double*)dalloc(c.get(), nL * sizeof(double));
+    c->kQ = (double*)dalloc(c.get(), nL * sizeof(double));
+    c->kscal = (KrylovScal*)dalloc(c.get(), sizeof(KrylovScal));
+    if (!c->kS || !c->kP || !c->kQ || !c->kscal) return SEMMG_ERR_NOMEM;
+  }
   const size_t nK = (size_t)c->ct.K[0] * c->ct.K[1] * c->ct.K[2];
   c->cX = (double*)dalloc(c.get(), nK * sizeof(double));
   c->cY = (double*)dalloc(c.get(), nK * sizeof(double));
   c->F0d = (double*)dalloc(c.get(), (size_t)c->geo[0].size * sizeof(double));
   c->U0d = (double*)dalloc(c.get(), (size_t)c->geo[0].size * sizeof(double));
   c->npart = 512;
-  c->part = (double*)dalloc(c.get(), c->npart * sizeof(double));
+  c->part = (double*)dalloc(c.get(), 2 * c->npart * sizeof(double));  // two partial-sum rows (Algorithm 5)
   c->dnorm = (double*)dalloc(c.get(), sizeof(double));
   c->star_counter = (int*)dalloc(c.get(), 4 * sizeof(int));
   if (!c->star_counter || cudaMemset(c->star_counter, 0, 4 * sizeof(int)) != cudaSuccess) return SEMMG_ERR_NOMEM;
@@ -759,24 +867,19 @@ int semmg_recover(semmg_ctx* c, const double* f, const double* uh, double* u, vo
 int semmg_solve(semmg_ctx* c, const double* f, double* u, double rtol, semmg_info* info, void* stream) {
   if (!c || !f || !u || !(rtol > 0.0)) return SEMMG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  const int L = c->L();
-  const int64_t n = c->geo[L].size;
   int rc = semmg_condense_rhs(c, f, c->Fh, stream);
   if (rc) return rc;
-  cudaMemsetAsync(c->Uh, 0, n * sizeof(double), st);
+  iter_start(c, st);
   double r0 = 0.0, rn = 0.0;
-  rc = norm2_sync(c, c->Fh, n, st, &r0);  // r_0 = Fhat - Hhat 0
+  rc = dnorm_sync(c, st, &r0);  // r_0 = Fhat - Hhat 0
   if (rc) return rc;
   int it = 0;
   int status = SEMMG_OK;
   if (!std::isfinite(r0)) status = SEMMG_ERR_NONFINITE;
   rn = r0;
-  const double* r = c->Fh;
   while (status == SEMMG_OK && rn > rtol * r0 && it < c->opts.max_iter) {
-    correction(c, c->Uh, r, st);
-    op_residual<double>(c, L, c->Fh, c->Uh, c->Rh, 0, st);
-    r = c->Rh;
-    rc = norm2_sync(c, c->Rh, n, st, &rn);
+    iter_step(c, st);
+    rc = dnorm_sync(c, st, &rn);
     if (rc) return rc;
     ++it;
     if (!std::isfinite(rn)) status = SEMMG_ERR_NONFINITE;
@@ -926,12 +1029,8 @@ namespace {
 
 // Enqueue one solve of context c (device nodal f -> u) into the capturing stream s.
 int capture_solve(semmg_ctx* c, const double* f, double* u, BatchCtl* ctl, cudaStream_t s, cudaStream_t sb) {
-  const int L = c->L();
-  const int64_t n = c->geo[L].size;
   semmg_condense_rhs(c, f, c->Fh, s);
-  cudaMemsetAsync(c->Uh, 0, n * sizeof(double), s);
-  launch_copy<double, double>(c->Rh, c->Fh, n, s);
-  launch_norm2<double>(c->Fh, n, c->part, c->npart, c->dnorm, s);
+  iter_start(c, s);
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g) != cudaSuccess || cs != cudaStreamCaptureStatusActive)
@@ -954,9 +1053,7 @@ int capture_solve(semmg_ctx* c, const double* f, double* u, BatchCtl* ctl, cudaS
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   if (cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
     return check_cuda(c, "batch: body capture");
-  correction(c, c->Uh, c->Rh, sb);
-  op_residual<double>(c, L, c->Fh, c->Uh, c->Rh, 0, sb);
-  launch_norm2<double>(c->Rh, n, c->part, c->npart, c->dnorm, sb);
+  iter_step(c, sb);
   k_batch_check<<<1, 32, 0, sb>>>(ctl, c->dnorm, h);
   cudaGraph_t got = nullptr;
   if (cudaStreamEndCapture(sb, &got) != cudaSuccess) return check_cuda(c, "batch: body end");
@@ -1099,12 +1196,14 @@ namespace {
 struct TuneChoice {
   size_t cap;
   int block;
+  int wide;
 };
 std::mutex g_tune_lock;
 std::map<std::tuple<int, int, int>, TuneChoice> g_tune;  // (kernel, element size, degree) -> choice
 
 const size_t kTuneCaps[3] = {48 * 1024, 100 * 1024, 200 * 1024};
 const int kTuneBlocks[2] = {256, 512};
+const int kTuneWide[2] = {0, 1};
 
 template <typename T>
 float time_launch(semmg_ctx* c, int l, int kernel, const LaunchCfg& cfg, const T* in, T* out, cudaStream_t st) {
@@ -1140,26 +1239,29 @@ void tune_one(semmg_ctx* c, int l, int kernel, LaunchCfg& slot, const T* in, cud
     std::lock_guard<std::mutex> g(g_tune_lock);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      LaunchCfg cf = kernel == 0 ? plan_star<T>(G, c->nsm, it->second.cap, it->second.block)
-                                 : plan_elem_schur<T>(G, c->nsm, it->second.cap, it->second.block);
+      const TuneChoice& ch = it->second;
+      LaunchCfg cf = kernel == 0 ? plan_star<T>(G, c->nsm, ch.cap, ch.block, ch.wide)
+                                 : plan_elem_schur<T>(G, c->nsm, ch.cap, ch.block, ch.wide);
       if (cf.ok && cf.ws_elems() * sizeof(T) <= c->ws_bytes) slot = cf;
       return;
     }
   }
   float best = 1e30f;
-  TuneChoice bc{0, 0};
+  TuneChoice bc{0, 0, 0};
   LaunchCfg bcfg = slot;
   for (size_t cap : kTuneCaps)
-    for (int blk : kTuneBlocks) {
-      LaunchCfg cf = kernel == 0 ? plan_star<T>(G, c->nsm, cap, blk) : plan_elem_schur<T>(G, c->nsm, cap, blk);
-      if (!cf.ok || cf.ws_elems() * sizeof(T) > c->ws_bytes) continue;
-      const float ms = time_launch<T>(c, l, kernel, cf, in, nullptr, st);
-      if (ms < best) {
-        best = ms;
-        bc = TuneChoice{cap, blk};
-        bcfg = cf;
+    for (int blk : kTuneBlocks)
+      for (int wide : kTuneWide) {
+        LaunchCfg cf = kernel == 0 ? plan_star<T>(G, c->nsm, cap, blk, wide)
+                                   : plan_elem_schur<T>(G, c->nsm, cap, blk, wide);
+        if (!cf.ok || cf.ws_elems() * sizeof(T) > c->ws_bytes) continue;
+        const float ms = time_launch<T>(c, l, kernel, cf, in, nullptr, st);
+        if (ms < best) {
+          best = ms;
+          bc = TuneChoice{cap, blk, wide};
+          bcfg = cf;
+        }
       }
-    }
   if (best < 1e30f) {
     slot = bcfg;
     std::lock_guard<std::mutex> g(g_tune_lock);
@@ -1176,27 +1278,60 @@ extern "C" int semmg_autotune(semmg_ctx* c, void* stream) {
   const int saved = c->timing;
   c->timing = 0;
   const int L = c->L();
-  const bool mixed = c->opts.precision == SEMMG_MIXED;
+  // the star kernel in the V-cycle precision; the Schur kernel in FP64 arithmetic
+  // except for the all-FP32 cycle (whose outer residual is FP64 too).  The FP64
+  // timing input is Uh, which holds at least as many values as any level.
+  const bool c32 = cycle32(c);
+  const bool all32 = c->opts.precision == SEMMG_MIXED_FP32;
   for (int l = 0; l <= L; ++l) {
-    if (mixed) {
-      const float* in = (const float*)c->dl[l].Fw;
-      if (l >= 1) tune_one<float>(c, l, 0, c->dl[l].star32, in, st);
-      if (c->geo[l].m > 0) tune_one<float>(c, l, 1, c->dl[l].schur32, in, st);
-    } else {
-      const double* in = (const double*)c->dl[l].Fw;
-      if (l >= 1) tune_one<double>(c, l, 0, c->dl[l].star64, in, st);
-      if (c->geo[l].m > 0) tune_one<double>(c, l, 1, c->dl[l].schur64, in, st);
+    if (l >= 1) {
+      if (c32)
+        tune_one<float>(c, l, 0, c->dl[l].star32, (const float*)c->dl[l].Fw, st);
+      else
+        tune_one<double>(c, l, 0, c->dl[l].star64, (const double*)c->dl[l].Fw, st);
     }
+    if (c->geo[l].m == 0) continue;
+    if (all32) tune_one<float>(c, l, 1, c->dl[l].schur32, (const float*)c->dl[l].Fw, st);
+    if (!all32 || l == L) tune_one<double>(c, l, 1, c->dl[l].schur64, c->Uh, st);
   }
-  if (mixed && c->geo[L].m > 0) tune_one<double>(c, L, 1, c->dl[L].schur64, c->Uh, st);
   c->timing = saved;
   if (cudaStreamSynchronize(st) != cudaSuccess) return check_cuda(c, "autotune");
   return check_cuda(c, "autotune");
 }
 
+extern "C" int semmg_set_launch(semmg_ctx* c, int level, int kernel, int dtype, int smem_cap, int block,
+                                int max_regs) {
+  if (!valid_level(c, level) || (kernel != 0 && kernel != 1) || (dtype != SEMMG_F64 && dtype != SEMMG_F32))
+    return SEMMG_ERR_INVALID_ARG;
+  if (smem_cap < 0 || smem_cap > 200 * 1024 || (block != 256 && block != 512) || (max_regs != 64 && max_regs != 128))
+    return SEMMG_ERR_INVALID_ARG;
+  if (kernel == 0 && level < 1) return SEMMG_ERR_INVALID_ARG;
+  if (kernel == 1 && c->geo[level].m == 0) return SEMMG_ERR_INVALID_ARG;
+  const Geo& G = c->geo[level];
+  const int wide = max_regs == 128 ? 1 : 0;
+  DevLevel& D = c->dl[level];
+  LaunchCfg cf;
+  size_t es;
+  if (dtype == SEMMG_F64) {
+    es = sizeof(double);
+    cf = kernel == 0 ? plan_star<double>(G, c->nsm, smem_cap, block, wide)
+                     : plan_elem_schur<double>(G, c->nsm, smem_cap, block, wide);
+  } else {
+    es = sizeof(float);
+    cf = kernel == 0 ? plan_star<float>(G, c->nsm, smem_cap, block, wide)
+                     : plan_elem_schur<float>(G, c->nsm, smem_cap, block, wide);
+  }
+  if (!cf.ok || cf.ws_elems() * es > c->ws_bytes)
+    return fail(c, SEMMG_ERR_UNSUPPORTED, "set_launch: shape does not fit the work memory of the context");
+  LaunchCfg& slot = kernel == 0 ? (dtype == SEMMG_F64 ? D.star64 : D.star32) : (dtype == SEMMG_F64 ? D.schur64 : D.schur32);
+  slot = cf;
+  return SEMMG_OK;
+}
+
 extern "C" int semmg_get_launch(const semmg_ctx* c, int level, int kernel, int dtype, int* block, int* smem,
-                                int* grid) {
-  if (!valid_level(c, level) || !block || !smem || !grid || (kernel != 0 && kernel != 1)) return SEMMG_ERR_INVALID_ARG;
+                                int* grid, int* max_regs) {
+  if (!valid_level(c, level) || !block || !smem || !grid || !max_regs || (kernel != 0 && kernel != 1))
+    return SEMMG_ERR_INVALID_ARG;
   const DevLevel& D = c->dl[level];
   const LaunchCfg* cf;
   if (kernel == 0) cf = dtype == SEMMG_F32 ? &D.star32 : &D.star64;
@@ -1204,5 +1339,6 @@ extern "C" int semmg_get_launch(const semmg_ctx* c, int level, int kernel, int d
   *block = cf->block;
   *smem = (int)cf->smem;
   *grid = cf->grid;
+  *max_regs = cf->wide ? 128 : 64;
   return SEMMG_OK;
 }

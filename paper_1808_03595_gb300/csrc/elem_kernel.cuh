@@ -21,6 +21,7 @@
 // and a_p[k] = +a_0[k] (even k) / -a_0[k] (odd k), so the two faces of one
 // axis enter as their sum (even k_d) and difference (odd k_d).  1/D comes from
 // a table per distinct width triple when one was built.
+#pragma once
 #include "semmg_internal.h"
 
 namespace semmg {
@@ -37,13 +38,16 @@ struct ElemScal {
 template <typename T>
 __device__ __forceinline__ ElemScal<T> elem_scalars(const Tabs<T>& t, int a1, int a2, int a3) {
   ElemScal<T> s;
-  const double h1 = (double)t.h[0][a1], h2 = (double)t.h[1][a2], h3 = (double)t.h[2][a3];
-  s.sf[0] = (T)(0.5 * sqrt(h2 * h3) * pow(2.0 / h1, 1.5));
-  s.sf[1] = (T)(0.5 * sqrt(h1 * h3) * pow(2.0 / h2, 1.5));
-  s.sf[2] = (T)(0.5 * sqrt(h1 * h2) * pow(2.0 / h3, 1.5));
-  s.e[0] = (T)(4.0 / (h1 * h1));
-  s.e[1] = (T)(4.0 / (h2 * h2));
-  s.e[2] = (T)(4.0 / (h3 * h3));
+  // c_f = sqrt(h_a h_b) / 2 and alpha_d = (2/h_d)^(3/2) from the per-width tables
+  const T* x1 = t.hx[0] + 6 * a1;
+  const T* x2 = t.hx[1] + 6 * a2;
+  const T* x3 = t.hx[2] + 6 * a3;
+  s.sf[0] = (T)0.5 * x2[3] * x3[3] * x1[4];
+  s.sf[1] = (T)0.5 * x1[3] * x3[3] * x2[4];
+  s.sf[2] = (T)0.5 * x1[3] * x2[3] * x3[4];
+  s.e[0] = x1[2];
+  s.e[1] = x2[2];
+  s.e[2] = x3[2];
   s.cls = ((int64_t)t.hcls[0][a1] * t.nhcls[1] + t.hcls[1][a2]) * t.nhcls[2] + t.hcls[2][a3];
   return s;
 }
@@ -348,9 +352,11 @@ __device__ __forceinline__ void elem_coords(const Geo& G, int64_t e, int* a1, in
 // y_e = H_BI H_II^{-1} H_IB u on the six faces of every element -> Z[e][f][.]
 // Work regions: 0 tables (Sh, a0, Lam), 1 X (6 m^2), 2 Tt (6 m^2), 3 W (m^3).
 // PC > 0 compiles the kernel for degree PC (constant extents); PC = 0 reads it from G.
-template <typename T, int PC>
-__global__ void __launch_bounds__(512) k_elem_schur(Geo G, Tabs<T> t, const T* __restrict__ u, T* __restrict__ Z,
-                                                     T* ws, WsPlan wp) {
+// TI is the element type of u (float u with double T: FP64 arithmetic on an
+// FP32 vector, the level residuals of the mixed form).
+template <typename T, int PC, int NB, typename TI = T>
+__global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const TI* __restrict__ u,
+                                                         T* __restrict__ Z, T* ws, WsPlan wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = PC ? PC - 1 : G.m, mm = m * m;
   const int64_t n3 = (int64_t)mm * m;
@@ -371,7 +377,7 @@ __global__ void __launch_bounds__(512) k_elem_schur(Geo G, Tabs<T> t, const T* _
     __syncthreads();
     for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
       const int f = idx / mm;
-      X[idx] = u[elem_face_base(G, a1, a2, a3, f) + (idx - f * mm)];
+      X[idx] = (T)u[elem_face_base(G, a1, a2, a3, f) + (idx - f * mm)];
     }
     __syncthreads();
     face_pairs(mm, X);
@@ -449,7 +455,7 @@ __device__ __forceinline__ int64_t interior_node(const Geo& G, int a1, int a2, i
 
 // Z[e][f] = (H_BI H_II^{-1} F_I) on the faces, F_I = (M f)_I element-local.
 template <int PC>
-__global__ void __launch_bounds__(256) k_elem_condense(Geo G, Tabs<double> t, const double* __restrict__ f,
+__global__ void __launch_bounds__(512, 1) k_elem_condense(Geo G, Tabs<double> t, const double* __restrict__ f,
                                                         double* __restrict__ Z, double* ws, WsPlan wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = PC ? PC - 1 : G.m, mm = m * m, mmm = mm * m;
@@ -462,9 +468,11 @@ __global__ void __launch_bounds__(256) k_elem_condense(Geo G, Tabs<double> t, co
     int a1, a2, a3;
     elem_coords(G, e, &a1, &a2, &a3);
     const ElemScal<double> sc = elem_scalars(t, a1, a2, a3);
-    const double h1 = t.h[0][a1], h2 = t.h[1][a2], h3 = t.h[2][a3];
-    const double vol = h1 * h2 * h3 / 8.0;
-    const double sig = sqrt(8.0 / (h1 * h2 * h3));
+    const double* x1 = t.hx[0] + 6 * a1;
+    const double* x2 = t.hx[1] + 6 * a2;
+    const double* x3 = t.hx[2] + 6 * a3;
+    const double vol = 0.125 * x1[0] * x2[0] * x3[0];  // h1 h2 h3 / 8
+    const double sig = x1[5] * x2[5] * x3[5];          // sqrt(8 / (h1 h2 h3))
     __syncthreads();
     for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
       const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / mm;
@@ -486,7 +494,7 @@ __global__ void __launch_bounds__(256) k_elem_condense(Geo G, Tabs<double> t, co
 
 // u_I = H_II^{-1} (F_I - H_IB uhat) written into the nodal array.
 template <int PC>
-__global__ void __launch_bounds__(256) k_elem_recover(Geo G, Tabs<double> t, const double* __restrict__ f,
+__global__ void __launch_bounds__(512, 1) k_elem_recover(Geo G, Tabs<double> t, const double* __restrict__ f,
                                                        const double* __restrict__ uh, double* __restrict__ un,
                                                        double* ws, WsPlan wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -500,9 +508,11 @@ __global__ void __launch_bounds__(256) k_elem_recover(Geo G, Tabs<double> t, con
     int a1, a2, a3;
     elem_coords(G, e, &a1, &a2, &a3);
     const ElemScal<double> sc = elem_scalars(t, a1, a2, a3);
-    const double h1 = t.h[0][a1], h2 = t.h[1][a2], h3 = t.h[2][a3];
-    const double vol = h1 * h2 * h3 / 8.0;
-    const double sig = sqrt(8.0 / (h1 * h2 * h3));
+    const double* x1 = t.hx[0] + 6 * a1;
+    const double* x2 = t.hx[1] + 6 * a2;
+    const double* x3 = t.hx[2] + 6 * a3;
+    const double vol = 0.125 * x1[0] * x2[0] * x3[0];  // h1 h2 h3 / 8
+    const double sig = x1[5] * x2[5] * x3[5];          // sqrt(8 / (h1 h2 h3))
     __syncthreads();
     for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
       const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / mm;
@@ -535,7 +545,7 @@ constexpr size_t kSchurSmemCap = 200 * 1024;
 }  // namespace
 
 template <typename T>
-LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap, int block) {
+LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap, int block, int wide) {
   LaunchCfg c;
   if (cap == 0) cap = kSchurSmemCap;
   const size_t m = G.m, mm = m * m;
@@ -543,88 +553,56 @@ LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap, int block) {
   c.ws = plan_regions(sizes, 4, sizeof(T), cap, &c.smem);
   c.ok = plan_ok(c.ws, sizes, 4, sizeof(T), c.smem);
   c.block = block ? block : (c.smem > 100 * 1024 ? 512 : 256);
-  int bps = blocks_per_sm(c.smem);
-  if (bps * c.block > 2048) bps = 2048 / c.block;
-  const int64_t grid = (int64_t)nsm * bps;
+  const int64_t grid = (int64_t)nsm * resident_blocks(c, wide);
   c.grid = (int)(G.nelem < grid ? G.nelem : grid);
   if (c.grid < 1) c.grid = 1;
   return c;
+}
+
+template <typename T, int NB, typename TI>
+void launch_elem_schur_nb(const Geo& G, const Tabs<T>& t, const TI* u, T* Z, T* ws, const LaunchCfg& c,
+                          cudaStream_t st) {
+  switch (G.p) {
+    case 2: k_elem_schur<T, 2, NB, TI><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 4: k_elem_schur<T, 4, NB, TI><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 8: k_elem_schur<T, 8, NB, TI><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 16: k_elem_schur<T, 16, NB, TI><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 32: k_elem_schur<T, 32, NB, TI><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    default: k_elem_schur<T, 0, NB, TI><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+  }
+}
+
+template <typename T, typename TI>
+void launch_elem_schur_any(const Geo& G, const Tabs<T>& t, const TI* u, T* Z, T* ws, const LaunchCfg& c,
+                           cudaStream_t st) {
+  if (G.m == 0 || G.nelem == 0 || !c.ok) return;
+  if (c.wide)
+    launch_elem_schur_nb<T, 1, TI>(G, t, u, Z, ws, c, st);
+  else
+    launch_elem_schur_nb<T, 2, TI>(G, t, u, Z, ws, c, st);
 }
 
 template <typename T>
 void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, const LaunchCfg& c,
                        cudaStream_t st) {
-  if (G.m == 0 || G.nelem == 0 || !c.ok) return;
-  switch (G.p) {
-    case 2: k_elem_schur<T, 2><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    case 4: k_elem_schur<T, 4><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    case 8: k_elem_schur<T, 8><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    case 16: k_elem_schur<T, 16><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    case 32: k_elem_schur<T, 32><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    default: k_elem_schur<T, 0><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-  }
+  launch_elem_schur_any<T, T>(G, t, u, Z, ws, c, st);
 }
 
-LaunchCfg plan_elem_fdm(const Geo& G, int nsm) {
-  LaunchCfg c;
-  const size_t m = G.m, mm = m * m;
-  const size_t sizes[4] = {2 * mm + 2 * m, 6 * mm, 6 * mm, 2 * mm * m};
-  c.ws = plan_regions(sizes, 4, sizeof(double), kSmemCap, &c.smem);
-  c.ok = plan_ok(c.ws, sizes, 4, sizeof(double), c.smem);
-  const int64_t grid = (int64_t)nsm * blocks_per_sm(c.smem);
-  c.grid = (int)(G.nelem < grid ? G.nelem : grid);
-  if (c.grid < 1) c.grid = 1;
-  return c;
-}
-
-void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f, double* Z, double* ws,
-                          const LaunchCfg& c, cudaStream_t st) {
-  if (G.m == 0 || G.nelem == 0 || !c.ok) return;
-  switch (G.p) {
-    case 16: k_elem_condense<16><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, ws, c.ws); break;
-    case 32: k_elem_condense<32><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, ws, c.ws); break;
-    default: k_elem_condense<0><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, ws, c.ws); break;
-  }
-}
-
-void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f, const double* uh, double* un,
-                         double* ws, const LaunchCfg& c, cudaStream_t st) {
-  if (G.m == 0 || G.nelem == 0 || !c.ok) return;
-  switch (G.p) {
-    case 16: k_elem_recover<16><<<c.grid, c.block, c.smem, st>>>(G, t, f, uh, un, ws, c.ws); break;
-    case 32: k_elem_recover<32><<<c.grid, c.block, c.smem, st>>>(G, t, f, uh, un, ws, c.ws); break;
-    default: k_elem_recover<0><<<c.grid, c.block, c.smem, st>>>(G, t, f, uh, un, ws, c.ws); break;
-  }
-}
-
-template LaunchCfg plan_elem_schur<double>(const Geo&, int, size_t, int);
-template LaunchCfg plan_elem_schur<float>(const Geo&, int, size_t, int);
-template void launch_elem_schur<double>(const Geo&, const Tabs<double>&, const double*, double*, double*,
-                                        const LaunchCfg&, cudaStream_t);
-template void launch_elem_schur<float>(const Geo&, const Tabs<float>&, const float*, float*, float*,
-                                       const LaunchCfg&, cudaStream_t);
-
-template <typename T>
-static int schur_attrs() {
+template <typename T, int NB, typename TI>
+static int schur_attrs_nb() {
   int bad = 0;
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 0, NB, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 2, NB, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 4, NB, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 8, NB, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 16, NB, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 32, NB, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return bad;
 }
 
-int set_elem_smem_limits() {
-  int bad = schur_attrs<double>() | schur_attrs<float>();
-  bad |= cudaFuncSetAttribute(k_elem_condense<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_condense<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_condense<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_recover<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_recover<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_recover<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  return bad;
+template <typename T, typename TI = T>
+static int schur_attrs() {
+  return schur_attrs_nb<T, 1, TI>() | schur_attrs_nb<T, 2, TI>();
 }
 
 }  // namespace semmg

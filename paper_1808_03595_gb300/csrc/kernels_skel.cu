@@ -36,8 +36,8 @@ __device__ __forceinline__ T mass1d(const Geo& G, const Tabs<T>& t, int d, int g
 // Line sum (Lg_d u)(g) over the skeleton nodes of the line through node s
 // along axis d.  `other` tells whether the node has a vertex-plane coordinate
 // on another axis, in which case every node of the line is a skeleton node.
-template <typename T>
-__device__ T line_sum(const Geo& G, const Tabs<T>& t, const T* __restrict__ u, int64_t s, int type, const int* g,
+template <typename T, typename TI>
+__device__ T line_sum(const Geo& G, const Tabs<T>& t, const TI* __restrict__ u, int64_t s, int type, const int* g,
                       int d, bool other) {
   const int p = G.p;
   const int a = divp(G, g[d]), q = g[d] - a * p;
@@ -46,7 +46,7 @@ __device__ T line_sum(const Geo& G, const Tabs<T>& t, const T* __restrict__ u, i
   const int P1 = p + 1;
   if (q) {
     // inside element a along d: endpoints are skeleton, the run is this entity
-    const T k = (T)2 / t.h[d][a];
+    const T k = t.hx[d][6 * a + 1];  // 2 / h
     const T* row = Ls + q * P1;
     T acc = 0;
     gg[d] = a * p;
@@ -54,12 +54,12 @@ __device__ T line_sum(const Geo& G, const Tabs<T>& t, const T* __restrict__ u, i
     gg[d] = a * p + p;
     acc += row[p] * u[skel_index(G, gg[0], gg[1], gg[2])];
     const int st = run_stride(G, type, d);
-    const T* ur = u + s - (int64_t)(q - 1) * st;  // slot of local index 1
+    const TI* ur = u + s - (int64_t)(q - 1) * st;  // slot of local index 1
     for (int j = 1; j < p; ++j) acc += row[j] * ur[(int64_t)(j - 1) * st];
     return k * acc;
   }
   // on vertex plane c = a (interior plane: 1 <= c <= n_d - 1)
-  const T kL = (T)2 / t.h[d][a - 1], kR = (T)2 / t.h[d][a];
+  const T kL = t.hx[d][6 * (a - 1) + 1], kR = t.hx[d][6 * a + 1];  // 2 / h on either side
   T acc = (kL * Ls[p * P1 + p] + kR * Ls[0]) * u[s];
   gg[d] = (a - 1) * p;
   acc += kL * Ls[p * P1 + 0] * u[skel_index(G, gg[0], gg[1], gg[2])];
@@ -101,11 +101,12 @@ __device__ __forceinline__ T face_z(const Geo& G, const T* __restrict__ Z, int t
   return Z[(em * 6 + 2 * d + 1) * mm + loc] + Z[(ep * 6 + 2 * d) * mm + loc];
 }
 
-// mode 0: out = F - Hhat u;  mode 1: out = Hhat u.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_assemble(Geo G, Tabs<T> t, const T* __restrict__ F,
-                                                        const T* __restrict__ u, const T* __restrict__ Z,
-                                                        T* __restrict__ out, int mode) {
+// mode 0: out = F - Hhat u;  mode 1: out = Hhat u.  Arithmetic in T, vectors
+// F, u, out of type TI (float TI with double T: the mixed form's level residuals).
+template <typename T, typename TI = T>
+__global__ void __launch_bounds__(kThreads) k_assemble(Geo G, Tabs<T> t, const TI* __restrict__ F,
+                                                        const TI* __restrict__ u, const T* __restrict__ Z,
+                                                        TI* __restrict__ out, int mode) {
   const int nd[3] = {G.n1, G.n2, G.n3};
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < G.size; s += (int64_t)gridDim.x * blockDim.x) {
     int g[3];
@@ -123,9 +124,9 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Geo G, Tabs<T> t, const T
       const bool other = on[(d + 1) % 3] || on[(d + 2) % 3];
       L[d] = line_sum(G, t, u, s, type, g, d, other);
     }
-    T Hu = (T)G.lam * M[0] * M[1] * M[2] * u[s] + M[1] * M[2] * L[0] + M[0] * M[2] * L[1] + M[0] * M[1] * L[2];
+    T Hu = (T)G.lam * M[0] * M[1] * M[2] * (T)u[s] + M[1] * M[2] * L[0] + M[0] * M[2] * L[1] + M[0] * M[1] * L[2];
     if (type <= ENT_F3 && Z) Hu -= face_z(G, Z, type, g);
-    out[s] = mode == 0 ? F[s] - Hu : Hu;
+    out[s] = (TI)(mode == 0 ? (T)F[s] - Hu : Hu);
   }
 }
 
@@ -261,6 +262,11 @@ template <typename T>
 void launch_assemble(const Geo& G, const Tabs<T>& t, const T* F, const T* u, const T* Z, T* out, int mode,
                      cudaStream_t st) {
   k_assemble<T><<<grid_for(G.size), kThreads, 0, st>>>(G, t, F, u, G.m > 0 ? Z : nullptr, out, mode);
+}
+
+void launch_assemble_mixed(const Geo& G, const Tabs<double>& t, const float* F, const float* u, const double* Z,
+                           float* out, int mode, cudaStream_t st) {
+  k_assemble<double, float><<<grid_for(G.size), kThreads, 0, st>>>(G, t, F, u, G.m > 0 ? Z : nullptr, out, mode);
 }
 
 void launch_assemble_rhs(const Geo& G, const Tabs<double>& t, const double* f, const double* Z, double* Fh,

@@ -198,6 +198,9 @@ struct Tabs {
   int nhcls[3];        // width classes per axis
   const T* Relem;      // per width-class triple: m^3 values 1/(lam + sum 4/h^2 Lam), or null
   const T* h[3];   // element widths per axis
+  // per axis, 6 derived values per element width h (computed on the host in
+  // FP64): h, 2/h, 4/h^2, sqrt(h), (2/h)^(3/2), sqrt(2/h)
+  const T* hx[3];
   const T* starS[3];    // per axis: nv_d blocks of nS x nS, S[j][k], row j <-> offset j-m
   const T* starLam[3];  // per axis: nv_d x nS
   const unsigned char* act[3];  // per axis: nv_d x nS active flags
@@ -235,6 +238,9 @@ struct LaunchCfg {
   size_t smem = 0;               // dynamic shared memory bytes
   WsPlan ws{};
   bool ok = false;               // plan_ok() passed
+  // register budget of the kernel build: 0 = at most 64 registers per thread
+  // (1024 resident threads per SM), 1 = at most 128 (512 resident threads)
+  int wide = 0;
   size_t ws_elems() const { return (size_t)ws.gstride * (size_t)grid; }
 };
 
@@ -291,9 +297,26 @@ inline int blocks_per_sm(size_t smem) {
   return b;
 }
 
-template <typename T> LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap = 0, int block = 0);
+// Resident CTAs per SM of c (block and smem set) under the shared-memory,
+// thread and register-file limits; sets c.wide (the register budget) from
+// `wide` (0 / 1), or, when wide < 0, to 1 exactly when the wider budget
+// costs no resident threads.
+inline int resident_blocks(LaunchCfg& c, int wide) {
+  int bps = blocks_per_sm(c.smem);
+  if (bps * c.block > 2048) bps = 2048 / c.block;
+  c.wide = wide >= 0 ? wide : (bps * c.block <= 512 ? 1 : 0);
+  const int reg_threads = c.wide ? 512 : 1024;  // 64K registers / (128 or 64) per thread
+  if (bps * c.block > reg_threads) bps = reg_threads / c.block;
+  return bps < 1 ? 1 : bps;
+}
+
+template <typename T> LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap = 0, int block = 0,
+                                                int wide = -1);
 template <typename T> void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws,
                                              const LaunchCfg& c, cudaStream_t st);
+// FP64 arithmetic on an FP32 u (Z in FP64), with a plan from plan_elem_schur<double>
+void launch_elem_schur_mixed(const Geo& G, const Tabs<double>& t, const float* u, double* Z, double* ws,
+                             const LaunchCfg& c, cudaStream_t st);
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm);
 void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f_nodal, double* Z,
                           double* ws, const LaunchCfg& c, cudaStream_t st);
@@ -301,11 +324,14 @@ void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f_no
                          double* u_nodal, double* ws, const LaunchCfg& c, cudaStream_t st);
 template <typename T> void launch_assemble(const Geo& G, const Tabs<T>& t, const T* F, const T* u,
                                            const T* Z, T* out, int mode, cudaStream_t st);
+// out = F - Hhat u (mode 0) / Hhat u (mode 1) in FP64 arithmetic on FP32 F, u, out
+void launch_assemble_mixed(const Geo& G, const Tabs<double>& t, const float* F, const float* u, const double* Z,
+                           float* out, int mode, cudaStream_t st);
 void launch_assemble_rhs(const Geo& G, const Tabs<double>& t, const double* f_nodal, const double* Z,
                          double* Fhat, cudaStream_t st);
 void launch_pack(const Geo& G, const double* nodal, double* hat, cudaStream_t st);
 void launch_unpack(const Geo& G, const double* hat, double* nodal, cudaStream_t st);
-template <typename T> LaunchCfg plan_star(const Geo& G, int nsm, size_t cap = 0, int block = 0);
+template <typename T> LaunchCfg plan_star(const Geo& G, int nsm, size_t cap = 0, int block = 0, int wide = -1);
 template <typename T> void launch_star(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws,
                                        const LaunchCfg& c, int* counter, cudaStream_t st);
 template <typename T> void launch_star_gather(const Geo& G, const T* Ob, T* du, int accumulate,
@@ -321,6 +347,22 @@ template <typename T> void launch_norm2(const T* x, int64_t n, double* partial, 
 template <typename TY, typename TX> void launch_axpy(TY* y, const TX* x, double a, int64_t n,
                                                      cudaStream_t st);
 template <typename TO, typename TI> void launch_copy(TO* y, const TI* x, int64_t n, cudaStream_t st);
+
+// Device-resident scalars of Algorithm 5.
+struct KrylovScal {
+  double gamma, gamma0, delta, beta, alpha, qp;
+};
+void launch_krylov_init(KrylovScal* k, cudaStream_t st);
+// gamma = z.r, gamma0 = z.s, beta = (gamma - gamma0) / delta, delta = gamma; p = beta p + z
+template <typename T> void launch_krylov_beta_dir(const T* z, const double* r, const double* s, double* p,
+                                                  int64_t n, double* part, int npart, KrylovScal* k,
+                                                  cudaStream_t st);
+// alpha = gamma / (q.p)
+void launch_krylov_alpha(const double* q, const double* p, int64_t n, double* part, int npart, KrylovScal* k,
+                         cudaStream_t st);
+// s = r; u += alpha p; r -= alpha q; *rnorm2 = ||r||^2
+void launch_krylov_update(double* u, double* r, double* s, const double* p, const double* q, int64_t n,
+                          double* part, int npart, const KrylovScal* k, double* rnorm2, cudaStream_t st);
 
 int set_kernel_smem_limits();
 int smooth_with_scratch(semmg_ctx* c, int level, int dtype, const void* r, void* du, void* scratch,

@@ -1,4 +1,6 @@
 // Star smoother: Algorithm 2 around Algorithm 1 (Sec. 3.2), one CTA per star.
+// Kernel templates; kernels_star_f64.cu and kernels_star_f32.cu instantiate
+// them for one element type each (two translation units compile in parallel).
 //
 // The star of vertex c is every skeleton node strictly inside its 2x2x2
 // element block; after condensation it is three planes of n_S x n_S points
@@ -16,6 +18,7 @@
 // Dirichlet boundary (Sec. 3.3).  The plane outputs are weighted with the
 // degree-7 weights W_i (Sec. 3.2) and the multiplicity, and written to a
 // per-star buffer; k_star_gather sums them per skeleton node.
+#pragma once
 #include "semmg_internal.h"
 
 namespace semmg {
@@ -250,8 +253,8 @@ __device__ __forceinline__ T unfold_value(int nS, int m, const int* sym, int alo
 
 // PC > 0 compiles the kernel for degree PC (constant extents, unrolled loops);
 // PC = 0 takes the degree from G.
-template <typename T, int PC>
-__global__ void __launch_bounds__(512) k_star(Geo G, Tabs<T> t, const T* __restrict__ r, T* __restrict__ Ob,
+template <typename T, int PC, int NB>
+__global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __restrict__ r, T* __restrict__ Ob,
                                                T* ws, WsPlan wp, int S_copy, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_next;
@@ -431,7 +434,7 @@ constexpr size_t kStarSmemCap = 200 * 1024;
 }  // namespace
 
 template <typename T>
-LaunchCfg plan_star(const Geo& G, int nsm, size_t cap, int block) {
+LaunchCfg plan_star(const Geo& G, int nsm, size_t cap, int block, int wide) {
   LaunchCfg c;
   if (cap == 0) cap = kStarSmemCap;
   const size_t nS = G.nS, n2 = nS * nS;
@@ -441,49 +444,53 @@ LaunchCfg plan_star(const Geo& G, int nsm, size_t cap, int block) {
   c.ws = plan_regions(sizes, 5, sizeof(T), cap, &c.smem, order);
   c.ok = plan_ok(c.ws, sizes, 5, sizeof(T), c.smem);
   c.block = block ? block : (c.smem > 100 * 1024 ? 512 : 256);  // a block that owns the SM brings more warps
-  int bps = blocks_per_sm(c.smem);
-  if (bps * c.block > 2048) bps = 2048 / c.block;
+  const int bps = resident_blocks(c, wide);
   const int64_t grid = (int64_t)nsm * bps;
   c.grid = (int)(G.nstar < grid ? G.nstar : grid);
   if (c.grid < 1) c.grid = 1;
   return c;
 }
 
+template <typename T, int NB>
+void launch_star_nb(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws, const LaunchCfg& c, int* counter,
+                    cudaStream_t st) {
+  // copy the S tables into the CTA's work memory only when that is shared memory
+  const int S_copy = c.ws.in_smem[0];
+  switch (G.p) {
+    case 2: k_star<T, 2, NB><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
+    case 4: k_star<T, 4, NB><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
+    case 8: k_star<T, 8, NB><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
+    case 16: k_star<T, 16, NB><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
+    case 32: k_star<T, 32, NB><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
+    default: k_star<T, 0, NB><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
+  }
+}
+
 template <typename T>
 void launch_star(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws, const LaunchCfg& c, int* counter,
                  cudaStream_t st) {
   if (G.nstar == 0 || !c.ok) return;
-  // copy the S tables into the CTA's work memory only when that is shared memory
-  const int S_copy = c.ws.in_smem[0];
-  switch (G.p) {
-    case 2: k_star<T, 2><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
-    case 4: k_star<T, 4><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
-    case 8: k_star<T, 8><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
-    case 16: k_star<T, 16><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
-    case 32: k_star<T, 32><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
-    default: k_star<T, 0><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, ws, c.ws, S_copy, counter); break;
-  }
+  if (c.wide)
+    launch_star_nb<T, 1>(G, t, r, Ob, ws, c, counter, st);
+  else
+    launch_star_nb<T, 2>(G, t, r, Ob, ws, c, counter, st);
 }
 
-template LaunchCfg plan_star<double>(const Geo&, int, size_t, int);
-template LaunchCfg plan_star<float>(const Geo&, int, size_t, int);
-template void launch_star<double>(const Geo&, const Tabs<double>&, const double*, double*, double*,
-                                  const LaunchCfg&, int*, cudaStream_t);
-template void launch_star<float>(const Geo&, const Tabs<float>&, const float*, float*, float*, const LaunchCfg&, int*,
-                                 cudaStream_t);
-
-template <typename T>
-static int star_attrs() {
+template <typename T, int NB>
+static int star_attrs_nb() {
   int bad = 0;
-  bad |= cudaFuncSetAttribute(k_star<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_star<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_star<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_star<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_star<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_star<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_star<T, 0, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_star<T, 2, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_star<T, 4, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_star<T, 8, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_star<T, 16, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_star<T, 32, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return bad;
 }
 
-int set_star_smem_limits() { return star_attrs<double>() | star_attrs<float>(); }
+template <typename T>
+static int star_attrs() {
+  return star_attrs_nb<T, 1>() | star_attrs_nb<T, 2>();
+}
 
 }  // namespace semmg

@@ -29,7 +29,8 @@ def _stream(stream=None):
 class Context:
     """A semmg context: mesh (per-axis element widths), degree p, lambda >= 0, options."""
 
-    def __init__(self, h, p, lam, p0=2, nu_pre=1, nu_post=1, precision="fp64", max_iter=50, stream=None):
+    def __init__(self, h, p, lam, p0=2, nu_pre=1, nu_post=1, precision="fp64", max_iter=50, solver="mg",
+                 nu_vary=False, stream=None):
         self._lib = L.load()
         self._ctx = ctypes.c_void_p()
         self.h = [np.ascontiguousarray(np.asarray(hd, dtype=np.float64)) for hd in h]
@@ -45,9 +46,12 @@ class Context:
         opts.p0 = p0
         opts.nu_pre = nu_pre
         opts.nu_post = nu_post
-        opts.precision = {"fp64": L.SEMMG_FP64, "mixed": L.SEMMG_MIXED}[precision]
+        opts.precision = {"fp64": L.SEMMG_FP64, "mixed": L.SEMMG_MIXED, "mixed_fp32": L.SEMMG_MIXED_FP32}[precision]
         opts.max_iter = max_iter
+        opts.solver = {"mg": L.SEMMG_SOLVER_MG, "kmg": L.SEMMG_SOLVER_KMG}[solver]
+        opts.nu_vary = 1 if nu_vary else 0
         self.precision = precision
+        self.solver = solver
         rc = self._lib.semmg_setup(ctypes.byref(mesh), self.p, self.lam, ctypes.byref(opts), _stream(stream),
                                    ctypes.byref(self._ctx))
         if rc != 0:
@@ -192,12 +196,18 @@ class Context:
         self._check(self._lib.semmg_autotune(self._ctx, _stream()))
 
     def launch_shape(self, level, kernel, dtype=torch.float64):
-        """(block, shared-memory bytes, grid) of kernel 'star' or 'schur' at a level."""
-        b, s, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        """(block, shared-memory bytes, grid, registers per thread) of kernel 'star' or 'schur' at a level."""
+        b, s, g, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._check(self._lib.semmg_get_launch(self._ctx, level, {"star": 0, "schur": 1}[kernel],
                                                L.SEMMG_F32 if dtype == torch.float32 else L.SEMMG_F64,
-                                               ctypes.byref(b), ctypes.byref(s), ctypes.byref(g)))
-        return b.value, s.value, g.value
+                                               ctypes.byref(b), ctypes.byref(s), ctypes.byref(g), ctypes.byref(r)))
+        return b.value, s.value, g.value, r.value
+
+    def set_launch(self, level, kernel, dtype, smem_cap, block, max_regs):
+        """Pin the launch shape of kernel 'star' or 'schur' at a level (semmg_set_launch)."""
+        self._check(self._lib.semmg_set_launch(self._ctx, level, {"star": 0, "schur": 1}[kernel],
+                                               L.SEMMG_F32 if dtype == torch.float32 else L.SEMMG_F64,
+                                               int(smem_cap), int(block), int(max_regs)))
 
     # ------------------------------------------------------------ timing
     def set_timing(self, enable=True):

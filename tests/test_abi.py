@@ -67,6 +67,13 @@ def test_setup_rejects_bad_arguments_without_touching_the_gpu(lib):
     opts = L.semmg_opts()
     lib.semmg_default_opts(ctypes.byref(opts))
     assert (opts.p0, opts.nu_pre, opts.nu_post, opts.precision, opts.max_iter) == (2, 1, 1, 0, 50)
+    assert (opts.solver, opts.nu_vary) == (L.SEMMG_SOLVER_MG, 0)
+    opts.solver = 7
+    assert lib.semmg_setup(ctypes.byref(mesh), 4, 1.0, ctypes.byref(opts), None, ctypes.byref(ctx)) == -1
+    opts.solver = L.SEMMG_SOLVER_KMG
+    opts.nu_vary = 2
+    assert lib.semmg_setup(ctypes.byref(mesh), 4, 1.0, ctypes.byref(opts), None, ctypes.byref(ctx)) == -1
+    opts.nu_vary = 0
     opts.p0 = 8
     assert lib.semmg_setup(ctypes.byref(mesh), 4, 1.0, ctypes.byref(opts), None, ctypes.byref(ctx)) == -2
     hbad = np.array([0.5, -0.5])

@@ -15,7 +15,7 @@ def _built():
     build.build()
 
 
-@pytest.mark.parametrize("p,precision", [(8, "fp64"), (16, "mixed"), (13, "mixed")])
+@pytest.mark.parametrize("p,precision", [(8, "fp64"), (16, "mixed"), (13, "mixed_fp32")])
 def test_autotune_is_bitwise_neutral(p, precision):
     from paper_1808_03595_gb300 import Context
     h = workloads.uniform_widths(4)
@@ -28,11 +28,12 @@ def test_autotune_is_bitwise_neutral(p, precision):
             if tune:
                 c.autotune()
                 for lv in range(1, c.nlevels):
-                    dt = torch.float32 if precision == "mixed" else torch.float64
-                    b, s, g = c.launch_shape(lv, "star", dt)
-                    assert b in (256, 512) and g >= 1 and 0 <= s <= 200 * 1024
+                    dt = torch.float64 if precision == "fp64" else torch.float32
+                    for kern in ("star", "schur"):
+                        blk, smem, grid, regs = c.launch_shape(lv, kern, dt)
+                        assert blk in (256, 512) and grid >= 1 and 0 <= smem <= 200 * 1024 and regs in (64, 128)
             rh = c.pack(c.L, torch.as_tensor(r, device="cuda"))
-            dt = torch.float32 if precision == "mixed" else torch.float64
+            dt = torch.float64 if precision == "fp64" else torch.float32
             du = c.smooth(c.L, rh.to(dt)).double().cpu().numpy()
             y = c.apply_condensed(c.L, rh).cpu().numpy()
             u, info = c.solve(torch.as_tensor(f, device="cuda"))
@@ -41,3 +42,44 @@ def test_autotune_is_bitwise_neutral(p, precision):
     assert np.array_equal(d0, d1)
     assert np.array_equal(y0, y1)
     assert np.array_equal(u0, u1) and i0 == i1
+
+
+@pytest.mark.parametrize("p", [4, 8, 16, 5])
+def test_every_launch_shape_is_bitwise_identical(p):
+    # all shapes the autotuner may pick (shared-memory budget x block x register
+    # budget) for the star and the element Schur kernel, in both element types;
+    # the FP32 Schur kernel is reached through a mixed-precision V-cycle
+    from paper_1808_03595_gb300 import Context
+    from paper_1808_03595_gb300.solver import SemmgError
+    h = workloads.uniform_widths(3)
+    m = dense.Mesh(h, p, 1.0)
+    r = np.where(matfree.condensed_mask(m), workloads.random_nodal(h, p, 33), 0.0)
+    # (precision, star element type, Schur element type): the SEMMG_MIXED cycle runs
+    # its level residuals with the FP64 Schur kernel on FP32 vectors
+    for precision, dt, dts in (("fp64", torch.float64, torch.float64), ("mixed", torch.float32, torch.float64),
+                               ("mixed_fp32", torch.float32, torch.float32)):
+        with Context(h, p, 1.0, p0=2, precision=precision) as c:
+            r64 = c.pack(c.L, torch.as_tensor(r, device="cuda"))
+            rh = r64.to(dt)
+            runs = {
+                "star": (dt, lambda: c.smooth(c.L, rh).cpu().numpy()),
+                "schur": (dts, (lambda: c.apply_condensed(c.L, rh).cpu().numpy()) if precision == "fp64" else
+                          (lambda: c.vcycle(torch.zeros_like(r64), r64).cpu().numpy())),
+            }
+            tried = 0
+            for kern, (kdt, run) in runs.items():
+                ref = run()
+                for cap in (48 * 1024, 100 * 1024, 200 * 1024):
+                    for block in (256, 512):
+                        for regs in (64, 128):
+                            try:
+                                c.set_launch(c.L, kern, kdt, cap, block, regs)
+                            except SemmgError:
+                                continue
+                            b, _, _, rr = c.launch_shape(c.L, kern, kdt)
+                            assert (b, rr) == (block, regs)
+                            out = run()
+                            diff = np.abs(out - ref).max() / np.abs(ref).max()
+                            assert np.array_equal(out, ref), (kern, precision, cap, block, regs, diff)
+                            tried += 1
+            assert tried >= 8

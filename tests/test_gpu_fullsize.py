@@ -78,7 +78,7 @@ def _oracle_residual_reduction(h, p, lam, f, u_nodal):
     return np.linalg.norm(r[mask]) / np.linalg.norm(Fh[mask]), m, uh
 
 
-@pytest.mark.parametrize("lam,precision", [(0.0, "fp64"), (100.0, "mixed"), (0.0, "mixed")])
+@pytest.mark.parametrize("lam,precision", [(0.0, "fp64"), (100.0, "mixed"), (0.0, "mixed"), (0.0, "mixed_fp32")])
 def test_solve_16x16x16_p16_full_size(lam, precision):
     from paper_1808_03595_gb300 import Context
     h, p, lam, f, p0 = workloads.config("helmholtz_16x16x16_p16", lam=lam)

@@ -237,7 +237,7 @@ def test_vcycle_vs_oracle(mesh_name, p, p0):
     assert rel(got[mask], ref[mask]) < 1e-11
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_fp32"])
 def test_solve_config1_poisson_4x4x4_p4(precision):
     h, p, lam, f, p0 = workloads.config("poisson_4x4x4_p4")
     m = omesh(h, p, lam)
@@ -261,7 +261,7 @@ def test_solve_helmholtz_8x8x8(p):
     h, p, lam, f, p0 = workloads.config(f"helmholtz_8x8x8_p{p}")
     m = omesh(h, p, lam)
     ref, it_ref, hist = matfree.solve(m, f, p0=p0)
-    for precision in ("fp64", "mixed"):
+    for precision in ("fp64", "mixed", "mixed_fp32"):
         with ctx_for(h, p, lam, p0=p0, precision=precision) as c:
             u, info = c.solve(cuda(f), rtol=1e-10)
             u = u.cpu().numpy()
