@@ -85,6 +85,8 @@ struct semmg_ctx {
   double* Fh = nullptr;
   double* Uh = nullptr;
   double* Rh = nullptr;
+  // FP64 copy of a level's u for the FP64 level residuals of the SEMMG_MIXED cycle
+  double* U64s = nullptr;
   // Algorithm 5 vectors (old residual s, search direction p, q = Hhat p) and scalars
   double* kS = nullptr;
   double* kP = nullptr;
@@ -316,15 +318,21 @@ void op_residual(semmg_ctx* c, int l, const T* F, const T* u, T* out, int mode, 
   const double zb = (double)G.nelem * 6 * G.m * G.m * sizeof(T);
   if constexpr (std::is_same<T, float>::value) {
     if (c->opts.precision == SEMMG_MIXED) {
+      // u widened to FP64 once, then the FP64 kernels; F and the result stay FP32
       const double zb64 = (double)G.nelem * 6 * G.m * G.m * sizeof(double);
       {
+        Tic t(c, SEMMG_K_VECTOR, st);
+        launch_copy<double, float>(c->U64s, u, G.size, st);
+        t.toc(0.0, (double)G.size * 12);
+      }
+      {
         Tic t(c, SEMMG_K_ELEM_SCHUR, st);
-        launch_elem_schur_mixed(G, c->dl[l].td, u, (double*)c->Zs, (double*)c->wss, c->dl[l].schur64, st);
-        t.toc(schur_flops(G), zb64 + zb / 2, G.m > 0 ? 1 : 0);
+        launch_elem_schur<double>(G, c->dl[l].td, c->U64s, (double*)c->Zs, (double*)c->wss, c->dl[l].schur64, st);
+        t.toc(schur_flops(G), zb64 * 2, G.m > 0 ? 1 : 0);
       }
       Tic t(c, SEMMG_K_ASSEMBLE, st);
-      launch_assemble_mixed(G, c->dl[l].td, F, u, (const double*)c->Zs, out, mode, st);
-      t.toc(0.0, vec * (mode == 0 ? 3 : 2) + zb64);
+      launch_assemble_mixed(G, c->dl[l].td, F, c->U64s, (const double*)c->Zs, out, mode, st);
+      t.toc(0.0, vec * (mode == 0 ? 2 : 1) + 2.0 * vec + zb64);
       return;
     }
   }
@@ -692,6 +700,10 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   c->Fh = (double*)dalloc(c.get(), nL * sizeof(double));
   c->Uh = (double*)dalloc(c.get(), nL * sizeof(double));
   c->Rh = (double*)dalloc(c.get(), nL * sizeof(double));
+  if (o.precision == SEMMG_MIXED) {
+    c->U64s = (double*)dalloc(c.get(), nL * sizeof(double));
+    if (!c->U64s) return SEMMG_ERR_NOMEM;
+  }
   if (o.solver == SEMMG_SOLVER_KMG) {
     c->kS = (double*)dalloc(c.get(), nL * sizeof(double));
     c->kP = (double*)dalloc(c.get(), nL * sizeof(double));

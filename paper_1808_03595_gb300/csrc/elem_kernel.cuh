@@ -352,10 +352,8 @@ __device__ __forceinline__ void elem_coords(const Geo& G, int64_t e, int* a1, in
 // y_e = H_BI H_II^{-1} H_IB u on the six faces of every element -> Z[e][f][.]
 // Work regions: 0 tables (Sh, a0, Lam), 1 X (6 m^2), 2 Tt (6 m^2), 3 W (m^3).
 // PC > 0 compiles the kernel for degree PC (constant extents); PC = 0 reads it from G.
-// TI is the element type of u (float u with double T: FP64 arithmetic on an
-// FP32 vector, the level residuals of the mixed form).
-template <typename T, int PC, int NB, typename TI = T>
-__global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const TI* __restrict__ u,
+template <typename T, int PC, int NB>
+__global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const T* __restrict__ u,
                                                          T* __restrict__ Z, T* ws, WsPlan wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = PC ? PC - 1 : G.m, mm = m * m;
@@ -377,7 +375,7 @@ __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const 
     __syncthreads();
     for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
       const int f = idx / mm;
-      X[idx] = (T)u[elem_face_base(G, a1, a2, a3, f) + (idx - f * mm)];
+      X[idx] = u[elem_face_base(G, a1, a2, a3, f) + (idx - f * mm)];
     }
     __syncthreads();
     face_pairs(mm, X);
@@ -559,50 +557,44 @@ LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap, int block, int wide
   return c;
 }
 
-template <typename T, int NB, typename TI>
-void launch_elem_schur_nb(const Geo& G, const Tabs<T>& t, const TI* u, T* Z, T* ws, const LaunchCfg& c,
+template <typename T, int NB>
+void launch_elem_schur_nb(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, const LaunchCfg& c,
                           cudaStream_t st) {
   switch (G.p) {
-    case 2: k_elem_schur<T, 2, NB, TI><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    case 4: k_elem_schur<T, 4, NB, TI><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    case 8: k_elem_schur<T, 8, NB, TI><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    case 16: k_elem_schur<T, 16, NB, TI><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    case 32: k_elem_schur<T, 32, NB, TI><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    default: k_elem_schur<T, 0, NB, TI><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 2: k_elem_schur<T, 2, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 4: k_elem_schur<T, 4, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 8: k_elem_schur<T, 8, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 16: k_elem_schur<T, 16, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    case 32: k_elem_schur<T, 32, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
+    default: k_elem_schur<T, 0, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
   }
-}
-
-template <typename T, typename TI>
-void launch_elem_schur_any(const Geo& G, const Tabs<T>& t, const TI* u, T* Z, T* ws, const LaunchCfg& c,
-                           cudaStream_t st) {
-  if (G.m == 0 || G.nelem == 0 || !c.ok) return;
-  if (c.wide)
-    launch_elem_schur_nb<T, 1, TI>(G, t, u, Z, ws, c, st);
-  else
-    launch_elem_schur_nb<T, 2, TI>(G, t, u, Z, ws, c, st);
 }
 
 template <typename T>
 void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, const LaunchCfg& c,
                        cudaStream_t st) {
-  launch_elem_schur_any<T, T>(G, t, u, Z, ws, c, st);
+  if (G.m == 0 || G.nelem == 0 || !c.ok) return;
+  if (c.wide)
+    launch_elem_schur_nb<T, 1>(G, t, u, Z, ws, c, st);
+  else
+    launch_elem_schur_nb<T, 2>(G, t, u, Z, ws, c, st);
 }
 
-template <typename T, int NB, typename TI>
+template <typename T, int NB>
 static int schur_attrs_nb() {
   int bad = 0;
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 0, NB, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 2, NB, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 4, NB, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 8, NB, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 16, NB, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 32, NB, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 0, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 2, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 4, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 8, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 16, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 32, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return bad;
 }
 
-template <typename T, typename TI = T>
+template <typename T>
 static int schur_attrs() {
-  return schur_attrs_nb<T, 1, TI>() | schur_attrs_nb<T, 2, TI>();
+  return schur_attrs_nb<T, 1>() | schur_attrs_nb<T, 2>();
 }
 
 }  // namespace semmg

@@ -48,9 +48,8 @@ template void launch_elem_schur<double>(const Geo&, const Tabs<double>&, const d
                                         const LaunchCfg&, cudaStream_t);
 
 int set_elem_smem_limits_f32();
-int set_elem_smem_limits_mixed();
 int set_elem_smem_limits() {
-  int bad = schur_attrs<double>() | set_elem_smem_limits_f32() | set_elem_smem_limits_mixed();
+  int bad = schur_attrs<double>() | set_elem_smem_limits_f32();
   bad |= cudaFuncSetAttribute(k_elem_condense<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_condense<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_condense<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -36,8 +36,8 @@ __device__ __forceinline__ T mass1d(const Geo& G, const Tabs<T>& t, int d, int g
 // Line sum (Lg_d u)(g) over the skeleton nodes of the line through node s
 // along axis d.  `other` tells whether the node has a vertex-plane coordinate
 // on another axis, in which case every node of the line is a skeleton node.
-template <typename T, typename TI>
-__device__ T line_sum(const Geo& G, const Tabs<T>& t, const TI* __restrict__ u, int64_t s, int type, const int* g,
+template <typename T>
+__device__ T line_sum(const Geo& G, const Tabs<T>& t, const T* __restrict__ u, int64_t s, int type, const int* g,
                       int d, bool other) {
   const int p = G.p;
   const int a = divp(G, g[d]), q = g[d] - a * p;
@@ -54,7 +54,7 @@ __device__ T line_sum(const Geo& G, const Tabs<T>& t, const TI* __restrict__ u, 
     gg[d] = a * p + p;
     acc += row[p] * u[skel_index(G, gg[0], gg[1], gg[2])];
     const int st = run_stride(G, type, d);
-    const TI* ur = u + s - (int64_t)(q - 1) * st;  // slot of local index 1
+    const T* ur = u + s - (int64_t)(q - 1) * st;  // slot of local index 1
     for (int j = 1; j < p; ++j) acc += row[j] * ur[(int64_t)(j - 1) * st];
     return k * acc;
   }
@@ -101,12 +101,12 @@ __device__ __forceinline__ T face_z(const Geo& G, const T* __restrict__ Z, int t
   return Z[(em * 6 + 2 * d + 1) * mm + loc] + Z[(ep * 6 + 2 * d) * mm + loc];
 }
 
-// mode 0: out = F - Hhat u;  mode 1: out = Hhat u.  Arithmetic in T, vectors
-// F, u, out of type TI (float TI with double T: the mixed form's level residuals).
-template <typename T, typename TI = T>
-__global__ void __launch_bounds__(kThreads) k_assemble(Geo G, Tabs<T> t, const TI* __restrict__ F,
-                                                        const TI* __restrict__ u, const T* __restrict__ Z,
-                                                        TI* __restrict__ out, int mode) {
+// mode 0: out = F - Hhat u;  mode 1: out = Hhat u.  Arithmetic in T, F and out
+// of type TF (float TF with double T: the mixed form's level residuals).
+template <typename T, typename TF = T>
+__global__ void __launch_bounds__(kThreads) k_assemble(Geo G, Tabs<T> t, const TF* __restrict__ F,
+                                                        const T* __restrict__ u, const T* __restrict__ Z,
+                                                        TF* __restrict__ out, int mode) {
   const int nd[3] = {G.n1, G.n2, G.n3};
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < G.size; s += (int64_t)gridDim.x * blockDim.x) {
     int g[3];
@@ -124,9 +124,9 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Geo G, Tabs<T> t, const T
       const bool other = on[(d + 1) % 3] || on[(d + 2) % 3];
       L[d] = line_sum(G, t, u, s, type, g, d, other);
     }
-    T Hu = (T)G.lam * M[0] * M[1] * M[2] * (T)u[s] + M[1] * M[2] * L[0] + M[0] * M[2] * L[1] + M[0] * M[1] * L[2];
+    T Hu = (T)G.lam * M[0] * M[1] * M[2] * u[s] + M[1] * M[2] * L[0] + M[0] * M[2] * L[1] + M[0] * M[1] * L[2];
     if (type <= ENT_F3 && Z) Hu -= face_z(G, Z, type, g);
-    out[s] = (TI)(mode == 0 ? (T)F[s] - Hu : Hu);
+    out[s] = (TF)(mode == 0 ? (T)F[s] - Hu : Hu);
   }
 }
 
@@ -264,7 +264,7 @@ void launch_assemble(const Geo& G, const Tabs<T>& t, const T* F, const T* u, con
   k_assemble<T><<<grid_for(G.size), kThreads, 0, st>>>(G, t, F, u, G.m > 0 ? Z : nullptr, out, mode);
 }
 
-void launch_assemble_mixed(const Geo& G, const Tabs<double>& t, const float* F, const float* u, const double* Z,
+void launch_assemble_mixed(const Geo& G, const Tabs<double>& t, const float* F, const double* u, const double* Z,
                            float* out, int mode, cudaStream_t st) {
   k_assemble<double, float><<<grid_for(G.size), kThreads, 0, st>>>(G, t, F, u, G.m > 0 ? Z : nullptr, out, mode);
 }

@@ -314,9 +314,6 @@ template <typename T> LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t ca
                                                 int wide = -1);
 template <typename T> void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws,
                                              const LaunchCfg& c, cudaStream_t st);
-// FP64 arithmetic on an FP32 u (Z in FP64), with a plan from plan_elem_schur<double>
-void launch_elem_schur_mixed(const Geo& G, const Tabs<double>& t, const float* u, double* Z, double* ws,
-                             const LaunchCfg& c, cudaStream_t st);
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm);
 void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f_nodal, double* Z,
                           double* ws, const LaunchCfg& c, cudaStream_t st);
@@ -324,8 +321,8 @@ void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f_no
                          double* u_nodal, double* ws, const LaunchCfg& c, cudaStream_t st);
 template <typename T> void launch_assemble(const Geo& G, const Tabs<T>& t, const T* F, const T* u,
                                            const T* Z, T* out, int mode, cudaStream_t st);
-// out = F - Hhat u (mode 0) / Hhat u (mode 1) in FP64 arithmetic on FP32 F, u, out
-void launch_assemble_mixed(const Geo& G, const Tabs<double>& t, const float* F, const float* u, const double* Z,
+// out = F - Hhat u (mode 0) / Hhat u (mode 1) in FP64 arithmetic with FP32 F and out
+void launch_assemble_mixed(const Geo& G, const Tabs<double>& t, const float* F, const double* u, const double* Z,
                            float* out, int mode, cudaStream_t st);
 void launch_assemble_rhs(const Geo& G, const Tabs<double>& t, const double* f_nodal, const double* Z,
                          double* Fhat, cudaStream_t st);

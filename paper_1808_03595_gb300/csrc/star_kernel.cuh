@@ -26,7 +26,7 @@ namespace semmg {
 namespace {
 
 // Work regions: 0 S tables (3 nS^2; optional), 1 P (3 nS^2), 2 Tt (3 nS^2),
-// 3 V slab (ts nS^2), 4 Lam + act (3 nS each, as T).
+// 3 V slab (ts nS^2), 4 Lam (3 nS) and s3^2 (nS, in a 3 nS slot).
 //
 // Plane dd (normal to axis dd) is stored [jb][ja] with a = the lower and b
 // the higher of the two in-plane axes.  Centrosymmetric lines (every interior
@@ -72,60 +72,6 @@ __device__ __forceinline__ void fold_pass(int nS, int m, const int* sym, int alo
   }
 }
 
-// Forward 1D transform of folded data along the fast (along=0) / slow (along=1)
-// index: out[k] = sum_j S[j][k] x[j] (folded sums on symmetric lines).
-template <typename T>
-__device__ __forceinline__ void tx_pass(int nS, int m, const int* sym, const T* const* S, int along, const T* Y, T* Z) {
-  const int n2 = nS * nS;
-  for (int idx = threadIdx.x; idx < 3 * n2; idx += blockDim.x) {
-    const int dd = idx / n2, rr = idx - dd * n2, row = rr / nS, col = rr - row * nS;
-    const int ax = along == 0 ? ax_fast(dd) : ax_slow(dd);
-    const T* Sa = S[ax];
-    const T* y = Y + dd * n2;
-    const int k = along == 0 ? col : row;
-    const int str = along == 0 ? 1 : nS;
-    const T* yy = along == 0 ? y + row * nS : y + col;
-    T s = 0;
-    if (!sym[ax]) {
-      for (int j = 0; j < nS; ++j) s += Sa[j * nS + k] * yy[j * str];
-    } else if (k <= m) {
-      for (int j = 0; j <= m; ++j) s += Sa[(m + j) * nS + k] * yy[j * str];
-    } else {
-      for (int j = 1; j <= m; ++j) s += Sa[(m + j) * nS + k] * yy[(m + j) * str];
-    }
-    Z[idx] = s;
-  }
-}
-
-// Transposed 1D transform into folded form: symmetric lines give E_j (j <= m)
-// and O_j (stored at m+j); others give x[j] = sum_k S[j][k] b[k].
-template <typename T>
-__device__ __forceinline__ void txT_pass(int nS, int m, const int* sym, const T* const* S, int along, const T* B, T* Y) {
-  const int n2 = nS * nS;
-  for (int idx = threadIdx.x; idx < 3 * n2; idx += blockDim.x) {
-    const int dd = idx / n2, rr = idx - dd * n2, row = rr / nS, col = rr - row * nS;
-    const int ax = along == 0 ? ax_fast(dd) : ax_slow(dd);
-    const T* Sa = S[ax];
-    const T* b = B + dd * n2;
-    const int j = along == 0 ? col : row;
-    const int str = along == 0 ? 1 : nS;
-    const T* bb = along == 0 ? b + row * nS : b + col;
-    T s = 0;
-    if (!sym[ax]) {
-      const T* sr = Sa + j * nS;
-      for (int k = 0; k < nS; ++k) s += sr[k] * bb[k * str];
-    } else if (j <= m) {
-      const T* sr = Sa + (m + j) * nS;
-      for (int k = 0; k <= m; ++k) s += sr[k] * bb[k * str];
-    } else {
-      const T* sr = Sa + j * nS;  // row m + (j - m)
-      for (int k = m + 1; k < nS; ++k) s += sr[k] * bb[k * str];
-    }
-    Y[idx] = s;
-  }
-}
-
-
 // ---- grouped passes: each thread computes kG outputs of one line that share
 // the input loads (kG independent multiply-add chains per thread).
 constexpr int kG = 4;
@@ -137,42 +83,66 @@ struct Block {
   int even;     // 1: even block (inputs j use row m + j), 0: odd block or unfolded (row j)
 };
 
-__device__ __forceinline__ int groups_per_line(int nS, int m, int symax) {
-  return symax ? (m + 1 + kG - 1) / kG + (m + kG - 1) / kG : (nS + kG - 1) / kG;
+// Index ranges of a star, per axis d: the active range [lo[d], hi[d]) of the
+// vertex line (all nS points inside the domain, or, for a line whose vertex
+// lies on the Dirichlet boundary, the m points on the inner side), and pa[d]:
+// whether the plane through the vertex normal to d holds active points (the
+// vertex itself is active along d).  Points outside the active ranges are
+// identity-padded with zero data, so every sum and every eigen index outside
+// them contributes exactly zero and is skipped.
+struct Ranges {
+  int lo[3], hi[3], pa[3];
+};
+
+__device__ __forceinline__ int groups_per_line(int m, int symax, int lo, int hi) {
+  return symax ? (m + 1 + kG - 1) / kG + (m + kG - 1) / kG : (hi - lo + kG - 1) / kG;
 }
 
-__device__ __forceinline__ Block block_of(int nS, int m, int symax, int g) {
+__device__ __forceinline__ Block block_of(int m, int symax, int lo, int hi, int g) {
   Block b;
   if (!symax) {
-    b.k0 = g * kG; b.k1 = min(b.k0 + kG, nS); b.j0 = 0; b.j1 = nS; b.even = 0;
+    b.k0 = lo + g * kG; b.k1 = min(b.k0 + kG, hi); b.j0 = lo; b.j1 = hi; b.even = 0;
   } else {
     const int ge = (m + 1 + kG - 1) / kG;
     if (g < ge) {
       b.k0 = g * kG; b.k1 = min(b.k0 + kG, m + 1); b.j0 = 0; b.j1 = m + 1; b.even = 1;
     } else {
-      b.k0 = m + 1 + (g - ge) * kG; b.k1 = min(b.k0 + kG, nS); b.j0 = m + 1; b.j1 = nS; b.even = 0;
+      b.k0 = m + 1 + (g - ge) * kG; b.k1 = min(b.k0 + kG, 2 * m + 1); b.j0 = m + 1; b.j1 = 2 * m + 1; b.even = 0;
     }
   }
   return b;
 }
 
-// Z = forward transform of folded Y along `along` (0: fast index, 1: slow index), grouped.
-template <typename T>
-__device__ __forceinline__ void tx_pass_g(int nS, int m, const int* sym, const T* const* S, int along, const T* Y,
-                                          T* Z) {
-  const int n2 = nS * nS;
+// Work items of a grouped pass: per active plane, the active lines (indexed
+// along the other in-plane axis) times the output groups of a line.
+struct PassItems {
   int gpl[3], acc[4];
-  acc[0] = 0;
+};
+
+__device__ __forceinline__ PassItems pass_items(int m, const int* sym, const Ranges& R, int along) {
+  PassItems it;
+  it.acc[0] = 0;
   for (int dd = 0; dd < 3; ++dd) {
     const int ax = along == 0 ? ax_fast(dd) : ax_slow(dd);
-    gpl[dd] = groups_per_line(nS, m, sym[ax]);
-    acc[dd + 1] = acc[dd] + nS * gpl[dd];
+    const int ox = along == 0 ? ax_slow(dd) : ax_fast(dd);
+    it.gpl[dd] = R.pa[dd] ? groups_per_line(m, sym[ax], R.lo[ax], R.hi[ax]) : 0;
+    it.acc[dd + 1] = it.acc[dd] + (R.hi[ox] - R.lo[ox]) * it.gpl[dd];
   }
-  for (int it = threadIdx.x; it < acc[3]; it += blockDim.x) {
-    const int dd = it < acc[1] ? 0 : (it < acc[2] ? 1 : 2);
-    const int r = it - acc[dd], line = r / gpl[dd], g = r - line * gpl[dd];
+  return it;
+}
+
+// Z = forward transform of folded Y along `along` (0: fast index, 1: slow index), grouped.
+template <typename T>
+__device__ __forceinline__ void tx_pass_g(int nS, int m, const int* sym, const Ranges& R, const T* const* S,
+                                          int along, const T* Y, T* Z) {
+  const int n2 = nS * nS;
+  const PassItems pi = pass_items(m, sym, R, along);
+  for (int it = threadIdx.x; it < pi.acc[3]; it += blockDim.x) {
+    const int dd = it < pi.acc[1] ? 0 : (it < pi.acc[2] ? 1 : 2);
     const int ax = along == 0 ? ax_fast(dd) : ax_slow(dd);
-    const Block b = block_of(nS, m, sym[ax], g);
+    const int ox = along == 0 ? ax_slow(dd) : ax_fast(dd);
+    const int r = it - pi.acc[dd], line = R.lo[ox] + r / pi.gpl[dd], g = r % pi.gpl[dd];
+    const Block b = block_of(m, sym[ax], R.lo[ax], R.hi[ax], g);
     const T* Sa = S[ax];
     const T* y = Y + dd * n2 + (along == 0 ? line * nS : line);
     const int ys = along == 0 ? 1 : nS;
@@ -195,23 +165,18 @@ __device__ __forceinline__ void tx_pass_g(int nS, int m, const int* sym, const T
 
 // Y = transposed transform into folded form (E_j / O_j), grouped over outputs j.
 template <typename T>
-__device__ __forceinline__ void txT_pass_g(int nS, int m, const int* sym, const T* const* S, int along, const T* B,
-                                           T* Y) {
+__device__ __forceinline__ void txT_pass_g(int nS, int m, const int* sym, const Ranges& R, const T* const* S,
+                                           int along, const T* B, T* Y) {
   const int n2 = nS * nS;
-  int gpl[3], acc[4];
-  acc[0] = 0;
-  for (int dd = 0; dd < 3; ++dd) {
+  const PassItems pi = pass_items(m, sym, R, along);
+  for (int it = threadIdx.x; it < pi.acc[3]; it += blockDim.x) {
+    const int dd = it < pi.acc[1] ? 0 : (it < pi.acc[2] ? 1 : 2);
     const int ax = along == 0 ? ax_fast(dd) : ax_slow(dd);
-    gpl[dd] = groups_per_line(nS, m, sym[ax]);
-    acc[dd + 1] = acc[dd] + nS * gpl[dd];
-  }
-  for (int it = threadIdx.x; it < acc[3]; it += blockDim.x) {
-    const int dd = it < acc[1] ? 0 : (it < acc[2] ? 1 : 2);
-    const int r = it - acc[dd], line = r / gpl[dd], g = r - line * gpl[dd];
-    const int ax = along == 0 ? ax_fast(dd) : ax_slow(dd);
+    const int ox = along == 0 ? ax_slow(dd) : ax_fast(dd);
+    const int r = it - pi.acc[dd], line = R.lo[ox] + r / pi.gpl[dd], g = r % pi.gpl[dd];
     // the group's outputs are folded positions [k0, k1); their sums run over the
     // eigen-index block of the same parity, [j0, j1) (same ranges as the forward pass)
-    const Block blk = block_of(nS, m, sym[ax], g);
+    const Block blk = block_of(m, sym[ax], R.lo[ax], R.hi[ax], g);
     const T* Sa = S[ax];
     const T* bb = B + dd * n2 + (along == 0 ? line * nS : line);
     const int bs = along == 0 ? 1 : nS;
@@ -259,14 +224,18 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_next;
   __shared__ int s_sym[3];
+  __shared__ Ranges s_rg;
+  __shared__ int Ac[3 * (2 * SEMMG_MAX_DEGREE - 1)];  // active flags of the three vertex lines
   const int p = PC ? PC : G.p, m = p - 1, nS = 2 * p - 1, n2 = nS * nS;
   T* Sbuf = ws_ptr<T>(wp, 0, smem_raw, ws);
   T* P = ws_ptr<T>(wp, 1, smem_raw, ws);
   T* Tt = ws_ptr<T>(wp, 2, smem_raw, ws);
   T* V = ws_ptr<T>(wp, 3, smem_raw, ws);
   T* Lm = ws_ptr<T>(wp, 4, smem_raw, ws);
-  T* Ac = Lm + 3 * nS;
+  T* s3sq = Lm + 3 * nS;  // s3[k]^2
   const T lam = (T)G.lam;
+  // 1 / (number of planes a node lies on): 1, 2 or 3 planes
+  const T rcp_mult[3] = {(T)1, (T)0.5, (T)1 / (T)3};
   int64_t st = blockIdx.x;
   while (st < G.nstar) {
     const int c[3] = {(int)(st % G.nv1), (int)((st / G.nv1) % G.nv2), (int)(st / ((int64_t)G.nv1 * G.nv2))};
@@ -283,23 +252,37 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
       }
       for (int i = threadIdx.x; i < nS; i += blockDim.x) {
         Lm[d * nS + i] = t.starLam[d][(int64_t)c[d] * nS + i];
-        Ac[d * nS + i] = (T)t.act[d][(int64_t)c[d] * nS + i];
+        Ac[d * nS + i] = t.act[d][(int64_t)c[d] * nS + i];
       }
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < nS; i += blockDim.x) {
+      const T v = S[2][m * nS + i];
+      s3sq[i] = v * v;
+    }
+    if (threadIdx.x < 3) {
+      const int d = threadIdx.x;
+      int lo = 0, hi = nS;
+      while (lo < nS && !Ac[d * nS + lo]) ++lo;
+      while (hi > lo && !Ac[d * nS + hi - 1]) --hi;
+      s_rg.lo[d] = lo;
+      s_rg.hi[d] = hi;
+      s_rg.pa[d] = Ac[d * nS + m];
+    }
+    __syncthreads();
     const int* sym = s_sym;
+    const Ranges rg = s_rg;
     // 1. gather the three planes, divided by the multiplicity, zero where not a star node
     for (int idx = threadIdx.x; idx < 3 * n2; idx += blockDim.x) {
       const int dd = idx / n2, rr = idx - dd * n2, jb = rr / nS - m, ja = rr % nS - m;
       const int ax_a = ax_fast(dd), ax_b = ax_slow(dd);
       T v = 0;
-      if (Ac[dd * nS + m] != (T)0 && Ac[ax_a * nS + ja + m] != (T)0 && Ac[ax_b * nS + jb + m] != (T)0) {
+      if (Ac[dd * nS + m] && Ac[ax_a * nS + ja + m] && Ac[ax_b * nS + jb + m]) {
         int g[3];
         g[dd] = c[dd] * p;
         g[ax_a] = c[ax_a] * p + ja;
         g[ax_b] = c[ax_b] * p + jb;
-        const T mult = (T)(1 + (ja == 0) + (jb == 0));
-        v = r[skel_index(G, g[0], g[1], g[2])] / mult;
+        v = r[skel_index(G, g[0], g[1], g[2])] * rcp_mult[(ja == 0) + (jb == 0)];
       }
       P[idx] = v;
     }
@@ -307,11 +290,11 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
     // 2a. in-plane transforms A = S_b^T P S_a (fold, transform; fast then slow index)
     fold_pass(nS, m, sym, 0, P, Tt);
     __syncthreads();
-    tx_pass_g(nS, m, sym, S, 0, Tt, P);
+    tx_pass_g(nS, m, sym, rg, S, 0, Tt, P);
     __syncthreads();
     fold_pass(nS, m, sym, 1, P, Tt);
     __syncthreads();
-    tx_pass_g(nS, m, sym, S, 1, Tt, P);
+    tx_pass_g(nS, m, sym, rg, S, 1, Tt, P);
     __syncthreads();
     // 2b + 3 + 4a. expansion along the normals with the vertex rows, times 1/D,
     // and the contractions back along the normals, in slabs of `ts` k3-planes
@@ -328,36 +311,81 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
       const int64_t cls = ((int64_t)t.starCls[0][c[0]] * t.ncls[1] + t.starCls[1][c[1]]) * t.ncls[2] + t.starCls[2][c[2]];
       R = t.Rtab + cls * n3;
     }
-    const int nz1 = sym[0] ? m + 1 : nS, nz2 = sym[1] ? m + 1 : nS, nz3 = sym[2] ? m + 1 : nS;
+    // live ranges [0, nz_d) of the vertex rows: s_d[k] may be non-zero only
+    // there (odd eigenvectors vanish at the vertex; a vertex on the boundary
+    // makes the whole row zero on the active range)
+    const int nz1 = rg.pa[0] ? (sym[0] ? m + 1 : nS) : 0;
+    const int nz2 = rg.pa[1] ? (sym[1] ? m + 1 : nS) : 0;
+    const int nz3 = rg.pa[2] ? (sym[2] ? m + 1 : nS) : 0;
+    const int lo1 = rg.lo[0], w1 = rg.hi[0] - rg.lo[0], lo2 = rg.lo[1], w2 = rg.hi[1] - rg.lo[1];
+    // (k1, k2) pairs, live ones first so that warps stay on one branch:
+    // k2 live (any k1), then k2 dead with k1 live, then both dead (only the
+    // x3-plane term, so only when that plane is active); live k_d are the
+    // first nz_d indices of a full range (a line with a live vertex row is
+    // active everywhere)
+    const int seg1 = nz2 * w1, seg2 = (w2 - nz2) * nz1, nlive = seg1 + seg2;
+    const int npair = nlive + (rg.pa[2] ? (w2 - nz2) * (w1 - nz1) : 0);
     const int ts = slab_thickness(nS);
     T* B1 = Tt;
     T* B2 = Tt + n2;
     T* B3 = Tt + 2 * n2;
     for (int i = threadIdx.x; i < n2; i += blockDim.x) B3[i] = 0;
-    for (int k3s = 0; k3s < nS; k3s += ts) {
-      const int tn = nS - k3s < ts ? nS - k3s : ts;
+    for (int k3s = rg.lo[2]; k3s < rg.hi[2]; k3s += ts) {
+      const int tn = rg.hi[2] - k3s < ts ? rg.hi[2] - k3s : ts;
       __syncthreads();
-      for (int pr = threadIdx.x; pr < n2; pr += blockDim.x) {
-        const int k1 = pr % nS, k2 = pr / nS;
-        const T a3 = P[2 * n2 + k2 * nS + k1];
-        T b3 = 0;
-        for (int kk = 0; kk < tn; ++kk) {
-          const int k3 = k3s + kk;
-          const T E = s1[k1] * P[k3 * nS + k2] + s2[k2] * P[n2 + k3 * nS + k1] + s3[k3] * a3;
-          const int64_t pt = (int64_t)k3 * n2 + pr;
-          const T v = R ? E * R[pt] : fast_div(E, lam + Lm[k1] + Lm[nS + k2] + Lm[2 * nS + k3]);
-          V[kk * n2 + pr] = v;
-          if (k3 < nz3) b3 += s3[k3] * v;
+      for (int i = threadIdx.x; i < npair; i += blockDim.x) {
+        int k1, k2;
+        if (i < seg1) {
+          k2 = lo2 + i / w1;
+          k1 = lo1 + i % w1;
+        } else if (i < nlive) {
+          const int j = i - seg1;
+          k2 = lo2 + nz2 + j / nz1;
+          k1 = lo1 + j % nz1;
+        } else {
+          const int j = i - nlive, wd = w1 - nz1;
+          k2 = lo2 + nz2 + j / wd;
+          k1 = lo1 + nz1 + j % wd;
         }
-        B3[pr] += b3;
+        const int pr = k2 * nS + k1;
+        const T a3 = rg.pa[2] ? P[2 * n2 + pr] : (T)0;
+        if (i < nlive) {
+          const T c1 = k1 < nz1 ? s1[k1] : (T)0, c2 = k2 < nz2 ? s2[k2] : (T)0;
+          T b3 = 0;
+          for (int kk = 0; kk < tn; ++kk) {
+            const int k3 = k3s + kk;
+            T E = c1 * P[k3 * nS + k2] + c2 * P[n2 + k3 * nS + k1];
+            if (k3 < nz3) E += s3[k3] * a3;
+            const int64_t pt = (int64_t)k3 * n2 + pr;
+            const T v = R ? E * R[pt] : fast_div(E, lam + Lm[k1] + Lm[nS + k2] + Lm[2 * nS + k3]);
+            V[kk * n2 + pr] = v;
+            if (k3 < nz3) b3 += s3[k3] * v;
+          }
+          if (nz3) B3[pr] += b3;
+        } else {
+          // s1[k1] = s2[k2] = 0: V = s3 a3 / D is read only by B3, which gets
+          // a3 sum_k3 s3^2 / D
+          T b3 = 0;
+          for (int kk = 0; kk < tn; ++kk) {
+            const int k3 = k3s + kk;
+            if (k3 >= nz3) break;
+            const int64_t pt = (int64_t)k3 * n2 + pr;
+            b3 += R ? s3sq[k3] * R[pt] : fast_div(s3sq[k3], lam + Lm[k1] + Lm[nS + k2] + Lm[2 * nS + k3]);
+          }
+          B3[pr] += a3 * b3;
+        }
       }
       __syncthreads();
-      for (int o = threadIdx.x; o < 2 * tn * nS; o += blockDim.x) {
-        const int which = o / (tn * nS), rr = o - which * tn * nS, kk = rr / nS, kx = rr % nS;
+      // B1[k3][k2] = sum_k1 s1 V (plane 0 active), B2[k3][k1] = sum_k2 s2 V (plane 1 active)
+      const int nb1 = rg.pa[0] ? tn * w2 : 0, nb2 = rg.pa[1] ? tn * w1 : 0;
+      for (int o = threadIdx.x; o < nb1 + nb2; o += blockDim.x) {
+        const bool first = o < nb1;
+        const int rr = first ? o : o - nb1, wx = first ? w2 : w1;
+        const int kk = rr / wx, kx = (first ? lo2 : lo1) + rr % wx;
         const T* vs = V + kk * n2;
         T s = 0;
         T s_1 = 0, s_2 = 0, s_3 = 0;  // four independent partial sums
-        if (which == 0) {  // B1[k3][k2 = kx] = sum over k1
+        if (first) {  // sum over k1
           const T* v = vs + kx * nS;
           int k = 0;
           for (; k + 3 < nz1; k += 4) {
@@ -368,7 +396,7 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
           }
           for (; k < nz1; ++k) s += s1[k] * v[k];
           B1[(k3s + kk) * nS + kx] = (s + s_1) + (s_2 + s_3);
-        } else {           // B2[k3][k1 = kx] = sum over k2
+        } else {      // sum over k2
           const T* v = vs + kx;
           int k = 0;
           for (; k + 3 < nz2; k += 4) {
@@ -384,25 +412,24 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
     }
     __syncthreads();
     // 4b. back to the planes: O = S_b B S_a^T (slow index first, then fast)
-    txT_pass_g(nS, m, sym, S, 1, Tt, P);
+    txT_pass_g(nS, m, sym, rg, S, 1, Tt, P);
     __syncthreads();
     for (int idx = threadIdx.x; idx < 3 * n2; idx += blockDim.x) {
       const int dd = idx / n2, rr = idx - dd * n2, row = rr / nS, col = rr - row * nS;
       Tt[idx] = unfold_value(nS, m, sym, 1, P, dd, row, col);
     }
     __syncthreads();
-    txT_pass_g(nS, m, sym, S, 0, Tt, P);
+    txT_pass_g(nS, m, sym, rg, S, 0, Tt, P);
     __syncthreads();
     T* ob = Ob + st * 3 * (int64_t)n2;
     for (int idx = threadIdx.x; idx < 3 * n2; idx += blockDim.x) {
       const int dd = idx / n2, rr = idx - dd * n2, jb = rr / nS, ja = rr % nS;
       const int ax_a = ax_fast(dd), ax_b = ax_slow(dd);
       const T s = unfold_value(nS, m, sym, 0, P, dd, jb, ja);
-      const bool active = Ac[dd * nS + m] != (T)0 && Ac[ax_a * nS + ja] != (T)0 && Ac[ax_b * nS + jb] != (T)0;
+      const bool active = Ac[dd * nS + m] && Ac[ax_a * nS + ja] && Ac[ax_b * nS + jb];
       const int oa = ja - m, obb = jb - m;
-      const T wgt = t.w1d[oa < 0 ? -oa : oa] * t.w1d[obb < 0 ? -obb : obb];
-      const T mult = (T)(1 + (oa == 0) + (obb == 0));
-      ob[idx] = active ? wgt * s / mult : (T)0;
+      const T wgt = t.w1d[oa < 0 ? -oa : oa] * t.w1d[obb < 0 ? -obb : obb] * rcp_mult[(oa == 0) + (obb == 0)];
+      ob[idx] = active ? wgt * s : (T)0;
     }
     // next star: from the shared counter when given (dynamic balance), else grid-strided
     if (counter) {
