@@ -85,6 +85,9 @@ struct semmg_ctx {
   double* Fh = nullptr;
   double* Uh = nullptr;
   double* Rh = nullptr;
+  // scaled interior eigen-coefficients of the right-hand side, kept from the
+  // condensation to the recovery of one solve (nelem m^3 at the finest level)
+  double* Gs = nullptr;
   // FP64 copy of a level's u for the FP64 level residuals of the SEMMG_MIXED cycle
   double* U64s = nullptr;
   // Algorithm 5 vectors (old residual s, search direction p, q = Hhat p) and scalars
@@ -465,6 +468,30 @@ void correction(semmg_ctx* c, double* u, const double* r, cudaStream_t st) {
   t.toc(0.0, (double)n * (16 + es));
 }
 
+// F_hat = F_B - H_BI H_II^{-1} F_I; with `save`, the scaled interior
+// eigen-coefficients of F_I are kept in Gs for recover_impl(..., use_saved).
+void condense_impl(semmg_ctx* c, const double* f, double* fh, bool save, cudaStream_t st) {
+  const int L = c->L();
+  const Geo& G = c->geo[L];
+  const double nn = (double)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
+  Tic t(c, SEMMG_K_CONDENSE, st);
+  launch_elem_condense(G, c->dl[L].td, f, (double*)c->Zs, save ? c->Gs : nullptr, (double*)c->wss, c->fdm, st);
+  launch_assemble_rhs(G, c->dl[L].td, f, (const double*)c->Zs, fh, st);
+  t.toc(G.m > 0 ? fdm_flops(G) : 0.0, 8.0 * (nn + G.size), 2);
+}
+
+// u = (u_hat, H_II^{-1}(F_I - H_IB u_hat)); use_saved: F_I's coefficients from
+// the preceding condense_impl(..., save = true) on the same f.
+void recover_impl(semmg_ctx* c, const double* f, const double* uh, double* u, bool use_saved, cudaStream_t st) {
+  const int L = c->L();
+  const Geo& G = c->geo[L];
+  const double nn = (double)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
+  Tic t(c, SEMMG_K_RECOVER, st);
+  launch_unpack(G, uh, u, st);
+  launch_elem_recover(G, c->dl[L].td, f, use_saved ? c->Gs : nullptr, uh, u, (double*)c->wss, c->fdm, st);
+  t.toc(G.m > 0 ? fdm_flops(G) : 0.0, 8.0 * (2 * nn + G.size), 2);
+}
+
 // Start of the outer iteration from u_hat = 0: r = F_hat, ||r||^2 into dnorm,
 // and for Algorithm 5 s = r, p = 0, delta = 1.
 void iter_start(semmg_ctx* c, cudaStream_t st) {
@@ -700,6 +727,14 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   c->Fh = (double*)dalloc(c.get(), nL * sizeof(double));
   c->Uh = (double*)dalloc(c.get(), nL * sizeof(double));
   c->Rh = (double*)dalloc(c.get(), nL * sizeof(double));
+  {
+    const Geo& GL = c->geo[nl - 1];
+    const size_t ng = (size_t)GL.nelem * GL.m * GL.m * GL.m;
+    if (ng > 0) {
+      c->Gs = (double*)dalloc(c.get(), ng * sizeof(double));
+      if (!c->Gs) return SEMMG_ERR_NOMEM;
+    }
+  }
   if (o.precision == SEMMG_MIXED) {
     c->U64s = (double*)dalloc(c.get(), nL * sizeof(double));
     if (!c->U64s) return SEMMG_ERR_NOMEM;
@@ -852,34 +887,21 @@ int semmg_vcycle(semmg_ctx* c, double* u, const double* f, void* stream) {
 
 int semmg_condense_rhs(semmg_ctx* c, const double* f, double* fh, void* stream) {
   if (!c || !f || !fh) return SEMMG_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int L = c->L();
-  const Geo& G = c->geo[L];
-  const double nn = (double)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
-  Tic t(c, SEMMG_K_CONDENSE, st);
-  launch_elem_condense(G, c->dl[L].td, f, (double*)c->Zs, (double*)c->wss, c->fdm, st);
-  launch_assemble_rhs(G, c->dl[L].td, f, (const double*)c->Zs, fh, st);
-  t.toc(G.m > 0 ? fdm_flops(G) : 0.0, 8.0 * (nn + G.size), 2);
+  condense_impl(c, f, fh, false, (cudaStream_t)stream);
   return check_cuda(c, "condense_rhs");
 }
 
 int semmg_recover(semmg_ctx* c, const double* f, const double* uh, double* u, void* stream) {
   if (!c || !f || !uh || !u) return SEMMG_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int L = c->L();
-  const Geo& G = c->geo[L];
-  const double nn = (double)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
-  Tic t(c, SEMMG_K_RECOVER, st);
-  launch_unpack(G, uh, u, st);
-  launch_elem_recover(G, c->dl[L].td, f, uh, u, (double*)c->wss, c->fdm, st);
-  t.toc(G.m > 0 ? fdm_flops(G) : 0.0, 8.0 * (2 * nn + G.size), 2);
+  recover_impl(c, f, uh, u, false, (cudaStream_t)stream);
   return check_cuda(c, "recover");
 }
 
 int semmg_solve(semmg_ctx* c, const double* f, double* u, double rtol, semmg_info* info, void* stream) {
   if (!c || !f || !u || !(rtol > 0.0)) return SEMMG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  int rc = semmg_condense_rhs(c, f, c->Fh, stream);
+  condense_impl(c, f, c->Fh, true, st);
+  int rc = check_cuda(c, "condense_rhs");
   if (rc) return rc;
   iter_start(c, st);
   double r0 = 0.0, rn = 0.0;
@@ -897,7 +919,8 @@ int semmg_solve(semmg_ctx* c, const double* f, double* u, double rtol, semmg_inf
     if (!std::isfinite(rn)) status = SEMMG_ERR_NONFINITE;
   }
   if (status == SEMMG_OK && rn > rtol * r0) status = SEMMG_ERR_NOT_CONVERGED;
-  rc = semmg_recover(c, f, c->Uh, u, stream);
+  recover_impl(c, f, c->Uh, u, true, st);
+  rc = check_cuda(c, "recover");
   if (rc) return rc;
   if (info) {
     info->iters = it;
@@ -1041,7 +1064,7 @@ namespace {
 
 // Enqueue one solve of context c (device nodal f -> u) into the capturing stream s.
 int capture_solve(semmg_ctx* c, const double* f, double* u, BatchCtl* ctl, cudaStream_t s, cudaStream_t sb) {
-  semmg_condense_rhs(c, f, c->Fh, s);
+  condense_impl(c, f, c->Fh, true, s);
   iter_start(c, s);
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
@@ -1071,7 +1094,7 @@ int capture_solve(semmg_ctx* c, const double* f, double* u, BatchCtl* ctl, cudaS
   if (cudaStreamEndCapture(sb, &got) != cudaSuccess) return check_cuda(c, "batch: body end");
   if (cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
     return check_cuda(c, "batch: dependencies");
-  semmg_recover(c, f, c->Uh, u, s);
+  recover_impl(c, f, c->Uh, u, true, s);
   return check_cuda(c, "batch: capture");
 }
 

@@ -453,8 +453,12 @@ __device__ __forceinline__ int64_t interior_node(const Geo& G, int a1, int a2, i
 
 // Z[e][f] = (H_BI H_II^{-1} F_I) on the faces, F_I = (M f)_I element-local.
 template <int PC>
+// When Gsave is given, the scaled interior eigen-coefficients
+// D^{-1} (S^T x S^T x S^T) F_I of every element are also stored there
+// (m^3 per element), for the recovery of the same solve.
 __global__ void __launch_bounds__(512, 1) k_elem_condense(Geo G, Tabs<double> t, const double* __restrict__ f,
-                                                        double* __restrict__ Z, double* ws, WsPlan wp) {
+                                                        double* __restrict__ Z, double* __restrict__ Gsave,
+                                                        double* ws, WsPlan wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = PC ? PC - 1 : G.m, mm = m * m, mmm = mm * m;
   FdmSmem s = fdm_layout(m, smem_raw, ws, wp);
@@ -478,9 +482,12 @@ __global__ void __launch_bounds__(512, 1) k_elem_condense(Geo G, Tabs<double> t,
     }
     __syncthreads();
     interior_forward(I, s.Sr, s.A, s.B, sig);
+    double* Ge = Gsave ? Gsave + e * (int64_t)mmm : nullptr;
     for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
       const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
-      s.A[idx] *= inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
+      const double v = s.A[idx] * inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
+      s.A[idx] = v;
+      if (Ge) Ge[idx] = v;
     }
     __syncthreads();
     faces_reduce(m, F.ne, s.a0, s.A, s.X);
@@ -490,9 +497,12 @@ __global__ void __launch_bounds__(512, 1) k_elem_condense(Geo G, Tabs<double> t,
   }
 }
 
-// u_I = H_II^{-1} (F_I - H_IB uhat) written into the nodal array.
+// u_I = H_II^{-1} (F_I - H_IB uhat) written into the nodal array.  With Gin
+// (the coefficients k_elem_condense stored for the same f) the forward
+// transform of F_I is taken from there instead of being recomputed.
 template <int PC>
 __global__ void __launch_bounds__(512, 1) k_elem_recover(Geo G, Tabs<double> t, const double* __restrict__ f,
+                                                       const double* __restrict__ Gin,
                                                        const double* __restrict__ uh, double* __restrict__ un,
                                                        double* ws, WsPlan wp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -512,23 +522,34 @@ __global__ void __launch_bounds__(512, 1) k_elem_recover(Geo G, Tabs<double> t, 
     const double vol = 0.125 * x1[0] * x2[0] * x3[0];  // h1 h2 h3 / 8
     const double sig = x1[5] * x2[5] * x3[5];          // sqrt(8 / (h1 h2 h3))
     __syncthreads();
-    for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
-      const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / mm;
-      s.A[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] * f[interior_node(G, a1, a2, a3, idx)];
+    if (!Gin) {
+      for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
+        const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / mm;
+        s.A[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] * f[interior_node(G, a1, a2, a3, idx)];
+      }
     }
     for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
       const int fc = idx / mm;
       s.X[idx] = uh[elem_face_base(G, a1, a2, a3, fc) + (idx - fc * mm)];
     }
     __syncthreads();
-    interior_forward(I, s.Sr, s.A, s.B, sig);
+    if (!Gin) interior_forward(I, s.Sr, s.A, s.B, sig);
     face_pairs(mm, s.X);
     __syncthreads();
     faces_forward(F, s.Sh, s.X, s.Tt, sc);
-    for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
-      const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
-      s.A[idx] = (s.A[idx] - face_expand(m, F.ne, s.a0, s.X, k1, k2, k3)) *
-                 inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
+    if (Gin) {
+      const double* Ge = Gin + e * (int64_t)mmm;
+      for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
+        const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
+        s.A[idx] = Ge[idx] - face_expand(m, F.ne, s.a0, s.X, k1, k2, k3) *
+                                 inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
+        const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
+        s.A[idx] = (s.A[idx] - face_expand(m, F.ne, s.a0, s.X, k1, k2, k3)) *
+                   inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
+      }
     }
     __syncthreads();
     interior_backward(I, s.Sr, s.A, s.B);

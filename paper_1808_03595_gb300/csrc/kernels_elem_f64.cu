@@ -23,23 +23,23 @@ LaunchCfg plan_elem_fdm(const Geo& G, int nsm) {
   return c;
 }
 
-void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f, double* Z, double* ws,
-                          const LaunchCfg& c, cudaStream_t st) {
+void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f, double* Z, double* Gsave,
+                          double* ws, const LaunchCfg& c, cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
   switch (G.p) {
-    case 16: k_elem_condense<16><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, ws, c.ws); break;
-    case 32: k_elem_condense<32><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, ws, c.ws); break;
-    default: k_elem_condense<0><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, ws, c.ws); break;
+    case 16: k_elem_condense<16><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, Gsave, ws, c.ws); break;
+    case 32: k_elem_condense<32><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, Gsave, ws, c.ws); break;
+    default: k_elem_condense<0><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, Gsave, ws, c.ws); break;
   }
 }
 
-void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f, const double* uh, double* un,
-                         double* ws, const LaunchCfg& c, cudaStream_t st) {
+void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f, const double* Gin,
+                         const double* uh, double* un, double* ws, const LaunchCfg& c, cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
   switch (G.p) {
-    case 16: k_elem_recover<16><<<c.grid, c.block, c.smem, st>>>(G, t, f, uh, un, ws, c.ws); break;
-    case 32: k_elem_recover<32><<<c.grid, c.block, c.smem, st>>>(G, t, f, uh, un, ws, c.ws); break;
-    default: k_elem_recover<0><<<c.grid, c.block, c.smem, st>>>(G, t, f, uh, un, ws, c.ws); break;
+    case 16: k_elem_recover<16><<<c.grid, c.block, c.smem, st>>>(G, t, f, Gin, uh, un, ws, c.ws); break;
+    case 32: k_elem_recover<32><<<c.grid, c.block, c.smem, st>>>(G, t, f, Gin, uh, un, ws, c.ws); break;
+    default: k_elem_recover<0><<<c.grid, c.block, c.smem, st>>>(G, t, f, Gin, uh, un, ws, c.ws); break;
   }
 }
 

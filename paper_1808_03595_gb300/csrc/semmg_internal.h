@@ -315,10 +315,12 @@ template <typename T> LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t ca
 template <typename T> void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws,
                                              const LaunchCfg& c, cudaStream_t st);
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm);
-void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f_nodal, double* Z,
+// Gsave (optional): scaled interior eigen-coefficients D^{-1} S^T F_I per element, m^3 each
+void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f_nodal, double* Z, double* Gsave,
                           double* ws, const LaunchCfg& c, cudaStream_t st);
-void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f_nodal, const double* uhat,
-                         double* u_nodal, double* ws, const LaunchCfg& c, cudaStream_t st);
+// Gin (optional): the coefficients saved by launch_elem_condense for the same f_nodal
+void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f_nodal, const double* Gin,
+                         const double* uhat, double* u_nodal, double* ws, const LaunchCfg& c, cudaStream_t st);
 template <typename T> void launch_assemble(const Geo& G, const Tabs<T>& t, const T* F, const T* u,
                                            const T* Z, T* out, int mode, cudaStream_t st);
 // out = F - Hhat u (mode 0) / Hhat u (mode 1) in FP64 arithmetic with FP32 F and out
