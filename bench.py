@@ -40,7 +40,8 @@ METRIC = "unknowns/s per solve to 1e-10 residual (FP64 vs mixed); smoother HBM G
 # timed forms: name -> (precision, outer iteration).  "fp64" is the headline value,
 # "mixed" the mixed-precision line (FP32 smoother and transfers, FP64 residuals).
 FORMS = {"fp64": ("fp64", "mg"), "mixed": ("mixed", "mg"), "mixed_fp32": ("mixed_fp32", "mg"),
-         "kmg_fp64": ("fp64", "kmg"), "kmg_mixed": ("mixed", "kmg")}
+         "mixed_tc": ("mixed_tc", "mg"), "kmg_fp64": ("fp64", "kmg"), "kmg_mixed": ("mixed", "kmg"),
+         "kmg_mixed_tc": ("mixed_tc", "kmg")}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 entry in the peaks file)
 # DRAM bytes (read + write) per k_star<double> launch, averaged over every launch of
 # `bench.py --forms fp64 --no-e2e --no-batch --no-cpu-baseline --steps 1 --warmup 3` under

@@ -65,7 +65,7 @@ enum {
   SEMMG_ERR_CUDA = -3,          /* a CUDA runtime call failed */
   SEMMG_ERR_NOT_CONVERGED = -4, /* max_iter cycles without reaching rtol; info filled */
   SEMMG_ERR_NONFINITE = -5,     /* NaN or Inf in a residual norm */
-  SEMMG_ERR_TIMEOUT = -6,       /* a bounded device wait ran out (batched form) */
+  SEMMG_ERR_TIMEOUT = -6,       /* a bounded device wait ran out (batched form, tensor-core smoother) */
   SEMMG_ERR_NOMEM = -7          /* device or host allocation failed */
 };
 
@@ -77,8 +77,11 @@ enum {
  *   SEMMG_MIXED       FP32 vectors, smoother and transfers in the V-cycle; its
  *                     level residuals F - Hhat u in FP64 arithmetic on the FP32
  *                     values (rounded once to FP32);
- *   SEMMG_MIXED_FP32  the whole V-cycle in FP32, level residuals included. */
-enum { SEMMG_FP64 = 0, SEMMG_MIXED = 1, SEMMG_MIXED_FP32 = 2 };
+ *   SEMMG_MIXED_FP32  the whole V-cycle in FP32, level residuals included;
+ *   SEMMG_MIXED_TC    as SEMMG_MIXED, with the star smoother's 1D transforms on
+ *                     tensor cores (tcgen05, TF32 operands, FP32 accumulation)
+ *                     on the levels with 16 <= p <= 32; other levels as SEMMG_MIXED. */
+enum { SEMMG_FP64 = 0, SEMMG_MIXED = 1, SEMMG_MIXED_FP32 = 2, SEMMG_MIXED_TC = 3 };
 /* outer iteration of semmg_solve and of the batched form */
 enum { SEMMG_SOLVER_MG = 0, SEMMG_SOLVER_KMG = 1 };
 /* element type of a vector argument of smooth / restrict / prolong_add */
@@ -93,7 +96,7 @@ typedef struct {
   int p0;          /* coarse degree, 1 <= p0 <= p (default 2, Sec. 4.1) */
   int nu_pre;      /* pre-smoothing steps per level (default 1, Algorithm 3) */
   int nu_post;     /* post-smoothing steps per level (default 1) */
-  int precision;   /* SEMMG_FP64 (default), SEMMG_MIXED or SEMMG_MIXED_FP32 */
+  int precision;   /* SEMMG_FP64 (default), SEMMG_MIXED, SEMMG_MIXED_FP32 or SEMMG_MIXED_TC */
   int max_iter;    /* iteration cap of semmg_solve (default 50) */
   int solver;      /* SEMMG_SOLVER_MG (Algorithm 4, default) or SEMMG_SOLVER_KMG (Algorithm 5) */
   int nu_vary;     /* 0 (default): nu_pre / nu_post steps on every level; 1: nu_pre 2^(L-l) and

@@ -23,7 +23,7 @@ ERRORS = {
     -7: "SEMMG_ERR_NOMEM",
 }
 SEMMG_ERR_NOT_CONVERGED = -4
-SEMMG_FP64, SEMMG_MIXED, SEMMG_MIXED_FP32 = 0, 1, 2
+SEMMG_FP64, SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC = 0, 1, 2, 3
 SEMMG_SOLVER_MG, SEMMG_SOLVER_KMG = 0, 1
 SEMMG_F64, SEMMG_F32 = 0, 1
 SEMMG_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024

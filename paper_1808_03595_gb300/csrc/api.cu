@@ -35,7 +35,29 @@ struct DevLevel {
   void* Uw = nullptr;
   void* Rw = nullptr;
   LaunchCfg schur64, schur32, star64, star32;
+  LaunchCfg startc;  // tensor-core star smoother (SEMMG_MIXED_TC), when the level allows it
 };
+
+// n_S rounded up to 16, the operand size of the tensor-core star tables
+int tc_pad(int nS) { return (nS + 15) / 16 * 16; }
+
+// IEEE float rounded to TF32 (10 stored mantissa bits), nearest-even
+float round_tf32(double x) {
+  float f = (float)x;
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  if ((b & 0x7F800000u) != 0x7F800000u) {
+    b += 0xFFFu + ((b >> 13) & 1u);
+    b &= ~0x1FFFu;
+  }
+  std::memcpy(&f, &b, 4);
+  return f;
+}
+
+// float offset of (row, k) in a K-major tensor-core operand with K = np
+size_t tc_off(int row, int k, int np) {
+  return ((size_t)(row >> 3) * (np >> 2) + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3);
+}
 
 Geo make_geo(const int n[3], int p, double lam) {
   Geo g{};
@@ -106,6 +128,8 @@ struct semmg_ctx {
   double* dnorm = nullptr;
   double* hnorm = nullptr;  // pinned
   int* star_counter = nullptr;  // work counter of the star kernel (self-resetting)
+  int* dev_err = nullptr;       // set by a kernel whose bounded device wait ran out
+  int* hdev_err = nullptr;      // pinned copy
   // host-buffer solve
   double* fnod = nullptr;
   double* unod = nullptr;
@@ -124,6 +148,7 @@ struct semmg_ctx {
     for (cudaEvent_t e : events) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
     if (hnorm) cudaFreeHost(hnorm);
+    if (hdev_err) cudaFreeHost(hdev_err);
     cudaGetLastError();
   }
 };
@@ -232,6 +257,32 @@ Tabs<T> upload_tabs(semmg_ctx* c, const HostLevel& H, const std::vector<double>*
   return t;
 }
 
+// Tensor-core operand tables T(S) and N(S) per axis and line class (TF32).
+void upload_tc_tables(semmg_ctx* c, const HostLevel& H, Tabs<float>& t, bool* ok) {
+  const int nS = 2 * H.p - 1, np = tc_pad(nS);
+  const size_t tb = (size_t)np * np;
+  for (int d = 0; d < 3; ++d) {
+    const size_t ncls = H.rep[d].size();
+    std::vector<float> T(ncls * tb, 0.0f), N(ncls * tb, 0.0f);
+    for (size_t r = 0; r < ncls; ++r) {
+      const double* S = &H.starS[d][(size_t)H.rep[d][r] * nS * nS];
+      for (int j = 0; j < nS; ++j)
+        for (int e = 0; e < nS; ++e) {
+          const float v = round_tf32(S[j * nS + e]);
+          T[r * tb + tc_off(e, j, np)] = v;
+          N[r * tb + tc_off(j, e, np)] = v;
+        }
+    }
+    float* dT = (float*)dalloc(c, T.size() * sizeof(float));
+    float* dN = (float*)dalloc(c, N.size() * sizeof(float));
+    if (!dT || !dN || cudaMemcpy(dT, T.data(), T.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dN, N.data(), N.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      *ok = false;
+    t.tcT[d] = dT;
+    t.tcN[d] = dN;
+  }
+}
+
 int g_limits_done = 0;
 
 template <typename T> const Tabs<T>& tabs(const semmg_ctx* c, int l);
@@ -309,8 +360,12 @@ void collect_timing(semmg_ctx* c) {
   c->ev_used = 0;
 }
 
-// V-cycle in FP32 (both mixed forms)
+// V-cycle in FP32 (the mixed forms)
 bool cycle32(const semmg_ctx* c) { return c->opts.precision != SEMMG_FP64; }
+// FP32 V-cycle whose level residuals are formed in FP64
+bool resid64(const semmg_ctx* c) {
+  return c->opts.precision == SEMMG_MIXED || c->opts.precision == SEMMG_MIXED_TC;
+}
 
 // out = F - Hhat u (mode 0) or Hhat u (mode 1) on level l.  FP32 vectors of
 // the SEMMG_MIXED form get FP64 arithmetic (FP64 face terms Z, FP64 sums).
@@ -320,7 +375,7 @@ void op_residual(semmg_ctx* c, int l, const T* F, const T* u, T* out, int mode, 
   const double vec = (double)G.size * sizeof(T);
   const double zb = (double)G.nelem * 6 * G.m * G.m * sizeof(T);
   if constexpr (std::is_same<T, float>::value) {
-    if (c->opts.precision == SEMMG_MIXED) {
+    if (resid64(c)) {
       // u widened to FP64 once, then the FP64 kernels; F and the result stay FP32
       const double zb64 = (double)G.nelem * 6 * G.m * G.m * sizeof(double);
       {
@@ -357,7 +412,14 @@ void op_smooth(semmg_ctx* c, int l, const T* r, T* du, int accumulate, cudaStrea
   const double ob = (double)G.nstar * 3 * G.nS * G.nS * sizeof(T);
   {
     Tic t(c, SEMMG_K_STAR, st);
-    launch_star<T>(G, tabs<T>(c, l), r, (T*)c->Obs, (T*)c->wss, star_cfg<T>(c, l), c->star_counter, st);
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (c->dl[l].startc.ok) {
+        launch_star_tc(G, c->dl[l].tf, r, (float*)c->Obs, c->dl[l].startc, c->star_counter, c->dev_err, st);
+        done = true;
+      }
+    }
+    if (!done) launch_star<T>(G, tabs<T>(c, l), r, (T*)c->Obs, (T*)c->wss, star_cfg<T>(c, l), c->star_counter, st);
     t.toc(star_flops(G), vec + ob);
   }
   Tic t(c, SEMMG_K_STAR_GATHER, st);
@@ -545,14 +607,16 @@ void iter_step(semmg_ctx* c, cudaStream_t st) {
 // sqrt of the squared norm left in dnorm by the last iteration (one 8-byte copy + sync)
 int dnorm_sync(semmg_ctx* c, cudaStream_t st, double* out) {
   cudaMemcpyAsync(c->hnorm, c->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(c->hdev_err, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return check_cuda(c, "norm");
   *out = std::sqrt(*c->hnorm);
+  if (*c->hdev_err) return fail(c, SEMMG_ERR_TIMEOUT, "a tensor-core completion wait ran out");
   return check_cuda(c, "norm");
 }
 
 int set_limits(semmg_ctx* c) {
   if (g_limits_done) return SEMMG_OK;
-  if (set_elem_smem_limits() | set_star_smem_limits() | set_transfer_smem_limits())
+  if (set_elem_smem_limits() | set_star_smem_limits() | set_transfer_smem_limits() | set_star_tc_smem_limits())
     return fail(c, SEMMG_ERR_CUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
   g_limits_done = 1;
   return SEMMG_OK;
@@ -628,7 +692,8 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   if (o.p0 < 1 || o.p0 > p) return SEMMG_ERR_UNSUPPORTED;
   if (!(lambda >= 0.0) || !std::isfinite(lambda)) return SEMMG_ERR_INVALID_ARG;
   if (o.nu_pre < 0 || o.nu_post < 0 || o.max_iter < 1) return SEMMG_ERR_INVALID_ARG;
-  if (o.precision != SEMMG_FP64 && o.precision != SEMMG_MIXED && o.precision != SEMMG_MIXED_FP32)
+  if (o.precision != SEMMG_FP64 && o.precision != SEMMG_MIXED && o.precision != SEMMG_MIXED_FP32 &&
+      o.precision != SEMMG_MIXED_TC)
     return SEMMG_ERR_INVALID_ARG;
   if (o.solver != SEMMG_SOLVER_MG && o.solver != SEMMG_SOLVER_KMG) return SEMMG_ERR_INVALID_ARG;
   if (o.nu_vary != 0 && o.nu_vary != 1) return SEMMG_ERR_INVALID_ARG;
@@ -694,6 +759,13 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     if (l >= 1) {
       D.star64 = plan_star<double>(G, c->nsm);
       D.star32 = plan_star<float>(G, c->nsm);
+      if (o.precision == SEMMG_MIXED_TC) {
+        D.startc = plan_star_tc(G, c->nsm);
+        if (D.startc.ok) {
+          upload_tc_tables(c.get(), c->hl[l], D.tf, &ok);
+          if (!ok) return SEMMG_ERR_NOMEM;
+        }
+      }
       wsb = std::max(wsb, D.star64.ws_elems() * sizeof(double));
       wsb = std::max(wsb, D.star32.ws_elems() * sizeof(float));
       obs = std::max(obs, (size_t)(G.nstar * 3 * (int64_t)G.nS * G.nS));
@@ -735,7 +807,7 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
       if (!c->Gs) return SEMMG_ERR_NOMEM;
     }
   }
-  if (o.precision == SEMMG_MIXED) {
+  if (o.precision == SEMMG_MIXED || o.precision == SEMMG_MIXED_TC) {
     c->U64s = (double*)dalloc(c.get(), nL * sizeof(double));
     if (!c->U64s) return SEMMG_ERR_NOMEM;
   }
@@ -756,14 +828,17 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   c->dnorm = (double*)dalloc(c.get(), sizeof(double));
   c->star_counter = (int*)dalloc(c.get(), 4 * sizeof(int));
   if (!c->star_counter || cudaMemset(c->star_counter, 0, 4 * sizeof(int)) != cudaSuccess) return SEMMG_ERR_NOMEM;
+  c->dev_err = (int*)dalloc(c.get(), sizeof(int));
+  if (!c->dev_err || cudaMemset(c->dev_err, 0, sizeof(int)) != cudaSuccess) return SEMMG_ERR_NOMEM;
   if (!c->Zs || !c->Obs || !c->FBs || !c->EBs || !c->wss || !c->Fh || !c->Uh || !c->Rh || !c->cX || !c->cY ||
       !c->F0d || !c->U0d || !c->part || !c->dnorm)
     return SEMMG_ERR_NOMEM;
-  if (cudaMallocHost((void**)&c->hnorm, sizeof(double)) != cudaSuccess) {
+  if (cudaMallocHost((void**)&c->hnorm, sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->hdev_err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
-    c->hnorm = nullptr;
     return SEMMG_ERR_NOMEM;
   }
+  *c->hdev_err = 0;
   *c->hnorm = 0.0;
   for (int l = 0; l < nl; ++l) {
     const size_t n = (size_t)c->geo[l].size;

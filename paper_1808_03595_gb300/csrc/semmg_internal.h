@@ -211,6 +211,11 @@ struct Tabs {
   const T* w1d;    // m+1: smoother weight at offset |j| (Sec. 3.2, weights)
   const T* J;      // (p+1) x (pc+1) interpolation from level-1, row-major; null on level 0
   int pc;
+  // tensor-core star tables (FP32 levels of the SEMMG_MIXED_TC form, else null):
+  // per axis and line class, T(S)[e][j] = S[j][e] and N(S)[j][e] = S[j][e] as
+  // K-major TF32 operands (8 x 4 core matrices), n_S rounded up to 16 and zero-padded
+  const T* tcT[3];
+  const T* tcN[3];
 };
 
 // Coarse fast-diagonalisation tables (level 0, FP64): K_d = n_d p0 - 1
@@ -333,6 +338,12 @@ void launch_unpack(const Geo& G, const double* hat, double* nodal, cudaStream_t 
 template <typename T> LaunchCfg plan_star(const Geo& G, int nsm, size_t cap = 0, int block = 0, int wide = -1);
 template <typename T> void launch_star(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws,
                                        const LaunchCfg& c, int* counter, cudaStream_t st);
+// Star smoother with tensor-core transforms (FP32 / TF32, 15 <= n_S <= 64); err
+// is set to 1 when a tensor-core completion wait runs out.
+LaunchCfg plan_star_tc(const Geo& G, int nsm);
+void launch_star_tc(const Geo& G, const Tabs<float>& t, const float* r, float* Ob, const LaunchCfg& c, int* counter,
+                    int* err, cudaStream_t st);
+int set_star_tc_smem_limits();
 template <typename T> void launch_star_gather(const Geo& G, const T* Ob, T* du, int accumulate,
                                               cudaStream_t st);
 template <typename T> void launch_prolong_add(const Geo& Gc, const Geo& Gf, const Tabs<T>& tf,

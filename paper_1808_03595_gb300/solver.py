@@ -46,7 +46,8 @@ class Context:
         opts.p0 = p0
         opts.nu_pre = nu_pre
         opts.nu_post = nu_post
-        opts.precision = {"fp64": L.SEMMG_FP64, "mixed": L.SEMMG_MIXED, "mixed_fp32": L.SEMMG_MIXED_FP32}[precision]
+        opts.precision = {"fp64": L.SEMMG_FP64, "mixed": L.SEMMG_MIXED, "mixed_fp32": L.SEMMG_MIXED_FP32,
+                          "mixed_tc": L.SEMMG_MIXED_TC}[precision]
         opts.max_iter = max_iter
         opts.solver = {"mg": L.SEMMG_SOLVER_MG, "kmg": L.SEMMG_SOLVER_KMG}[solver]
         opts.nu_vary = 1 if nu_vary else 0

@@ -1,0 +1,91 @@
+"""Star smoother with tcgen05 tensor-core transforms (SEMMG_MIXED_TC).
+
+The four in-plane 1D transforms of Algorithm 1 run as TF32 products with FP32
+accumulation; the eigenspace step stays FP32.  The smoother output is checked
+against the FP64 oracle at a TF32 tolerance (an 11-bit significand: each of the
+four transform stages rounds its operands once), and solves in this form must
+still reach the 1e-10 residual reduction, re-checked with the oracle's own
+condensed residual.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import dense, matfree
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_TF32 = 5e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1808_03595_gb300 import build
+    build.build()
+
+
+def _skel(h, p, seed):
+    m = dense.Mesh(h, p, 0.0)
+    return np.where(matfree.condensed_mask(m), workloads.random_nodal(h, p, seed), 0.0)
+
+
+@pytest.mark.parametrize("p,n,stretched", [(16, 3, False), (16, 2, True), (32, 2, False), (24, 2, False),
+                                           (19, 3, True), (8, 3, False)])
+def test_tc_smoother_matches_oracle(p, n, stretched):
+    from paper_1808_03595_gb300 import Context
+    h = workloads.stretched_widths(n, 11) if stretched else workloads.uniform_widths(n)
+    lam = 2.0
+    m = dense.Mesh(h, p, lam)
+    r = _skel(h, p, 61)
+    ref = matfree.smooth(m, r, chunk=16)
+    mask = matfree.condensed_mask(m)
+    with Context(h, p, lam, p0=2, precision="mixed_tc") as c:
+        rh = c.pack(c.L, torch.as_tensor(r, device="cuda")).float()
+        got = c.unpack(c.L, c.smooth(c.L, rh).double()).cpu().numpy()
+    err = np.abs(got[mask] - ref[mask]).max() / np.abs(ref[mask]).max()
+    assert err < TOL_TF32, err
+    assert np.all(got[~mask] == 0.0)
+
+
+@pytest.mark.parametrize("p", [16, 32])
+def test_tc_solve_reaches_1e10(p):
+    from paper_1808_03595_gb300 import Context
+    h, p, lam, f, p0 = workloads.config(f"helmholtz_8x8x8_p{p}")
+    fd = torch.as_tensor(f, device="cuda")
+    with Context(h, p, lam, p0=p0) as c:
+        _, info64 = c.solve(fd)
+    with Context(h, p, lam, p0=p0, precision="mixed_tc") as c:
+        u, info = c.solve(fd)
+        u = u.cpu().numpy()
+    assert info.status == 0 and info.res_final <= 1e-10 * info.res0
+    assert info.iters <= info64.iters + 2
+    m = dense.Mesh(h, p, lam)
+    mask = matfree.condensed_mask(m)
+    Fh = matfree.condense_rhs(m, f)
+    res = Fh - matfree.apply_condensed(m, np.where(mask, u, 0.0))
+    assert np.linalg.norm(res[mask]) / np.linalg.norm(Fh[mask]) < 2e-10
+
+
+def test_tc_krylov_and_batch():
+    from paper_1808_03595_gb300 import Batch, Context
+    cases = [(workloads.uniform_widths(3), 16, 1.0), (workloads.stretched_widths(2, 5), 20, 10.0)]
+    ctxs, fs, us, refs = [], [], [], []
+    for i, (h, p, lam) in enumerate(cases):
+        c = Context(h, p, lam, p0=2, precision="mixed_tc", solver="kmg")
+        fd = torch.as_tensor(workloads.random_nodal(h, p, 70 + i, "uniform"), device="cuda")
+        u_ref, info = c.solve(fd)
+        assert info.status == 0 and info.res_final <= 1e-10 * info.res0
+        refs.append((u_ref.cpu().numpy(), info.iters))
+        ctxs.append(c)
+        fs.append(fd)
+        us.append(torch.full_like(fd, float("nan")))
+    b = Batch(ctxs, fs, us)
+    rc, infos = b.solve()
+    assert rc == 0
+    for (u_ref, it_ref), u, info in zip(refs, us, infos):
+        assert info.status == 0 and info.iters == it_ref
+        assert np.abs(u.cpu().numpy() - u_ref).max() <= 1e-12 * np.abs(u_ref).max()
+    b.close()
+    for c in ctxs:
+        c.close()
