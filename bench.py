@@ -43,12 +43,14 @@ FORMS = {"fp64": ("fp64", "mg"), "mixed": ("mixed", "mg"), "mixed_fp32": ("mixed
          "mixed_tc": ("mixed_tc", "mg"), "kmg_fp64": ("fp64", "kmg"), "kmg_mixed": ("mixed", "kmg"),
          "kmg_mixed_tc": ("mixed_tc", "kmg")}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 entry in the peaks file)
-# DRAM bytes (read + write) per k_star<double> launch, averaged over every launch of
-# `bench.py --forms fp64 --no-e2e --no-batch --no-cpu-baseline --steps 1 --warmup 3` under
-# ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (profiles/k_star_f64_dram_helmholtz_8x8x8.md);
-# valid only for the star-kernel source it was measured on.
-STAR_TRAFFIC_BYTES = 20.70e6
-STAR_TRAFFIC_SOURCE = "6788e2e1dafe5fd0"
+# DRAM bytes (read + write) per k_star<double> launch of the timed FP64 sweep: ncu
+# --metrics dram__bytes_read.sum,dram__bytes_write.sum per launch of `bench.py --forms fp64
+# --no-e2e --no-batch --no-configs --no-cpu-baseline --steps 1 --warmup 3`, averaged per degree and
+# weighted by the sweep's star launches per degree (28 at p = 4, 20 at 8, 12 at 16, 6 at 32);
+# profiles/k_star_f64_dram_helmholtz_8x8x8.md.  Valid only for the star-kernel source it was
+# measured on (hash below).
+STAR_TRAFFIC_BYTES = 7.896e6
+STAR_TRAFFIC_SOURCE = "60486a70c5a71e71"
 STAR_SOURCES = ("star_kernel.cuh", "kernels_star_f64.cu")
 
 
@@ -390,6 +392,9 @@ def run_semmg(args, world, rank, local, pg):
     }
     if args.batch and rank == 0:
         line["batched"] = run_batch(args, dev, stream, flush)
+        line["batched_kmg"] = run_batch(args, dev, stream, flush, solver="kmg")
+    if args.configs and rank == 0:
+        line["configs"] = run_configs(args, dev, stream, flush)
     if rank == 0 and not args.no_cpu_baseline:
         n, dt, _ = oracle_sample(args.cpu_sample_p)
         line["cpu_baseline"] = {"value": n / dt, "unit": "unknowns/s", "cores": os.cpu_count(), "kind": "oracle",
@@ -403,7 +408,46 @@ def run_semmg(args, world, rank, local, pg):
     return 0
 
 
-def run_batch(args, dev, stream, flush):
+def run_configs(args, dev, stream, flush):
+    """The other workloads of the paper's shape, one solve per form each (not part of `value`):
+    Helmholtz 16^3 at p = 16 (lambda 0 and 100) and Poisson on 6^3 stretched elements at p = 48."""
+    import torch
+    from paper_1808_03595_gb300 import Context
+    out = {}
+    plan = [("helmholtz_16x16x16_p16", 0.0, ["fp64", "mixed", "mixed_tc", "kmg_mixed"]),
+            ("helmholtz_16x16x16_p16", 100.0, ["fp64", "mixed"]),
+            ("poisson_6x6x6_p48_stretched", None, ["fp64", "mixed", "kmg_fp64", "kmg_mixed"])]
+    for name, lam, forms in plan:
+        h, p, lam0, f, p0 = workloads.config(name, lam=lam)
+        lam = lam0 if lam is None else lam
+        fd = torch.as_tensor(f, dtype=torch.float64, device=dev)
+        ud = torch.empty_like(fd)
+        n = int(fd.numel())
+        key = f"{name}_lambda{lam:g}"
+        out[key] = {"unknowns": n}
+        for form in forms:
+            prec, solver = FORMS[form]
+            with Context(h, p, lam, p0=p0, precision=prec, solver=solver) as c:
+                if args.autotune:
+                    c.autotune()
+                for _ in range(args.warmup):
+                    c.solve(fd, out=ud)
+                ms = 0.0
+                for _ in range(args.steps):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    _, info = c.solve(fd, out=ud)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms += e0.elapsed_time(e1)
+                    assert info.res_final <= 1e-10 * info.res0, (key, form)
+            out[key][form] = {"value": n * args.steps / (ms / 1e3), "ms": ms / args.steps, "iterations": info.iters}
+    return out
+
+
+def run_batch(args, dev, stream, flush, solver="mg"):
     """64 independent Helmholtz solves (n ~ U{2..12}, p ~ U{4..24}, lambda = 10^U(-2,3), mixed form) in one
     CUDA graph launch; throughput = total unknowns / graph time."""
     import torch
@@ -411,7 +455,7 @@ def run_batch(args, dev, stream, flush):
     cases = workloads.batch64()
     ctxs, fs, us = [], [], []
     for h, p, lam, f in cases:
-        ctxs.append(Context(h, p, lam, p0=2, precision="mixed"))
+        ctxs.append(Context(h, p, lam, p0=2, precision="mixed", solver=solver))
         fs.append(torch.as_tensor(f, dtype=torch.float64, device=dev))
         us.append(torch.empty_like(fs[-1]))
     t0 = time.perf_counter()
@@ -439,7 +483,7 @@ def run_batch(args, dev, stream, flush):
         iters = [i.iters for i in infos]
     unknowns = sum(int(f.numel()) for f in fs)
     out = {"workload": "batch64 (n~U{2..12}, p~U{4..24}, lambda=10^U(-2,3), f~U(-1,1), seed 1808035955)",
-           "value": unknowns * args.steps / (ms / 1e3), "unit": "unknowns/s", "dtype": "f64+f32",
+           "solver": solver, "value": unknowns * args.steps / (ms / 1e3), "unit": "unknowns/s", "dtype": "f64+f32",
            "solves": len(cases), "unknowns": unknowns, "ms_per_batch": ms / args.steps,
            "graph_nodes": b.graph_nodes(), "capture_s": t_capture, "autotune_s": t_tune,
            "iterations": {"min": min(iters), "max": max(iters), "mean": sum(iters) / len(iters)}}
@@ -463,6 +507,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing (profiling runs)")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="tune launch shapes per degree before the warm-up (outside the timed region)")
+    ap.add_argument("--configs", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the 16^3 p=16 and 6^3 p=48 stretched workloads (reported under configs)")
     ap.add_argument("--batch", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the 64-solve batched graph workload")
     args = ap.parse_args()

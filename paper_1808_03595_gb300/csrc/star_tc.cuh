@@ -106,10 +106,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// round a finite float to TF32 (10 stored mantissa bits), nearest-even, with
+// integer operations (the conversion instruction issues on a slow pipe)
 __device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  uint32_t b = __float_as_uint(x);
+  b += 0xFFFu + ((b >> 13) & 1u);
+  return __uint_as_float(b & ~0x1FFFu);
 }
 
 // float offset of element (row, k) in a K-major operand with K = np columns
