@@ -26,9 +26,15 @@ from .gll import gll, interp_matrix, standard_matrices, weight_poly
 
 
 class Mesh:
-    """Tensor-product mesh: per-axis element widths h[d] (length n_d), degree p, lambda."""
+    """Tensor-product mesh: per-axis element widths h[d] (length n_d), degree p, lambda.
 
-    def __init__(self, h, p, lam):
+    bc: boundary condition of the faces -x1, +x1, -x2, +x2, -x3, +x3, each "D"
+    (homogeneous Dirichlet, the default) or "N" (homogeneous Neumann, Sec. 3.3:
+    the boundary nodes are unknowns and the ghost element beyond the face is
+    decoupled).
+    """
+
+    def __init__(self, h, p, lam, bc=None):
         self.h = [np.asarray(hd, dtype=float).copy() for hd in h]
         if len(self.h) != 3:
             raise ValueError("need three width arrays")
@@ -38,9 +44,18 @@ class Mesh:
         self.N = [nd * self.p + 1 for nd in self.n]
         # vertex coordinates along each axis, origin at 0
         self.X = [np.concatenate([[0.0], np.cumsum(hd)]) for hd in self.h]
+        self.bc = tuple(bc) if bc is not None else ("D",) * 6
+        if len(self.bc) != 6 or any(b not in ("D", "N") for b in self.bc):
+            raise ValueError("bc: six entries, each 'D' or 'N'")
 
     def with_degree(self, p):
-        return Mesh(self.h, p, self.lam)
+        return Mesh(self.h, p, self.lam, self.bc)
+
+    def g_range(self, d):
+        """Global node indices [lo, hi] along axis d that are unknowns (not Dirichlet)."""
+        lo = 1 if self.bc[2 * d] == "D" else 0
+        hi = self.N[d] - 2 if self.bc[2 * d + 1] == "D" else self.N[d] - 1
+        return lo, hi
 
     @property
     def shape(self):
@@ -115,7 +130,8 @@ def index_sets(mesh):
     on_bdry = np.zeros(mesh.shape, bool)
     skel = np.zeros(mesh.shape, bool)
     for d in range(3):
-        on_bdry |= (Gs[d] == 0) | (Gs[d] == mesh.N[d] - 1)
+        lo, hi = mesh.g_range(d)
+        on_bdry |= (Gs[d] < lo) | (Gs[d] > hi)
         skel |= (Gs[d] % p == 0)
     free = ~on_bdry
     B = np.flatnonzero((free & skel).ravel())
@@ -234,9 +250,10 @@ def assembled_1d(mesh, d):
 def star_line_table(mesh, d, c):
     """1D block eigen-table of vertex line c along axis d (Sec. 3.2 and 3.3).
 
-    Block nodes g = c p + j, j = -(p-1)..(p-1).  A node is active when it is a
-    free node of the domain (1 <= g <= N_d - 2); inactive nodes (ghost element,
-    Dirichlet vertex) are decoupled by padding S with identity and Lambda with 1.
+    Block nodes g = c p + j, j = -(p-1)..(p-1).  A node is active when it is an
+    unknown of the domain (inside the mesh and not on a Dirichlet face);
+    inactive nodes (ghost element, Dirichlet vertex) are decoupled by padding S
+    with identity and Lambda with 1.
     Returns S (n_S x n_S) with S^T M S = I, S^T L S = Lambda on the active block,
     Lambda (n_S) and the active mask.
     """
@@ -245,7 +262,8 @@ def star_line_table(mesh, d, c):
     nS = 2 * m + 1
     Mg, Lg = assembled_1d(mesh, d)
     g = c * p + np.arange(-m, m + 1)
-    active = (g >= 1) & (g <= mesh.N[d] - 2)
+    lo, hi = mesh.g_range(d)
+    active = (g >= lo) & (g <= hi)
     S = np.eye(nS)
     lam = np.ones(nS)
     ia = np.flatnonzero(active)

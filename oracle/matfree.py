@@ -64,13 +64,15 @@ def assemble_blocks(blocks, mesh):
 
 
 def masks(mesh):
-    """Boolean nodal masks: skeleton (element boundaries) and free (not Dirichlet)."""
+    """Boolean nodal masks: skeleton (element boundaries) and free (not on a Dirichlet face)."""
     p = mesh.p
     G = np.meshgrid(np.arange(mesh.N[2]), np.arange(mesh.N[1]), np.arange(mesh.N[0]), indexing="ij")
     g3, g2, g1 = G
     skel = (g1 % p == 0) | (g2 % p == 0) | (g3 % p == 0)
-    free = ((g1 > 0) & (g1 < mesh.N[0] - 1) & (g2 > 0) & (g2 < mesh.N[1] - 1)
-            & (g3 > 0) & (g3 < mesh.N[2] - 1))
+    free = np.ones(mesh.shape, bool)
+    for d, g in enumerate((g1, g2, g3)):
+        lo, hi = mesh.g_range(d)
+        free &= (g >= lo) & (g <= hi)
     return skel, free
 
 

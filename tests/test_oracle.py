@@ -20,12 +20,18 @@ def _rng(seed=0):
     return np.random.default_rng(seed)
 
 
-def _mesh_small(p=4, lam=1.5, stretched=True):
+# boundary conditions of the faces -x1, +x1, -x2, +x2, -x3, +x3 (Sec. 3.3)
+DIRICHLET = ("D",) * 6
+MIXED_BC = ("N", "D", "D", "N", "N", "N")
+NEUMANN = ("N",) * 6
+
+
+def _mesh_small(p=4, lam=1.5, stretched=True, bc=None):
     if stretched:
         h = [np.full(3, 1 / 3), np.array([0.2, 0.5, 0.3]), np.array([0.7, 0.3])]
     else:
         h = [np.full(3, 1 / 3)] * 3
-    return dense.Mesh(h, p, lam)
+    return dense.Mesh(h, p, lam, bc)
 
 
 # ---------------------------------------------------------------- 1D basis (Sec. 2.1)
@@ -108,9 +114,10 @@ def test_assembly_is_kronecker_sum():
     np.testing.assert_allclose(H, Hk, atol=1e-13)
 
 
-@pytest.mark.parametrize("p,lam", [(2, 0.0), (4, 1.5), (5, 100.0)])
-def test_condensed_operator_spd_and_matrix_free(p, lam):
-    mesh = _mesh_small(p=p, lam=lam)
+@pytest.mark.parametrize("p,lam,bc", [(2, 0.0, DIRICHLET), (4, 1.5, DIRICHLET), (5, 100.0, DIRICHLET),
+                                      (3, 0.0, MIXED_BC), (4, 2.0, NEUMANN)])
+def test_condensed_operator_spd_and_matrix_free(p, lam, bc):
+    mesh = _mesh_small(p=p, lam=lam, bc=bc)
     cond = dense.Condensed(mesh)
     Hh = cond.Hhat
     assert np.abs(Hh - Hh.T).max() < 1e-12 * np.abs(Hh).max()
@@ -124,8 +131,9 @@ def test_condensed_operator_spd_and_matrix_free(p, lam):
     assert np.all(y[~matfree.condensed_mask(mesh)] == 0)
 
 
-def test_condensation_reproduces_full_solution():
-    mesh = _mesh_small(p=4, lam=0.5)
+@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC])
+def test_condensation_reproduces_full_solution(bc):
+    mesh = _mesh_small(p=4, lam=0.5, bc=bc)
     cond = dense.Condensed(mesh)
     f = _rng(3).standard_normal(mesh.shape)
     F = cond.load(f)
@@ -165,12 +173,43 @@ def test_manufactured_solution_spectral(p):
     assert err < bound, (p, err)
 
 
+@pytest.mark.parametrize("bc,kind", [(NEUMANN, "ccc"), (("D", "D", "N", "N", "N", "N"), "scc"),
+                                     (("N", "D", "N", "D", "D", "N"), "mixed")])
+def test_manufactured_solution_neumann(bc, kind):
+    # homogeneous Neumann faces (Sec. 3.3): u = cos(pi x) cos(pi y) cos(pi z) has zero normal
+    # derivative on every face of the unit cube; sin in x for Dirichlet x-faces; and a
+    # quarter-wave product for faces that alternate Neumann / Dirichlet
+    p = 8
+    mesh = dense.Mesh([np.full(3, 1 / 3)] * 3, p, 1.0, bc)
+    x = mesh.node_coords()
+    X3, X2, X1 = np.meshgrid(x[2], x[1], x[0], indexing="ij")
+    pi = np.pi
+    if kind == "ccc":
+        ue, k2 = np.cos(pi * X1) * np.cos(pi * X2) * np.cos(pi * X3), 3 * pi**2
+    elif kind == "scc":
+        ue, k2 = np.sin(pi * X1) * np.cos(pi * X2) * np.cos(pi * X3), 3 * pi**2
+    else:
+        ue, k2 = np.cos(pi * X1 / 2) * np.cos(pi * X2 / 2) * np.sin(pi * X3 / 2), 3 * (pi / 2) ** 2
+    f = (mesh.lam + k2) * ue
+    u, it, hist = matfree.solve(mesh, f, p0=1)
+    assert hist[-1] <= 1e-10 * hist[0]
+    assert np.abs(u - ue).max() < 1e-9
+    # the Neumann boundary nodes are unknowns, the Dirichlet ones stay zero
+    skel, free = matfree.masks(mesh)
+    assert np.all(u[~free] == 0.0)
+    assert np.count_nonzero(free) > np.prod([Nd - 2 for Nd in mesh.N])
+
+
 # ---------------------------------------------------------------- stars (Sec. 2.3, 3)
 
-@pytest.mark.parametrize("c", [(1, 1, 1), (0, 1, 1), (3, 0, 2), (0, 0, 0), (3, 3, 2), (2, 1, 0)])
-def test_alg1_is_inverse_of_condensed_star(c):
-    # (dense Hhat_i) x (Algorithm 1 applied to each unit vector) = I, interior and boundary stars
-    mesh = _mesh_small(p=4, lam=0.7)
+@pytest.mark.parametrize("c,bc", [((1, 1, 1), DIRICHLET), ((0, 1, 1), DIRICHLET), ((3, 0, 2), DIRICHLET),
+                                  ((0, 0, 0), DIRICHLET), ((3, 3, 2), DIRICHLET), ((2, 1, 0), DIRICHLET),
+                                  ((0, 1, 1), MIXED_BC), ((0, 2, 2), MIXED_BC), ((3, 0, 0), MIXED_BC),
+                                  ((0, 0, 0), NEUMANN), ((3, 3, 2), NEUMANN)])
+def test_alg1_is_inverse_of_condensed_star(c, bc):
+    # (dense Hhat_i) x (Algorithm 1 applied to each unit vector) = I, interior and boundary
+    # stars; with Neumann faces the boundary vertex and face nodes belong to the star
+    mesh = _mesh_small(p=4, lam=0.7, bc=bc)
     cond = dense.Condensed(mesh)
     pos, j = dense.star_positions(mesh, cond.B, c)
     Hi = cond.Hhat[np.ix_(pos, pos)]
@@ -192,8 +231,9 @@ def test_alg1_is_inverse_of_condensed_star(c):
     np.testing.assert_allclose(Hi @ X, np.eye(len(pos)), atol=1e-11)
 
 
-def test_star_tables_generalized_eigen():
-    mesh = _mesh_small(p=5)
+@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC])
+def test_star_tables_generalized_eigen(bc):
+    mesh = _mesh_small(p=5, bc=bc)
     for d in range(3):
         Mg, Lg = dense.assembled_1d(mesh, d)
         for c in range(mesh.n[d] + 1):
@@ -206,8 +246,9 @@ def test_star_tables_generalized_eigen():
             np.testing.assert_allclose(Sa.T @ La @ Sa, np.diag(lam[ia]), atol=1e-10 * lam.max())
 
 
-def test_weights_partition_of_unity():
-    mesh = _mesh_small(p=6)
+@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC, NEUMANN])
+def test_weights_partition_of_unity(bc):
+    mesh = _mesh_small(p=6, bc=bc)
     cond = dense.Condensed(mesh, dense=False)
     W = np.zeros(len(cond.B))
     for c in dense.star_vertices(mesh):
@@ -216,9 +257,10 @@ def test_weights_partition_of_unity():
     np.testing.assert_allclose(W, 1.0, atol=1e-13)
 
 
-@pytest.mark.parametrize("p,lam", [(3, 0.0), (4, 2.0)])
-def test_smoother_alg1_equals_dense_inverse(p, lam):
-    mesh = _mesh_small(p=p, lam=lam)
+@pytest.mark.parametrize("p,lam,bc", [(3, 0.0, DIRICHLET), (4, 2.0, DIRICHLET), (3, 0.5, MIXED_BC),
+                                      (4, 1.0, NEUMANN)])
+def test_smoother_alg1_equals_dense_inverse(p, lam, bc):
+    mesh = _mesh_small(p=p, lam=lam, bc=bc)
     cond = dense.Condensed(mesh)
     r = _rng(5).standard_normal(len(cond.B))
     d_dense = dense.smoother_dense(mesh, cond, r)
@@ -233,9 +275,9 @@ def test_smoother_alg1_equals_dense_inverse(p, lam):
 
 # ---------------------------------------------------------------- transfers (Sec. 4.1)
 
-@pytest.mark.parametrize("pc,pf", [(1, 2), (2, 4), (4, 6)])
-def test_transfers_adjoint_and_explicit(pc, pf):
-    mesh_f = _mesh_small(p=pf)
+@pytest.mark.parametrize("pc,pf,bc", [(1, 2, DIRICHLET), (2, 4, DIRICHLET), (4, 6, DIRICHLET), (2, 4, MIXED_BC)])
+def test_transfers_adjoint_and_explicit(pc, pf, bc):
+    mesh_f = _mesh_small(p=pf, bc=bc)
     mesh_c = mesh_f.with_degree(pc)
     cf = dense.Condensed(mesh_f, dense=False)
     cc = dense.Condensed(mesh_c, dense=False)
@@ -276,9 +318,9 @@ def test_level_degrees():
     assert dense.level_degrees(2, 2) == [2]
 
 
-@pytest.mark.parametrize("p0", [1, 2])
-def test_vcycle_o2_equals_o1(p0):
-    mesh = _mesh_small(p=4, lam=1.0)
+@pytest.mark.parametrize("p0,bc", [(1, DIRICHLET), (2, DIRICHLET), (1, MIXED_BC), (2, NEUMANN)])
+def test_vcycle_o2_equals_o1(p0, bc):
+    mesh = _mesh_small(p=4, lam=1.0, bc=bc)
     hier = dense.Hierarchy(mesh, p0=p0)
     mg = matfree.MG(mesh, p0=p0)
     B = hier.conds[-1].B
@@ -294,8 +336,9 @@ def test_vcycle_o2_equals_o1(p0):
     assert np.abs(v1 - v2).max() < 1e-12 * np.abs(v1).max()
 
 
-def test_mg_solve_matches_direct_solve():
-    mesh = _mesh_small(p=5, lam=0.0)
+@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC])
+def test_mg_solve_matches_direct_solve(bc):
+    mesh = _mesh_small(p=5, lam=0.0, bc=bc)
     cond = dense.Condensed(mesh)
     f = _rng(11).uniform(-1, 1, mesh.shape)
     F = cond.load(f)
