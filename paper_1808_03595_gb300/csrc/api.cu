@@ -59,8 +59,9 @@ size_t tc_off(int row, int k, int np) {
   return ((size_t)(row >> 3) * (np >> 2) + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3);
 }
 
-Geo make_geo(const int n[3], int p, double lam) {
+Geo make_geo(const int n[3], int p, double lam, const int bc[6]) {
   Geo g{};
+  for (int f = 0; f < 6; ++f) g.dir[f] = bc[f] == SEMMG_BC_DIRICHLET ? 1 : 0;
   g.p = p;
   g.m = p - 1;
   g.nS = 2 * p - 1;
@@ -697,6 +698,12 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     return SEMMG_ERR_INVALID_ARG;
   if (o.solver != SEMMG_SOLVER_MG && o.solver != SEMMG_SOLVER_KMG) return SEMMG_ERR_INVALID_ARG;
   if (o.nu_vary != 0 && o.nu_vary != 1) return SEMMG_ERR_INVALID_ARG;
+  bool any_dirichlet = false;
+  for (int f = 0; f < 6; ++f) {
+    if (mesh->bc[f] != SEMMG_BC_DIRICHLET && mesh->bc[f] != SEMMG_BC_NEUMANN) return SEMMG_ERR_INVALID_ARG;
+    any_dirichlet |= mesh->bc[f] == SEMMG_BC_DIRICHLET;
+  }
+  if (!any_dirichlet && !(lambda > 0.0)) return SEMMG_ERR_UNSUPPORTED;  // singular (pure Neumann, lambda = 0)
   for (int d = 0; d < 3; ++d) {
     if (mesh->n[d] < 1 || !mesh->h[d]) return SEMMG_ERR_INVALID_ARG;
     if ((int64_t)mesh->n[d] * p + 1 >= (1 << 20)) return SEMMG_ERR_UNSUPPORTED;
@@ -725,16 +732,16 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   c->hl.resize(nl);
   c->dl.resize(nl);
   for (int l = 0; l < nl; ++l) {
-    c->geo[l] = make_geo(mesh->n, degs[l], lambda);
+    c->geo[l] = make_geo(mesh->n, degs[l], lambda, mesh->bc);
     c->hl[l].p = degs[l];
     c->hl[l].lam = lambda;
-    build_level_tables(c->hl[l], c->h);
+    build_level_tables(c->hl[l], c->h, mesh->bc);
     if (l > 0) {
       lagrange_interp(c->hl[l - 1].x, c->hl[l].x, c->hl[l].J);
       c->hl[l].pc = degs[l - 1];
     }
   }
-  build_coarse_tables(degs[0], c->h, c->hc);
+  build_coarse_tables(degs[0], c->h, mesh->bc, c->hc);
   bool ok = true;
   for (int l = 0; l < nl; ++l) {
     c->dl[l].td = upload_tabs<double>(c.get(), c->hl[l], c->h, &ok);
@@ -742,6 +749,7 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   }
   for (int d = 0; d < 3; ++d) {
     c->ct.K[d] = c->hc.K[d];
+    c->ct.g0[d] = c->hc.g0[d];
     c->ct.S[d] = upload<double>(c.get(), c->hc.S[d], &ok);
     c->ct.lam[d] = upload<double>(c.get(), c->hc.lam[d], &ok);
   }

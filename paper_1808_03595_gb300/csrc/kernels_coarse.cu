@@ -4,8 +4,8 @@
 // assembled 1D matrices, so it is inverted by global fast diagonalisation
 // (eq. fast_diagonalization on the whole domain):
 //   H^{-1} = (S3(x)S2(x)S1) (lam + Lam1 + Lam2 + Lam3)^{-1} (S3(x)S2(x)S1)^T
-// with S_d^T Mg_d S_d = I, S_d^T Lg_d S_d = Lam_d on the K_d = n_d p0 - 1
-// interior grid points of axis d.  The condensed right-hand side is embedded
+// with S_d^T Mg_d S_d = I, S_d^T Lg_d S_d = Lam_d on the K_d grid points of
+// axis d that are unknowns (all but the points on a Dirichlet face).  The condensed right-hand side is embedded
 // with zeros at the element-interior nodes; by the embedding argument of
 // Sec. 3.1 the skeleton part of the full solution is the condensed solution.
 // At p0 = 1 there are no interior nodes and this is the condensed system itself.
@@ -28,7 +28,7 @@ __global__ void k_coarse_embed(Geo G, CoarseTabs ct, const double* __restrict__ 
   const int64_t n = (int64_t)K1 * K2 * K3;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int k1 = (int)(i % K1), k2 = (int)((i / K1) % K2), k3 = (int)(i / ((int64_t)K1 * K2));
-    const int64_t s = skel_index(G, k1 + 1, k2 + 1, k3 + 1);
+    const int64_t s = skel_index(G, k1 + ct.g0[0], k2 + ct.g0[1], k3 + ct.g0[2]);
     X[i] = s >= 0 ? F0[s] : 0.0;
   }
 }
@@ -62,7 +62,7 @@ __global__ void k_coarse_extract(Geo G, CoarseTabs ct, const double* __restrict_
   const int64_t n = (int64_t)K1 * K2 * K3;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int k1 = (int)(i % K1), k2 = (int)((i / K1) % K2), k3 = (int)(i / ((int64_t)K1 * K2));
-    const int64_t s = skel_index(G, k1 + 1, k2 + 1, k3 + 1);
+    const int64_t s = skel_index(G, k1 + ct.g0[0], k2 + ct.g0[1], k3 + ct.g0[2]);
     if (s >= 0) U0[s] = X[i];
   }
 }

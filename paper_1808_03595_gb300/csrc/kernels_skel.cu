@@ -39,6 +39,7 @@ __device__ __forceinline__ T mass1d(const Geo& G, const Tabs<T>& t, int d, int g
 template <typename T>
 __device__ T line_sum(const Geo& G, const Tabs<T>& t, const T* __restrict__ u, int64_t s, int type, const int* g,
                       int d, bool other) {
+  const int nd = ncount(G, d);
   const int p = G.p;
   const int a = divp(G, g[d]), q = g[d] - a * p;
   int gg[3] = {g[0], g[1], g[2]};
@@ -58,23 +59,35 @@ __device__ T line_sum(const Geo& G, const Tabs<T>& t, const T* __restrict__ u, i
     for (int j = 1; j < p; ++j) acc += row[j] * ur[(int64_t)(j - 1) * st];
     return k * acc;
   }
-  // on vertex plane c = a (interior plane: 1 <= c <= n_d - 1)
-  const T kL = t.hx[d][6 * (a - 1) + 1], kR = t.hx[d][6 * a + 1];  // 2 / h on either side
+  // on vertex plane c = a; the element on either side may be missing at a
+  // (Neumann) face of the domain: 0 <= c <= n_d
+  const bool hasL = a > 0, hasR = a < nd;
+  const T kL = hasL ? t.hx[d][6 * (a - 1) + 1] : (T)0, kR = hasR ? t.hx[d][6 * a + 1] : (T)0;  // 2 / h
   T acc = (kL * Ls[p * P1 + p] + kR * Ls[0]) * u[s];
-  gg[d] = (a - 1) * p;
-  acc += kL * Ls[p * P1 + 0] * u[skel_index(G, gg[0], gg[1], gg[2])];
-  gg[d] = (a + 1) * p;
-  acc += kR * Ls[0 * P1 + p] * u[skel_index(G, gg[0], gg[1], gg[2])];
+  if (hasL) {
+    gg[d] = (a - 1) * p;
+    acc += kL * Ls[p * P1 + 0] * u[skel_index(G, gg[0], gg[1], gg[2])];
+  }
+  if (hasR) {
+    gg[d] = (a + 1) * p;
+    acc += kR * Ls[0 * P1 + p] * u[skel_index(G, gg[0], gg[1], gg[2])];
+  }
   if (other && p > 1) {
-    int rt;
-    gg[d] = (a - 1) * p + 1;
-    const int64_t bL = skel_index(G, gg[0], gg[1], gg[2], &rt);
-    const int st = run_stride(G, rt, d);
     T sL = 0, sR = 0;
-    for (int j = 1; j < p; ++j) sL += Ls[p * P1 + j] * u[bL + (int64_t)(j - 1) * st];
-    gg[d] = a * p + 1;
-    const int64_t bR = skel_index(G, gg[0], gg[1], gg[2]);
-    for (int j = 1; j < p; ++j) sR += Ls[0 * P1 + j] * u[bR + (int64_t)(j - 1) * st];
+    if (hasL) {
+      int rt;
+      gg[d] = (a - 1) * p + 1;
+      const int64_t bL = skel_index(G, gg[0], gg[1], gg[2], &rt);
+      const int st = run_stride(G, rt, d);
+      for (int j = 1; j < p; ++j) sL += Ls[p * P1 + j] * u[bL + (int64_t)(j - 1) * st];
+    }
+    if (hasR) {
+      int rt;
+      gg[d] = a * p + 1;
+      const int64_t bR = skel_index(G, gg[0], gg[1], gg[2], &rt);
+      const int st = run_stride(G, rt, d);
+      for (int j = 1; j < p; ++j) sR += Ls[0 * P1 + j] * u[bR + (int64_t)(j - 1) * st];
+    }
     acc += kL * sL + kR * sR;
   }
   return acc;
@@ -94,11 +107,18 @@ __device__ __forceinline__ T face_z(const Geo& G, const T* __restrict__ Z, int t
   const int ia = (d == 0) ? 1 : 0, ib = (d == 2) ? 1 : 2;
   const int64_t loc = (int64_t)(q[ib] - 1) * m + (q[ia] - 1);
   int e[3] = {a[0], a[1], a[2]};
-  e[d] = a[d] - 1;  // element on the minus side: this face is its side p
-  const int64_t em = ((int64_t)e[2] * G.n2 + e[1]) * G.n1 + e[0];
-  e[d] = a[d];      // element on the plus side: side 0
-  const int64_t ep = ((int64_t)e[2] * G.n2 + e[1]) * G.n1 + e[0];
-  return Z[(em * 6 + 2 * d + 1) * mm + loc] + Z[(ep * 6 + 2 * d) * mm + loc];
+  T z = 0;
+  if (a[d] > 0) {  // element on the minus side (absent at the low face of the domain): this face is its side p
+    e[d] = a[d] - 1;
+    const int64_t em = ((int64_t)e[2] * G.n2 + e[1]) * G.n1 + e[0];
+    z += Z[(em * 6 + 2 * d + 1) * mm + loc];
+  }
+  if (a[d] < ncount(G, d)) {  // element on the plus side (absent at the high face): side 0
+    e[d] = a[d];
+    const int64_t ep = ((int64_t)e[2] * G.n2 + e[1]) * G.n1 + e[0];
+    z += Z[(ep * 6 + 2 * d) * mm + loc];
+  }
+  return z;
 }
 
 // mode 0: out = F - Hhat u;  mode 1: out = Hhat u.  Arithmetic in T, F and out

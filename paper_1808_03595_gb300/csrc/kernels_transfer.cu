@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_faces(Geo Gc, Geo Gf, cons
   const int d = f < n0 ? 0 : (f < n0 + n1 ? 1 : 2);
   f -= d == 0 ? 0 : (d == 1 ? n0 : n0 + n1);
   const FaceRef fr = face_ref(Gf, d, f);
-  if (fr.c == 0 || fr.c == plane_count(Gf, d) - 1) return;  // Dirichlet face
+  if (dir_plane(Gf, d, fr.c)) return;  // Dirichlet face
   for (int idx = threadIdx.x; idx < P1 * P1; idx += blockDim.x) {
     const int ib = idx / P1, ia = idx - ib * P1;
     int g[3];
@@ -144,7 +144,7 @@ __global__ void k_prolong_edges(Geo Gc, Geo Gf, const T* __restrict__ J, const T
     int ca, cb, e;
     edge_ref(Gf, d, k, &ca, &cb, &e);
     const int ax_a = d == 0 ? 1 : 0, ax_b = d == 2 ? 1 : 2;
-    if (ca == 0 || ca == plane_count(Gf, ax_a) - 1 || cb == 0 || cb == plane_count(Gf, ax_b) - 1) continue;
+    if (dir_plane(Gf, ax_a, ca) || dir_plane(Gf, ax_b, cb)) continue;  // on a Dirichlet face
     int g[3];
     g[ax_a] = ca * pc;
     g[ax_b] = cb * pc;
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict_faces(Geo Gf, Geo Gc, con
   const int64_t fnum = blockIdx.x;  // FB face numbers follow the concatenated groups
   T* fb = FB + fnum * (int64_t)P1 * P1;
   T* rcf = rc + face_group_offset(Gc, d) + f * (int64_t)mc * mc;
-  if (fr.c == 0 || fr.c == plane_count(Gf, d) - 1) {
+  if (dir_plane(Gf, d, fr.c)) {
     for (int idx = threadIdx.x; idx < P1 * P1; idx += blockDim.x) fb[idx] = 0;
     for (int idx = threadIdx.x; idx < mc * mc; idx += blockDim.x) rcf[idx] = 0;
     return;
@@ -225,7 +225,7 @@ __global__ void k_restrict_edges(Geo Gf, Geo Gc, const T* __restrict__ J, const 
     const T* re = rf + edge_group_offset(Gf, d) + k * mf;
     T s = 0;
     for (int I = 0; I < mf; ++I) s += J[(I + 1) * P1 + i] * re[I];
-    EB[kk * P1 + i] = s;  // boundary edges hold zero residual, so their entries are zero
+    EB[kk * P1 + i] = s;  // edges on Dirichlet faces hold zero residual, so their entries are zero
   }
 }
 
@@ -248,7 +248,7 @@ __global__ void k_restrict_gather(Geo Gf, Geo Gc, const T* __restrict__ rf, T* _
       edge_ref(Gc, d, k, &ca, &cb, &e);
       const int ax_a = d == 0 ? 1 : 0, ax_b = d == 2 ? 1 : 2;
       T* out = rc + edge_group_offset(Gc, d) + k * mc + (ic - 1);
-      if (ca == 0 || ca == plane_count(Gc, ax_a) - 1 || cb == 0 || cb == plane_count(Gc, ax_b) - 1) {
+      if (dir_plane(Gc, ax_a, ca) || dir_plane(Gc, ax_b, cb)) {
         *out = 0;
         continue;
       }
@@ -277,7 +277,7 @@ __global__ void k_restrict_gather(Geo Gf, Geo Gc, const T* __restrict__ rf, T* _
       const int64_t v = t - nE;
       const int c[3] = {(int)(v % Gc.nv1), (int)((v / Gc.nv1) % Gc.nv2), (int)(v / ((int64_t)Gc.nv1 * Gc.nv2))};
       T* out = rc + Gc.oV + v;
-      if (c[0] == 0 || c[0] == Gc.n1 || c[1] == 0 || c[1] == Gc.n2 || c[2] == 0 || c[2] == Gc.n3) {
+      if (dir_plane(Gc, 0, c[0]) || dir_plane(Gc, 1, c[1]) || dir_plane(Gc, 2, c[2])) {
         *out = 0;
         continue;
       }

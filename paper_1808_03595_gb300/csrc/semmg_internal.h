@@ -27,7 +27,15 @@ struct Geo {
   int64_t nelem, nstar;
   uint64_t pinv;  // ceil(2^32 / p): exact division g / p for 0 <= g < 2^20
   double lam;
+  unsigned char dir[6];  // faces -x1, +x1, -x2, +x2, -x3, +x3: 1 = Dirichlet, 0 = Neumann
 };
+
+SEMMG_HD int ncount(const Geo& G, int d) { return d == 0 ? G.n1 : (d == 1 ? G.n2 : G.n3); }
+
+// Whether vertex plane c along axis d is a Dirichlet face of the domain.
+SEMMG_HD bool dir_plane(const Geo& G, int d, int c) {
+  return (c == 0 && G.dir[2 * d]) || (c == ncount(G, d) && G.dir[2 * d + 1]);
+}
 
 enum EntityType { ENT_F1 = 0, ENT_F2, ENT_F3, ENT_E1, ENT_E2, ENT_E3, ENT_V, ENT_NONE };
 
@@ -87,7 +95,7 @@ SEMMG_HD int run_stride(const Geo& G, int type, int d) {
 }
 
 // Decode a skeleton slot into its global node coordinates; returns the entity
-// type and whether the node lies on the Dirichlet boundary.
+// type and whether the node lies on a Dirichlet face.
 SEMMG_HD int skel_decode(const Geo& G, int64_t s, int* g, bool* bdry) {
   const int p = G.p, m = G.m;
   const int64_t mm = (int64_t)m * m;
@@ -102,7 +110,7 @@ SEMMG_HD int skel_decode(const Geo& G, int64_t s, int* g, bool* bdry) {
     const int64_t f2 = f / G.nv1;
     const int a2 = (int)(f2 % G.n2), a3 = (int)(f2 / G.n2);
     g[0] = c1 * p; g[1] = a2 * p + i2 + 1; g[2] = a3 * p + i3 + 1;
-    *bdry = (c1 == 0 || c1 == G.n1);
+    *bdry = dir_plane(G, 0, c1);
   } else if (s < G.oF3) {
     t = ENT_F2;
     int64_t r = s - G.oF2;
@@ -113,7 +121,7 @@ SEMMG_HD int skel_decode(const Geo& G, int64_t s, int* g, bool* bdry) {
     c2 = (int)(f2 % G.nv2);
     const int a3 = (int)(f2 / G.nv2);
     g[0] = a1 * p + i1 + 1; g[1] = c2 * p; g[2] = a3 * p + i3 + 1;
-    *bdry = (c2 == 0 || c2 == G.n2);
+    *bdry = dir_plane(G, 1, c2);
   } else if (s < G.oE1) {
     t = ENT_F3;
     int64_t r = s - G.oF3;
@@ -124,7 +132,7 @@ SEMMG_HD int skel_decode(const Geo& G, int64_t s, int* g, bool* bdry) {
     const int a2 = (int)(f2 % G.n2);
     c3 = (int)(f2 / G.n2);
     g[0] = a1 * p + i1 + 1; g[1] = a2 * p + i2 + 1; g[2] = c3 * p;
-    *bdry = (c3 == 0 || c3 == G.n3);
+    *bdry = dir_plane(G, 2, c3);
   } else if (s < G.oE2) {
     t = ENT_E1;
     int64_t r = s - G.oE1;
@@ -135,7 +143,7 @@ SEMMG_HD int skel_decode(const Geo& G, int64_t s, int* g, bool* bdry) {
     c2 = (int)(e2 % G.nv2);
     c3 = (int)(e2 / G.nv2);
     g[0] = a1 * p + i1 + 1; g[1] = c2 * p; g[2] = c3 * p;
-    *bdry = (c2 == 0 || c2 == G.n2 || c3 == 0 || c3 == G.n3);
+    *bdry = dir_plane(G, 1, c2) || dir_plane(G, 2, c3);
   } else if (s < G.oE3) {
     t = ENT_E2;
     int64_t r = s - G.oE2;
@@ -146,7 +154,7 @@ SEMMG_HD int skel_decode(const Geo& G, int64_t s, int* g, bool* bdry) {
     const int a2 = (int)(e2 % G.n2);
     c3 = (int)(e2 / G.n2);
     g[0] = c1 * p; g[1] = a2 * p + i2 + 1; g[2] = c3 * p;
-    *bdry = (c1 == 0 || c1 == G.n1 || c3 == 0 || c3 == G.n3);
+    *bdry = dir_plane(G, 0, c1) || dir_plane(G, 2, c3);
   } else if (s < G.oV) {
     t = ENT_E3;
     int64_t r = s - G.oE3;
@@ -157,7 +165,7 @@ SEMMG_HD int skel_decode(const Geo& G, int64_t s, int* g, bool* bdry) {
     c2 = (int)(e2 % G.nv2);
     const int a3 = (int)(e2 / G.nv2);
     g[0] = c1 * p; g[1] = c2 * p; g[2] = a3 * p + i3 + 1;
-    *bdry = (c1 == 0 || c1 == G.n1 || c2 == 0 || c2 == G.n2);
+    *bdry = dir_plane(G, 0, c1) || dir_plane(G, 1, c2);
   } else {
     t = ENT_V;
     int64_t r = s - G.oV;
@@ -166,7 +174,7 @@ SEMMG_HD int skel_decode(const Geo& G, int64_t s, int* g, bool* bdry) {
     c2 = (int)(r2 % G.nv2);
     c3 = (int)(r2 / G.nv2);
     g[0] = c1 * p; g[1] = c2 * p; g[2] = c3 * p;
-    *bdry = (c1 == 0 || c1 == G.n1 || c2 == 0 || c2 == G.n2 || c3 == 0 || c3 == G.n3);
+    *bdry = dir_plane(G, 0, c1) || dir_plane(G, 1, c2) || dir_plane(G, 2, c3);
   }
   return t;
 }
@@ -222,6 +230,7 @@ struct Tabs {
 // interior grid points per axis.
 struct CoarseTabs {
   int K[3];
+  int g0[3];  // global node index of coarse grid point 0 along each axis (1 after a Dirichlet face, else 0)
   const double* S[3];    // K_d x K_d, S[g][k]
   const double* lam[3];  // K_d
 };

@@ -2,6 +2,8 @@
 // solver, and the per-level tables of Sec. 2-4.  Runs once per semmg_setup.
 #include "setup_host.h"
 
+#include "semmg.h"
+
 #include <algorithm>
 #include <cmath>
 #include <stdexcept>
@@ -255,7 +257,7 @@ double weight_poly(double t) {
   return 1.0 - 35.0 * t4 + 84.0 * t4 * t - 70.0 * t4 * t2 + 20.0 * t4 * t2 * t;
 }
 
-void build_level_tables(HostLevel& L, const std::vector<double>* h) {
+void build_level_tables(HostLevel& L, const std::vector<double>* h, const int* bc) {
   const int p = L.p, m = p - 1, P1 = p + 1, nS = 2 * m + 1;
   gll_host(p, L.x, L.w);
   stiffness(p, L.x, L.w, L.Ls);
@@ -306,10 +308,13 @@ void build_level_tables(HostLevel& L, const std::vector<double>* h) {
           }
         }
       }
+      // active: nodes that are unknowns of the domain (inside it, not on a Dirichlet face)
+      const int glo = bc[2 * d] == SEMMG_BC_DIRICHLET ? 1 : 0;
+      const int ghi = bc[2 * d + 1] == SEMMG_BC_DIRICHLET ? Nd - 2 : Nd - 1;
       std::vector<int> act;
       for (int j = -m; j <= m; ++j) {
         const int g = c * p + j;
-        if (g >= 1 && g <= Nd - 2) act.push_back(j + m);
+        if (g >= glo && g <= ghi) act.push_back(j + m);
       }
       double* S = &L.starS[d][(size_t)c * nS * nS];
       double* lam = &L.starLam[d][(size_t)c * nS];
@@ -425,14 +430,18 @@ void build_level_tables(HostLevel& L, const std::vector<double>* h) {
   for (int k = 0; k <= m; ++k) L.w1d[k] = weight_poly(0.5 * (1.0 + L.x[k]));
 }
 
-void build_coarse_tables(int p0, const std::vector<double>* h, HostCoarse& C) {
+void build_coarse_tables(int p0, const std::vector<double>* h, const int* bc, HostCoarse& C) {
   std::vector<double> x, w, Ls;
   gll_host(p0, x, w);
   stiffness(p0, x, w, Ls);
   const int P1 = p0 + 1;
   for (int d = 0; d < 3; ++d) {
     const int nd = (int)h[d].size();
-    const int N = nd * p0 + 1, K = N - 2;
+    const int N = nd * p0 + 1;
+    const int glo = bc[2 * d] == SEMMG_BC_DIRICHLET ? 1 : 0;
+    const int ghi = bc[2 * d + 1] == SEMMG_BC_DIRICHLET ? N - 2 : N - 1;
+    const int K = ghi - glo + 1;
+    C.g0[d] = glo;
     C.K[d] = K > 0 ? K : 0;
     C.S[d].clear();
     C.lam[d].clear();
@@ -445,8 +454,8 @@ void build_coarse_tables(int p0, const std::vector<double>* h, HostCoarse& C) {
       }
     std::vector<double> Li((size_t)K * K), Mi(K);
     for (int i = 0; i < K; ++i) {
-      Mi[i] = Mg[i + 1];
-      for (int j = 0; j < K; ++j) Li[(size_t)i * K + j] = Lg[(size_t)(i + 1) * N + (j + 1)];
+      Mi[i] = Mg[i + glo];
+      for (int j = 0; j < K; ++j) Li[(size_t)i * K + j] = Lg[(size_t)(i + glo) * N + (j + glo)];
     }
     gen_eig_diag_mass(K, Li, Mi, C.S[d], C.lam[d]);
   }

@@ -29,6 +29,7 @@ struct HostLevel {
 
 struct HostCoarse {
   int K[3] = {0, 0, 0};
+  int g0[3] = {1, 1, 1};
   std::vector<double> S[3], lam[3];
 };
 
@@ -42,7 +43,8 @@ void gen_eig_diag_mass(int n, const std::vector<double>& L, const std::vector<do
 void gen_eig_centrosym(int n, const std::vector<double>& L, const std::vector<double>& Md, std::vector<double>& S,
                        std::vector<double>& lam);
 double weight_poly(double t);
-void build_level_tables(HostLevel& L, const std::vector<double>* h);
-void build_coarse_tables(int p0, const std::vector<double>* h, HostCoarse& C);
+// bc: faces -x1, +x1, -x2, +x2, -x3, +x3, SEMMG_BC_DIRICHLET or SEMMG_BC_NEUMANN
+void build_level_tables(HostLevel& L, const std::vector<double>* h, const int* bc);
+void build_coarse_tables(int p0, const std::vector<double>* h, const int* bc, HostCoarse& C);
 
 }  // namespace semmg

@@ -84,10 +84,11 @@ struct Block {
 };
 
 // Index ranges of a star, per axis d: the active range [lo[d], hi[d]) of the
-// vertex line (all nS points inside the domain, or, for a line whose vertex
-// lies on the Dirichlet boundary, the m points on the inner side), and pa[d]:
-// whether the plane through the vertex normal to d holds active points (the
-// vertex itself is active along d).  Points outside the active ranges are
+// vertex line (all nS points inside the domain; for a line whose vertex lies
+// on a face of the domain, the points on the inner side: m of them beside a
+// Dirichlet vertex, m + 1 including a Neumann vertex), and pa[d]: whether the
+// plane through the vertex normal to d holds active points (the vertex itself
+// is active along d).  Points outside the active ranges are
 // identity-padded with zero data, so every sum and every eigen index outside
 // them contributes exactly zero and is skipped.
 struct Ranges {
@@ -311,18 +312,18 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
       const int64_t cls = ((int64_t)t.starCls[0][c[0]] * t.ncls[1] + t.starCls[1][c[1]]) * t.ncls[2] + t.starCls[2][c[2]];
       R = t.Rtab + cls * n3;
     }
-    // live ranges [0, nz_d) of the vertex rows: s_d[k] may be non-zero only
-    // there (odd eigenvectors vanish at the vertex; a vertex on the boundary
-    // makes the whole row zero on the active range)
-    const int nz1 = rg.pa[0] ? (sym[0] ? m + 1 : nS) : 0;
-    const int nz2 = rg.pa[1] ? (sym[1] ? m + 1 : nS) : 0;
-    const int nz3 = rg.pa[2] ? (sym[2] ? m + 1 : nS) : 0;
+    // live ranges [lo_d, lo_d + nz_d) of the vertex rows: s_d[k] may be non-zero
+    // only there (odd eigenvectors vanish at the vertex; a vertex on a Dirichlet
+    // face makes the whole row zero on the active range)
     const int lo1 = rg.lo[0], w1 = rg.hi[0] - rg.lo[0], lo2 = rg.lo[1], w2 = rg.hi[1] - rg.lo[1];
+    const int lo3 = rg.lo[2], w3 = rg.hi[2] - rg.lo[2];
+    const int nz1 = rg.pa[0] ? (sym[0] ? m + 1 : w1) : 0;
+    const int nz2 = rg.pa[1] ? (sym[1] ? m + 1 : w2) : 0;
+    const int nz3 = rg.pa[2] ? (sym[2] ? m + 1 : w3) : 0;
     // (k1, k2) pairs, live ones first so that warps stay on one branch:
     // k2 live (any k1), then k2 dead with k1 live, then both dead (only the
-    // x3-plane term, so only when that plane is active); live k_d are the
-    // first nz_d indices of a full range (a line with a live vertex row is
-    // active everywhere)
+    // x3-plane term, so only when that plane is active); the live k_d are the
+    // first nz_d indices of the active range
     const int seg1 = nz2 * w1, seg2 = (w2 - nz2) * nz1, nlive = seg1 + seg2;
     const int npair = nlive + (rg.pa[2] ? (w2 - nz2) * (w1 - nz1) : 0);
     const int ts = slab_thickness(nS);
@@ -350,16 +351,16 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
         const int pr = k2 * nS + k1;
         const T a3 = rg.pa[2] ? P[2 * n2 + pr] : (T)0;
         if (i < nlive) {
-          const T c1 = k1 < nz1 ? s1[k1] : (T)0, c2 = k2 < nz2 ? s2[k2] : (T)0;
+          const T c1 = k1 - lo1 < nz1 ? s1[k1] : (T)0, c2 = k2 - lo2 < nz2 ? s2[k2] : (T)0;
           T b3 = 0;
           for (int kk = 0; kk < tn; ++kk) {
             const int k3 = k3s + kk;
             T E = c1 * P[k3 * nS + k2] + c2 * P[n2 + k3 * nS + k1];
-            if (k3 < nz3) E += s3[k3] * a3;
+            if (k3 - lo3 < nz3) E += s3[k3] * a3;
             const int64_t pt = (int64_t)k3 * n2 + pr;
             const T v = R ? E * R[pt] : fast_div(E, lam + Lm[k1] + Lm[nS + k2] + Lm[2 * nS + k3]);
             V[kk * n2 + pr] = v;
-            if (k3 < nz3) b3 += s3[k3] * v;
+            if (k3 - lo3 < nz3) b3 += s3[k3] * v;
           }
           if (nz3) B3[pr] += b3;
         } else {
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
           T b3 = 0;
           for (int kk = 0; kk < tn; ++kk) {
             const int k3 = k3s + kk;
-            if (k3 >= nz3) break;
+            if (k3 - lo3 >= nz3) break;
             const int64_t pt = (int64_t)k3 * n2 + pr;
             b3 += R ? s3sq[k3] * R[pt] : fast_div(s3sq[k3], lam + Lm[k1] + Lm[nS + k2] + Lm[2 * nS + k3]);
           }
@@ -386,26 +387,28 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
         T s = 0;
         T s_1 = 0, s_2 = 0, s_3 = 0;  // four independent partial sums
         if (first) {  // sum over k1
-          const T* v = vs + kx * nS;
+          const T* v = vs + kx * nS + lo1;
+          const T* sv = s1 + lo1;
           int k = 0;
           for (; k + 3 < nz1; k += 4) {
-            s += s1[k] * v[k];
-            s_1 += s1[k + 1] * v[k + 1];
-            s_2 += s1[k + 2] * v[k + 2];
-            s_3 += s1[k + 3] * v[k + 3];
+            s += sv[k] * v[k];
+            s_1 += sv[k + 1] * v[k + 1];
+            s_2 += sv[k + 2] * v[k + 2];
+            s_3 += sv[k + 3] * v[k + 3];
           }
-          for (; k < nz1; ++k) s += s1[k] * v[k];
+          for (; k < nz1; ++k) s += sv[k] * v[k];
           B1[(k3s + kk) * nS + kx] = (s + s_1) + (s_2 + s_3);
         } else {      // sum over k2
-          const T* v = vs + kx;
+          const T* v = vs + kx + lo2 * nS;
+          const T* sv = s2 + lo2;
           int k = 0;
           for (; k + 3 < nz2; k += 4) {
-            s += s2[k] * v[k * nS];
-            s_1 += s2[k + 1] * v[(k + 1) * nS];
-            s_2 += s2[k + 2] * v[(k + 2) * nS];
-            s_3 += s2[k + 3] * v[(k + 3) * nS];
+            s += sv[k] * v[k * nS];
+            s_1 += sv[k + 1] * v[(k + 1) * nS];
+            s_2 += sv[k + 2] * v[(k + 2) * nS];
+            s_3 += sv[k + 3] * v[(k + 3) * nS];
           }
-          for (; k < nz2; ++k) s += s2[k] * v[k * nS];
+          for (; k < nz2; ++k) s += sv[k] * v[k * nS];
           B2[(k3s + kk) * nS + kx] = (s + s_1) + (s_2 + s_3);
         }
       }

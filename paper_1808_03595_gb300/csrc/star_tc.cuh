@@ -314,10 +314,11 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
     const float* P0 = P;
     const float* P1 = P + np * ld;
     const float* P2 = P + 2 * np * ld;
-    const int nz1 = rg.pa[0] ? (sym[0] ? m + 1 : nS) : 0;
-    const int nz2 = rg.pa[1] ? (sym[1] ? m + 1 : nS) : 0;
-    const int nz3 = rg.pa[2] ? (sym[2] ? m + 1 : nS) : 0;
     const int lo1 = rg.lo[0], w1 = rg.hi[0] - rg.lo[0], lo2 = rg.lo[1], w2 = rg.hi[1] - rg.lo[1];
+    const int lo3 = rg.lo[2], w3 = rg.hi[2] - rg.lo[2];
+    const int nz1 = rg.pa[0] ? (sym[0] ? m + 1 : w1) : 0;
+    const int nz2 = rg.pa[1] ? (sym[1] ? m + 1 : w2) : 0;
+    const int nz3 = rg.pa[2] ? (sym[2] ? m + 1 : w3) : 0;
     const int seg1 = nz2 * w1, seg2 = (w2 - nz2) * nz1, nlive = seg1 + seg2;
     const int npair = nlive + (rg.pa[2] ? (w2 - nz2) * (w1 - nz1) : 0);
     const int ts = slab_thickness(nS);
@@ -344,22 +345,22 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
         const float a3 = rg.pa[2] ? P2[k2 * ld + k1] : 0.0f;
         float* b3p = B3 + tc::coff(k1, k2, np);
         if (i < nlive) {
-          const float c1 = k1 < nz1 ? s1[k1] : 0.0f, c2 = k2 < nz2 ? s2[k2] : 0.0f;
+          const float c1 = k1 - lo1 < nz1 ? s1[k1] : 0.0f, c2 = k2 - lo2 < nz2 ? s2[k2] : 0.0f;
           float b3 = 0.0f;
           for (int kk = 0; kk < tn; ++kk) {
             const int k3 = k3s + kk;
             float E = c1 * P0[k3 * ld + k2] + c2 * P1[k3 * ld + k1];
-            if (k3 < nz3) E += s3[k3] * a3;
+            if (k3 - lo3 < nz3) E += s3[k3] * a3;
             const float v = fast_div(E, lam + Lm[k1] + Lm[nS + k2] + Lm[2 * nS + k3]);
             V[kk * n2 + pr] = v;
-            if (k3 < nz3) b3 += s3[k3] * v;
+            if (k3 - lo3 < nz3) b3 += s3[k3] * v;
           }
           if (nz3) *b3p += b3;
         } else {
           float b3 = 0.0f;
           for (int kk = 0; kk < tn; ++kk) {
             const int k3 = k3s + kk;
-            if (k3 >= nz3) break;
+            if (k3 - lo3 >= nz3) break;
             b3 += fast_div(s3sq[k3], lam + Lm[k1] + Lm[nS + k2] + Lm[2 * nS + k3]);
           }
           *b3p += a3 * b3;
@@ -374,26 +375,28 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
         const float* vs = V + kk * n2;
         float s = 0.0f, s_1 = 0.0f, s_2 = 0.0f, s_3 = 0.0f;
         if (first) {
-          const float* v = vs + kx * nS;
+          const float* v = vs + kx * nS + lo1;
+          const float* sv = s1 + lo1;
           int k = 0;
           for (; k + 3 < nz1; k += 4) {
-            s += s1[k] * v[k];
-            s_1 += s1[k + 1] * v[k + 1];
-            s_2 += s1[k + 2] * v[k + 2];
-            s_3 += s1[k + 3] * v[k + 3];
+            s += sv[k] * v[k];
+            s_1 += sv[k + 1] * v[k + 1];
+            s_2 += sv[k + 2] * v[k + 2];
+            s_3 += sv[k + 3] * v[k + 3];
           }
-          for (; k < nz1; ++k) s += s1[k] * v[k];
+          for (; k < nz1; ++k) s += sv[k] * v[k];
           R1[tc::coff(kx, k3s + kk, np)] = (s + s_1) + (s_2 + s_3);
         } else {
-          const float* v = vs + kx;
+          const float* v = vs + kx + lo2 * nS;
+          const float* sv = s2 + lo2;
           int k = 0;
           for (; k + 3 < nz2; k += 4) {
-            s += s2[k] * v[k * nS];
-            s_1 += s2[k + 1] * v[(k + 1) * nS];
-            s_2 += s2[k + 2] * v[(k + 2) * nS];
-            s_3 += s2[k + 3] * v[(k + 3) * nS];
+            s += sv[k] * v[k * nS];
+            s_1 += sv[k + 1] * v[(k + 1) * nS];
+            s_2 += sv[k + 2] * v[(k + 2) * nS];
+            s_3 += sv[k + 3] * v[(k + 3) * nS];
           }
-          for (; k < nz2; ++k) s += s2[k] * v[k * nS];
+          for (; k < nz2; ++k) s += sv[k] * v[k * nS];
           R1[tc::coff(np + kx, k3s + kk, np)] = (s + s_1) + (s_2 + s_3);
         }
       }

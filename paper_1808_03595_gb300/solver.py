@@ -30,7 +30,7 @@ class Context:
     """A semmg context: mesh (per-axis element widths), degree p, lambda >= 0, options."""
 
     def __init__(self, h, p, lam, p0=2, nu_pre=1, nu_post=1, precision="fp64", max_iter=50, solver="mg",
-                 nu_vary=False, stream=None):
+                 nu_vary=False, bc=None, stream=None):
         self._lib = L.load()
         self._ctx = ctypes.c_void_p()
         self.h = [np.ascontiguousarray(np.asarray(hd, dtype=np.float64)) for hd in h]
@@ -41,6 +41,12 @@ class Context:
         for d in range(3):
             mesh.n[d] = self.n[d]
             mesh.h[d] = self.h[d].ctypes.data_as(L.P_double)
+        # faces -x1, +x1, -x2, +x2, -x3, +x3: "D" (Dirichlet, default) or "N" (Neumann)
+        self.bc = tuple(bc) if bc is not None else ("D",) * 6
+        if len(self.bc) != 6 or any(b not in ("D", "N") for b in self.bc):
+            raise ValueError("bc: six entries, each 'D' or 'N'")
+        for f in range(6):
+            mesh.bc[f] = L.SEMMG_BC_NEUMANN if self.bc[f] == "N" else L.SEMMG_BC_DIRICHLET
         opts = L.semmg_opts()
         self._lib.semmg_default_opts(ctypes.byref(opts))
         opts.p0 = p0

@@ -76,6 +76,14 @@ def test_setup_rejects_bad_arguments_without_touching_the_gpu(lib):
     opts.nu_vary = 0
     opts.p0 = 8
     assert lib.semmg_setup(ctypes.byref(mesh), 4, 1.0, ctypes.byref(opts), None, ctypes.byref(ctx)) == -2
+    # boundary conditions: unknown kind rejected; pure Neumann needs lambda > 0 (singular otherwise)
+    mesh.bc[3] = 7
+    assert lib.semmg_setup(ctypes.byref(mesh), 4, 1.0, None, None, ctypes.byref(ctx)) == -1
+    for f in range(6):
+        mesh.bc[f] = L.SEMMG_BC_NEUMANN
+    assert lib.semmg_setup(ctypes.byref(mesh), 4, 0.0, None, None, ctypes.byref(ctx)) == -2
+    for f in range(6):
+        mesh.bc[f] = L.SEMMG_BC_DIRICHLET
     hbad = np.array([0.5, -0.5])
     mesh.h[0] = hbad.ctypes.data_as(L.P_double)
     assert lib.semmg_setup(ctypes.byref(mesh), 4, 1.0, None, None, ctypes.byref(ctx)) == -1
