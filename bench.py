@@ -410,24 +410,26 @@ def run_semmg(args, world, rank, local, pg):
 
 def run_configs(args, dev, stream, flush):
     """The other workloads of the paper's shape, one solve per form each (not part of `value`):
-    Helmholtz 16^3 at p = 16 (lambda 0 and 100) and Poisson on 6^3 stretched elements at p = 48."""
+    Helmholtz 16^3 at p = 16 (lambda 0 and 100, Dirichlet; lambda 1 with Neumann faces) and Poisson on
+    6^3 stretched elements at p = 48."""
     import torch
     from paper_1808_03595_gb300 import Context
     out = {}
-    plan = [("helmholtz_16x16x16_p16", 0.0, ["fp64", "mixed", "mixed_tc", "kmg_mixed"]),
-            ("helmholtz_16x16x16_p16", 100.0, ["fp64", "mixed"]),
-            ("poisson_6x6x6_p48_stretched", None, ["fp64", "mixed", "kmg_fp64", "kmg_mixed"])]
-    for name, lam, forms in plan:
+    plan = [("helmholtz_16x16x16_p16", 0.0, None, ["fp64", "mixed", "mixed_tc", "kmg_mixed"]),
+            ("helmholtz_16x16x16_p16", 100.0, None, ["fp64", "mixed"]),
+            ("helmholtz_16x16x16_p16", 1.0, ("N",) * 6, ["fp64", "mixed", "kmg_mixed"]),
+            ("poisson_6x6x6_p48_stretched", None, None, ["fp64", "mixed", "kmg_fp64", "kmg_mixed"])]
+    for name, lam, bc, forms in plan:
         h, p, lam0, f, p0 = workloads.config(name, lam=lam)
         lam = lam0 if lam is None else lam
         fd = torch.as_tensor(f, dtype=torch.float64, device=dev)
         ud = torch.empty_like(fd)
         n = int(fd.numel())
-        key = f"{name}_lambda{lam:g}"
+        key = f"{name}_lambda{lam:g}" + ("_neumann" if bc else "")
         out[key] = {"unknowns": n}
         for form in forms:
             prec, solver = FORMS[form]
-            with Context(h, p, lam, p0=p0, precision=prec, solver=solver) as c:
+            with Context(h, p, lam, p0=p0, precision=prec, solver=solver, bc=bc) as c:
                 if args.autotune:
                     c.autotune()
                 for _ in range(args.warmup):

@@ -29,9 +29,12 @@ class Mesh:
     """Tensor-product mesh: per-axis element widths h[d] (length n_d), degree p, lambda.
 
     bc: boundary condition of the faces -x1, +x1, -x2, +x2, -x3, +x3, each "D"
-    (homogeneous Dirichlet, the default) or "N" (homogeneous Neumann, Sec. 3.3:
+    (homogeneous Dirichlet, the default), "N" (homogeneous Neumann, Sec. 3.3:
     the boundary nodes are unknowns and the ghost element beyond the face is
-    decoupled).
+    decoupled) or "P" (periodic, both faces of an axis, at least two elements
+    along it: the ghost element is the element at the other end, Sec. 3.3).
+    On a periodic axis the last node plane of a nodal array is the image of the
+    first one (global node g and g + n_d p are the same unknown).
     """
 
     def __init__(self, h, p, lam, bc=None):
@@ -45,17 +48,27 @@ class Mesh:
         # vertex coordinates along each axis, origin at 0
         self.X = [np.concatenate([[0.0], np.cumsum(hd)]) for hd in self.h]
         self.bc = tuple(bc) if bc is not None else ("D",) * 6
-        if len(self.bc) != 6 or any(b not in ("D", "N") for b in self.bc):
-            raise ValueError("bc: six entries, each 'D' or 'N'")
+        if len(self.bc) != 6 or any(b not in ("D", "N", "P") for b in self.bc):
+            raise ValueError("bc: six entries, each 'D', 'N' or 'P'")
+        for d in range(3):
+            if (self.bc[2 * d] == "P") != (self.bc[2 * d + 1] == "P") or (self.bc[2 * d] == "P" and self.n[d] < 2):
+                raise ValueError("periodic: both faces of an axis, with at least two elements along it")
 
     def with_degree(self, p):
         return Mesh(self.h, p, self.lam, self.bc)
 
+    def periodic(self, d):
+        return self.bc[2 * d] == "P"
+
     def g_range(self, d):
-        """Global node indices [lo, hi] along axis d that are unknowns (not Dirichlet)."""
+        """Global node indices [lo, hi] along axis d that are unknowns (not Dirichlet, not a periodic image)."""
         lo = 1 if self.bc[2 * d] == "D" else 0
-        hi = self.N[d] - 2 if self.bc[2 * d + 1] == "D" else self.N[d] - 1
+        hi = self.N[d] - 2 if self.bc[2 * d + 1] in ("D", "P") else self.N[d] - 1
         return lo, hi
+
+    def wrap(self, g, d):
+        """Global node index along axis d, periodic images mapped to their unknown."""
+        return np.mod(g, self.n[d] * self.p) if self.periodic(d) else g
 
     @property
     def shape(self):
@@ -85,11 +98,24 @@ def element_operator(p, h1, h2, h3, lam):
     return d0 * k(M, k(M, M)) + d1 * k(M, k(M, L)) + d2 * k(M, k(L, M)) + d3 * k(L, k(M, M))
 
 
+def sync_images(mesh, u):
+    """Copy the first node plane of every periodic axis onto its image (last) plane."""
+    u = np.array(u, dtype=float, copy=True)
+    for d in range(3):
+        if mesh.periodic(d):
+            ax = 2 - d  # nodal arrays are [g3, g2, g1]
+            first = np.take(u, [0], axis=ax)
+            idx = [slice(None)] * 3
+            idx[ax] = slice(u.shape[ax] - 1, u.shape[ax])
+            u[tuple(idx)] = first
+    return u
+
+
 def _element_global_index(mesh, a1, a2, a3):
     p = mesh.p
     i = np.arange(p + 1)
     i3, i2, i1 = np.meshgrid(i, i, i, indexing="ij")
-    return mesh.flat(a1 * p + i1, a2 * p + i2, a3 * p + i3).ravel()
+    return mesh.flat(mesh.wrap(a1 * p + i1, 0), mesh.wrap(a2 * p + i2, 1), mesh.wrap(a3 * p + i3, 2)).ravel()
 
 
 def assemble_H(mesh):
@@ -195,13 +221,14 @@ class Condensed:
         return Fh
 
     def recover(self, F, uB):
-        """Nodal solution: u_B from the condensed system, u_I = H_II^{-1}(F_I - H_IB u_B); 0 on the Dirichlet boundary."""
+        """Nodal solution: u_B from the condensed system, u_I = H_II^{-1}(F_I - H_IB u_B); 0 on the Dirichlet
+        boundary, periodic images set."""
         F = np.asarray(F, float).ravel()
         u = np.zeros(int(np.prod(self.mesh.N)))
         u[self.B] = uB
         if len(self.I):
             u[self.I] = self._solve_ii(F[self.I] - self.Hib @ uB)
-        return u.reshape(self.mesh.shape)
+        return sync_images(self.mesh, u.reshape(self.mesh.shape))
 
     def full_solve(self, F):
         """Exact discrete solution of the uncondensed system H u = F (free nodes), nodal array."""
@@ -209,7 +236,7 @@ class Condensed:
         Hff = self.H[self.free][:, self.free].tocsc()
         u = np.zeros(int(np.prod(self.mesh.N)))
         u[self.free] = spla.spsolve(Hff, F[self.free])
-        return u.reshape(self.mesh.shape)
+        return sync_images(self.mesh, u.reshape(self.mesh.shape))
 
 
 # --------------------------------------------------------------------------
@@ -217,9 +244,10 @@ class Condensed:
 # --------------------------------------------------------------------------
 
 def star_vertices(mesh):
-    """All (n1+1)(n2+1)(n3+1) vertices, boundary ones included (Sec. 3.3)."""
-    return [(c1, c2, c3) for c3 in range(mesh.n[2] + 1) for c2 in range(mesh.n[1] + 1)
-            for c1 in range(mesh.n[0] + 1)]
+    """All (n1+1)(n2+1)(n3+1) vertices, boundary ones included (Sec. 3.3); on a periodic
+    axis the last vertex plane is the first one."""
+    nv = [mesh.n[d] + (0 if mesh.periodic(d) else 1) for d in range(3)]
+    return [(c1, c2, c3) for c3 in range(nv[2]) for c2 in range(nv[1]) for c1 in range(nv[0])]
 
 
 def star_positions(mesh, B, c):
@@ -229,6 +257,10 @@ def star_positions(mesh, B, c):
     g2 = (B // mesh.N[0]) % mesh.N[1]
     g3 = B // (mesh.N[0] * mesh.N[1])
     j = np.stack([g1 - c[0] * p, g2 - c[1] * p, g3 - c[2] * p], axis=1)
+    for d in range(3):  # periodic axes: offset to the nearest image of the vertex
+        if mesh.periodic(d):
+            Lp = mesh.n[d] * p
+            j[:, d] = np.mod(j[:, d] + Lp // 2, Lp) - Lp // 2
     inside = np.all(np.abs(j) <= p - 1, axis=1)
     pos = np.flatnonzero(inside)
     return pos, j[pos]
@@ -241,9 +273,9 @@ def assembled_1d(mesh, d):
     Mg = np.zeros((Nd, Nd))
     Lg = np.zeros((Nd, Nd))
     for a in range(mesh.n[d]):
-        s = slice(a * p, (a + 1) * p + 1)
-        Mg[s, s] += 0.5 * mesh.h[d][a] * M
-        Lg[s, s] += 2.0 / mesh.h[d][a] * L
+        g = mesh.wrap(np.arange(a * p, (a + 1) * p + 1), d)
+        Mg[np.ix_(g, g)] += 0.5 * mesh.h[d][a] * M
+        Lg[np.ix_(g, g)] += 2.0 / mesh.h[d][a] * L
     return Mg, Lg
 
 
@@ -261,7 +293,7 @@ def star_line_table(mesh, d, c):
     m = p - 1
     nS = 2 * m + 1
     Mg, Lg = assembled_1d(mesh, d)
-    g = c * p + np.arange(-m, m + 1)
+    g = mesh.wrap(c * p + np.arange(-m, m + 1), d)
     lo, hi = mesh.g_range(d)
     active = (g >= lo) & (g <= hi)
     S = np.eye(nS)
@@ -364,7 +396,15 @@ def star_weights(mesh, B, c, pos):
     for d, g in enumerate((g1, g2, g3)):
         xv = mesh.X[d][c[d]]
         dist = x[d][g] - xv
-        side = np.where(dist >= 0, c[d], c[d] - 1)
+        if mesh.periodic(d):
+            # the image of the vertex on the side the node's index offset points to
+            Lp = mesh.n[d] * mesh.p
+            j = np.mod(g - c[d] * mesh.p + Lp // 2, Lp) - Lp // 2
+            per = mesh.X[d][-1]
+            dist = np.where((j > 0) & (dist < 0), dist + per, np.where((j < 0) & (dist > 0), dist - per, dist))
+            side = np.mod(np.where(j >= 0, c[d], c[d] - 1), mesh.n[d])
+        else:
+            side = np.where(dist >= 0, c[d], c[d] - 1)
         side = np.clip(side, 0, mesh.n[d] - 1)
         t = np.abs(dist) / mesh.h[d][side]
         W *= weight_poly(t)

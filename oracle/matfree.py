@@ -44,7 +44,21 @@ def elem_view(u, mesh):
 
 
 def elem_blocks(u, mesh):
-    return np.array(elem_view(np.ascontiguousarray(u, dtype=float), mesh))
+    """Element blocks of a nodal array; periodic images take the value of their unknown."""
+    return np.array(elem_view(np.ascontiguousarray(dense.sync_images(mesh, u), dtype=float), mesh))
+
+
+def _fold_images(out, mesh):
+    """Periodic axes: add the image plane into the first plane, then copy it back."""
+    for d in range(3):
+        if mesh.periodic(d):
+            ax = 2 - d
+            idx0 = [slice(None)] * 3
+            idx1 = [slice(None)] * 3
+            idx0[ax] = 0
+            idx1[ax] = out.shape[ax] - 1
+            out[tuple(idx0)] += out[tuple(idx1)]
+    return dense.sync_images(mesh, out)
 
 
 def assemble_blocks(blocks, mesh):
@@ -60,7 +74,7 @@ def assemble_blocks(blocks, mesh):
         for q2 in (0, 1):
             for q1 in (0, 1):
                 view[q3::2, q2::2, q1::2] += blocks[q3::2, q2::2, q1::2]
-    return out
+    return _fold_images(out, mesh)
 
 
 def masks(mesh):
@@ -198,7 +212,7 @@ def recover(mesh, f, uhat, chunk=512):
     p = mesh.p
     u = np.where(condensed_mask(mesh), uhat, 0.0)
     if p == 1:
-        return u
+        return dense.sync_images(mesh, u)
     F = mass_diag(mesh) * np.asarray(f, float)
     d = elem_coeffs(mesh)
     ub = elem_blocks(u, mesh).reshape(-1, p + 1, p + 1, p + 1)
@@ -216,7 +230,7 @@ def recover(mesh, f, uhat, chunk=512):
         for a2 in range(n2):
             for a1 in range(n1):
                 out[a3 * p + 1:(a3 + 1) * p, a2 * p + 1:(a2 + 1) * p, a1 * p + 1:(a1 + 1) * p] = ui[a3, a2, a1]
-    return out
+    return dense.sync_images(mesh, out)
 
 
 # --------------------------------------------------------------------------
@@ -233,15 +247,20 @@ class StarTables:
         self.S, self.Lam, self.act, self.wl = [], [], [], []
         x = mesh.node_coords()
         j = np.arange(-m, m + 1)
+        xi, _ = gll(p)
         for d in range(3):
             Sd, Ld, Ad, Wd = [], [], [], []
-            for c in range(mesh.n[d] + 1):
+            for c in range(mesh.n[d] + (0 if mesh.periodic(d) else 1)):
                 S, lam, act = dense.star_line_table(mesh, d, c)
                 Sd.append(S)
                 Ld.append(lam)
                 Ad.append(act)
                 g = c * p + j
                 wv = np.zeros(len(j))
+                if mesh.periodic(d):
+                    # every offset lies inside the domain; t = its reference distance to the vertex
+                    Wd.append(weight_poly((1.0 + xi[np.abs(j)]) / 2.0))
+                    continue
                 for k, gg in enumerate(g):
                     if 0 <= gg < mesh.N[d]:
                         dist = x[d][gg] - mesh.X[d][c]
@@ -270,7 +289,7 @@ def smooth(mesh, r, tables=None, chunk=128):
         tables = StarTables(mesh)
     r = np.where(condensed_mask(mesh), r, 0.0)
     P = p  # padding so every star plane slice is in range
-    rp = np.pad(r, P)
+    rp = _pad_star(mesh, r, P)
     dup = np.zeros_like(rp)
     verts = np.array(dense.star_vertices(mesh))
     j = np.arange(-m, m + 1)
@@ -318,8 +337,47 @@ def smooth(mesh, r, tables=None, chunk=128):
         np.add.at(dup, i1, W1 * O1 / mult)
         np.add.at(dup, i2, W2 * O2 / mult)
         np.add.at(dup, i3, W3 * O3 / mult)
-    du = dup[P:-P, P:-P, P:-P]
+    du = _unpad_star(mesh, dup, P)
     return np.where(condensed_mask(mesh), du, 0.0)
+
+
+def _pad_star(mesh, r, P):
+    """Pad a nodal array by P on every side: zeros, or on a periodic axis the
+    values wrapped around the n_d p unknowns (a star near one end reads the other)."""
+    for d in range(3):
+        ax = 2 - d
+        if mesh.periodic(d):
+            Lp = mesh.n[d] * mesh.p
+            core = np.take(r, np.arange(Lp), axis=ax)
+            r = np.concatenate([np.take(core, np.arange(Lp - P, Lp), axis=ax), core,
+                                np.take(core, np.arange(0, P + 1), axis=ax)], axis=ax)
+        else:
+            pad = [(0, 0)] * 3
+            pad[ax] = (P, P)
+            r = np.pad(r, pad)
+    return r
+
+
+def _unpad_star(mesh, dup, P):
+    """Inverse of _pad_star for accumulated values: margins of a periodic axis
+    are added to the unknowns they wrap onto, then the image plane is set."""
+    for d in range(3):
+        ax = 2 - d
+        Np = dup.shape[ax]
+        if mesh.periodic(d):
+            Lp = mesh.n[d] * mesh.p
+            core = np.take(dup, np.arange(P, P + Lp), axis=ax)
+            left = np.take(dup, np.arange(0, P), axis=ax)            # wraps onto Lp - P .. Lp - 1
+            right = np.take(dup, np.arange(P + Lp, Np), axis=ax)     # wraps onto 0 .. P
+            idx = [slice(None)] * 3
+            idx[ax] = slice(Lp - P, Lp)
+            core[tuple(idx)] += left
+            idx[ax] = slice(0, right.shape[ax])
+            core[tuple(idx)] += right
+            dup = np.concatenate([core, np.take(core, [0], axis=ax)], axis=ax)
+        else:
+            dup = np.take(dup, np.arange(P, Np - P), axis=ax)
+    return dup
 
 
 # --------------------------------------------------------------------------

@@ -24,6 +24,7 @@ def _rng(seed=0):
 DIRICHLET = ("D",) * 6
 MIXED_BC = ("N", "D", "D", "N", "N", "N")
 NEUMANN = ("N",) * 6
+PERIODIC_BC = ("P", "P", "N", "D", "P", "P")
 
 
 def _mesh_small(p=4, lam=1.5, stretched=True, bc=None):
@@ -115,7 +116,8 @@ def test_assembly_is_kronecker_sum():
 
 
 @pytest.mark.parametrize("p,lam,bc", [(2, 0.0, DIRICHLET), (4, 1.5, DIRICHLET), (5, 100.0, DIRICHLET),
-                                      (3, 0.0, MIXED_BC), (4, 2.0, NEUMANN)])
+                                      (3, 0.0, MIXED_BC), (4, 2.0, NEUMANN), (3, 0.0, PERIODIC_BC),
+                                      (4, 1.0, ("P",) * 6)])
 def test_condensed_operator_spd_and_matrix_free(p, lam, bc):
     mesh = _mesh_small(p=p, lam=lam, bc=bc)
     cond = dense.Condensed(mesh)
@@ -131,7 +133,7 @@ def test_condensed_operator_spd_and_matrix_free(p, lam, bc):
     assert np.all(y[~matfree.condensed_mask(mesh)] == 0)
 
 
-@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC])
+@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC, PERIODIC_BC])
 def test_condensation_reproduces_full_solution(bc):
     mesh = _mesh_small(p=4, lam=0.5, bc=bc)
     cond = dense.Condensed(mesh)
@@ -200,12 +202,36 @@ def test_manufactured_solution_neumann(bc, kind):
     assert np.count_nonzero(free) > np.prod([Nd - 2 for Nd in mesh.N])
 
 
+@pytest.mark.parametrize("bc,kind", [(("P",) * 6, "ccc2"), (("P", "P", "D", "D", "D", "D"), "css"),
+                                     (("P", "P", "N", "N", "D", "D"), "scs")])
+def test_manufactured_solution_periodic(bc, kind):
+    # periodic axes (Sec. 3.3: the ghost element is the element at the other end):
+    # period-1 trigonometric solutions on the unit cube; the image plane equals the first
+    p = 8
+    mesh = dense.Mesh([np.full(3, 1 / 3)] * 3, p, 1.0, bc)
+    x = mesh.node_coords()
+    X3, X2, X1 = np.meshgrid(x[2], x[1], x[0], indexing="ij")
+    pi = np.pi
+    if kind == "ccc2":
+        ue, k2 = np.cos(2 * pi * X1) * np.cos(2 * pi * X2) * np.cos(2 * pi * X3), 12 * pi**2
+    elif kind == "css":
+        ue, k2 = np.cos(2 * pi * X1) * np.sin(pi * X2) * np.sin(pi * X3), 6 * pi**2
+    else:
+        ue, k2 = np.sin(2 * pi * X1) * np.cos(pi * X2) * np.sin(pi * X3), 6 * pi**2
+    f = (mesh.lam + k2) * ue
+    u, it, hist = matfree.solve(mesh, f, p0=1)
+    assert hist[-1] <= 1e-10 * hist[0]
+    assert np.abs(u - ue).max() < 1e-8
+    assert np.array_equal(u[:, :, 0], u[:, :, -1])  # periodic image of the x1 = 0 plane
+
+
 # ---------------------------------------------------------------- stars (Sec. 2.3, 3)
 
 @pytest.mark.parametrize("c,bc", [((1, 1, 1), DIRICHLET), ((0, 1, 1), DIRICHLET), ((3, 0, 2), DIRICHLET),
                                   ((0, 0, 0), DIRICHLET), ((3, 3, 2), DIRICHLET), ((2, 1, 0), DIRICHLET),
                                   ((0, 1, 1), MIXED_BC), ((0, 2, 2), MIXED_BC), ((3, 0, 0), MIXED_BC),
-                                  ((0, 0, 0), NEUMANN), ((3, 3, 2), NEUMANN)])
+                                  ((0, 0, 0), NEUMANN), ((3, 3, 2), NEUMANN),
+                                  ((0, 0, 0), PERIODIC_BC), ((2, 3, 1), PERIODIC_BC), ((0, 1, 0), ("P",) * 6)])
 def test_alg1_is_inverse_of_condensed_star(c, bc):
     # (dense Hhat_i) x (Algorithm 1 applied to each unit vector) = I, interior and boundary
     # stars; with Neumann faces the boundary vertex and face nodes belong to the star
@@ -231,14 +257,14 @@ def test_alg1_is_inverse_of_condensed_star(c, bc):
     np.testing.assert_allclose(Hi @ X, np.eye(len(pos)), atol=1e-11)
 
 
-@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC])
+@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC, PERIODIC_BC])
 def test_star_tables_generalized_eigen(bc):
     mesh = _mesh_small(p=5, bc=bc)
     for d in range(3):
         Mg, Lg = dense.assembled_1d(mesh, d)
         for c in range(mesh.n[d] + 1):
             S, lam, act = dense.star_line_table(mesh, d, c)
-            g = c * mesh.p + np.arange(-(mesh.p - 1), mesh.p)
+            g = mesh.wrap(c * mesh.p + np.arange(-(mesh.p - 1), mesh.p), d)  # block nodes (periodic: wrapped)
             ia = np.flatnonzero(act)
             Sa = S[np.ix_(ia, ia)]
             Ma, La = Mg[np.ix_(g[ia], g[ia])], Lg[np.ix_(g[ia], g[ia])]
@@ -246,7 +272,7 @@ def test_star_tables_generalized_eigen(bc):
             np.testing.assert_allclose(Sa.T @ La @ Sa, np.diag(lam[ia]), atol=1e-10 * lam.max())
 
 
-@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC, NEUMANN])
+@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC, NEUMANN, PERIODIC_BC, ("P",) * 6])
 def test_weights_partition_of_unity(bc):
     mesh = _mesh_small(p=6, bc=bc)
     cond = dense.Condensed(mesh, dense=False)
@@ -258,7 +284,7 @@ def test_weights_partition_of_unity(bc):
 
 
 @pytest.mark.parametrize("p,lam,bc", [(3, 0.0, DIRICHLET), (4, 2.0, DIRICHLET), (3, 0.5, MIXED_BC),
-                                      (4, 1.0, NEUMANN)])
+                                      (4, 1.0, NEUMANN), (3, 0.0, PERIODIC_BC), (4, 1.0, ("P",) * 6)])
 def test_smoother_alg1_equals_dense_inverse(p, lam, bc):
     mesh = _mesh_small(p=p, lam=lam, bc=bc)
     cond = dense.Condensed(mesh)
@@ -275,7 +301,8 @@ def test_smoother_alg1_equals_dense_inverse(p, lam, bc):
 
 # ---------------------------------------------------------------- transfers (Sec. 4.1)
 
-@pytest.mark.parametrize("pc,pf,bc", [(1, 2, DIRICHLET), (2, 4, DIRICHLET), (4, 6, DIRICHLET), (2, 4, MIXED_BC)])
+@pytest.mark.parametrize("pc,pf,bc", [(1, 2, DIRICHLET), (2, 4, DIRICHLET), (4, 6, DIRICHLET), (2, 4, MIXED_BC),
+                                      (1, 3, PERIODIC_BC)])
 def test_transfers_adjoint_and_explicit(pc, pf, bc):
     mesh_f = _mesh_small(p=pf, bc=bc)
     mesh_c = mesh_f.with_degree(pc)
@@ -318,7 +345,8 @@ def test_level_degrees():
     assert dense.level_degrees(2, 2) == [2]
 
 
-@pytest.mark.parametrize("p0,bc", [(1, DIRICHLET), (2, DIRICHLET), (1, MIXED_BC), (2, NEUMANN)])
+@pytest.mark.parametrize("p0,bc", [(1, DIRICHLET), (2, DIRICHLET), (1, MIXED_BC), (2, NEUMANN), (1, PERIODIC_BC),
+                                   (2, ("P",) * 6)])
 def test_vcycle_o2_equals_o1(p0, bc):
     mesh = _mesh_small(p=4, lam=1.0, bc=bc)
     hier = dense.Hierarchy(mesh, p0=p0)
@@ -336,7 +364,7 @@ def test_vcycle_o2_equals_o1(p0, bc):
     assert np.abs(v1 - v2).max() < 1e-12 * np.abs(v1).max()
 
 
-@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC])
+@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC, PERIODIC_BC])
 def test_mg_solve_matches_direct_solve(bc):
     mesh = _mesh_small(p=5, lam=0.0, bc=bc)
     cond = dense.Condensed(mesh)
