@@ -88,15 +88,18 @@ enum { SEMMG_SOLVER_MG = 0, SEMMG_SOLVER_KMG = 1 };
 enum { SEMMG_F64 = 0, SEMMG_F32 = 1 };
 
 /* boundary condition of a face of the domain (Sec. 3.3) */
-enum { SEMMG_BC_DIRICHLET = 0, SEMMG_BC_NEUMANN = 1 };
+enum { SEMMG_BC_DIRICHLET = 0, SEMMG_BC_NEUMANN = 1, SEMMG_BC_PERIODIC = 2 };
 
 typedef struct {
   int n[3];              /* elements per axis, each >= 1 */
   const double* h[3];    /* HOST arrays: n[d] element widths along axis d, > 0 */
   int bc[6];             /* faces -x1, +x1, -x2, +x2, -x3, +x3: SEMMG_BC_DIRICHLET (0, homogeneous,
-                            the value of a zero-initialised struct) or SEMMG_BC_NEUMANN (homogeneous:
-                            the face's nodes are unknowns, the ghost element beyond it is decoupled).
-                            All-Neumann needs lambda > 0. */
+                            the value of a zero-initialised struct), SEMMG_BC_NEUMANN (homogeneous:
+                            the face's nodes are unknowns, the ghost element beyond it is decoupled)
+                            or SEMMG_BC_PERIODIC (both faces of an axis, n[d] >= 2: the ghost element
+                            is the element at the other end; nodal arrays keep n[d] p + 1 planes along
+                            d, the last one the image of the first).  Without a Dirichlet face
+                            lambda must be > 0. */
 } semmg_mesh;
 
 typedef struct {

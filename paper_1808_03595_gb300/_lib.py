@@ -25,7 +25,7 @@ ERRORS = {
 SEMMG_ERR_NOT_CONVERGED = -4
 SEMMG_FP64, SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC = 0, 1, 2, 3
 SEMMG_SOLVER_MG, SEMMG_SOLVER_KMG = 0, 1
-SEMMG_BC_DIRICHLET, SEMMG_BC_NEUMANN = 0, 1
+SEMMG_BC_DIRICHLET, SEMMG_BC_NEUMANN, SEMMG_BC_PERIODIC = 0, 1, 2
 SEMMG_F64, SEMMG_F32 = 0, 1
 SEMMG_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 

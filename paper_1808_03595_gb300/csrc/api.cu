@@ -62,6 +62,7 @@ size_t tc_off(int row, int k, int np) {
 Geo make_geo(const int n[3], int p, double lam, const int bc[6]) {
   Geo g{};
   for (int f = 0; f < 6; ++f) g.dir[f] = bc[f] == SEMMG_BC_DIRICHLET ? 1 : 0;
+  for (int d = 0; d < 3; ++d) g.per[d] = bc[2 * d] == SEMMG_BC_PERIODIC ? 1 : 0;
   g.p = p;
   g.m = p - 1;
   g.nS = 2 * p - 1;
@@ -700,8 +701,14 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   if (o.nu_vary != 0 && o.nu_vary != 1) return SEMMG_ERR_INVALID_ARG;
   bool any_dirichlet = false;
   for (int f = 0; f < 6; ++f) {
-    if (mesh->bc[f] != SEMMG_BC_DIRICHLET && mesh->bc[f] != SEMMG_BC_NEUMANN) return SEMMG_ERR_INVALID_ARG;
+    if (mesh->bc[f] != SEMMG_BC_DIRICHLET && mesh->bc[f] != SEMMG_BC_NEUMANN && mesh->bc[f] != SEMMG_BC_PERIODIC)
+      return SEMMG_ERR_INVALID_ARG;
     any_dirichlet |= mesh->bc[f] == SEMMG_BC_DIRICHLET;
+  }
+  for (int d = 0; d < 3; ++d) {
+    const bool plo = mesh->bc[2 * d] == SEMMG_BC_PERIODIC, phi = mesh->bc[2 * d + 1] == SEMMG_BC_PERIODIC;
+    if (plo != phi) return SEMMG_ERR_INVALID_ARG;         // periodic pairs the two faces of an axis
+    if (plo && mesh->n[d] < 2) return SEMMG_ERR_UNSUPPORTED;  // a star would meet itself
   }
   if (!any_dirichlet && !(lambda > 0.0)) return SEMMG_ERR_UNSUPPORTED;  // singular (pure Neumann, lambda = 0)
   for (int d = 0; d < 3; ++d) {

@@ -28,7 +28,7 @@ __device__ __forceinline__ T mass1d(const Geo& G, const Tabs<T>& t, int d, int g
   const int a = divp(G, g), q = g - a * G.p;
   if (q) return (T)0.5 * t.h[d][a] * t.w[q];
   T s = 0;
-  if (a > 0) s += (T)0.5 * t.h[d][a - 1] * t.w[G.p];
+  if (a > 0 || G.per[d]) s += (T)0.5 * t.h[d][wrape(G, d, a - 1)] * t.w[G.p];  // periodic: the last element
   if (a < nd) s += (T)0.5 * t.h[d][a] * t.w[0];
   return s;
 }
@@ -60,9 +60,11 @@ __device__ T line_sum(const Geo& G, const Tabs<T>& t, const T* __restrict__ u, i
     return k * acc;
   }
   // on vertex plane c = a; the element on either side may be missing at a
-  // (Neumann) face of the domain: 0 <= c <= n_d
-  const bool hasL = a > 0, hasR = a < nd;
-  const T kL = hasL ? t.hx[d][6 * (a - 1) + 1] : (T)0, kR = hasR ? t.hx[d][6 * a + 1] : (T)0;  // 2 / h
+  // (Neumann) face of the domain: 0 <= c <= n_d; neighbour nodes past a
+  // periodic end wrap in skel_index
+  // (on a periodic axis the element left of plane 0 is the last one)
+  const bool hasL = a > 0 || G.per[d], hasR = a < nd;
+  const T kL = hasL ? t.hx[d][6 * wrape(G, d, a - 1) + 1] : (T)0, kR = hasR ? t.hx[d][6 * a + 1] : (T)0;  // 2 / h
   T acc = (kL * Ls[p * P1 + p] + kR * Ls[0]) * u[s];
   if (hasL) {
     gg[d] = (a - 1) * p;
@@ -108,8 +110,8 @@ __device__ __forceinline__ T face_z(const Geo& G, const T* __restrict__ Z, int t
   const int64_t loc = (int64_t)(q[ib] - 1) * m + (q[ia] - 1);
   int e[3] = {a[0], a[1], a[2]};
   T z = 0;
-  if (a[d] > 0) {  // element on the minus side (absent at the low face of the domain): this face is its side p
-    e[d] = a[d] - 1;
+  if (a[d] > 0 || G.per[d]) {  // element on the minus side (absent at a low non-periodic face): this face is its side p
+    e[d] = wrape(G, d, a[d] - 1);
     const int64_t em = ((int64_t)e[2] * G.n2 + e[1]) * G.n1 + e[0];
     z += Z[(em * 6 + 2 * d + 1) * mm + loc];
   }
@@ -180,13 +182,16 @@ __global__ void k_pack(Geo G, const double* __restrict__ nodal, double* __restri
   }
 }
 
+// Every skeleton node of the nodal array; a periodic image takes the value of
+// the unknown it repeats (the slot skel_index maps it to).
 __global__ void k_unpack(Geo G, const double* __restrict__ hat, double* __restrict__ nodal) {
   const int64_t N1 = (int64_t)G.n1 * G.p + 1, N2 = (int64_t)G.n2 * G.p + 1;
+  const bool anyper = G.per[0] || G.per[1] || G.per[2];
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < G.size; s += (int64_t)gridDim.x * blockDim.x) {
     int g[3];
     bool bd;
     skel_decode(G, s, g, &bd);
-    nodal[((int64_t)g[2] * N2 + g[1]) * N1 + g[0]] = hat[s];
+    nodal[((int64_t)g[2] * N2 + g[1]) * N1 + g[0]] = anyper ? hat[skel_index(G, g[0], g[1], g[2])] : hat[s];
   }
 }
 
@@ -215,7 +220,7 @@ __global__ void __launch_bounds__(kThreads) k_star_gather(Geo G, const T* __rest
         no[d] = 2;
         c[d][0] = a;
         j[d][0] = q;
-        c[d][1] = a + 1;
+        c[d][1] = (G.per[d] && a + 1 == ncount(G, d)) ? 0 : a + 1;  // periodic: the star at plane 0
         j[d][1] = q - p;
       }
     }

@@ -261,7 +261,7 @@ __global__ void k_restrict_gather(Geo Gf, Geo Gc, const T* __restrict__ rf, T* _
           const int oth = which == 0 ? ax_b : ax_a;
           const int cn = which == 0 ? ca : cb;
           const int co = which == 0 ? cb : ca;
-          const int eo = co - 1 + side;  // element along oth
+          const int eo = wrape(Gc, oth, co - 1 + side);  // element along oth (periodic: wrapped)
           if (eo < 0 || eo >= elem_count(Gc, oth)) continue;
           const int lo = side == 1 ? 0 : pc;  // local index along oth
           // tangential ordering: a' < b'
@@ -285,7 +285,7 @@ __global__ void k_restrict_gather(Geo Gf, Geo Gc, const T* __restrict__ rf, T* _
       for (int d = 0; d < 3; ++d) {  // six edges
         const int ax_a = d == 0 ? 1 : 0, ax_b = d == 2 ? 1 : 2;
         for (int side = 0; side < 2; ++side) {
-          const int e = c[d] - 1 + side;
+          const int e = wrape(Gc, d, c[d] - 1 + side);
           if (e < 0 || e >= elem_count(Gc, d)) continue;
           const int64_t en = eoff[d] + edge_number(Gc, d, c[ax_a], c[ax_b], e);
           s += EB[en * P1 + (side == 1 ? 0 : pc)];
@@ -295,7 +295,7 @@ __global__ void k_restrict_gather(Geo Gf, Geo Gc, const T* __restrict__ rf, T* _
         const int ax_a = d == 0 ? 1 : 0, ax_b = d == 2 ? 1 : 2;
         for (int sb = 0; sb < 2; ++sb)
           for (int sa = 0; sa < 2; ++sa) {
-            const int ea = c[ax_a] - 1 + sa, eb = c[ax_b] - 1 + sb;
+            const int ea = wrape(Gc, ax_a, c[ax_a] - 1 + sa), eb = wrape(Gc, ax_b, c[ax_b] - 1 + sb);
             if (ea < 0 || ea >= elem_count(Gc, ax_a) || eb < 0 || eb >= elem_count(Gc, ax_b)) continue;
             const int64_t fn = foff[d] + face_number(Gc, d, c[d], ea, eb);
             s += FB[fn * P1 * P1 + (sb == 1 ? 0 : pc) * P1 + (sa == 1 ? 0 : pc)];

@@ -27,14 +27,32 @@ struct Geo {
   int64_t nelem, nstar;
   uint64_t pinv;  // ceil(2^32 / p): exact division g / p for 0 <= g < 2^20
   double lam;
-  unsigned char dir[6];  // faces -x1, +x1, -x2, +x2, -x3, +x3: 1 = Dirichlet, 0 = Neumann
+  unsigned char dir[6];  // faces -x1, +x1, -x2, +x2, -x3, +x3: 1 = Dirichlet, 0 = Neumann or periodic
+  unsigned char per[3];  // periodic axes: vertex plane n_d is the image of plane 0 (its slots unused)
 };
 
 SEMMG_HD int ncount(const Geo& G, int d) { return d == 0 ? G.n1 : (d == 1 ? G.n2 : G.n3); }
 
-// Whether vertex plane c along axis d is a Dirichlet face of the domain.
+// Whether vertex plane c along axis d holds no unknowns: a Dirichlet face, or
+// the image plane of a periodic axis.
 SEMMG_HD bool dir_plane(const Geo& G, int d, int c) {
-  return (c == 0 && G.dir[2 * d]) || (c == ncount(G, d) && G.dir[2 * d + 1]);
+  const int nd = ncount(G, d);
+  return (c == 0 && G.dir[2 * d]) || (c == nd && (G.dir[2 * d + 1] || G.per[d]));
+}
+
+// Global node index along a periodic axis mapped onto [0, n_d p) (offsets of
+// at most one period); unchanged on other axes.
+SEMMG_HD int wrapg(const Geo& G, int d, int g) {
+  if (!G.per[d]) return g;
+  const int L = ncount(G, d) * G.p;
+  return g < 0 ? g + L : (g >= L ? g - L : g);
+}
+
+// Element index along a periodic axis mapped onto [0, n_d).
+SEMMG_HD int wrape(const Geo& G, int d, int a) {
+  if (!G.per[d]) return a;
+  const int nd = ncount(G, d);
+  return a < 0 ? a + nd : (a >= nd ? a - nd : a);
 }
 
 enum EntityType { ENT_F1 = 0, ENT_F2, ENT_F3, ENT_E1, ENT_E2, ENT_E3, ENT_V, ENT_NONE };
@@ -44,8 +62,12 @@ SEMMG_HD int divp(const Geo& G, int g) {
 }
 
 // Skeleton slot of the global GLL node (g1, g2, g3), or -1 for an element
-// interior node.  `type` receives the entity group.
+// interior node; periodic images and offsets past a periodic end map to the
+// unknown they repeat.  `type` receives the entity group.
 SEMMG_HD int64_t skel_index(const Geo& G, int g1, int g2, int g3, int* type = nullptr) {
+  g1 = wrapg(G, 0, g1);
+  g2 = wrapg(G, 1, g2);
+  g3 = wrapg(G, 2, g3);
   const int a1 = divp(G, g1), a2 = divp(G, g2), a3 = divp(G, g3);
   const int q1 = g1 - a1 * G.p, q2 = g2 - a2 * G.p, q3 = g3 - a3 * G.p;
   const int m = G.m;
@@ -184,10 +206,20 @@ SEMMG_HD int skel_decode(const Geo& G, int64_t s, int* g, bool* bdry) {
 SEMMG_HD int64_t elem_face_base(const Geo& G, int a1, int a2, int a3, int f) {
   const int64_t mm = (int64_t)G.m * G.m;
   const int side = f & 1;
+  // the far face of the last element of a periodic axis is plane 0
   switch (f >> 1) {
-    case 0: return G.oF1 + (((int64_t)a3 * G.n2 + a2) * G.nv1 + a1 + side) * mm;
-    case 1: return G.oF2 + (((int64_t)a3 * G.nv2 + a2 + side) * G.n1 + a1) * mm;
-    default: return G.oF3 + (((int64_t)(a3 + side) * G.n2 + a2) * G.n1 + a1) * mm;
+    case 0: {
+      const int c = (side && G.per[0] && a1 + 1 == G.n1) ? 0 : a1 + side;
+      return G.oF1 + (((int64_t)a3 * G.n2 + a2) * G.nv1 + c) * mm;
+    }
+    case 1: {
+      const int c = (side && G.per[1] && a2 + 1 == G.n2) ? 0 : a2 + side;
+      return G.oF2 + (((int64_t)a3 * G.nv2 + c) * G.n1 + a1) * mm;
+    }
+    default: {
+      const int c = (side && G.per[2] && a3 + 1 == G.n3) ? 0 : a3 + side;
+      return G.oF3 + (((int64_t)c * G.n2 + a2) * G.n1 + a1) * mm;
+    }
   }
 }
 

@@ -292,11 +292,14 @@ void build_level_tables(HostLevel& L, const std::vector<double>* h, const int* b
     L.starLam[d].assign((size_t)(nd + 1) * nS, 1.0);
     L.act[d].assign((size_t)(nd + 1) * nS, 0);
     L.sym[d].assign(nd + 1, 0);
+    const bool per = bc[2 * d] == SEMMG_BC_PERIODIC;
     for (int c = 0; c <= nd; ++c) {
       std::vector<double> Mb(nS, 0.0), Lb(nS * nS, 0.0);
       for (int a = c - 1; a <= c; ++a) {
-        if (a < 0 || a >= nd) continue;
-        const double ha = h[d][a];
+        // on a periodic axis the element beyond an end is the one at the other end
+        const int aw = per ? (a + nd) % nd : a;
+        if (aw < 0 || aw >= nd) continue;
+        const double ha = h[d][aw];
         for (int i = 0; i <= p; ++i) {
           const int ji = a * p + i - c * p;
           if (ji < -m || ji > m) continue;
@@ -314,14 +317,15 @@ void build_level_tables(HostLevel& L, const std::vector<double>* h, const int* b
       std::vector<int> act;
       for (int j = -m; j <= m; ++j) {
         const int g = c * p + j;
-        if (g >= glo && g <= ghi) act.push_back(j + m);
+        if (per || (g >= glo && g <= ghi)) act.push_back(j + m);
       }
       double* S = &L.starS[d][(size_t)c * nS * nS];
       double* lam = &L.starLam[d][(size_t)c * nS];
       unsigned char* ac = &L.act[d][(size_t)c * nS];
       for (int i = 0; i < nS; ++i) S[i * nS + i] = 1.0;  // identity padding
       const int na = (int)act.size();
-      const bool sym = (c >= 1 && c <= nd - 1 && na == nS && h[d][c - 1] == h[d][c]);
+      const bool sym = per ? (na == nS && h[d][(c + nd - 1) % nd] == h[d][c % nd])
+                           : (c >= 1 && c <= nd - 1 && na == nS && h[d][c - 1] == h[d][c]);
       L.sym[d][c] = sym ? 1 : 0;
       if (sym) {
         std::vector<double> Ss, ls;
@@ -437,7 +441,8 @@ void build_coarse_tables(int p0, const std::vector<double>* h, const int* bc, Ho
   const int P1 = p0 + 1;
   for (int d = 0; d < 3; ++d) {
     const int nd = (int)h[d].size();
-    const int N = nd * p0 + 1;
+    const bool per = bc[2 * d] == SEMMG_BC_PERIODIC;
+    const int N = per ? nd * p0 : nd * p0 + 1;  // periodic: the last plane is the first
     const int glo = bc[2 * d] == SEMMG_BC_DIRICHLET ? 1 : 0;
     const int ghi = bc[2 * d + 1] == SEMMG_BC_DIRICHLET ? N - 2 : N - 1;
     const int K = ghi - glo + 1;
@@ -449,8 +454,9 @@ void build_coarse_tables(int p0, const std::vector<double>* h, const int* bc, Ho
     std::vector<double> Mg(N, 0.0), Lg((size_t)N * N, 0.0);
     for (int a = 0; a < nd; ++a)
       for (int i = 0; i <= p0; ++i) {
-        Mg[a * p0 + i] += 0.5 * h[d][a] * w[i];
-        for (int k = 0; k <= p0; ++k) Lg[(size_t)(a * p0 + i) * N + (a * p0 + k)] += 2.0 / h[d][a] * Ls[i * P1 + k];
+        const int gi = (a * p0 + i) % N;
+        Mg[gi] += 0.5 * h[d][a] * w[i];
+        for (int k = 0; k <= p0; ++k) Lg[(size_t)gi * N + (a * p0 + k) % N] += 2.0 / h[d][a] * Ls[i * P1 + k];
       }
     std::vector<double> Li((size_t)K * K), Mi(K);
     for (int i = 0; i < K; ++i) {

@@ -240,6 +240,9 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
   int64_t st = blockIdx.x;
   while (st < G.nstar) {
     const int c[3] = {(int)(st % G.nv1), (int)((st / G.nv1) % G.nv2), (int)(st / ((int64_t)G.nv1 * G.nv2))};
+    // the last vertex plane of a periodic axis repeats plane 0: its stars are never read
+    const bool alias = (G.per[0] && c[0] == G.n1) || (G.per[1] && c[1] == G.n2) || (G.per[2] && c[2] == G.n3);
+    if (!alias) {
     const T* S[3];
     __syncthreads();
     if (threadIdx.x < 3) s_sym[threadIdx.x] = t.starSym[threadIdx.x][c[threadIdx.x]];
@@ -434,6 +437,7 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
       const T wgt = t.w1d[oa < 0 ? -oa : oa] * t.w1d[obb < 0 ? -obb : obb] * rcp_mult[(oa == 0) + (obb == 0)];
       ob[idx] = active ? wgt * s : (T)0;
     }
+    }  // !alias
     // next star: from the shared counter when given (dynamic balance), else grid-strided
     if (counter) {
       __syncthreads();

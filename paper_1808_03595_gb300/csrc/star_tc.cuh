@@ -231,6 +231,9 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
   int64_t st = blockIdx.x;
   while (st < G.nstar) {
     const int c[3] = {(int)(st % G.nv1), (int)((st / G.nv1) % G.nv2), (int)(st / ((int64_t)G.nv1 * G.nv2))};
+    // the last vertex plane of a periodic axis repeats plane 0: its stars are never read
+    const bool alias = (G.per[0] && c[0] == G.n1) || (G.per[1] && c[1] == G.n2) || (G.per[2] && c[2] == G.n3);
+    if (!alias) {
     __syncthreads();
     if (tid < 3) s_sym[tid] = t.starSym[tid][c[tid]];
     for (int d = 0; d < 3; ++d)
@@ -443,6 +446,7 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
         ob[dd * n2 + jb * nS + ja] = active ? wgt * v[q] : 0.0f;
       }
     });
+    }  // !alias
     // next star
     if (counter) {
       __syncthreads();

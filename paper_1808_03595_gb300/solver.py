@@ -41,12 +41,13 @@ class Context:
         for d in range(3):
             mesh.n[d] = self.n[d]
             mesh.h[d] = self.h[d].ctypes.data_as(L.P_double)
-        # faces -x1, +x1, -x2, +x2, -x3, +x3: "D" (Dirichlet, default) or "N" (Neumann)
+        # faces -x1, +x1, -x2, +x2, -x3, +x3: "D" (Dirichlet, default), "N" (Neumann), "P" (periodic)
         self.bc = tuple(bc) if bc is not None else ("D",) * 6
-        if len(self.bc) != 6 or any(b not in ("D", "N") for b in self.bc):
-            raise ValueError("bc: six entries, each 'D' or 'N'")
+        if len(self.bc) != 6 or any(b not in ("D", "N", "P") for b in self.bc):
+            raise ValueError("bc: six entries, each 'D', 'N' or 'P'")
+        kinds = {"D": L.SEMMG_BC_DIRICHLET, "N": L.SEMMG_BC_NEUMANN, "P": L.SEMMG_BC_PERIODIC}
         for f in range(6):
-            mesh.bc[f] = L.SEMMG_BC_NEUMANN if self.bc[f] == "N" else L.SEMMG_BC_DIRICHLET
+            mesh.bc[f] = kinds[self.bc[f]]
         opts = L.semmg_opts()
         self._lib.semmg_default_opts(ctypes.byref(opts))
         opts.p0 = p0
