@@ -410,14 +410,15 @@ def run_semmg(args, world, rank, local, pg):
 
 def run_configs(args, dev, stream, flush):
     """The other workloads of the paper's shape, one solve per form each (not part of `value`):
-    Helmholtz 16^3 at p = 16 (lambda 0 and 100, Dirichlet; lambda 1 with Neumann faces) and Poisson on
-    6^3 stretched elements at p = 48."""
+    Helmholtz 16^3 at p = 16 (lambda 0 and 100, Dirichlet; lambda 1 with Neumann faces and periodic) and
+    Poisson on 6^3 stretched elements at p = 48."""
     import torch
     from paper_1808_03595_gb300 import Context
     out = {}
     plan = [("helmholtz_16x16x16_p16", 0.0, None, ["fp64", "mixed", "mixed_tc", "kmg_mixed"]),
             ("helmholtz_16x16x16_p16", 100.0, None, ["fp64", "mixed"]),
             ("helmholtz_16x16x16_p16", 1.0, ("N",) * 6, ["fp64", "mixed", "kmg_mixed"]),
+            ("helmholtz_16x16x16_p16", 1.0, ("P",) * 6, ["fp64", "mixed", "kmg_mixed"]),
             ("poisson_6x6x6_p48_stretched", None, None, ["fp64", "mixed", "kmg_fp64", "kmg_mixed"])]
     for name, lam, bc, forms in plan:
         h, p, lam0, f, p0 = workloads.config(name, lam=lam)
@@ -425,7 +426,7 @@ def run_configs(args, dev, stream, flush):
         fd = torch.as_tensor(f, dtype=torch.float64, device=dev)
         ud = torch.empty_like(fd)
         n = int(fd.numel())
-        key = f"{name}_lambda{lam:g}" + ("_neumann" if bc else "")
+        key = f"{name}_lambda{lam:g}" + ({"N": "_neumann", "P": "_periodic"}[bc[0]] if bc else "")
         out[key] = {"unknowns": n}
         for form in forms:
             prec, solver = FORMS[form]
