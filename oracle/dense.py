@@ -89,6 +89,17 @@ class Mesh:
     def flat(self, g1, g2, g3):
         return (np.asarray(g3) * self.N[1] + np.asarray(g2)) * self.N[0] + np.asarray(g1)
 
+    def dirichlet_mask(self):
+        """Nodal mask of the nodes on a Dirichlet face (where boundary values are prescribed)."""
+        G3, G2, G1 = np.meshgrid(np.arange(self.N[2]), np.arange(self.N[1]), np.arange(self.N[0]), indexing="ij")
+        m = np.zeros(self.shape, bool)
+        for d, g in enumerate((G1, G2, G3)):
+            if self.bc[2 * d] == "D":
+                m |= g == 0
+            if self.bc[2 * d + 1] == "D":
+                m |= g == self.N[d] - 1
+        return m
+
 
 def element_operator(p, h1, h2, h3, lam):
     """Dense element Helmholtz operator, eq. helmholtzop with coefficients d_e (Sec. 2.1)."""
@@ -229,6 +240,19 @@ class Condensed:
         if len(self.I):
             u[self.I] = self._solve_ii(F[self.I] - self.Hib @ uB)
         return sync_images(self.mesh, u.reshape(self.mesh.shape))
+
+    def lifted_load(self, f_nodal, g_nodal):
+        """Inhomogeneous Dirichlet data by lifting (Sec. 5.2 test problem): u = u_0 + E g with E g equal to g on
+        the Dirichlet-face nodes and zero elsewhere, so H u_0 = M f - H E g with homogeneous conditions."""
+        Eg = np.where(self.mesh.dirichlet_mask(), np.asarray(g_nodal, float), 0.0).ravel()
+        return self.load(f_nodal) - self.H @ Eg
+
+    def full_solve_dirichlet(self, f_nodal, g_nodal):
+        """Exact discrete solution of H u = M f with u = g on the Dirichlet faces: the free rows of the
+        uncondensed system with the prescribed values moved to the right-hand side."""
+        dm = self.mesh.dirichlet_mask()
+        u = np.where(dm, np.asarray(g_nodal, float), 0.0)
+        return self.full_solve(self.lifted_load(f_nodal, g_nodal)) + u
 
     def full_solve(self, F):
         """Exact discrete solution of the uncondensed system H u = F (free nodes), nodal array."""

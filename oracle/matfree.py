@@ -186,10 +186,35 @@ def mass_diag(mesh):
     return assemble_blocks(blocks, mesh)
 
 
+def apply_full(mesh, u, chunk=512):
+    """H u on every node of a nodal array (eq. helmholtzop per element, assembled), periodic images synced."""
+    p = mesh.p
+    d = elem_coeffs(mesh)
+    n1, n2, n3 = mesh.n
+    bflat = elem_blocks(u, mesh).reshape(-1, p + 1, p + 1, p + 1)
+    dflat = d.reshape(-1, 4)
+    out = np.empty_like(bflat)
+    for s in range(0, bflat.shape[0], chunk):
+        out[s:s + chunk] = apply_elem_op(bflat[s:s + chunk], dflat[s:s + chunk], p)
+    return assemble_blocks(out.reshape(n3, n2, n1, p + 1, p + 1, p + 1), mesh)
+
+
+def lifted_load(mesh, f, g):
+    """Load of the homogeneous problem for u = u_0 + E g (inhomogeneous Dirichlet data by lifting, the Sec. 5.2
+    test problem): F = M f - H E g, E g equal to g on the Dirichlet-face nodes and zero elsewhere."""
+    Eg = np.where(mesh.dirichlet_mask(), np.asarray(g, float), 0.0)
+    return mass_diag(mesh) * np.asarray(f, float) - apply_full(mesh, Eg)
+
+
 def condense_rhs(mesh, f, chunk=512):
     """F = M f;  Fhat = F_B - sum_e H_BI H_II^{-1} F_I (Algorithm 4, condensation step)."""
+    return condense_load(mesh, mass_diag(mesh) * np.asarray(f, float), chunk)
+
+
+def condense_load(mesh, F, chunk=512):
+    """Fhat = F_B - sum_e H_BI H_II^{-1} F_I for an assembled nodal load F (Sec. 2.2)."""
     p = mesh.p
-    F = mass_diag(mesh) * np.asarray(f, float)
+    F = np.asarray(F, float)
     Fh = np.where(condensed_mask(mesh), F, 0.0)
     if p == 1:
         return Fh
@@ -209,11 +234,16 @@ def condense_rhs(mesh, f, chunk=512):
 
 def recover(mesh, f, uhat, chunk=512):
     """Nodal u: skeleton values from uhat, u_I = H_II^{-1} (F_I - H_IB u_B) per element."""
+    return recover_load(mesh, mass_diag(mesh) * np.asarray(f, float), uhat, chunk)
+
+
+def recover_load(mesh, F, uhat, chunk=512):
+    """recover() for an assembled nodal load F instead of M f."""
     p = mesh.p
     u = np.where(condensed_mask(mesh), uhat, 0.0)
     if p == 1:
         return dense.sync_images(mesh, u)
-    F = mass_diag(mesh) * np.asarray(f, float)
+    F = np.asarray(F, float)
     d = elem_coeffs(mesh)
     ub = elem_blocks(u, mesh).reshape(-1, p + 1, p + 1, p + 1)
     fb = elem_blocks(F, mesh).reshape(-1, p + 1, p + 1, p + 1)
@@ -551,3 +581,15 @@ def solve(mesh, f, p0=1, rtol=1e-10, maxit=50):
     Fh = condense_rhs(mesh, f)
     uh, it, hist = mg_solve(mg, Fh, rtol, maxit)
     return recover(mesh, f, uh), it, hist
+
+
+def solve_dirichlet(mesh, f, g, p0=1, rtol=1e-10, maxit=50, krylov=False, mg=None):
+    """Whole solver with inhomogeneous Dirichlet data g (nodal; read on the Dirichlet faces only), by lifting:
+    F = M f - H E g, condense, Algorithm 4 (or 5), recover u_0, u = u_0 + E g.
+    Returns (u_nodal, iterations, history)."""
+    mg = mg or MG(mesh, p0)
+    F = lifted_load(mesh, f, g)
+    Fh = condense_load(mesh, F)
+    uh, it, hist = (kmg_solve if krylov else mg_solve)(mg, Fh, rtol, maxit)
+    u = recover_load(mesh, F, uh) + np.where(mesh.dirichlet_mask(), np.asarray(g, float), 0.0)
+    return u, it, hist

@@ -225,6 +225,106 @@ def test_manufactured_solution_periodic(bc, kind):
     assert np.array_equal(u[:, :, 0], u[:, :, -1])  # periodic image of the x1 = 0 plane
 
 
+# ---------------------------------------------------------------- inhomogeneous Dirichlet data (Sec. 5.2)
+
+def _poly_case(kind, mesh):
+    """u of degree <= 3 in every variable, fitting the boundary kinds, and f = lam u - Laplace u at the nodes.
+
+    Such u lies in the discrete space, and GLL quadrature with p + 1 points integrates the stiffness
+    terms against it exactly, so the discrete solution with Dirichlet data g = u equals u at every node
+    (up to rounding) on any mesh, for any lambda: a dropped or sign-flipped lifting term fails."""
+    x = mesh.node_coords()
+    X3, X2, X1 = np.meshgrid(x[2], x[1], x[0], indexing="ij")
+    if kind == "D":      # all faces Dirichlet
+        u = 1 + X1 - 2 * X2**2 + X3**3 + X1 * X2 * X3 + X1**2 * X2
+        lap = 2 * X2 - 4 + 6 * X3
+    elif kind == "ND":   # x1 faces Neumann: q'(0) = q'(L1) = 0
+        L1 = mesh.X[0][-1]
+        q, q2 = X1**2 * (3 * L1 - 2 * X1), 6 * L1 - 12 * X1
+        r = 1 + X2 - X3**2 + X2 * X3
+        u, lap = q * r, q2 * r - 2 * q
+    else:                # "PD": x1, x2 periodic (u constant along them), x3 Dirichlet
+        u, lap = X3**3 - 2 * X3 + 1, 6 * X3
+    return u, mesh.lam * u - lap
+
+
+POLY_CASES = [("D", DIRICHLET, 0.0), ("D", DIRICHLET, 0.7), ("ND", ("N", "N", "D", "D", "D", "D"), 0.0),
+              ("ND", ("N", "N", "D", "D", "D", "D"), 2.0), ("PD", ("P", "P", "P", "P", "D", "D"), 0.3)]
+
+
+@pytest.mark.parametrize("p", [3, 4])
+@pytest.mark.parametrize("kind,bc,lam", POLY_CASES)
+def test_lifting_reproduces_polynomials(kind, bc, lam, p):
+    mesh = _mesh_small(p=p, lam=lam, bc=bc)
+    ue, f = _poly_case(kind, mesh)
+    scale = np.abs(ue).max()
+    cond = dense.Condensed(mesh)
+    # uncondensed system with the prescribed values moved to the right-hand side
+    assert np.abs(cond.full_solve_dirichlet(f, ue) - ue).max() < 1e-11 * scale
+    # condensed: Fhat of the lifted load, dense Schur solve, recovery, plus the lifting
+    F = cond.lifted_load(f, ue)
+    uB = np.linalg.solve(cond.Hhat, cond.condense_rhs(F))
+    u = cond.recover(F, uB) + np.where(mesh.dirichlet_mask(), ue, 0.0)
+    assert np.abs(u - ue).max() < 1e-11 * scale
+    # O2: Algorithms 4 and 5 to a 1e-13 residual reduction
+    for krylov in (False, True):
+        u2, it, hist = matfree.solve_dirichlet(mesh, f, ue, p0=1, rtol=1e-13, krylov=krylov)
+        assert hist[-1] <= 1e-13 * hist[0]
+        assert np.abs(u2 - ue).max() < 1e-9 * scale, (krylov, np.abs(u2 - ue).max())
+    # the lifted load of O2 equals O1's at the unknowns
+    F2 = matfree.lifted_load(mesh, f, ue)
+    assert np.abs(F2.ravel()[cond.free] - F[cond.free]).max() < 1e-12 * np.abs(F).max()
+
+
+def test_lifting_load_is_linear_and_local():
+    # F = M f - H E g: zero data gives M f; data on a Neumann face is ignored; the lifting changes the load
+    # only on nodes of elements that touch a Dirichlet face
+    mesh = _mesh_small(p=3, lam=1.0, bc=("D", "N", "N", "N", "N", "N"))
+    rng = _rng(21)
+    f = rng.standard_normal(mesh.shape)
+    g = rng.standard_normal(mesh.shape)
+    F0 = matfree.lifted_load(mesh, f, np.zeros(mesh.shape))
+    assert np.array_equal(F0, matfree.mass_diag(mesh) * f)
+    dm = mesh.dirichlet_mask()
+    g2 = np.where(dm, g, rng.standard_normal(mesh.shape))
+    assert np.array_equal(matfree.lifted_load(mesh, f, g), matfree.lifted_load(mesh, f, g2))
+    dF = matfree.lifted_load(mesh, f, g) - F0
+    assert np.all(dF[:, :, mesh.p + 1:] == 0.0)  # beyond the first element layer along x1
+    assert np.abs(dF[:, :, :mesh.p + 1]).max() > 0
+
+
+@pytest.mark.parametrize("p,bound", [(4, 6e-2), (6, 3e-3), (8, 8e-5), (10, 2e-6)])
+def test_paper_solution_spectral(p, bound):
+    # the runtime tests' manufactured solution of Sec. 5.2 on (0, 2 pi)^3 with inhomogeneous Dirichlet data
+    # at all faces, lambda = 0 (k = 1/2 so that 3^3 elements resolve it): the error decays spectrally
+    import workloads as W
+    h = [np.full(3, 2 * np.pi / 3)] * 3
+    mesh = dense.Mesh(h, p, 0.0)
+    ue, f = W.paper_solution(h, p, k=0.5, lam=0.0)
+    u, it, hist = matfree.solve_dirichlet(mesh, f, ue, p0=1)
+    assert hist[-1] <= 1e-10 * hist[0]
+    assert np.abs(u - ue).max() < bound, (p, np.abs(u - ue).max())
+    assert np.array_equal(u[mesh.dirichlet_mask()], ue[mesh.dirichlet_mask()])
+
+
+def test_paper_solution_laplacian_by_finite_differences():
+    # the analytic right-hand side of the Sec. 5.2 solution against a 4th-order central difference
+    import workloads as W
+    rng = _rng(22)
+    P = rng.uniform(0, 2 * np.pi, size=(3, 7))
+    k, lam, e = 5.0, 0.7, 2e-3
+    u, f = W.paper_solution_at(*P, k, lam)
+    lap = 0.0
+    for d in range(3):
+        vals = []
+        for s in (-2, -1, 1, 2):
+            Q = P.copy()
+            Q[d] += s * e
+            vals.append(W.paper_solution_at(*Q, k, lam)[0])
+        lap = lap + (-vals[0] + 16 * vals[1] - 30 * u + 16 * vals[2] - vals[3]) / (12 * e * e)
+    assert np.abs(lam * u - lap - f).max() < 1e-5 * np.abs(f).max()
+
+
 # ---------------------------------------------------------------- stars (Sec. 2.3, 3)
 
 @pytest.mark.parametrize("c,bc", [((1, 1, 1), DIRICHLET), ((0, 1, 1), DIRICHLET), ((3, 0, 2), DIRICHLET),

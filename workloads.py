@@ -16,6 +16,10 @@ Workloads (names used by bench.py and the tests):
   expansion_widths(n, alpha)
                           per-axis widths in geometric progression on (0, 2 pi), the stretched
                           meshes of the paper's iteration-count table (Sec. 5.4)
+  paper_solution(h, p, k, lam)
+                          the manufactured solution of the paper's runtime tests (Sec. 5.2) on
+                          (0, 2 pi)^3 with inhomogeneous Dirichlet data: (u_ex, f = lam u_ex - Laplace u_ex)
+                          at the GLL nodes, k = 5 in the paper
   batch64                 64 solves, n ~ U{2..12}, p ~ U{4..24}, lambda = 10^U(-2, 3), f ~ U(-1, 1),
                           seed 1808035955
 """
@@ -87,6 +91,39 @@ def sinsinsin(h, p):
 def manufactured_rhs(h, p, lam):
     """f = (lam + 3 pi^2) sin(pi x) sin(pi y) sin(pi z) at the GLL nodes (unit cube)."""
     return (lam + 3 * np.pi**2) * sinsinsin(h, p)
+
+
+# u_ex of Sec. 5.2 as a product of five plane waves trig(k (a . x + b)): (is_cos, a, b)
+_PAPER_FACTORS = ((True, (1.0, -3.0, 2.0), 0.0), (False, (1.0, 0.0, 0.0), 1.0), (False, (0.0, -1.0, 0.0), 1.0),
+                  (False, (2.0, 1.0, 0.0), 0.0), (False, (3.0, -2.0, 2.0), 0.0))
+
+
+def paper_solution_at(X1, X2, X3, k, lam):
+    """(u_ex, f) of Sec. 5.2 at points (X1, X2, X3).  With u = prod_i phi_i, phi_i = trig(theta_i),
+    theta_i = k (a_i . x + b_i):  Laplace u = -k^2 sum_i |a_i|^2 u + 2 k^2 sum_{i<j} (a_i . a_j) phi_i' phi_j'
+    prod_{l != i, j} phi_l, phi' the derivative of trig."""
+    X = (X1, X2, X3)
+    val, der, aa = [], [], []
+    for is_cos, a, b in _PAPER_FACTORS:
+        th = k * (a[0] * X[0] + a[1] * X[1] + a[2] * X[2] + b)
+        val.append(np.cos(th) if is_cos else np.sin(th))
+        der.append(-np.sin(th) if is_cos else np.cos(th))
+        aa.append(np.asarray(a))
+    u = np.prod(val, axis=0)
+    lap = -k * k * sum(float(a @ a) for a in aa) * u
+    nf = len(val)
+    for i in range(nf):
+        for j in range(i + 1, nf):
+            rest = np.prod([val[l] for l in range(nf) if l not in (i, j)], axis=0)
+            lap = lap + 2.0 * k * k * float(aa[i] @ aa[j]) * der[i] * der[j] * rest
+    return u, lam * u - lap
+
+
+def paper_solution(h, p, k=5.0, lam=0.0):
+    """(u_ex, f) of Sec. 5.2 at the GLL nodes of the mesh with widths h (arrays [g3, g2, g1])."""
+    x = node_coords(h, p)
+    X3, X2, X1 = np.meshgrid(x[2], x[1], x[0], indexing="ij")
+    return paper_solution_at(X1, X2, X3, k, lam)
 
 
 def random_nodal(h, p, seed, kind="normal"):
