@@ -12,7 +12,9 @@ gll       1D Gauss-Lobatto-Legendre basis: nodes, weights, differentiation and
 dense     O1: the plain definitions with explicit (sparse/dense) matrices on tiny
           meshes -- element assembly (Sec. 2.1), Schur complement (Sec. 2.2),
           dense star inverses (Sec. 2.3), Algorithm 1 with explicit tables,
-          Algorithm 2, embedded-interpolation transfers, Algorithms 3 and 4.
+          Algorithm 2, element-centred block inverses (Sec. 3.4),
+          embedded-interpolation transfers, Algorithms 3 and 4, boundary
+          kinds (Sec. 3.3) and inhomogeneous Dirichlet data by lifting (Sec. 5.2).
 matfree   O2: the same steps matrix-free on nodal arrays, written as loops over
           elements and stars with per-element tensor-product operators, for
           meshes too large for O1.  Pinned against O1 by the tests.

@@ -462,6 +462,107 @@ def smoother_dense(mesh, cond, r, use_alg1=False):
 
 
 # --------------------------------------------------------------------------
+# Element-centred blocks (Sec. 3.4): the 3x3x3 element block around each element
+# --------------------------------------------------------------------------
+
+def eblock_centres(mesh):
+    """One block per element (c1, c2, c3), x1 fastest."""
+    return [(c1, c2, c3) for c3 in range(mesh.n[2]) for c2 in range(mesh.n[1]) for c1 in range(mesh.n[0])]
+
+
+def eblock_check(mesh):
+    """The block of element c spans elements c-1, c, c+1 along every axis (full overlap); on a periodic
+    axis these must be three different elements."""
+    for d in range(3):
+        if mesh.periodic(d) and mesh.n[d] < 3:
+            raise ValueError("element-centred blocks need at least three elements along a periodic axis")
+
+
+def eblock_offsets(mesh, g, c, d):
+    """Offset j of global node indices g inside the block of centre c along axis d: the block's nodes are
+    (c-1) p < g < (c+2) p, j = g - (c-1) p in 1 .. 3p-1 (on a periodic axis, of the image in that range);
+    returns j, or 0 where g is outside."""
+    p = mesh.p
+    j = np.asarray(g) - (c - 1) * p
+    if mesh.periodic(d):
+        j = np.mod(j, mesh.n[d] * p)
+    return np.where((j >= 1) & (j <= 3 * p - 1), j, 0)
+
+
+def eblock_positions(mesh, B, c):
+    """Positions in the condensed vector of the nodes strictly inside the block of element c, and their
+    offsets (j1, j2, j3), each in 1 .. 3p-1."""
+    g1 = B % mesh.N[0]
+    g2 = (B // mesh.N[0]) % mesh.N[1]
+    g3 = B // (mesh.N[0] * mesh.N[1])
+    j = np.stack([eblock_offsets(mesh, g, c[d], d) for d, g in enumerate((g1, g2, g3))], axis=1)
+    pos = np.flatnonzero(np.all(j > 0, axis=1))
+    return pos, j[pos]
+
+
+def eblock_line_table(mesh, d, c):
+    """1D eigen-table of the block line of element c along axis d (Sec. 3.4 with the padding of Sec. 3.3).
+
+    Block nodes g = (c-1) p + j, j = 1 .. 3p-1 (n_S = 3p - 1): the assembled 1D matrices restricted to them
+    are those of the three elements c-1, c, c+1 with the block ends removed.  Nodes that are not unknowns
+    of the domain (ghost elements beyond a face, Dirichlet faces) are decoupled: S padded with identity,
+    Lambda with 1.  Returns S with S^T M S = I and S^T L S = Lambda on the active nodes, Lambda, active mask.
+    """
+    p = mesh.p
+    nS = 3 * p - 1
+    Mg, Lg = assembled_1d(mesh, d)
+    graw = (c - 1) * p + np.arange(1, 3 * p)
+    lo, hi = mesh.g_range(d)
+    if mesh.periodic(d):
+        g = mesh.wrap(graw, d)
+        active = np.ones(nS, bool)
+    else:
+        g = graw
+        active = (g >= lo) & (g <= hi)
+    S = np.eye(nS)
+    lam = np.ones(nS)
+    ia = np.flatnonzero(active)
+    if ia.size:
+        ga = g[ia]
+        ev, V = sla.eigh(Lg[np.ix_(ga, ga)], Mg[np.ix_(ga, ga)])
+        S[np.ix_(ia, ia)] = V
+        lam[ia] = ev
+    return S, lam, active
+
+
+def eblock_count_1d(mesh, d):
+    """Per global node index along axis d: the number of element-centred blocks whose node range holds it."""
+    g = np.arange(mesh.N[d])
+    return sum((eblock_offsets(mesh, g, c, d) > 0).astype(int) for c in range(mesh.n[d]))
+
+
+def eblock_weights(mesh, B, pos):
+    """Inverse multiplicity (Sec. 2.3: each point weighted with the inverse of the number of subdomains it
+    lies in) at condensed positions pos; block membership is a tensor product, so the count is the product
+    of the per-axis counts."""
+    g = (B[pos] % mesh.N[0], (B[pos] // mesh.N[0]) % mesh.N[1], B[pos] // (mesh.N[0] * mesh.N[1]))
+    cnt = np.ones(len(pos))
+    for d in range(3):
+        cnt *= eblock_count_1d(mesh, d)[g[d]]
+    return 1.0 / cnt
+
+
+def smoother_eblock_dense(mesh, cond, r):
+    """Element-centred Schwarz smoother (Sec. 3.4 as a drop-in for the stars in eq. smoother_definition):
+    Delta u = sum_c R_c^T W_c Hhat_c^{-1} R_c r over all elements c, Hhat_c = R_c Hhat R_c^T, W_c the
+    inverse multiplicity; each block inverse applied densely."""
+    eblock_check(mesh)
+    du = np.zeros_like(r)
+    for c in eblock_centres(mesh):
+        pos, _ = eblock_positions(mesh, cond.B, c)
+        if pos.size == 0:
+            continue
+        dui = np.linalg.solve(cond.Hhat[np.ix_(pos, pos)], r[pos])
+        du[pos] += eblock_weights(mesh, cond.B, pos) * dui
+    return du
+
+
+# --------------------------------------------------------------------------
 # p-multigrid (Sec. 4.1)
 # --------------------------------------------------------------------------
 

@@ -12,7 +12,10 @@ O(p^3) factorisations except where the paper prescribes them (Algorithm 1):
         (H_e [u_B; 0])_B - (H_e [0; H_II^{-1} (H_e [u_B; 0])_I])_B,
     with H_II^{-1} by 3D fast diagonalisation of the element interior block
     (eq. fast_diagonalization for one element);
-  * smoother: Algorithm 2 around Algorithm 1 on every vertex star;
+  * smoother: Algorithm 2 around Algorithm 1 on every vertex star; or the
+    element-centred 3^3-element blocks of Sec. 3.4, each inverted by the
+    embedding of Sec. 3.1 and the full block's fast diagonalisation, weighted
+    with the inverse multiplicity;
   * transfers: per-element 3D embedded interpolation and its exact transpose;
   * coarse solve: exact sparse direct solve of the full coarse system with the
     embedded right-hand side (F_hat, 0) (Sec. 3.1, eq. star_right_hand_side_full
@@ -371,6 +374,61 @@ def smooth(mesh, r, tables=None, chunk=128):
     return np.where(condensed_mask(mesh), du, 0.0)
 
 
+class EBlockTables:
+    """Per element and axis the block line eigen-tables (Sec. 3.4) and the 1D inverse-multiplicity factors."""
+
+    def __init__(self, mesh):
+        dense.eblock_check(mesh)
+        self.mesh = mesh
+        self.S, self.Lam, self.act = [], [], []
+        for d in range(3):
+            tabs = [dense.eblock_line_table(mesh, d, c) for c in range(mesh.n[d])]
+            self.S.append(np.array([t[0] for t in tabs]))
+            self.Lam.append(np.array([t[1] for t in tabs]))
+            self.act.append(np.array([t[2] for t in tabs]))
+        self.winv = [1.0 / np.maximum(dense.eblock_count_1d(mesh, d), 1) for d in range(3)]
+
+
+def smooth_eblock(mesh, r, tables=None):
+    """Delta u = sum_c R_c^T W_c Hhat_c^{-1} R_c r over the element-centred blocks (Sec. 3.4).
+
+    Each block inverse by the embedding of Sec. 3.1 and the block's fast diagonalisation: the condensed
+    residual, zero at element-interior nodes, is the right-hand side of the full 3^3-element block
+    problem; its solution (S3 x S2 x S1) D^{-1} (S3 x S2 x S1)^T on the block, read at the block's skeleton
+    nodes, is Hhat_c^{-1} R_c r.  W_c = inverse multiplicity.
+    """
+    p = mesh.p
+    tables = tables or EBlockTables(mesh)
+    r = np.where(condensed_mask(mesh), r, 0.0)
+    du = np.zeros(mesh.shape)
+    j = np.arange(1, 3 * p)
+    on_plane = (j == p) | (j == 2 * p)
+    lam = mesh.lam
+    for c in dense.eblock_centres(mesh):
+        gi, ok = [], []
+        for d in range(3):
+            g = (c[d] - 1) * p + j
+            if mesh.periodic(d):
+                gi.append(np.mod(g, mesh.n[d] * p))
+                ok.append(np.ones(len(j), bool))
+            else:
+                ok.append((g >= 0) & (g < mesh.N[d]))
+                gi.append(np.clip(g, 0, mesh.N[d] - 1))
+        idx = np.ix_(gi[2], gi[1], gi[0])
+        inside = ok[2][:, None, None] & ok[1][None, :, None] & ok[0][None, None, :]
+        R = np.where(inside, r[idx], 0.0)
+        S1, S2, S3 = tables.S[0][c[0]], tables.S[1][c[1]], tables.S[2][c[2]]
+        Ft = np.einsum("ijk,ic,jb,ka->cba", R, S3, S2, S1, optimize=True)
+        D = lam + tables.Lam[2][c[2]][:, None, None] + tables.Lam[1][c[1]][None, :, None] \
+            + tables.Lam[0][c[0]][None, None, :]
+        U = np.einsum("cba,ic,jb,ka->ijk", Ft / D, S3, S2, S1, optimize=True)
+        skel = on_plane[:, None, None] | on_plane[None, :, None] | on_plane[None, None, :]
+        W = tables.winv[2][gi[2]][:, None, None] * tables.winv[1][gi[1]][None, :, None] \
+            * tables.winv[0][gi[0]][None, None, :]
+        np.add.at(du, idx, np.where(inside & skel, W * U, 0.0))
+    return np.where(condensed_mask(mesh), du, 0.0)
+
+
 def _pad_star(mesh, r, P):
     """Pad a nodal array by P on every side: zeros, or on a periodic axis the
     values wrapped around the n_d p unknowns (a star near one end reads the other)."""
@@ -476,10 +534,14 @@ class CoarseSolver:
 class MG:
     """p-multigrid hierarchy (Sec. 4.1) on nodal condensed arrays."""
 
-    def __init__(self, mesh, p0=1, nu_pre=1, nu_post=1, nu_vary=False):
+    def __init__(self, mesh, p0=1, nu_pre=1, nu_post=1, nu_vary=False, smoother="star"):
         self.degs = dense.level_degrees(mesh.p, p0)
         self.meshes = [mesh.with_degree(q) for q in self.degs]
-        self.tables = [StarTables(m) for m in self.meshes]
+        if smoother not in ("star", "element"):
+            raise ValueError("smoother: 'star' (Algorithm 2) or 'element' (element-centred blocks, Sec. 3.4)")
+        self.smoother = smoother
+        self.tables = [(StarTables(m) if smoother == "star" else EBlockTables(m)) if l > 0 else None
+                       for l, m in enumerate(self.meshes)]
         self.coarse = CoarseSolver(self.meshes[0])
         self.nu_pre, self.nu_post = nu_pre, nu_post
         self.nu_vary = nu_vary
@@ -496,6 +558,8 @@ class MG:
         return apply_condensed(self.meshes[l], u)
 
     def smooth(self, l, r):
+        if self.smoother == "element":
+            return smooth_eblock(self.meshes[l], r, self.tables[l])
         return smooth(self.meshes[l], r, self.tables[l])
 
 

@@ -399,6 +399,98 @@ def test_smoother_alg1_equals_dense_inverse(p, lam, bc):
     assert np.abs(d_o2 - d_dense).max() < 1e-12 * scale
 
 
+# ---------------------------------------------------------------- element-centred blocks (Sec. 3.4)
+
+def _mesh_eblock(p=3, lam=0.8, bc=None):
+    # three elements along every axis (a periodic axis needs three for distinct block elements)
+    return dense.Mesh([np.full(3, 1 / 3), np.array([0.2, 0.5, 0.3]), np.array([0.7, 0.3, 0.4])], p, lam, bc)
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC, PERIODIC_BC, ("P",) * 6])
+def test_eblock_tables_generalized_eigen(bc):
+    mesh = _mesh_eblock(p=4, bc=bc)
+    for d in range(3):
+        Mg, Lg = dense.assembled_1d(mesh, d)
+        for c in range(mesh.n[d]):
+            S, lam, act = dense.eblock_line_table(mesh, d, c)
+            assert S.shape == (3 * mesh.p - 1,) * 2
+            g = mesh.wrap((c - 1) * mesh.p + np.arange(1, 3 * mesh.p), d)
+            ia = np.flatnonzero(act)
+            Sa = S[np.ix_(ia, ia)]
+            Ma, La = Mg[np.ix_(g[ia], g[ia])], Lg[np.ix_(g[ia], g[ia])]
+            np.testing.assert_allclose(Sa.T @ Ma @ Sa, np.eye(len(ia)), atol=1e-12)
+            np.testing.assert_allclose(Sa.T @ La @ Sa, np.diag(lam[ia]), atol=1e-10 * lam.max())
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC, NEUMANN, PERIODIC_BC, ("P",) * 6])
+def test_eblock_weights_partition_of_unity(bc):
+    # sum over the blocks holding an unknown of its weight is one (inverse multiplicity, Sec. 2.3)
+    mesh = _mesh_eblock(p=3, bc=bc)
+    cond = dense.Condensed(mesh, dense=False)
+    tot = np.zeros(len(cond.B))
+    cnt = np.zeros(len(cond.B))
+    for c in dense.eblock_centres(mesh):
+        pos, j = dense.eblock_positions(mesh, cond.B, c)
+        tot[pos] += dense.eblock_weights(mesh, cond.B, pos)
+        cnt[pos] += 1
+        assert np.all((j >= 1) & (j <= 3 * mesh.p - 1))
+    np.testing.assert_allclose(tot, 1.0, rtol=0, atol=1e-15)
+    # a face node of an interior element lies in 2 x 3 x 3 blocks
+    assert cnt.max() <= 27 and cnt.min() >= 1
+
+
+@pytest.mark.parametrize("p,lam,bc", [(2, 0.0, DIRICHLET), (3, 0.8, DIRICHLET), (4, 2.0, MIXED_BC),
+                                      (3, 0.5, NEUMANN), (3, 0.0, PERIODIC_BC), (4, 1.0, ("P",) * 6)])
+def test_eblock_fdm_equals_dense_inverse(p, lam, bc):
+    # the embedding of Sec. 3.1 applied to the 3^3-element block: the full block's fast diagonalisation
+    # read on the block's skeleton equals the inverse of the restricted condensed operator
+    mesh = _mesh_eblock(p=p, lam=lam, bc=bc)
+    cond = dense.Condensed(mesh)
+    r = _rng(23).standard_normal(len(cond.B))
+    d_dense = dense.smoother_eblock_dense(mesh, cond, r)
+    rn = np.zeros(mesh.shape)
+    rn.ravel()[cond.B] = r
+    d_o2 = matfree.smooth_eblock(mesh, rn).ravel()[cond.B]
+    assert np.abs(d_o2 - d_dense).max() < 1e-12 * np.abs(d_dense).max()
+
+
+@pytest.mark.parametrize("bc", [("N", "N", "D", "D", "D", "D"), ("N", "D", "N", "D", "D", "N"), NEUMANN])
+def test_eblock_single_element_is_exact_inverse(bc):
+    # one element (its skeleton unknowns are on the Neumann faces): its block holds every unknown with
+    # weight one, so the smoother is Hhat^{-1}
+    mesh = dense.Mesh([np.array([0.7]), np.array([1.3]), np.array([0.4])], 5, 0.6, bc)
+    cond = dense.Condensed(mesh)
+    r = _rng(24).standard_normal(len(cond.B))
+    exact = np.linalg.solve(cond.Hhat, r)
+    assert np.abs(dense.smoother_eblock_dense(mesh, cond, r) - exact).max() < 1e-12 * np.abs(exact).max()
+    rn = np.zeros(mesh.shape)
+    rn.ravel()[cond.B] = r
+    d_o2 = matfree.smooth_eblock(mesh, rn).ravel()[cond.B]
+    assert np.abs(d_o2 - exact).max() < 1e-11 * np.abs(exact).max()
+
+
+def test_eblock_periodic_needs_three_elements():
+    mesh = dense.Mesh([np.full(2, 0.5), np.full(3, 1 / 3), np.full(3, 1 / 3)], 3, 1.0, ("P", "P", "D", "D", "D", "D"))
+    with pytest.raises(ValueError):
+        matfree.EBlockTables(mesh)
+
+
+@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC, PERIODIC_BC])
+def test_eblock_mg_matches_direct_solve(bc):
+    # the element-centred smoother as a drop-in in Algorithms 3 and 4 (and 5)
+    mesh = _mesh_eblock(p=5, lam=0.0 if bc == DIRICHLET else 1.0, bc=bc)
+    cond = dense.Condensed(mesh)
+    f = _rng(25).uniform(-1, 1, mesh.shape)
+    uex = cond.full_solve(cond.load(f))
+    mg = matfree.MG(mesh, p0=1, smoother="element")
+    Fh = matfree.condense_rhs(mesh, f)
+    for solve in (matfree.mg_solve, matfree.kmg_solve):
+        uh, it, hist = solve(mg, Fh)
+        assert hist[-1] <= 1e-10 * hist[0] and it <= 12
+        u = matfree.recover(mesh, f, uh)
+        assert np.abs(u - uex).max() < 1e-8 * np.abs(uex).max()
+
+
 # ---------------------------------------------------------------- transfers (Sec. 4.1)
 
 @pytest.mark.parametrize("pc,pf,bc", [(1, 2, DIRICHLET), (2, 4, DIRICHLET), (4, 6, DIRICHLET), (2, 4, MIXED_BC),
