@@ -19,6 +19,7 @@ Multi-GPU runs are replicas (the path has no exchange step on one mesh).
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -41,7 +42,10 @@ METRIC = "unknowns/s per solve to 1e-10 residual (FP64 vs mixed); smoother HBM G
 # "mixed" the mixed-precision line (FP32 smoother and transfers, FP64 residuals).
 FORMS = {"fp64": ("fp64", "mg"), "mixed": ("mixed", "mg"), "mixed_fp32": ("mixed_fp32", "mg"),
          "mixed_tc": ("mixed_tc", "mg"), "kmg_fp64": ("fp64", "kmg"), "kmg_mixed": ("mixed", "kmg"),
-         "kmg_mixed_tc": ("mixed_tc", "kmg")}
+         "kmg_mixed_tc": ("mixed_tc", "kmg"), "eblock_fp64": ("fp64", "mg"), "eblock_mixed": ("mixed", "mg"),
+         "eblock_mult_mixed": ("mixed", "mg")}
+# forms with the element-centred block smoother (Sec. 3.4) instead of the vertex stars
+ELEMENT_FORMS = {"eblock_fp64": "element", "eblock_mixed": "element", "eblock_mult_mixed": "element_mult"}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 entry in the peaks file)
 # DRAM bytes (read + write) per k_star<double> launch of the timed FP64 sweep: ncu
 # --metrics dram__bytes_read.sum,dram__bytes_write.sum per launch of `bench.py --forms fp64
@@ -49,8 +53,16 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 entry in th
 # weighted by the sweep's star launches per degree (28 at p = 4, 20 at 8, 12 at 16, 6 at 32);
 # profiles/k_star_f64_dram_helmholtz_8x8x8.md.  Valid only for the star-kernel source it was
 # measured on (hash below).
-STAR_TRAFFIC_BYTES = 7.896e6
-STAR_TRAFFIC_SOURCE = "60486a70c5a71e71"
+STAR_TRAFFIC_BYTES = 6.770e6
+STAR_TRAFFIC_SOURCE = "648dc13e3897f612"
+# Executed FP64 operations (2 DFMA + DMUL + DADD thread instructions, ncu sass counters) per
+# k_star<double> launch, per level degree, from `bench.py --degrees 32 --forms fp64 --no-e2e --no-batch
+# --no-configs --no-cpu-baseline --no-autotune --steps 1 --warmup 3` (the first launch at each of
+# p = 32, 16, 8, 4; profiles/k_star_f64_executed_ops_helmholtz_8x8x8.md), weighted like the traffic:
+# the kernel executes 34-42 % of the paper's 37 n_S^3 count, so this rate measures the FP64 pipe.
+STAR_EXEC_FLOPS = {4: 0.00392e9, 8: 0.03320e9, 16: 0.27501e9, 32: 2.26214e9}
+STAR_EXEC_WEIGHTS = {4: 28, 8: 20, 16: 12, 32: 6}
+STAR_EXEC_SOURCE = "648dc13e3897f612"
 STAR_SOURCES = ("star_kernel.cuh", "kernels_star_f64.cu")
 
 
@@ -164,7 +176,7 @@ def max_over_ranks(pg, value):
 
 # ---------------------------------------------------------------- reference arm: the oracle on the host
 
-def oracle_sample(p=8):
+def oracle_sample(p=16):
     """One O2 (oracle) solve of the 8x8x8 Helmholtz workload at degree p; returns (unknowns, seconds, iters)."""
     from oracle import dense, matfree
     h, p, lam, f, p0 = workloads.config(f"helmholtz_8x8x8_p{p}")
@@ -231,7 +243,8 @@ def run_semmg(args, world, rank, local, pg):
         c = {"p": p, "n": int(fd.numel()), "f": fd, "u": ud, "fh": fh, "uh": uh}
         for form in forms:
             prec, solver = FORMS[form]
-            c[form] = Context(h, p, lam, p0=p0, precision=prec, solver=solver)
+            c[form] = Context(h, p, lam, p0=p0, precision=prec, solver=solver,
+                              smoother=ELEMENT_FORMS.get(form, "star"))
         cases.append(c)
     tuned = {}
     if args.autotune:
@@ -309,9 +322,10 @@ def run_semmg(args, world, rank, local, pg):
         kk = kstform.setdefault(form, {})
         for c in cases:
             for k, v in c[form].kstats().items():
-                acc = kk.setdefault(k, {"ms": 0.0, "launches": 0})
+                acc = kk.setdefault(k, {"ms": 0.0, "launches": 0, "flops": 0.0})
                 acc["ms"] += v["ms"]
                 acc["launches"] += v["launches"]
+                acc["flops"] += v["flops"]
             c[form].set_timing(False)
     t32 = tform.get("mixed", float("nan"))
     it32 = itform.get("mixed", {})
@@ -337,10 +351,12 @@ def run_semmg(args, world, rank, local, pg):
                           "iterations": it64}}
     for form, tf in tform.items():
         v = world * unknowns * args.steps / (tf / 1e3)
-        forms_out[form] = {"precision": FORMS[form][0], "solver": FORMS[form][1], "value": v,
+        forms_out[form] = {"precision": FORMS[form][0], "solver": FORMS[form][1],
+                           "smoother": ELEMENT_FORMS.get(form, "star"), "value": v,
                            "ms_per_step": tf / args.steps, "iterations": itform[form], "speedup_vs_fp64": v / value,
                            "kernels": {k: {"ms_per_step": x["ms"] / args.steps,
-                                           "launches_per_step": x["launches"] / args.steps}
+                                           "launches_per_step": x["launches"] / args.steps,
+                                           "tflops": (x["flops"] / (x["ms"] / 1e3) / 1e12) if x["flops"] else None}
                                        for k, x in kstform[form].items()}}
 
     # roofline of the dominant kernel (FP64 form): FP64-ALU bound
@@ -353,10 +369,15 @@ def run_semmg(args, world, rank, local, pg):
     if dom == "star":
         if star_source_hash() == STAR_TRAFFIC_SOURCE:
             traffic = STAR_TRAFFIC_BYTES
+    executed = None
+    if dom == "star" and star_source_hash() == STAR_EXEC_SOURCE and degrees == SWEEP:
+        per_launch = sum(STAR_EXEC_FLOPS[q] * STAR_EXEC_WEIGHTS[q] for q in SWEEP) / sum(STAR_EXEC_WEIGHTS.values())
+        rate = per_launch * d["launches"] / (d["ms"] / 1e3) / 1e12
+        executed = {"flops_per_launch": per_launch, "achieved": rate, "frac": rate / FP64_PEAK_TFLOPS}
     if d["flops"] > 0:
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom, "executed": executed,
                 "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
                 "peak_source": "nominal FP64 1.25 TFLOP/s (2 FP64 FMA/clk/SM x 152 SMs at 2.07 GHz)",
                 "launches": d["launches"], "share_of_kernel_time": d["ms"] / total_ms,
@@ -419,10 +440,20 @@ def run_configs(args, dev, stream, flush):
             ("helmholtz_16x16x16_p16", 100.0, None, ["fp64", "mixed"]),
             ("helmholtz_16x16x16_p16", 1.0, ("N",) * 6, ["fp64", "mixed", "kmg_mixed"]),
             ("helmholtz_16x16x16_p16", 1.0, ("P",) * 6, ["fp64", "mixed", "kmg_mixed"]),
-            ("poisson_6x6x6_p48_stretched", None, None, ["fp64", "mixed", "kmg_fp64", "kmg_mixed"])]
+            ("poisson_6x6x6_p48_stretched", None, None, ["fp64", "mixed", "kmg_fp64", "kmg_mixed"]),
+            ("paper_sec52_8x8x8_p16", 0.0, None, ["fp64", "mixed", "kmg_mixed"]),
+            ("paper_sec52_8x8x8_p32", 0.0, None, ["fp64", "mixed", "kmg_mixed"])]
     for name, lam, bc, forms in plan:
-        h, p, lam0, f, p0 = workloads.config(name, lam=lam)
-        lam = lam0 if lam is None else lam
+        gd = ue = None
+        if name.startswith("paper_sec52"):
+            # the runtime tests' problem: (0, 2 pi)^3, k = 5, lambda = 0, inhomogeneous Dirichlet data
+            p, p0 = int(name.rsplit("_p", 1)[1]), 2
+            h = workloads.uniform_widths(8, 2 * math.pi)
+            ue, f = workloads.paper_solution(h, p, 5.0, lam)
+            gd = torch.as_tensor(ue, dtype=torch.float64, device=dev)
+        else:
+            h, p, lam0, f, p0 = workloads.config(name, lam=lam)
+            lam = lam0 if lam is None else lam
         fd = torch.as_tensor(f, dtype=torch.float64, device=dev)
         ud = torch.empty_like(fd)
         n = int(fd.numel())
@@ -434,19 +465,21 @@ def run_configs(args, dev, stream, flush):
                 if args.autotune:
                     c.autotune()
                 for _ in range(args.warmup):
-                    c.solve(fd, out=ud)
+                    c.solve(fd, out=ud, g=gd)
                 ms = 0.0
                 for _ in range(args.steps):
                     flush.fill_(1.0)
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    _, info = c.solve(fd, out=ud)
+                    _, info = c.solve(fd, out=ud, g=gd)
                     e1.record(stream)
                     e1.synchronize()
                     ms += e0.elapsed_time(e1)
                     assert info.res_final <= 1e-10 * info.res0, (key, form)
             out[key][form] = {"value": n * args.steps / (ms / 1e3), "ms": ms / args.steps, "iterations": info.iters}
+            if ue is not None:
+                out[key][form]["max_error_vs_exact"] = float(torch.max(torch.abs(ud - gd)))
     return out
 
 
@@ -503,7 +536,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="semmg", choices=["semmg", "reference"])
     ap.add_argument("--degrees", default=",".join(str(p) for p in SWEEP))
-    ap.add_argument("--cpu-sample-p", type=int, default=8)
+    ap.add_argument("--cpu-sample-p", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--forms", default=",".join(FORMS),
                     help="forms to time, from " + ", ".join(FORMS) + " (fp64 is always timed: the headline)")
@@ -511,7 +544,7 @@ def main():
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="tune launch shapes per degree before the warm-up (outside the timed region)")
     ap.add_argument("--configs", action=argparse.BooleanOptionalAction, default=True,
-                    help="also time the 16^3 p=16 and 6^3 p=48 stretched workloads (reported under configs)")
+                    help="also time the 16^3 p=16, 6^3 p=48 stretched and Sec. 5.2 workloads (under configs)")
     ap.add_argument("--batch", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the 64-solve batched graph workload")
     args = ap.parse_args()

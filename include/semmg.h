@@ -84,6 +84,14 @@ enum {
 enum { SEMMG_FP64 = 0, SEMMG_MIXED = 1, SEMMG_MIXED_FP32 = 2, SEMMG_MIXED_TC = 3 };
 /* outer iteration of semmg_solve and of the batched form */
 enum { SEMMG_SOLVER_MG = 0, SEMMG_SOLVER_KMG = 1 };
+/* Schwarz smoother of the V-cycle levels */
+enum {
+  SEMMG_SMOOTHER_STAR = 0,         /* vertex stars, Algorithm 2 around Algorithm 1 (Sec. 3.2), default */
+  SEMMG_SMOOTHER_ELEMENT = 1,      /* element-centred 3x3x3-element blocks with full overlap (Sec. 3.4),
+                                      weights one on the element's own nodes, zero on the other elements',
+                                      one half on faces shared with a neighbour block */
+  SEMMG_SMOOTHER_ELEMENT_MULT = 2  /* the same blocks, inverse-multiplicity weights (Sec. 2.3) */
+};  /* the element-centred smoothers need n[d] >= 3 on periodic axes */
 /* element type of a vector argument of smooth / restrict / prolong_add */
 enum { SEMMG_F64 = 0, SEMMG_F32 = 1 };
 
@@ -111,6 +119,7 @@ typedef struct {
   int solver;      /* SEMMG_SOLVER_MG (Algorithm 4, default) or SEMMG_SOLVER_KMG (Algorithm 5) */
   int nu_vary;     /* 0 (default): nu_pre / nu_post steps on every level; 1: nu_pre 2^(L-l) and
                       nu_post 2^(L-l) steps on level l (Sec. 4.1, "kvMG" with SEMMG_SOLVER_KMG) */
+  int smoother;    /* SEMMG_SMOOTHER_STAR (default), SEMMG_SMOOTHER_ELEMENT or SEMMG_SMOOTHER_ELEMENT_MULT */
 } semmg_opts;
 
 typedef struct {
@@ -152,6 +161,14 @@ int semmg_nodal_size(const semmg_ctx* ctx, int level, int64_t* n);
 int semmg_pack(semmg_ctx* ctx, int level, const double* u_nodal, double* u_hat, void* stream);
 int semmg_unpack(semmg_ctx* ctx, int level, const double* u_hat, double* u_nodal, void* stream);
 
+/* u_hat = E g: the values of the nodal array g_nodal at the nodes on Dirichlet
+ * faces copied into their (boundary) skeleton slots, zero in every other slot.
+ * A condensed vector whose boundary slots hold Dirichlet data is read by
+ * semmg_apply_condensed, semmg_residual and semmg_recover as the prescribed
+ * boundary values (the lifting of inhomogeneous Dirichlet data, used by the
+ * paper's test problem of Sec. 5.2); their outputs stay zero in those slots. */
+int semmg_pack_dirichlet(semmg_ctx* ctx, int level, const double* g_nodal, double* u_hat, void* stream);
+
 /* y_hat = Hhat u_hat, Hhat = H_BB - H_BI H_II^{-1} H_IB the condensed operator
  * (Sec. 2.2) applied matrix-free in O(p^3) per element, FP64.  y_hat must not
  * alias u_hat. */
@@ -162,9 +179,14 @@ int semmg_residual(semmg_ctx* ctx, int level, const double* f_hat, const double*
                    double* r_hat, void* stream);
 
 /* du_hat = Smoother(r_hat): Algorithm 2 around Algorithm 1 on the stars of all
- * (n1+1)(n2+1)(n3+1) vertices of the level (Sec. 3.2), level >= 1.  dtype
- * SEMMG_F64 or SEMMG_F32 gives the element type of both vectors and the
- * arithmetic.  Overwrites du_hat (zero on the Dirichlet boundary). */
+ * (n1+1)(n2+1)(n3+1) vertices of the level (Sec. 3.2), level >= 1; with
+ * opts.smoother = SEMMG_SMOOTHER_ELEMENT(_MULT) the element-centred blocks of
+ * Sec. 3.4 instead: per element the 3x3x3-element block, condensed to the six
+ * planes through the element's faces (n_E = 3p - 1 points a side) and inverted
+ * by the block's fast diagonalisation restricted to those planes (73 n_E^3
+ * operations), outputs weighted as the option says.  dtype SEMMG_F64 or SEMMG_F32
+ * gives the element type of both vectors and the arithmetic.  Overwrites du_hat
+ * (zero on the Dirichlet boundary). */
 int semmg_smooth(semmg_ctx* ctx, int level, int dtype, const void* r_hat, void* du_hat, void* stream);
 
 /* coarse = J^T fine: restriction from level `level` (>= 1) to level-1, the exact
@@ -212,6 +234,17 @@ int semmg_recover(semmg_ctx* ctx, const double* f_nodal, const double* u_hat, do
  * last iterate), SEMMG_ERR_NONFINITE on a NaN/Inf residual norm. */
 int semmg_solve(semmg_ctx* ctx, const double* f_nodal, double* u_nodal, double rtol,
                 semmg_info* info, void* stream);
+
+/* semmg_solve with inhomogeneous Dirichlet data (Sec. 5.2: u = g on the
+ * Dirichlet faces).  g_nodal is a device nodal array of the finest level read
+ * at the nodes on Dirichlet faces only (its other entries are ignored; it may
+ * alias u_nodal).  Lifting: the iteration starts from u_hat = E g (see
+ * semmg_pack_dirichlet), so r_0 = f_hat - Hhat E g carries the boundary data;
+ * the V-cycle corrections vanish on the boundary slots, and the recovery reads
+ * them, so u_nodal = g on the Dirichlet faces.  Same options, info and return
+ * codes as semmg_solve; with g = 0 the result equals semmg_solve's. */
+int semmg_solve_dirichlet(semmg_ctx* ctx, const double* f_nodal, const double* g_nodal, double* u_nodal,
+                          double rtol, semmg_info* info, void* stream);
 
 /* semmg_solve with HOST nodal arrays: copies f to the device, solves, copies u
  * back, and synchronises `stream` before returning. */
@@ -289,6 +322,8 @@ int semmg_set_launch(semmg_ctx* ctx, int level, int kernel, int dtype, int smem_
  *   - The first call on a device looks the array's address up (once per
  *     device, with that device current); make that first call before any
  *     stream capture.
+ *   - Vertex-star smoother only: a context set up with an element-centred
+ *     smoother returns SEMMG_ERR_UNSUPPORTED.
  *   - A level whose star output buffer (nstar * 3 * n_S^2 elements) plus one
  *     block's work arrays exceeds the array returns SEMMG_ERR_UNSUPPORTED,
  *     with the sizes in semmg_last_error(ctx); larger work arrays only lower

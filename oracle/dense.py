@@ -536,21 +536,44 @@ def eblock_count_1d(mesh, d):
     return sum((eblock_offsets(mesh, g, c, d) > 0).astype(int) for c in range(mesh.n[d]))
 
 
-def eblock_weights(mesh, B, pos):
-    """Inverse multiplicity (Sec. 2.3: each point weighted with the inverse of the number of subdomains it
-    lies in) at condensed positions pos; block membership is a tensor product, so the count is the product
-    of the per-axis counts."""
+def eblock_weight_1d(mesh, d, c, j, kind):
+    """1D factor of the weight W_c of block c at line offsets j (1 .. 3p-1) along axis d.
+
+    kind "element": one on the element's own nodes and zero on the other elements' (the element-centred
+    counterpart of the star weights, which are one on their vertex and zero on every other vertex,
+    Sec. 3.2), so a node on one of its faces, shared with the neighbour's block, takes one half (one where
+    no neighbour block exists beyond a domain face).
+    kind "multiplicity": the inverse number of blocks holding the node (Sec. 2.3)."""
+    p = mesh.p
+    j = np.asarray(j)
+    if kind == "multiplicity":
+        g = (c - 1) * p + j
+        if mesh.periodic(d):
+            g = np.mod(g, mesh.n[d] * p)
+        g = np.clip(g, 0, mesh.N[d] - 1)
+        return 1.0 / np.maximum(eblock_count_1d(mesh, d)[g], 1)
+    if kind != "element":
+        raise ValueError("kind: 'element' or 'multiplicity'")
+    lo_shared = c > 0 or mesh.periodic(d)
+    hi_shared = c < mesh.n[d] - 1 or mesh.periodic(d)
+    w = np.where((j > p) & (j < 2 * p), 1.0, 0.0)
+    w = np.where(j == p, 0.5 if lo_shared else 1.0, w)
+    return np.where(j == 2 * p, 0.5 if hi_shared else 1.0, w)
+
+
+def eblock_weights(mesh, B, pos, c, kind="element"):
+    """W_c at the condensed positions pos of block c: the product of the 1D factors."""
     g = (B[pos] % mesh.N[0], (B[pos] // mesh.N[0]) % mesh.N[1], B[pos] // (mesh.N[0] * mesh.N[1]))
-    cnt = np.ones(len(pos))
+    W = np.ones(len(pos))
     for d in range(3):
-        cnt *= eblock_count_1d(mesh, d)[g[d]]
-    return 1.0 / cnt
+        W *= eblock_weight_1d(mesh, d, c[d], eblock_offsets(mesh, g[d], c[d], d), kind)
+    return W
 
 
-def smoother_eblock_dense(mesh, cond, r):
+def smoother_eblock_dense(mesh, cond, r, kind="element"):
     """Element-centred Schwarz smoother (Sec. 3.4 as a drop-in for the stars in eq. smoother_definition):
-    Delta u = sum_c R_c^T W_c Hhat_c^{-1} R_c r over all elements c, Hhat_c = R_c Hhat R_c^T, W_c the
-    inverse multiplicity; each block inverse applied densely."""
+    Delta u = sum_c R_c^T W_c Hhat_c^{-1} R_c r over all elements c, Hhat_c = R_c Hhat R_c^T, W_c of the
+    given kind (eblock_weight_1d); each block inverse applied densely."""
     eblock_check(mesh)
     du = np.zeros_like(r)
     for c in eblock_centres(mesh):
@@ -558,7 +581,7 @@ def smoother_eblock_dense(mesh, cond, r):
         if pos.size == 0:
             continue
         dui = np.linalg.solve(cond.Hhat[np.ix_(pos, pos)], r[pos])
-        du[pos] += eblock_weights(mesh, cond.B, pos) * dui
+        du[pos] += eblock_weights(mesh, cond.B, pos, c, kind) * dui
     return du
 
 

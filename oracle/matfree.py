@@ -375,18 +375,21 @@ def smooth(mesh, r, tables=None, chunk=128):
 
 
 class EBlockTables:
-    """Per element and axis the block line eigen-tables (Sec. 3.4) and the 1D inverse-multiplicity factors."""
+    """Per element and axis the block line eigen-tables (Sec. 3.4) and the 1D weight factors of the blocks
+    (dense.eblock_weight_1d of the given kind, at line offsets 1 .. 3p-1)."""
 
-    def __init__(self, mesh):
+    def __init__(self, mesh, kind="element"):
         dense.eblock_check(mesh)
         self.mesh = mesh
-        self.S, self.Lam, self.act = [], [], []
+        self.kind = kind
+        self.S, self.Lam, self.act, self.wl = [], [], [], []
+        j = np.arange(1, 3 * mesh.p)
         for d in range(3):
             tabs = [dense.eblock_line_table(mesh, d, c) for c in range(mesh.n[d])]
             self.S.append(np.array([t[0] for t in tabs]))
             self.Lam.append(np.array([t[1] for t in tabs]))
             self.act.append(np.array([t[2] for t in tabs]))
-        self.winv = [1.0 / np.maximum(dense.eblock_count_1d(mesh, d), 1) for d in range(3)]
+            self.wl.append(np.array([dense.eblock_weight_1d(mesh, d, c, j, kind) for c in range(mesh.n[d])]))
 
 
 def smooth_eblock(mesh, r, tables=None):
@@ -395,7 +398,7 @@ def smooth_eblock(mesh, r, tables=None):
     Each block inverse by the embedding of Sec. 3.1 and the block's fast diagonalisation: the condensed
     residual, zero at element-interior nodes, is the right-hand side of the full 3^3-element block
     problem; its solution (S3 x S2 x S1) D^{-1} (S3 x S2 x S1)^T on the block, read at the block's skeleton
-    nodes, is Hhat_c^{-1} R_c r.  W_c = inverse multiplicity.
+    nodes, is Hhat_c^{-1} R_c r.  W_c: the tables' weights (dense.eblock_weight_1d).
     """
     p = mesh.p
     tables = tables or EBlockTables(mesh)
@@ -423,8 +426,7 @@ def smooth_eblock(mesh, r, tables=None):
             + tables.Lam[0][c[0]][None, None, :]
         U = np.einsum("cba,ic,jb,ka->ijk", Ft / D, S3, S2, S1, optimize=True)
         skel = on_plane[:, None, None] | on_plane[None, :, None] | on_plane[None, None, :]
-        W = tables.winv[2][gi[2]][:, None, None] * tables.winv[1][gi[1]][None, :, None] \
-            * tables.winv[0][gi[0]][None, None, :]
+        W = tables.wl[2][c[2]][:, None, None] * tables.wl[1][c[1]][None, :, None] * tables.wl[0][c[0]][None, None, :]
         np.add.at(du, idx, np.where(inside & skel, W * U, 0.0))
     return np.where(condensed_mask(mesh), du, 0.0)
 
@@ -537,10 +539,12 @@ class MG:
     def __init__(self, mesh, p0=1, nu_pre=1, nu_post=1, nu_vary=False, smoother="star"):
         self.degs = dense.level_degrees(mesh.p, p0)
         self.meshes = [mesh.with_degree(q) for q in self.degs]
-        if smoother not in ("star", "element"):
-            raise ValueError("smoother: 'star' (Algorithm 2) or 'element' (element-centred blocks, Sec. 3.4)")
+        kinds = {"element": "element", "element_mult": "multiplicity"}
+        if smoother != "star" and smoother not in kinds:
+            raise ValueError("smoother: 'star' (Algorithm 2), 'element' or 'element_mult' (element-centred "
+                             "blocks of Sec. 3.4 with element or inverse-multiplicity weights)")
         self.smoother = smoother
-        self.tables = [(StarTables(m) if smoother == "star" else EBlockTables(m)) if l > 0 else None
+        self.tables = [(StarTables(m) if smoother == "star" else EBlockTables(m, kinds[smoother])) if l > 0 else None
                        for l, m in enumerate(self.meshes)]
         self.coarse = CoarseSolver(self.meshes[0])
         self.nu_pre, self.nu_post = nu_pre, nu_post
@@ -558,7 +562,7 @@ class MG:
         return apply_condensed(self.meshes[l], u)
 
     def smooth(self, l, r):
-        if self.smoother == "element":
+        if self.smoother != "star":
             return smooth_eblock(self.meshes[l], r, self.tables[l])
         return smooth(self.meshes[l], r, self.tables[l])
 

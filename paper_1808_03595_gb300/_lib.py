@@ -25,6 +25,7 @@ ERRORS = {
 SEMMG_ERR_NOT_CONVERGED = -4
 SEMMG_FP64, SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC = 0, 1, 2, 3
 SEMMG_SOLVER_MG, SEMMG_SOLVER_KMG = 0, 1
+SEMMG_SMOOTHER_STAR, SEMMG_SMOOTHER_ELEMENT, SEMMG_SMOOTHER_ELEMENT_MULT = 0, 1, 2
 SEMMG_BC_DIRICHLET, SEMMG_BC_NEUMANN, SEMMG_BC_PERIODIC = 0, 1, 2
 SEMMG_F64, SEMMG_F32 = 0, 1
 SEMMG_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
@@ -36,7 +37,7 @@ class semmg_mesh(ctypes.Structure):
 
 class semmg_opts(ctypes.Structure):
     _fields_ = [("p0", c_int), ("nu_pre", c_int), ("nu_post", c_int), ("precision", c_int), ("max_iter", c_int),
-                ("solver", c_int), ("nu_vary", c_int)]
+                ("solver", c_int), ("nu_vary", c_int), ("smoother", c_int)]
 
 
 class semmg_kstat(ctypes.Structure):
@@ -63,6 +64,7 @@ SIGNATURES = {
     "semmg_nodal_size": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64)]),
     "semmg_pack": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "semmg_unpack": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "semmg_pack_dirichlet": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "semmg_apply_condensed": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "semmg_residual": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "semmg_smooth": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
@@ -73,6 +75,8 @@ SIGNATURES = {
     "semmg_condense_rhs": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "semmg_recover": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "semmg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(semmg_info), c_void_p]),
+    "semmg_solve_dirichlet": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(semmg_info),
+                                      c_void_p]),
     "semmg_solve_host": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(semmg_info), c_void_p]),
     "semmg_smooth_noalloc": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "semmg_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_void_p),

@@ -36,6 +36,7 @@ struct DevLevel {
   void* Rw = nullptr;
   LaunchCfg schur64, schur32, star64, star32;
   LaunchCfg startc;  // tensor-core star smoother (SEMMG_MIXED_TC), when the level allows it
+  LaunchCfg eb64, eb32;  // element-centred block smoother (SEMMG_SMOOTHER_ELEMENT)
 };
 
 // n_S rounded up to 16, the operand size of the tensor-core star tables
@@ -254,6 +255,22 @@ Tabs<T> upload_tabs(semmg_ctx* c, const HostLevel& H, const std::vector<double>*
   }
   t.Relem = H.Relem.empty() ? nullptr : upload<T>(c, H.Relem, ok);
   t.w1d = upload<T>(c, H.w1d, ok);
+  for (int d = 0; d < 3; ++d) {
+    t.ebS[d] = H.ebS[d].empty() ? nullptr : upload<T>(c, H.ebS[d], ok);
+    t.ebST[d] = H.ebST[d].empty() ? nullptr : upload<T>(c, H.ebST[d], ok);
+    t.ebLam[d] = H.ebLam[d].empty() ? nullptr : upload<T>(c, H.ebLam[d], ok);
+    t.ebW[d] = H.ebW[d].empty() ? nullptr : upload<T>(c, H.ebW[d], ok);
+    t.ebCls[d] = nullptr;
+    t.ebNcls[d] = (int)H.ebRep[d].size();
+    if (!H.ebCls[d].empty()) {
+      int* dc = (int*)dalloc(c, H.ebCls[d].size() * sizeof(int));
+      if (!dc || cudaMemcpy(dc, H.ebCls[d].data(), H.ebCls[d].size() * sizeof(int), cudaMemcpyHostToDevice) !=
+                     cudaSuccess)
+        *ok = false;
+      t.ebCls[d] = dc;
+    }
+  }
+  t.ebR = H.ebR.empty() ? nullptr : upload<T>(c, H.ebR, ok);
   t.J = H.J.empty() ? nullptr : upload<T>(c, H.J, ok);
   t.pc = H.pc;
   return t;
@@ -302,6 +319,11 @@ int ev_get(semmg_ctx* c);
 
 // Algorithmic work per launch (see semmg.h, timing).
 double star_flops(const Geo& G) { return 37.0 * G.nS * (double)G.nS * G.nS * (double)G.nstar; }
+// 73 n_E^3 per element-centred block (Sec. 3.4), n_E = 3p - 1
+double eblock_flops(const Geo& G) {
+  const double nE = 3.0 * G.p - 1.0;
+  return 73.0 * nE * nE * nE * (double)G.nelem;
+}
 double schur_flops(const Geo& G) { return 73.0 * G.m * (double)G.m * G.m * (double)G.nelem; }
 double fdm_flops(const Geo& G) {
   const double p = G.p;
@@ -411,6 +433,20 @@ template <typename T>
 void op_smooth(semmg_ctx* c, int l, const T* r, T* du, int accumulate, cudaStream_t st) {
   const Geo& G = c->geo[l];
   const double vec = (double)G.size * sizeof(T);
+  if (c->opts.smoother != SEMMG_SMOOTHER_STAR) {
+    const double nE = 3.0 * G.p - 1.0;
+    const double obe = (double)G.nelem * 6 * nE * nE * sizeof(T);
+    {
+      Tic t(c, SEMMG_K_STAR, st);
+      const LaunchCfg& cfg = std::is_same<T, double>::value ? c->dl[l].eb64 : c->dl[l].eb32;
+      launch_eblock<T>(G, tabs<T>(c, l), r, (T*)c->Obs, (T*)c->wss, cfg, st);
+      t.toc(eblock_flops(G), vec + obe);
+    }
+    Tic t(c, SEMMG_K_STAR_GATHER, st);
+    launch_eblock_gather<T>(G, (const T*)c->Obs, du, accumulate, st);
+    t.toc(0.0, obe + vec * (accumulate ? 2 : 1));
+    return;
+  }
   const double ob = (double)G.nstar * 3 * G.nS * G.nS * sizeof(T);
   {
     Tic t(c, SEMMG_K_STAR, st);
@@ -556,15 +592,26 @@ void recover_impl(semmg_ctx* c, const double* f, const double* uh, double* u, bo
   t.toc(G.m > 0 ? fdm_flops(G) : 0.0, 8.0 * (2 * nn + G.size), 2);
 }
 
-// Start of the outer iteration from u_hat = 0: r = F_hat, ||r||^2 into dnorm,
-// and for Algorithm 5 s = r, p = 0, delta = 1.
-void iter_start(semmg_ctx* c, cudaStream_t st) {
+// Start of the outer iteration from u_hat = 0 (g = NULL): r = F_hat; or, with
+// Dirichlet data g, from u_hat = E g: r = F_hat - Hhat E g (lifting).  ||r||^2
+// into dnorm, and for Algorithm 5 s = r, p = 0, delta = 1.
+void iter_start(semmg_ctx* c, cudaStream_t st, const double* g = nullptr) {
   const int L = c->L();
   const int64_t n = c->geo[L].size;
+  if (g) {
+    {
+      Tic t(c, SEMMG_K_VECTOR, st);
+      launch_pack_dirichlet(c->geo[L], g, c->Uh, st);
+      t.toc(0.0, 16.0 * n);
+    }
+    op_residual<double>(c, L, c->Fh, c->Uh, c->Rh, 0, st);
+  }
   Tic t(c, SEMMG_K_VECTOR, st);
-  cudaMemsetAsync(c->Uh, 0, n * sizeof(double), st);
-  launch_copy<double, double>(c->Rh, c->Fh, n, st);
-  launch_norm2<double>(c->Fh, n, c->part, c->npart, c->dnorm, st);
+  if (!g) {
+    cudaMemsetAsync(c->Uh, 0, n * sizeof(double), st);
+    launch_copy<double, double>(c->Rh, c->Fh, n, st);
+  }
+  launch_norm2<double>(c->Rh, n, c->part, c->npart, c->dnorm, st);
   if (c->opts.solver == SEMMG_SOLVER_KMG) {
     launch_copy<double, double>(c->kS, c->Rh, n, st);
     cudaMemsetAsync(c->kP, 0, n * sizeof(double), st);
@@ -618,7 +665,8 @@ int dnorm_sync(semmg_ctx* c, cudaStream_t st, double* out) {
 
 int set_limits(semmg_ctx* c) {
   if (g_limits_done) return SEMMG_OK;
-  if (set_elem_smem_limits() | set_star_smem_limits() | set_transfer_smem_limits() | set_star_tc_smem_limits())
+  if (set_elem_smem_limits() | set_star_smem_limits() | set_transfer_smem_limits() | set_star_tc_smem_limits() |
+      set_eblock_smem_limits())
     return fail(c, SEMMG_ERR_CUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
   g_limits_done = 1;
   return SEMMG_OK;
@@ -637,6 +685,8 @@ int smooth_with_scratch(semmg_ctx* c, int level, int dtype, const void* r, void*
                         size_t scratch_bytes, cudaStream_t st) {
   if (!valid_level(c, level) || level < 1 || !r || !du || r == du || !scratch) return SEMMG_ERR_INVALID_ARG;
   if (dtype != SEMMG_F64 && dtype != SEMMG_F32) return SEMMG_ERR_INVALID_ARG;
+  if (c->opts.smoother != SEMMG_SMOOTHER_STAR)
+    return fail(c, SEMMG_ERR_UNSUPPORTED, "smooth_noalloc: vertex-star smoother only");
   const Geo& G = c->geo[level];
   const size_t es = dtype == SEMMG_F64 ? sizeof(double) : sizeof(float);
   LaunchCfg cfg = dtype == SEMMG_F64 ? c->dl[level].star64 : c->dl[level].star32;
@@ -680,6 +730,7 @@ void semmg_default_opts(semmg_opts* o) {
   o->max_iter = 50;
   o->solver = SEMMG_SOLVER_MG;
   o->nu_vary = 0;
+  o->smoother = SEMMG_SMOOTHER_STAR;
 }
 
 int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* opts, void* stream,
@@ -699,6 +750,9 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     return SEMMG_ERR_INVALID_ARG;
   if (o.solver != SEMMG_SOLVER_MG && o.solver != SEMMG_SOLVER_KMG) return SEMMG_ERR_INVALID_ARG;
   if (o.nu_vary != 0 && o.nu_vary != 1) return SEMMG_ERR_INVALID_ARG;
+  if (o.smoother != SEMMG_SMOOTHER_STAR && o.smoother != SEMMG_SMOOTHER_ELEMENT &&
+      o.smoother != SEMMG_SMOOTHER_ELEMENT_MULT)
+    return SEMMG_ERR_INVALID_ARG;
   bool any_dirichlet = false;
   for (int f = 0; f < 6; ++f) {
     if (mesh->bc[f] != SEMMG_BC_DIRICHLET && mesh->bc[f] != SEMMG_BC_NEUMANN && mesh->bc[f] != SEMMG_BC_PERIODIC)
@@ -709,6 +763,8 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     const bool plo = mesh->bc[2 * d] == SEMMG_BC_PERIODIC, phi = mesh->bc[2 * d + 1] == SEMMG_BC_PERIODIC;
     if (plo != phi) return SEMMG_ERR_INVALID_ARG;         // periodic pairs the two faces of an axis
     if (plo && mesh->n[d] < 2) return SEMMG_ERR_UNSUPPORTED;  // a star would meet itself
+    // an element-centred block spans three elements along each axis, which must differ
+    if (plo && o.smoother != SEMMG_SMOOTHER_STAR && mesh->n[d] < 3) return SEMMG_ERR_UNSUPPORTED;
   }
   if (!any_dirichlet && !(lambda > 0.0)) return SEMMG_ERR_UNSUPPORTED;  // singular (pure Neumann, lambda = 0)
   for (int d = 0; d < 3; ++d) {
@@ -743,6 +799,7 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     c->hl[l].p = degs[l];
     c->hl[l].lam = lambda;
     build_level_tables(c->hl[l], c->h, mesh->bc);
+    if (l > 0 && o.smoother != SEMMG_SMOOTHER_STAR) build_eblock_tables(c->hl[l], c->h, mesh->bc, o.smoother);
     if (l > 0) {
       lagrange_interp(c->hl[l - 1].x, c->hl[l].x, c->hl[l].J);
       c->hl[l].pc = degs[l - 1];
@@ -774,7 +831,16 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     if (l >= 1) {
       D.star64 = plan_star<double>(G, c->nsm);
       D.star32 = plan_star<float>(G, c->nsm);
-      if (o.precision == SEMMG_MIXED_TC) {
+      if (o.smoother != SEMMG_SMOOTHER_STAR) {
+        D.eb64 = plan_eblock<double>(G, c->nsm);
+        D.eb32 = plan_eblock<float>(G, c->nsm);
+        if (!D.eb64.ok || !D.eb32.ok) return SEMMG_ERR_UNSUPPORTED;
+        wsb = std::max(wsb, D.eb64.ws_elems() * sizeof(double));
+        wsb = std::max(wsb, D.eb32.ws_elems() * sizeof(float));
+        const int64_t nE = 3 * (int64_t)G.p - 1;
+        obs = std::max(obs, (size_t)(G.nelem * 6 * nE * nE));
+      }
+      if (o.precision == SEMMG_MIXED_TC && o.smoother == SEMMG_SMOOTHER_STAR) {
         D.startc = plan_star_tc(G, c->nsm);
         if (D.startc.ok) {
           upload_tc_tables(c.get(), c->hl[l], D.tf, &ok);
@@ -909,6 +975,12 @@ int semmg_pack(semmg_ctx* c, int level, const double* u_nodal, double* u_hat, vo
   return check_cuda(c, "pack");
 }
 
+int semmg_pack_dirichlet(semmg_ctx* c, int level, const double* g_nodal, double* u_hat, void* stream) {
+  if (!valid_level(c, level) || !g_nodal || !u_hat) return SEMMG_ERR_INVALID_ARG;
+  launch_pack_dirichlet(c->geo[level], g_nodal, u_hat, (cudaStream_t)stream);
+  return check_cuda(c, "pack_dirichlet");
+}
+
 int semmg_unpack(semmg_ctx* c, int level, const double* u_hat, double* u_nodal, void* stream) {
   if (!valid_level(c, level) || !u_nodal || !u_hat) return SEMMG_ERR_INVALID_ARG;
   launch_unpack(c->geo[level], u_hat, u_nodal, (cudaStream_t)stream);
@@ -987,15 +1059,19 @@ int semmg_recover(semmg_ctx* c, const double* f, const double* uh, double* u, vo
   return check_cuda(c, "recover");
 }
 
-int semmg_solve(semmg_ctx* c, const double* f, double* u, double rtol, semmg_info* info, void* stream) {
-  if (!c || !f || !u || !(rtol > 0.0)) return SEMMG_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// condense, Algorithm 4 or 5 from u_hat = 0 (or E g), recover
+int solve_impl(semmg_ctx* c, const double* f, const double* g, double* u, double rtol, semmg_info* info,
+               cudaStream_t st) {
   condense_impl(c, f, c->Fh, true, st);
   int rc = check_cuda(c, "condense_rhs");
   if (rc) return rc;
-  iter_start(c, st);
+  iter_start(c, st, g);
   double r0 = 0.0, rn = 0.0;
-  rc = dnorm_sync(c, st, &r0);  // r_0 = Fhat - Hhat 0
+  rc = dnorm_sync(c, st, &r0);  // r_0 = Fhat - Hhat u_hat_0
   if (rc) return rc;
   int it = 0;
   int status = SEMMG_OK;
@@ -1021,6 +1097,21 @@ int semmg_solve(semmg_ctx* c, const double* f, double* u, double rtol, semmg_inf
   }
   if (status != SEMMG_OK) fail(c, status, "solve: %s after %d cycles", semmg_strerror(status), it);
   return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int semmg_solve(semmg_ctx* c, const double* f, double* u, double rtol, semmg_info* info, void* stream) {
+  if (!c || !f || !u || !(rtol > 0.0)) return SEMMG_ERR_INVALID_ARG;
+  return solve_impl(c, f, nullptr, u, rtol, info, (cudaStream_t)stream);
+}
+
+int semmg_solve_dirichlet(semmg_ctx* c, const double* f, const double* g, double* u, double rtol,
+                          semmg_info* info, void* stream) {
+  if (!c || !f || !g || !u || !(rtol > 0.0)) return SEMMG_ERR_INVALID_ARG;
+  return solve_impl(c, f, g, u, rtol, info, (cudaStream_t)stream);
 }
 
 int semmg_solve_host(semmg_ctx* c, const double* f_host, double* u_host, double rtol, semmg_info* info,

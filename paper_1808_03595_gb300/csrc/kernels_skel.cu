@@ -182,6 +182,20 @@ __global__ void k_pack(Geo G, const double* __restrict__ nodal, double* __restri
   }
 }
 
+// E g: the nodal values on Dirichlet faces in their skeleton slots, 0 elsewhere.
+__global__ void k_pack_dirichlet(Geo G, const double* __restrict__ nodal, double* __restrict__ hat) {
+  const int64_t N1 = (int64_t)G.n1 * G.p + 1, N2 = (int64_t)G.n2 * G.p + 1;
+  const int top[3] = {G.n1 * G.p, G.n2 * G.p, G.n3 * G.p};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < G.size; s += (int64_t)gridDim.x * blockDim.x) {
+    int g[3];
+    bool bd;
+    skel_decode(G, s, g, &bd);
+    bool on = false;
+    for (int d = 0; d < 3; ++d) on |= (g[d] == 0 && G.dir[2 * d]) || (g[d] == top[d] && G.dir[2 * d + 1]);
+    hat[s] = on ? nodal[((int64_t)g[2] * N2 + g[1]) * N1 + g[0]] : 0.0;
+  }
+}
+
 // Every skeleton node of the nodal array; a periodic image takes the value of
 // the unknown it repeats (the slot skel_index maps it to).
 __global__ void k_unpack(Geo G, const double* __restrict__ hat, double* __restrict__ nodal) {
@@ -301,6 +315,10 @@ void launch_assemble_rhs(const Geo& G, const Tabs<double>& t, const double* f, c
 
 void launch_pack(const Geo& G, const double* nodal, double* hat, cudaStream_t st) {
   k_pack<<<grid_for(G.size), kThreads, 0, st>>>(G, nodal, hat);
+}
+
+void launch_pack_dirichlet(const Geo& G, const double* nodal, double* hat, cudaStream_t st) {
+  k_pack_dirichlet<<<grid_for(G.size), kThreads, 0, st>>>(G, nodal, hat);
 }
 
 void launch_unpack(const Geo& G, const double* hat, double* nodal, cudaStream_t st) {

@@ -256,6 +256,16 @@ struct Tabs {
   // K-major TF32 operands (8 x 4 core matrices), n_S rounded up to 16 and zero-padded
   const T* tcT[3];
   const T* tcN[3];
+  // element-centred blocks (Sec. 3.4), when that smoother is selected (else null): per axis
+  // n_d block lines of nE x nE eigenvectors S[j][k], nE eigenvalues and nE weight factors
+  // (nE = 3p - 1)
+  const T* ebS[3];
+  const T* ebST[3];      // transposes: ST[k][j] = S[j][k]
+  const T* ebLam[3];
+  const T* ebW[3];
+  const int* ebCls[3];   // line class of every block line
+  int ebNcls[3];
+  const T* ebR;          // per class triple: nE^3 values 1/(lam + Lam1 + Lam2 + Lam3) [k3][k2][k1], or null
 };
 
 // Coarse fast-diagonalisation tables (level 0, FP64): K_d = n_d p0 - 1
@@ -287,6 +297,7 @@ struct LaunchCfg {
   // register budget of the kernel build: 0 = at most 64 registers per thread
   // (1024 resident threads per SM), 1 = at most 128 (512 resident threads)
   int wide = 0;
+  int depth = 0;                 // element-block kernel: k3-planes of the eigenspace slab
   size_t ws_elems() const { return (size_t)ws.gstride * (size_t)grid; }
 };
 
@@ -376,6 +387,16 @@ void launch_assemble_rhs(const Geo& G, const Tabs<double>& t, const double* f_no
                          double* Fhat, cudaStream_t st);
 void launch_pack(const Geo& G, const double* nodal, double* hat, cudaStream_t st);
 void launch_unpack(const Geo& G, const double* hat, double* nodal, cudaStream_t st);
+void launch_pack_dirichlet(const Geo& G, const double* nodal, double* hat, cudaStream_t st);
+
+// element-centred block smoother (kernels_eblock.cu)
+template <typename T>
+LaunchCfg plan_eblock(const Geo& G, int nsm);
+template <typename T>
+void launch_eblock(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws, const LaunchCfg& c, cudaStream_t st);
+template <typename T>
+void launch_eblock_gather(const Geo& G, const T* Ob, T* du, int accumulate, cudaStream_t st);
+int set_eblock_smem_limits();
 template <typename T> LaunchCfg plan_star(const Geo& G, int nsm, size_t cap = 0, int block = 0, int wide = -1);
 template <typename T> void launch_star(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws,
                                        const LaunchCfg& c, int* counter, cudaStream_t st);

@@ -434,6 +434,140 @@ void build_level_tables(HostLevel& L, const std::vector<double>* h, const int* b
   for (int k = 0; k <= m; ++k) L.w1d[k] = weight_poly(0.5 * (1.0 + L.x[k]));
 }
 
+// Element-centred blocks (Sec. 3.4): the block of element c spans elements c-1, c, c+1 along
+// each axis; its line holds the nE = 3p - 1 nodes strictly inside, j = 0..nE-1 at global
+// index (c-1) p + 1 + j.  Assembled 1D matrices of the three elements, identity / 1 padding
+// where a node is not an unknown of the domain (ghost element, Dirichlet face, Sec. 3.3).
+// Lines with equal inputs (uniform meshes) share one eigen-decomposition.
+void build_eblock_tables(HostLevel& L, const std::vector<double>* h, const int* bc, int weights) {
+  const int p = L.p, P1 = p + 1, nE = 3 * p - 1;
+  for (int d = 0; d < 3; ++d) {
+    const int nd = (int)h[d].size();
+    const int Nd = nd * p + 1;
+    const bool per = bc[2 * d] == SEMMG_BC_PERIODIC;
+    const int glo = bc[2 * d] == SEMMG_BC_DIRICHLET ? 1 : 0;
+    const int ghi = bc[2 * d + 1] == SEMMG_BC_DIRICHLET ? Nd - 2 : Nd - 1;
+    L.ebS[d].assign((size_t)nd * nE * nE, 0.0);
+    L.ebLam[d].assign((size_t)nd * nE, 1.0);
+    std::vector<std::vector<double>> seenL, seenM;
+    std::vector<int>& seenC = L.ebRep[d];
+    seenC.clear();
+    L.ebCls[d].assign(nd, 0);
+    for (int c = 0; c < nd; ++c) {
+      std::vector<double> Mb(nE, 0.0), Lb((size_t)nE * nE, 0.0);
+      for (int a = c - 1; a <= c + 1; ++a) {
+        const int aw = per ? (a + nd) % nd : a;
+        if (aw < 0 || aw >= nd) continue;
+        const double ha = h[d][aw];
+        for (int i = 0; i <= p; ++i) {
+          const int ji = (a - c + 1) * p + i - 1;  // block line index of local node i of element a
+          if (ji < 0 || ji >= nE) continue;
+          Mb[ji] += 0.5 * ha * L.w[i];
+          for (int k = 0; k <= p; ++k) {
+            const int jk = (a - c + 1) * p + k - 1;
+            if (jk < 0 || jk >= nE) continue;
+            Lb[(size_t)ji * nE + jk] += 2.0 / ha * L.Ls[i * P1 + k];
+          }
+        }
+      }
+      std::vector<int> act;
+      for (int j = 0; j < nE; ++j) {
+        const int g = (c - 1) * p + 1 + j;
+        if (per || (g >= glo && g <= ghi)) act.push_back(j);
+      }
+      // inactive nodes carry no coupling: zero their rows so equal lines compare equal
+      std::vector<char> on(nE, 0);
+      for (int j : act) on[j] = 1;
+      for (int i = 0; i < nE; ++i)
+        if (!on[i]) {
+          Mb[i] = 0.0;
+          for (int k = 0; k < nE; ++k) Lb[(size_t)i * nE + k] = Lb[(size_t)k * nE + i] = 0.0;
+        }
+      double* S = &L.ebS[d][(size_t)c * nE * nE];
+      double* lam = &L.ebLam[d][(size_t)c * nE];
+      int same = -1;
+      for (size_t r = 0; r < seenC.size() && same < 0; ++r)
+        if (seenL[r] == Lb && seenM[r] == Mb) {
+          same = seenC[r];
+          L.ebCls[d][c] = (int)r;
+        }
+      if (same >= 0) {
+        std::copy(&L.ebS[d][(size_t)same * nE * nE], &L.ebS[d][(size_t)(same + 1) * nE * nE], S);
+        std::copy(&L.ebLam[d][(size_t)same * nE], &L.ebLam[d][(size_t)(same + 1) * nE], lam);
+        continue;
+      }
+      L.ebCls[d][c] = (int)seenC.size();
+      seenL.push_back(Lb);
+      seenM.push_back(Mb);
+      seenC.push_back(c);
+      for (int i = 0; i < nE; ++i) S[(size_t)i * nE + i] = 1.0;  // identity padding
+      const int na = (int)act.size();
+      if (na == 0) continue;
+      std::vector<double> La((size_t)na * na), Ma(na), Sa, la;
+      for (int i = 0; i < na; ++i) {
+        Ma[i] = Mb[act[i]];
+        for (int j = 0; j < na; ++j) La[(size_t)i * na + j] = Lb[(size_t)act[i] * nE + act[j]];
+      }
+      gen_eig_diag_mass(na, La, Ma, Sa, la);
+      for (int i = 0; i < na; ++i) {
+        S[(size_t)act[i] * nE + act[i]] = 0.0;
+        lam[act[i]] = la[i];
+      }
+      for (int i = 0; i < na; ++i)
+        for (int k = 0; k < na; ++k) S[(size_t)act[i] * nE + act[k]] = Sa[(size_t)i * na + k];
+    }
+    // 1D weight factor of block line c at index j (global node (c-1) p + 1 + j):
+    // SEMMG_SMOOTHER_ELEMENT: 1 strictly inside element c, 1/2 on its two faces when the
+    // neighbour block beyond exists (else 1), 0 elsewhere;
+    // SEMMG_SMOOTHER_ELEMENT_MULT: 1 / (number of blocks c' with (c'-1) p < g < (c'+2) p)
+    L.ebW[d].assign((size_t)nd * nE, 0.0);
+    for (int c = 0; c < nd; ++c)
+      for (int j = 0; j < nE; ++j) {
+        double w = 0.0;
+        if (weights == SEMMG_SMOOTHER_ELEMENT) {
+          const int o = j + 1;  // offset from the block's low end, p and 2p on the element's faces
+          if (o > p && o < 2 * p) w = 1.0;
+          if (o == p) w = (c > 0 || per) ? 0.5 : 1.0;
+          if (o == 2 * p) w = (c < nd - 1 || per) ? 0.5 : 1.0;
+        } else {
+          int g = (c - 1) * p + 1 + j;
+          if (per) g = ((g % (nd * p)) + nd * p) % (nd * p);
+          int cnt = 0;
+          for (int c2 = 0; c2 < nd; ++c2) {
+            int o = g - (c2 - 1) * p;
+            if (per) o = ((o % (nd * p)) + nd * p) % (nd * p);
+            if (o >= 1 && o <= 3 * p - 1) ++cnt;
+          }
+          w = cnt > 0 ? 1.0 / cnt : 0.0;
+        }
+        L.ebW[d][(size_t)c * nE + j] = w;
+      }
+    L.ebST[d].resize(L.ebS[d].size());
+    for (int c = 0; c < nd; ++c)
+      for (int j = 0; j < nE; ++j)
+        for (int k = 0; k < nE; ++k)
+          L.ebST[d][((size_t)c * nE + k) * nE + j] = L.ebS[d][((size_t)c * nE + j) * nE + k];
+  }
+  // 1/(lam + Lam1[k1] + Lam2[k2] + Lam3[k3]) per class triple, index ((cl3 ncls2 + cl2) ncls1 + cl1)
+  const size_t n3 = (size_t)nE * nE * nE;
+  const size_t ncls = L.ebRep[0].size() * L.ebRep[1].size() * L.ebRep[2].size();
+  L.ebR.clear();
+  if (ncls * n3 <= kMaxRtabEntries) {
+    L.ebR.resize(ncls * n3);
+    size_t o = 0;
+    for (int r3 : L.ebRep[2])
+      for (int r2 : L.ebRep[1])
+        for (int r1 : L.ebRep[0]) {
+          const double* l1 = &L.ebLam[0][(size_t)r1 * nE];
+          const double* l2 = &L.ebLam[1][(size_t)r2 * nE];
+          const double* l3 = &L.ebLam[2][(size_t)r3 * nE];
+          for (int k3 = 0; k3 < nE; ++k3)
+            for (int k2 = 0; k2 < nE; ++k2)
+              for (int k1 = 0; k1 < nE; ++k1) L.ebR[o++] = 1.0 / (L.lam + l1[k1] + l2[k2] + l3[k3]);
+        }
+  }
+}
+
 void build_coarse_tables(int p0, const std::vector<double>* h, const int* bc, HostCoarse& C) {
   std::vector<double> x, w, Ls;
   gll_host(p0, x, w);

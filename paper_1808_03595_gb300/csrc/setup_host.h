@@ -25,6 +25,13 @@ struct HostLevel {
   std::vector<double> w1d;                         // smoother weights at |offset|
   std::vector<double> J;                           // interpolation from the next coarser level
   int pc = 0;
+  // element-centred blocks (Sec. 3.4), built on request: per axis n_d block lines of
+  // nE x nE eigenvectors (and their transposes), nE eigenvalues and nE weight factors
+  // (nE = 3p - 1); lines with equal tables share a class, and per class triple
+  // 1/(lam + Lam1 + Lam2 + Lam3) is tabulated when small enough
+  std::vector<double> ebS[3], ebST[3], ebLam[3], ebW[3];
+  std::vector<int> ebCls[3], ebRep[3];
+  std::vector<double> ebR;
 };
 
 struct HostCoarse {
@@ -46,5 +53,8 @@ double weight_poly(double t);
 // bc: faces -x1, +x1, -x2, +x2, -x3, +x3, SEMMG_BC_DIRICHLET or SEMMG_BC_NEUMANN
 void build_level_tables(HostLevel& L, const std::vector<double>* h, const int* bc);
 void build_coarse_tables(int p0, const std::vector<double>* h, const int* bc, HostCoarse& C);
+// element-centred block tables of a level whose GLL tables are built (needs 3 elements per periodic axis);
+// weights: SEMMG_SMOOTHER_ELEMENT or SEMMG_SMOOTHER_ELEMENT_MULT
+void build_eblock_tables(HostLevel& L, const std::vector<double>* h, const int* bc, int weights);
 
 }  // namespace semmg

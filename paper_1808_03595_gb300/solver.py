@@ -30,7 +30,7 @@ class Context:
     """A semmg context: mesh (per-axis element widths), degree p, lambda >= 0, options."""
 
     def __init__(self, h, p, lam, p0=2, nu_pre=1, nu_post=1, precision="fp64", max_iter=50, solver="mg",
-                 nu_vary=False, bc=None, stream=None):
+                 nu_vary=False, bc=None, stream=None, smoother="star"):
         self._lib = L.load()
         self._ctx = ctypes.c_void_p()
         self.h = [np.ascontiguousarray(np.asarray(hd, dtype=np.float64)) for hd in h]
@@ -58,6 +58,11 @@ class Context:
         opts.max_iter = max_iter
         opts.solver = {"mg": L.SEMMG_SOLVER_MG, "kmg": L.SEMMG_SOLVER_KMG}[solver]
         opts.nu_vary = 1 if nu_vary else 0
+        # "star": vertex stars (Algorithms 1 and 2); "element" / "element_mult": element-centred blocks
+        # (Sec. 3.4) weighted one on the element / by the inverse multiplicity
+        opts.smoother = {"star": L.SEMMG_SMOOTHER_STAR, "element": L.SEMMG_SMOOTHER_ELEMENT,
+                         "element_mult": L.SEMMG_SMOOTHER_ELEMENT_MULT}[smoother]
+        self.smoother = smoother
         self.precision = precision
         self.solver = solver
         rc = self._lib.semmg_setup(ctypes.byref(mesh), self.p, self.lam, ctypes.byref(opts), _stream(stream),
@@ -124,6 +129,12 @@ class Context:
         self._check(self._lib.semmg_pack(self._ctx, level, _ptr(u_nodal), _ptr(out), _stream()))
         return out
 
+    def pack_dirichlet(self, level, g_nodal, out=None):
+        """E g: the Dirichlet-face values of g_nodal in their skeleton slots, zero elsewhere."""
+        out = self._hat(level) if out is None else out
+        self._check(self._lib.semmg_pack_dirichlet(self._ctx, level, _ptr(g_nodal), _ptr(out), _stream()))
+        return out
+
     def unpack(self, level, u_hat, out=None):
         out = torch.zeros(self.nodal_shape(level), dtype=torch.float64, device="cuda") if out is None else out
         self._check(self._lib.semmg_unpack(self._ctx, level, _ptr(u_hat), _ptr(out), _stream()))
@@ -182,12 +193,17 @@ class Context:
         self._check(self._lib.semmg_recover(self._ctx, _ptr(f_nodal), _ptr(u_hat), _ptr(out), _stream()))
         return out
 
-    def solve(self, f_nodal, rtol=1e-10, out=None, allow_not_converged=False):
+    def solve(self, f_nodal, rtol=1e-10, out=None, allow_not_converged=False, g=None):
+        """Solve for u; g (nodal, optional): inhomogeneous Dirichlet data, read on the Dirichlet faces."""
         out = torch.empty(self.nodal_shape(), dtype=torch.float64, device="cuda") if out is None else out
         info = L.semmg_info()
         allow = (L.SEMMG_ERR_NOT_CONVERGED,) if allow_not_converged else ()
-        self._check(self._lib.semmg_solve(self._ctx, _ptr(f_nodal), _ptr(out), rtol, ctypes.byref(info), _stream()),
-                    allow)
+        if g is None:
+            rc = self._lib.semmg_solve(self._ctx, _ptr(f_nodal), _ptr(out), rtol, ctypes.byref(info), _stream())
+        else:
+            rc = self._lib.semmg_solve_dirichlet(self._ctx, _ptr(f_nodal), _ptr(g), _ptr(out), rtol,
+                                                 ctypes.byref(info), _stream())
+        self._check(rc, allow)
         return out, info
 
     def solve_host(self, f_host, u_host, rtol=1e-10, allow_not_converged=False):

@@ -67,7 +67,15 @@ def test_setup_rejects_bad_arguments_without_touching_the_gpu(lib):
     opts = L.semmg_opts()
     lib.semmg_default_opts(ctypes.byref(opts))
     assert (opts.p0, opts.nu_pre, opts.nu_post, opts.precision, opts.max_iter) == (2, 1, 1, 0, 50)
-    assert (opts.solver, opts.nu_vary) == (L.SEMMG_SOLVER_MG, 0)
+    assert (opts.solver, opts.nu_vary, opts.smoother) == (L.SEMMG_SOLVER_MG, 0, L.SEMMG_SMOOTHER_STAR)
+    opts.smoother = 5
+    assert lib.semmg_setup(ctypes.byref(mesh), 4, 1.0, ctypes.byref(opts), None, ctypes.byref(ctx)) == -1
+    # element-centred blocks span three elements: a periodic axis of two is unsupported
+    opts.smoother = L.SEMMG_SMOOTHER_ELEMENT
+    mesh.bc[0] = mesh.bc[1] = L.SEMMG_BC_PERIODIC
+    assert lib.semmg_setup(ctypes.byref(mesh), 4, 1.0, ctypes.byref(opts), None, ctypes.byref(ctx)) == -2
+    mesh.bc[0] = mesh.bc[1] = L.SEMMG_BC_DIRICHLET
+    opts.smoother = L.SEMMG_SMOOTHER_STAR
     opts.solver = 7
     assert lib.semmg_setup(ctypes.byref(mesh), 4, 1.0, ctypes.byref(opts), None, ctypes.byref(ctx)) == -1
     opts.solver = L.SEMMG_SOLVER_KMG

@@ -422,35 +422,44 @@ def test_eblock_tables_generalized_eigen(bc):
             np.testing.assert_allclose(Sa.T @ La @ Sa, np.diag(lam[ia]), atol=1e-10 * lam.max())
 
 
+@pytest.mark.parametrize("kind", ["element", "multiplicity"])
 @pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC, NEUMANN, PERIODIC_BC, ("P",) * 6])
-def test_eblock_weights_partition_of_unity(bc):
-    # sum over the blocks holding an unknown of its weight is one (inverse multiplicity, Sec. 2.3)
+def test_eblock_weights_partition_of_unity(bc, kind):
+    # the weights of the blocks holding an unknown sum to one (Sec. 2.3, eq. smoother_definition)
     mesh = _mesh_eblock(p=3, bc=bc)
     cond = dense.Condensed(mesh, dense=False)
     tot = np.zeros(len(cond.B))
     cnt = np.zeros(len(cond.B))
     for c in dense.eblock_centres(mesh):
         pos, j = dense.eblock_positions(mesh, cond.B, c)
-        tot[pos] += dense.eblock_weights(mesh, cond.B, pos)
+        W = dense.eblock_weights(mesh, cond.B, pos, c, kind)
+        tot[pos] += W
         cnt[pos] += 1
         assert np.all((j >= 1) & (j <= 3 * mesh.p - 1))
+        if kind == "element":  # zero outside the element's closure, one strictly inside it
+            outside = np.any((j < mesh.p) | (j > 2 * mesh.p), axis=1)
+            assert np.all(W[outside] == 0.0)
+            assert np.all(W[np.all((j > mesh.p) & (j < 2 * mesh.p), axis=1)] == 1.0)
+        else:
+            assert np.all(W > 0.0)
     np.testing.assert_allclose(tot, 1.0, rtol=0, atol=1e-15)
     # a face node of an interior element lies in 2 x 3 x 3 blocks
     assert cnt.max() <= 27 and cnt.min() >= 1
 
 
-@pytest.mark.parametrize("p,lam,bc", [(2, 0.0, DIRICHLET), (3, 0.8, DIRICHLET), (4, 2.0, MIXED_BC),
-                                      (3, 0.5, NEUMANN), (3, 0.0, PERIODIC_BC), (4, 1.0, ("P",) * 6)])
-def test_eblock_fdm_equals_dense_inverse(p, lam, bc):
+@pytest.mark.parametrize("p,lam,bc,kind", [(2, 0.0, DIRICHLET, "element"), (3, 0.8, DIRICHLET, "multiplicity"),
+                                           (4, 2.0, MIXED_BC, "element"), (3, 0.5, NEUMANN, "multiplicity"),
+                                           (3, 0.0, PERIODIC_BC, "element"), (4, 1.0, ("P",) * 6, "multiplicity")])
+def test_eblock_fdm_equals_dense_inverse(p, lam, bc, kind):
     # the embedding of Sec. 3.1 applied to the 3^3-element block: the full block's fast diagonalisation
     # read on the block's skeleton equals the inverse of the restricted condensed operator
     mesh = _mesh_eblock(p=p, lam=lam, bc=bc)
     cond = dense.Condensed(mesh)
     r = _rng(23).standard_normal(len(cond.B))
-    d_dense = dense.smoother_eblock_dense(mesh, cond, r)
+    d_dense = dense.smoother_eblock_dense(mesh, cond, r, kind)
     rn = np.zeros(mesh.shape)
     rn.ravel()[cond.B] = r
-    d_o2 = matfree.smooth_eblock(mesh, rn).ravel()[cond.B]
+    d_o2 = matfree.smooth_eblock(mesh, rn, matfree.EBlockTables(mesh, kind)).ravel()[cond.B]
     assert np.abs(d_o2 - d_dense).max() < 1e-12 * np.abs(d_dense).max()
 
 
@@ -462,11 +471,13 @@ def test_eblock_single_element_is_exact_inverse(bc):
     cond = dense.Condensed(mesh)
     r = _rng(24).standard_normal(len(cond.B))
     exact = np.linalg.solve(cond.Hhat, r)
-    assert np.abs(dense.smoother_eblock_dense(mesh, cond, r) - exact).max() < 1e-12 * np.abs(exact).max()
     rn = np.zeros(mesh.shape)
     rn.ravel()[cond.B] = r
-    d_o2 = matfree.smooth_eblock(mesh, rn).ravel()[cond.B]
-    assert np.abs(d_o2 - exact).max() < 1e-11 * np.abs(exact).max()
+    for kind in ("element", "multiplicity"):
+        d1 = dense.smoother_eblock_dense(mesh, cond, r, kind)
+        assert np.abs(d1 - exact).max() < 1e-12 * np.abs(exact).max()
+        d_o2 = matfree.smooth_eblock(mesh, rn, matfree.EBlockTables(mesh, kind)).ravel()[cond.B]
+        assert np.abs(d_o2 - exact).max() < 1e-11 * np.abs(exact).max()
 
 
 def test_eblock_periodic_needs_three_elements():
@@ -475,14 +486,14 @@ def test_eblock_periodic_needs_three_elements():
         matfree.EBlockTables(mesh)
 
 
-@pytest.mark.parametrize("bc", [DIRICHLET, MIXED_BC, PERIODIC_BC])
-def test_eblock_mg_matches_direct_solve(bc):
+@pytest.mark.parametrize("bc,smoother", [(DIRICHLET, "element"), (MIXED_BC, "element_mult"), (PERIODIC_BC, "element")])
+def test_eblock_mg_matches_direct_solve(bc, smoother):
     # the element-centred smoother as a drop-in in Algorithms 3 and 4 (and 5)
     mesh = _mesh_eblock(p=5, lam=0.0 if bc == DIRICHLET else 1.0, bc=bc)
     cond = dense.Condensed(mesh)
     f = _rng(25).uniform(-1, 1, mesh.shape)
     uex = cond.full_solve(cond.load(f))
-    mg = matfree.MG(mesh, p0=1, smoother="element")
+    mg = matfree.MG(mesh, p0=1, smoother=smoother)
     Fh = matfree.condense_rhs(mesh, f)
     for solve in (matfree.mg_solve, matfree.kmg_solve):
         uh, it, hist = solve(mg, Fh)

@@ -16,6 +16,9 @@ Workloads (names used by bench.py and the tests):
   expansion_widths(n, alpha)
                           per-axis widths in geometric progression on (0, 2 pi), the stretched
                           meshes of the paper's iteration-count table (Sec. 5.4)
+  paper_sec52_8x8x8_p{16,32}
+                          paper_solution on 8^3 uniform elements of (0, 2 pi)^3, k = 5, lambda = 0,
+                          Dirichlet data u_ex at all faces (the problem of the runtime tests, Sec. 5.2)
   paper_solution(h, p, k, lam)
                           the manufactured solution of the paper's runtime tests (Sec. 5.2) on
                           (0, 2 pi)^3 with inhomogeneous Dirichlet data: (u_ex, f = lam u_ex - Laplace u_ex)
