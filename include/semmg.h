@@ -80,8 +80,10 @@ enum {
  *   SEMMG_MIXED_FP32  the whole V-cycle in FP32, level residuals included;
  *   SEMMG_MIXED_TC    as SEMMG_MIXED, with the star smoother's 1D transforms on
  *                     tensor cores (tcgen05, TF32 operands, FP32 accumulation)
- *                     on the levels with 16 <= p <= 32; other levels as SEMMG_MIXED. */
-enum { SEMMG_FP64 = 0, SEMMG_MIXED = 1, SEMMG_MIXED_FP32 = 2, SEMMG_MIXED_TC = 3 };
+ *                     on the levels with 16 <= p <= 32; other levels as SEMMG_MIXED;
+ *   SEMMG_MIXED_FP32_TC  as SEMMG_MIXED_FP32, with the tensor-core smoother of
+ *                     SEMMG_MIXED_TC on the levels it covers. */
+enum { SEMMG_FP64 = 0, SEMMG_MIXED = 1, SEMMG_MIXED_FP32 = 2, SEMMG_MIXED_TC = 3, SEMMG_MIXED_FP32_TC = 4 };
 /* outer iteration of semmg_solve and of the batched form */
 enum { SEMMG_SOLVER_MG = 0, SEMMG_SOLVER_KMG = 1 };
 /* Schwarz smoother of the V-cycle levels */
@@ -114,7 +116,7 @@ typedef struct {
   int p0;          /* coarse degree, 1 <= p0 <= p (default 2, Sec. 4.1) */
   int nu_pre;      /* pre-smoothing steps per level (default 1, Algorithm 3) */
   int nu_post;     /* post-smoothing steps per level (default 1) */
-  int precision;   /* SEMMG_FP64 (default), SEMMG_MIXED, SEMMG_MIXED_FP32 or SEMMG_MIXED_TC */
+  int precision;   /* SEMMG_FP64 (default), SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC or SEMMG_MIXED_FP32_TC */
   int max_iter;    /* iteration cap of semmg_solve (default 50) */
   int solver;      /* SEMMG_SOLVER_MG (Algorithm 4, default) or SEMMG_SOLVER_KMG (Algorithm 5) */
   int nu_vary;     /* 0 (default): nu_pre / nu_post steps on every level; 1: nu_pre 2^(L-l) and
@@ -269,11 +271,17 @@ int semmg_solve_host(semmg_ctx* ctx, const double* f_host, double* u_host, doubl
  * semmg_batch_solve launches the graph on `stream`, waits for it, and fills
  * infos[0..nb-1] (NULL allowed); it returns SEMMG_OK when every solve
  * converged, else the first non-zero status.
+ * semmg_batch_create_dirichlet is the same with Dirichlet data per solve:
+ * g_nodal[i] (device nodal array of context i, or NULL for homogeneous data;
+ * g_nodal itself may be NULL) is read as semmg_solve_dirichlet reads it.
  * semmg_batch_graph_nodes reports the node count of the captured top-level
  * graph (kernel and memset nodes plus one conditional node per solve). */
 typedef struct semmg_batch semmg_batch;
 int semmg_batch_create(semmg_ctx* const* ctxs, int nb, const double* const* f_nodal, double* const* u_nodal,
                        double rtol, void* stream, semmg_batch** out);
+int semmg_batch_create_dirichlet(semmg_ctx* const* ctxs, int nb, const double* const* f_nodal,
+                                 const double* const* g_nodal, double* const* u_nodal, double rtol, void* stream,
+                                 semmg_batch** out);
 int semmg_batch_solve(semmg_batch* batch, semmg_info* infos, void* stream);
 int semmg_batch_graph_nodes(const semmg_batch* batch, int64_t* nodes);
 void semmg_batch_destroy(semmg_batch* batch);

@@ -23,7 +23,7 @@ ERRORS = {
     -7: "SEMMG_ERR_NOMEM",
 }
 SEMMG_ERR_NOT_CONVERGED = -4
-SEMMG_FP64, SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC = 0, 1, 2, 3
+SEMMG_FP64, SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC = 0, 1, 2, 3, 4
 SEMMG_SOLVER_MG, SEMMG_SOLVER_KMG = 0, 1
 SEMMG_SMOOTHER_STAR, SEMMG_SMOOTHER_ELEMENT, SEMMG_SMOOTHER_ELEMENT_MULT = 0, 1, 2
 SEMMG_BC_DIRICHLET, SEMMG_BC_NEUMANN, SEMMG_BC_PERIODIC = 0, 1, 2
@@ -81,6 +81,9 @@ SIGNATURES = {
     "semmg_smooth_noalloc": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "semmg_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_void_p),
                                    ctypes.POINTER(c_void_p), c_double, c_void_p, ctypes.POINTER(c_void_p)]),
+    "semmg_batch_create_dirichlet": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_void_p),
+                                             ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_double, c_void_p,
+                                             ctypes.POINTER(c_void_p)]),
     "semmg_batch_solve": (c_int, [c_void_p, ctypes.POINTER(semmg_info), c_void_p]),
     "semmg_batch_graph_nodes": (c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "semmg_batch_destroy": (None, [c_void_p]),

@@ -35,7 +35,7 @@ struct DevLevel {
   void* Uw = nullptr;
   void* Rw = nullptr;
   LaunchCfg schur64, schur32, star64, star32;
-  LaunchCfg startc;  // tensor-core star smoother (SEMMG_MIXED_TC), when the level allows it
+  LaunchCfg startc;  // tensor-core star smoother (SEMMG_MIXED_TC, _FP32_TC), when the level allows it
   LaunchCfg eb64, eb32;  // element-centred block smoother (SEMMG_SMOOTHER_ELEMENT)
 };
 
@@ -746,7 +746,7 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   if (!(lambda >= 0.0) || !std::isfinite(lambda)) return SEMMG_ERR_INVALID_ARG;
   if (o.nu_pre < 0 || o.nu_post < 0 || o.max_iter < 1) return SEMMG_ERR_INVALID_ARG;
   if (o.precision != SEMMG_FP64 && o.precision != SEMMG_MIXED && o.precision != SEMMG_MIXED_FP32 &&
-      o.precision != SEMMG_MIXED_TC)
+      o.precision != SEMMG_MIXED_TC && o.precision != SEMMG_MIXED_FP32_TC)
     return SEMMG_ERR_INVALID_ARG;
   if (o.solver != SEMMG_SOLVER_MG && o.solver != SEMMG_SOLVER_KMG) return SEMMG_ERR_INVALID_ARG;
   if (o.nu_vary != 0 && o.nu_vary != 1) return SEMMG_ERR_INVALID_ARG;
@@ -840,7 +840,7 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
         const int64_t nE = 3 * (int64_t)G.p - 1;
         obs = std::max(obs, (size_t)(G.nelem * 6 * nE * nE));
       }
-      if (o.precision == SEMMG_MIXED_TC && o.smoother == SEMMG_SMOOTHER_STAR) {
+      if ((o.precision == SEMMG_MIXED_TC || o.precision == SEMMG_MIXED_FP32_TC) && o.smoother == SEMMG_SMOOTHER_STAR) {
         D.startc = plan_star_tc(G, c->nsm);
         if (D.startc.ok) {
           upload_tc_tables(c.get(), c->hl[l], D.tf, &ok);
@@ -1244,9 +1244,10 @@ struct semmg_batch {
 namespace {
 
 // Enqueue one solve of context c (device nodal f -> u) into the capturing stream s.
-int capture_solve(semmg_ctx* c, const double* f, double* u, BatchCtl* ctl, cudaStream_t s, cudaStream_t sb) {
+int capture_solve(semmg_ctx* c, const double* f, const double* gdata, double* u, BatchCtl* ctl, cudaStream_t s,
+                  cudaStream_t sb) {
   condense_impl(c, f, c->Fh, true, s);
-  iter_start(c, s);
+  iter_start(c, s, gdata);
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g) != cudaSuccess || cs != cudaStreamCaptureStatusActive)
@@ -1285,6 +1286,11 @@ extern "C" {
 
 int semmg_batch_create(semmg_ctx* const* ctxs, int nb, const double* const* f, double* const* u, double rtol,
                        void* stream, semmg_batch** out) {
+  return semmg_batch_create_dirichlet(ctxs, nb, f, nullptr, u, rtol, stream, out);
+}
+
+int semmg_batch_create_dirichlet(semmg_ctx* const* ctxs, int nb, const double* const* f, const double* const* g,
+                                 double* const* u, double rtol, void* stream, semmg_batch** out) {
   if (!out) return SEMMG_ERR_INVALID_ARG;
   *out = nullptr;
   if (!ctxs || !f || !u || nb < 1 || !(rtol > 0.0)) return SEMMG_ERR_INVALID_ARG;
@@ -1348,20 +1354,20 @@ int semmg_batch_create(semmg_ctx* const* ctxs, int nb, const double* const* f, d
   cudaEventRecord(ev[nb], cap);
   for (int i = 0; i < nb && rc == SEMMG_OK; ++i) {
     cudaStreamWaitEvent(s[i], ev[nb], 0);
-    rc = capture_solve(ctxs[i], f[i], u[i], b->dctl + i, s[i], sb[i]);
+    rc = capture_solve(ctxs[i], f[i], g ? g[i] : nullptr, u[i], b->dctl + i, s[i], sb[i]);
     cudaEventRecord(ev[i], s[i]);
     cudaStreamWaitEvent(cap, ev[i], 0);
   }
-  cudaGraph_t g = nullptr;
-  const cudaError_t ee = cudaStreamEndCapture(cap, &g);
-  if (rc == SEMMG_OK && (ee != cudaSuccess || !g)) rc = SEMMG_ERR_CUDA;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+  if (rc == SEMMG_OK && (ee != cudaSuccess || !graph)) rc = SEMMG_ERR_CUDA;
   if (rc == SEMMG_OK) {
     size_t nn = 0;
-    cudaGraphGetNodes(g, nullptr, &nn);
+    cudaGraphGetNodes(graph, nullptr, &nn);
     b->nodes = (int64_t)nn;
-    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) rc = SEMMG_ERR_CUDA;
+    if (cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) rc = SEMMG_ERR_CUDA;
   }
-  b->graph = g;
+  b->graph = graph;
   cudaGetLastError();
   cleanup();
   if (rc != SEMMG_OK) return rc;
@@ -1498,7 +1504,7 @@ extern "C" int semmg_autotune(semmg_ctx* c, void* stream) {
   // except for the all-FP32 cycle (whose outer residual is FP64 too).  The FP64
   // timing input is Uh, which holds at least as many values as any level.
   const bool c32 = cycle32(c);
-  const bool all32 = c->opts.precision == SEMMG_MIXED_FP32;
+  const bool all32 = c->opts.precision == SEMMG_MIXED_FP32 || c->opts.precision == SEMMG_MIXED_FP32_TC;
   for (int l = 0; l <= L; ++l) {
     if (l >= 1) {
       if (c32)

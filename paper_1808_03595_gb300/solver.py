@@ -54,7 +54,7 @@ class Context:
         opts.nu_pre = nu_pre
         opts.nu_post = nu_post
         opts.precision = {"fp64": L.SEMMG_FP64, "mixed": L.SEMMG_MIXED, "mixed_fp32": L.SEMMG_MIXED_FP32,
-                          "mixed_tc": L.SEMMG_MIXED_TC}[precision]
+                          "mixed_tc": L.SEMMG_MIXED_TC, "mixed_fp32_tc": L.SEMMG_MIXED_FP32_TC}[precision]
         opts.max_iter = max_iter
         opts.solver = {"mg": L.SEMMG_SOLVER_MG, "kmg": L.SEMMG_SOLVER_KMG}[solver]
         opts.nu_vary = 1 if nu_vary else 0
@@ -257,15 +257,22 @@ class Batch:
     the f tensors in place and call solve() again to solve new right-hand sides.
     """
 
-    def __init__(self, ctxs, f_list, u_list, rtol=1e-10, stream=None):
+    def __init__(self, ctxs, f_list, u_list, rtol=1e-10, stream=None, g_list=None):
+        """g_list (optional): per solve a device nodal tensor of Dirichlet data, or None."""
         self._lib = L.load()
         self._b = ctypes.c_void_p()
         self.ctxs, self.f, self.u = list(ctxs), list(f_list), list(u_list)
+        self.g = list(g_list) if g_list is not None else None
         nb = len(self.ctxs)
         arr = (ctypes.c_void_p * nb)
-        rc = self._lib.semmg_batch_create(arr(*[c._ctx.value for c in self.ctxs]), nb,
-                                          arr(*[t.data_ptr() for t in self.f]), arr(*[t.data_ptr() for t in self.u]),
-                                          rtol, _stream(stream), ctypes.byref(self._b))
+        ctx_a = arr(*[c._ctx.value for c in self.ctxs])
+        f_a, u_a = arr(*[t.data_ptr() for t in self.f]), arr(*[t.data_ptr() for t in self.u])
+        if self.g is None:
+            rc = self._lib.semmg_batch_create(ctx_a, nb, f_a, u_a, rtol, _stream(stream), ctypes.byref(self._b))
+        else:
+            g_a = arr(*[(t.data_ptr() if t is not None else None) for t in self.g])
+            rc = self._lib.semmg_batch_create_dirichlet(ctx_a, nb, f_a, g_a, u_a, rtol, _stream(stream),
+                                                        ctypes.byref(self._b))
         if rc != 0:
             raise SemmgError(rc, "batch_create")
 

@@ -86,3 +86,32 @@ def test_batch_rejects_a_context_twice():
     with pytest.raises(SemmgError):
         Batch([c, c], [fd, fd], [torch.empty_like(fd), torch.empty_like(fd)])
     c.close()
+
+
+def test_batch_with_dirichlet_data_and_element_smoother():
+    # per-solve Dirichlet data (None: homogeneous) and the element-centred smoother inside the graph:
+    # each branch equals its stand-alone semmg_solve_dirichlet / semmg_solve
+    from paper_1808_03595_gb300 import Batch, Context
+    specs = [(workloads.uniform_widths(3), 6, 0.0, "fp64", "star", True),
+             (workloads.stretched_widths(3, 8), 5, 1.0, "mixed", "element", True),
+             (workloads.uniform_widths(2), 8, 2.0, "fp64", "star", False)]
+    ctxs, fs, gs, us, refs = [], [], [], [], []
+    for i, (h, p, lam, prec, sm, lifted) in enumerate(specs):
+        c = Context(h, p, lam, p0=2, precision=prec, smoother=sm)
+        fd = torch.as_tensor(workloads.random_nodal(h, p, 90 + i, "uniform"), device="cuda")
+        gd = torch.as_tensor(workloads.random_nodal(h, p, 95 + i, "uniform"), device="cuda") if lifted else None
+        u_ref, info = c.solve(fd, g=gd)
+        refs.append((u_ref.cpu().numpy(), info.iters))
+        ctxs.append(c)
+        fs.append(fd)
+        gs.append(gd)
+        us.append(torch.full_like(fd, float("nan")))
+    b = Batch(ctxs, fs, us, g_list=gs)
+    rc, infos = b.solve()
+    assert rc == 0
+    for (u_ref, it_ref), u, info in zip(refs, us, infos):
+        assert info.status == 0 and info.iters == it_ref
+        assert np.abs(u.cpu().numpy() - u_ref).max() <= 1e-12 * np.abs(u_ref).max()
+    b.close()
+    for c in ctxs:
+        c.close()

@@ -40,22 +40,25 @@ def test_tc_smoother_matches_oracle(p, n, stretched):
     r = _skel(h, p, 61)
     ref = matfree.smooth(m, r, chunk=16)
     mask = matfree.condensed_mask(m)
-    with Context(h, p, lam, p0=2, precision="mixed_tc") as c:
-        rh = c.pack(c.L, torch.as_tensor(r, device="cuda")).float()
-        got = c.unpack(c.L, c.smooth(c.L, rh).double()).cpu().numpy()
-    err = np.abs(got[mask] - ref[mask]).max() / np.abs(ref[mask]).max()
-    assert err < TOL_TF32, err
-    assert np.all(got[~mask] == 0.0)
+    for precision in ("mixed_tc", "mixed_fp32_tc"):
+        with Context(h, p, lam, p0=2, precision=precision) as c:
+            rh = c.pack(c.L, torch.as_tensor(r, device="cuda")).float()
+            got = c.unpack(c.L, c.smooth(c.L, rh).double()).cpu().numpy()
+        err = np.abs(got[mask] - ref[mask]).max() / np.abs(ref[mask]).max()
+        assert err < TOL_TF32, (precision, err)
+        assert np.all(got[~mask] == 0.0)
 
 
+@pytest.mark.parametrize("precision", ["mixed_tc", "mixed_fp32_tc"])
 @pytest.mark.parametrize("p", [16, 32])
-def test_tc_solve_reaches_1e10(p):
+def test_tc_solve_reaches_1e10(p, precision):
+    # mixed_fp32_tc: the tensor-core smoother inside the all-FP32 V-cycle (FP32 level residuals)
     from paper_1808_03595_gb300 import Context
     h, p, lam, f, p0 = workloads.config(f"helmholtz_8x8x8_p{p}")
     fd = torch.as_tensor(f, device="cuda")
     with Context(h, p, lam, p0=p0) as c:
         _, info64 = c.solve(fd)
-    with Context(h, p, lam, p0=p0, precision="mixed_tc") as c:
+    with Context(h, p, lam, p0=p0, precision=precision) as c:
         u, info = c.solve(fd)
         u = u.cpu().numpy()
     assert info.status == 0 and info.res_final <= 1e-10 * info.res0
