@@ -107,7 +107,8 @@ def test_apply_condensed_vs_dense_schur(mesh_name, p, lam):
 
 @pytest.mark.parametrize("mesh_name,p,lam", [("uniform_5x4x3", 8, 1.0), ("stretched_3x2x2", 12, 0.0),
                                              ("uniform_3", 16, 100.0), ("thin_2x1x2", 24, 1.0),
-                                             ("thin_2x1x2", 32, 0.5)])
+                                             ("thin_2x1x2", 32, 0.5), ("thin_2x1x2", 47, 0.0),
+                                             ("thin_2x1x2", 48, 2.0)])
 def test_apply_condensed_vs_matrix_free_oracle(mesh_name, p, lam):
     h = MESHES[mesh_name]
     m = omesh(h, p, lam)
@@ -138,7 +139,8 @@ def test_smooth_vs_dense_star_inverses(mesh_name, p, lam):
 
 
 @pytest.mark.parametrize("mesh_name,p,lam", [("uniform_5x4x3", 8, 1.0), ("stretched_3x2x2", 11, 0.0),
-                                             ("uniform_3", 16, 100.0), ("thin_2x1x2", 24, 1.0)])
+                                             ("uniform_3", 16, 100.0), ("thin_2x1x2", 24, 1.0),
+                                             ("thin_2x1x2", 47, 0.5), ("thin_2x1x2", 48, 0.0)])
 def test_smooth_vs_matrix_free_oracle(mesh_name, p, lam):
     h = MESHES[mesh_name]
     m = omesh(h, p, lam)
@@ -203,7 +205,7 @@ def test_coarse_solve_exact(mesh_name, p0, lam):
 # ------------------------------------------------------------------ condensation, recovery (Algorithm 4)
 
 @pytest.mark.parametrize("mesh_name,p,lam", [("stretched_3x2x2", 4, 1.0), ("uniform_5x4x3", 9, 0.0),
-                                             ("thin_2x1x2", 20, 2.0)])
+                                             ("thin_2x1x2", 20, 2.0), ("thin_2x1x2", 48, 0.5)])
 def test_condense_and_recover_vs_oracle(mesh_name, p, lam):
     h = MESHES[mesh_name]
     m = omesh(h, p, lam)
