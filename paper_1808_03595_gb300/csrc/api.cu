@@ -827,6 +827,8 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     D.schur32 = plan_elem_schur<float>(G, c->nsm);
     wsb = std::max(wsb, D.schur64.ws_elems() * sizeof(double));
     wsb = std::max(wsb, D.schur32.ws_elems() * sizeof(float));
+    if (G.m >= 7)  // room for the split Schur form, which the autotuner may pick
+      wsb = std::max(wsb, plan_elem_schur<double>(G, c->nsm, 0, 0, -1, 1).ws_elems() * sizeof(double));
     zs = std::max(zs, (size_t)(G.nelem * 6 * (int64_t)G.m * G.m));
     if (l >= 1) {
       D.star64 = plan_star<double>(G, c->nsm);
@@ -1419,6 +1421,7 @@ struct TuneChoice {
   size_t cap;
   int block;
   int wide;
+  int split;  // element Schur kernel: 1 = the split form
 };
 std::mutex g_tune_lock;
 std::map<std::tuple<int, int, int>, TuneChoice> g_tune;  // (kernel, element size, degree) -> choice
@@ -1463,27 +1466,39 @@ void tune_one(semmg_ctx* c, int l, int kernel, LaunchCfg& slot, const T* in, cud
     if (it != g_tune.end()) {
       const TuneChoice& ch = it->second;
       LaunchCfg cf = kernel == 0 ? plan_star<T>(G, c->nsm, ch.cap, ch.block, ch.wide)
-                                 : plan_elem_schur<T>(G, c->nsm, ch.cap, ch.block, ch.wide);
+                                 : plan_elem_schur<T>(G, c->nsm, ch.cap, ch.block, ch.wide, ch.split);
       if (cf.ok && cf.ws_elems() * sizeof(T) <= c->ws_bytes) slot = cf;
       return;
     }
   }
   float best = 1e30f;
-  TuneChoice bc{0, 0, 0};
+  TuneChoice bc{0, 0, 0, 0};
   LaunchCfg bcfg = slot;
   for (size_t cap : kTuneCaps)
     for (int blk : kTuneBlocks)
       for (int wide : kTuneWide) {
         LaunchCfg cf = kernel == 0 ? plan_star<T>(G, c->nsm, cap, blk, wide)
-                                   : plan_elem_schur<T>(G, c->nsm, cap, blk, wide);
+                                   : plan_elem_schur<T>(G, c->nsm, cap, blk, wide, 0);
         if (!cf.ok || cf.ws_elems() * sizeof(T) > c->ws_bytes) continue;
         const float ms = time_launch<T>(c, l, kernel, cf, in, nullptr, st);
         if (ms < best) {
           best = ms;
-          bc = TuneChoice{cap, blk, wide};
+          bc = TuneChoice{cap, blk, wide, 0};
           bcfg = cf;
         }
       }
+  // the split form of the Schur kernel, both register budgets (elements with p >= 8)
+  for (int wide : kTuneWide) {
+    if (kernel != 1 || G.m < 7) break;
+    LaunchCfg cf = plan_elem_schur<T>(G, c->nsm, 0, 0, wide, 1);
+    if (!cf.ok || cf.ws_elems() * sizeof(T) > c->ws_bytes) continue;
+    const float ms = time_launch<T>(c, l, kernel, cf, in, nullptr, st);
+    if (ms < best) {
+      best = ms;
+      bc = TuneChoice{0, 0, wide, 1};
+      bcfg = cf;
+    }
+  }
   if (best < 1e30f) {
     slot = bcfg;
     std::lock_guard<std::mutex> g(g_tune_lock);
@@ -1537,11 +1552,11 @@ extern "C" int semmg_set_launch(semmg_ctx* c, int level, int kernel, int dtype, 
   if (dtype == SEMMG_F64) {
     es = sizeof(double);
     cf = kernel == 0 ? plan_star<double>(G, c->nsm, smem_cap, block, wide)
-                     : plan_elem_schur<double>(G, c->nsm, smem_cap, block, wide);
+                     : plan_elem_schur<double>(G, c->nsm, smem_cap, block, wide, 0);
   } else {
     es = sizeof(float);
     cf = kernel == 0 ? plan_star<float>(G, c->nsm, smem_cap, block, wide)
-                     : plan_elem_schur<float>(G, c->nsm, smem_cap, block, wide);
+                     : plan_elem_schur<float>(G, c->nsm, smem_cap, block, wide, 0);
   }
   if (!cf.ok || cf.ws_elems() * es > c->ws_bytes)
     return fail(c, SEMMG_ERR_UNSUPPORTED, "set_launch: shape does not fit the work memory of the context");

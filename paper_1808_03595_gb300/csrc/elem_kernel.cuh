@@ -322,6 +322,54 @@ __device__ __forceinline__ void faces_reduce(int m, int ne, const T* a0, const T
   }
 }
 
+// The Schur kernels' reduction order, shared by the fused and the split forms
+// so that both give bitwise the same result: faces 0..3 (sums over k1 or k2 at
+// fixed k3) as in faces_reduce; faces 4, 5 (sums over k3) in slabs of
+// schur_slab(m) k3-values, one chain per slab, slabs added in order.
+__host__ __device__ __forceinline__ int schur_slab(int m) { return m > 31 ? 4 : 8; }
+
+// Faces 0..3 at the k3 rows [r0, r1) of the eigenspace slab W (rows r0..r1-1
+// stored from W[0]): X[f][k3][.] for f < 4.
+template <typename T>
+__device__ __forceinline__ void faces_reduce_rows(int m, int ne, const T* a0, const T* W, int r0, int r1, T* X) {
+  const int mm = m * m, nr = r1 - r0;
+  for (int idx = threadIdx.x; idx < 4 * nr * m; idx += blockDim.x) {
+    const int f = idx / (nr * m), r = idx - f * nr * m, k3 = r0 + r / m, kx = r - (r / m) * m;
+    const int k0 = (f & 1) ? ne : 0, k1 = (f & 1) ? m : ne;
+    const T* w;
+    int ws;
+    if (f < 2) {
+      w = W + ((k3 - r0) * m + kx) * m;  // along k1 at (k3, k2 = kx)
+      ws = 1;
+    } else {
+      w = W + (k3 - r0) * mm + kx;       // along k2 at (k3, k1 = kx)
+      ws = m;
+    }
+    T s0 = 0, s1 = 0;
+    int k = k0;
+    for (; k + 1 < k1; k += 2) {
+      s0 += a0[k] * w[k * ws];
+      s1 += a0[k + 1] * w[(k + 1) * ws];
+    }
+    if (k < k1) s0 += a0[k] * w[k * ws];
+    X[f * mm + k3 * m + kx] = s0 + s1;
+  }
+}
+
+// Partial sums of faces 4, 5 over the k3 rows [r0, r1) of one slab (W as above):
+// P[f - 4][k2][k1], one chain over k3 within the parity range of the face.
+template <typename T>
+__device__ __forceinline__ void faces_reduce_slab45(int m, int ne, const T* a0, const T* W, int r0, int r1, T* P) {
+  const int mm = m * m;
+  for (int idx = threadIdx.x; idx < 2 * mm; idx += blockDim.x) {
+    const int f = idx / mm, r = idx - f * mm;
+    const int lo = max(r0, f ? ne : 0), hi = min(r1, f ? m : ne);
+    T acc = 0;
+    for (int k3 = lo; k3 < hi; ++k3) acc += a0[k3] * W[(k3 - r0) * mm + r];
+    P[idx] = acc;
+  }
+}
+
 __device__ __forceinline__ double inv_d(const Tabs<double>& t, const ElemScal<double>& sc, const double* lI,
                                         double lam, int64_t idx, int k1, int k2, int k3, int64_t n3) {
   if (t.Relem) return t.Relem[sc.cls * n3 + idx];
@@ -386,10 +434,154 @@ __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const 
       W[idx] = face_expand(m, ne, a0, X, k1, k2, k3) * inv_d(t, sc, lI, lam, idx, k1, k2, k3, n3);
     }
     __syncthreads();
-    faces_reduce(m, ne, a0, W, X);
+    faces_reduce_rows(m, ne, a0, W, 0, m, X);
+    // faces 4, 5: slab partials in order (schur_slab(m) k3-rows each), as the split form sums them
+    const int slab = schur_slab(m);
+    for (int idx = threadIdx.x; idx < 2 * mm; idx += blockDim.x) {
+      const int f = idx / mm, r = idx - f * mm;
+      const int flo = f ? ne : 0, fhi = f ? m : ne;
+      T tot = 0;
+      for (int r0 = 0; r0 < m; r0 += slab) {
+        const int lo = max(r0, flo), hi = min(r0 + slab, fhi);
+        T acc = 0;
+        for (int k3 = lo; k3 < hi; ++k3) acc += a0[k3] * W[k3 * mm + r];
+        tot = r0 == 0 ? acc : tot + acc;
+      }
+      X[(4 + f) * mm + r] = tot;
+    }
     __syncthreads();
     T* Ze = Z + e * 6 * mm;
     faces_backward(F, Sh, X, Tt, sc, [&](int idx, T v) { Ze[idx] = v; });
+  }
+}
+
+// ---------------------------------------------------------------- split Schur form
+// The same Schur term in three launches whose work units are smaller than an
+// element, so that few large elements still fill every SM: (e, axis) units
+// transform one face pair forward, (e, k3-slab) units build one slab of the
+// eigenspace with its face reductions, (e, axis) units transform one pair back.
+// Bitwise the same result as k_elem_schur (same per-output arithmetic and the
+// shared reduction order).  Global arrays (per element): Xf transformed faces
+// (6 m^2), Xr reduced faces 0..3 (4 m^2), Xp slab partials of faces 4, 5
+// (nslab x 2 m^2).
+
+// (e, d): faces 2d, 2d+1 -> pair sum / difference -> forward 2D transform -> Xf[e][2d..2d+1]
+template <typename T, int PC, int NB>
+__global__ void __launch_bounds__(256, 2 * NB) k_schur_fwd(Geo G, Tabs<T> t, const T* __restrict__ u, T* __restrict__ Xf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = PC ? PC - 1 : G.m, mm = m * m;
+  T* Sh = reinterpret_cast<T*>(smem_raw);
+  T* X = Sh + mm;
+  T* Tt = X + 2 * mm;
+  __shared__ T sc2[2];
+  for (int i = threadIdx.x; i < mm; i += blockDim.x) Sh[i] = t.Sh[i];
+  const Lines F{m, m / 2, (m + 1) / 2, m, m, 2 * mm};
+  for (int64_t unit = blockIdx.x; unit < 3 * G.nelem; unit += gridDim.x) {
+    const int64_t e = unit / 3;
+    const int d = (int)(unit - 3 * e);
+    int a1, a2, a3;
+    elem_coords(G, e, &a1, &a2, &a3);
+    const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
+    __syncthreads();
+    if (threadIdx.x < 2) sc2[threadIdx.x] = sc.sf[d];
+    for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+      const T a = u[elem_face_base(G, a1, a2, a3, 2 * d) + i], b = u[elem_face_base(G, a1, a2, a3, 2 * d + 1) + i];
+      X[i] = a + b;
+      X[mm + i] = a - b;
+    }
+    __syncthreads();
+    fold_lines(F, 0, X, Tt);
+    __syncthreads();
+    tx_lines_g(F, 0, Sh, Tt, X, (T)1, (const T*)nullptr);
+    __syncthreads();
+    fold_lines(F, 1, X, Tt);
+    __syncthreads();
+    T* out = Xf + (e * 6 + 2 * d) * (int64_t)mm;
+    tx_lines_g(F, 1, Sh, Tt, out, (T)1, (const T*)sc2);
+  }
+}
+
+// (e, s): eigenspace rows k3 in slab s -> W -> faces 0..3 rows (complete) and faces 4, 5 partials
+template <typename T, int PC, int NB>
+__global__ void __launch_bounds__(256, 2 * NB) k_schur_eig(Geo G, Tabs<T> t, const T* __restrict__ Xf, T* __restrict__ Xr,
+                                                       T* __restrict__ Xp, int nslab) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = PC ? PC - 1 : G.m, mm = m * m, ne = (m + 1) / 2;
+  const int64_t n3 = (int64_t)mm * m;
+  T* a0 = reinterpret_cast<T*>(smem_raw);
+  T* lI = a0 + m;
+  T* X = lI + m;
+  T* W = X + 6 * mm;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    a0[i] = t.a0[i];
+    lI[i] = t.lamI[i];
+  }
+  const T lam = (T)G.lam;
+  for (int64_t unit = blockIdx.x; unit < (int64_t)nslab * G.nelem; unit += gridDim.x) {
+    const int64_t e = unit / nslab;
+    const int sl = (int)(unit - e * nslab);
+    const int r0 = sl * schur_slab(m), r1 = min(r0 + schur_slab(m), m);
+    int a1, a2, a3;
+    elem_coords(G, e, &a1, &a2, &a3);
+    const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
+    __syncthreads();
+    const T* xf = Xf + e * 6 * (int64_t)mm;
+    for (int i = threadIdx.x; i < 6 * mm; i += blockDim.x) X[i] = xf[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < (r1 - r0) * mm; i += blockDim.x) {
+      const int64_t idx = (int64_t)r0 * mm + i;
+      const int k1 = (int)(idx % m), k2 = (int)((idx / m) % m), k3 = (int)(idx / mm);
+      W[i] = face_expand(m, ne, a0, X, k1, k2, k3) * inv_d(t, sc, lI, lam, idx, k1, k2, k3, n3);
+    }
+    __syncthreads();
+    faces_reduce_rows(m, ne, a0, W, r0, r1, Xr + e * 4 * (int64_t)mm);
+    faces_reduce_slab45(m, ne, a0, W, r0, r1, Xp + (e * nslab + sl) * 2 * (int64_t)mm);
+  }
+}
+
+// (e, d): faces 2d, 2d+1 reduced (d = 2: slab partials summed in order) -> backward transform -> Z
+template <typename T, int PC, int NB>
+__global__ void __launch_bounds__(256, 2 * NB) k_schur_bwd(Geo G, Tabs<T> t, const T* __restrict__ Xr,
+                                                       const T* __restrict__ Xp, T* __restrict__ Z, int nslab) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = PC ? PC - 1 : G.m, mm = m * m;
+  T* Sh = reinterpret_cast<T*>(smem_raw);
+  T* X = Sh + mm;
+  T* Tt = X + 2 * mm;
+  for (int i = threadIdx.x; i < mm; i += blockDim.x) Sh[i] = t.Sh[i];
+  const Lines F{m, m / 2, (m + 1) / 2, m, m, 2 * mm};
+  for (int64_t unit = blockIdx.x; unit < 3 * G.nelem; unit += gridDim.x) {
+    const int64_t e = unit / 3;
+    const int d = (int)(unit - 3 * e);
+    int a1, a2, a3;
+    elem_coords(G, e, &a1, &a2, &a3);
+    const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
+    __syncthreads();
+    if (d < 2) {
+      const T* xr = Xr + (e * 4 + 2 * d) * (int64_t)mm;
+      for (int i = threadIdx.x; i < 2 * mm; i += blockDim.x) X[i] = xr[i];
+    } else {
+      const T* xp = Xp + e * nslab * 2 * (int64_t)mm;
+      for (int i = threadIdx.x; i < 2 * mm; i += blockDim.x) {
+        T tot = xp[i];
+        for (int sl = 1; sl < nslab; ++sl) tot = tot + xp[(int64_t)sl * 2 * mm + i];
+        X[i] = tot;
+      }
+    }
+    __syncthreads();
+    txT_lines_g(F, 0, Sh, X, Tt);
+    __syncthreads();
+    unfold_lines(F, 0, Tt, X);
+    __syncthreads();
+    txT_lines_g(F, 1, Sh, X, Tt);
+    __syncthreads();
+    T* Ze = Z + e * 6 * (int64_t)mm;
+    for (int r = threadIdx.x; r < mm; r += blockDim.x) {
+      const T ye = unfold_at(F, 1, Tt, r);
+      const T yo = unfold_at(F, 1, Tt, mm + r);
+      Ze[(2 * d) * mm + r] = sc.sf[d] * (ye + yo);
+      Ze[(2 * d + 1) * mm + r] = sc.sf[d] * (ye - yo);
+    }
   }
 }
 
@@ -563,11 +755,35 @@ constexpr size_t kSchurSmemCap = 200 * 1024;
 
 }  // namespace
 
+// Shared memory of the split kernels: forward / backward (Sh, a pair, its scratch)
+// and the eigenspace slab kernel (a0, Lam, six faces, one slab).
+inline size_t schur_split_smem_fb(int m, size_t es) { return (size_t)5 * m * m * es; }
+inline size_t schur_split_smem_eig(int m, size_t es) {
+  return ((size_t)2 * m + (size_t)(6 + schur_slab(m)) * m * m) * es;
+}
+
 template <typename T>
-LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap, int block, int wide) {
+LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap, int block, int wide, int split) {
+  const size_t m = G.m, mm = m * m;
+  const size_t es = sizeof(T);
+  // the split form (sub-element work units) when asked; the automatic choice is the fused
+  // kernel (measured faster in FP64 on the 8^3 meshes), the autotuner times both
+  const bool fits = m >= 1 && schur_split_smem_eig((int)m, es) <= 200 * 1024;
+  if (split > 0) {
+    LaunchCfg c;
+    const int nslab = ((int)m + schur_slab((int)m) - 1) / schur_slab((int)m);
+    c.depth = nslab;
+    c.block = 256;
+    c.wide = wide >= 0 ? wide : 1;
+    c.smem = schur_split_smem_eig((int)m, es);
+    const int64_t units = (int64_t)nslab * G.nelem;
+    c.grid = (int)(units < (1 << 30) ? units : (1 << 30));
+    c.flat = (size_t)G.nelem * (10 + 2 * (size_t)nslab) * mm;
+    c.ok = fits;
+    return c;
+  }
   LaunchCfg c;
   if (cap == 0) cap = kSchurSmemCap;
-  const size_t m = G.m, mm = m * m;
   const size_t sizes[4] = {mm + 2 * m, 6 * mm, 6 * mm, mm * m};
   c.ws = plan_regions(sizes, 4, sizeof(T), cap, &c.smem);
   c.ok = plan_ok(c.ws, sizes, 4, sizeof(T), c.smem);
@@ -591,19 +807,61 @@ void launch_elem_schur_nb(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* w
   }
 }
 
+template <typename T, int PC, int NB>
+void launch_schur_split_pc(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, const LaunchCfg& c,
+                           cudaStream_t st) {
+  const int m = G.m, nslab = c.depth;
+  const int64_t mm = (int64_t)m * m;
+  T* Xf = ws;
+  T* Xr = Xf + G.nelem * 6 * mm;
+  T* Xp = Xr + G.nelem * 4 * mm;
+  const size_t sfb = schur_split_smem_fb(m, sizeof(T)), seig = schur_split_smem_eig(m, sizeof(T));
+  const int64_t u3 = 3 * G.nelem, us = (int64_t)nslab * G.nelem;
+  const int g3 = (int)(u3 < (1 << 30) ? u3 : (1 << 30)), gs = (int)(us < (1 << 30) ? us : (1 << 30));
+  k_schur_fwd<T, PC, NB><<<g3, 256, sfb, st>>>(G, t, u, Xf);
+  k_schur_eig<T, PC, NB><<<gs, 256, seig, st>>>(G, t, Xf, Xr, Xp, nslab);
+  k_schur_bwd<T, PC, NB><<<g3, 256, sfb, st>>>(G, t, Xr, Xp, Z, nslab);
+}
+
+template <typename T, int NB>
+void launch_schur_split(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, const LaunchCfg& c,
+                        cudaStream_t st) {
+  switch (G.p) {
+    case 16: launch_schur_split_pc<T, 16, NB>(G, t, u, Z, ws, c, st); break;
+    case 32: launch_schur_split_pc<T, 32, NB>(G, t, u, Z, ws, c, st); break;
+    default: launch_schur_split_pc<T, 0, NB>(G, t, u, Z, ws, c, st); break;
+  }
+}
+
 template <typename T>
 void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, const LaunchCfg& c,
                        cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
+  if (c.depth > 0) {
+    if (c.wide)
+      launch_schur_split<T, 1>(G, t, u, Z, ws, c, st);
+    else
+      launch_schur_split<T, 2>(G, t, u, Z, ws, c, st);
+    return;
+  }
   if (c.wide)
     launch_elem_schur_nb<T, 1>(G, t, u, Z, ws, c, st);
   else
     launch_elem_schur_nb<T, 2>(G, t, u, Z, ws, c, st);
 }
 
+template <typename T, int PC, int NB>
+static int schur_split_attrs_pc() {
+  int bad = 0;
+  bad |= cudaFuncSetAttribute(k_schur_fwd<T, PC, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_schur_eig<T, PC, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_schur_bwd<T, PC, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return bad;
+}
+
 template <typename T, int NB>
 static int schur_attrs_nb() {
-  int bad = 0;
+  int bad = schur_split_attrs_pc<T, 0, NB>() | schur_split_attrs_pc<T, 16, NB>() | schur_split_attrs_pc<T, 32, NB>();
   bad |= cudaFuncSetAttribute(k_elem_schur<T, 0, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_schur<T, 2, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_schur<T, 4, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -3,7 +3,7 @@
 
 namespace semmg {
 
-template LaunchCfg plan_elem_schur<float>(const Geo&, int, size_t, int, int);
+template LaunchCfg plan_elem_schur<float>(const Geo&, int, size_t, int, int, int);
 template void launch_elem_schur<float>(const Geo&, const Tabs<float>&, const float*, float*, float*,
                                        const LaunchCfg&, cudaStream_t);
 

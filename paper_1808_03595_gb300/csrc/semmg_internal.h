@@ -297,8 +297,13 @@ struct LaunchCfg {
   // register budget of the kernel build: 0 = at most 64 registers per thread
   // (1024 resident threads per SM), 1 = at most 128 (512 resident threads)
   int wide = 0;
-  int depth = 0;                 // element-block kernel: k3-planes of the eigenspace slab
-  size_t ws_elems() const { return (size_t)ws.gstride * (size_t)grid; }
+  int depth = 0;                 // element-block kernel: k3-planes of the eigenspace slab;
+                                 // Schur term: k3-slabs of the split form (0: one fused kernel)
+  size_t flat = 0;               // work elements of a form whose buffers are not per CTA
+  size_t ws_elems() const {
+    const size_t per_cta = (size_t)ws.gstride * (size_t)grid;
+    return per_cta > flat ? per_cta : flat;
+  }
 };
 
 // Greedy placement: regions visited in `order` (all regions when order is
@@ -367,8 +372,10 @@ inline int resident_blocks(LaunchCfg& c, int wide) {
   return bps < 1 ? 1 : bps;
 }
 
+// split: -1 automatic (the fused kernel), 0 the fused kernel with the launch shape given,
+// 1 the split form (sub-element work units; the autotuner times it against the fused one)
 template <typename T> LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap = 0, int block = 0,
-                                                int wide = -1);
+                                                int wide = -1, int split = -1);
 template <typename T> void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws,
                                              const LaunchCfg& c, cudaStream_t st);
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm);
