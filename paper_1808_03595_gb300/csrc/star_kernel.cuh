@@ -44,6 +44,24 @@ __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(
 // k3-planes of the eigenspace held at once.
 __host__ __device__ __forceinline__ int slab_thickness(int nS) { return nS <= 16 ? 8 : (nS <= 32 ? 4 : 2); }
 
+// f(b1 + o1, b2 + o2) for the n pairs j = o2 w + o1 of a segment, j strided by the
+// block: each thread divides once and then steps its (o1, o2) by the block size.
+template <typename F>
+__device__ __forceinline__ void for_pairs(int n, int w, int b1, int b2, F f) {
+  if (n <= 0 || w <= 0) return;
+  const int nT = blockDim.x, q = nT / w, r = nT - q * w;
+  int o2 = threadIdx.x / w, o1 = threadIdx.x - o2 * w;
+  for (int j = threadIdx.x; j < n; j += nT) {
+    f(b1 + o1, b2 + o2);
+    o1 += r;
+    o2 += q;
+    if (o1 >= w) {
+      o1 -= w;
+      ++o2;
+    }
+  }
+}
+
 // Plane pass helpers: axis index of the fast (a) and slow (b) in-plane axes.
 __device__ __forceinline__ int ax_fast(int dd) { return dd == 0 ? 1 : 0; }
 __device__ __forceinline__ int ax_slow(int dd) { return dd == 2 ? 1 : 2; }
@@ -323,9 +341,9 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
     const int nz1 = rg.pa[0] ? (sym[0] ? m + 1 : w1) : 0;
     const int nz2 = rg.pa[1] ? (sym[1] ? m + 1 : w2) : 0;
     const int nz3 = rg.pa[2] ? (sym[2] ? m + 1 : w3) : 0;
-    // (k1, k2) pairs, live ones first so that warps stay on one branch:
-    // k2 live (any k1), then k2 dead with k1 live, then both dead (only the
-    // x3-plane term, so only when that plane is active); the live k_d are the
+    // (k1, k2) pairs in three segments, each its own loop so that warps stay on
+    // one branch: k2 live (any k1), then k2 dead with k1 live, then both dead (only
+    // the x3-plane term, so only when that plane is active); the live k_d are the
     // first nz_d indices of the active range
     const int seg1 = nz2 * w1, seg2 = (w2 - nz2) * nz1, nlive = seg1 + seg2;
     const int npair = nlive + (rg.pa[2] ? (w2 - nz2) * (w1 - nz1) : 0);
@@ -337,23 +355,10 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
     for (int k3s = rg.lo[2]; k3s < rg.hi[2]; k3s += ts) {
       const int tn = rg.hi[2] - k3s < ts ? rg.hi[2] - k3s : ts;
       __syncthreads();
-      for (int i = threadIdx.x; i < npair; i += blockDim.x) {
-        int k1, k2;
-        if (i < seg1) {
-          k2 = lo2 + i / w1;
-          k1 = lo1 + i % w1;
-        } else if (i < nlive) {
-          const int j = i - seg1;
-          k2 = lo2 + nz2 + j / nz1;
-          k1 = lo1 + j % nz1;
-        } else {
-          const int j = i - nlive, wd = w1 - nz1;
-          k2 = lo2 + nz2 + j / wd;
-          k1 = lo1 + nz1 + j % wd;
-        }
+      auto live = [&](int k1, int k2) {
         const int pr = k2 * nS + k1;
         const T a3 = rg.pa[2] ? P[2 * n2 + pr] : (T)0;
-        if (i < nlive) {
+        {
           const T c1 = k1 - lo1 < nz1 ? s1[k1] : (T)0, c2 = k2 - lo2 < nz2 ? s2[k2] : (T)0;
           T b3 = 0;
           for (int kk = 0; kk < tn; ++kk) {
@@ -366,7 +371,12 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
             if (k3 - lo3 < nz3) b3 += s3[k3] * v;
           }
           if (nz3) B3[pr] += b3;
-        } else {
+        }
+      };
+      auto dead = [&](int k1, int k2) {
+        const int pr = k2 * nS + k1;
+        const T a3 = rg.pa[2] ? P[2 * n2 + pr] : (T)0;
+        {
           // s1[k1] = s2[k2] = 0: V = s3 a3 / D is read only by B3, which gets
           // a3 sum_k3 s3^2 / D
           T b3 = 0;
@@ -378,7 +388,10 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
           }
           B3[pr] += a3 * b3;
         }
-      }
+      };
+      for_pairs(seg1, w1, lo1, lo2, live);
+      for_pairs(seg2, nz1, lo1, lo2 + nz2, live);
+      if (rg.pa[2]) for_pairs(npair - nlive, w1 - nz1, lo1 + nz1, lo2 + nz2, dead);
       __syncthreads();
       // B1[k3][k2] = sum_k1 s1 V (plane 0 active), B2[k3][k1] = sum_k2 s2 V (plane 1 active)
       const int nb1 = rg.pa[0] ? tn * w2 : 0, nb2 = rg.pa[1] ? tn * w1 : 0;

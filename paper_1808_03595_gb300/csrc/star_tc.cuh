@@ -330,36 +330,43 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
     for (int k3s = rg.lo[2]; k3s < rg.hi[2]; k3s += ts) {
       const int tn = rg.hi[2] - k3s < ts ? rg.hi[2] - k3s : ts;
       __syncthreads();
-      for (int i = tid; i < npair; i += blockDim.x) {
-        int k1, k2;
-        if (i < seg1) {
-          k2 = lo2 + i / w1;
-          k1 = lo1 + i % w1;
-        } else if (i < nlive) {
-          const int j = i - seg1;
-          k2 = lo2 + nz2 + j / nz1;
-          k1 = lo1 + j % nz1;
-        } else {
-          const int j = i - nlive, wd = w1 - nz1;
-          k2 = lo2 + nz2 + j / wd;
-          k1 = lo1 + nz1 + j % wd;
-        }
+      auto live = [&](int k1, int k2) {
         const int pr = k2 * nS + k1;
         const float a3 = rg.pa[2] ? P2[k2 * ld + k1] : 0.0f;
         float* b3p = B3 + tc::coff(k1, k2, np);
-        if (i < nlive) {
+        {
           const float c1 = k1 - lo1 < nz1 ? s1[k1] : 0.0f, c2 = k2 - lo2 < nz2 ? s2[k2] : 0.0f;
+          // loop invariants of the k3 run (as in k_star): the (k1, k2) part of D and the rows
+          // where s3 may be non-zero
+          const float d12 = lam + Lm[k1] + Lm[nS + k2];
+          const float* p0 = P0 + k3s * ld + k2;
+          const float* p1 = P1 + k3s * ld + k1;
+          const int kl = min(max(lo3 + nz3 - k3s, 0), tn);
           float b3 = 0.0f;
-          for (int kk = 0; kk < tn; ++kk) {
+          // unrolled: four independent load - divide - store chains in flight per thread
+#pragma unroll 4
+          for (int kk = 0; kk < kl; ++kk) {
             const int k3 = k3s + kk;
-            float E = c1 * P0[k3 * ld + k2] + c2 * P1[k3 * ld + k1];
-            if (k3 - lo3 < nz3) E += s3[k3] * a3;
-            const float v = fast_div(E, lam + Lm[k1] + Lm[nS + k2] + Lm[2 * nS + k3]);
+            float E = c1 * p0[kk * ld] + c2 * p1[kk * ld];
+            E += s3[k3] * a3;
+            const float v = fast_div(E, d12 + Lm[2 * nS + k3]);
             V[kk * n2 + pr] = v;
-            if (k3 - lo3 < nz3) b3 += s3[k3] * v;
+            b3 += s3[k3] * v;
+          }
+#pragma unroll 4
+          for (int kk = kl; kk < tn; ++kk) {
+            const float E = c1 * p0[kk * ld] + c2 * p1[kk * ld];
+            V[kk * n2 + pr] = fast_div(E, d12 + Lm[2 * nS + k3s + kk]);
           }
           if (nz3) *b3p += b3;
-        } else {
+        }
+      };
+      auto dead = [&](int k1, int k2) {
+        const int pr = k2 * nS + k1;
+        const float a3 = rg.pa[2] ? P2[k2 * ld + k1] : 0.0f;
+        float* b3p = B3 + tc::coff(k1, k2, np);
+        (void)pr;
+        {
           float b3 = 0.0f;
           for (int kk = 0; kk < tn; ++kk) {
             const int k3 = k3s + kk;
@@ -368,7 +375,10 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
           }
           *b3p += a3 * b3;
         }
-      }
+      };
+      for_pairs(seg1, w1, lo1, lo2, live);
+      for_pairs(seg2, nz1, lo1, lo2 + nz2, live);
+      if (rg.pa[2]) for_pairs(npair - nlive, w1 - nz1, lo1 + nz1, lo2 + nz2, dead);
       __syncthreads();
       const int nb1 = rg.pa[0] ? tn * w2 : 0, nb2 = rg.pa[1] ? tn * w1 : 0;
       for (int o = tid; o < nb1 + nb2; o += blockDim.x) {
