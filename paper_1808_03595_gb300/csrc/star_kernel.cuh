@@ -21,6 +21,8 @@
 #pragma once
 #include "semmg_internal.h"
 
+#include <type_traits>
+
 namespace semmg {
 
 namespace {
@@ -355,15 +357,24 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
     for (int k3s = rg.lo[2]; k3s < rg.hi[2]; k3s += ts) {
       const int tn = rg.hi[2] - k3s < ts ? rg.hi[2] - k3s : ts;
       __syncthreads();
-      auto live = [&](int k1, int k2) {
+      // which = 0: s1[k1] and s2[k2] may both be non-zero; 1: only s1[k1] (k2 dead);
+      // 2: only s2[k2] (k1 dead) -- the zero term is left out
+      auto live = [&](auto which, int k1, int k2) {
+        constexpr int W = decltype(which)::value;
         const int pr = k2 * nS + k1;
         const T a3 = rg.pa[2] ? P[2 * n2 + pr] : (T)0;
         {
           const T c1 = k1 - lo1 < nz1 ? s1[k1] : (T)0, c2 = k2 - lo2 < nz2 ? s2[k2] : (T)0;
           T b3 = 0;
-          for (int kk = 0; kk < tn; ++kk) {
+          // bounded by the slab thickness, a constant in the degree-specialised builds
+#pragma unroll
+          for (int kk = 0; kk < ts; ++kk) {
+            if (kk >= tn) break;
             const int k3 = k3s + kk;
-            T E = c1 * P[k3 * nS + k2] + c2 * P[n2 + k3 * nS + k1];
+            T E;
+            if constexpr (W == 0) E = c1 * P[k3 * nS + k2] + c2 * P[n2 + k3 * nS + k1];
+            if constexpr (W == 1) E = c1 * P[k3 * nS + k2];
+            if constexpr (W == 2) E = c2 * P[n2 + k3 * nS + k1];
             if (k3 - lo3 < nz3) E += s3[k3] * a3;
             const int64_t pt = (int64_t)k3 * n2 + pr;
             const T v = R ? E * R[pt] : fast_div(E, lam + Lm[k1] + Lm[nS + k2] + Lm[2 * nS + k3]);
@@ -373,6 +384,9 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
           if (nz3) B3[pr] += b3;
         }
       };
+      auto live_both = [&](int k1, int k2) { live(std::integral_constant<int, 0>{}, k1, k2); };
+      auto live_1 = [&](int k1, int k2) { live(std::integral_constant<int, 1>{}, k1, k2); };
+      auto live_2 = [&](int k1, int k2) { live(std::integral_constant<int, 2>{}, k1, k2); };
       auto dead = [&](int k1, int k2) {
         const int pr = k2 * nS + k1;
         const T a3 = rg.pa[2] ? P[2 * n2 + pr] : (T)0;
@@ -389,8 +403,9 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
           B3[pr] += a3 * b3;
         }
       };
-      for_pairs(seg1, w1, lo1, lo2, live);
-      for_pairs(seg2, nz1, lo1, lo2 + nz2, live);
+      for_pairs(nz2 * nz1, nz1, lo1, lo2, live_both);                 // k1, k2 live
+      for_pairs(nz2 * (w1 - nz1), w1 - nz1, lo1 + nz1, lo2, live_2);  // k2 live, k1 dead
+      for_pairs(seg2, nz1, lo1, lo2 + nz2, live_1);                   // k1 live, k2 dead
       if (rg.pa[2]) for_pairs(npair - nlive, w1 - nz1, lo1 + nz1, lo2 + nz2, dead);
       __syncthreads();
       // B1[k3][k2] = sum_k1 s1 V (plane 0 active), B2[k3][k1] = sum_k2 s2 V (plane 1 active)
