@@ -410,37 +410,73 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
       __syncthreads();
       // B1[k3][k2] = sum_k1 s1 V (plane 0 active), B2[k3][k1] = sum_k2 s2 V (plane 1 active)
       const int nb1 = rg.pa[0] ? tn * w2 : 0, nb2 = rg.pa[1] ? tn * w1 : 0;
-      for (int o = threadIdx.x; o < nb1 + nb2; o += blockDim.x) {
-        const bool first = o < nb1;
-        const int rr = first ? o : o - nb1, wx = first ? w2 : w1;
-        const int kk = rr / wx, kx = (first ? lo2 : lo1) + rr % wx;
-        const T* vs = V + kk * n2;
-        T s = 0;
-        T s_1 = 0, s_2 = 0, s_3 = 0;  // four independent partial sums
-        if (first) {  // sum over k1
-          const T* v = vs + kx * nS + lo1;
-          const T* sv = s1 + lo1;
-          int k = 0;
-          for (; k + 3 < nz1; k += 4) {
-            s += sv[k] * v[k];
-            s_1 += sv[k + 1] * v[k + 1];
-            s_2 += sv[k + 2] * v[k + 2];
-            s_3 += sv[k + 3] * v[k + 3];
+      if constexpr (sizeof(T) == sizeof(double)) {
+        // four consecutive lanes per output, lane q summing the terms k = q (mod 4) of the
+        // full groups of four and lane 0 also the leftover ones -- the four partial sums and
+        // their combination (s0 + s1) + (s2 + s3) of a one-thread four-chain loop
+        const int nq = 4 * (nb1 + nb2);
+        for (int base = 0; base < nq; base += blockDim.x) {  // same trip count for every thread
+          const int o4 = base + (int)threadIdx.x, q = o4 & 3, o = o4 >> 2;
+          T sq = 0;
+          bool first = false;
+          int kk = 0, kx = 0;
+          if (o4 < nq) {
+            first = o < nb1;
+            const int rr = first ? o : o - nb1, wx = first ? w2 : w1;
+            kk = rr / wx;
+            kx = (first ? lo2 : lo1) + rr % wx;
+            const T* vs = V + kk * n2;
+            const int nz = first ? nz1 : nz2, full = nz & ~3;
+            const T* sv = first ? s1 + lo1 : s2 + lo2;
+            const T* v = first ? vs + kx * nS + lo1 : vs + kx + lo2 * nS;
+            const int vst = first ? 1 : nS;
+            for (int k = q; k < full; k += 4) sq += sv[k] * v[k * vst];
+            if (q == 0)
+              for (int k = full; k < nz; ++k) sq += sv[k] * v[k * vst];
           }
-          for (; k < nz1; ++k) s += sv[k] * v[k];
-          B1[(k3s + kk) * nS + kx] = (s + s_1) + (s_2 + s_3);
-        } else {      // sum over k2
-          const T* v = vs + kx + lo2 * nS;
-          const T* sv = s2 + lo2;
-          int k = 0;
-          for (; k + 3 < nz2; k += 4) {
-            s += sv[k] * v[k * nS];
-            s_1 += sv[k + 1] * v[(k + 1) * nS];
-            s_2 += sv[k + 2] * v[(k + 2) * nS];
-            s_3 += sv[k + 3] * v[(k + 3) * nS];
+          const T t1 = sq + __shfl_down_sync(0xffffffffu, sq, 1, 4);  // lanes 0, 2: s0 + s1, s2 + s3
+          const T t2 = t1 + __shfl_down_sync(0xffffffffu, t1, 2, 4);  // lane 0: (s0 + s1) + (s2 + s3)
+          if (o4 < nq && q == 0) {
+            if (first)
+              B1[(k3s + kk) * nS + kx] = t2;
+            else
+              B2[(k3s + kk) * nS + kx] = t2;
           }
-          for (; k < nz2; ++k) s += sv[k] * v[k * nS];
-          B2[(k3s + kk) * nS + kx] = (s + s_1) + (s_2 + s_3);
+        }
+      } else {
+        // one thread per output, four independent partial sums
+        for (int o = threadIdx.x; o < nb1 + nb2; o += blockDim.x) {
+          const bool first = o < nb1;
+          const int rr = first ? o : o - nb1, wx = first ? w2 : w1;
+          const int kk = rr / wx, kx = (first ? lo2 : lo1) + rr % wx;
+          const T* vs = V + kk * n2;
+          T s = 0;
+          T s_1 = 0, s_2 = 0, s_3 = 0;  // four independent partial sums
+          if (first) {  // sum over k1
+            const T* v = vs + kx * nS + lo1;
+            const T* sv = s1 + lo1;
+            int k = 0;
+            for (; k + 3 < nz1; k += 4) {
+              s += sv[k] * v[k];
+              s_1 += sv[k + 1] * v[k + 1];
+              s_2 += sv[k + 2] * v[k + 2];
+              s_3 += sv[k + 3] * v[k + 3];
+            }
+            for (; k < nz1; ++k) s += sv[k] * v[k];
+            B1[(k3s + kk) * nS + kx] = (s + s_1) + (s_2 + s_3);
+          } else {      // sum over k2
+            const T* v = vs + kx + lo2 * nS;
+            const T* sv = s2 + lo2;
+            int k = 0;
+            for (; k + 3 < nz2; k += 4) {
+              s += sv[k] * v[k * nS];
+              s_1 += sv[k + 1] * v[(k + 1) * nS];
+              s_2 += sv[k + 2] * v[(k + 2) * nS];
+              s_3 += sv[k + 3] * v[(k + 3) * nS];
+            }
+            for (; k < nz2; ++k) s += sv[k] * v[k * nS];
+            B2[(k3s + kk) * nS + kx] = (s + s_1) + (s_2 + s_3);
+          }
         }
       }
     }
