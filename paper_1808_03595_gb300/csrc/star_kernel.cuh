@@ -46,19 +46,37 @@ __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(
 // k3-planes of the eigenspace held at once.
 __host__ __device__ __forceinline__ int slab_thickness(int nS) { return nS <= 16 ? 8 : (nS <= 32 ? 4 : 2); }
 
-// f(b1 + o1, b2 + o2) for the n pairs j = o2 w + o1 of a segment, j strided by the
-// block: each thread divides once and then steps its (o1, o2) by the block size.
+// The n pairs j = o2 w + o1 of a segment, j strided by the block: the thread's
+// first pair and the block-size step, decoded once per star (integer division
+// goes through the FP64 pipe, which the FP64 kernel needs for its arithmetic).
+struct PairSeg {
+  int n, w, b1, b2, q, r, o1, o2;
+};
+
+__device__ __forceinline__ PairSeg pair_seg(int n, int w, int b1, int b2) {
+  PairSeg s{n, w, b1, b2, 0, 0, 0, 0};
+  if (n <= 0 || w <= 0) {
+    s.n = 0;
+    return s;
+  }
+  const int nT = blockDim.x;
+  s.q = nT / w;
+  s.r = nT - s.q * w;
+  s.o2 = threadIdx.x / w;
+  s.o1 = threadIdx.x - s.o2 * w;
+  return s;
+}
+
+// f(b1 + o1, b2 + o2) for this thread's pairs of the segment
 template <typename F>
-__device__ __forceinline__ void for_pairs(int n, int w, int b1, int b2, F f) {
-  if (n <= 0 || w <= 0) return;
-  const int nT = blockDim.x, q = nT / w, r = nT - q * w;
-  int o2 = threadIdx.x / w, o1 = threadIdx.x - o2 * w;
-  for (int j = threadIdx.x; j < n; j += nT) {
-    f(b1 + o1, b2 + o2);
-    o1 += r;
-    o2 += q;
-    if (o1 >= w) {
-      o1 -= w;
+__device__ __forceinline__ void for_pairs(const PairSeg& s, F f) {
+  int o1 = s.o1, o2 = s.o2;
+  for (int j = threadIdx.x; j < s.n; j += blockDim.x) {
+    f(s.b1 + o1, s.b2 + o2);
+    o1 += s.r;
+    o2 += s.q;
+    if (o1 >= s.w) {
+      o1 -= s.w;
       ++o2;
     }
   }
@@ -350,6 +368,11 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
     const int seg1 = nz2 * w1, seg2 = (w2 - nz2) * nz1, nlive = seg1 + seg2;
     const int npair = nlive + (rg.pa[2] ? (w2 - nz2) * (w1 - nz1) : 0);
     const int ts = slab_thickness(nS);
+    // the four pair segments (the same for every slab of the star)
+    const PairSeg sg_both = pair_seg(nz2 * nz1, nz1, lo1, lo2);                  // k1, k2 live
+    const PairSeg sg_k2 = pair_seg(nz2 * (w1 - nz1), w1 - nz1, lo1 + nz1, lo2);  // k2 live, k1 dead
+    const PairSeg sg_k1 = pair_seg(seg2, nz1, lo1, lo2 + nz2);                    // k1 live, k2 dead
+    const PairSeg sg_dead = pair_seg(rg.pa[2] ? npair - nlive : 0, w1 - nz1, lo1 + nz1, lo2 + nz2);
     T* B1 = Tt;
     T* B2 = Tt + n2;
     T* B3 = Tt + 2 * n2;
@@ -403,10 +426,10 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
           B3[pr] += a3 * b3;
         }
       };
-      for_pairs(nz2 * nz1, nz1, lo1, lo2, live_both);                 // k1, k2 live
-      for_pairs(nz2 * (w1 - nz1), w1 - nz1, lo1 + nz1, lo2, live_2);  // k2 live, k1 dead
-      for_pairs(seg2, nz1, lo1, lo2 + nz2, live_1);                   // k1 live, k2 dead
-      if (rg.pa[2]) for_pairs(npair - nlive, w1 - nz1, lo1 + nz1, lo2 + nz2, dead);
+      for_pairs(sg_both, live_both);
+      for_pairs(sg_k2, live_2);
+      for_pairs(sg_k1, live_1);
+      for_pairs(sg_dead, dead);
       __syncthreads();
       // B1[k3][k2] = sum_k1 s1 V (plane 0 active), B2[k3][k1] = sum_k2 s2 V (plane 1 active)
       const int nb1 = rg.pa[0] ? tn * w2 : 0, nb2 = rg.pa[1] ? tn * w1 : 0;
@@ -422,9 +445,13 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
           int kk = 0, kx = 0;
           if (o4 < nq) {
             first = o < nb1;
-            const int rr = first ? o : o - nb1, wx = first ? w2 : w1;
-            kk = rr / wx;
-            kx = (first ? lo2 : lo1) + rr % wx;
+            const int wx = first ? w2 : w1;
+            int rr = first ? o : o - nb1;
+            while (rr >= wx) {  // rr / wx < tn <= slab depth: subtract instead of dividing
+              rr -= wx;
+              ++kk;
+            }
+            kx = (first ? lo2 : lo1) + rr;
             const T* vs = V + kk * n2;
             const int nz = first ? nz1 : nz2, full = nz & ~3;
             const T* sv = first ? s1 + lo1 : s2 + lo2;
@@ -447,8 +474,13 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
         // one thread per output, four independent partial sums
         for (int o = threadIdx.x; o < nb1 + nb2; o += blockDim.x) {
           const bool first = o < nb1;
-          const int rr = first ? o : o - nb1, wx = first ? w2 : w1;
-          const int kk = rr / wx, kx = (first ? lo2 : lo1) + rr % wx;
+          const int wx = first ? w2 : w1;
+          int rr = first ? o : o - nb1, kk = 0;
+          while (rr >= wx) {  // rr / wx < tn <= slab depth: subtract instead of dividing
+            rr -= wx;
+            ++kk;
+          }
+          const int kx = (first ? lo2 : lo1) + rr;
           const T* vs = V + kk * n2;
           T s = 0;
           T s_1 = 0, s_2 = 0, s_3 = 0;  // four independent partial sums

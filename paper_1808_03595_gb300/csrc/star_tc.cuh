@@ -325,6 +325,10 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
     const int seg1 = nz2 * w1, seg2 = (w2 - nz2) * nz1, nlive = seg1 + seg2;
     const int npair = nlive + (rg.pa[2] ? (w2 - nz2) * (w1 - nz1) : 0);
     const int ts = slab_thickness(nS);
+    // the pair segments, the same for every slab of the star
+    const PairSeg sg_live1 = pair_seg(seg1, w1, lo1, lo2);
+    const PairSeg sg_live2 = pair_seg(seg2, nz1, lo1, lo2 + nz2);
+    const PairSeg sg_dead = pair_seg(rg.pa[2] ? npair - nlive : 0, w1 - nz1, lo1 + nz1, lo2 + nz2);
     float* B3 = R1 + 2 * tb;
     for (int i = tid; i < tb; i += blockDim.x) B3[i] = 0.0f;
     for (int k3s = rg.lo[2]; k3s < rg.hi[2]; k3s += ts) {
@@ -376,15 +380,20 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
           *b3p += a3 * b3;
         }
       };
-      for_pairs(seg1, w1, lo1, lo2, live);
-      for_pairs(seg2, nz1, lo1, lo2 + nz2, live);
-      if (rg.pa[2]) for_pairs(npair - nlive, w1 - nz1, lo1 + nz1, lo2 + nz2, dead);
+      for_pairs(sg_live1, live);
+      for_pairs(sg_live2, live);
+      for_pairs(sg_dead, dead);
       __syncthreads();
       const int nb1 = rg.pa[0] ? tn * w2 : 0, nb2 = rg.pa[1] ? tn * w1 : 0;
       for (int o = tid; o < nb1 + nb2; o += blockDim.x) {
         const bool first = o < nb1;
-        const int rr = first ? o : o - nb1, wx = first ? w2 : w1;
-        const int kk = rr / wx, kx = (first ? lo2 : lo1) + rr % wx;
+        const int wx = first ? w2 : w1;
+        int rr = first ? o : o - nb1, kk = 0;
+        while (rr >= wx) {  // rr / wx < tn <= slab depth: subtract instead of dividing
+          rr -= wx;
+          ++kk;
+        }
+        const int kx = (first ? lo2 : lo1) + rr;
         const float* vs = V + kk * n2;
         float s = 0.0f, s_1 = 0.0f, s_2 = 0.0f, s_3 = 0.0f;
         if (first) {
