@@ -54,16 +54,16 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 entry in th
 # weighted by the sweep's star launches per degree (28 at p = 4, 20 at 8, 12 at 16, 6 at 32);
 # profiles/k_star_f64_dram_helmholtz_8x8x8.md.  Valid only for the star-kernel source it was
 # measured on (hash below).
-STAR_TRAFFIC_BYTES = 7.993e6
-STAR_TRAFFIC_SOURCE = "a97920a3e327df7b"
+STAR_TRAFFIC_BYTES = 7.771e6
+STAR_TRAFFIC_SOURCE = "fb81d2dbe05b46a3"
 # Executed FP64 operations (2 DFMA + DMUL + DADD thread instructions, ncu sass counters) per
 # k_star<double> launch, per level degree, from `bench.py --degrees 32 --forms fp64 --no-e2e --no-batch
 # --no-configs --no-cpu-baseline --no-autotune --steps 1 --warmup 3` (the first launch at each of
 # p = 32, 16, 8, 4; profiles/k_star_f64_executed_ops_helmholtz_8x8x8.md), weighted like the traffic:
-# the kernel executes 34-42 % of the paper's 37 n_S^3 count, so this rate measures the FP64 pipe.
-STAR_EXEC_FLOPS = {4: 0.00388e9, 8: 0.03322e9, 16: 0.27498e9, 32: 2.26206e9}
+# the kernel executes 32-44 % of the paper's 37 n_S^3 count, so this rate measures the FP64 pipe.
+STAR_EXEC_FLOPS = {4: 0.004116e9, 8: 0.032777e9, 16: 0.264593e9, 32: 2.158269e9}
 STAR_EXEC_WEIGHTS = {4: 28, 8: 20, 16: 12, 32: 6}
-STAR_EXEC_SOURCE = "a97920a3e327df7b"
+STAR_EXEC_SOURCE = "fb81d2dbe05b46a3"
 STAR_SOURCES = ("star_kernel.cuh", "kernels_star_f64.cu")
 
 
