@@ -1521,7 +1521,7 @@ extern "C" int semmg_autotune(semmg_ctx* c, void* stream) {
   const bool c32 = cycle32(c);
   const bool all32 = c->opts.precision == SEMMG_MIXED_FP32 || c->opts.precision == SEMMG_MIXED_FP32_TC;
   for (int l = 0; l <= L; ++l) {
-    if (l >= 1) {
+    if (l >= 1 && c->opts.smoother == SEMMG_SMOOTHER_STAR) {  // the element-centred kernel has one shape
       if (c32)
         tune_one<float>(c, l, 0, c->dl[l].star32, (const float*)c->dl[l].Fw, st);
       else
