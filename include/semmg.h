@@ -66,7 +66,8 @@ enum {
   SEMMG_ERR_NOT_CONVERGED = -4, /* max_iter cycles without reaching rtol; info filled */
   SEMMG_ERR_NONFINITE = -5,     /* NaN or Inf in a residual norm */
   SEMMG_ERR_TIMEOUT = -6,       /* a bounded device wait ran out (batched form, tensor-core smoother) */
-  SEMMG_ERR_NOMEM = -7          /* device or host allocation failed */
+  SEMMG_ERR_NOMEM = -7,         /* device or host allocation failed */
+  SEMMG_ERR_DIVERGED = -8       /* the residual norm grew above 1e3 ||r_0||: stopped early; info filled */
 };
 
 #define SEMMG_MAX_DEGREE 48
@@ -233,7 +234,9 @@ int semmg_recover(semmg_ctx* ctx, const double* f_nodal, const double* u_hat, do
  * f_nodal and u_nodal are device nodal arrays of the finest level.  info may
  * be NULL; info->iters counts iterations (V-cycles).  Returns
  * SEMMG_ERR_NOT_CONVERGED after max_iter iterations (u_nodal still holds the
- * last iterate), SEMMG_ERR_NONFINITE on a NaN/Inf residual norm. */
+ * last iterate), SEMMG_ERR_NONFINITE on a NaN/Inf residual norm,
+ * SEMMG_ERR_DIVERGED as soon as ||r|| > 1e3 ||r_0|| (the iteration is not
+ * contracting: a wrong operator, data or option, not a slow start). */
 int semmg_solve(semmg_ctx* ctx, const double* f_nodal, double* u_nodal, double rtol,
                 semmg_info* info, void* stream);
 

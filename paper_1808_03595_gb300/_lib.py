@@ -21,8 +21,9 @@ ERRORS = {
     -5: "SEMMG_ERR_NONFINITE",
     -6: "SEMMG_ERR_TIMEOUT",
     -7: "SEMMG_ERR_NOMEM",
+    -8: "SEMMG_ERR_DIVERGED",
 }
-SEMMG_ERR_NOT_CONVERGED = -4
+SEMMG_ERR_NOT_CONVERGED, SEMMG_ERR_NONFINITE, SEMMG_ERR_DIVERGED = -4, -5, -8
 SEMMG_FP64, SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC = 0, 1, 2, 3, 4
 SEMMG_SOLVER_MG, SEMMG_SOLVER_KMG = 0, 1
 SEMMG_SMOOTHER_STAR, SEMMG_SMOOTHER_ELEMENT, SEMMG_SMOOTHER_ELEMENT_MULT = 0, 1, 2

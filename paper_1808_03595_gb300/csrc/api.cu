@@ -28,6 +28,10 @@ using namespace semmg;
 
 namespace {
 
+// the outer iteration stops when ||r|| exceeds this multiple of ||r_0||
+constexpr double kDivergence = 1e3;
+
+
 struct DevLevel {
   Tabs<double> td{};
   Tabs<float> tf{};
@@ -1084,7 +1088,10 @@ int solve_impl(semmg_ctx* c, const double* f, const double* g, double* u, double
     rc = dnorm_sync(c, st, &rn);
     if (rc) return rc;
     ++it;
-    if (!std::isfinite(rn)) status = SEMMG_ERR_NONFINITE;
+    if (!std::isfinite(rn))
+      status = SEMMG_ERR_NONFINITE;
+    else if (rn > kDivergence * r0)
+      status = SEMMG_ERR_DIVERGED;
   }
   if (status == SEMMG_OK && rn > rtol * r0) status = SEMMG_ERR_NOT_CONVERGED;
   recover_impl(c, f, c->Uh, u, true, st);
@@ -1145,6 +1152,7 @@ const char* semmg_strerror(int code) {
     case SEMMG_ERR_NONFINITE: return "non-finite residual";
     case SEMMG_ERR_TIMEOUT: return "device wait timed out";
     case SEMMG_ERR_NOMEM: return "out of memory";
+    case SEMMG_ERR_DIVERGED: return "residual diverged";
     default: return "unknown error";
   }
 }
@@ -1217,6 +1225,9 @@ __global__ void k_batch_check(BatchCtl* ctl, const double* dnorm, cudaGraphCondi
     cont = 0u;
   } else if (r <= ctl->rtol * ctl->rtol * ctl->res0sq) {
     ctl->status = SEMMG_OK;
+    cont = 0u;
+  } else if (r > kDivergence * kDivergence * ctl->res0sq) {
+    ctl->status = SEMMG_ERR_DIVERGED;
     cont = 0u;
   } else if (ctl->iters >= ctl->maxit) {
     ctl->status = SEMMG_ERR_NOT_CONVERGED;

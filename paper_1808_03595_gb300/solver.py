@@ -281,7 +281,7 @@ class Batch:
         nb = len(self.ctxs)
         infos = (L.semmg_info * nb)()
         rc = self._lib.semmg_batch_solve(self._b, infos, _stream(stream))
-        if rc not in (0, L.SEMMG_ERR_NOT_CONVERGED, -5):
+        if rc not in (0, L.SEMMG_ERR_NOT_CONVERGED, L.SEMMG_ERR_NONFINITE, L.SEMMG_ERR_DIVERGED):
             raise SemmgError(rc, "batch_solve")
         return rc, list(infos)
 

@@ -45,6 +45,10 @@ def test_every_declared_symbol_is_exported(lib):
 def test_strerror_without_gpu(lib):
     assert lib.semmg_strerror(0) == b"success"
     assert lib.semmg_strerror(-4) == b"not converged"
+    assert lib.semmg_strerror(-8) == b"residual diverged"
+    from paper_1808_03595_gb300 import _lib as L
+    for code in L.ERRORS:
+        assert lib.semmg_strerror(code) != lib.semmg_strerror(12345), code
     assert lib.semmg_last_error(None) == b"null context"
 
 
