@@ -294,9 +294,9 @@ void semmg_batch_destroy(semmg_batch* batch);
  * smoother (vertex-star contexts only) and of the element Schur kernel -- the
  * shared-memory budget per block (which decides which work arrays stay on
  * chip and how many blocks share an SM), the threads per block and the
- * register budget per thread (64 or 128, two builds of each kernel), and for
- * the Schur term also its split three-launch form -- on the context's own
- * buffers and keeps the fastest.  Every shape computes bitwise the same
+ * register budget per thread (64 or 128, two builds of each kernel); the
+ * Schur kernel is timed within a whole operator application -- on the
+ * context's own buffers, and keeps the fastest.  Every shape computes bitwise the same
  * result; only the time changes.  Choices are cached per process by (kernel, element size,
  * degree) and reused by later contexts without timing.  Synchronises the
  * stream; call it before capturing a batch. */

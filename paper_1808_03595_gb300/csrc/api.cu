@@ -20,6 +20,7 @@ namespace semmg {
 int set_elem_smem_limits();
 int set_star_smem_limits();
 int set_transfer_smem_limits();
+int set_face_smem_limits();
 int64_t restrict_face_buffer(const Geo& Gf, int pc);
 int64_t restrict_edge_buffer(const Geo& Gf, int pc);
 }  // namespace semmg
@@ -119,6 +120,9 @@ struct semmg_ctx {
   double* Gs = nullptr;
   // FP64 copy of a level's u for the FP64 level residuals of the SEMMG_MIXED cycle
   double* U64s = nullptr;
+  // faces of a level's u in the interior eigenbasis (face-parallel operator form;
+  // face slots of the finest level, in doubles)
+  void* Uts = nullptr;
   // Algorithm 5 vectors (old residual s, search direction p, q = Hhat p) and scalars
   double* kS = nullptr;
   double* kP = nullptr;
@@ -395,41 +399,64 @@ bool resid64(const semmg_ctx* c) {
   return c->opts.precision == SEMMG_MIXED || c->opts.precision == SEMMG_MIXED_TC;
 }
 
+// Whether level G runs the face-parallel form of the operator (the face
+// transforms once per face, launch_face_fwd / launch_face_bwd_assemble): from
+// p = 12 on, where the saved element work outweighs the extra launch (at p = 8
+// the element-face form is faster on GB300).
+bool face_form(const Geo& G) { return G.m >= 11; }
+
+// out = F - Hhat u (mode 0) or Hhat u (mode 1) on level l with arithmetic in T
+// (u, Schur terms) and F, out of type TF; cfg: the Schur kernel's launch shape.
+template <typename T, typename TF>
+void apply_op(semmg_ctx* c, int l, const Tabs<T>& tb, const LaunchCfg& cfg, const TF* F, const T* u, TF* out,
+              int mode, cudaStream_t st) {
+  const Geo& G = c->geo[l];
+  const double vec = (double)G.size * sizeof(TF), uvec = (double)G.size * sizeof(T);
+  const double zb = (double)G.nelem * 6 * G.m * G.m * sizeof(T);
+  const double fb = (double)G.oE1 * sizeof(T);
+  if (face_form(G)) {
+    {
+      Tic t(c, SEMMG_K_ELEM_SCHUR, st);
+      launch_face_fwd<T>(G, tb, u, (T*)c->Uts, st);
+      launch_elem_schur<T>(G, tb, (const T*)c->Uts, (T*)c->Zs, (T*)c->wss, cfg, st, 1);
+      t.toc(schur_flops(G), 3 * fb + zb, 2);
+    }
+    Tic t(c, SEMMG_K_ASSEMBLE, st);
+    launch_face_bwd_assemble<T, TF>(G, tb, F, u, (const T*)c->Uts, (const T*)c->Zs, out, mode, st);
+    t.toc(0.0, vec * (mode == 0 ? 2 : 1) + uvec + zb);
+    return;
+  }
+  {
+    Tic t(c, SEMMG_K_ELEM_SCHUR, st);
+    launch_elem_schur<T>(G, tb, u, (T*)c->Zs, (T*)c->wss, cfg, st);
+    t.toc(schur_flops(G), zb * 2, G.m > 0 ? 1 : 0);
+  }
+  Tic t(c, SEMMG_K_ASSEMBLE, st);
+  if constexpr (std::is_same<T, TF>::value)
+    launch_assemble<T>(G, tb, F, u, (T*)c->Zs, out, mode, st);
+  else
+    launch_assemble_mixed(G, tb, F, u, (const double*)c->Zs, out, mode, st);
+  t.toc(0.0, vec * (mode == 0 ? 2 : 1) + uvec + zb);
+}
+
 // out = F - Hhat u (mode 0) or Hhat u (mode 1) on level l.  FP32 vectors of
 // the SEMMG_MIXED form get FP64 arithmetic (FP64 face terms Z, FP64 sums).
 template <typename T>
 void op_residual(semmg_ctx* c, int l, const T* F, const T* u, T* out, int mode, cudaStream_t st) {
   const Geo& G = c->geo[l];
-  const double vec = (double)G.size * sizeof(T);
-  const double zb = (double)G.nelem * 6 * G.m * G.m * sizeof(T);
   if constexpr (std::is_same<T, float>::value) {
     if (resid64(c)) {
       // u widened to FP64 once, then the FP64 kernels; F and the result stay FP32
-      const double zb64 = (double)G.nelem * 6 * G.m * G.m * sizeof(double);
       {
         Tic t(c, SEMMG_K_VECTOR, st);
         launch_copy<double, float>(c->U64s, u, G.size, st);
         t.toc(0.0, (double)G.size * 12);
       }
-      {
-        Tic t(c, SEMMG_K_ELEM_SCHUR, st);
-        launch_elem_schur<double>(G, c->dl[l].td, c->U64s, (double*)c->Zs, (double*)c->wss, c->dl[l].schur64, st);
-        t.toc(schur_flops(G), zb64 * 2, G.m > 0 ? 1 : 0);
-      }
-      Tic t(c, SEMMG_K_ASSEMBLE, st);
-      launch_assemble_mixed(G, c->dl[l].td, F, c->U64s, (const double*)c->Zs, out, mode, st);
-      t.toc(0.0, vec * (mode == 0 ? 2 : 1) + 2.0 * vec + zb64);
+      apply_op<double, float>(c, l, c->dl[l].td, c->dl[l].schur64, F, c->U64s, out, mode, st);
       return;
     }
   }
-  {
-    Tic t(c, SEMMG_K_ELEM_SCHUR, st);
-    launch_elem_schur<T>(G, tabs<T>(c, l), u, (T*)c->Zs, (T*)c->wss, schur_cfg<T>(c, l), st);
-    t.toc(schur_flops(G), zb * 2, G.m > 0 ? 1 : 0);
-  }
-  Tic t(c, SEMMG_K_ASSEMBLE, st);
-  launch_assemble<T>(G, tabs<T>(c, l), F, u, (T*)c->Zs, out, mode, st);
-  t.toc(0.0, vec * (mode == 0 ? 3 : 2) + zb);
+  apply_op<T, T>(c, l, tabs<T>(c, l), schur_cfg<T>(c, l), F, u, out, mode, st);
 }
 
 // du = Smoother(r) (accumulate: du += Smoother(r)) on level l >= 1
@@ -670,7 +697,7 @@ int dnorm_sync(semmg_ctx* c, cudaStream_t st, double* out) {
 int set_limits(semmg_ctx* c) {
   if (g_limits_done) return SEMMG_OK;
   if (set_elem_smem_limits() | set_star_smem_limits() | set_transfer_smem_limits() | set_star_tc_smem_limits() |
-      set_eblock_smem_limits())
+      set_eblock_smem_limits() | set_face_smem_limits())
     return fail(c, SEMMG_ERR_CUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
   g_limits_done = 1;
   return SEMMG_OK;
@@ -831,8 +858,6 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     D.schur32 = plan_elem_schur<float>(G, c->nsm);
     wsb = std::max(wsb, D.schur64.ws_elems() * sizeof(double));
     wsb = std::max(wsb, D.schur32.ws_elems() * sizeof(float));
-    if (G.m >= 7)  // room for the split Schur form, which the autotuner may pick
-      wsb = std::max(wsb, plan_elem_schur<double>(G, c->nsm, 0, 0, -1, 1).ws_elems() * sizeof(double));
     zs = std::max(zs, (size_t)(G.nelem * 6 * (int64_t)G.m * G.m));
     if (l >= 1) {
       D.star64 = plan_star<double>(G, c->nsm);
@@ -893,6 +918,10 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
       c->Gs = (double*)dalloc(c.get(), ng * sizeof(double));
       if (!c->Gs) return SEMMG_ERR_NOMEM;
     }
+  }
+  if (c->geo[nl - 1].oE1 > 0) {
+    c->Uts = dalloc(c.get(), (size_t)c->geo[nl - 1].oE1 * sizeof(double));
+    if (!c->Uts) return SEMMG_ERR_NOMEM;
   }
   if (o.precision == SEMMG_MIXED || o.precision == SEMMG_MIXED_TC) {
     c->U64s = (double*)dalloc(c.get(), nL * sizeof(double));
@@ -1432,7 +1461,6 @@ struct TuneChoice {
   size_t cap;
   int block;
   int wide;
-  int split;  // element Schur kernel: 1 = the split form
 };
 std::mutex g_tune_lock;
 std::map<std::tuple<int, int, int>, TuneChoice> g_tune;  // (kernel, element size, degree) -> choice
@@ -1447,11 +1475,13 @@ float time_launch(semmg_ctx* c, int l, int kernel, const LaunchCfg& cfg, const T
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // the Schur kernel is timed inside the whole operator application (its face-parallel form
+  // moves work between the Schur and the assembly launches); out: a level-sized scratch vector
   auto run = [&]() {
     if (kernel == 0)
       launch_star<T>(G, tabs<T>(c, l), in, (T*)c->Obs, (T*)c->wss, cfg, c->star_counter, st);
     else
-      launch_elem_schur<T>(G, tabs<T>(c, l), in, (T*)c->Zs, (T*)c->wss, cfg, st);
+      apply_op<T, T>(c, l, tabs<T>(c, l), cfg, (const T*)nullptr, in, out, 1, st);
   };
   run();
   cudaEventRecord(e0, st);
@@ -1463,12 +1493,11 @@ float time_launch(semmg_ctx* c, int l, int kernel, const LaunchCfg& cfg, const T
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  (void)out;
   return ms / reps;
 }
 
 template <typename T>
-void tune_one(semmg_ctx* c, int l, int kernel, LaunchCfg& slot, const T* in, cudaStream_t st) {
+void tune_one(semmg_ctx* c, int l, int kernel, LaunchCfg& slot, const T* in, T* out, cudaStream_t st) {
   const Geo& G = c->geo[l];
   const auto key = std::make_tuple(kernel, (int)sizeof(T), G.p);
   {
@@ -1477,39 +1506,27 @@ void tune_one(semmg_ctx* c, int l, int kernel, LaunchCfg& slot, const T* in, cud
     if (it != g_tune.end()) {
       const TuneChoice& ch = it->second;
       LaunchCfg cf = kernel == 0 ? plan_star<T>(G, c->nsm, ch.cap, ch.block, ch.wide)
-                                 : plan_elem_schur<T>(G, c->nsm, ch.cap, ch.block, ch.wide, ch.split);
+                                 : plan_elem_schur<T>(G, c->nsm, ch.cap, ch.block, ch.wide);
       if (cf.ok && cf.ws_elems() * sizeof(T) <= c->ws_bytes) slot = cf;
       return;
     }
   }
   float best = 1e30f;
-  TuneChoice bc{0, 0, 0, 0};
+  TuneChoice bc{0, 0, 0};
   LaunchCfg bcfg = slot;
   for (size_t cap : kTuneCaps)
     for (int blk : kTuneBlocks)
       for (int wide : kTuneWide) {
         LaunchCfg cf = kernel == 0 ? plan_star<T>(G, c->nsm, cap, blk, wide)
-                                   : plan_elem_schur<T>(G, c->nsm, cap, blk, wide, 0);
+                                   : plan_elem_schur<T>(G, c->nsm, cap, blk, wide);
         if (!cf.ok || cf.ws_elems() * sizeof(T) > c->ws_bytes) continue;
-        const float ms = time_launch<T>(c, l, kernel, cf, in, nullptr, st);
+        const float ms = time_launch<T>(c, l, kernel, cf, in, out, st);
         if (ms < best) {
           best = ms;
-          bc = TuneChoice{cap, blk, wide, 0};
+          bc = TuneChoice{cap, blk, wide};
           bcfg = cf;
         }
       }
-  // the split form of the Schur kernel, both register budgets (elements with p >= 8)
-  for (int wide : kTuneWide) {
-    if (kernel != 1 || G.m < 7) break;
-    LaunchCfg cf = plan_elem_schur<T>(G, c->nsm, 0, 0, wide, 1);
-    if (!cf.ok || cf.ws_elems() * sizeof(T) > c->ws_bytes) continue;
-    const float ms = time_launch<T>(c, l, kernel, cf, in, nullptr, st);
-    if (ms < best) {
-      best = ms;
-      bc = TuneChoice{0, 0, wide, 1};
-      bcfg = cf;
-    }
-  }
   if (best < 1e30f) {
     slot = bcfg;
     std::lock_guard<std::mutex> g(g_tune_lock);
@@ -1534,13 +1551,14 @@ extern "C" int semmg_autotune(semmg_ctx* c, void* stream) {
   for (int l = 0; l <= L; ++l) {
     if (l >= 1 && c->opts.smoother == SEMMG_SMOOTHER_STAR) {  // the element-centred kernel has one shape
       if (c32)
-        tune_one<float>(c, l, 0, c->dl[l].star32, (const float*)c->dl[l].Fw, st);
+        tune_one<float>(c, l, 0, c->dl[l].star32, (const float*)c->dl[l].Fw, nullptr, st);
       else
-        tune_one<double>(c, l, 0, c->dl[l].star64, (const double*)c->dl[l].Fw, st);
+        tune_one<double>(c, l, 0, c->dl[l].star64, (const double*)c->dl[l].Fw, nullptr, st);
     }
     if (c->geo[l].m == 0) continue;
-    if (all32) tune_one<float>(c, l, 1, c->dl[l].schur32, (const float*)c->dl[l].Fw, st);
-    if (!all32 || l == L) tune_one<double>(c, l, 1, c->dl[l].schur64, c->Uh, st);
+    // operator outputs: the level's FP32 work vector / the finest-level FP64 residual (scratch here)
+    if (all32) tune_one<float>(c, l, 1, c->dl[l].schur32, (const float*)c->dl[l].Fw, (float*)c->dl[l].Rw, st);
+    if (!all32 || l == L) tune_one<double>(c, l, 1, c->dl[l].schur64, c->Uh, c->Rh, st);
   }
   c->timing = saved;
   if (cudaStreamSynchronize(st) != cudaSuccess) return check_cuda(c, "autotune");
@@ -1563,11 +1581,11 @@ extern "C" int semmg_set_launch(semmg_ctx* c, int level, int kernel, int dtype, 
   if (dtype == SEMMG_F64) {
     es = sizeof(double);
     cf = kernel == 0 ? plan_star<double>(G, c->nsm, smem_cap, block, wide)
-                     : plan_elem_schur<double>(G, c->nsm, smem_cap, block, wide, 0);
+                     : plan_elem_schur<double>(G, c->nsm, smem_cap, block, wide);
   } else {
     es = sizeof(float);
     cf = kernel == 0 ? plan_star<float>(G, c->nsm, smem_cap, block, wide)
-                     : plan_elem_schur<float>(G, c->nsm, smem_cap, block, wide, 0);
+                     : plan_elem_schur<float>(G, c->nsm, smem_cap, block, wide);
   }
   if (!cf.ok || cf.ws_elems() * es > c->ws_bytes)
     return fail(c, SEMMG_ERR_UNSUPPORTED, "set_launch: shape does not fit the work memory of the context");

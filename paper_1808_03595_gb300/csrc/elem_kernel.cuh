@@ -31,6 +31,7 @@ namespace {
 template <typename T>
 struct ElemScal {
   T sf[3];      // c_f alpha_d for the two faces of axis d
+  T al[3];      // alpha_d alone (faces transformed beforehand, scaled by c_f there)
   T e[3];       // 4 / h_d^2
   int64_t cls;  // width-class triple of the element (for the 1/D table)
 };
@@ -45,6 +46,9 @@ __device__ __forceinline__ ElemScal<T> elem_scalars(const Tabs<T>& t, int a1, in
   s.sf[0] = (T)0.5 * x2[3] * x3[3] * x1[4];
   s.sf[1] = (T)0.5 * x1[3] * x3[3] * x2[4];
   s.sf[2] = (T)0.5 * x1[3] * x2[3] * x3[4];
+  s.al[0] = x1[4];
+  s.al[1] = x2[4];
+  s.al[2] = x3[4];
   s.e[0] = x1[2];
   s.e[1] = x2[2];
   s.e[2] = x3[2];
@@ -322,10 +326,9 @@ __device__ __forceinline__ void faces_reduce(int m, int ne, const T* a0, const T
   }
 }
 
-// The Schur kernels' reduction order, shared by the fused and the split forms
-// so that both give bitwise the same result: faces 0..3 (sums over k1 or k2 at
-// fixed k3) as in faces_reduce; faces 4, 5 (sums over k3) in slabs of
-// schur_slab(m) k3-values, one chain per slab, slabs added in order.
+// The Schur kernel's reduction order: faces 0..3 (sums over k1 or k2 at fixed
+// k3) as in faces_reduce; faces 4, 5 (sums over k3) in slabs of schur_slab(m)
+// k3-values, one chain per slab, slabs added in order (shorter dependent chains).
 __host__ __device__ __forceinline__ int schur_slab(int m) { return m > 31 ? 4 : 8; }
 
 // Faces 0..3 at the k3 rows [r0, r1) of the eigenspace slab W (rows r0..r1-1
@@ -400,9 +403,14 @@ __device__ __forceinline__ void elem_coords(const Geo& G, int64_t e, int* a1, in
 // y_e = H_BI H_II^{-1} H_IB u on the six faces of every element -> Z[e][f][.]
 // Work regions: 0 tables (Sh, a0, Lam), 1 X (6 m^2), 2 Tt (6 m^2), 3 W (m^3).
 // PC > 0 compiles the kernel for degree PC (constant extents); PC = 0 reads it from G.
+// pre = 1: u holds every face already in the eigenbasis, c_f Sh^T U_f Sh (the
+// transform is the same for the two elements sharing the face, so it is done
+// once per face), and Z receives the element's face terms in that basis,
+// alpha_d (X_even +- X_odd), for one back transform per face after the two
+// elements' terms are summed.
 template <typename T, int PC, int NB>
 __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const T* __restrict__ u,
-                                                         T* __restrict__ Z, T* ws, WsPlan wp) {
+                                                         T* __restrict__ Z, T* ws, WsPlan wp, int pre) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = PC ? PC - 1 : G.m, mm = m * m;
   const int64_t n3 = (int64_t)mm * m;
@@ -426,16 +434,27 @@ __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const 
       X[idx] = u[elem_face_base(G, a1, a2, a3, f) + (idx - f * mm)];
     }
     __syncthreads();
-    face_pairs(mm, X);
-    __syncthreads();
-    faces_forward(F, Sh, X, Tt, sc);
+    if (pre) {
+      // pair sums / differences of the transformed faces, scaled by alpha_d
+      for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
+        const int d = idx / mm, r = idx - d * mm;
+        const T a = X[(2 * d) * mm + r], b = X[(2 * d + 1) * mm + r];
+        X[(2 * d) * mm + r] = sc.al[d] * (a + b);
+        X[(2 * d + 1) * mm + r] = sc.al[d] * (a - b);
+      }
+      __syncthreads();
+    } else {
+      face_pairs(mm, X);
+      __syncthreads();
+      faces_forward(F, Sh, X, Tt, sc);
+    }
     for (int64_t idx = threadIdx.x; idx < n3; idx += blockDim.x) {
       const int k1 = (int)(idx % m), k2 = (int)((idx / m) % m), k3 = (int)(idx / mm);
       W[idx] = face_expand(m, ne, a0, X, k1, k2, k3) * inv_d(t, sc, lI, lam, idx, k1, k2, k3, n3);
     }
     __syncthreads();
     faces_reduce_rows(m, ne, a0, W, 0, m, X);
-    // faces 4, 5: slab partials in order (schur_slab(m) k3-rows each), as the split form sums them
+    // faces 4, 5: slab partials in order (schur_slab(m) k3-rows each)
     const int slab = schur_slab(m);
     for (int idx = threadIdx.x; idx < 2 * mm; idx += blockDim.x) {
       const int f = idx / mm, r = idx - f * mm;
@@ -451,136 +470,15 @@ __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const 
     }
     __syncthreads();
     T* Ze = Z + e * 6 * mm;
-    faces_backward(F, Sh, X, Tt, sc, [&](int idx, T v) { Ze[idx] = v; });
-  }
-}
-
-// ---------------------------------------------------------------- split Schur form
-// The same Schur term in three launches whose work units are smaller than an
-// element, so that few large elements still fill every SM: (e, axis) units
-// transform one face pair forward, (e, k3-slab) units build one slab of the
-// eigenspace with its face reductions, (e, axis) units transform one pair back.
-// Bitwise the same result as k_elem_schur (same per-output arithmetic and the
-// shared reduction order).  Global arrays (per element): Xf transformed faces
-// (6 m^2), Xr reduced faces 0..3 (4 m^2), Xp slab partials of faces 4, 5
-// (nslab x 2 m^2).
-
-// (e, d): faces 2d, 2d+1 -> pair sum / difference -> forward 2D transform -> Xf[e][2d..2d+1]
-template <typename T, int PC, int NB>
-__global__ void __launch_bounds__(256, 2 * NB) k_schur_fwd(Geo G, Tabs<T> t, const T* __restrict__ u, T* __restrict__ Xf) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = PC ? PC - 1 : G.m, mm = m * m;
-  T* Sh = reinterpret_cast<T*>(smem_raw);
-  T* X = Sh + mm;
-  T* Tt = X + 2 * mm;
-  __shared__ T sc2[2];
-  for (int i = threadIdx.x; i < mm; i += blockDim.x) Sh[i] = t.Sh[i];
-  const Lines F{m, m / 2, (m + 1) / 2, m, m, 2 * mm};
-  for (int64_t unit = blockIdx.x; unit < 3 * G.nelem; unit += gridDim.x) {
-    const int64_t e = unit / 3;
-    const int d = (int)(unit - 3 * e);
-    int a1, a2, a3;
-    elem_coords(G, e, &a1, &a2, &a3);
-    const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
-    __syncthreads();
-    if (threadIdx.x < 2) sc2[threadIdx.x] = sc.sf[d];
-    for (int i = threadIdx.x; i < mm; i += blockDim.x) {
-      const T a = u[elem_face_base(G, a1, a2, a3, 2 * d) + i], b = u[elem_face_base(G, a1, a2, a3, 2 * d + 1) + i];
-      X[i] = a + b;
-      X[mm + i] = a - b;
-    }
-    __syncthreads();
-    fold_lines(F, 0, X, Tt);
-    __syncthreads();
-    tx_lines_g(F, 0, Sh, Tt, X, (T)1, (const T*)nullptr);
-    __syncthreads();
-    fold_lines(F, 1, X, Tt);
-    __syncthreads();
-    T* out = Xf + (e * 6 + 2 * d) * (int64_t)mm;
-    tx_lines_g(F, 1, Sh, Tt, out, (T)1, (const T*)sc2);
-  }
-}
-
-// (e, s): eigenspace rows k3 in slab s -> W -> faces 0..3 rows (complete) and faces 4, 5 partials
-template <typename T, int PC, int NB>
-__global__ void __launch_bounds__(256, 2 * NB) k_schur_eig(Geo G, Tabs<T> t, const T* __restrict__ Xf, T* __restrict__ Xr,
-                                                       T* __restrict__ Xp, int nslab) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = PC ? PC - 1 : G.m, mm = m * m, ne = (m + 1) / 2;
-  const int64_t n3 = (int64_t)mm * m;
-  T* a0 = reinterpret_cast<T*>(smem_raw);
-  T* lI = a0 + m;
-  T* X = lI + m;
-  T* W = X + 6 * mm;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    a0[i] = t.a0[i];
-    lI[i] = t.lamI[i];
-  }
-  const T lam = (T)G.lam;
-  for (int64_t unit = blockIdx.x; unit < (int64_t)nslab * G.nelem; unit += gridDim.x) {
-    const int64_t e = unit / nslab;
-    const int sl = (int)(unit - e * nslab);
-    const int r0 = sl * schur_slab(m), r1 = min(r0 + schur_slab(m), m);
-    int a1, a2, a3;
-    elem_coords(G, e, &a1, &a2, &a3);
-    const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
-    __syncthreads();
-    const T* xf = Xf + e * 6 * (int64_t)mm;
-    for (int i = threadIdx.x; i < 6 * mm; i += blockDim.x) X[i] = xf[i];
-    __syncthreads();
-    for (int i = threadIdx.x; i < (r1 - r0) * mm; i += blockDim.x) {
-      const int64_t idx = (int64_t)r0 * mm + i;
-      const int k1 = (int)(idx % m), k2 = (int)((idx / m) % m), k3 = (int)(idx / mm);
-      W[i] = face_expand(m, ne, a0, X, k1, k2, k3) * inv_d(t, sc, lI, lam, idx, k1, k2, k3, n3);
-    }
-    __syncthreads();
-    faces_reduce_rows(m, ne, a0, W, r0, r1, Xr + e * 4 * (int64_t)mm);
-    faces_reduce_slab45(m, ne, a0, W, r0, r1, Xp + (e * nslab + sl) * 2 * (int64_t)mm);
-  }
-}
-
-// (e, d): faces 2d, 2d+1 reduced (d = 2: slab partials summed in order) -> backward transform -> Z
-template <typename T, int PC, int NB>
-__global__ void __launch_bounds__(256, 2 * NB) k_schur_bwd(Geo G, Tabs<T> t, const T* __restrict__ Xr,
-                                                       const T* __restrict__ Xp, T* __restrict__ Z, int nslab) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = PC ? PC - 1 : G.m, mm = m * m;
-  T* Sh = reinterpret_cast<T*>(smem_raw);
-  T* X = Sh + mm;
-  T* Tt = X + 2 * mm;
-  for (int i = threadIdx.x; i < mm; i += blockDim.x) Sh[i] = t.Sh[i];
-  const Lines F{m, m / 2, (m + 1) / 2, m, m, 2 * mm};
-  for (int64_t unit = blockIdx.x; unit < 3 * G.nelem; unit += gridDim.x) {
-    const int64_t e = unit / 3;
-    const int d = (int)(unit - 3 * e);
-    int a1, a2, a3;
-    elem_coords(G, e, &a1, &a2, &a3);
-    const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
-    __syncthreads();
-    if (d < 2) {
-      const T* xr = Xr + (e * 4 + 2 * d) * (int64_t)mm;
-      for (int i = threadIdx.x; i < 2 * mm; i += blockDim.x) X[i] = xr[i];
-    } else {
-      const T* xp = Xp + e * nslab * 2 * (int64_t)mm;
-      for (int i = threadIdx.x; i < 2 * mm; i += blockDim.x) {
-        T tot = xp[i];
-        for (int sl = 1; sl < nslab; ++sl) tot = tot + xp[(int64_t)sl * 2 * mm + i];
-        X[i] = tot;
+    if (pre) {
+      for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
+        const int d = idx / mm, r = idx - d * mm;
+        const T xe = X[(2 * d) * mm + r], xo = X[(2 * d + 1) * mm + r];
+        Ze[(2 * d) * mm + r] = sc.al[d] * (xe + xo);
+        Ze[(2 * d + 1) * mm + r] = sc.al[d] * (xe - xo);
       }
-    }
-    __syncthreads();
-    txT_lines_g(F, 0, Sh, X, Tt);
-    __syncthreads();
-    unfold_lines(F, 0, Tt, X);
-    __syncthreads();
-    txT_lines_g(F, 1, Sh, X, Tt);
-    __syncthreads();
-    T* Ze = Z + e * 6 * (int64_t)mm;
-    for (int r = threadIdx.x; r < mm; r += blockDim.x) {
-      const T ye = unfold_at(F, 1, Tt, r);
-      const T yo = unfold_at(F, 1, Tt, mm + r);
-      Ze[(2 * d) * mm + r] = sc.sf[d] * (ye + yo);
-      Ze[(2 * d + 1) * mm + r] = sc.sf[d] * (ye - yo);
+    } else {
+      faces_backward(F, Sh, X, Tt, sc, [&](int idx, T v) { Ze[idx] = v; });
     }
   }
 }
@@ -755,33 +653,9 @@ constexpr size_t kSchurSmemCap = 200 * 1024;
 
 }  // namespace
 
-// Shared memory of the split kernels: forward / backward (Sh, a pair, its scratch)
-// and the eigenspace slab kernel (a0, Lam, six faces, one slab).
-inline size_t schur_split_smem_fb(int m, size_t es) { return (size_t)5 * m * m * es; }
-inline size_t schur_split_smem_eig(int m, size_t es) {
-  return ((size_t)2 * m + (size_t)(6 + schur_slab(m)) * m * m) * es;
-}
-
 template <typename T>
-LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap, int block, int wide, int split) {
+LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap, int block, int wide) {
   const size_t m = G.m, mm = m * m;
-  const size_t es = sizeof(T);
-  // the split form (sub-element work units) when asked; the automatic choice is the fused
-  // kernel (measured faster in FP64 on the 8^3 meshes), the autotuner times both
-  const bool fits = m >= 1 && schur_split_smem_eig((int)m, es) <= 200 * 1024;
-  if (split > 0) {
-    LaunchCfg c;
-    const int nslab = ((int)m + schur_slab((int)m) - 1) / schur_slab((int)m);
-    c.depth = nslab;
-    c.block = 256;
-    c.wide = wide >= 0 ? wide : 1;
-    c.smem = schur_split_smem_eig((int)m, es);
-    const int64_t units = (int64_t)nslab * G.nelem;
-    c.grid = (int)(units < (1 << 30) ? units : (1 << 30));
-    c.flat = (size_t)G.nelem * (10 + 2 * (size_t)nslab) * mm;
-    c.ok = fits;
-    return c;
-  }
   LaunchCfg c;
   if (cap == 0) cap = kSchurSmemCap;
   const size_t sizes[4] = {mm + 2 * m, 6 * mm, 6 * mm, mm * m};
@@ -796,73 +670,30 @@ LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap, int block, int wide
 
 template <typename T, int NB>
 void launch_elem_schur_nb(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, const LaunchCfg& c,
-                          cudaStream_t st) {
+                          cudaStream_t st, int pre) {
   switch (G.p) {
-    case 2: k_elem_schur<T, 2, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    case 4: k_elem_schur<T, 4, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    case 8: k_elem_schur<T, 8, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    case 16: k_elem_schur<T, 16, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    case 32: k_elem_schur<T, 32, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-    default: k_elem_schur<T, 0, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws); break;
-  }
-}
-
-template <typename T, int PC, int NB>
-void launch_schur_split_pc(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, const LaunchCfg& c,
-                           cudaStream_t st) {
-  const int m = G.m, nslab = c.depth;
-  const int64_t mm = (int64_t)m * m;
-  T* Xf = ws;
-  T* Xr = Xf + G.nelem * 6 * mm;
-  T* Xp = Xr + G.nelem * 4 * mm;
-  const size_t sfb = schur_split_smem_fb(m, sizeof(T)), seig = schur_split_smem_eig(m, sizeof(T));
-  const int64_t u3 = 3 * G.nelem, us = (int64_t)nslab * G.nelem;
-  const int g3 = (int)(u3 < (1 << 30) ? u3 : (1 << 30)), gs = (int)(us < (1 << 30) ? us : (1 << 30));
-  k_schur_fwd<T, PC, NB><<<g3, 256, sfb, st>>>(G, t, u, Xf);
-  k_schur_eig<T, PC, NB><<<gs, 256, seig, st>>>(G, t, Xf, Xr, Xp, nslab);
-  k_schur_bwd<T, PC, NB><<<g3, 256, sfb, st>>>(G, t, Xr, Xp, Z, nslab);
-}
-
-template <typename T, int NB>
-void launch_schur_split(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, const LaunchCfg& c,
-                        cudaStream_t st) {
-  switch (G.p) {
-    case 16: launch_schur_split_pc<T, 16, NB>(G, t, u, Z, ws, c, st); break;
-    case 32: launch_schur_split_pc<T, 32, NB>(G, t, u, Z, ws, c, st); break;
-    default: launch_schur_split_pc<T, 0, NB>(G, t, u, Z, ws, c, st); break;
+    case 2: k_elem_schur<T, 2, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws, pre); break;
+    case 4: k_elem_schur<T, 4, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws, pre); break;
+    case 8: k_elem_schur<T, 8, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws, pre); break;
+    case 16: k_elem_schur<T, 16, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws, pre); break;
+    case 32: k_elem_schur<T, 32, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws, pre); break;
+    default: k_elem_schur<T, 0, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws, pre); break;
   }
 }
 
 template <typename T>
 void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, const LaunchCfg& c,
-                       cudaStream_t st) {
+                       cudaStream_t st, int pre) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
-  if (c.depth > 0) {
-    if (c.wide)
-      launch_schur_split<T, 1>(G, t, u, Z, ws, c, st);
-    else
-      launch_schur_split<T, 2>(G, t, u, Z, ws, c, st);
-    return;
-  }
   if (c.wide)
-    launch_elem_schur_nb<T, 1>(G, t, u, Z, ws, c, st);
+    launch_elem_schur_nb<T, 1>(G, t, u, Z, ws, c, st, pre);
   else
-    launch_elem_schur_nb<T, 2>(G, t, u, Z, ws, c, st);
-}
-
-template <typename T, int PC, int NB>
-static int schur_split_attrs_pc() {
-  int bad = 0;
-  bad |= cudaFuncSetAttribute(k_schur_fwd<T, PC, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_schur_eig<T, PC, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_schur_bwd<T, PC, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  return bad;
+    launch_elem_schur_nb<T, 2>(G, t, u, Z, ws, c, st, pre);
 }
 
 template <typename T, int NB>
 static int schur_attrs_nb() {
-  int bad = schur_split_attrs_pc<T, 0, NB>() | schur_split_attrs_pc<T, 16, NB>() | schur_split_attrs_pc<T, 32, NB>();
-  bad |= cudaFuncSetAttribute(k_elem_schur<T, 0, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  int bad = cudaFuncSetAttribute(k_elem_schur<T, 0, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_schur<T, 2, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_schur<T, 4, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_schur<T, 8, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -3,9 +3,9 @@
 
 namespace semmg {
 
-template LaunchCfg plan_elem_schur<float>(const Geo&, int, size_t, int, int, int);
+template LaunchCfg plan_elem_schur<float>(const Geo&, int, size_t, int, int);
 template void launch_elem_schur<float>(const Geo&, const Tabs<float>&, const float*, float*, float*,
-                                       const LaunchCfg&, cudaStream_t);
+                                       const LaunchCfg&, cudaStream_t, int);
 
 int set_elem_smem_limits_f32() { return schur_attrs<float>(); }
 

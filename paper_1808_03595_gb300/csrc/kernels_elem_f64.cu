@@ -43,9 +43,9 @@ void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f, c
   }
 }
 
-template LaunchCfg plan_elem_schur<double>(const Geo&, int, size_t, int, int, int);
+template LaunchCfg plan_elem_schur<double>(const Geo&, int, size_t, int, int);
 template void launch_elem_schur<double>(const Geo&, const Tabs<double>&, const double*, double*, double*,
-                                        const LaunchCfg&, cudaStream_t);
+                                        const LaunchCfg&, cudaStream_t, int);
 
 int set_elem_smem_limits_f32();
 int set_elem_smem_limits() {

@@ -297,12 +297,9 @@ struct LaunchCfg {
   // register budget of the kernel build: 0 = at most 64 registers per thread
   // (1024 resident threads per SM), 1 = at most 128 (512 resident threads)
   int wide = 0;
-  int depth = 0;                 // element-block kernel: k3-planes of the eigenspace slab;
-                                 // Schur term: k3-slabs of the split form (0: one fused kernel)
-  size_t flat = 0;               // work elements of a form whose buffers are not per CTA
+  int depth = 0;                 // element-block kernel: k3-planes of the eigenspace slab
   size_t ws_elems() const {
-    const size_t per_cta = (size_t)ws.gstride * (size_t)grid;
-    return per_cta > flat ? per_cta : flat;
+    return (size_t)ws.gstride * (size_t)grid;
   }
 };
 
@@ -372,12 +369,26 @@ inline int resident_blocks(LaunchCfg& c, int wide) {
   return bps < 1 ? 1 : bps;
 }
 
-// split: -1 automatic (the fused kernel), 0 the fused kernel with the launch shape given,
-// 1 the split form (sub-element work units; the autotuner times it against the fused one)
 template <typename T> LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap = 0, int block = 0,
-                                                int wide = -1, int split = -1);
+                                                int wide = -1);
+// pre = 1 (fused form only): u holds the faces transformed by launch_face_fwd and Z
+// receives the element terms in the face eigenbasis, for launch_face_bwd_assemble
 template <typename T> void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws,
-                                             const LaunchCfg& c, cudaStream_t st);
+                                             const LaunchCfg& c, cudaStream_t st, int pre = 0);
+// Face-parallel form of the condensed operator (kernels_face.cu), for levels
+// with face interiors (m >= 1):
+//   launch_face_fwd: Ut[s] = c_f (Sh^T U_f Sh) on every face f (slots of the
+//     face groups, same indexing as u; Ut holds at least G.oE1 values);
+//   launch_face_bwd_assemble: per face, the two elements' eigenbasis terms
+//     and the face part of H_BB u (from Ut) combined and transformed back once,
+//     then out = F - Hhat u (mode 0) or Hhat u (mode 1) on the face slots;
+//     edges and vertices as launch_assemble.
+template <typename T> void launch_face_fwd(const Geo& G, const Tabs<T>& t, const T* u, T* Ut, cudaStream_t st);
+template <typename T, typename TF>
+void launch_face_bwd_assemble(const Geo& G, const Tabs<T>& t, const TF* F, const T* u, const T* Ut, const T* Zh,
+                              TF* out, int mode, cudaStream_t st);
+int set_face_smem_limits();
+size_t face_smem_bytes(int p);
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm);
 // Gsave (optional): scaled interior eigen-coefficients D^{-1} S^T F_I per element, m^3 each
 void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f_nodal, double* Z, double* Gsave,

@@ -63,7 +63,8 @@ def to_nodal(c, level, hat):
 @pytest.mark.parametrize("mesh_name,bc,p,lam", [("stretched_3x2x2", "mixed", 4, 0.0), ("uniform_3", "neumann", 5, 1.0),
                                                 ("thin_2x1x2", "alt", 8, 2.0), ("uniform_3", "mixed", 16, 0.5),
                                                 ("stretched_3x2x2", "per", 4, 0.0), ("uniform_3", "perall", 8, 1.0),
-                                                ("uniform_3", "perd", 16, 0.0)])
+                                                ("uniform_3", "perd", 16, 0.0), ("uniform_3", "perall", 12, 1.0),
+                                                ("thin_2x1x2", "alt", 13, 2.0), ("stretched_3x2x2", "per", 14, 0.0)])
 def test_apply_condensed_and_pack(mesh_name, bc, p, lam):
     h = MESHES[mesh_name]
     m = dense.Mesh(h, p, lam, BCS[bc])
