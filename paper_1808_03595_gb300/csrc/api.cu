@@ -218,9 +218,87 @@ const unsigned char* upload_u8(semmg_ctx* c, const std::vector<unsigned char>& v
   return d;
 }
 
+// The face records of a face-parallel level (FaceRec), in face order.
 template <typename T>
-Tabs<T> upload_tabs(semmg_ctx* c, const HostLevel& H, const std::vector<double>* h, bool* ok) {
+std::vector<FaceRec<T>> build_face_recs(const Geo& G, const HostLevel& H, const std::vector<double>* h) {
+  const int p = G.p, P1 = p + 1;
+  const int64_t mm = (int64_t)G.m * G.m;
+  const int nd[3] = {G.n1, G.n2, G.n3}, nv[3] = {G.nv1, G.nv2, G.nv3};
+  std::vector<FaceRec<T>> out;
+  out.reserve((size_t)((G.oE1 - G.oF1) / mm));
+  for (int d = 0; d < 3; ++d) {
+    const int ia = d == 0 ? 1 : 0, ib = d == 2 ? 1 : 2;
+    // slot order of the group: F1 [a3][a2][c1], F2 [a3][c2][a1], F3 [c3][a2][a1]
+    int ext[3];
+    for (int e = 0; e < 3; ++e) ext[e] = e == d ? nv[e] : nd[e];
+    for (int i2 = 0; i2 < ext[2]; ++i2)
+      for (int i1 = 0; i1 < ext[1]; ++i1)
+        for (int i0 = 0; i0 < ext[0]; ++i0) {
+          int a[3] = {i0, i1, i2};
+          const int c = a[d];
+          FaceRec<T> r{};
+          const int64_t f = (int64_t)out.size() - (d == 0 ? 0 : (d == 1 ? (G.oF2 - G.oF1) / mm : (G.oF3 - G.oF1) / mm));
+          r.base = (d == 0 ? G.oF1 : (d == 1 ? G.oF2 : G.oF3)) + f * mm;
+          r.dir = dir_plane(G, d, c);
+          const bool hasL = c > 0 || G.per[d], hasR = c < nd[d];
+          const int eL = hasL ? wrape(G, d, c - 1) : 0;
+          r.zm = r.zp = r.nbL = r.nbR = -1;
+          if (hasL) {
+            int e[3] = {a[0], a[1], a[2]};
+            e[d] = eL;
+            r.zm = ((((int64_t)e[2] * G.n2 + e[1]) * G.n1 + e[0]) * 6 + 2 * d + 1) * mm;
+          }
+          if (hasR) r.zp = ((((int64_t)a[2] * G.n2 + a[1]) * G.n1 + a[0]) * 6 + 2 * d) * mm;
+          const double ha = h[ia][a[ia]], hb = h[ib][a[ib]];
+          const double cA = 0.5 * ha, cB = 0.5 * hb, kA = 2.0 / ha, kB = 2.0 / hb;
+          const double kL = hasL ? 2.0 / h[d][eL] : 0.0, kR = hasR ? 2.0 / h[d][c] : 0.0;
+          double Md = 0.0;
+          if (hasL) Md += 0.5 * h[d][eL] * H.w[p];
+          if (hasR) Md += 0.5 * h[d][c] * H.w[0];
+          const double cd0 = kL * H.Ls[(size_t)p * P1 + p] + kR * H.Ls[0];
+          const double cf = 0.5 * std::sqrt(ha) * std::sqrt(hb);
+          r.cf = (T)cf;
+          r.e0 = (T)(cf * (G.lam * Md + cd0));
+          r.ea = (T)(Md * cB * kA / cf);
+          r.eb = (T)(Md * cA * kB / cf);
+          r.cdL = (T)(kL * H.Ls[(size_t)p * P1]);
+          r.cdR = (T)(kR * H.Ls[p]);
+          r.edA = (T)(Md * cB * kA);
+          r.edB = (T)(Md * cA * kB);
+          int g[3];
+          g[d] = c * p;
+          g[ia] = a[ia] * p;
+          g[ib] = a[ib] * p + 1;
+          r.eA0 = skel_index(G, g[0], g[1], g[2]);
+          g[ia] = a[ia] * p + p;
+          r.eAp = skel_index(G, g[0], g[1], g[2]);
+          g[ia] = a[ia] * p + 1;
+          g[ib] = a[ib] * p;
+          r.eB0 = skel_index(G, g[0], g[1], g[2]);
+          g[ib] = a[ib] * p + p;
+          r.eBp = skel_index(G, g[0], g[1], g[2]);
+          g[ib] = a[ib] * p + 1;
+          g[d] = (c - 1) * p;  // wraps on a periodic axis
+          if (hasL) r.nbL = skel_index(G, g[0], g[1], g[2]);
+          g[d] = (c + 1) * p;
+          if (hasR) r.nbR = skel_index(G, g[0], g[1], g[2]);
+          out.push_back(r);
+        }
+  }
+  return out;
+}
+
+template <typename T>
+Tabs<T> upload_tabs(semmg_ctx* c, const Geo& G, const HostLevel& H, const std::vector<double>* h, bool* ok) {
   Tabs<T> t{};
+  t.faces = nullptr;
+  if (face_form(G)) {
+    const std::vector<FaceRec<T>> fr = build_face_recs<T>(G, H, h);
+    void* d = dalloc(c, fr.size() * sizeof(FaceRec<T>));
+    if (!d || cudaMemcpy(d, fr.data(), fr.size() * sizeof(FaceRec<T>), cudaMemcpyHostToDevice) != cudaSuccess)
+      *ok = false;
+    t.faces = (const FaceRec<T>*)d;
+  }
   t.w = upload<T>(c, H.w, ok);
   t.Ls = upload<T>(c, H.Ls, ok);
   t.Sh = upload<T>(c, H.Sh, ok);
@@ -398,12 +476,6 @@ bool cycle32(const semmg_ctx* c) { return c->opts.precision != SEMMG_FP64; }
 bool resid64(const semmg_ctx* c) {
   return c->opts.precision == SEMMG_MIXED || c->opts.precision == SEMMG_MIXED_TC;
 }
-
-// Whether level G runs the face-parallel form of the operator (the face
-// transforms once per face, launch_face_fwd / launch_face_bwd_assemble): from
-// p = 12 on, where the saved element work outweighs the extra launch (at p = 8
-// the element-face form is faster on GB300).
-bool face_form(const Geo& G) { return G.m >= 11; }
 
 // out = F - Hhat u (mode 0) or Hhat u (mode 1) on level l with arithmetic in T
 // (u, Schur terms) and F, out of type TF; cfg: the Schur kernel's launch shape.
@@ -839,8 +911,8 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   build_coarse_tables(degs[0], c->h, mesh->bc, c->hc);
   bool ok = true;
   for (int l = 0; l < nl; ++l) {
-    c->dl[l].td = upload_tabs<double>(c.get(), c->hl[l], c->h, &ok);
-    c->dl[l].tf = upload_tabs<float>(c.get(), c->hl[l], c->h, &ok);
+    c->dl[l].td = upload_tabs<double>(c.get(), c->geo[l], c->hl[l], c->h, &ok);
+    c->dl[l].tf = upload_tabs<float>(c.get(), c->geo[l], c->hl[l], c->h, &ok);
   }
   for (int d = 0; d < 3; ++d) {
     c->ct.K[d] = c->hc.K[d];

@@ -224,6 +224,30 @@ SEMMG_HD int64_t elem_face_base(const Geo& G, int a1, int a2, int a3, int f) {
 }
 
 // ---------------------------------------------------------------- tables
+// One face of the face groups (F1, F2, F3 in slot order) for the face-parallel
+// form of the operator (kernels_face.cu), built on the host at setup.  The face
+// has normal axis d and in-plane axes a (fast) and b (slow); Md is the
+// assembled normal mass on its plane, cd0 / cdL / cdR the normal stiffness
+// line sum (cd0 u + cdL u(plane below) + cdR u(plane above)).
+template <typename T>
+struct FaceRec {
+  int64_t base;                // slot of the face's first node
+  int64_t zm, zp;              // Z offsets of the face as side 2d+1 of the element below / 2d of the one above, or -1
+  int64_t eA0, eAp, eB0, eBp;  // first slots of the edges at q_a = 0, q_a = p, q_b = 0, q_b = p
+  int64_t nbL, nbR;            // first slots of the parallel faces on the planes below / above, or -1
+  int dir;                     // no unknowns (Dirichlet plane or periodic image plane)
+  int pad;
+  T cf;                        // sqrt(h_a h_b) / 2
+  T e0, ea, eb;                // face part of H_BB in the face eigenbasis / c_f: e0 + ea Lam[k_a] + eb Lam[k_b]
+  T cdL, cdR;
+  T edA, edB;                  // edge couplings: Md (h_b/2)(2/h_a), Md (h_a/2)(2/h_b)
+};
+
+// Levels that run the face-parallel form of the operator: from p = 12 on, where
+// the saved element work outweighs the extra launch (at p = 8 the element-face
+// form is faster on GB300).
+inline bool face_form(const Geo& G) { return G.m >= 11; }
+
 // Device tables of one level in one precision.
 template <typename T>
 struct Tabs {
@@ -266,6 +290,7 @@ struct Tabs {
   const int* ebCls[3];   // line class of every block line
   int ebNcls[3];
   const T* ebR;          // per class triple: nE^3 values 1/(lam + Lam1 + Lam2 + Lam3) [k3][k2][k1], or null
+  const FaceRec<T>* faces;  // face-parallel operator levels (face_form), else null
 };
 
 // Coarse fast-diagonalisation tables (level 0, FP64): K_d = n_d p0 - 1
@@ -388,7 +413,6 @@ template <typename T, typename TF>
 void launch_face_bwd_assemble(const Geo& G, const Tabs<T>& t, const TF* F, const T* u, const T* Ut, const T* Zh,
                               TF* out, int mode, cudaStream_t st);
 int set_face_smem_limits();
-size_t face_smem_bytes(int p);
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm);
 // Gsave (optional): scaled interior eigen-coefficients D^{-1} S^T F_I per element, m^3 each
 void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f_nodal, double* Z, double* Gsave,
