@@ -73,21 +73,37 @@ __global__ void __launch_bounds__(kFaceThreads) k_face_fwd(Geo G, Tabs<T> t, con
 // and the edge couplings are added node by node:
 //   Md ((h_b/2) w_{q_b} (2/h_a) (Ls[q_a][0] U(0, q_b) + Ls[q_a][p] U(p, q_b)) + (a <-> b)).
 
-// Edge and vertex slots (no Schur term): one slot per thread.
+// Edge and vertex slots (no Schur term).  Their H_BB rows are three line sums
+// of about 2p terms each, so three threads share a slot (one axis each) and
+// the block combines them: kEdgeSlots slots per block.
+constexpr int kEdgeSlots = 64;
+
 template <typename T, typename TF>
-__global__ void __launch_bounds__(kFaceThreads) k_edge_assemble(Geo G, Tabs<T> t, const TF* __restrict__ F,
-                                                               const T* __restrict__ u, TF* __restrict__ out,
-                                                               int mode) {
-  const int64_t s = G.oE1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= G.size) return;
+__global__ void __launch_bounds__(3 * kEdgeSlots) k_edge_assemble(Geo G, Tabs<T> t, const TF* __restrict__ F,
+                                                                 const T* __restrict__ u, TF* __restrict__ out,
+                                                                 int mode) {
+  __shared__ T Ms[3][kEdgeSlots], Lsum[3][kEdgeSlots];
+  const int d = threadIdx.x / kEdgeSlots, k = threadIdx.x - d * kEdgeSlots;
+  const int64_t s = G.oE1 + (int64_t)blockIdx.x * kEdgeSlots + k;
   int g[3];
-  bool bd;
-  const int type = skel_decode(G, s, g, &bd);
+  bool bd = true;
+  int type = 0;
+  if (s < G.size) type = skel_decode(G, s, g, &bd);
+  if (!bd) {
+    const int nd[3] = {G.n1, G.n2, G.n3};
+    bool on[3];
+    for (int e = 0; e < 3; ++e) on[e] = (g[e] - divp(G, g[e]) * G.p) == 0;
+    Ms[d][k] = mass1d(G, t, d, g[d], nd[d]);
+    Lsum[d][k] = line_sum(G, t, u, s, type, g, d, on[(d + 1) % 3] || on[(d + 2) % 3]);
+  }
+  __syncthreads();
+  if (d != 0 || s >= G.size) return;
   if (bd) {
     out[s] = 0;
     return;
   }
-  const T Hu = node_hbb(G, t, u, s, type, g);
+  const T M0 = Ms[0][k], M1 = Ms[1][k], M2 = Ms[2][k];
+  const T Hu = (T)G.lam * M0 * M1 * M2 * u[s] + M1 * M2 * Lsum[0][k] + M0 * M2 * Lsum[1][k] + M0 * M1 * Lsum[2][k];
   out[s] = (TF)(mode == 0 ? (T)F[s] - Hu : Hu);
 }
 
@@ -191,10 +207,10 @@ void face_bwd_pc(const Geo& G, const Tabs<T>& t, const TF* F, const T* u, const 
   const int64_t nF = face_count(G);
   const int nfb = face_nfb(G.m);
   const int64_t fblocks = (nF + nfb - 1) / nfb;
-  const int64_t eblocks = (G.size - G.oE1 + kFaceThreads - 1) / kFaceThreads;
+  const int64_t eblocks = (G.size - G.oE1 + kEdgeSlots - 1) / kEdgeSlots;
   k_face_bwd<T, TF, PC><<<(unsigned)fblocks, kFaceThreads, face_bwd_smem<T>(G.m, nfb), st>>>(G, t, F, u, Ut, Zh, out,
                                                                                             mode, nfb, nF);
-  if (eblocks > 0) k_edge_assemble<T, TF><<<(unsigned)eblocks, kFaceThreads, 0, st>>>(G, t, F, u, out, mode);
+  if (eblocks > 0) k_edge_assemble<T, TF><<<(unsigned)eblocks, 3 * kEdgeSlots, 0, st>>>(G, t, F, u, out, mode);
 }
 
 template <typename T, typename TF, int PC>
