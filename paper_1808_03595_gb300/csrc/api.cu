@@ -152,10 +152,23 @@ struct semmg_ctx {
   std::vector<Pending> pending;
   int ev_used = 0;
   semmg_kstat ks[SEMMG_K_COUNT] = {};
+  // one outer iteration captured as a CUDA graph (replayed by semmg_solve while
+  // timing is off); rebuilt after launch shapes change
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  int step_capture_failed = 0;
 
   int L() const { return (int)geo.size() - 1; }
 
+  void drop_step_graph() {
+    if (step_exec) cudaGraphExecDestroy(step_exec);
+    step_exec = nullptr;
+    step_capture_failed = 0;
+  }
+
   ~semmg_ctx() {
+    drop_step_graph();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (cudaEvent_t e : events) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
     if (hnorm) cudaFreeHost(hnorm);
@@ -756,6 +769,35 @@ void iter_step(semmg_ctx* c, cudaStream_t st) {
   t.toc(8.0 * n, 8.0 * n * 9, 4);
 }
 
+// One outer iteration on stream st: replayed from a CUDA graph captured on the
+// context's own stream at the first call (one launch instead of one per kernel,
+// which is what the low-degree levels are bound by); launched kernel by kernel
+// while timing is on or if the capture failed.
+void run_step(semmg_ctx* c, cudaStream_t st) {
+  if (c->timing) {
+    iter_step(c, st);
+    return;
+  }
+  if (!c->step_exec && !c->step_capture_failed) {
+    bool ok = c->cap_stream || cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    cudaGraph_t g = nullptr;
+    if (ok && cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      iter_step(c, c->cap_stream);
+      ok = cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess && g;
+      if (ok && cudaGraphInstantiate(&c->step_exec, g, 0) != cudaSuccess) c->step_exec = nullptr;
+      if (g) cudaGraphDestroy(g);
+    }
+    if (!c->step_exec) {
+      cudaGetLastError();
+      c->step_capture_failed = 1;
+    }
+  }
+  if (c->step_exec)
+    cudaGraphLaunch(c->step_exec, st);
+  else
+    iter_step(c, st);
+}
+
 // sqrt of the squared norm left in dnorm by the last iteration (one 8-byte copy + sync)
 int dnorm_sync(semmg_ctx* c, cudaStream_t st, double* out) {
   cudaMemcpyAsync(c->hnorm, c->dnorm, sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -1185,7 +1227,7 @@ int solve_impl(semmg_ctx* c, const double* f, const double* g, double* u, double
   if (!std::isfinite(r0)) status = SEMMG_ERR_NONFINITE;
   rn = r0;
   while (status == SEMMG_OK && rn > rtol * r0 && it < c->opts.max_iter) {
-    iter_step(c, st);
+    run_step(c, st);
     rc = dnorm_sync(c, st, &rn);
     if (rc) return rc;
     ++it;
@@ -1611,6 +1653,7 @@ void tune_one(semmg_ctx* c, int l, int kernel, LaunchCfg& slot, const T* in, T* 
 extern "C" int semmg_autotune(semmg_ctx* c, void* stream) {
   if (!c) return SEMMG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  c->drop_step_graph();
   collect_timing(c);
   const int saved = c->timing;
   c->timing = 0;
@@ -1663,6 +1706,7 @@ extern "C" int semmg_set_launch(semmg_ctx* c, int level, int kernel, int dtype, 
     return fail(c, SEMMG_ERR_UNSUPPORTED, "set_launch: shape does not fit the work memory of the context");
   LaunchCfg& slot = kernel == 0 ? (dtype == SEMMG_F64 ? D.star64 : D.star32) : (dtype == SEMMG_F64 ? D.schur64 : D.schur32);
   slot = cf;
+  c->drop_step_graph();
   return SEMMG_OK;
 }
 

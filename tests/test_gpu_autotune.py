@@ -83,3 +83,24 @@ def test_every_launch_shape_is_bitwise_identical(p):
                             assert np.array_equal(out, ref), (kern, precision, cap, block, regs, diff)
                             tried += 1
             assert tried >= 8
+
+
+@pytest.mark.parametrize("p,precision,solver", [(4, "fp64", "mg"), (8, "mixed", "kmg"), (16, "mixed_fp32", "mg")])
+def test_graph_replayed_iterations_match_direct_launches(p, precision, solver):
+    # with timing off the outer iteration is replayed from a captured CUDA graph;
+    # with timing on it is launched kernel by kernel: bitwise the same solve
+    from paper_1808_03595_gb300 import Context
+    h = workloads.uniform_widths(3)
+    f = torch.as_tensor(workloads.random_nodal(h, p, 34, "uniform"), device="cuda")
+    out = []
+    for timing in (False, True, False):
+        with Context(h, p, 1.0, p0=2, precision=precision, solver=solver) as c:
+            c.set_timing(timing)
+            u1, i1 = c.solve(f)
+            u1 = u1.clone()
+            u2, i2 = c.solve(f)  # second solve: the graph captured by the first is replayed
+            assert torch.equal(u1, u2) and i1.iters == i2.iters
+            out.append((u2.cpu().numpy(), i2.iters))
+    (a, ia), (b, ib), (d, idd) = out
+    assert ia == ib == idd
+    assert np.array_equal(a, b) and np.array_equal(a, d)
