@@ -157,6 +157,13 @@ struct semmg_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t step_exec = nullptr;
   int step_capture_failed = 0;
+  // per-kernel timing inside that graph: its own events (recorded by event nodes) and
+  // launch groups, read after every replay
+  bool capturing = false;
+  std::vector<cudaEvent_t> step_events;
+  std::vector<Pending> step_pending;
+  int step_ev_used = 0;
+  bool step_replayed = false;
 
   int L() const { return (int)geo.size() - 1; }
 
@@ -164,11 +171,14 @@ struct semmg_ctx {
     if (step_exec) cudaGraphExecDestroy(step_exec);
     step_exec = nullptr;
     step_capture_failed = 0;
+    step_pending.clear();
+    step_replayed = false;
   }
 
   ~semmg_ctx() {
     drop_step_graph();
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (cudaEvent_t e : step_events) cudaEventDestroy(e);
     for (cudaEvent_t e : events) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
     if (hnorm) cudaFreeHost(hnorm);
@@ -435,16 +445,27 @@ namespace {
 bool valid_level(const semmg_ctx* c, int level) { return c && level >= 0 && level <= c->L(); }
 
 // ---- timing: an event pair around each launch group of one kernel class
+// Next timing event: from the context's pool, or, while the outer iteration is
+// being captured, from the pool of its graph.
 int ev_get(semmg_ctx* c) {
-  if (c->ev_used == (int)c->events.size()) {
+  std::vector<cudaEvent_t>& pool = c->capturing ? c->step_events : c->events;
+  int& used = c->capturing ? c->step_ev_used : c->ev_used;
+  if (used == (int)pool.size()) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) {
       cudaGetLastError();
       return -1;
     }
-    c->events.push_back(e);
+    pool.push_back(e);
   }
-  return c->ev_used++;
+  return used++;
+}
+
+void ev_record(semmg_ctx* c, int ev, cudaStream_t st) {
+  if (c->capturing)
+    cudaEventRecordWithFlags(c->step_events[ev], st, cudaEventRecordExternal);  // an event node of the graph
+  else
+    cudaEventRecord(c->events[ev], st);
 }
 
 struct Tic {
@@ -455,19 +476,37 @@ struct Tic {
   Tic(semmg_ctx* c_, int kind_, cudaStream_t st_) : c(c_), kind(kind_), st(st_) {
     if (c->timing) {
       ev = ev_get(c);
-      if (ev >= 0) cudaEventRecord(c->events[ev], st);
+      if (ev >= 0) ev_record(c, ev, st);
     }
   }
   void toc(double flops, double bytes, int64_t launches = 1) {
     if (!c->timing || ev < 0) return;
     const int e1 = ev_get(c);
     if (e1 < 0) return;
-    cudaEventRecord(c->events[e1], st);
-    c->pending.push_back({kind, ev, flops, bytes, launches});
+    ev_record(c, e1, st);
+    (c->capturing ? c->step_pending : c->pending).push_back({kind, ev, flops, bytes, launches});
   }
 };
 
+// the launch groups of the last replay of the captured outer iteration
+void collect_step_timing(semmg_ctx* c) {
+  if (!c->step_replayed) return;
+  c->step_replayed = false;
+  if (c->step_pending.empty()) return;
+  cudaEventSynchronize(c->step_events[c->step_ev_used - 1]);
+  for (const auto& p : c->step_pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->step_events[p.ev], c->step_events[p.ev + 1]);
+    semmg_kstat& k = c->ks[p.kind];
+    k.ms += ms;
+    k.launches += p.launches;
+    k.flops += p.flops;
+    k.bytes += p.bytes;
+  }
+}
+
 void collect_timing(semmg_ctx* c) {
+  collect_step_timing(c);
   if (c->pending.empty()) return;
   cudaEventSynchronize(c->events[c->ev_used - 1]);
   for (const auto& p : c->pending) {
@@ -774,15 +813,16 @@ void iter_step(semmg_ctx* c, cudaStream_t st) {
 // which is what the low-degree levels are bound by); launched kernel by kernel
 // while timing is on or if the capture failed.
 void run_step(semmg_ctx* c, cudaStream_t st) {
-  if (c->timing) {
-    iter_step(c, st);
-    return;
-  }
+  collect_step_timing(c);  // the previous replay's events are reused
   if (!c->step_exec && !c->step_capture_failed) {
     bool ok = c->cap_stream || cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     cudaGraph_t g = nullptr;
+    c->step_pending.clear();
+    c->step_ev_used = 0;
     if (ok && cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      c->capturing = true;
       iter_step(c, c->cap_stream);
+      c->capturing = false;
       ok = cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess && g;
       if (ok && cudaGraphInstantiate(&c->step_exec, g, 0) != cudaSuccess) c->step_exec = nullptr;
       if (g) cudaGraphDestroy(g);
@@ -790,12 +830,15 @@ void run_step(semmg_ctx* c, cudaStream_t st) {
     if (!c->step_exec) {
       cudaGetLastError();
       c->step_capture_failed = 1;
+      c->step_pending.clear();
     }
   }
-  if (c->step_exec)
+  if (c->step_exec) {
     cudaGraphLaunch(c->step_exec, st);
-  else
+    c->step_replayed = true;
+  } else {
     iter_step(c, st);
+  }
 }
 
 // sqrt of the squared norm left in dnorm by the last iteration (one 8-byte copy + sync)
@@ -1309,6 +1352,7 @@ extern "C" {
 int semmg_set_timing(semmg_ctx* c, int enable) {
   if (!c) return SEMMG_ERR_INVALID_ARG;
   collect_timing(c);
+  if (c->timing != (enable ? 1 : 0)) c->drop_step_graph();  // recaptured with or without event nodes
   c->timing = enable ? 1 : 0;
   for (auto& k : c->ks) k = semmg_kstat{};
   return check_cuda(c, "set_timing");

@@ -104,3 +104,29 @@ def test_graph_replayed_iterations_match_direct_launches(p, precision, solver):
     (a, ia), (b, ib), (d, idd) = out
     assert ia == ib == idd
     assert np.array_equal(a, b) and np.array_equal(a, d)
+
+
+def test_kernel_timing_inside_replayed_iterations():
+    # per-kernel timing stays complete when the iterations run from the captured graph:
+    # the capturing solve and a replaying solve report the same launches and operation
+    # counts per kernel class, with positive times
+    from paper_1808_03595_gb300 import Context
+    h = workloads.uniform_widths(3)
+    p = 8
+    f = torch.as_tensor(workloads.random_nodal(h, p, 35, "uniform"), device="cuda")
+    with Context(h, p, 1.0, p0=2) as c:
+        c.set_timing(True)
+        stats = []
+        for _ in range(3):
+            c.reset_kstats()
+            _, info = c.solve(f)
+            assert info.iters >= 2
+            stats.append(c.kstats())
+    for s in stats[1:]:
+        for k, v in stats[0].items():
+            assert s[k]["launches"] == v["launches"] and s[k]["flops"] == v["flops"], k
+    assert stats[0]["star"]["launches"] > 0
+    for s in stats:
+        for k, v in s.items():
+            if v["launches"] > 0:
+                assert v["ms"] > 0.0, k
