@@ -298,7 +298,7 @@ void semmg_batch_destroy(semmg_batch* batch);
  * Schur kernel is timed within a whole operator application -- on the
  * context's own buffers, and keeps the fastest.  Every shape computes bitwise the same
  * result; only the time changes.  Choices are cached per process by (kernel, element size,
- * degree) and reused by later contexts without timing.  Synchronises the
+ * degree, number of elements) and reused by later contexts without timing.  Synchronises the
  * stream; call it before capturing a batch. */
 int semmg_autotune(semmg_ctx* ctx, void* stream);
 /* Launch shape in use for `kernel` (0 = star smoother, 1 = element Schur

@@ -1621,7 +1621,9 @@ struct TuneChoice {
   int wide;
 };
 std::mutex g_tune_lock;
-std::map<std::tuple<int, int, int>, TuneChoice> g_tune;  // (kernel, element size, degree) -> choice
+// (kernel, element size, degree, elements) -> choice: the best shape depends on how many
+// stars / elements share the SMs, so each mesh size is timed once per process
+std::map<std::tuple<int, int, int, int64_t>, TuneChoice> g_tune;
 
 const size_t kTuneCaps[3] = {48 * 1024, 100 * 1024, 200 * 1024};
 const int kTuneBlocks[2] = {256, 512};
@@ -1657,7 +1659,7 @@ float time_launch(semmg_ctx* c, int l, int kernel, const LaunchCfg& cfg, const T
 template <typename T>
 void tune_one(semmg_ctx* c, int l, int kernel, LaunchCfg& slot, const T* in, T* out, cudaStream_t st) {
   const Geo& G = c->geo[l];
-  const auto key = std::make_tuple(kernel, (int)sizeof(T), G.p);
+  const auto key = std::make_tuple(kernel, (int)sizeof(T), G.p, (int64_t)G.nelem);
   {
     std::lock_guard<std::mutex> g(g_tune_lock);
     auto it = g_tune.find(key);
