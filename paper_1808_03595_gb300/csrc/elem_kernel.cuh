@@ -401,7 +401,7 @@ __device__ __forceinline__ void elem_coords(const Geo& G, int64_t e, int* a1, in
 }
 
 // y_e = H_BI H_II^{-1} H_IB u on the six faces of every element -> Z[e][f][.]
-// Work regions: 0 tables (Sh, a0, Lam), 1 X (6 m^2), 2 Tt (6 m^2), 3 W (m^3).
+// Work regions: 0 tables (Sh, a0, Lam), 1 X (6 m^2), 2 Tt (6 m^2; empty in eigenbasis mode), 3 W (m^3).
 // PC > 0 compiles the kernel for degree PC (constant extents); PC = 0 reads it from G.
 // pre = 1: u holds every face already in the eigenbasis, c_f Sh^T U_f Sh (the
 // transform is the same for the two elements sharing the face, so it is done
@@ -658,7 +658,9 @@ LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap, int block, int wide
   const size_t m = G.m, mm = m * m;
   LaunchCfg c;
   if (cap == 0) cap = kSchurSmemCap;
-  const size_t sizes[4] = {mm + 2 * m, 6 * mm, 6 * mm, mm * m};
+  // levels of the face-parallel form run the kernel in eigenbasis mode, which has no
+  // face transforms and so no transform scratch (region 2)
+  const size_t sizes[4] = {mm + 2 * m, 6 * mm, face_form(G) ? 0 : 6 * mm, mm * m};
   c.ws = plan_regions(sizes, 4, sizeof(T), cap, &c.smem);
   c.ok = plan_ok(c.ws, sizes, 4, sizeof(T), c.smem);
   c.block = block ? block : (c.smem > 100 * 1024 ? 512 : 256);
