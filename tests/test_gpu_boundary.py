@@ -166,12 +166,14 @@ def test_coarse_solve_and_vcycle(mesh_name, bc, p0, lam):
     assert rel(got[mask], ref[mask]) < 1e-11
 
 
-@pytest.mark.parametrize("bc,kind,solver,precision", [(NEUMANN, "ccc", "mg", "fp64"), (NEUMANN, "ccc", "kmg", "mixed"),
-                                                      (("D", "D", "N", "N", "N", "N"), "scc", "mg", "mixed"),
-                                                      (("N", "D", "N", "D", "D", "N"), "mixed", "kmg", "fp64")])
-def test_solve_manufactured(bc, kind, solver, precision):
-    # solutions with zero normal derivative on the Neumann faces (see the oracle pins)
-    p = 8
+@pytest.mark.parametrize("bc,kind,solver,precision,p", [(NEUMANN, "ccc", "mg", "fp64", 8), (NEUMANN, "ccc", "kmg", "mixed", 8),
+                                                        (("D", "D", "N", "N", "N", "N"), "scc", "mg", "mixed", 8),
+                                                        (("N", "D", "N", "D", "D", "N"), "mixed", "kmg", "fp64", 8),
+                                                        (NEUMANN, "ccc", "kmg", "fp64", 12),
+                                                        (("N", "D", "N", "D", "D", "N"), "mixed", "mg", "mixed_fp32", 13)])
+def test_solve_manufactured(bc, kind, solver, precision, p):
+    # solutions with zero normal derivative on the Neumann faces (see the oracle pins);
+    # p >= 12 runs the face-parallel operator
     h = workloads.uniform_widths(3)
     m = dense.Mesh(h, p, 1.0, bc)
     x = workloads.node_coords(h, p)
