@@ -236,7 +236,11 @@ int semmg_recover(semmg_ctx* ctx, const double* f_nodal, const double* u_hat, do
  * SEMMG_ERR_NOT_CONVERGED after max_iter iterations (u_nodal still holds the
  * last iterate), SEMMG_ERR_NONFINITE on a NaN/Inf residual norm,
  * SEMMG_ERR_DIVERGED as soon as ||r|| > 1e3 ||r_0|| (the iteration is not
- * contracting: a wrong operator, data or option, not a slow start). */
+ * contracting: a wrong operator, data or option, not a slow start).
+ * Each iteration runs as one CUDA graph launch on `stream`: the first call
+ * captures it on a stream the context owns (re-captured after semmg_autotune,
+ * semmg_set_launch or a change of semmg_set_timing); results are bitwise those
+ * of launching the kernels one by one. */
 int semmg_solve(semmg_ctx* ctx, const double* f_nodal, double* u_nodal, double rtol,
                 semmg_info* info, void* stream);
 
