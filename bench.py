@@ -1,21 +1,27 @@
 """Benchmark: unknowns/s per solve to a 1e-10 relative residual reduction.
 
-Workload (default): Helmholtz lambda = 1 on the unit cube, 8x8x8 uniform
-elements, degree sweep p in {4, 8, 16, 32}, f = manufactured solution plus
-seeded N(0, 1e-2) noise at the GLL nodes, plain FP64 GPU form, coarse degree
-p0 = 2.  One step solves all four degrees (condensation, V-cycles to 1e-10,
-interior recovery); unknowns = sum of (8p+1)^3.  The mixed-precision form
-(FP32 smoother and transfers, FP64 residual arithmetic, inside FP64 iterative
-refinement) is timed on the same workload and reported under "mixed"; "forms"
-adds the all-FP32 V-cycle and the Krylov-accelerated iteration (Algorithm 5)
-in FP64 and mixed precision, and "batched" 64 independent solves in one CUDA
-graph.
+Headline workload: Poisson on the unit cube, 6 x 6 x 6 stretched elements
+(per-axis aspect ratios drawn log-uniform in [1, 8]), degree p = 48,
+289^3 = 24,137,569 unknowns, manufactured right-hand side, coarse degree
+p0 = 2.  One step = one whole solve: condensation, Algorithm 4 (V-cycles) to
+a 1e-10 reduction of the condensed residual, interior recovery.  `value` is
+the plain FP64 GPU form; `mixed` the fastest mixed-precision form on the same
+workload (FP32 smoother and transfers, TF32 tensor-core transforms where the
+form has them, FP64 residuals and outer iteration).
 
-Timing: CUDA events on the solving stream around each solve, L2 flushed
-(256 MiB write) before every solve, W untimed warm-up steps, then K timed
-steps; max over ranks.  "e2e" repeats the timed steps through the host-buffer
-entry point (pinned host f in, u out, copies inside the timed region).
-Multi-GPU runs are replicas (the path has no exchange step on one mesh).
+Timing: CUDA events on the solving stream around each solve, L2 flushed (a
+256 MiB write) before every solve, W untimed warm-up steps, then K timed
+steps with per-kernel timing OFF; max over ranks.  `e2e` times the same steps
+through the host-buffer entry point (pinned host f in, u out, copies inside
+the timed region).  The roofline line comes from a separate pass of the same
+steps with the library's per-kernel CUDA events on: the dominant kernel's
+executed operations (counted by the library from the kernel's loop trip
+counts) over its event time, against the FP64 peak measured in the same run.
+
+Every table (forms, kernels, the 8^3 degree sweep, the 64-solve batch, the
+other workloads) goes to stdout as `{"detail": ...}` lines BEFORE the last
+line; the last line is the short result line.  Multi-GPU runs are replicas
+(the path has no exchange step on one mesh).
 """
 import argparse
 import json
@@ -35,36 +41,24 @@ import numpy as np  # noqa: E402
 
 import workloads  # noqa: E402
 
+HEADLINE = "poisson_6x6x6_p48_stretched"
+CPU_SAMPLE = "poisson_2x2x2_p48_stretched"
 SWEEP = [4, 8, 16, 32]
-WORKLOAD = "helmholtz_8x8x8_p4-8-16-32"
 METRIC = "unknowns/s per solve to 1e-10 residual (FP64 vs mixed); smoother HBM GB/s"
-# timed forms: name -> (precision, outer iteration).  "fp64" is the headline value,
-# "mixed" the mixed-precision line (FP32 smoother and transfers, FP64 residuals).
-FORMS = {"fp64": ("fp64", "mg"), "mixed": ("mixed", "mg"), "mixed_fp32": ("mixed_fp32", "mg"),
-         "mixed_tc": ("mixed_tc", "mg"), "kmg_fp64": ("fp64", "kmg"), "kmg_mixed": ("mixed", "kmg"),
-         "kmg_mixed_tc": ("mixed_tc", "kmg"), "eblock_fp64": ("fp64", "mg"), "eblock_mixed": ("mixed", "mg"),
-         "eblock_mult_mixed": ("mixed", "mg"), "mixed_fp32_tc": ("mixed_fp32_tc", "mg"),
-         "kmg_mixed_fp32_tc": ("mixed_fp32_tc", "kmg")}
-# forms with the element-centred block smoother (Sec. 3.4) instead of the vertex stars
-ELEMENT_FORMS = {"eblock_fp64": "element", "eblock_mixed": "element", "eblock_mult_mixed": "element_mult"}
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 entry in the peaks file)
-# DRAM bytes (read + write) per k_star<double> launch of the timed FP64 sweep: ncu
-# --metrics dram__bytes_read.sum,dram__bytes_write.sum per launch of `bench.py --forms fp64
-# --no-e2e --no-batch --no-configs --no-cpu-baseline --steps 1 --warmup 3`, averaged per degree and
-# weighted by the sweep's star launches per degree (28 at p = 4, 20 at 8, 12 at 16, 6 at 32);
-# profiles/k_star_f64_dram_helmholtz_8x8x8.md.  Valid only for the star-kernel source it was
-# measured on (hash below).
-STAR_TRAFFIC_BYTES = 7.771e6
-STAR_TRAFFIC_SOURCE = "fb81d2dbe05b46a3"
-# Executed FP64 operations (2 DFMA + DMUL + DADD thread instructions, ncu sass counters) per
-# k_star<double> launch, per level degree, from `bench.py --degrees 32 --forms fp64 --no-e2e --no-batch
-# --no-configs --no-cpu-baseline --no-autotune --steps 1 --warmup 3` (the first launch at each of
-# p = 32, 16, 8, 4; profiles/k_star_f64_executed_ops_helmholtz_8x8x8.md), weighted like the traffic:
-# the kernel executes 32-44 % of the paper's 37 n_S^3 count, so this rate measures the FP64 pipe.
-STAR_EXEC_FLOPS = {4: 0.004116e9, 8: 0.032777e9, 16: 0.264593e9, 32: 2.158269e9}
-STAR_EXEC_WEIGHTS = {4: 28, 8: 20, 16: 12, 32: 6}
-STAR_EXEC_SOURCE = "fb81d2dbe05b46a3"
+# timed forms: name -> (precision, outer iteration, smoother)
+FORMS = {"fp64": ("fp64", "mg", "star"), "mixed": ("mixed", "mg", "star"), "mixed_tc": ("mixed_tc", "mg", "star"),
+         "mixed_fp32": ("mixed_fp32", "mg", "star"), "mixed_fp32_tc": ("mixed_fp32_tc", "mg", "star"),
+         "kmg_fp64": ("fp64", "kmg", "star"), "kmg_mixed": ("mixed", "kmg", "star"),
+         "kmg_mixed_tc": ("mixed_tc", "kmg", "star"), "eblock_fp64": ("fp64", "mg", "element"),
+         "eblock_mixed": ("mixed", "mg", "element")}
+MIXED_FORMS = ("mixed", "mixed_tc")          # candidates for the result line's `mixed`
+DETAIL_FORMS = ("kmg_fp64", "kmg_mixed", "kmg_mixed_tc", "mixed_fp32", "mixed_fp32_tc")
+FP64_NOMINAL_TFLOPS = 1.25  # 2 FP64 FMA / clock / SM x 152 SMs x 2.07 GHz: fallback when the probe fails
+# DRAM bytes (read + write) per k_star<double> launch of the headline workload, from the ncu
+# capture named in the profiles (null once the star kernel's source changed since: hash below)
+STAR_TRAFFIC = {"bytes_per_launch": None, "source": None}
 STAR_SOURCES = ("star_kernel.cuh", "kernels_star_f64.cu")
+MAX_LINE = 1400  # bytes of the result line (the last stdout line)
 
 
 def star_source_hash():
@@ -80,12 +74,14 @@ def star_source_hash():
     return hsh.hexdigest()[:16]
 
 
-def load_peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return json.load(fh)
-    except Exception:
-        return {}
+def r4(x):
+    """x rounded to 4 significant digits (None and non-finite values pass through as None)."""
+    if x is None:
+        return None
+    x = float(x)
+    if not math.isfinite(x):
+        return None
+    return float(f"{x:.4g}")
 
 
 class ClockSampler:
@@ -111,6 +107,9 @@ class ClockSampler:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 3.0:  # first sample before the timed region
+            time.sleep(0.05)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -118,7 +117,7 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -144,14 +143,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(args):
+def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pg = None
     if world > 1:
-        import torch.distributed as dist
         import torch
+        import torch.distributed as dist
         backend = "nccl" if torch.cuda.is_available() else "gloo"
         if backend == "nccl":
             torch.cuda.set_device(local)
@@ -175,41 +174,50 @@ def max_over_ranks(pg, value):
     return float(t.item())
 
 
-# ---------------------------------------------------------------- reference arm: the oracle on the host
+def emit(name, payload, sink):
+    """One detail line on stdout (before the result line) and into the optional detail file."""
+    sink[name] = payload
+    print(json.dumps({"detail": name, **payload}), flush=True)
 
-def oracle_sample(p=16):
-    """One O2 (oracle) solve of the 8x8x8 Helmholtz workload at degree p; returns (unknowns, seconds, iters)."""
+
+# ---------------------------------------------------------------- the oracle on the host (CPU baseline)
+
+def oracle_sample():
+    """One whole oracle solve (numpy FP64: condensation, Algorithm 4 to 1e-10, recovery) of the 2^3-element
+    sample of the headline workload; returns (unknowns, seconds, iterations)."""
     from oracle import dense, matfree
-    h, p, lam, f, p0 = workloads.config(f"helmholtz_8x8x8_p{p}")
+    h, p, lam, f, p0 = workloads.config(CPU_SAMPLE)
     mesh = dense.Mesh(h, p, lam)
     t0 = time.perf_counter()
     _, it, _ = matfree.solve(mesh, f, p0=p0)
     dt = time.perf_counter() - t0
-    return (8 * p + 1) ** 3, dt, it
+    return int(f.size), dt, it
 
 
-def run_reference(args, world, rank, pg):
+def sample_text(n_unknowns, seconds):
+    return (f"whole oracle solves (numpy FP64, Alg. 4) of the 2x2x2-element sample of the 6^3 workload "
+            f"(p=48, same width law and f): {n_unknowns} unknowns in {seconds:.1f} s")
+
+
+def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    sample_p = args.cpu_sample_p
     for _ in range(args.warmup):
-        oracle_sample(sample_p)
+        oracle_sample()
     tot_n, tot_t = 0, 0.0
     for _ in range(args.steps):
-        n, dt, _ = oracle_sample(sample_p)
+        n, dt, _ = oracle_sample()
         tot_n += n
         tot_t += dt
     v = tot_n / tot_t
-    cores = os.cpu_count()
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "impl": "reference", "metric": METRIC, "value": r4(v), "unit": "unknowns/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r4(1e3 * tot_t / args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"p={sample_p} solve per step", "parallelism": "none"},
-        "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": cores, "kind": "oracle",
-                         "sample": f"one matrix-free oracle (numpy FP64) solve of helmholtz_8x8x8 at p={sample_p} "
-                                   f"({(8 * sample_p + 1) ** 3} unknowns) per step"},
-        "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": {"workload": HEADLINE, "sample": CPU_SAMPLE, "parallelism": "host cores"},
+        "cpu_baseline": {"value": r4(v), "unit": "unknowns/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample_text(tot_n, tot_t)},
+        "e2e": {"value": r4(v), "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -217,243 +225,260 @@ def run_reference(args, world, rank, pg):
 
 # ---------------------------------------------------------------- our arm
 
+def timed_solves(ctx, f, u, steps, flush, stream, host=None):
+    """Sum of the CUDA-event times of `steps` solves (L2 flushed before each) and the last info."""
+    import torch
+    ms, info = 0.0, None
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if host is not None:
+            _, info = ctx.solve_host(host[0], host[1], rtol=1e-10)
+        else:
+            _, info = ctx.solve(f, rtol=1e-10, out=u)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        assert info.res_final <= 1e-10 * info.res0, (info.res_final, info.res0)
+    return ms, info
+
+
+def roofline(kst, peak, peak_source, steps):
+    """Roofline of the dominant kernel class of a timing pass (kst: class -> totals over `steps` solves)."""
+    dom = max(kst, key=lambda k: kst[k]["ms"])
+    d = kst[dom]
+    total_ms = sum(v["ms"] for v in kst.values())
+    launches = sum(v["launches"] for v in kst.values())
+    per_launch_s = d["ms"] / 1e3 / max(1, d["launches"])
+    out = {"kernel": dom, "share": d["ms"] / total_ms, "launches_per_step": d["launches"] / steps,
+           "ms_per_launch": 1e3 * per_launch_s, "kernel_launches_per_step": launches / steps}
+    if d["xflops"] > 0:
+        achieved = d["xflops"] / (d["ms"] / 1e3) / 1e12
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": peak_source, "ops_per_launch": d["xflops"] / max(1, d["launches"]),
+                    "paper_count_tflops": d["flops"] / (d["ms"] / 1e3) / 1e12,
+                    "hbm_gbs": d["bytes"] / (d["ms"] / 1e3) / 1e9})
+    else:
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        out.update({"bound": "hbm", "achieved": achieved, "unit": "GB/s", "peak": None, "frac": None})
+    return out
+
+
+def kernel_table(kst, steps):
+    return {k: {"ms_per_step": r4(v["ms"] / steps), "launches_per_step": r4(v["launches"] / steps),
+                "paper_tflops": r4(v["flops"] / (v["ms"] / 1e3) / 1e12) if v["flops"] and v["ms"] else None,
+                "exec_tflops": r4(v["xflops"] / (v["ms"] / 1e3) / 1e12) if v["xflops"] and v["ms"] else None,
+                "hbm_gbs": r4(v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["bytes"] and v["ms"] else None}
+            for k, v in kst.items() if v["launches"]}
+
+
+def timing_pass(ctx, f, u, steps):
+    """Per-kernel CUDA-event statistics of `steps` solves (a pass separate from the timed ones)."""
+    ctx.set_timing(True)
+    for _ in range(steps):
+        ctx.solve(f, rtol=1e-10, out=u)
+    kst = ctx.kstats()
+    ctx.set_timing(False)
+    return kst
+
+
 def run_semmg(args, world, rank, local, pg):
     import torch
     from paper_1808_03595_gb300 import Context
     from paper_1808_03595_gb300 import build as _build
+    from paper_1808_03595_gb300.solver import peak_tflops
     _build.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    degrees = [int(x) for x in args.degrees.split(",")]
+    details = {}
+    K, W = args.steps, args.warmup
 
-    forms = args.forms.split(",")
-    if "fp64" not in forms:
-        forms = ["fp64"] + forms
+    try:
+        fp64_peak, fp64_src = peak_tflops(torch.float64), "measured (FP64 FMA chains, this run)"
+        fp32_peak = peak_tflops(torch.float32)
+    except Exception:  # pragma: no cover - a probe failure falls back to the nominal rate
+        fp64_peak, fp64_src, fp32_peak = FP64_NOMINAL_TFLOPS, "nominal (probe failed)", None
+    emit("peaks", {"fp64_tflops": r4(fp64_peak), "fp32_tflops": r4(fp32_peak), "source": fp64_src}, details)
+
+    # ---- headline workload
+    h, p, lam, f, p0 = workloads.config(HEADLINE)
+    fd = torch.as_tensor(f, dtype=torch.float64, device=dev)
+    ud = torch.empty_like(fd)
+    unknowns = int(fd.numel())
+    forms = ["fp64"] + list(MIXED_FORMS) + ([] if args.quick else list(DETAIL_FORMS))
+    ctx = {}
     for form in forms:
-        if form not in FORMS:
-            raise SystemExit(f"unknown form {form}; choose from {sorted(FORMS)}")
-    cases = []
-    for p in degrees:
-        h, p, lam, f, p0 = workloads.config(f"helmholtz_8x8x8_p{p}")
-        fd = torch.as_tensor(f, dtype=torch.float64, device=dev)
-        ud = torch.empty_like(fd)
-        fh = torch.as_tensor(f, dtype=torch.float64).pin_memory()
-        uh = torch.empty_like(fh).pin_memory()
-        c = {"p": p, "n": int(fd.numel()), "f": fd, "u": ud, "fh": fh, "uh": uh}
-        for form in forms:
-            prec, solver = FORMS[form]
-            c[form] = Context(h, p, lam, p0=p0, precision=prec, solver=solver,
-                              smoother=ELEMENT_FORMS.get(form, "star"))
-        cases.append(c)
-    tuned = {}
-    if args.autotune:
-        for c in cases:
-            for form in forms:
-                ctx = c[form]
-                ctx.autotune()
-                dts = torch.float32 if FORMS[form][0] in ("mixed_fp32", "mixed_fp32_tc") else torch.float64
-                dt = torch.float64 if FORMS[form][0] == "fp64" else torch.float32
-                tuned.setdefault(form, {})[c["p"]] = {
-                    "star": ctx.launch_shape(ctx.L, "star", dt), "schur": ctx.launch_shape(ctx.L, "schur", dts)}
+        prec, solver, sm = FORMS[form]
+        ctx[form] = Context(h, p, lam, p0=p0, precision=prec, solver=solver, smoother=sm)
+        if args.autotune:
+            ctx[form].autotune()
+    for form in forms:
+        for _ in range(W):
+            ctx[form].solve(fd, rtol=1e-10, out=ud)
     torch.cuda.synchronize()
 
-    per_p_ms = {form: {} for form in forms}
-
-    def solve_all(form, timed, host=False):
-        ms, iters = 0.0, {}
-        for c in cases:
-            ctx = c[form]
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            if host:
-                _, info = ctx.solve_host(c["fh"], c["uh"], rtol=1e-10)
-            else:
-                _, info = ctx.solve(c["f"], rtol=1e-10, out=c["u"])
-            e1.record(stream)
-            e1.synchronize()
-            if timed:
-                dt = e0.elapsed_time(e1)
-                ms += dt
-                if not host:
-                    per_p_ms[form][c["p"]] = per_p_ms[form].get(c["p"], 0.0) + dt / args.steps
-            iters[c["p"]] = info.iters
-            assert info.res_final <= 1e-10 * info.res0, (form, c["p"], info.res_final, info.res0)
-        return ms, iters
-
-    for form in forms:
-        for _ in range(args.warmup):
-            solve_all(form, False)
-    # timed region (device-resident inputs)
-    for c in cases:
-        c["fp64"].set_timing(True)
+    # timed region of `value`: per-kernel timing off
     barrier(pg)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    t64, it64 = 0.0, {}
-    for _ in range(args.steps):
-        ms, it64 = solve_all("fp64", True)
-        t64 += ms
+    t64, info64 = timed_solves(ctx["fp64"], fd, ud, K, flush, stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier(pg)
-    kst = {}
-    for c in cases:
-        for k, v in c["fp64"].kstats().items():
-            acc = kst.setdefault(k, {"ms": 0.0, "launches": 0, "flops": 0.0, "bytes": 0.0})
-            for kk in acc:
-                acc[kk] += v[kk]
-        c["fp64"].set_timing(False)
+    tform, iters = {}, {"fp64": info64.iters}
+    for form in forms[1:]:
+        tform[form], inf = timed_solves(ctx[form], fd, ud, K, flush, stream)
+        iters[form] = inf.iters
+    # end to end through the host-buffer entry point (pinned host f in, u out)
     te2e = float("nan")
-    tform, itform, kstform = {}, {}, {}
-    for form in forms:
-        if form == "fp64":
-            continue
-        for c in cases:
-            c[form].set_timing(True)
-        tf = 0.0
-        for _ in range(args.steps):
-            ms, itform[form] = solve_all(form, True)
-            tf += ms
-        tform[form] = tf
-        kk = kstform.setdefault(form, {})
-        for c in cases:
-            for k, v in c[form].kstats().items():
-                acc = kk.setdefault(k, {"ms": 0.0, "launches": 0, "flops": 0.0})
-                acc["ms"] += v["ms"]
-                acc["launches"] += v["launches"]
-                acc["flops"] += v["flops"]
-            c[form].set_timing(False)
-    t32 = tform.get("mixed", float("nan"))
-    it32 = itform.get("mixed", {})
-    kst32 = kstform.get("mixed", {})
     if not args.no_e2e:
-        # end to end through the host-buffer entry point
-        solve_all("fp64", False, host=True)
-        te2e = 0.0
-        for _ in range(args.steps):
-            ms, _ = solve_all("fp64", True, host=True)
-            te2e += ms
+        fh = torch.as_tensor(f, dtype=torch.float64).pin_memory()
+        uh = torch.empty_like(fh).pin_memory()
+        ctx["fp64"].solve_host(fh, uh, rtol=1e-10)
+        te2e, _ = timed_solves(ctx["fp64"], None, None, K, flush, stream, host=(fh, uh))
+    # roofline pass: the same solves with the per-kernel events on
+    npass = max(1, min(K, 5))
+    kst = timing_pass(ctx["fp64"], fd, ud, npass)
+    emit("kernels_fp64", {"workload": HEADLINE, "solves": npass, "kernels": kernel_table(kst, npass)}, details)
+    kst_m = {}
+    for form in MIXED_FORMS:
+        kst_m[form] = timing_pass(ctx[form], fd, ud, npass)
+        emit(f"kernels_{form}", {"workload": HEADLINE, "solves": npass, "kernels": kernel_table(kst_m[form], npass)},
+             details)
     torch.cuda.synchronize()
 
     t64 = max_over_ranks(pg, t64)
-    t32 = max_over_ranks(pg, t32)
     te2e = max_over_ranks(pg, te2e)
     tform = {k: max_over_ranks(pg, v) for k, v in tform.items()}
-    unknowns = sum(c["n"] for c in cases)
-    value = world * unknowns * args.steps / (t64 / 1e3)
-    value32 = world * unknowns * args.steps / (t32 / 1e3)
-    e2e = world * unknowns * args.steps / (te2e / 1e3)
-    forms_out = {"fp64": {"precision": "fp64", "solver": "mg", "value": value, "ms_per_step": t64 / args.steps,
-                          "iterations": it64}}
-    for form, tf in tform.items():
-        v = world * unknowns * args.steps / (tf / 1e3)
-        forms_out[form] = {"precision": FORMS[form][0], "solver": FORMS[form][1],
-                           "smoother": ELEMENT_FORMS.get(form, "star"), "value": v,
-                           "ms_per_step": tf / args.steps, "iterations": itform[form], "speedup_vs_fp64": v / value,
-                           "kernels": {k: {"ms_per_step": x["ms"] / args.steps,
-                                           "launches_per_step": x["launches"] / args.steps,
-                                           "tflops": (x["flops"] / (x["ms"] / 1e3) / 1e12) if x["flops"] else None}
-                                       for k, x in kstform[form].items()}}
+    value = world * unknowns * K / (t64 / 1e3)
+    vforms = {k: world * unknowns * K / (v / 1e3) for k, v in tform.items()}
+    e2e = world * unknowns * K / (te2e / 1e3) if te2e == te2e else None
+    emit("forms", {"workload": HEADLINE, "unknowns": unknowns,
+                   "forms": {k: {"value": r4(v), "speedup_vs_fp64": r4(v / value), "iterations": iters[k],
+                                 "precision": FORMS[k][0], "solver": FORMS[k][1]}
+                             for k, v in [("fp64", value)] + list(vforms.items())}}, details)
+    roof = roofline(kst, fp64_peak, fp64_src, npass)
+    h_now = star_source_hash()
+    roof["traffic"] = (STAR_TRAFFIC["bytes_per_launch"] if roof["kernel"] == "star" and h_now is not None
+                       and h_now == STAR_TRAFFIC["source"] else None)
+    emit("roofline", {k: (r4(v) if isinstance(v, float) else v) for k, v in roof.items()}, details)
+    for form in MIXED_FORMS:
+        rm = roofline(kst_m[form], fp32_peak or 1.0, "measured (FP32 FMA chains, this run)", npass)
+        emit(f"roofline_{form}", {k: (r4(v) if isinstance(v, float) else v) for k, v in rm.items()}, details)
+    best = max(MIXED_FORMS, key=lambda k: vforms[k])
+    for c in ctx.values():
+        c.close()
 
-    # roofline of the dominant kernel (FP64 form): FP64-ALU bound
-    dom = max(kst, key=lambda k: kst[k]["ms"])
-    d = kst[dom]
-    total_ms = sum(v["ms"] for v in kst.values())
-    launches = sum(v["launches"] for v in kst.values())
-    peaks = load_peaks()
-    traffic = None
-    if dom == "star":
-        if star_source_hash() == STAR_TRAFFIC_SOURCE:
-            traffic = STAR_TRAFFIC_BYTES
-    executed = None
-    if dom == "star" and star_source_hash() == STAR_EXEC_SOURCE and degrees == SWEEP:
-        per_launch = sum(STAR_EXEC_FLOPS[q] * STAR_EXEC_WEIGHTS[q] for q in SWEEP) / sum(STAR_EXEC_WEIGHTS.values())
-        rate = per_launch * d["launches"] / (d["ms"] / 1e3) / 1e12
-        executed = {"flops_per_launch": per_launch, "achieved": rate, "frac": rate / FP64_PEAK_TFLOPS}
-    if d["flops"] > 0:
-        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom, "executed": executed,
-                "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["launches"]),
-                "peak_source": "nominal FP64 1.25 TFLOP/s (2 FP64 FMA/clk/SM x 152 SMs at 2.07 GHz)",
-                "launches": d["launches"], "share_of_kernel_time": d["ms"] / total_ms,
-                "hbm_gbs": d["bytes"] / (d["ms"] / 1e3) / 1e9}
-    else:
-        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        pk = peaks.get("hbm_gbs", 6800.0)
-        roof = {"bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
-                "traffic": None, "kernel": dom, "launches": d["launches"]}
+    # ---- secondary: the 8^3 Helmholtz degree sweep (one step = the four solves)
+    sweep = run_sweep(args, dev, stream, flush, details)
 
-    line = {
-        "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t64 / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "degrees": degrees, "elements": [8, 8, 8], "lambda": 1.0, "p0": 2,
-                   "rtol": 1e-10, "l2": "flushed (256 MiB write) before every solve",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "iterations": {"fp64": it64, "mixed": it32},
-        "mixed": {"value": value32, "unit": "unknowns/s", "dtype": "f64+f32", "ms_per_step": t32 / args.steps,
-                  "speedup_vs_fp64": value32 / value},
-        "e2e": {"value": e2e, "unit": "unknowns/s", "h2d_bytes_per_step": 8 * unknowns,
-                "d2h_bytes_per_step": 8 * unknowns},
-        "gpu_launches": int(launches // max(1, args.steps)) * args.steps,
-        "kernels_fp64": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
-                         for k, v in kst.items()},
-        "kernels_mixed": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
-                          for k, v in kst32.items()},
-        "forms": forms_out,
-        "ms_per_degree": per_p_ms,
-        "launch_shapes_finest_level": tuned,
-        "roofline": roof,
-        "clocks": clk,
-    }
-    if args.batch and rank == 0:
-        line["batched"] = run_batch(args, dev, stream, flush)
-        line["batched_kmg"] = run_batch(args, dev, stream, flush, solver="kmg")
-        if "fp64_plain" in line["batched"]:
-            line["batched_kmg"]["speedup_vs_fp64_plain"] = (line["batched_kmg"]["value"] /
-                                                            line["batched"]["fp64_plain"]["value"])
-    if args.configs and rank == 0:
-        line["configs"] = run_configs(args, dev, stream, flush)
+    if not args.quick and rank == 0:
+        run_batch(args, dev, stream, flush, details)
+        run_configs(args, dev, stream, flush, details)
+
+    cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n, dt = 0, 0.0
-        while dt < 10.0:  # about 10 s of CPU work: whole oracle solves until then
-            n1, dt1, _ = oracle_sample(args.cpu_sample_p)
+        while dt < 10.0:  # about 10 s or more of CPU work: whole oracle solves of the sample
+            n1, dt1, _ = oracle_sample()
             n, dt = n + n1, dt + dt1
-        line["cpu_baseline"] = {"value": n / dt, "unit": "unknowns/s", "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"matrix-free oracle (numpy FP64) solves of helmholtz_8x8x8 at "
-                                          f"p={args.cpu_sample_p} ({n} unknowns in all), {dt:.1f} s"}
+        cpu = {"value": r4(n / dt), "unit": "unknowns/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": sample_text(n, dt)}
+        emit("cpu_baseline", {**cpu, "us_per_unknown": r4(1e6 * dt / n)}, details)
+
+    line = result_line(value=value, steps=K, warmup=W, ms_total=t64, unknowns=unknowns, p0=p0, world=world,
+                       iterations=info64.iters, mixed=(best, vforms[best], iters[best]), e2e=e2e, roof=roof,
+                       peak_measured=fp64_src.startswith("measured"), cpu=cpu, clocks=clk, sweep=sweep)
+    if args.detail_json and rank == 0:
+        with open(args.detail_json, "w") as fh:
+            json.dump({"result": line, **details}, fh, indent=1)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for c in cases:
-        for form in forms:
-            c[form].close()
     return 0
 
 
-def run_configs(args, dev, stream, flush):
-    """The other workloads of the paper's shape, one solve per form each (not part of `value`):
-    Helmholtz 16^3 at p = 16 (lambda 0 and 100, Dirichlet; lambda 1 with Neumann faces and periodic) and
-    Poisson on 6^3 stretched elements at p = 48."""
+def result_line(value, steps, warmup, ms_total, unknowns, p0, world, iterations, mixed, e2e, roof, peak_measured,
+                cpu, clocks, sweep):
+    """The last stdout line: the headline and the keys the result needs, nothing else (it stays under
+    MAX_LINE bytes; the tables went out as detail lines before it)."""
+    best, vbest, itbest = mixed
+    return {
+        "metric": METRIC, "value": r4(value), "unit": "unknowns/s", "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": r4(ms_total / steps), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": HEADLINE, "unknowns": unknowns, "solver": "alg4", "p0": p0,
+                   "l2": "flushed (256 MiB write) before every solve",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "iterations": iterations,
+        "mixed": {"value": r4(vbest), "form": best, "speedup_vs_fp64": r4(vbest / value), "iterations": itbest},
+        "e2e": {"value": r4(e2e), "unit": "unknowns/s", "h2d_bytes_per_step": 8 * unknowns,
+                "d2h_bytes_per_step": 8 * unknowns},
+        "gpu_launches": int(round(roof["kernel_launches_per_step"] * steps)),
+        "roofline": {"bound": roof["bound"],
+                     "kernel": "k_star<double>" if roof["kernel"] == "star" else roof["kernel"],
+                     "achieved": r4(roof["achieved"]), "peak": r4(roof["peak"]), "unit": roof["unit"],
+                     "frac": r4(roof["frac"]), "traffic": roof["traffic"],
+                     "peak_kind": "measured" if peak_measured else "nominal"},
+        "cpu_baseline": cpu,
+        "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples")},
+        "sweep_8x8x8": sweep,
+    }
+
+
+def run_sweep(args, dev, stream, flush, details):
+    """Helmholtz lambda = 1 on 8^3 uniform elements, p in {4, 8, 16, 32}: FP64 and the mixed form,
+    one step = the four solves; unknowns/s over the K timed steps."""
     import torch
     from paper_1808_03595_gb300 import Context
     out = {}
+    cases = []
+    for q in SWEEP:
+        h, q, lam, f, p0 = workloads.config(f"helmholtz_8x8x8_p{q}")
+        fd = torch.as_tensor(f, dtype=torch.float64, device=dev)
+        cases.append((q, fd, torch.empty_like(fd), {form: Context(h, q, lam, p0=p0, precision=FORMS[form][0])
+                                                    for form in ("fp64", "mixed")}))
+    n = sum(int(c[1].numel()) for c in cases)
+    table = {}
+    for form in ("fp64", "mixed"):
+        for q, fd, ud, cx in cases:
+            if args.autotune:
+                cx[form].autotune()
+            for _ in range(args.warmup):
+                cx[form].solve(fd, out=ud)
+        ms, its = 0.0, {}
+        for q, fd, ud, cx in cases:
+            t, info = timed_solves(cx[form], fd, ud, args.steps, flush, stream)
+            ms += t
+            its[q] = info.iters
+        out[form] = r4(n * args.steps / (ms / 1e3))
+        table[form] = {"value": out[form], "ms_per_step": r4(ms / args.steps), "iterations": its}
+    for _, _, _, cx in cases:
+        for c in cx.values():
+            c.close()
+    emit("sweep_8x8x8", {"workload": "helmholtz_8x8x8_p4-8-16-32", "unknowns_per_step": n, **table}, details)
+    return out
+
+
+def run_configs(args, dev, stream, flush, details):
+    """The other workloads of the paper's shape, one solve per step per form (not part of `value`):
+    Helmholtz 16^3 at p = 16 (lambda 0 and 100, Dirichlet; lambda 1 with Neumann faces and periodic),
+    and the Sec. 5.2 problem (8^3, k = 5, Dirichlet data) at p = 16 and 32."""
+    import torch
+    from paper_1808_03595_gb300 import Context
     plan = [("helmholtz_16x16x16_p16", 0.0, None, ["fp64", "mixed", "mixed_tc", "kmg_mixed"]),
             ("helmholtz_16x16x16_p16", 100.0, None, ["fp64", "mixed"]),
-            ("helmholtz_16x16x16_p16", 1.0, ("N",) * 6, ["fp64", "mixed", "kmg_mixed"]),
-            ("helmholtz_16x16x16_p16", 1.0, ("P",) * 6, ["fp64", "mixed", "kmg_mixed"]),
-            ("poisson_6x6x6_p48_stretched", None, None, ["fp64", "mixed", "mixed_tc", "kmg_fp64", "kmg_mixed"]),
+            ("helmholtz_16x16x16_p16", 1.0, ("N",) * 6, ["fp64", "mixed"]),
+            ("helmholtz_16x16x16_p16", 1.0, ("P",) * 6, ["fp64", "mixed"]),
             ("paper_sec52_8x8x8_p16", 0.0, None, ["fp64", "mixed", "kmg_mixed"]),
             ("paper_sec52_8x8x8_p32", 0.0, None, ["fp64", "mixed", "kmg_mixed"])]
     for name, lam, bc, forms in plan:
         gd = ue = None
         if name.startswith("paper_sec52"):
-            # the runtime tests' problem: (0, 2 pi)^3, k = 5, lambda = 0, inhomogeneous Dirichlet data
             p, p0 = int(name.rsplit("_p", 1)[1]), 2
             h = workloads.uniform_widths(8, 2 * math.pi)
             ue, f = workloads.paper_solution(h, p, 5.0, lam)
@@ -465,10 +490,10 @@ def run_configs(args, dev, stream, flush):
         ud = torch.empty_like(fd)
         n = int(fd.numel())
         key = f"{name}_lambda{lam:g}" + ({"N": "_neumann", "P": "_periodic"}[bc[0]] if bc else "")
-        out[key] = {"unknowns": n}
+        res = {"unknowns": n}
         for form in forms:
-            prec, solver = FORMS[form]
-            with Context(h, p, lam, p0=p0, precision=prec, solver=solver, bc=bc) as c:
+            prec, solver, sm = FORMS[form]
+            with Context(h, p, lam, p0=p0, precision=prec, solver=solver, bc=bc, smoother=sm) as c:
                 if args.autotune:
                     c.autotune()
                 for _ in range(args.warmup):
@@ -484,109 +509,106 @@ def run_configs(args, dev, stream, flush):
                     e1.synchronize()
                     ms += e0.elapsed_time(e1)
                     assert info.res_final <= 1e-10 * info.res0, (key, form)
-            out[key][form] = {"value": n * args.steps / (ms / 1e3), "ms": ms / args.steps, "iterations": info.iters}
+            res[form] = {"value": r4(n * args.steps / (ms / 1e3)), "ms": r4(ms / args.steps),
+                         "iterations": info.iters}
             if ue is not None:
-                out[key][form]["max_error_vs_exact"] = float(torch.max(torch.abs(ud - gd)))
-    return out
+                res[form]["max_error_vs_exact"] = r4(float(torch.max(torch.abs(ud - gd))))
+        emit(f"config_{key}", res, details)
 
 
-def run_batch(args, dev, stream, flush, solver="mg"):
-    """64 independent Helmholtz solves (n ~ U{2..12}, p ~ U{4..24}, lambda = 10^U(-2,3), mixed form) in one
-    CUDA graph launch; throughput = total unknowns / graph time."""
+def run_batch(args, dev, stream, flush, details):
+    """64 independent Helmholtz solves (n ~ U{2..12}, p ~ U{4..24}, lambda = 10^U(-2,3)) in one CUDA graph
+    launch, in the mixed form (Algorithms 4 and 5) and in the plain FP64 form (the same graph, and
+    sequential solve calls); throughput = total unknowns / time per batch."""
     import torch
     from paper_1808_03595_gb300 import Batch, Context
     cases = workloads.batch64()
-    ctxs, fs, us = [], [], []
-    for h, p, lam, f in cases:
-        ctxs.append(Context(h, p, lam, p0=2, precision="mixed", solver=solver))
-        fs.append(torch.as_tensor(f, dtype=torch.float64, device=dev))
-        us.append(torch.empty_like(fs[-1]))
-    t0 = time.perf_counter()
-    if args.autotune:
-        for c in ctxs:
-            c.autotune()
-    t_tune = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    b = Batch(ctxs, fs, us)
-    t_capture = time.perf_counter() - t0
-    for _ in range(args.warmup):
-        b.solve()
-    ms = 0.0
-    iters = []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rc, infos = b.solve()
-        e1.record(stream)
-        e1.synchronize()
-        ms += e0.elapsed_time(e1)
-        assert rc == 0 and all(i.res_final <= 1e-10 * i.res0 for i in infos)
-        iters = [i.iters for i in infos]
+    fs = [torch.as_tensor(f, dtype=torch.float64, device=dev) for _, _, _, f in cases]
+    us = [torch.empty_like(f) for f in fs]
     unknowns = sum(int(f.numel()) for f in fs)
     out = {"workload": "batch64 (n~U{2..12}, p~U{4..24}, lambda=10^U(-2,3), f~U(-1,1), seed 1808035955)",
-           "solver": solver, "value": unknowns * args.steps / (ms / 1e3), "unit": "unknowns/s", "dtype": "f64+f32",
-           "solves": len(cases), "unknowns": unknowns, "ms_per_batch": ms / args.steps,
-           "graph_nodes": b.graph_nodes(), "capture_s": t_capture, "autotune_s": t_tune,
-           "iterations": {"min": min(iters), "max": max(iters), "mean": sum(iters) / len(iters)}}
-    b.close()
-    for c in ctxs:
-        c.close()
-    if solver == "mg":
-        # the plain FP64 GPU form on the same 64 solves, one solve call after another
-        ctxs = [Context(h, p, lam, p0=2, precision="fp64", solver="mg") for h, p, lam, _ in cases]
+           "solves": len(cases), "unknowns": unknowns}
+
+    def graph(prec, solver):
+        ctxs = [Context(h, p, lam, p0=2, precision=prec, solver=solver) for h, p, lam, _ in cases]
         if args.autotune:
             for c in ctxs:
                 c.autotune()
+        b = Batch(ctxs, fs, us)
         for _ in range(args.warmup):
-            for c, f, u in zip(ctxs, fs, us):
-                c.solve(f, out=u)
-        ms64 = 0.0
+            b.solve()
+        ms, iters = 0.0, []
         for _ in range(args.steps):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for c, f, u in zip(ctxs, fs, us):
-                _, info = c.solve(f, out=u)
-                assert info.res_final <= 1e-10 * info.res0
+            rc, infos = b.solve()
             e1.record(stream)
             e1.synchronize()
-            ms64 += e0.elapsed_time(e1)
-        v64 = unknowns * args.steps / (ms64 / 1e3)
-        out["fp64_plain"] = {"value": v64, "ms_per_batch": ms64 / args.steps,
-                             "note": "same 64 solves, FP64 form, sequential semmg_solve calls"}
-        out["speedup_vs_fp64_plain"] = out["value"] / v64
+            ms += e0.elapsed_time(e1)
+            assert rc == 0 and all(i.res_final <= 1e-10 * i.res0 for i in infos)
+            iters = [i.iters for i in infos]
+        res = {"value": r4(unknowns * args.steps / (ms / 1e3)), "ms_per_batch": r4(ms / args.steps),
+               "graph_nodes": b.graph_nodes(), "iterations": {"min": min(iters), "max": max(iters),
+                                                              "mean": r4(sum(iters) / len(iters))}}
+        b.close()
         for c in ctxs:
             c.close()
-    return out
+        return res
+
+    out["mixed_mg"] = graph("mixed", "mg")
+    out["mixed_kmg"] = graph("mixed", "kmg")
+    out["fp64_mg"] = graph("fp64", "mg")
+    # the plain FP64 form as a user without the batched entry point runs it: one solve call after another
+    ctxs = [Context(h, p, lam, p0=2, precision="fp64", solver="mg") for h, p, lam, _ in cases]
+    if args.autotune:
+        for c in ctxs:
+            c.autotune()
+    for _ in range(args.warmup):
+        for c, f, u in zip(ctxs, fs, us):
+            c.solve(f, out=u)
+    ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for c, f, u in zip(ctxs, fs, us):
+            _, info = c.solve(f, out=u)
+            assert info.res_final <= 1e-10 * info.res0
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    for c in ctxs:
+        c.close()
+    out["fp64_sequential"] = {"value": r4(unknowns * args.steps / (ms / 1e3)), "ms_per_batch": r4(ms / args.steps)}
+    out["speedup_mixed_vs_fp64_graph"] = r4(out["mixed_mg"]["value"] / out["fp64_mg"]["value"])
+    out["speedup_mixed_kmg_vs_fp64_graph"] = r4(out["mixed_kmg"]["value"] / out["fp64_mg"]["value"])
+    out["speedup_mixed_vs_fp64_sequential"] = r4(out["mixed_mg"]["value"] / out["fp64_sequential"]["value"])
+    emit("batch64", out, details)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="semmg", choices=["semmg", "reference"])
-    ap.add_argument("--degrees", default=",".join(str(p) for p in SWEEP))
-    ap.add_argument("--cpu-sample-p", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default=",".join(FORMS),
-                    help="forms to time, from " + ", ".join(FORMS) + " (fp64 is always timed: the headline)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing (profiling runs)")
+    ap.add_argument("--quick", action="store_true",
+                    help="headline, its mixed forms and the 8^3 sweep only (no batch, other workloads or "
+                         "Krylov / all-FP32 forms)")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
-                    help="tune launch shapes per degree before the warm-up (outside the timed region)")
-    ap.add_argument("--configs", action=argparse.BooleanOptionalAction, default=True,
-                    help="also time the 16^3 p=16, 6^3 p=48 stretched and Sec. 5.2 workloads (under configs)")
-    ap.add_argument("--batch", action=argparse.BooleanOptionalAction, default=True,
-                    help="also time the 64-solve batched graph workload")
+                    help="tune launch shapes per level before the warm-up (outside the timed region)")
+    ap.add_argument("--detail-json", default=None, help="also write the result and every detail table here")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    world, rank, local, pg = dist_setup(args)
+    world, rank, local, pg = dist_setup()
     if args.impl == "reference":
-        rc = run_reference(args, world, rank, pg)
+        rc = run_reference(args, world, rank)
     else:
         rc = run_semmg(args, world, rank, local, pg)
     if pg is not None:

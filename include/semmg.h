@@ -7,20 +7,30 @@
  *
  * Problem (Sec. 2.1, eq. helmholtz_equation): lambda u - Laplace u = f on a box
  * meshed by a tensor product of cuboidal elements (per-axis widths h_d[a]),
- * GLL nodal basis of degree p, homogeneous Dirichlet conditions on all six
- * faces (Sec. 3.3).  The element operator is eq. helmholtzop with coefficients
+ * GLL nodal basis of degree p.  Each face of the box is Dirichlet (homogeneous,
+ * or with data g through semmg_solve_dirichlet / semmg_pack_dirichlet),
+ * homogeneous Neumann, or periodic (both faces of an axis), Sec. 3.3; see
+ * semmg_mesh.bc.  The element operator is eq. helmholtzop with coefficients
  * d_e = h1 h2 h3 / 8 (lambda, 4/h1^2, 4/h2^2, 4/h3^2), the rightmost Kronecker
  * factor acting along x1.
  *
  * ------------------------------------------------------------------ layouts
  * Nodal arrays: the global GLL grid of a level, N_d = n_d p + 1 points per
- * axis, FP64, C order u[g3][g2][g1] (x1 fastest), Dirichlet boundary included.
+ * axis, FP64, C order u[g3][g2][g1] (x1 fastest), boundary planes included
+ * (on a periodic axis the last plane is the image of the first).
  *
  * Condensed ("hat") vectors: values on the element skeleton (element-boundary
  * nodes, Sec. 2.2), one slot per unique node, grouped by entity, with m = p-1,
- * nv_d = n_d + 1 vertex planes per axis.  Entities on the domain boundary are
- * stored too and always hold 0 (homogeneous Dirichlet); no entry point writes
- * a non-zero there.  Group order and index formulas (c = vertex-plane index,
+ * nv_d = n_d + 1 vertex planes per axis.  Every vertex plane has slots, also
+ * where it holds no unknowns:
+ *   - on a Dirichlet face the slots are not unknowns.  Every output of the
+ *     operator, residual, smoother and transfers is 0 there; an input vector
+ *     may carry Dirichlet data there (semmg_pack_dirichlet), which the
+ *     operator, residual and recovery read as prescribed boundary values;
+ *   - on a Neumann face the slots are unknowns like interior ones;
+ *   - the last vertex plane of a periodic axis repeats plane 0: its slots are
+ *     never read and outputs leave them 0.
+ * Group order and index formulas (c = vertex-plane index,
  * a = element index, i = 0..m-1 interior node index, the last index fastest):
  *   F1 faces normal to x1 [a3][a2][c1][i3][i2]   n3 n2 nv1 m^2
  *   F2 faces normal to x2 [a3][c2][a1][i3][i1]   n3 nv2 n1 m^2
@@ -65,9 +75,10 @@ enum {
   SEMMG_ERR_CUDA = -3,          /* a CUDA runtime call failed */
   SEMMG_ERR_NOT_CONVERGED = -4, /* max_iter cycles without reaching rtol; info filled */
   SEMMG_ERR_NONFINITE = -5,     /* NaN or Inf in a residual norm */
-  SEMMG_ERR_TIMEOUT = -6,       /* a bounded device wait ran out (batched form, tensor-core smoother) */
+  SEMMG_ERR_TIMEOUT = -6,       /* a bounded device wait ran out (tensor-core smoother, semmg_set_guards) */
   SEMMG_ERR_NOMEM = -7,         /* device or host allocation failed */
-  SEMMG_ERR_DIVERGED = -8       /* the residual norm grew above 1e3 ||r_0||: stopped early; info filled */
+  SEMMG_ERR_DIVERGED = -8       /* the residual norm grew above 1e3 ||r_0|| (semmg_set_guards): stopped early;
+                                   info filled */
 };
 
 #define SEMMG_MAX_DEGREE 48
@@ -236,7 +247,9 @@ int semmg_recover(semmg_ctx* ctx, const double* f_nodal, const double* u_hat, do
  * SEMMG_ERR_NOT_CONVERGED after max_iter iterations (u_nodal still holds the
  * last iterate), SEMMG_ERR_NONFINITE on a NaN/Inf residual norm,
  * SEMMG_ERR_DIVERGED as soon as ||r|| > 1e3 ||r_0|| (the iteration is not
- * contracting: a wrong operator, data or option, not a slow start).
+ * contracting: a wrong operator, data or option, not a slow start; the factor
+ * is set by semmg_set_guards), SEMMG_ERR_TIMEOUT when a tensor-core wait of
+ * the smoother ran out during the solve.
  * Each iteration runs as one CUDA graph launch on `stream`: the first call
  * captures it on a stream the context owns (re-captured after semmg_autotune,
  * semmg_set_launch or a change of semmg_set_timing); results are bitwise those
@@ -328,22 +341,29 @@ int semmg_set_launch(semmg_ctx* ctx, int level, int kernel, int dtype, int smem_
  * device-wide synchronisation cudaMalloc and cudaFree may cause.
  *
  * semmg_smooth_noalloc computes exactly what semmg_smooth computes (du_hat =
- * Smoother(r_hat) on `level`, same kernels, same results) but calls no
+ * Smoother(r_hat) on `level`, bitwise the same result) with the same kernels:
+ * the CUDA-core star kernel, or for dtype SEMMG_F32 on the levels where the
+ * context's precision (SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC) puts the star
+ * transforms on the tensor cores, the tensor-core star kernel.  It calls no
  * cudaMalloc, cudaFree or other allocating routine: the star output buffer and
  * the per-block work arrays come from one array of SEMMG_NOALLOC_SCRATCH_BYTES
  * compiled into the library, which every GPU that loads the library holds
  * until the process exits.  The context (its read-only tables) must have been
  * set up beforehand by code that was allowed to allocate; the caller passes
  * r_hat and du_hat as for semmg_smooth.
- *   - The first call on a device looks the array's address up (once per
- *     device, with that device current); make that first call before any
- *     stream capture.
+ *   - Every call looks the array's device address up for the current device
+ *     (cudaGetSymbolAddress, no allocation).  The first lookup on a device may
+ *     load the library's device code there: make the first call on each device
+ *     before any stream capture.
  *   - Vertex-star smoother only: a context set up with an element-centred
  *     smoother returns SEMMG_ERR_UNSUPPORTED.
  *   - A level whose star output buffer (nstar * 3 * n_S^2 elements) plus one
  *     block's work arrays exceeds the array returns SEMMG_ERR_UNSUPPORTED,
  *     with the sizes in semmg_last_error(ctx); larger work arrays only lower
- *     the number of blocks that run at once.
+ *     the number of blocks that run at once.  So does a level without a
+ *     usable star launch plan.
+ *   - A tensor-core completion wait that runs out sets the context's device
+ *     error flag, as in semmg_smooth; the next semmg_solve clears it.
  *   - Every call, on every context, shares the one array and it keeps the
  *     last call's contents; each call writes every scratch entry it later
  *     reads, so nothing has to start at zero.  Calls whose executions overlap
@@ -380,6 +400,9 @@ typedef struct {
   int64_t launches;  /* kernel launches of this class */
   double flops;      /* algorithmic flops of those launches */
   double bytes;      /* compulsory bytes of those launches */
+  double xflops;     /* operations those launches execute, from the kernels' own loop trip counts (adds,
+                        multiplies and divisions 1, fused multiply-adds 2); counted for the CUDA-core
+                        star kernel (SEMMG_K_STAR), 0 for the other classes */
 } semmg_kstat;
 
 /* Switch timing on (1) or off (0); switching resets the statistics. */
@@ -388,6 +411,30 @@ int semmg_set_timing(semmg_ctx* ctx, int enable);
  * with the last recorded event. */
 int semmg_get_kstat(semmg_ctx* ctx, int kind, semmg_kstat* out);
 int semmg_reset_kstats(semmg_ctx* ctx);
+
+/* ------------------------------------------------------------------ failure detection
+ * Limits of the two failure checks of a context.
+ *   divergence: semmg_solve (and the batched form) stops with
+ *     SEMMG_ERR_DIVERGED as soon as ||r|| > divergence ||r_0|| after an
+ *     iteration (default 1e3; > 0, +inf switches the check off).  A value below
+ *     the first iteration's reduction makes the check trip on the first
+ *     iteration, which is how the check itself is tested.
+ *   tc_wait_cycles: budget, in SM clock cycles, of each completion wait of the
+ *     tensor-core star smoother (default 4e9, about 2 s at 2 GHz; >= 0).  When
+ *     a wait runs out the kernel sets the context's device error flag, waits
+ *     (with the default budget) for the products it has in flight, frees its
+ *     tensor memory and returns; semmg_solve then returns SEMMG_ERR_TIMEOUT.
+ *     A budget of 0 makes every wait that is not already complete run out.
+ * The device error flag is cleared at the start of every semmg_solve, so the
+ * context stays usable.  Returns SEMMG_ERR_INVALID_ARG for a value out of range. */
+int semmg_set_guards(semmg_ctx* ctx, double divergence, long long tc_wait_cycles);
+
+/* Measured arithmetic peak of the current device in TFLOP/s: fused multiply-add
+ * chains (eight independent chains per thread, four 256-thread blocks per SM),
+ * dtype SEMMG_F64 or SEMMG_F32, one warm-up launch and one launch of about 10 ms
+ * timed with CUDA events on `stream` (synchronises it).  The denominator of the
+ * roofline fraction of ALU-bound kernels; no context needed. */
+int semmg_peak_tflops(int dtype, double* tflops, void* stream);
 
 /* Static message for an error code / last error message of a context. */
 const char* semmg_strerror(int code);

@@ -23,7 +23,7 @@ ERRORS = {
     -7: "SEMMG_ERR_NOMEM",
     -8: "SEMMG_ERR_DIVERGED",
 }
-SEMMG_ERR_NOT_CONVERGED, SEMMG_ERR_NONFINITE, SEMMG_ERR_DIVERGED = -4, -5, -8
+SEMMG_ERR_NOT_CONVERGED, SEMMG_ERR_NONFINITE, SEMMG_ERR_TIMEOUT, SEMMG_ERR_DIVERGED = -4, -5, -6, -8
 SEMMG_FP64, SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC = 0, 1, 2, 3, 4
 SEMMG_SOLVER_MG, SEMMG_SOLVER_KMG = 0, 1
 SEMMG_SMOOTHER_STAR, SEMMG_SMOOTHER_ELEMENT, SEMMG_SMOOTHER_ELEMENT_MULT = 0, 1, 2
@@ -42,7 +42,8 @@ class semmg_opts(ctypes.Structure):
 
 
 class semmg_kstat(ctypes.Structure):
-    _fields_ = [("ms", c_double), ("launches", c_int64), ("flops", c_double), ("bytes", c_double)]
+    _fields_ = [("ms", c_double), ("launches", c_int64), ("flops", c_double), ("bytes", c_double),
+                ("xflops", c_double)]
 
 
 KSTAT_KINDS = ["star", "star_gather", "elem_schur", "assemble", "transfer", "coarse", "condense", "recover",
@@ -95,6 +96,8 @@ SIGNATURES = {
     "semmg_set_timing": (c_int, [c_void_p, c_int]),
     "semmg_get_kstat": (c_int, [c_void_p, c_int, ctypes.POINTER(semmg_kstat)]),
     "semmg_reset_kstats": (c_int, [c_void_p]),
+    "semmg_set_guards": (c_int, [c_void_p, c_double, ctypes.c_longlong]),
+    "semmg_peak_tflops": (c_int, [c_int, ctypes.POINTER(c_double), c_void_p]),
     "semmg_strerror": (ctypes.c_char_p, [c_int]),
     "semmg_last_error": (ctypes.c_char_p, [c_void_p]),
 }

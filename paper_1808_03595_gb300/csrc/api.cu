@@ -1,5 +1,6 @@
 // C ABI of the semmg library: context setup (level hierarchy of Sec. 4.1),
 // buffer management and the orchestration of Algorithms 2-4 on one stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -29,7 +30,8 @@ using namespace semmg;
 
 namespace {
 
-// the outer iteration stops when ||r|| exceeds this multiple of ||r_0||
+// default of the divergence stop: the outer iteration ends when ||r|| exceeds
+// this multiple of ||r_0|| (semmg_set_guards changes it per context)
 constexpr double kDivergence = 1e3;
 
 
@@ -141,13 +143,16 @@ struct semmg_ctx {
   int* star_counter = nullptr;  // work counter of the star kernel (self-resetting)
   int* dev_err = nullptr;       // set by a kernel whose bounded device wait ran out
   int* hdev_err = nullptr;      // pinned copy
+  // failure-detection limits (semmg_set_guards)
+  double divergence = kDivergence;
+  long long tc_wait = kTcWaitDefault;
   // host-buffer solve
   double* fnod = nullptr;
   double* unod = nullptr;
   std::string err;
   // timing
   int timing = 0;
-  struct Pending { int kind; int ev; double flops, bytes; int64_t launches; };
+  struct Pending { int kind; int ev; double flops, bytes; int64_t launches; double xflops; };
   std::vector<cudaEvent_t> events;
   std::vector<Pending> pending;
   int ev_used = 0;
@@ -354,7 +359,7 @@ Tabs<T> upload_tabs(semmg_ctx* c, const Geo& G, const HostLevel& H, const std::v
     t.starCls[d] = dci;
     t.ncls[d] = (int)H.rep[d].size();
   }
-  t.Rtab = H.Rtab.empty() ? nullptr : upload<T>(c, H.Rtab, ok);
+  t.Rtab = nullptr;  // built by build_star_rtab (FP64 only)
   for (int d = 0; d < 3; ++d) {
     const std::vector<int>& hc = H.hcls[d];
     int* dhc = (int*)dalloc(c, hc.size() * sizeof(int));
@@ -410,6 +415,28 @@ void upload_tc_tables(semmg_ctx* c, const HostLevel& H, Tabs<float>& t, bool* ok
     t.tcN[d] = dN;
   }
 }
+
+// 1/(lam + Lam1[k1] + Lam2[k2] + Lam3[k3]) for every star class (class
+// (r1 n2c + r2) n3c + r3, layout [k3][k2][k1] per class), from the eigenvalues
+// of the classes' representative vertex lines; IEEE division, the sum in the
+// order lam + Lam1 + Lam2 + Lam3.
+__global__ void k_build_rtab(int nS, int n2c, int n3c, const int* __restrict__ rep1, const int* __restrict__ rep2,
+                             const int* __restrict__ rep3, const double* __restrict__ L1,
+                             const double* __restrict__ L2, const double* __restrict__ L3, double lam, int64_t total,
+                             double* __restrict__ R) {
+  const int64_t n3 = (int64_t)nS * nS * nS;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cls = i / n3, k = i - cls * n3;
+    const int k1 = (int)(k % nS), k2 = (int)((k / nS) % nS), k3 = (int)(k / ((int64_t)nS * nS));
+    const int r3 = (int)(cls % n3c), r2 = (int)((cls / n3c) % n2c), r1 = (int)(cls / ((int64_t)n3c * n2c));
+    R[i] = 1.0 / (lam + L1[(int64_t)rep1[r1] * nS + k1] + L2[(int64_t)rep2[r2] * nS + k2] +
+                  L3[(int64_t)rep3[r3] * nS + k3]);
+  }
+}
+
+// The FP64 star kernel's 1/D tables of a level (Tabs::Rtab), built on the device
+// when they have at most `cap` entries; otherwise the kernel divides.
+void build_star_rtab(semmg_ctx* c, const Geo& G, const HostLevel& H, Tabs<double>& t, size_t cap, bool* ok);
 
 int g_limits_done = 0;
 
@@ -479,12 +506,12 @@ struct Tic {
       if (ev >= 0) ev_record(c, ev, st);
     }
   }
-  void toc(double flops, double bytes, int64_t launches = 1) {
+  void toc(double flops, double bytes, int64_t launches = 1, double xflops = 0.0) {
     if (!c->timing || ev < 0) return;
     const int e1 = ev_get(c);
     if (e1 < 0) return;
     ev_record(c, e1, st);
-    (c->capturing ? c->step_pending : c->pending).push_back({kind, ev, flops, bytes, launches});
+    (c->capturing ? c->step_pending : c->pending).push_back({kind, ev, flops, bytes, launches, xflops});
   }
 };
 
@@ -502,6 +529,7 @@ void collect_step_timing(semmg_ctx* c) {
     k.launches += p.launches;
     k.flops += p.flops;
     k.bytes += p.bytes;
+    k.xflops += p.xflops;
   }
 }
 
@@ -517,9 +545,87 @@ void collect_timing(semmg_ctx* c) {
     k.launches += p.launches;
     k.flops += p.flops;
     k.bytes += p.bytes;
+    k.xflops += p.xflops;
   }
   c->pending.clear();
   c->ev_used = 0;
+}
+
+// Operations one launch of the CUDA-core star kernel (star_kernel.cuh) executes
+// on level l, from its loop trip counts: adds, multiplies and divisions count 1,
+// fused multiply-adds 2, as ncu counts FP64 thread instructions (a division counts
+// 1 here although the hardware runs it as several instructions).  Per star, from
+// the folding flag and active range of its three vertex lines: the gather, the
+// folds and unfolds, the grouped transforms (the backward ones run every lane of
+// a group), the eigenspace segments of every k3-slab (1/D from the table or by
+// division) with the contractions along the normals (in FP64 four lanes per
+// output and two combining adds per thread and round), and the weighted output.
+double star_exec_ops(const semmg_ctx* c, int l, bool fp64, int block) {
+  const Geo& G = c->geo[l];
+  const HostLevel& H = c->hl[l];
+  const int nS = G.nS, m = G.m, ts = star_slab_thickness(nS), kG = kStarGroup;
+  const bool rtab = fp64 && c->dl[l].td.Rtab != nullptr;
+  struct Line { int sym, lo, hi, pa; };
+  std::vector<Line> ln[3];
+  const int nv[3] = {G.nv1, G.nv2, G.nv3};
+  for (int d = 0; d < 3; ++d) {
+    ln[d].resize(nv[d]);
+    for (int cc = 0; cc < nv[d]; ++cc) {
+      const unsigned char* a = &H.act[d][(size_t)cc * nS];
+      int lo = 0, hi = nS;
+      while (lo < nS && !a[lo]) ++lo;
+      while (hi > lo && !a[hi - 1]) --hi;
+      ln[d][cc] = Line{H.sym[d][cc] ? 1 : 0, lo, hi, a[m] ? 1 : 0};
+    }
+  }
+  auto fwd = [&](int sy, int w) { return sy ? (double)(m + 1) * (m + 1) + (double)m * m : (double)w * w; };
+  auto bwd = [&](int sy, int w) {
+    if (sy) return (double)((m + kG) / kG) * kG * (m + 1) + (double)((m + kG - 1) / kG) * kG * m;
+    return (double)((w + kG - 1) / kG) * kG * w;
+  };
+  const double n2 = (double)nS * nS;
+  double total = 0.0;
+  for (int c3 = 0; c3 < G.nv3; ++c3)
+    for (int c2 = 0; c2 < G.nv2; ++c2)
+      for (int c1 = 0; c1 < G.nv1; ++c1) {
+        if ((G.per[0] && c1 == G.n1) || (G.per[1] && c2 == G.n2) || (G.per[2] && c3 == G.n3)) continue;
+        const Line L[3] = {ln[0][c1], ln[1][c2], ln[2][c3]};
+        int w[3];
+        for (int d = 0; d < 3; ++d) w[d] = L[d].hi - L[d].lo;
+        double ops = 0.0;
+        for (int dd = 0; dd < 3; ++dd) {
+          const int a = dd == 0 ? 1 : 0, b = dd == 2 ? 1 : 2;  // fast and slow in-plane axes
+          ops += 2.0 * (L[a].sym + L[b].sym) * nS * (nS - 1.0);  // folds and unfolds of all n_S^2 points
+          ops += 3.0 * n2;                                        // weights and weighted output
+          if (!L[dd].pa) continue;
+          ops += (double)w[a] * w[b];                             // gather: residual / multiplicity
+          ops += 2.0 * (w[b] * (fwd(L[a].sym, w[a]) + bwd(L[a].sym, w[a])) +
+                        w[a] * (fwd(L[b].sym, w[b]) + bwd(L[b].sym, w[b])));
+        }
+        int nz[3];
+        for (int d = 0; d < 3; ++d) nz[d] = L[d].pa ? (L[d].sym ? m + 1 : w[d]) : 0;
+        const double both = (double)nz[1] * nz[0], one = (double)nz[1] * (w[0] - nz[0]) + (double)(w[1] - nz[1]) * nz[0];
+        const double dead = L[2].pa ? (double)(w[1] - nz[1]) * (w[0] - nz[0]) : 0.0;
+        const double vop = rtab ? 1.0 : 4.0;  // E / D: the table's product, or the sum of D and a division
+        for (int k3s = L[2].lo; k3s < L[2].hi; k3s += ts) {
+          const int tn = std::min(ts, L[2].hi - k3s);
+          const int kl = std::min(std::max(L[2].lo + nz[2] - k3s, 0), tn);  // k3 with s3[k3] live
+          const double tail = nz[2] ? 1.0 : 0.0;
+          ops += both * (tn * (3.0 + vop) + kl * 4.0 + tail);
+          ops += one * (tn * (1.0 + vop) + kl * 4.0 + tail);
+          ops += dead * (kl * (rtab ? 2.0 : 5.0) + 2.0);
+          const double nb1 = L[0].pa ? (double)tn * w[1] : 0.0, nb2 = L[1].pa ? (double)tn * w[0] : 0.0;
+          ops += 2.0 * (nb1 * nz[0] + nb2 * nz[1]);
+          if (fp64) {
+            const double rounds = std::ceil(4.0 * (nb1 + nb2) / block);
+            ops += 2.0 * block * rounds;
+          } else {
+            ops += 3.0 * (nb1 + nb2);
+          }
+        }
+        total += ops;
+      }
+  return total;
 }
 
 // V-cycle in FP32 (the mixed forms)
@@ -606,14 +712,19 @@ void op_smooth(semmg_ctx* c, int l, const T* r, T* du, int accumulate, cudaStrea
   {
     Tic t(c, SEMMG_K_STAR, st);
     bool done = false;
+    double xf = 0.0;
     if constexpr (std::is_same<T, float>::value) {
       if (c->dl[l].startc.ok) {
-        launch_star_tc(G, c->dl[l].tf, r, (float*)c->Obs, c->dl[l].startc, c->star_counter, c->dev_err, st);
+        launch_star_tc(G, c->dl[l].tf, r, (float*)c->Obs, c->dl[l].startc, c->star_counter, c->dev_err,
+                       c->tc_wait, st);
         done = true;
       }
     }
-    if (!done) launch_star<T>(G, tabs<T>(c, l), r, (T*)c->Obs, (T*)c->wss, star_cfg<T>(c, l), c->star_counter, st);
-    t.toc(star_flops(G), vec + ob);
+    if (!done) {
+      launch_star<T>(G, tabs<T>(c, l), r, (T*)c->Obs, (T*)c->wss, star_cfg<T>(c, l), c->star_counter, st);
+      if (c->timing) xf = star_exec_ops(c, l, std::is_same<T, double>::value, star_cfg<T>(c, l).block);
+    }
+    t.toc(star_flops(G), vec + ob, 1, xf);
   }
   Tic t(c, SEMMG_K_STAR_GATHER, st);
   launch_star_gather<T>(G, (const T*)c->Obs, du, accumulate, st);
@@ -851,6 +962,36 @@ int dnorm_sync(semmg_ctx* c, cudaStream_t st, double* out) {
   return check_cuda(c, "norm");
 }
 
+void build_star_rtab(semmg_ctx* c, const Geo& G, const HostLevel& H, Tabs<double>& t, size_t cap, bool* ok) {
+  t.Rtab = nullptr;
+  const size_t nS = (size_t)G.nS, n3 = nS * nS * nS;
+  const size_t n2c = H.rep[1].size(), n3c = H.rep[2].size();
+  const size_t total = H.rep[0].size() * n2c * n3c * n3;
+  if (total == 0 || total > cap) return;
+  int* dr[3];
+  for (int d = 0; d < 3; ++d) {
+    dr[d] = (int*)dalloc(c, H.rep[d].size() * sizeof(int));
+    if (!dr[d] || cudaMemcpy(dr[d], H.rep[d].data(), H.rep[d].size() * sizeof(int), cudaMemcpyHostToDevice) !=
+                      cudaSuccess) {
+      *ok = false;
+      return;
+    }
+  }
+  double* R = (double*)dalloc(c, total * sizeof(double));
+  if (!R) {
+    *ok = false;
+    return;
+  }
+  k_build_rtab<<<4 * c->nsm, 256>>>(G.nS, (int)n2c, (int)n3c, dr[0], dr[1], dr[2], t.starLam[0], t.starLam[1],
+                                    t.starLam[2], G.lam, (int64_t)total, R);
+  // done before setup returns, whatever stream the caller orders its work on
+  if (cudaStreamSynchronize(0) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    *ok = false;
+    return;
+  }
+  t.Rtab = R;
+}
+
 int set_limits(semmg_ctx* c) {
   if (g_limits_done) return SEMMG_OK;
   if (set_elem_smem_limits() | set_star_smem_limits() | set_transfer_smem_limits() | set_star_tc_smem_limits() |
@@ -865,21 +1006,29 @@ int set_limits(semmg_ctx* c) {
 
 namespace semmg {
 
-// Star smoothing of one level (semmg_smooth's work) with the star output
-// buffer and the per-block work arrays placed in caller-provided device
-// memory instead of the context's scratch; the grid shrinks until the work
-// arrays fit.  Returns SEMMG_ERR_UNSUPPORTED when the level does not fit.
+// Star smoothing of one level (semmg_smooth's work, with the same kernels:
+// the tensor-core star kernel where semmg_smooth takes it, else the CUDA-core
+// one) with the star output buffer and the per-block work arrays placed in
+// caller-provided device memory instead of the context's scratch; the grid of
+// the CUDA-core kernel shrinks until its work arrays fit.  Returns
+// SEMMG_ERR_UNSUPPORTED when the level does not fit or its star launch plan is
+// unusable, SEMMG_ERR_INVALID_ARG for a scratch base that is not 256-byte aligned.
 int smooth_with_scratch(semmg_ctx* c, int level, int dtype, const void* r, void* du, void* scratch,
                         size_t scratch_bytes, cudaStream_t st) {
   if (!valid_level(c, level) || level < 1 || !r || !du || r == du || !scratch) return SEMMG_ERR_INVALID_ARG;
   if (dtype != SEMMG_F64 && dtype != SEMMG_F32) return SEMMG_ERR_INVALID_ARG;
+  if (((uintptr_t)scratch & 255u) != 0)
+    return fail(c, SEMMG_ERR_INVALID_ARG, "smooth_noalloc: scratch base is not 256-byte aligned");
   if (c->opts.smoother != SEMMG_SMOOTHER_STAR)
     return fail(c, SEMMG_ERR_UNSUPPORTED, "smooth_noalloc: vertex-star smoother only");
   const Geo& G = c->geo[level];
   const size_t es = dtype == SEMMG_F64 ? sizeof(double) : sizeof(float);
-  LaunchCfg cfg = dtype == SEMMG_F64 ? c->dl[level].star64 : c->dl[level].star32;
+  const bool tensor = dtype == SEMMG_F32 && c->dl[level].startc.ok;  // as op_smooth<float> decides
+  LaunchCfg cfg = dtype == SEMMG_F64 ? c->dl[level].star64 : (tensor ? c->dl[level].startc : c->dl[level].star32);
+  if (!cfg.ok)
+    return fail(c, SEMMG_ERR_UNSUPPORTED, "smooth_noalloc: no usable star launch plan on level %d", level);
   const size_t ob_bytes = ((size_t)G.nstar * 3 * G.nS * G.nS * es + 255) & ~size_t(255);
-  const size_t per_cta = (size_t)cfg.ws.gstride * es;
+  const size_t per_cta = tensor ? 0 : (size_t)cfg.ws.gstride * es;  // the tensor-core kernel has no work arrays
   if (ob_bytes > scratch_bytes)
     return fail(c, SEMMG_ERR_UNSUPPORTED,
                 "smooth_noalloc: level %d needs %zu bytes of star output buffer, more than the %zu-byte scratch",
@@ -898,8 +1047,11 @@ int smooth_with_scratch(semmg_ctx* c, int level, int dtype, const void* r, void*
                         nullptr, st);
     launch_star_gather<double>(G, (const double*)base, (double*)du, 0, st);
   } else {
-    launch_star<float>(G, c->dl[level].tf, (const float*)r, (float*)base, (float*)(base + ob_bytes), cfg, nullptr,
-                       st);
+    if (tensor)
+      launch_star_tc(G, c->dl[level].tf, (const float*)r, (float*)base, cfg, nullptr, c->dev_err, c->tc_wait, st);
+    else
+      launch_star<float>(G, c->dl[level].tf, (const float*)r, (float*)base, (float*)(base + ob_bytes), cfg, nullptr,
+                         st);
     launch_star_gather<float>(G, (const float*)base, (float*)du, 0, st);
   }
   return check_cuda(c, "smooth_noalloc");
@@ -998,6 +1150,11 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   for (int l = 0; l < nl; ++l) {
     c->dl[l].td = upload_tabs<double>(c.get(), c->geo[l], c->hl[l], c->h, &ok);
     c->dl[l].tf = upload_tabs<float>(c.get(), c->geo[l], c->hl[l], c->h, &ok);
+    // 1/D tables of the FP64 star kernel: always when small; up to kMaxStarRtabFp64 entries (GB on
+    // stretched meshes, where every vertex line is its own class) for the FP64 V-cycle
+    if (l >= 1 && ok && o.smoother == SEMMG_SMOOTHER_STAR)
+      build_star_rtab(c.get(), c->geo[l], c->hl[l], c->dl[l].td,
+                      o.precision == SEMMG_FP64 ? kMaxStarRtabFp64 : kMaxRtabEntries, &ok);
   }
   for (int d = 0; d < 3; ++d) {
     c->ct.K[d] = c->hc.K[d];
@@ -1258,6 +1415,7 @@ namespace {
 // condense, Algorithm 4 or 5 from u_hat = 0 (or E g), recover
 int solve_impl(semmg_ctx* c, const double* f, const double* g, double* u, double rtol, semmg_info* info,
                cudaStream_t st) {
+  cudaMemsetAsync(c->dev_err, 0, sizeof(int), st);  // a wait that ran out in an earlier call is not this one's
   condense_impl(c, f, c->Fh, true, st);
   int rc = check_cuda(c, "condense_rhs");
   if (rc) return rc;
@@ -1276,7 +1434,7 @@ int solve_impl(semmg_ctx* c, const double* f, const double* g, double* u, double
     ++it;
     if (!std::isfinite(rn))
       status = SEMMG_ERR_NONFINITE;
-    else if (rn > kDivergence * r0)
+    else if (rn > c->divergence * r0)
       status = SEMMG_ERR_DIVERGED;
   }
   if (status == SEMMG_OK && rn > rtol * r0) status = SEMMG_ERR_NOT_CONVERGED;
@@ -1372,6 +1530,14 @@ int semmg_reset_kstats(semmg_ctx* c) {
   return check_cuda(c, "reset_kstats");
 }
 
+int semmg_set_guards(semmg_ctx* c, double divergence, long long tc_wait_cycles) {
+  if (!c || !(divergence > 0.0) || tc_wait_cycles < 0) return SEMMG_ERR_INVALID_ARG;
+  c->divergence = divergence;
+  if (c->tc_wait != tc_wait_cycles) c->drop_step_graph();  // the captured launches hold the budget
+  c->tc_wait = tc_wait_cycles;
+  return SEMMG_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------- batched form (one CUDA graph)
@@ -1382,6 +1548,7 @@ struct BatchCtl {
   double res0sq;
   double ressq;
   double rtol;
+  double div;  // divergence factor of the solve's context
   int iters;
   int maxit;
   int status;
@@ -1413,7 +1580,7 @@ __global__ void k_batch_check(BatchCtl* ctl, const double* dnorm, cudaGraphCondi
   } else if (r <= ctl->rtol * ctl->rtol * ctl->res0sq) {
     ctl->status = SEMMG_OK;
     cont = 0u;
-  } else if (r > kDivergence * kDivergence * ctl->res0sq) {
+  } else if (r > ctl->div * ctl->div * ctl->res0sq) {
     ctl->status = SEMMG_ERR_DIVERGED;
     cont = 0u;
   } else if (ctl->iters >= ctl->maxit) {
@@ -1508,7 +1675,7 @@ int semmg_batch_create_dirichlet(semmg_ctx* const* ctxs, int nb, const double* c
     return SEMMG_ERR_NOMEM;
   }
   for (int i = 0; i < nb; ++i) {
-    b->hctl[i] = BatchCtl{0.0, 0.0, rtol, 0, ctxs[i]->opts.max_iter, 0, 0};
+    b->hctl[i] = BatchCtl{0.0, 0.0, rtol, ctxs[i]->divergence, 0, ctxs[i]->opts.max_iter, 0, 0};
   }
   if (cudaMemcpy(b->dctl, b->hctl, nb * sizeof(BatchCtl), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();

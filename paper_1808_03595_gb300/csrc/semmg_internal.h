@@ -57,6 +57,11 @@ SEMMG_HD int wrape(const Geo& G, int d, int a) {
 
 enum EntityType { ENT_F1 = 0, ENT_F2, ENT_F3, ENT_E1, ENT_E2, ENT_E3, ENT_V, ENT_NONE };
 
+// Star kernel constants shared with the host-side operation count: k3-planes of
+// the eigenspace held at once, and outputs per thread in the grouped transforms.
+SEMMG_HD int star_slab_thickness(int nS) { return nS <= 16 ? 8 : (nS <= 32 ? 4 : 2); }
+constexpr int kStarGroup = 4;
+
 SEMMG_HD int divp(const Geo& G, int g) {
   return (int)(((unsigned long long)(unsigned)g * G.pinv) >> 32);
 }
@@ -443,10 +448,13 @@ template <typename T> LaunchCfg plan_star(const Geo& G, int nsm, size_t cap = 0,
 template <typename T> void launch_star(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws,
                                        const LaunchCfg& c, int* counter, cudaStream_t st);
 // Star smoother with tensor-core transforms (FP32 / TF32, 15 <= n_S <= 64); err
-// is set to 1 when a tensor-core completion wait runs out.
+// is set to 1 when a tensor-core completion wait runs out (wait_budget clock
+// cycles per wait); the kernel then drains its products and returns.
 LaunchCfg plan_star_tc(const Geo& G, int nsm);
 void launch_star_tc(const Geo& G, const Tabs<float>& t, const float* r, float* Ob, const LaunchCfg& c, int* counter,
-                    int* err, cudaStream_t st);
+                    int* err, long long wait_budget, cudaStream_t st);
+// default budget of a tensor-core completion wait: about 2 s at 2 GHz
+constexpr long long kTcWaitDefault = 4000000000LL;
 int set_star_tc_smem_limits();
 template <typename T> void launch_star_gather(const Geo& G, const T* Ob, T* du, int accumulate,
                                               cudaStream_t st);

@@ -375,26 +375,8 @@ void build_level_tables(HostLevel& L, const std::vector<double>* h, const int* b
       }
     }
   }
-  // inverse 3D eigenvalues 1/(lam + Lam1 + Lam2 + Lam3) per star class, when small enough
-  {
-    const size_t n3 = (size_t)nS * nS * nS;
-    const size_t ncls = L.rep[0].size() * L.rep[1].size() * L.rep[2].size();
-    L.Rtab.clear();
-    if (ncls * n3 <= kMaxRtabEntries) {
-      L.Rtab.resize(ncls * n3);
-      size_t o = 0;
-      for (size_t r1 = 0; r1 < L.rep[0].size(); ++r1)
-        for (size_t r2 = 0; r2 < L.rep[1].size(); ++r2)
-          for (size_t r3 = 0; r3 < L.rep[2].size(); ++r3) {
-            const double* l1 = &L.starLam[0][(size_t)L.rep[0][r1] * nS];
-            const double* l2 = &L.starLam[1][(size_t)L.rep[1][r2] * nS];
-            const double* l3 = &L.starLam[2][(size_t)L.rep[2][r3] * nS];
-            for (int k3 = 0; k3 < nS; ++k3)
-              for (int k2 = 0; k2 < nS; ++k2)
-                for (int k1 = 0; k1 < nS; ++k1) L.Rtab[o++] = 1.0 / (L.lam + l1[k1] + l2[k2] + l3[k3]);
-          }
-    }
-  }
+  // the inverse 3D eigenvalues 1/(lam + Lam1 + Lam2 + Lam3) per star class are
+  // tabulated on the device at upload (the tables of stretched meshes reach GB)
   // element classes: elements with equal widths share their interior eigen-tables,
   // so 1/(lam + sum_d 4/h_d^2 Lam[k_d]) is tabulated per distinct width triple
   for (int d = 0; d < 3; ++d) {

@@ -6,8 +6,11 @@
 
 namespace semmg {
 
-// Largest number of inverse-eigenvalue entries precomputed per level.
+// Largest number of inverse-eigenvalue entries precomputed per level (element
+// and element-centred block classes; the star classes of an FP64 V-cycle may
+// take up to kMaxStarRtabFp64 entries, built on the device).
 constexpr size_t kMaxRtabEntries = size_t(1) << 25;
+constexpr size_t kMaxStarRtabFp64 = size_t(1) << 29;
 
 struct HostLevel {
   int p = 0;
@@ -21,7 +24,6 @@ struct HostLevel {
   std::vector<unsigned char> act[3];
   std::vector<unsigned char> sym[3];               // per vertex line: centrosymmetric (folded) tables
   std::vector<int> cls[3], rep[3];                 // line class per vertex line, representative line per class
-  std::vector<double> Rtab;                        // per star class [k3][k2][k1]: 1/(lam + Lam1 + Lam2 + Lam3)
   std::vector<double> w1d;                         // smoother weights at |offset|
   std::vector<double> J;                           // interpolation from the next coarser level
   int pc = 0;

@@ -44,7 +44,7 @@ __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
 
 // k3-planes of the eigenspace held at once.
-__host__ __device__ __forceinline__ int slab_thickness(int nS) { return nS <= 16 ? 8 : (nS <= 32 ? 4 : 2); }
+__host__ __device__ __forceinline__ int slab_thickness(int nS) { return star_slab_thickness(nS); }
 
 // The n pairs j = o2 w + o1 of a segment, j strided by the block: the thread's
 // first pair and the block-size step, decoded once per star (integer division
@@ -112,7 +112,7 @@ __device__ __forceinline__ void fold_pass(int nS, int m, const int* sym, int alo
 
 // ---- grouped passes: each thread computes kG outputs of one line that share
 // the input loads (kG independent multiply-add chains per thread).
-constexpr int kG = 4;
+constexpr int kG = kStarGroup;
 
 // Output block of group g on a line: [k0, k1) and the input range of that block.
 struct Block {

@@ -84,12 +84,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
   return ok != 0;
 }
 
-// wait for the phase with the given parity, at most `budget` clock cycles
+// non-blocking probe: has the phase with the given parity completed?
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// wait for the phase with the given parity, at most `budget` clock cycles: one
+// non-blocking probe, then potentially blocking probes while the budget lasts (a
+// try_wait may suspend the thread until the phase completes, so a budget of a
+// few cycles still ends after the first probe when the products are in flight)
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long long budget) {
   const long long t0 = clock64();
-  while (!mbar_try_wait(mbar, parity))
-    if (clock64() - t0 > budget) return false;
-  return true;
+  if (mbar_test_wait(mbar, parity)) return true;
+  while (clock64() - t0 <= budget)
+    if (mbar_try_wait(mbar, parity)) return true;
+  return false;
 }
 
 // tensor-memory load: thread l of the warp reads lane (quadrant base + l), 16 consecutive columns
@@ -123,7 +138,9 @@ __device__ __forceinline__ int coff(int row, int k, int np) {
 
 namespace {
 
-constexpr long long kTcWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+// bound of the wait for products still in flight after an abort (about 2 s at
+// 2 GHz); the completion waits of the normal rounds take the caller's budget
+constexpr long long kTcWaitCycles = 4000000000LL;
 
 __host__ __device__ __forceinline__ int tc_np(int nS) { return (nS + 15) / 16 * 16; }
 __host__ __device__ __forceinline__ int tc_ld(int np) { return np + 4; }  // row stride of the eigenspace planes
@@ -152,7 +169,8 @@ __device__ __forceinline__ void tc_product(uint32_t tmem, int col, const float* 
 
 template <int PC>
 __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const float* __restrict__ r,
-                                                     float* __restrict__ Ob, int* counter, int* err) {
+                                                     float* __restrict__ Ob, int* counter, int* err,
+                                                     long long wait_budget) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint64_t s_mbar;
   __shared__ uint32_t s_tmem;
@@ -197,7 +215,7 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
       issue();
       tc::mma_commit(&s_mbar);
     }
-    const bool ok = tc::mbar_wait(&s_mbar, phase, kTcWaitCycles);
+    const bool ok = tc::mbar_wait(&s_mbar, phase, wait_budget);
     phase ^= 1u;
     if (!ok) {
       s_abort = 1;
@@ -512,12 +530,12 @@ LaunchCfg plan_star_tc(const Geo& G, int nsm) {
 }
 
 void launch_star_tc(const Geo& G, const Tabs<float>& t, const float* r, float* Ob, const LaunchCfg& c, int* counter,
-                    int* err, cudaStream_t st) {
+                    int* err, long long wait_budget, cudaStream_t st) {
   if (G.nstar == 0 || !c.ok) return;
   switch (G.p) {
-    case 16: k_star_tc<16><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err); break;
-    case 32: k_star_tc<32><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err); break;
-    default: k_star_tc<0><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err); break;
+    case 16: k_star_tc<16><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err, wait_budget); break;
+    case 32: k_star_tc<32><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err, wait_budget); break;
+    default: k_star_tc<0><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err, wait_budget); break;
   }
 }
 

@@ -233,6 +233,11 @@ class Context:
                                                L.SEMMG_F32 if dtype == torch.float32 else L.SEMMG_F64,
                                                int(smem_cap), int(block), int(max_regs)))
 
+    # ------------------------------------------------------------ failure detection
+    def set_guards(self, divergence=1e3, tc_wait_cycles=4_000_000_000):
+        """Divergence factor of the outer iteration and the budget of each tensor-core wait (semmg_set_guards)."""
+        self._check(self._lib.semmg_set_guards(self._ctx, float(divergence), int(tc_wait_cycles)))
+
     # ------------------------------------------------------------ timing
     def set_timing(self, enable=True):
         self._check(self._lib.semmg_set_timing(self._ctx, 1 if enable else 0))
@@ -246,7 +251,7 @@ class Context:
         for i, name in enumerate(L.KSTAT_KINDS):
             k = L.semmg_kstat()
             self._check(self._lib.semmg_get_kstat(self._ctx, i, ctypes.byref(k)))
-            out[name] = {"ms": k.ms, "launches": k.launches, "flops": k.flops, "bytes": k.bytes}
+            out[name] = {"ms": k.ms, "launches": k.launches, "flops": k.flops, "bytes": k.bytes, "xflops": k.xflops}
         return out
 
 
@@ -300,3 +305,14 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def peak_tflops(dtype=torch.float64, stream=None):
+    """Measured FMA-chain peak of the current device in TFLOP/s (semmg_peak_tflops)."""
+    lib = L.load()
+    out = ctypes.c_double()
+    rc = lib.semmg_peak_tflops(L.SEMMG_F64 if dtype == torch.float64 else L.SEMMG_F32, ctypes.byref(out),
+                               _stream(stream))
+    if rc != 0:
+        raise SemmgError(rc, "peak_tflops")
+    return out.value

@@ -100,3 +100,11 @@ def test_setup_rejects_bad_arguments_without_touching_the_gpu(lib):
     mesh.h[0] = hbad.ctypes.data_as(L.P_double)
     assert lib.semmg_setup(ctypes.byref(mesh), 4, 1.0, None, None, ctypes.byref(ctx)) == -1
     assert not ctx.value
+
+
+def test_guards_and_peak_probe_reject_bad_arguments_without_a_gpu(lib):
+    import ctypes as C
+    assert lib.semmg_set_guards(None, 1e3, 10) == -1
+    out = C.c_double()
+    assert lib.semmg_peak_tflops(7, C.byref(out), None) == -1
+    assert lib.semmg_peak_tflops(0, None, None) == -1

@@ -13,6 +13,9 @@ Workloads (names used by bench.py and the tests):
   poisson_6x6x6_p48_stretched
                           lambda = 0, per-axis widths exp(U(0, ln 8)) normalised to 1 (seed 1808035954),
                           manufactured f
+  poisson_2x2x2_p48_stretched
+                          the same degree, width law, seed and f on 2 x 2 x 2 elements: the bounded
+                          sample of the 6^3 workload that the oracle is timed on
   expansion_widths(n, alpha)
                           per-axis widths in geometric progression on (0, 2 pi), the stretched
                           meshes of the paper's iteration-count table (Sec. 5.4)
@@ -153,8 +156,8 @@ def config(name, p=None, lam=None):
         lam = 0.0 if lam is None else lam
         h = uniform_widths(16)
         return h, 16, lam, random_nodal(h, 16, SEED_CFG3, "uniform"), 2
-    if name == "poisson_6x6x6_p48_stretched":
-        h = stretched_widths(6)
+    if name in ("poisson_6x6x6_p48_stretched", "poisson_2x2x2_p48_stretched"):
+        h = stretched_widths(int(name.split("_")[1][0]))
         return h, 48, 0.0, manufactured_rhs(h, 48, 0.0), 2
     raise KeyError(name)
 
