@@ -47,11 +47,12 @@ SWEEP = [4, 8, 16, 32]
 METRIC = "unknowns/s per solve to 1e-10 residual (FP64 vs mixed); smoother HBM GB/s"
 # timed forms: name -> (precision, outer iteration, smoother)
 FORMS = {"fp64": ("fp64", "mg", "star"), "mixed": ("mixed", "mg", "star"), "mixed_tc": ("mixed_tc", "mg", "star"),
+         "mixed_bf16": ("mixed_bf16", "mg", "star"),
          "mixed_fp32": ("mixed_fp32", "mg", "star"), "mixed_fp32_tc": ("mixed_fp32_tc", "mg", "star"),
          "kmg_fp64": ("fp64", "kmg", "star"), "kmg_mixed": ("mixed", "kmg", "star"),
          "kmg_mixed_tc": ("mixed_tc", "kmg", "star"), "eblock_fp64": ("fp64", "mg", "element"),
          "eblock_mixed": ("mixed", "mg", "element")}
-MIXED_FORMS = ("mixed", "mixed_tc")          # candidates for the result line's `mixed`
+MIXED_FORMS = ("mixed", "mixed_tc", "mixed_bf16")  # candidates for the result line's `mixed`
 DETAIL_FORMS = ("kmg_fp64", "kmg_mixed", "kmg_mixed_tc", "mixed_fp32", "mixed_fp32_tc")
 FP64_NOMINAL_TFLOPS = 1.25  # 2 FP64 FMA / clock / SM x 152 SMs x 2.07 GHz: fallback when the probe fails
 # DRAM bytes (read + write) per k_star<double> launch of the headline workload, from the ncu
@@ -431,8 +432,8 @@ def result_line(value, steps, warmup, ms_total, unknowns, p0, world, iterations,
 
 
 def run_sweep(args, dev, stream, flush, details):
-    """Helmholtz lambda = 1 on 8^3 uniform elements, p in {4, 8, 16, 32}: FP64 and the mixed form,
-    one step = the four solves; unknowns/s over the K timed steps."""
+    """Helmholtz lambda = 1 on 8^3 uniform elements, p in {4, 8, 16, 32}: FP64 and two mixed forms (CUDA-core
+    and tensor-core smoother), one step = the four solves; unknowns/s over the K timed steps."""
     import torch
     from paper_1808_03595_gb300 import Context
     out = {}
@@ -441,10 +442,10 @@ def run_sweep(args, dev, stream, flush, details):
         h, q, lam, f, p0 = workloads.config(f"helmholtz_8x8x8_p{q}")
         fd = torch.as_tensor(f, dtype=torch.float64, device=dev)
         cases.append((q, fd, torch.empty_like(fd), {form: Context(h, q, lam, p0=p0, precision=FORMS[form][0])
-                                                    for form in ("fp64", "mixed")}))
+                                                    for form in ("fp64", "mixed", "mixed_tc")}))
     n = sum(int(c[1].numel()) for c in cases)
     table = {}
-    for form in ("fp64", "mixed"):
+    for form in ("fp64", "mixed", "mixed_tc"):
         for q, fd, ud, cx in cases:
             if args.autotune:
                 cx[form].autotune()

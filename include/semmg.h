@@ -92,10 +92,19 @@ enum {
  *   SEMMG_MIXED_FP32  the whole V-cycle in FP32, level residuals included;
  *   SEMMG_MIXED_TC    as SEMMG_MIXED, with the star smoother's 1D transforms on
  *                     tensor cores (tcgen05, TF32 operands, FP32 accumulation)
- *                     on the levels with 16 <= p <= 32; other levels as SEMMG_MIXED;
+ *                     on the levels with 16 <= p <= 48; other levels as SEMMG_MIXED;
  *   SEMMG_MIXED_FP32_TC  as SEMMG_MIXED_FP32, with the tensor-core smoother of
- *                     SEMMG_MIXED_TC on the levels it covers. */
-enum { SEMMG_FP64 = 0, SEMMG_MIXED = 1, SEMMG_MIXED_FP32 = 2, SEMMG_MIXED_TC = 3, SEMMG_MIXED_FP32_TC = 4 };
+ *                     SEMMG_MIXED_TC on the levels it covers;
+ *   SEMMG_MIXED_BF16  as SEMMG_MIXED_TC with BF16 operands (8-bit significand,
+ *                     FP32 accumulation) in the tensor-core transforms. */
+enum {
+  SEMMG_FP64 = 0,
+  SEMMG_MIXED = 1,
+  SEMMG_MIXED_FP32 = 2,
+  SEMMG_MIXED_TC = 3,
+  SEMMG_MIXED_FP32_TC = 4,
+  SEMMG_MIXED_BF16 = 5
+};
 /* outer iteration of semmg_solve and of the batched form */
 enum { SEMMG_SOLVER_MG = 0, SEMMG_SOLVER_KMG = 1 };
 /* Schwarz smoother of the V-cycle levels */
@@ -128,7 +137,8 @@ typedef struct {
   int p0;          /* coarse degree, 1 <= p0 <= p (default 2, Sec. 4.1) */
   int nu_pre;      /* pre-smoothing steps per level (default 1, Algorithm 3) */
   int nu_post;     /* post-smoothing steps per level (default 1) */
-  int precision;   /* SEMMG_FP64 (default), SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC or SEMMG_MIXED_FP32_TC */
+  int precision;   /* SEMMG_FP64 (default), SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC
+                      or SEMMG_MIXED_BF16 */
   int max_iter;    /* iteration cap of semmg_solve (default 50) */
   int solver;      /* SEMMG_SOLVER_MG (Algorithm 4, default) or SEMMG_SOLVER_KMG (Algorithm 5) */
   int nu_vary;     /* 0 (default): nu_pre / nu_post steps on every level; 1: nu_pre 2^(L-l) and
@@ -321,7 +331,9 @@ int semmg_autotune(semmg_ctx* ctx, void* stream);
 /* Launch shape in use for `kernel` (0 = star smoother, 1 = element Schur
  * kernel) at `level` in element type dtype (SEMMG_F64 / SEMMG_F32):
  * threads per block, dynamic shared memory, blocks, and the register budget
- * per thread of the kernel build that runs (64 or 128). */
+ * per thread of the kernel build that runs (64 or 128).  On the levels where
+ * a tensor-core form runs the FP32 star smoother on the tensor cores, the
+ * shape of that kernel (which autotuning leaves as it is). */
 int semmg_get_launch(const semmg_ctx* ctx, int level, int kernel, int dtype, int* block, int* smem_bytes, int* grid,
                      int* max_regs);
 /* Pin the launch shape of `kernel` at `level` in dtype: a shared-memory budget
@@ -343,7 +355,7 @@ int semmg_set_launch(semmg_ctx* ctx, int level, int kernel, int dtype, int smem_
  * semmg_smooth_noalloc computes exactly what semmg_smooth computes (du_hat =
  * Smoother(r_hat) on `level`, bitwise the same result) with the same kernels:
  * the CUDA-core star kernel, or for dtype SEMMG_F32 on the levels where the
- * context's precision (SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC) puts the star
+ * context's precision (SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC, SEMMG_MIXED_BF16) puts the star
  * transforms on the tensor cores, the tensor-core star kernel.  It calls no
  * cudaMalloc, cudaFree or other allocating routine: the star output buffer and
  * the per-block work arrays come from one array of SEMMG_NOALLOC_SCRATCH_BYTES

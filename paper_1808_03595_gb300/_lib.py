@@ -24,7 +24,7 @@ ERRORS = {
     -8: "SEMMG_ERR_DIVERGED",
 }
 SEMMG_ERR_NOT_CONVERGED, SEMMG_ERR_NONFINITE, SEMMG_ERR_TIMEOUT, SEMMG_ERR_DIVERGED = -4, -5, -6, -8
-SEMMG_FP64, SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC = 0, 1, 2, 3, 4
+SEMMG_FP64, SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC, SEMMG_MIXED_BF16 = 0, 1, 2, 3, 4, 5
 SEMMG_SOLVER_MG, SEMMG_SOLVER_KMG = 0, 1
 SEMMG_SMOOTHER_STAR, SEMMG_SMOOTHER_ELEMENT, SEMMG_SMOOTHER_ELEMENT_MULT = 0, 1, 2
 SEMMG_BC_DIRICHLET, SEMMG_BC_NEUMANN, SEMMG_BC_PERIODIC = 0, 1, 2

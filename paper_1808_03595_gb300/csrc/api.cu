@@ -42,7 +42,7 @@ struct DevLevel {
   void* Uw = nullptr;
   void* Rw = nullptr;
   LaunchCfg schur64, schur32, star64, star32;
-  LaunchCfg startc;  // tensor-core star smoother (SEMMG_MIXED_TC, _FP32_TC), when the level allows it
+  LaunchCfg startc;  // tensor-core star smoother (SEMMG_MIXED_TC, _FP32_TC, _BF16), when the level allows it
   LaunchCfg eb64, eb32;  // element-centred block smoother (SEMMG_SMOOTHER_ELEMENT)
 };
 
@@ -62,9 +62,19 @@ float round_tf32(double x) {
   return f;
 }
 
-// float offset of (row, k) in a K-major tensor-core operand with K = np
-size_t tc_off(int row, int k, int np) {
-  return ((size_t)(row >> 3) * (np >> 2) + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3);
+// IEEE float rounded to BF16 (7 stored mantissa bits), nearest-even: the bit pattern
+uint16_t round_bf16_bits(double x) {
+  float f = (float)x;
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  if ((b & 0x7F800000u) != 0x7F800000u) b += 0x7FFFu + ((b >> 16) & 1u);
+  return (uint16_t)(b >> 16);
+}
+
+// element offset of (row, k) in a K-major tensor-core operand with K = np and E
+// elements per 16-byte core-matrix row (4 for TF32, 8 for BF16)
+size_t tc_off(int row, int k, int np, int E) {
+  return ((size_t)(row >> 3) * (np / E) + (k / E)) * (8 * E) + (row & 7) * E + (k % E);
 }
 
 Geo make_geo(const int n[3], int p, double lam, const int bc[6]) {
@@ -390,29 +400,51 @@ Tabs<T> upload_tabs(semmg_ctx* c, const Geo& G, const HostLevel& H, const std::v
   return t;
 }
 
-// Tensor-core operand tables T(S) and N(S) per axis and line class (TF32).
-void upload_tc_tables(semmg_ctx* c, const HostLevel& H, Tabs<float>& t, bool* ok) {
-  const int nS = 2 * H.p - 1, np = tc_pad(nS);
+// Tensor-core operand tables T(S) and N(S) per axis and line class, TF32 or BF16.
+void upload_tc_tables(semmg_ctx* c, const HostLevel& H, Tabs<float>& t, bool bf16, bool* ok) {
+  const int nS = 2 * H.p - 1, np = tc_pad(nS), E = bf16 ? 8 : 4;
   const size_t tb = (size_t)np * np;
   for (int d = 0; d < 3; ++d) {
     const size_t ncls = H.rep[d].size();
-    std::vector<float> T(ncls * tb, 0.0f), N(ncls * tb, 0.0f);
+    std::vector<float> T, N;
+    std::vector<uint16_t> Tb, Nb;
+    if (bf16) {
+      Tb.assign(ncls * tb, 0);
+      Nb.assign(ncls * tb, 0);
+    } else {
+      T.assign(ncls * tb, 0.0f);
+      N.assign(ncls * tb, 0.0f);
+    }
     for (size_t r = 0; r < ncls; ++r) {
       const double* S = &H.starS[d][(size_t)H.rep[d][r] * nS * nS];
       for (int j = 0; j < nS; ++j)
         for (int e = 0; e < nS; ++e) {
-          const float v = round_tf32(S[j * nS + e]);
-          T[r * tb + tc_off(e, j, np)] = v;
-          N[r * tb + tc_off(j, e, np)] = v;
+          if (bf16) {
+            const uint16_t v = round_bf16_bits(S[j * nS + e]);
+            Tb[r * tb + tc_off(e, j, np, E)] = v;
+            Nb[r * tb + tc_off(j, e, np, E)] = v;
+          } else {
+            const float v = round_tf32(S[j * nS + e]);
+            T[r * tb + tc_off(e, j, np, E)] = v;
+            N[r * tb + tc_off(j, e, np, E)] = v;
+          }
         }
     }
-    float* dT = (float*)dalloc(c, T.size() * sizeof(float));
-    float* dN = (float*)dalloc(c, N.size() * sizeof(float));
-    if (!dT || !dN || cudaMemcpy(dT, T.data(), T.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(dN, N.data(), N.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    const size_t bytes = ncls * tb * (bf16 ? 2 : 4);
+    void* dT = dalloc(c, bytes);
+    void* dN = dalloc(c, bytes);
+    const void* hT = bf16 ? (const void*)Tb.data() : (const void*)T.data();
+    const void* hN = bf16 ? (const void*)Nb.data() : (const void*)N.data();
+    if (!dT || !dN || cudaMemcpy(dT, hT, bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dN, hN, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
       *ok = false;
-    t.tcT[d] = dT;
-    t.tcN[d] = dN;
+    if (bf16) {
+      t.bfT[d] = (const unsigned short*)dT;
+      t.bfN[d] = (const unsigned short*)dN;
+    } else {
+      t.tcT[d] = (const float*)dT;
+      t.tcN[d] = (const float*)dN;
+    }
   }
 }
 
@@ -632,7 +664,8 @@ double star_exec_ops(const semmg_ctx* c, int l, bool fp64, int block) {
 bool cycle32(const semmg_ctx* c) { return c->opts.precision != SEMMG_FP64; }
 // FP32 V-cycle whose level residuals are formed in FP64
 bool resid64(const semmg_ctx* c) {
-  return c->opts.precision == SEMMG_MIXED || c->opts.precision == SEMMG_MIXED_TC;
+  return c->opts.precision == SEMMG_MIXED || c->opts.precision == SEMMG_MIXED_TC ||
+         c->opts.precision == SEMMG_MIXED_BF16;
 }
 
 // out = F - Hhat u (mode 0) or Hhat u (mode 1) on level l with arithmetic in T
@@ -1086,7 +1119,7 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   if (!(lambda >= 0.0) || !std::isfinite(lambda)) return SEMMG_ERR_INVALID_ARG;
   if (o.nu_pre < 0 || o.nu_post < 0 || o.max_iter < 1) return SEMMG_ERR_INVALID_ARG;
   if (o.precision != SEMMG_FP64 && o.precision != SEMMG_MIXED && o.precision != SEMMG_MIXED_FP32 &&
-      o.precision != SEMMG_MIXED_TC && o.precision != SEMMG_MIXED_FP32_TC)
+      o.precision != SEMMG_MIXED_TC && o.precision != SEMMG_MIXED_FP32_TC && o.precision != SEMMG_MIXED_BF16)
     return SEMMG_ERR_INVALID_ARG;
   if (o.solver != SEMMG_SOLVER_MG && o.solver != SEMMG_SOLVER_KMG) return SEMMG_ERR_INVALID_ARG;
   if (o.nu_vary != 0 && o.nu_vary != 1) return SEMMG_ERR_INVALID_ARG;
@@ -1185,10 +1218,13 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
         const int64_t nE = 3 * (int64_t)G.p - 1;
         obs = std::max(obs, (size_t)(G.nelem * 6 * nE * nE));
       }
-      if ((o.precision == SEMMG_MIXED_TC || o.precision == SEMMG_MIXED_FP32_TC) && o.smoother == SEMMG_SMOOTHER_STAR) {
-        D.startc = plan_star_tc(G, c->nsm);
+      const bool tcform = o.precision == SEMMG_MIXED_TC || o.precision == SEMMG_MIXED_FP32_TC ||
+                          o.precision == SEMMG_MIXED_BF16;
+      if (tcform && o.smoother == SEMMG_SMOOTHER_STAR) {
+        const bool bf16 = o.precision == SEMMG_MIXED_BF16;
+        D.startc = plan_star_tc(G, c->nsm, bf16 ? 1 : 0);
         if (D.startc.ok) {
-          upload_tc_tables(c.get(), c->hl[l], D.tf, &ok);
+          upload_tc_tables(c.get(), c->hl[l], D.tf, bf16, &ok);
           if (!ok) return SEMMG_ERR_NOMEM;
         }
       }
@@ -1237,7 +1273,7 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     c->Uts = dalloc(c.get(), (size_t)c->geo[nl - 1].oE1 * sizeof(double));
     if (!c->Uts) return SEMMG_ERR_NOMEM;
   }
-  if (o.precision == SEMMG_MIXED || o.precision == SEMMG_MIXED_TC) {
+  if (o.precision == SEMMG_MIXED || o.precision == SEMMG_MIXED_TC || o.precision == SEMMG_MIXED_BF16) {
     c->U64s = (double*)dalloc(c.get(), nL * sizeof(double));
     if (!c->U64s) return SEMMG_ERR_NOMEM;
   }
@@ -1929,7 +1965,7 @@ extern "C" int semmg_get_launch(const semmg_ctx* c, int level, int kernel, int d
     return SEMMG_ERR_INVALID_ARG;
   const DevLevel& D = c->dl[level];
   const LaunchCfg* cf;
-  if (kernel == 0) cf = dtype == SEMMG_F32 ? &D.star32 : &D.star64;
+  if (kernel == 0) cf = dtype == SEMMG_F32 ? (D.startc.ok ? &D.startc : &D.star32) : &D.star64;
   else cf = dtype == SEMMG_F32 ? &D.schur32 : &D.schur64;
   *block = cf->block;
   *smem = (int)cf->smem;

@@ -1,6 +1,5 @@
 // FP32 instantiation of the star smoother kernels (the V-cycle of the mixed form).
 #include "star_kernel.cuh"
-#include "star_tc.cuh"
 
 namespace semmg {
 

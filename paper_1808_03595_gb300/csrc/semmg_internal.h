@@ -280,11 +280,14 @@ struct Tabs {
   const T* w1d;    // m+1: smoother weight at offset |j| (Sec. 3.2, weights)
   const T* J;      // (p+1) x (pc+1) interpolation from level-1, row-major; null on level 0
   int pc;
-  // tensor-core star tables (FP32 levels of the SEMMG_MIXED_TC form, else null):
-  // per axis and line class, T(S)[e][j] = S[j][e] and N(S)[j][e] = S[j][e] as
-  // K-major TF32 operands (8 x 4 core matrices), n_S rounded up to 16 and zero-padded
+  // tensor-core star tables (FP32 levels of the tensor-core forms, else null): per
+  // axis and line class, T(S)[e][j] = S[j][e] and N(S)[j][e] = S[j][e] as K-major
+  // operands (core matrices of 8 rows x 16 bytes), n_S rounded up to 16 and
+  // zero-padded: TF32 (tcT, tcN) or BF16 bit patterns (bfT, bfN)
   const T* tcT[3];
   const T* tcN[3];
+  const unsigned short* bfT[3];
+  const unsigned short* bfN[3];
   // element-centred blocks (Sec. 3.4), when that smoother is selected (else null): per axis
   // n_d block lines of nE x nE eigenvectors S[j][k], nE eigenvalues and nE weight factors
   // (nE = 3p - 1)
@@ -328,6 +331,7 @@ struct LaunchCfg {
   // (1024 resident threads per SM), 1 = at most 128 (512 resident threads)
   int wide = 0;
   int depth = 0;                 // element-block kernel: k3-planes of the eigenspace slab
+  int bf16 = 0;                  // tensor-core star kernel: BF16 operands (else TF32)
   size_t ws_elems() const {
     return (size_t)ws.gstride * (size_t)grid;
   }
@@ -447,10 +451,11 @@ int set_eblock_smem_limits();
 template <typename T> LaunchCfg plan_star(const Geo& G, int nsm, size_t cap = 0, int block = 0, int wide = -1);
 template <typename T> void launch_star(const Geo& G, const Tabs<T>& t, const T* r, T* Ob, T* ws,
                                        const LaunchCfg& c, int* counter, cudaStream_t st);
-// Star smoother with tensor-core transforms (FP32 / TF32, 15 <= n_S <= 64); err
-// is set to 1 when a tensor-core completion wait runs out (wait_budget clock
-// cycles per wait); the kernel then drains its products and returns.
-LaunchCfg plan_star_tc(const Geo& G, int nsm);
+// Star smoother with tensor-core transforms (FP32 data, TF32 or BF16 operands,
+// 31 <= n_S <= 95); err is set to 1 when a tensor-core completion wait runs out
+// (wait_budget clock cycles per wait); the kernel then drains its products and
+// returns.
+LaunchCfg plan_star_tc(const Geo& G, int nsm, int bf16);
 void launch_star_tc(const Geo& G, const Tabs<float>& t, const float* r, float* Ob, const LaunchCfg& c, int* counter,
                     int* err, long long wait_budget, cudaStream_t st);
 // default budget of a tensor-core completion wait: about 2 s at 2 GHz

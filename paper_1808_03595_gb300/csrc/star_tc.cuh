@@ -1,24 +1,45 @@
 // Star smoother with the in-plane 1D transforms on the 5th-generation tensor
-// cores (tcgen05, TF32 operands, FP32 accumulators in tensor memory); the
-// eigenspace step (expansion along the normals, 1/D, contractions back) stays
-// on the FP32 cores.  Same mathematics as k_star (Algorithm 1 inside
-// Algorithm 2, Sec. 3.2); used by the SEMMG_MIXED_TC form for 31 <= 2p-1 <= 64.
+// cores (tcgen05, FP32 accumulators in tensor memory), TF32 or BF16 operands;
+// the eigenspace step (expansion along the normals, 1/D, contractions back)
+// stays on the FP32 cores.  Same mathematics as k_star (Algorithm 1 inside
+// Algorithm 2, Sec. 3.2); used by the tensor-core mixed forms for
+// 31 <= n_S = 2p-1 <= 95 (16 <= p <= 48).
 //
-// A plane transform S_b^T X S_a is two dense products per plane, run as
-// D[M=128][N] += A[M][K] B[N][K] (K-major operands in shared memory, 8 rows x
-// 16 bytes core matrices, no swizzle), with K = N = NP = n_S rounded up to 16:
-//   forward, along the slow axis:  W  = T(S_b) . P^T     (planes 0 and 1 share
-//                                   the x3 tables and are stacked along N)
-//   forward, along the fast axis:  Z  = W . T(S_a)
-//   backward, slow axis:           O  = N(S_b) . B^T     (B: eigenspace result)
-//   backward, fast axis:           Y  = O . N(S_a)
-// with T(S)[e][j] = S[j][e] and N(S)[j][e] = S[j][e] prepared at setup, rounded
-// to TF32.  Rows 64..127 of every M = 128 product are padding (their input rows
-// are other data in shared memory; their outputs are not read).
+// A plane transform S_b^T X S_a is two dense products per plane, each run as
+// D[M=128][N] += A[M][K] B[N][K] (K-major operands in shared memory, core
+// matrices of 8 rows x 16 bytes, no swizzle) with K = N = NP = n_S rounded up
+// to 16; rows NP..127 of every product are padding (they read whatever shared
+// memory follows the A operand; their outputs are never read):
+//   forward, slow axis:  W  = T(S_b) . P^T     (planes 0 and 1 share the x3
+//                                              tables and are stacked along N)
+//   forward, fast axis:  Z  = W . T(S_a)
+//   backward, slow axis: O  = N(S_b) . B^T     (B: eigenspace result; one
+//                                              plane at a time)
+//   backward, fast axis: Y  = O . N(S_a)
+// with T(S)[e][j] = S[j][e] and N(S)[j][e] = S[j][e] prepared at setup in the
+// operand type.
+//
+// Shared memory (bytes, regions in this order): X, the three planes in turn as
+// gathered operands, slow-axis results, FP32 eigenspace planes [dd][row][LD]
+// and the eigenspace results B written in place; T0 and T1, two table slots;
+// Y, one plane's B operand for the backward slow-axis product, or the partial
+// sums of the x2 contraction during the eigenspace step; then Lam_d and the
+// vertex rows s_d.  The allocation extends at least 128 operand rows past the
+// start of every A operand (the three planes in X and the two table slots),
+// so the padding rows of every product stay inside it.
+//
+// The eigenspace step holds V in registers: warp w owns the k2 rows
+// lo2 + w + 16 i, its lanes the k1 columns lo1 + lane + 32 j.  Per k3 it forms
+// E = s1 P0 + s2 P1 + s3 P2 and V = E / D for its (k2, k1) points, and reduces
+// B1[k3][k2] = sum_k1 s1 V over its lanes (shuffle tree), keeps the partial
+// B2[k3][k1] = sum over its k2 of s2 V and accumulates B3[k2][k1] = sum_k3 s3 V
+// in registers.  The B2 partials of the 16 warps are summed in warp order
+// after every block of kTcKB k3-planes.  Every sum runs in a fixed order, so
+// results are bitwise reproducible.
 #pragma once
 #include <cstdint>
 
-#include "star_kernel.cuh"
+#include "semmg_internal.h"
 
 namespace semmg {
 
@@ -51,9 +72,13 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint3
   return d;
 }
 
-// kind::tf32 instruction descriptor: FP32 accumulator, TF32 A and B, both K-major
+// instruction descriptors, FP32 accumulator, A and B K-major: kind::tf32 with
+// TF32 operands (format 2), kind::f16 with BF16 operands (format 1)
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -61,6 +86,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -129,68 +163,153 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(b & ~0x1FFFu);
 }
 
-// float offset of element (row, k) in a K-major operand with K = np columns
-__device__ __forceinline__ int coff(int row, int k, int np) {
-  return ((row >> 3) * (np >> 2) + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3);
+// a finite float rounded to BF16 (7 stored mantissa bits), nearest-even: the bit pattern
+__device__ __forceinline__ uint16_t to_bf16(float x) {
+  uint32_t b = __float_as_uint(x);
+  b += 0x7FFFu + ((b >> 16) & 1u);
+  return (uint16_t)(b >> 16);
 }
 
 }  // namespace tc
+
+// Operand types of the tensor-core star kernel.  E: elements per 16-byte core
+// matrix row.
+struct TcTf32 {
+  using S = float;
+  static constexpr int E = 4;
+  __device__ static S cvt(float x) { return tc::to_tf32(x); }
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    tc::mma_tf32(d, a, b, id, acc);
+  }
+  __host__ __device__ static constexpr uint32_t idesc(int M, int N) { return tc::idesc_tf32(M, N); }
+  __device__ static const S* tabT(const Tabs<float>& t, int d) { return t.tcT[d]; }
+  __device__ static const S* tabN(const Tabs<float>& t, int d) { return t.tcN[d]; }
+};
+
+struct TcBf16 {
+  using S = uint16_t;
+  static constexpr int E = 8;
+  __device__ static S cvt(float x) { return tc::to_bf16(x); }
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    tc::mma_bf16(d, a, b, id, acc);
+  }
+  __host__ __device__ static constexpr uint32_t idesc(int M, int N) { return tc::idesc_bf16(M, N); }
+  __device__ static const S* tabT(const Tabs<float>& t, int d) { return t.bfT[d]; }
+  __device__ static const S* tabN(const Tabs<float>& t, int d) { return t.bfN[d]; }
+};
+
+// element offset of (row, k) in a K-major operand with K = np columns
+template <int E>
+__host__ __device__ __forceinline__ int tc_opoff(int row, int k, int np) {
+  return ((row >> 3) * (np / E) + k / E) * (8 * E) + (row & 7) * E + (k % E);
+}
 
 namespace {
 
 // bound of the wait for products still in flight after an abort (about 2 s at
 // 2 GHz); the completion waits of the normal rounds take the caller's budget
 constexpr long long kTcWaitCycles = 4000000000LL;
+constexpr int kTcWarps = 16;  // 512 threads
+constexpr int kTcKB = 4;      // k3-planes per block of the x2-contraction sums
 
 __host__ __device__ __forceinline__ int tc_np(int nS) { return (nS + 15) / 16 * 16; }
-__host__ __device__ __forceinline__ int tc_ld(int np) { return np + 4; }  // row stride of the eigenspace planes
-__host__ __device__ __forceinline__ int tc_cols(int np) {
-  int c = 32;
-  while (c < 3 * np) c *= 2;
-  return c;
+__host__ __device__ __forceinline__ size_t tc_al(size_t b) { return (b + 127) & ~size_t(127); }
+
+// byte offsets of the shared-memory regions (see the file comment)
+struct TcLayout {
+  int np, ld;
+  size_t x, t0, t1, y, lm, sv, total;
+};
+
+__host__ __device__ __forceinline__ TcLayout tc_layout(int nS, int esize) {
+  TcLayout L;
+  L.np = tc_np(nS);
+  L.ld = L.np + 4;
+  const size_t tb = (size_t)L.np * L.np * esize;
+  const size_t xb = (size_t)3 * L.np * L.ld * 4 > 3 * tb ? (size_t)3 * L.np * L.ld * 4 : 3 * tb;
+  const size_t yb = (size_t)kTcWarps * kTcKB * L.np * 4 > tb ? (size_t)kTcWarps * kTcKB * L.np * 4 : tb;
+  L.x = 0;
+  L.t0 = tc_al(xb);
+  L.t1 = L.t0 + tc_al(tb);
+  L.y = L.t1 + tc_al(tb);
+  L.lm = L.y + tc_al(yb);
+  L.sv = L.lm + tc_al((size_t)3 * nS * 4);
+  L.total = L.sv + tc_al((size_t)3 * nS * 4);
+  // an M = 128 product reads 128 operand rows from the start of its A operand (rows np..127 are
+  // padding): the allocation reaches 128 rows past the last A operand, the table in slot T1
+  const size_t a_end = L.t1 + (size_t)128 * L.np * esize;
+  if (L.total < a_end) L.total = a_end;
+  return L;
 }
 
-// Shared-memory layout in floats: tables 3 NP^2 | operands 3 NP^2 | planes
-// 3 NP LD | V slab ts nS^2 | Lam 3 nS | s 3 nS | s3^2 nS (tables and operands
-// first: an M = 128 product over the last table or operand reads the next
-// region as padding rows).
-__host__ __device__ __forceinline__ size_t tc_smem_floats(int nS) {
-  const int np = tc_np(nS);
-  return (size_t)6 * np * np + (size_t)3 * np * tc_ld(np) + (size_t)slab_thickness(nS) * nS * nS + 7 * nS + 8;
+// TMEM columns [col, col + N) = A (M = 128 rows, K = np) B^T (N rows, K = np), whole K extent
+template <typename OP>
+__device__ __forceinline__ void tc_product(uint32_t tmem, int col, const typename OP::S* A,
+                                           const typename OP::S* B, int N, int np) {
+  constexpr int esz = (int)sizeof(typename OP::S);
+  const uint32_t sbo = (uint32_t)(np / OP::E) * 128;  // bytes per 8-row group
+  const uint32_t idesc = OP::idesc(128, N);
+  const unsigned char* a = reinterpret_cast<const unsigned char*>(A);
+  const unsigned char* b = reinterpret_cast<const unsigned char*>(B);
+  const int steps = np * esz / 32;  // 32 bytes of K per instruction
+  for (int s = 0; s < steps; ++s)
+    OP::mma(tmem + col, tc::smem_desc(a + 256 * s, 128, sbo), tc::smem_desc(b + 256 * s, 128, sbo), idesc, s > 0);
 }
 
-// D columns [col, col + N) += A (M = 128, K = np) B^T over the whole K extent.
-__device__ __forceinline__ void tc_product(uint32_t tmem, int col, const float* A, const float* B, int N, int np) {
-  const uint32_t sbo = (uint32_t)np * 32;  // bytes per 8-row group
-  const uint32_t idesc = tc::idesc_tf32(128, N);
-  for (int s = 0; s < np / 8; ++s)
-    tc::mma_tf32(tmem + col, tc::smem_desc(A + 64 * s, 128, sbo), tc::smem_desc(B + 64 * s, 128, sbo), idesc, s > 0);
+// 16 consecutive K entries k0..k0+15 of operand row `row` (k0 a multiple of 16), rounded to the operand type
+template <typename OP>
+__device__ __forceinline__ void tc_store16(typename OP::S* dst, int row, int k0, const float* v, int np) {
+  constexpr int E = OP::E;
+  union Pack {
+    uint4 u;
+    typename OP::S s[E];
+  };
+#pragma unroll
+  for (int g = 0; g < 16; g += E) {
+    Pack w;
+#pragma unroll
+    for (int e = 0; e < E; ++e) w.s[e] = OP::cvt(v[g + e]);
+    *reinterpret_cast<uint4*>(dst + tc_opoff<E>(row, k0 + g, np)) = w.u;
+  }
 }
 
-template <int PC>
+__device__ __forceinline__ int tc_ax_fast(int dd) { return dd == 0 ? 1 : 0; }
+__device__ __forceinline__ int tc_ax_slow(int dd) { return dd == 2 ? 1 : 2; }
+
+struct TcRanges {
+  int lo[3], hi[3], pa[3];
+};
+
+template <typename OP, int PC>
 __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const float* __restrict__ r,
                                                      float* __restrict__ Ob, int* counter, int* err,
                                                      long long wait_budget) {
+  using S = typename OP::S;
+  constexpr int E = OP::E;
+  // compile-time bounds of the eigenspace registers: k1 chunks of 32 lanes, k2 rows per warp
+  constexpr int NJ = PC ? (2 * PC - 1 + 31) / 32 : 3;
+  constexpr int NI = PC ? (2 * PC - 1 + kTcWarps - 1) / kTcWarps : 6;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint64_t s_mbar;
   __shared__ uint32_t s_tmem;
   __shared__ int s_next, s_abort;
-  __shared__ int s_sym[3];
-  __shared__ Ranges s_rg;
+  __shared__ TcRanges s_rg;
   __shared__ int Ac[3 * (2 * SEMMG_MAX_DEGREE - 1)];
   const int p = PC ? PC : G.p, m = p - 1, nS = 2 * p - 1, n2 = nS * nS;
-  const int np = tc_np(nS), tb = np * np, ld = tc_ld(np);
-  float* Tb = reinterpret_cast<float*>(smem_raw);  // tables T(S_d) or N(S_d), d = 0..2
-  float* R1 = Tb + 3 * tb;                          // operands of the current product
-  float* P = R1 + 3 * tb;                           // eigenspace planes [dd][k_b][k_a], row stride ld
-  float* V = P + 3 * np * ld;
-  float* Lm = V + slab_thickness(nS) * n2;
-  float* Sv = Lm + 3 * nS;  // vertex rows s_d
-  float* s3sq = Sv + 3 * nS;
+  const TcLayout lay = tc_layout(nS, (int)sizeof(S));
+  const int np = lay.np, ld = lay.ld, tb = np * np;
+  float* X = reinterpret_cast<float*>(smem_raw + lay.x);  // FP32 planes [dd][row][ld]
+  S* Xo = reinterpret_cast<S*>(smem_raw + lay.x);         // operands, tb elements per plane
+  S* T0 = reinterpret_cast<S*>(smem_raw + lay.t0);
+  S* T1 = reinterpret_cast<S*>(smem_raw + lay.t1);
+  S* Yo = reinterpret_cast<S*>(smem_raw + lay.y);
+  float* Yf = reinterpret_cast<float*>(smem_raw + lay.y);  // x2-contraction partials [warp][kb][np]
+  float* Lm = reinterpret_cast<float*>(smem_raw + lay.lm);
+  float* Sv = reinterpret_cast<float*>(smem_raw + lay.sv);  // vertex rows s_d
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const float lam = (float)G.lam;
   const float rcp_mult[3] = {1.0f, 0.5f, 1.0f / 3.0f};
-  const uint32_t ncols = (uint32_t)tc_cols(np);
+  const uint32_t ncols = 3 * np <= 256 ? 256u : 512u;
   if (tid == 0) {
     tc::mbar_init(&s_mbar, 1);
     s_abort = 0;
@@ -225,26 +344,25 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
     __syncthreads();
     return s_abort == 0;
   };
-  // TMEM lanes [0, np) x columns [c0, c0 + 16 * nchunk): 16-column chunks spread
-  // over the warps of quadrants 0 and 1 (lanes 0..63); f(row, col, v[16])
-  auto readout = [&](int c0, int ncol, auto f) {
+  // TMEM lanes [0, np) x columns [0, ncol): 16-column chunks spread over the four warps of
+  // each lane quadrant; f(row, col, v[16])
+  auto readout = [&](int ncol, auto f) {
     const int q = warp & 3;
-    if (q < 2 && q * 32 < np) {
-      const int nchunk = ncol / 16, wq = warp >> 2;  // 4 warps per quadrant
-      for (int ch = wq; ch < nchunk; ch += 4) {
+    if (q * 32 < np) {
+      const int nchunk = ncol / 16, wq = warp >> 2;
+      for (int ch = wq; ch < nchunk; ch += kTcWarps / 4) {
         float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c0 + 16 * ch), v);
+        tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(16 * ch), v);
         const int row = q * 32 + lane;
         if (row < np) f(row, 16 * ch, v);
       }
     }
   };
-  auto load_tables = [&](const float* const* src, const int* c) {
-    for (int d = 0; d < 3; ++d) {
-      const float4* s4 = reinterpret_cast<const float4*>(src[d] + (int64_t)t.starCls[d][c[d]] * tb);
-      float4* d4 = reinterpret_cast<float4*>(Tb + d * tb);
-      for (int i = tid; i < tb / 4; i += blockDim.x) d4[i] = s4[i];
-    }
+  auto load_table = [&](S* dst, const S* src, int cls) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + (int64_t)cls * tb);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    const int nv = tb * (int)sizeof(S) / 16;
+    for (int i = tid; i < nv; i += blockDim.x) d4[i] = s4[i];
   };
   int64_t st = blockIdx.x;
   while (st < G.nstar) {
@@ -253,16 +371,16 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
     const bool alias = (G.per[0] && c[0] == G.n1) || (G.per[1] && c[1] == G.n2) || (G.per[2] && c[2] == G.n3);
     if (!alias) {
     __syncthreads();
-    if (tid < 3) s_sym[tid] = t.starSym[tid][c[tid]];
     for (int d = 0; d < 3; ++d)
       for (int i = tid; i < nS; i += blockDim.x) {
         Lm[d * nS + i] = t.starLam[d][(int64_t)c[d] * nS + i];
         Ac[d * nS + i] = t.act[d][(int64_t)c[d] * nS + i];
         Sv[d * nS + i] = t.starS[d][(int64_t)c[d] * n2 + m * nS + i];
       }
-    load_tables(t.tcT, c);
+    // forward slow-axis tables: x3 for planes 0 and 1, x2 for plane 2
+    load_table(T0, OP::tabT(t, 2), t.starCls[2][c[2]]);
+    load_table(T1, OP::tabT(t, 1), t.starCls[1][c[1]]);
     __syncthreads();
-    for (int i = tid; i < nS; i += blockDim.x) s3sq[i] = Sv[2 * nS + i] * Sv[2 * nS + i];
     if (tid < 3) {
       const int d = tid;
       int lo = 0, hi = nS;
@@ -272,206 +390,181 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
       s_rg.hi[d] = hi;
       s_rg.pa[d] = Ac[d * nS + m];
     }
-    // 1. gather the planes divided by the multiplicity, as B operands P_dd^T:
-    //    row n = dd np + ja, column k = jb (zero outside the star and in the padding)
+    // 1. the planes divided by the multiplicity, as B operands P_dd^T: row n = ja, K index jb
+    //    (zero outside the star and in the padding)
     for (int idx = tid; idx < 3 * tb; idx += blockDim.x) {
       const int dd = idx / tb, rr = idx - dd * tb, jbp = rr / np, jap = rr - jbp * np;
       float v = 0.0f;
       if (jap < nS && jbp < nS) {
         const int ja = jap - m, jb = jbp - m;
-        const int ax_a = ax_fast(dd), ax_b = ax_slow(dd);
+        const int ax_a = tc_ax_fast(dd), ax_b = tc_ax_slow(dd);
         if (Ac[dd * nS + m] && Ac[ax_a * nS + jap] && Ac[ax_b * nS + jbp]) {
           int g[3];
           g[dd] = c[dd] * p;
           g[ax_a] = c[ax_a] * p + ja;
           g[ax_b] = c[ax_b] * p + jb;
-          v = tc::to_tf32(r[skel_index(G, g[0], g[1], g[2])] * rcp_mult[(ja == 0) + (jb == 0)]);
+          v = r[skel_index(G, g[0], g[1], g[2])] * rcp_mult[(ja == 0) + (jb == 0)];
         }
       }
-      R1[tc::coff(dd * np + jap, jbp, np)] = v;
+      Xo[dd * tb + tc_opoff<E>(jap, jbp, np)] = OP::cvt(v);
     }
-    // 2. forward, slow axis: W = T(S_b) P^T (planes 0, 1: x3 tables; plane 2: x2 tables)
+    // 2. forward, slow axis: W = T(S_b) P^T
     if (!round([&] {
-          tc_product(tmem, 0, Tb + 2 * tb, R1, 2 * np, np);
-          tc_product(tmem, 2 * np, Tb + 1 * tb, R1 + 2 * tb, np, np);
+          tc_product<OP>(tmem, 0, T0, Xo, 2 * np, np);
+          tc_product<OP>(tmem, 2 * np, T1, Xo + 2 * tb, np, np);
         }))
       break;
-    // W (lanes k_b, columns dd np + ja) -> A operands (row k_b, k = ja)
-    readout(0, 3 * np, [&](int row, int col, const float* v) {
-      const int dd = col / np, k0 = col - dd * np;
-      float* a = R1 + dd * tb;
-#pragma unroll
-      for (int q = 0; q < 16; q += 4) {
-        const float4 w4 = make_float4(tc::to_tf32(v[q]), tc::to_tf32(v[q + 1]), tc::to_tf32(v[q + 2]),
-                                      tc::to_tf32(v[q + 3]));
-        *reinterpret_cast<float4*>(a + tc::coff(row, k0 + q, np)) = w4;
-      }
+    // W (lanes k_b, columns dd np + ja) -> A operands (row k_b, K index ja); x1 tables into slot 0
+    readout(3 * np, [&](int row, int col, const float* v) {
+      const int dd = col / np;
+      tc_store16<OP>(Xo + dd * tb, row, col - dd * np, v, np);
     });
+    load_table(T0, OP::tabT(t, 0), t.starCls[0][c[0]]);
     // 3. forward, fast axis: Z_dd = W_dd T(S_a) (plane 0: x2 tables; planes 1, 2: x1 tables)
     if (!round([&] {
-          tc_product(tmem, 0, R1, Tb + 1 * tb, np, np);
-          tc_product(tmem, np, R1 + tb, Tb, np, np);
-          tc_product(tmem, 2 * np, R1 + 2 * tb, Tb, np, np);
+          tc_product<OP>(tmem, 0, Xo, T1, np, np);
+          tc_product<OP>(tmem, np, Xo + tb, T0, np, np);
+          tc_product<OP>(tmem, 2 * np, Xo + 2 * tb, T0, np, np);
         }))
       break;
-    readout(0, 3 * np, [&](int row, int col, const float* v) {
+    readout(3 * np, [&](int row, int col, const float* v) {
       const int dd = col / np, k0 = col - dd * np;
-      float* dst = P + (dd * np + row) * ld + k0;
+      float* dst = X + (dd * np + row) * ld + k0;
 #pragma unroll
       for (int q = 0; q < 16; q += 4) *reinterpret_cast<float4*>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
     });
+    // backward slow-axis tables (x3, x2) load while the eigenspace step runs
+    load_table(T0, OP::tabN(t, 2), t.starCls[2][c[2]]);
+    load_table(T1, OP::tabN(t, 1), t.starCls[1][c[1]]);
     __syncthreads();
-    // the backward tables replace the forward ones while the eigenspace step runs
-    load_tables(t.tcN, c);
-    const int* sym = s_sym;
-    const Ranges rg = s_rg;
-    // 4. eigenspace: E = sum_d s_d (x) P_d, V = E / D, B_d = contraction of V with s_d;
-    //    results as the B operands of the backward slow-axis product:
-    //    plane 0: B1[k3][k2] at (n = k2, k = k3), plane 1: B2[k3][k1] at (np + k1, k3),
-    //    plane 2: B3[k2][k1] at (2 np + k1, k2)
-    const float* s1 = Sv;
-    const float* s2 = Sv + nS;
-    const float* s3 = Sv + 2 * nS;
-    const float* P0 = P;
-    const float* P1 = P + np * ld;
-    const float* P2 = P + 2 * np * ld;
-    const int lo1 = rg.lo[0], w1 = rg.hi[0] - rg.lo[0], lo2 = rg.lo[1], w2 = rg.hi[1] - rg.lo[1];
-    const int lo3 = rg.lo[2], w3 = rg.hi[2] - rg.lo[2];
-    const int nz1 = rg.pa[0] ? (sym[0] ? m + 1 : w1) : 0;
-    const int nz2 = rg.pa[1] ? (sym[1] ? m + 1 : w2) : 0;
-    const int nz3 = rg.pa[2] ? (sym[2] ? m + 1 : w3) : 0;
-    const int seg1 = nz2 * w1, seg2 = (w2 - nz2) * nz1, nlive = seg1 + seg2;
-    const int npair = nlive + (rg.pa[2] ? (w2 - nz2) * (w1 - nz1) : 0);
-    const int ts = slab_thickness(nS);
-    // the pair segments, the same for every slab of the star
-    const PairSeg sg_live1 = pair_seg(seg1, w1, lo1, lo2);
-    const PairSeg sg_live2 = pair_seg(seg2, nz1, lo1, lo2 + nz2);
-    const PairSeg sg_dead = pair_seg(rg.pa[2] ? npair - nlive : 0, w1 - nz1, lo1 + nz1, lo2 + nz2);
-    float* B3 = R1 + 2 * tb;
-    for (int i = tid; i < tb; i += blockDim.x) B3[i] = 0.0f;
-    for (int k3s = rg.lo[2]; k3s < rg.hi[2]; k3s += ts) {
-      const int tn = rg.hi[2] - k3s < ts ? rg.hi[2] - k3s : ts;
-      __syncthreads();
-      auto live = [&](int k1, int k2) {
-        const int pr = k2 * nS + k1;
-        const float a3 = rg.pa[2] ? P2[k2 * ld + k1] : 0.0f;
-        float* b3p = B3 + tc::coff(k1, k2, np);
-        {
-          const float c1 = k1 - lo1 < nz1 ? s1[k1] : 0.0f, c2 = k2 - lo2 < nz2 ? s2[k2] : 0.0f;
-          // loop invariants of the k3 run (as in k_star): the (k1, k2) part of D and the rows
-          // where s3 may be non-zero
-          const float d12 = lam + Lm[k1] + Lm[nS + k2];
-          const float* p0 = P0 + k3s * ld + k2;
-          const float* p1 = P1 + k3s * ld + k1;
-          const int kl = min(max(lo3 + nz3 - k3s, 0), tn);
-          float b3 = 0.0f;
-          // unrolled: four independent load - divide - store chains in flight per thread
-#pragma unroll 4
-          for (int kk = 0; kk < kl; ++kk) {
-            const int k3 = k3s + kk;
-            float E = c1 * p0[kk * ld] + c2 * p1[kk * ld];
-            E += s3[k3] * a3;
-            const float v = fast_div(E, d12 + Lm[2 * nS + k3]);
-            V[kk * n2 + pr] = v;
-            b3 += s3[k3] * v;
-          }
-#pragma unroll 4
-          for (int kk = kl; kk < tn; ++kk) {
-            const float E = c1 * p0[kk * ld] + c2 * p1[kk * ld];
-            V[kk * n2 + pr] = fast_div(E, d12 + Lm[2 * nS + k3s + kk]);
-          }
-          if (nz3) *b3p += b3;
+    // 4. eigenspace step (see the file comment): B1, B2, B3 replace P0, P1, P2 in X
+    {
+      const TcRanges rg = s_rg;
+      const int lo1 = rg.lo[0], hi1 = rg.hi[0], lo2 = rg.lo[1], hi2 = rg.hi[1], lo3 = rg.lo[2], hi3 = rg.hi[2];
+      float* P0 = X;
+      float* P1 = X + np * ld;
+      float* P2 = X + 2 * np * ld;
+      const float* s1 = Sv;
+      const float* s2 = Sv + nS;
+      const float* s3 = Sv + 2 * nS;
+      int k1v[NJ];
+      bool ok1[NJ];
+      float s1r[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        k1v[j] = lo1 + lane + 32 * j;
+        ok1[j] = k1v[j] < hi1;
+        s1r[j] = ok1[j] ? s1[k1v[j]] : 0.0f;
+      }
+      float p2r[NI][NJ], b3[NI][NJ], d12[NI][NJ], s2r[NI];
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int k2 = lo2 + warp + kTcWarps * i;
+        const bool ok2 = k2 < hi2;
+        s2r[i] = ok2 ? s2[k2] : 0.0f;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const bool ok = ok2 && ok1[j];
+          p2r[i][j] = ok ? P2[k2 * ld + k1v[j]] : 0.0f;
+          d12[i][j] = ok ? lam + Lm[k1v[j]] + Lm[nS + k2] : 1.0f;
+          b3[i][j] = 0.0f;
         }
-      };
-      auto dead = [&](int k1, int k2) {
-        const int pr = k2 * nS + k1;
-        const float a3 = rg.pa[2] ? P2[k2 * ld + k1] : 0.0f;
-        float* b3p = B3 + tc::coff(k1, k2, np);
-        (void)pr;
-        {
-          float b3 = 0.0f;
-          for (int kk = 0; kk < tn; ++kk) {
-            const int k3 = k3s + kk;
-            if (k3 - lo3 >= nz3) break;
-            b3 += fast_div(s3sq[k3], lam + Lm[k1] + Lm[nS + k2] + Lm[2 * nS + k3]);
+      }
+      const int w1 = hi1 - lo1;
+      for (int k3b = lo3; k3b < hi3; k3b += kTcKB) {
+        const int nb = hi3 - k3b < kTcKB ? hi3 - k3b : kTcKB;
+        for (int kb = 0; kb < nb; ++kb) {
+          const int k3 = k3b + kb;
+          const float s3k = s3[k3], l3 = Lm[2 * nS + k3];
+          float p1r[NJ], b2[NJ];
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            p1r[j] = ok1[j] ? P1[k3 * ld + k1v[j]] : 0.0f;
+            b2[j] = 0.0f;
           }
-          *b3p += a3 * b3;
+#pragma unroll
+          for (int i = 0; i < NI; ++i) {
+            const int k2 = lo2 + warp + kTcWarps * i;
+            if (k2 < hi2) {  // warp-uniform
+              const float p0 = P0[k3 * ld + k2];
+              float b1 = 0.0f;
+#pragma unroll
+              for (int j = 0; j < NJ; ++j) {
+                if (ok1[j]) {
+                  float e = s1r[j] * p0;
+                  e += s2r[i] * p1r[j];
+                  e += s3k * p2r[i][j];
+                  const float v = __fdividef(e, d12[i][j] + l3);
+                  b1 += s1r[j] * v;
+                  b2[j] += s2r[i] * v;
+                  b3[i][j] += s3k * v;
+                }
+              }
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+              // this warp alone reads P0[k3][k2]: B1[k3][k2] takes its place
+              if (lane == 0) P0[k3 * ld + k2] = rg.pa[0] ? b1 : 0.0f;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < NJ; ++j)
+            if (ok1[j]) Yf[(warp * kTcKB + kb) * np + k1v[j]] = b2[j];
         }
-      };
-      for_pairs(sg_live1, live);
-      for_pairs(sg_live2, live);
-      for_pairs(sg_dead, dead);
-      __syncthreads();
-      const int nb1 = rg.pa[0] ? tn * w2 : 0, nb2 = rg.pa[1] ? tn * w1 : 0;
-      for (int o = tid; o < nb1 + nb2; o += blockDim.x) {
-        const bool first = o < nb1;
-        const int wx = first ? w2 : w1;
-        int rr = first ? o : o - nb1, kk = 0;
-        while (rr >= wx) {  // rr / wx < tn <= slab depth: subtract instead of dividing
-          rr -= wx;
-          ++kk;
+        __syncthreads();
+        // B2 rows of the block: the 16 warps' partial sums in warp order, in place of P1's rows
+        for (int o = tid; o < nb * w1; o += blockDim.x) {
+          const int kb = o / w1, k1 = lo1 + (o - kb * w1);
+          float sum = 0.0f;
+#pragma unroll
+          for (int w = 0; w < kTcWarps; ++w) sum += Yf[(w * kTcKB + kb) * np + k1];
+          P1[(k3b + kb) * ld + k1] = rg.pa[1] ? sum : 0.0f;
         }
-        const int kx = (first ? lo2 : lo1) + rr;
-        const float* vs = V + kk * n2;
-        float s = 0.0f, s_1 = 0.0f, s_2 = 0.0f, s_3 = 0.0f;
-        if (first) {
-          const float* v = vs + kx * nS + lo1;
-          const float* sv = s1 + lo1;
-          int k = 0;
-          for (; k + 3 < nz1; k += 4) {
-            s += sv[k] * v[k];
-            s_1 += sv[k + 1] * v[k + 1];
-            s_2 += sv[k + 2] * v[k + 2];
-            s_3 += sv[k + 3] * v[k + 3];
-          }
-          for (; k < nz1; ++k) s += sv[k] * v[k];
-          R1[tc::coff(kx, k3s + kk, np)] = (s + s_1) + (s_2 + s_3);
-        } else {
-          const float* v = vs + kx + lo2 * nS;
-          const float* sv = s2 + lo2;
-          int k = 0;
-          for (; k + 3 < nz2; k += 4) {
-            s += sv[k] * v[k * nS];
-            s_1 += sv[k + 1] * v[(k + 1) * nS];
-            s_2 += sv[k + 2] * v[(k + 2) * nS];
-            s_3 += sv[k + 3] * v[(k + 3) * nS];
-          }
-          for (; k < nz2; ++k) s += sv[k] * v[k * nS];
-          R1[tc::coff(np + kx, k3s + kk, np)] = (s + s_1) + (s_2 + s_3);
+        __syncthreads();
+      }
+      // B3 in place of P2 (the rows this warp owns and alone has read)
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int k2 = lo2 + warp + kTcWarps * i;
+        if (k2 < hi2) {
+#pragma unroll
+          for (int j = 0; j < NJ; ++j)
+            if (ok1[j]) P2[k2 * ld + k1v[j]] = rg.pa[2] ? b3[i][j] : 0.0f;
         }
       }
     }
-    __syncthreads();
-    for (int i = tid; i < 3 * tb; i += blockDim.x) R1[i] = tc::to_tf32(R1[i]);
-    // 5. backward, slow axis: O = N(S_b) B^T
-    if (!round([&] {
-          tc_product(tmem, 0, Tb + 2 * tb, R1, 2 * np, np);
-          tc_product(tmem, 2 * np, Tb + 1 * tb, R1 + 2 * tb, np, np);
-        }))
-      break;
-    readout(0, 3 * np, [&](int row, int col, const float* v) {
-      const int dd = col / np, k0 = col - dd * np;
-      float* a = R1 + dd * tb;
-#pragma unroll
-      for (int q = 0; q < 16; q += 4) {
-        const float4 w4 = make_float4(tc::to_tf32(v[q]), tc::to_tf32(v[q + 1]), tc::to_tf32(v[q + 2]),
-                                      tc::to_tf32(v[q + 3]));
-        *reinterpret_cast<float4*>(a + tc::coff(row, k0 + q, np)) = w4;
+    // 5. backward, slow axis, one plane at a time: O_dd = N(S_b) B_dd^T with B_dd (rows k_b,
+    //    columns k_a in X) staged in Y as the B operand (row n = k_a, K index k_b)
+    bool aborted = false;
+    for (int dd = 0; dd < 3 && !aborted; ++dd) {
+      if (dd > 0) __syncthreads();  // the previous round's operand is consumed (round() waited)
+      const float* B = X + dd * np * ld;
+      for (int idx = tid; idx < tb; idx += blockDim.x) {
+        const int kb = idx / np, ka = idx - kb * np;
+        Yo[tc_opoff<E>(ka, kb, np)] = OP::cvt(B[kb * ld + ka]);
       }
+      aborted = !round([&] { tc_product<OP>(tmem, dd * np, dd == 2 ? T1 : T0, Yo, np, np); });
+    }
+    if (aborted) break;
+    // O (lanes j_b, columns dd np + k_a) -> A operands (row j_b, K index k_a) in X, whose B planes
+    // are consumed; the x1 tables replace the x3 ones (the x2 ones stay for plane 0)
+    readout(3 * np, [&](int row, int col, const float* v) {
+      const int dd = col / np;
+      tc_store16<OP>(Xo + dd * tb, row, col - dd * np, v, np);
     });
-    // 6. backward, fast axis: Y_dd = O_dd N(S_a)
+    load_table(T0, OP::tabN(t, 0), t.starCls[0][c[0]]);
+    // 6. backward, fast axis: Y_dd = O_dd N(S_a) (plane 0: x2 tables; planes 1, 2: x1 tables)
     if (!round([&] {
-          tc_product(tmem, 0, R1, Tb + 1 * tb, np, np);
-          tc_product(tmem, np, R1 + tb, Tb, np, np);
-          tc_product(tmem, 2 * np, R1 + 2 * tb, Tb, np, np);
+          tc_product<OP>(tmem, 0, Xo, T1, np, np);
+          tc_product<OP>(tmem, np, Xo + tb, T0, np, np);
+          tc_product<OP>(tmem, 2 * np, Xo + 2 * tb, T0, np, np);
         }))
       break;
-    // 7. weights, multiplicity and mask -> per-star output planes
+    // 7. weights, multiplicity and mask -> the star's output planes
     float* ob = Ob + st * 3 * (int64_t)n2;
-    readout(0, 3 * np, [&](int row, int col, const float* v) {
+    readout(3 * np, [&](int row, int col, const float* v) {
       const int dd = col / np, k0 = col - dd * np, jb = row;
       if (jb >= nS) return;
-      const int ax_a = ax_fast(dd), ax_b = ax_slow(dd);
+      const int ax_a = tc_ax_fast(dd), ax_b = tc_ax_slow(dd);
       const int obb = jb - m;
       const bool rowact = Ac[dd * nS + m] && Ac[ax_b * nS + jb];
       for (int q = 0; q < 16; ++q) {
@@ -511,17 +604,44 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
   }
 }
 
+// dynamic shared memory of the kernel, bytes; the launch also holds about 1.3 KB of static shared memory
+size_t tc_smem_bytes(int nS, int bf16) { return tc_layout(nS, bf16 ? 2 : 4).total; }
+
+constexpr size_t kTcSmemMax = 225 * 1024;  // the opt-in limit less the kernel's 2 KB of static shared memory
+
+template <typename OP>
+void launch_tc(const Geo& G, const Tabs<float>& t, const float* r, float* Ob, const LaunchCfg& c, int* counter,
+               int* err, long long wait_budget, cudaStream_t st) {
+  switch (G.p) {
+    case 16: k_star_tc<OP, 16><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err, wait_budget); break;
+    case 32: k_star_tc<OP, 32><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err, wait_budget); break;
+    case 48: k_star_tc<OP, 48><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err, wait_budget); break;
+    default: k_star_tc<OP, 0><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err, wait_budget); break;
+  }
+}
+
+template <typename OP>
+int tc_attrs() {
+  int bad = 0;
+  bad |= cudaFuncSetAttribute(k_star_tc<OP, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
+  bad |= cudaFuncSetAttribute(k_star_tc<OP, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
+  bad |= cudaFuncSetAttribute(k_star_tc<OP, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
+  bad |= cudaFuncSetAttribute(k_star_tc<OP, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
+  return bad;
+}
+
 }  // namespace
 
-LaunchCfg plan_star_tc(const Geo& G, int nsm) {
+LaunchCfg plan_star_tc(const Geo& G, int nsm, int bf16) {
   LaunchCfg c;
-  // np <= 64: the stacked products fit N <= 128 and M = 128; below n_S = 31 the
-  // CUDA-core kernel is as fast (measured: p = 8 slower on the tensor cores)
-  if (G.nS > 64 || G.nS < 31) return c;
-  c.smem = tc_smem_floats(G.nS) * sizeof(float);
-  if (c.smem > 200 * 1024) return c;
-  c.block = 512;
+  // 31 <= n_S <= 95 (np <= 96: the stacked products fit N <= 256 and the tensor memory 512
+  // columns); below n_S = 31 the CUDA-core kernel is as fast
+  if (G.nS > 95 || G.nS < 31) return c;
+  c.smem = tc_smem_bytes(G.nS, bf16);
+  if (c.smem > kTcSmemMax) return c;
+  c.block = 32 * kTcWarps;
   c.wide = 1;
+  c.bf16 = bf16 ? 1 : 0;
   c.ws = WsPlan{};
   c.grid = (int)(G.nstar < nsm ? G.nstar : nsm);
   if (c.grid < 1) c.grid = 1;
@@ -532,19 +652,12 @@ LaunchCfg plan_star_tc(const Geo& G, int nsm) {
 void launch_star_tc(const Geo& G, const Tabs<float>& t, const float* r, float* Ob, const LaunchCfg& c, int* counter,
                     int* err, long long wait_budget, cudaStream_t st) {
   if (G.nstar == 0 || !c.ok) return;
-  switch (G.p) {
-    case 16: k_star_tc<16><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err, wait_budget); break;
-    case 32: k_star_tc<32><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err, wait_budget); break;
-    default: k_star_tc<0><<<c.grid, c.block, c.smem, st>>>(G, t, r, Ob, counter, err, wait_budget); break;
-  }
+  if (c.bf16)
+    launch_tc<TcBf16>(G, t, r, Ob, c, counter, err, wait_budget, st);
+  else
+    launch_tc<TcTf32>(G, t, r, Ob, c, counter, err, wait_budget, st);
 }
 
-int set_star_tc_smem_limits() {
-  int bad = 0;
-  bad |= cudaFuncSetAttribute(k_star_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_star_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_star_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  return bad;
-}
+int set_star_tc_smem_limits() { return tc_attrs<TcTf32>() | tc_attrs<TcBf16>(); }
 
 }  // namespace semmg

@@ -54,7 +54,8 @@ class Context:
         opts.nu_pre = nu_pre
         opts.nu_post = nu_post
         opts.precision = {"fp64": L.SEMMG_FP64, "mixed": L.SEMMG_MIXED, "mixed_fp32": L.SEMMG_MIXED_FP32,
-                          "mixed_tc": L.SEMMG_MIXED_TC, "mixed_fp32_tc": L.SEMMG_MIXED_FP32_TC}[precision]
+                          "mixed_tc": L.SEMMG_MIXED_TC, "mixed_fp32_tc": L.SEMMG_MIXED_FP32_TC,
+                          "mixed_bf16": L.SEMMG_MIXED_BF16}[precision]
         opts.max_iter = max_iter
         opts.solver = {"mg": L.SEMMG_SOLVER_MG, "kmg": L.SEMMG_SOLVER_KMG}[solver]
         opts.nu_vary = 1 if nu_vary else 0
