@@ -592,7 +592,7 @@ void collect_timing(semmg_ctx* c) {
 // a group), the eigenspace segments of every k3-slab (1/D from the table or by
 // division) with the contractions along the normals (in FP64 four lanes per
 // output and two combining adds per thread and round), and the weighted output.
-double star_exec_ops(const semmg_ctx* c, int l, bool fp64, int block) {
+double star_exec_ops(const semmg_ctx* c, int l, bool fp64, int block, std::vector<double>* each = nullptr) {
   const Geo& G = c->geo[l];
   const HostLevel& H = c->hl[l];
   const int nS = G.nS, m = G.m, ts = star_slab_thickness(nS), kG = kStarGroup;
@@ -617,6 +617,7 @@ double star_exec_ops(const semmg_ctx* c, int l, bool fp64, int block) {
   };
   const double n2 = (double)nS * nS;
   double total = 0.0;
+  if (each) each->assign((size_t)G.nstar, 0.0);
   for (int c3 = 0; c3 < G.nv3; ++c3)
     for (int c2 = 0; c2 < G.nv2; ++c2)
       for (int c1 = 0; c1 < G.nv1; ++c1) {
@@ -656,8 +657,24 @@ double star_exec_ops(const semmg_ctx* c, int l, bool fp64, int block) {
           }
         }
         total += ops;
+        if (each) (*each)[((size_t)c3 * G.nv2 + c2) * G.nv1 + c1] = ops;
       }
   return total;
+}
+
+// Star order of level l for the star kernels: most operations first (per-star counts of
+// star_exec_ops), so the long stars start first and the short ones fill the tail.
+bool upload_star_order(semmg_ctx* c, int l) {
+  std::vector<double> cost;
+  star_exec_ops(c, l, true, 512, &cost);
+  std::vector<int> order(cost.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  int* d = (int*)dalloc(c, order.size() * sizeof(int));
+  if (!d || cudaMemcpy(d, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return false;
+  c->dl[l].td.order = d;
+  c->dl[l].tf.order = d;
+  return true;
 }
 
 // V-cycle in FP32 (the mixed forms)
@@ -1189,6 +1206,9 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
       build_star_rtab(c.get(), c->geo[l], c->hl[l], c->dl[l].td,
                       o.precision == SEMMG_FP64 ? kMaxStarRtabFp64 : kMaxRtabEntries, &ok);
   }
+  // longest-first star order per smoothing level (scheduling only: results are unchanged)
+  for (int l = 1; ok && l < nl; ++l)
+    if (o.smoother == SEMMG_SMOOTHER_STAR && !upload_star_order(c.get(), l)) ok = false;
   for (int d = 0; d < 3; ++d) {
     c->ct.K[d] = c->hc.K[d];
     c->ct.g0[d] = c->hc.g0[d];

@@ -111,6 +111,35 @@ SEMMG_HD int64_t skel_index(const Geo& G, int g1, int g2, int g3, int* type = nu
   return s;
 }
 
+// Skeleton slot of the node at in-plane offsets (ja, jb), -m <= ja, jb <= m, from
+// vertex (c1, c2, c3) on the star plane normal to axis dd (ja along the fast
+// in-plane axis: x2 for dd = 0, else x1; jb along the slow one: x3 for dd < 2,
+// else x2): skel_index of that node, from the entity it lies on (a face
+// quadrant, a half edge or the vertex) without decoding global coordinates.
+// The vertex must not lie on the image plane of a periodic axis.
+SEMMG_HD int64_t star_plane_slot(const Geo& G, int dd, int c1, int c2, int c3, int ja, int jb) {
+  const int m = G.m;
+  const int64_t mm = (int64_t)m * m;
+  const int ia = ja > 0 ? ja - 1 : m + ja, ib = jb > 0 ? jb - 1 : m + jb;  // interior indices
+  if (dd == 0) {  // plane c1: x2 (ja), x3 (jb)
+    const int a2 = ja > 0 ? c2 : wrape(G, 1, c2 - 1), a3 = jb > 0 ? c3 : wrape(G, 2, c3 - 1);
+    if (ja != 0 && jb != 0) return G.oF1 + (((int64_t)a3 * G.n2 + a2) * G.nv1 + c1) * mm + (int64_t)ib * m + ia;
+    if (jb != 0) return G.oE3 + (((int64_t)a3 * G.nv2 + c2) * G.nv1 + c1) * m + ib;
+    if (ja != 0) return G.oE2 + (((int64_t)c3 * G.n2 + a2) * G.nv1 + c1) * m + ia;
+  } else if (dd == 1) {  // plane c2: x1 (ja), x3 (jb)
+    const int a1 = ja > 0 ? c1 : wrape(G, 0, c1 - 1), a3 = jb > 0 ? c3 : wrape(G, 2, c3 - 1);
+    if (ja != 0 && jb != 0) return G.oF2 + (((int64_t)a3 * G.nv2 + c2) * G.n1 + a1) * mm + (int64_t)ib * m + ia;
+    if (jb != 0) return G.oE3 + (((int64_t)a3 * G.nv2 + c2) * G.nv1 + c1) * m + ib;
+    if (ja != 0) return G.oE1 + (((int64_t)c3 * G.nv2 + c2) * G.n1 + a1) * m + ia;
+  } else {  // plane c3: x1 (ja), x2 (jb)
+    const int a1 = ja > 0 ? c1 : wrape(G, 0, c1 - 1), a2 = jb > 0 ? c2 : wrape(G, 1, c2 - 1);
+    if (ja != 0 && jb != 0) return G.oF3 + (((int64_t)c3 * G.n2 + a2) * G.n1 + a1) * mm + (int64_t)ib * m + ia;
+    if (jb != 0) return G.oE2 + (((int64_t)c3 * G.n2 + a2) * G.nv1 + c1) * m + ib;
+    if (ja != 0) return G.oE1 + (((int64_t)c3 * G.nv2 + c2) * G.n1 + a1) * m + ia;
+  }
+  return G.oV + ((int64_t)c3 * G.nv2 + c2) * G.nv1 + c1;
+}
+
 // Index stride of a run of nodes along axis d (0-based) inside one entity.
 SEMMG_HD int run_stride(const Geo& G, int type, int d) {
   switch (type) {
@@ -278,6 +307,7 @@ struct Tabs {
   int ncls[3];                     // classes per axis
   const T* Rtab;   // per star class (c1*ncls2 + c2)*ncls3 + c3: nS^3 values 1/(lam+Lam1+Lam2+Lam3), or null
   const T* w1d;    // m+1: smoother weight at offset |j| (Sec. 3.2, weights)
+  const int* order;  // nstar star indices, most operations first (longest-first hand-out), or null
   const T* J;      // (p+1) x (pc+1) interpolation from level-1, row-major; null on level 0
   int pc;
   // tensor-core star tables (FP32 levels of the tensor-core forms, else null): per

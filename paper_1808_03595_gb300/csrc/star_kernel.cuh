@@ -275,8 +275,10 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
   const T lam = (T)G.lam;
   // 1 / (number of planes a node lies on): 1, 2 or 3 planes
   const T rcp_mult[3] = {(T)1, (T)0.5, (T)1 / (T)3};
-  int64_t st = blockIdx.x;
-  while (st < G.nstar) {
+  // position in the star order (most work first when the level has an order table)
+  int64_t it = blockIdx.x;
+  while (it < G.nstar) {
+    const int64_t st = t.order ? (int64_t)t.order[it] : it;
     const int c[3] = {(int)(st % G.nv1), (int)((st / G.nv1) % G.nv2), (int)(st / ((int64_t)G.nv1 * G.nv2))};
     // the last vertex plane of a periodic axis repeats plane 0: its stars are never read
     const bool alias = (G.per[0] && c[0] == G.n1) || (G.per[1] && c[1] == G.n2) || (G.per[2] && c[2] == G.n3);
@@ -319,13 +321,8 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
       const int dd = idx / n2, rr = idx - dd * n2, jb = rr / nS - m, ja = rr % nS - m;
       const int ax_a = ax_fast(dd), ax_b = ax_slow(dd);
       T v = 0;
-      if (Ac[dd * nS + m] && Ac[ax_a * nS + ja + m] && Ac[ax_b * nS + jb + m]) {
-        int g[3];
-        g[dd] = c[dd] * p;
-        g[ax_a] = c[ax_a] * p + ja;
-        g[ax_b] = c[ax_b] * p + jb;
-        v = r[skel_index(G, g[0], g[1], g[2])] * rcp_mult[(ja == 0) + (jb == 0)];
-      }
+      if (Ac[dd * nS + m] && Ac[ax_a * nS + ja + m] && Ac[ax_b * nS + jb + m])
+        v = r[star_plane_slot(G, dd, c[0], c[1], c[2], ja, jb)] * rcp_mult[(ja == 0) + (jb == 0)];
       P[idx] = v;
     }
     __syncthreads();
@@ -539,9 +536,9 @@ __global__ void __launch_bounds__(512, NB) k_star(Geo G, Tabs<T> t, const T* __r
       __syncthreads();
       if (threadIdx.x == 0) s_next = atomicAdd(&counter[0], 1) + (int)gridDim.x;
       __syncthreads();
-      st = s_next;
+      it = s_next;
     } else {
-      st += gridDim.x;
+      it += gridDim.x;
     }
   }
   if (counter) {

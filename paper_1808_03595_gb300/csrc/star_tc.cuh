@@ -218,7 +218,7 @@ __host__ __device__ __forceinline__ size_t tc_al(size_t b) { return (b + 127) & 
 // byte offsets of the shared-memory regions (see the file comment)
 struct TcLayout {
   int np, ld;
-  size_t x, t0, t1, y, lm, sv, total;
+  size_t x, t0, t1, y, lm, sv, wt, total;
 };
 
 __host__ __device__ __forceinline__ TcLayout tc_layout(int nS, int esize) {
@@ -234,7 +234,8 @@ __host__ __device__ __forceinline__ TcLayout tc_layout(int nS, int esize) {
   L.y = L.t1 + tc_al(tb);
   L.lm = L.y + tc_al(yb);
   L.sv = L.lm + tc_al((size_t)3 * nS * 4);
-  L.total = L.sv + tc_al((size_t)3 * nS * 4);
+  L.wt = L.sv + tc_al((size_t)3 * nS * 4);
+  L.total = L.wt + tc_al((size_t)(nS + 1) / 2 * 4);
   // an M = 128 product reads 128 operand rows from the start of its A operand (rows np..127 are
   // padding): the allocation reaches 128 rows past the last A operand, the table in slot T1
   const size_t a_end = L.t1 + (size_t)128 * L.np * esize;
@@ -280,6 +281,41 @@ struct TcRanges {
   int lo[3], hi[3], pa[3];
 };
 
+// Sums over the 32 lanes of R values per lane (R a power of two, at most 8), all at
+// once: R - 1 shuffles halve the values each lane holds while doubling the lanes
+// they sum, then a butterfly over the remaining lane bits.  Returns the total of
+// value rs_index<R>(lane) (every lane of a group returns the same bits: a + b is
+// exact-commutative).  A fixed order of additions: bitwise reproducible.
+template <int R>
+__device__ __forceinline__ float rs_reduce(float* v, int lane) {
+  int off = 16;
+#pragma unroll
+  for (int n = R; n > 1; n >>= 1, off >>= 1) {
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < n / 2; ++k) {
+      const float send = hi ? v[k] : v[k + n / 2];
+      const float keep = hi ? v[k + n / 2] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  float t = v[0];
+#pragma unroll
+  for (; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  return t;
+}
+
+template <int R>
+__device__ __forceinline__ int rs_index(int lane) {
+  int idx = 0, off = 16;
+#pragma unroll
+  for (int n = R; n > 1; n >>= 1, off >>= 1)
+    if (lane & off) idx += n / 2;
+  return idx;
+}
+
+__host__ __device__ constexpr int tc_pow2(int n) { return n <= 1 ? 1 : (n <= 2 ? 2 : (n <= 4 ? 4 : 8)); }
+
 template <typename OP, int PC>
 __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const float* __restrict__ r,
                                                      float* __restrict__ Ob, int* counter, int* err,
@@ -306,14 +342,17 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
   float* Yf = reinterpret_cast<float*>(smem_raw + lay.y);  // x2-contraction partials [warp][kb][np]
   float* Lm = reinterpret_cast<float*>(smem_raw + lay.lm);
   float* Sv = reinterpret_cast<float*>(smem_raw + lay.sv);  // vertex rows s_d
+  float* Wt = reinterpret_cast<float*>(smem_raw + lay.wt);  // smoother weights at offsets 0..m
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const float lam = (float)G.lam;
-  const float rcp_mult[3] = {1.0f, 0.5f, 1.0f / 3.0f};
+  // 1 / (number of planes a node lies on) for 0, 1 or 2 zero in-plane offsets
+  auto rcp_mult = [](int zeros) { return zeros == 0 ? 1.0f : (zeros == 1 ? 0.5f : 1.0f / 3.0f); };
   const uint32_t ncols = 3 * np <= 256 ? 256u : 512u;
   if (tid == 0) {
     tc::mbar_init(&s_mbar, 1);
     s_abort = 0;
   }
+  for (int i = tid; i <= m; i += blockDim.x) Wt[i] = t.w1d[i];
   if (warp == 0) {
     tc::tmem_alloc(&s_tmem, ncols);
     tc::tmem_relinquish();
@@ -364,8 +403,10 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
     const int nv = tb * (int)sizeof(S) / 16;
     for (int i = tid; i < nv; i += blockDim.x) d4[i] = s4[i];
   };
-  int64_t st = blockIdx.x;
-  while (st < G.nstar) {
+  // position in the star order (most work first when the level has an order table)
+  int64_t it = blockIdx.x;
+  while (it < G.nstar) {
+    const int64_t st = t.order ? (int64_t)t.order[it] : it;
     const int c[3] = {(int)(st % G.nv1), (int)((st / G.nv1) % G.nv2), (int)(st / ((int64_t)G.nv1 * G.nv2))};
     // the last vertex plane of a periodic axis repeats plane 0: its stars are never read
     const bool alias = (G.per[0] && c[0] == G.n1) || (G.per[1] && c[1] == G.n2) || (G.per[2] && c[2] == G.n3);
@@ -391,22 +432,31 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
       s_rg.pa[d] = Ac[d * nS + m];
     }
     // 1. the planes divided by the multiplicity, as B operands P_dd^T: row n = ja, K index jb
-    //    (zero outside the star and in the padding)
-    for (int idx = tid; idx < 3 * tb; idx += blockDim.x) {
-      const int dd = idx / tb, rr = idx - dd * tb, jbp = rr / np, jap = rr - jbp * np;
-      float v = 0.0f;
-      if (jap < nS && jbp < nS) {
-        const int ja = jap - m, jb = jbp - m;
-        const int ax_a = tc_ax_fast(dd), ax_b = tc_ax_slow(dd);
-        if (Ac[dd * nS + m] && Ac[ax_a * nS + jap] && Ac[ax_b * nS + jbp]) {
-          int g[3];
-          g[dd] = c[dd] * p;
-          g[ax_a] = c[ax_a] * p + ja;
-          g[ax_b] = c[ax_b] * p + jb;
-          v = r[skel_index(G, g[0], g[1], g[2])] * rcp_mult[(ja == 0) + (jb == 0)];
+    //    (zero outside the star and in the padding).  The operands are filled in their memory
+    //    order (a warp writes whole core matrices: no bank conflicts), four independent loads in
+    //    flight per thread.
+    for (int base = tid; base < 3 * tb; base += 4 * (int)blockDim.x) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + u * (int)blockDim.x;
+        v[u] = 0.0f;
+        if (idx < 3 * tb) {
+          const int dd = idx / tb, w = idx - dd * tb, cm = w / (8 * E), e = w - cm * (8 * E);
+          const int jap = (cm / (np / E)) * 8 + e / E, jbp = (cm % (np / E)) * E + e % E;
+          if (jap < nS && jbp < nS) {
+            const int ja = jap - m, jb = jbp - m;
+            const int ax_a = tc_ax_fast(dd), ax_b = tc_ax_slow(dd);
+            if (Ac[dd * nS + m] && Ac[ax_a * nS + jap] && Ac[ax_b * nS + jbp])
+              v[u] = __ldg(r + star_plane_slot(G, dd, c[0], c[1], c[2], ja, jb)) * rcp_mult((ja == 0) + (jb == 0));
+          }
         }
       }
-      Xo[dd * tb + tc_opoff<E>(jap, jbp, np)] = OP::cvt(v);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + u * (int)blockDim.x;
+        if (idx < 3 * tb) Xo[idx] = OP::cvt(v[u]);
+      }
     }
     // 2. forward, slow axis: W = T(S_b) P^T
     if (!round([&] {
@@ -437,7 +487,9 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
     load_table(T0, OP::tabN(t, 2), t.starCls[2][c[2]]);
     load_table(T1, OP::tabN(t, 1), t.starCls[1][c[1]]);
     __syncthreads();
-    // 4. eigenspace step (see the file comment): B1, B2, B3 replace P0, P1, P2 in X
+    // 4. eigenspace step (see the file comment): B1, B2, B3 replace P0, P1, P2 in X.  Rows and
+    //    columns outside the active ranges carry zeros (s = 0, P = 0, D = 1), so the loops have
+    //    no branches; only the stores are guarded.
     {
       const TcRanges rg = s_rg;
       const int lo1 = rg.lo[0], hi1 = rg.hi[0], lo2 = rg.lo[1], hi2 = rg.hi[1], lo3 = rg.lo[2], hi3 = rg.hi[2];
@@ -447,8 +499,9 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
       const float* s1 = Sv;
       const float* s2 = Sv + nS;
       const float* s3 = Sv + 2 * nS;
-      int k1v[NJ];
-      bool ok1[NJ];
+      constexpr int R = tc_pow2(NI);
+      int k1v[NJ], k2v[NI];
+      bool ok1[NJ], ok2[NI];
       float s1r[NJ];
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
@@ -459,53 +512,54 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
       float p2r[NI][NJ], b3[NI][NJ], d12[NI][NJ], s2r[NI];
 #pragma unroll
       for (int i = 0; i < NI; ++i) {
-        const int k2 = lo2 + warp + kTcWarps * i;
-        const bool ok2 = k2 < hi2;
-        s2r[i] = ok2 ? s2[k2] : 0.0f;
+        k2v[i] = lo2 + warp + kTcWarps * i;
+        ok2[i] = k2v[i] < hi2;
+        s2r[i] = ok2[i] ? s2[k2v[i]] : 0.0f;
+        if (!ok2[i]) k2v[i] = lo2;  // a valid row to read from; its contributions are zero or unused
 #pragma unroll
         for (int j = 0; j < NJ; ++j) {
-          const bool ok = ok2 && ok1[j];
-          p2r[i][j] = ok ? P2[k2 * ld + k1v[j]] : 0.0f;
-          d12[i][j] = ok ? lam + Lm[k1v[j]] + Lm[nS + k2] : 1.0f;
+          const bool ok = ok2[i] && ok1[j];
+          p2r[i][j] = ok ? P2[k2v[i] * ld + k1v[j]] : 0.0f;
+          d12[i][j] = ok ? lam + Lm[k1v[j]] + Lm[nS + k2v[i]] : 1.0f;
           b3[i][j] = 0.0f;
         }
       }
+      const int me = rs_index<R>(lane);  // the row whose B1 this lane receives
+      const bool wr1 = (lane & (32 / R - 1)) == 0 && me < NI;
       const int w1 = hi1 - lo1;
       for (int k3b = lo3; k3b < hi3; k3b += kTcKB) {
         const int nb = hi3 - k3b < kTcKB ? hi3 - k3b : kTcKB;
         for (int kb = 0; kb < nb; ++kb) {
           const int k3 = k3b + kb;
           const float s3k = s3[k3], l3 = Lm[2 * nS + k3];
-          float p1r[NJ], b2[NJ];
+          float p1r[NJ], b2[NJ], p0[NI], b1[R];
 #pragma unroll
           for (int j = 0; j < NJ; ++j) {
             p1r[j] = ok1[j] ? P1[k3 * ld + k1v[j]] : 0.0f;
             b2[j] = 0.0f;
           }
 #pragma unroll
+          for (int i = 0; i < NI; ++i) p0[i] = P0[k3 * ld + k2v[i]];
+#pragma unroll
+          for (int i = 0; i < R; ++i) b1[i] = 0.0f;
+#pragma unroll
           for (int i = 0; i < NI; ++i) {
-            const int k2 = lo2 + warp + kTcWarps * i;
-            if (k2 < hi2) {  // warp-uniform
-              const float p0 = P0[k3 * ld + k2];
-              float b1 = 0.0f;
 #pragma unroll
-              for (int j = 0; j < NJ; ++j) {
-                if (ok1[j]) {
-                  float e = s1r[j] * p0;
-                  e += s2r[i] * p1r[j];
-                  e += s3k * p2r[i][j];
-                  const float v = __fdividef(e, d12[i][j] + l3);
-                  b1 += s1r[j] * v;
-                  b2[j] += s2r[i] * v;
-                  b3[i][j] += s3k * v;
-                }
-              }
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) b1 += __shfl_xor_sync(0xffffffffu, b1, o);
-              // this warp alone reads P0[k3][k2]: B1[k3][k2] takes its place
-              if (lane == 0) P0[k3 * ld + k2] = rg.pa[0] ? b1 : 0.0f;
+            for (int j = 0; j < NJ; ++j) {
+              float e = s1r[j] * p0[i];
+              e += s2r[i] * p1r[j];
+              e += s3k * p2r[i][j];
+              const float v = __fdividef(e, d12[i][j] + l3);
+              b1[i] += s1r[j] * v;
+              b2[j] += s2r[i] * v;
+              b3[i][j] += s3k * v;
             }
           }
+          const float t1 = rs_reduce<R>(b1, lane);
+          // this warp alone reads P0[k3][k2] of its rows (all read above): B1 takes their place
+#pragma unroll
+          for (int i = 0; i < NI; ++i)
+            if (wr1 && me == i && ok2[i]) P0[k3 * ld + k2v[i]] = rg.pa[0] ? t1 : 0.0f;
 #pragma unroll
           for (int j = 0; j < NJ; ++j)
             if (ok1[j]) Yf[(warp * kTcKB + kb) * np + k1v[j]] = b2[j];
@@ -524,11 +578,10 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
       // B3 in place of P2 (the rows this warp owns and alone has read)
 #pragma unroll
       for (int i = 0; i < NI; ++i) {
-        const int k2 = lo2 + warp + kTcWarps * i;
-        if (k2 < hi2) {
+        if (ok2[i]) {
 #pragma unroll
           for (int j = 0; j < NJ; ++j)
-            if (ok1[j]) P2[k2 * ld + k1v[j]] = rg.pa[2] ? b3[i][j] : 0.0f;
+            if (ok1[j]) P2[k2v[i] * ld + k1v[j]] = rg.pa[2] ? b3[i][j] : 0.0f;
         }
       }
     }
@@ -538,9 +591,10 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
     for (int dd = 0; dd < 3 && !aborted; ++dd) {
       if (dd > 0) __syncthreads();  // the previous round's operand is consumed (round() waited)
       const float* B = X + dd * np * ld;
-      for (int idx = tid; idx < tb; idx += blockDim.x) {
-        const int kb = idx / np, ka = idx - kb * np;
-        Yo[tc_opoff<E>(ka, kb, np)] = OP::cvt(B[kb * ld + ka]);
+      for (int idx = tid; idx < tb; idx += blockDim.x) {  // operand memory order: whole core matrices
+        const int cm = idx / (8 * E), e = idx - cm * (8 * E);
+        const int ka = (cm / (np / E)) * 8 + e / E, kb = (cm % (np / E)) * E + e % E;
+        Yo[idx] = OP::cvt(B[kb * ld + ka]);
       }
       aborted = !round([&] { tc_product<OP>(tmem, dd * np, dd == 2 ? T1 : T0, Yo, np, np); });
     }
@@ -559,32 +613,42 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
           tc_product<OP>(tmem, 2 * np, Xo + 2 * tb, T0, np, np);
         }))
       break;
-    // 7. weights, multiplicity and mask -> the star's output planes
-    float* ob = Ob + st * 3 * (int64_t)n2;
+    // 7. weights, multiplicity and mask -> X rows [dd][jb][ja] (the O operands there are
+    //    consumed), then coalesced copies to the star's output planes
     readout(3 * np, [&](int row, int col, const float* v) {
       const int dd = col / np, k0 = col - dd * np, jb = row;
-      if (jb >= nS) return;
       const int ax_a = tc_ax_fast(dd), ax_b = tc_ax_slow(dd);
       const int obb = jb - m;
-      const bool rowact = Ac[dd * nS + m] && Ac[ax_b * nS + jb];
+      const bool rowact = jb < nS && Ac[dd * nS + m] && Ac[ax_b * nS + jb];
+      const float wb = rowact ? Wt[obb < 0 ? -obb : obb] : 0.0f;
+      float w[16];
+#pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const int ja = k0 + q;
-        if (ja >= nS) break;
-        const int oa = ja - m;
-        const bool active = rowact && Ac[ax_a * nS + ja];
-        const float wgt = t.w1d[oa < 0 ? -oa : oa] * t.w1d[obb < 0 ? -obb : obb] * rcp_mult[(oa == 0) + (obb == 0)];
-        ob[dd * n2 + jb * nS + ja] = active ? wgt * v[q] : 0.0f;
+        const int ja = k0 + q, oa = ja - m;
+        const bool active = rowact && ja < nS && Ac[ax_a * nS + ja];
+        w[q] = active ? Wt[oa < 0 ? -oa : oa] * wb * rcp_mult((oa == 0) + (obb == 0)) * v[q] : 0.0f;
       }
+      float* dst = X + (dd * np + row) * ld + k0;
+#pragma unroll
+      for (int q = 0; q < 16; q += 4) *reinterpret_cast<float4*>(dst + q) = make_float4(w[q], w[q + 1], w[q + 2], w[q + 3]);
     });
+    __syncthreads();
+    {
+      float* ob = Ob + st * 3 * (int64_t)n2;
+      for (int idx = tid; idx < 3 * n2; idx += blockDim.x) {
+        const int dd = idx / n2, rr = idx - dd * n2, jb = rr / nS, ja = rr - jb * nS;
+        ob[idx] = X[(dd * np + jb) * ld + ja];
+      }
+    }
     }  // !alias
     // next star
     if (counter) {
       __syncthreads();
       if (tid == 0) s_next = atomicAdd(&counter[0], 1) + (int)gridDim.x;
       __syncthreads();
-      st = s_next;
+      it = s_next;
     } else {
-      st += gridDim.x;
+      it += gridDim.x;
     }
   }
   if (s_abort) tc::mbar_wait(&s_mbar, phase ^ 1u, kTcWaitCycles);  // products still in flight
