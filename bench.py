@@ -55,9 +55,11 @@ FORMS = {"fp64": ("fp64", "mg", "star"), "mixed": ("mixed", "mg", "star"), "mixe
 MIXED_FORMS = ("mixed", "mixed_tc", "mixed_bf16")  # candidates for the result line's `mixed`
 DETAIL_FORMS = ("kmg_fp64", "kmg_mixed", "kmg_mixed_tc", "mixed_fp32", "mixed_fp32_tc")
 FP64_NOMINAL_TFLOPS = 1.25  # 2 FP64 FMA / clock / SM x 152 SMs x 2.07 GHz: fallback when the probe fails
-# DRAM bytes (read + write) per k_star<double> launch of the headline workload, from the ncu
-# capture named in the profiles (null once the star kernel's source changed since: hash below)
-STAR_TRAFFIC = {"bytes_per_launch": None, "source": None}
+# DRAM bytes (read + write) per k_star<double> launch of the timed FP64 region of the headline
+# workload (all levels, every launch of two steps), from an ncu capture of that region
+# (dram__bytes_read.sum + dram__bytes_write.sum); null once the star kernel's source changed since
+# (hash below).  Mostly the per-class 1/D tables (6.9 MB per star at p = 48).
+STAR_TRAFFIC = {"bytes_per_launch": 5.520e8, "source": "893852f947b890f2"}
 STAR_SOURCES = ("star_kernel.cuh", "kernels_star_f64.cu")
 MAX_LINE = 1400  # bytes of the result line (the last stdout line)
 
@@ -327,13 +329,17 @@ def run_semmg(args, world, rank, local, pg):
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
+    torch.cuda.nvtx.range_push("fp64_timed")  # NVTX ranges name the timed regions for profilers
     t64, info64 = timed_solves(ctx["fp64"], fd, ud, K, flush, stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier(pg)
     tform, iters = {}, {"fp64": info64.iters}
     for form in forms[1:]:
+        torch.cuda.nvtx.range_push(f"{form}_timed")
         tform[form], inf = timed_solves(ctx[form], fd, ud, K, flush, stream)
+        torch.cuda.nvtx.range_pop()
         iters[form] = inf.iters
     # end to end through the host-buffer entry point (pinned host f in, u out)
     te2e = float("nan")
@@ -468,13 +474,15 @@ def run_sweep(args, dev, stream, flush, details):
 def run_configs(args, dev, stream, flush, details):
     """The other workloads of the paper's shape, one solve per step per form (not part of `value`):
     Helmholtz 16^3 at p = 16 (lambda 0 and 100, Dirichlet; lambda 1 with Neumann faces and periodic),
-    and the Sec. 5.2 problem (8^3, k = 5, Dirichlet data) at p = 16 and 32."""
+    Helmholtz 8^3 at p = 16 with the element-centred block smoother (Sec. 3.4), and the Sec. 5.2
+    problem (8^3, k = 5, Dirichlet data) at p = 16 and 32."""
     import torch
     from paper_1808_03595_gb300 import Context
     plan = [("helmholtz_16x16x16_p16", 0.0, None, ["fp64", "mixed", "mixed_tc", "kmg_mixed"]),
             ("helmholtz_16x16x16_p16", 100.0, None, ["fp64", "mixed"]),
             ("helmholtz_16x16x16_p16", 1.0, ("N",) * 6, ["fp64", "mixed"]),
             ("helmholtz_16x16x16_p16", 1.0, ("P",) * 6, ["fp64", "mixed"]),
+            ("helmholtz_8x8x8_p16", None, None, ["eblock_fp64", "eblock_mixed"]),
             ("paper_sec52_8x8x8_p16", 0.0, None, ["fp64", "mixed", "kmg_mixed"]),
             ("paper_sec52_8x8x8_p32", 0.0, None, ["fp64", "mixed", "kmg_mixed"])]
     for name, lam, bc, forms in plan:
@@ -519,8 +527,8 @@ def run_configs(args, dev, stream, flush, details):
 
 def run_batch(args, dev, stream, flush, details):
     """64 independent Helmholtz solves (n ~ U{2..12}, p ~ U{4..24}, lambda = 10^U(-2,3)) in one CUDA graph
-    launch, in the mixed form (Algorithms 4 and 5) and in the plain FP64 form (the same graph, and
-    sequential solve calls); throughput = total unknowns / time per batch."""
+    launch, in the mixed form with the tensor-core smoother (Algorithms 4 and 5) and in the plain FP64
+    form (the same graph, and sequential solve calls); throughput = total unknowns / time per batch."""
     import torch
     from paper_1808_03595_gb300 import Batch, Context
     cases = workloads.batch64()
@@ -558,8 +566,8 @@ def run_batch(args, dev, stream, flush, details):
             c.close()
         return res
 
-    out["mixed_mg"] = graph("mixed", "mg")
-    out["mixed_kmg"] = graph("mixed", "kmg")
+    out["mixed_mg"] = graph("mixed_tc", "mg")
+    out["mixed_kmg"] = graph("mixed_tc", "kmg")
     out["fp64_mg"] = graph("fp64", "mg")
     # the plain FP64 form as a user without the batched entry point runs it: one solve call after another
     ctxs = [Context(h, p, lam, p0=2, precision="fp64", solver="mg") for h, p, lam, _ in cases]

@@ -703,7 +703,7 @@ void apply_op(semmg_ctx* c, int l, const Tabs<T>& tb, const LaunchCfg& cfg, cons
     }
     Tic t(c, SEMMG_K_ASSEMBLE, st);
     launch_face_bwd_assemble<T, TF>(G, tb, F, u, (const T*)c->Uts, (const T*)c->Zs, out, mode, st);
-    t.toc(0.0, vec * (mode == 0 ? 2 : 1) + uvec + zb);
+    t.toc(0.0, vec * (mode == 0 ? 2 : 1) + uvec + zb, 2);  // face back transforms, edge and vertex slots
     return;
   }
   {
