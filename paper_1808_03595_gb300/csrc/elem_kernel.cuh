@@ -28,6 +28,28 @@ namespace semmg {
 
 namespace {
 
+// The threads working on one element: the CTA, or the two CTAs of a cluster.
+// Work items are spread over all of them (id, n) and phases are separated by
+// sync(): a CTA barrier, or a cluster barrier with release / acquire
+// semantics, which orders the global-memory work arrays the two CTAs share.
+struct Team {
+  int id, n, cs;
+  __device__ __forceinline__ static Team block() { return Team{(int)threadIdx.x, (int)blockDim.x, 1}; }
+  __device__ __forceinline__ void sync() const {
+    if (cs == 1)
+      __syncthreads();
+    else
+      asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+  }
+};
+
+// The team of a kernel launched with clusters of cs CTAs (cs = 1: no clusters).
+__device__ __forceinline__ Team team_of(int cs) {
+  unsigned rank = 0;
+  if (cs > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  return Team{(int)(rank * blockDim.x + threadIdx.x), (int)(cs * blockDim.x), cs};
+}
+
 template <typename T>
 struct ElemScal {
   T sf[3];      // c_f alpha_d for the two faces of axis d
@@ -71,9 +93,9 @@ struct Lines {
 };
 
 template <typename T>
-__device__ __forceinline__ void fold_lines(const Lines& L, int ax, const T* X, T* Y) {
+__device__ __forceinline__ void fold_lines(const Lines& L, int ax, const T* X, T* Y, const Team& tm = Team::block()) {
   const int str = L.stride(ax);
-  for (int idx = threadIdx.x; idx < L.total; idx += blockDim.x) {
+  for (int idx = tm.id; idx < L.total; idx += tm.n) {
     const int j = L.pos(idx, ax);
     const int base = idx - j * str;
     T v;
@@ -174,10 +196,10 @@ __device__ __forceinline__ void line_block(const Lines& L, int g, int* k0, int* 
 // Z = (scale or sc2[i2]) * forward transform of folded Y along ax.
 template <typename T>
 __device__ __forceinline__ void tx_lines_g(const Lines& L, int ax, const T* __restrict__ S, const T* Y, T* Z,
-                                           T scale, const T* sc2) {
+                                           T scale, const T* sc2, const Team& tm = Team::block()) {
   const int G = line_groups(L), n = L.n;
   const int items = nlines(L) * G;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+  for (int it = tm.id; it < items; it += tm.n) {
     const int l = it / G, g = it - l * G;
     int base, str, i2, k0, k1, j0, j1, even;
     line_of(L, ax, l, &base, &str, &i2);
@@ -201,10 +223,11 @@ __device__ __forceinline__ void tx_lines_g(const Lines& L, int ax, const T* __re
 
 // Y = transposed transform of B along ax into folded form (E_j, O_q).
 template <typename T>
-__device__ __forceinline__ void txT_lines_g(const Lines& L, int ax, const T* __restrict__ S, const T* B, T* Y) {
+__device__ __forceinline__ void txT_lines_g(const Lines& L, int ax, const T* __restrict__ S, const T* B, T* Y,
+                                            const Team& tm = Team::block()) {
   const int G = line_groups(L), n = L.n;
   const int items = nlines(L) * G;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+  for (int it = tm.id; it < items; it += tm.n) {
     const int l = it / G, g = it - l * G;
     int base, str, i2, k0, k1, j0, j1, even;
     line_of(L, ax, l, &base, &str, &i2);
@@ -241,16 +264,16 @@ __device__ __forceinline__ T unfold_at(const Lines& L, int ax, const T* Y, int i
 }
 
 template <typename T>
-__device__ __forceinline__ void unfold_lines(const Lines& L, int ax, const T* Y, T* X) {
-  for (int idx = threadIdx.x; idx < L.total; idx += blockDim.x) X[idx] = unfold_at(L, ax, Y, idx);
+__device__ __forceinline__ void unfold_lines(const Lines& L, int ax, const T* Y, T* X, const Team& tm = Team::block()) {
+  for (int idx = tm.id; idx < L.total; idx += tm.n) X[idx] = unfold_at(L, ax, Y, idx);
 }
 
 // ---------------------------------------------------------------- face helpers
 // Six faces X[f][ib][ia] (f = 2d + side) -> pair sums and differences
 // X[2d] = X[2d] + X[2d+1], X[2d+1] = X[2d] - X[2d+1].
 template <typename T>
-__device__ __forceinline__ void face_pairs(int mm, T* X) {
-  for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
+__device__ __forceinline__ void face_pairs(int mm, T* X, const Team& tm = Team::block()) {
+  for (int idx = tm.id; idx < 3 * mm; idx += tm.n) {
     const int d = idx / mm, r = idx - d * mm;
     const T a = X[(2 * d) * mm + r], b = X[(2 * d + 1) * mm + r];
     X[(2 * d) * mm + r] = a + b;
@@ -260,31 +283,33 @@ __device__ __forceinline__ void face_pairs(int mm, T* X) {
 
 // forward 2D transform of the six face arrays, scaled by c_f alpha_d
 template <typename T>
-__device__ __forceinline__ void faces_forward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc) {
+__device__ __forceinline__ void faces_forward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc,
+                                              const Team& tm = Team::block()) {
   __shared__ T sc6[6];
   if (threadIdx.x < 6) sc6[threadIdx.x] = sc.sf[threadIdx.x >> 1];
-  fold_lines(F, 0, X, Tt);
-  __syncthreads();
-  tx_lines_g(F, 0, Sh, Tt, X, (T)1, (const T*)nullptr);
-  __syncthreads();
-  fold_lines(F, 1, X, Tt);
-  __syncthreads();
-  tx_lines_g(F, 1, Sh, Tt, X, (T)1, (const T*)sc6);
-  __syncthreads();
+  fold_lines(F, 0, X, Tt, tm);
+  tm.sync();
+  tx_lines_g(F, 0, Sh, Tt, X, (T)1, (const T*)nullptr, tm);
+  tm.sync();
+  fold_lines(F, 1, X, Tt, tm);
+  tm.sync();
+  tx_lines_g(F, 1, Sh, Tt, X, (T)1, (const T*)sc6, tm);
+  tm.sync();
 }
 
 // Back transform of the six reduced arrays (pairs: even / odd parts of axis d)
 // and store of both faces: Z[2d] = sf (Ye + Yo), Z[2d+1] = sf (Ye - Yo).
 template <typename T, typename Store>
-__device__ __forceinline__ void faces_backward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc, Store store) {
-  txT_lines_g(F, 0, Sh, X, Tt);
-  __syncthreads();
-  unfold_lines(F, 0, Tt, X);
-  __syncthreads();
-  txT_lines_g(F, 1, Sh, X, Tt);
-  __syncthreads();
+__device__ __forceinline__ void faces_backward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc, Store store,
+                                               const Team& tm = Team::block()) {
+  txT_lines_g(F, 0, Sh, X, Tt, tm);
+  tm.sync();
+  unfold_lines(F, 0, Tt, X, tm);
+  tm.sync();
+  txT_lines_g(F, 1, Sh, X, Tt, tm);
+  tm.sync();
   const int mm = F.D0 * F.D1;
-  for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
+  for (int idx = tm.id; idx < 3 * mm; idx += tm.n) {
     const int d = idx / mm, r = idx - d * mm;
     const T ye = unfold_at(F, 1, Tt, (2 * d) * mm + r);
     const T yo = unfold_at(F, 1, Tt, (2 * d + 1) * mm + r);
@@ -303,9 +328,9 @@ __device__ __forceinline__ T face_expand(int m, int ne, const T* a0, const T* X,
 
 // X[2d + parity][kb][ka] <- sum over k_d of that parity of a0[k_d] W(k)
 template <typename T>
-__device__ __forceinline__ void faces_reduce(int m, int ne, const T* a0, const T* W, T* X) {
+__device__ __forceinline__ void faces_reduce(int m, int ne, const T* a0, const T* W, T* X, const Team& tm = Team::block()) {
   const int mm = m * m;
-  for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
+  for (int idx = tm.id; idx < 6 * mm; idx += tm.n) {
     const int f = idx / mm, r = idx - f * mm, kb = r / m, ka = r - kb * m;
     const int k0 = (f & 1) ? ne : 0, k1 = (f & 1) ? m : ne;
     const T* w;
@@ -410,25 +435,36 @@ __device__ __forceinline__ void elem_coords(const Geo& G, int64_t e, int* a1, in
 // elements' terms are summed.
 template <typename T, int PC, int NB>
 __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const T* __restrict__ u,
-                                                         T* __restrict__ Z, T* ws, WsPlan wp, int pre) {
+                                                         T* __restrict__ Z, T* ws, WsPlan wp, int pre, int cs) {
+  // cs = 2 (eigenbasis mode, W in global memory): the two CTAs of a cluster share an
+  // element: each keeps its own copy of the face data X, the expansion into W is split
+  // over both (one cluster barrier), and each reduces and stores its own half of the
+  // in-face index r, so nothing else crosses CTAs; every output has the summation order
+  // of cs = 1
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = PC ? PC - 1 : G.m, mm = m * m;
   const int64_t n3 = (int64_t)mm * m;
-  T* Sh = ws_ptr<T>(wp, 0, smem_raw, ws);
+  const Team tm = team_of(cs);
+  const int crank = tm.id / (int)blockDim.x;
+  auto at = [&](int i) {
+    return wp.in_smem[i] ? reinterpret_cast<T*>(smem_raw) + wp.off[i] : ws + (blockIdx.x / cs) * wp.gstride + wp.off[i];
+  };
+  T* Sh = at(0);
   T* a0 = Sh + mm;
   T* lI = a0 + m;
-  T* X = ws_ptr<T>(wp, 1, smem_raw, ws);
-  T* Tt = ws_ptr<T>(wp, 2, smem_raw, ws);
-  T* W = ws_ptr<T>(wp, 3, smem_raw, ws);
+  T* X = at(1);
+  T* Tt = at(2);
+  T* W = at(3);
   load_tables(m, t, Sh, a0, lI);
   const Lines F{m, m / 2, (m + 1) / 2, m, m, 6 * mm};
   const int ne = F.ne;
   const T lam = (T)G.lam;
-  for (int64_t e = blockIdx.x; e < G.nelem; e += gridDim.x) {
+  const int rlo = crank * mm / cs, rhi = (crank + 1) * mm / cs, nr = rhi - rlo;  // this CTA's r range
+  for (int64_t e = blockIdx.x / cs; e < G.nelem; e += gridDim.x / cs) {
     int a1, a2, a3;
     elem_coords(G, e, &a1, &a2, &a3);
     const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
-    __syncthreads();
+    tm.sync();  // W (shared by the cluster) is free again
     for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
       const int f = idx / mm;
       X[idx] = u[elem_face_base(G, a1, a2, a3, f) + (idx - f * mm)];
@@ -448,16 +484,34 @@ __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const 
       __syncthreads();
       faces_forward(F, Sh, X, Tt, sc);
     }
-    for (int64_t idx = threadIdx.x; idx < n3; idx += blockDim.x) {
+    for (int64_t idx = tm.id; idx < n3; idx += tm.n) {
       const int k1 = (int)(idx % m), k2 = (int)((idx / m) % m), k3 = (int)(idx / mm);
       W[idx] = face_expand(m, ne, a0, X, k1, k2, k3) * inv_d(t, sc, lI, lam, idx, k1, k2, k3, n3);
     }
-    __syncthreads();
-    faces_reduce_rows(m, ne, a0, W, 0, m, X);
+    tm.sync();
+    if (cs == 1) {
+      faces_reduce_rows(m, ne, a0, W, 0, m, X);
+    } else {
+      // faces 0..3 on this CTA's r range, each output as faces_reduce_rows sums it
+      for (int idx = threadIdx.x; idx < 4 * nr; idx += blockDim.x) {
+        const int f = idx / nr, r = rlo + (idx - f * nr), k3 = r / m, kx = r - k3 * m;
+        const int k0 = (f & 1) ? ne : 0, k1 = (f & 1) ? m : ne;
+        const T* w = f < 2 ? W + (k3 * m + kx) * m : W + k3 * mm + kx;
+        const int wst = f < 2 ? 1 : m;
+        T s0 = 0, s1 = 0;
+        int k = k0;
+        for (; k + 1 < k1; k += 2) {
+          s0 += a0[k] * w[k * wst];
+          s1 += a0[k + 1] * w[(k + 1) * wst];
+        }
+        if (k < k1) s0 += a0[k] * w[k * wst];
+        X[f * mm + r] = s0 + s1;
+      }
+    }
     // faces 4, 5: slab partials in order (schur_slab(m) k3-rows each)
     const int slab = schur_slab(m);
-    for (int idx = threadIdx.x; idx < 2 * mm; idx += blockDim.x) {
-      const int f = idx / mm, r = idx - f * mm;
+    for (int idx = threadIdx.x; idx < 2 * nr; idx += blockDim.x) {
+      const int f = idx / nr, r = rlo + (idx - f * nr);
       const int flo = f ? ne : 0, fhi = f ? m : ne;
       T tot = 0;
       for (int r0 = 0; r0 < m; r0 += slab) {
@@ -471,8 +525,8 @@ __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const 
     __syncthreads();
     T* Ze = Z + e * 6 * mm;
     if (pre) {
-      for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
-        const int d = idx / mm, r = idx - d * mm;
+      for (int idx = threadIdx.x; idx < 3 * nr; idx += blockDim.x) {
+        const int d = idx / nr, r = rlo + (idx - d * nr);
         const T xe = X[(2 * d) * mm + r], xo = X[(2 * d + 1) * mm + r];
         Ze[(2 * d) * mm + r] = sc.al[d] * (xe + xo);
         Ze[(2 * d + 1) * mm + r] = sc.al[d] * (xe - xo);
@@ -485,34 +539,35 @@ __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const 
 
 // Interior 3D transforms with the folded reference eigenvectors.
 // forward: A <- scale * (Sref^T (x) Sref^T (x) Sref^T) A, B is scratch.
-__device__ __forceinline__ void interior_forward(const Lines& I, const double* Sr, double* A, double* B, double scale) {
-  fold_lines(I, 0, A, B);
-  __syncthreads();
-  tx_lines_g(I, 0, Sr, B, A, 1.0, (const double*)nullptr);
-  __syncthreads();
-  fold_lines(I, 1, A, B);
-  __syncthreads();
-  tx_lines_g(I, 1, Sr, B, A, 1.0, (const double*)nullptr);
-  __syncthreads();
-  fold_lines(I, 2, A, B);
-  __syncthreads();
-  tx_lines_g(I, 2, Sr, B, A, scale, (const double*)nullptr);
-  __syncthreads();
+__device__ __forceinline__ void interior_forward(const Lines& I, const double* Sr, double* A, double* B, double scale,
+                                                 const Team& tm) {
+  fold_lines(I, 0, A, B, tm);
+  tm.sync();
+  tx_lines_g(I, 0, Sr, B, A, 1.0, (const double*)nullptr, tm);
+  tm.sync();
+  fold_lines(I, 1, A, B, tm);
+  tm.sync();
+  tx_lines_g(I, 1, Sr, B, A, 1.0, (const double*)nullptr, tm);
+  tm.sync();
+  fold_lines(I, 2, A, B, tm);
+  tm.sync();
+  tx_lines_g(I, 2, Sr, B, A, scale, (const double*)nullptr, tm);
+  tm.sync();
 }
 
 // backward along x3 and x2 (natural order in A afterwards), then the x1
 // transposed transform into B; the caller unfolds B along x1.
-__device__ __forceinline__ void interior_backward(const Lines& I, const double* Sr, double* A, double* B) {
-  txT_lines_g(I, 2, Sr, A, B);
-  __syncthreads();
-  unfold_lines(I, 2, B, A);
-  __syncthreads();
-  txT_lines_g(I, 1, Sr, A, B);
-  __syncthreads();
-  unfold_lines(I, 1, B, A);
-  __syncthreads();
-  txT_lines_g(I, 0, Sr, A, B);
-  __syncthreads();
+__device__ __forceinline__ void interior_backward(const Lines& I, const double* Sr, double* A, double* B, const Team& tm) {
+  txT_lines_g(I, 2, Sr, A, B, tm);
+  tm.sync();
+  unfold_lines(I, 2, B, A, tm);
+  tm.sync();
+  txT_lines_g(I, 1, Sr, A, B, tm);
+  tm.sync();
+  unfold_lines(I, 1, B, A, tm);
+  tm.sync();
+  txT_lines_g(I, 0, Sr, A, B, tm);
+  tm.sync();
 }
 
 struct FdmSmem {
@@ -520,16 +575,21 @@ struct FdmSmem {
 };
 
 // Work regions: 0 tables (Sh, Sref, a0, Lam), 1 X (6 m^2), 2 Tt (6 m^2), 3 A+B (2 m^3).
-__device__ FdmSmem fdm_layout(int m, unsigned char* smem, double* ws, const WsPlan& wp) {
+// Work arrays of the team: shared memory of this CTA, or the team's slice of the global
+// workspace (slice = the team's index: the CTA, or the cluster, in the grid).
+__device__ FdmSmem fdm_layout(int m, unsigned char* smem, double* ws, const WsPlan& wp, int64_t slice) {
   const int mm = m * m;
+  auto at = [&](int i) {
+    return wp.in_smem[i] ? reinterpret_cast<double*>(smem) + wp.off[i] : ws + slice * wp.gstride + wp.off[i];
+  };
   FdmSmem s;
-  s.Sh = ws_ptr<double>(wp, 0, smem, ws);
+  s.Sh = at(0);
   s.Sr = s.Sh + mm;
   s.a0 = s.Sr + mm;
   s.lI = s.a0 + m;
-  s.X = ws_ptr<double>(wp, 1, smem, ws);
-  s.Tt = ws_ptr<double>(wp, 2, smem, ws);
-  s.A = ws_ptr<double>(wp, 3, smem, ws);
+  s.X = at(1);
+  s.Tt = at(2);
+  s.A = at(3);
   s.B = s.A + (int64_t)mm * m;
   return s;
 }
@@ -542,21 +602,23 @@ __device__ __forceinline__ int64_t interior_node(const Geo& G, int a1, int a2, i
 }
 
 // Z[e][f] = (H_BI H_II^{-1} F_I) on the faces, F_I = (M f)_I element-local.
-template <int PC>
 // When Gsave is given, the scaled interior eigen-coefficients
 // D^{-1} (S^T x S^T x S^T) F_I of every element are also stored there
-// (m^3 per element), for the recovery of the same solve.
+// (m^3 per element), for the recovery of the same solve.  cs = 2: launched in
+// clusters of two CTAs that share each element's work (global work arrays).
+template <int PC>
 __global__ void __launch_bounds__(512, 1) k_elem_condense(Geo G, Tabs<double> t, const double* __restrict__ f,
                                                         double* __restrict__ Z, double* __restrict__ Gsave,
-                                                        double* ws, WsPlan wp) {
+                                                        double* ws, WsPlan wp, int cs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = PC ? PC - 1 : G.m, mm = m * m, mmm = mm * m;
-  FdmSmem s = fdm_layout(m, smem_raw, ws, wp);
+  const Team tm = team_of(cs);
+  FdmSmem s = fdm_layout(m, smem_raw, ws, wp, blockIdx.x / cs);
   load_tables(m, t, s.Sh, s.a0, s.lI);
   for (int i = threadIdx.x; i < mm; i += blockDim.x) s.Sr[i] = t.Sref[i];
   const Lines F{m, m / 2, (m + 1) / 2, m, m, 6 * mm};
   const Lines I{m, m / 2, (m + 1) / 2, m, m, mmm};
-  for (int64_t e = blockIdx.x; e < G.nelem; e += gridDim.x) {
+  for (int64_t e = blockIdx.x / cs; e < G.nelem; e += gridDim.x / cs) {
     int a1, a2, a3;
     elem_coords(G, e, &a1, &a2, &a3);
     const ElemScal<double> sc = elem_scalars(t, a1, a2, a3);
@@ -565,44 +627,46 @@ __global__ void __launch_bounds__(512, 1) k_elem_condense(Geo G, Tabs<double> t,
     const double* x3 = t.hx[2] + 6 * a3;
     const double vol = 0.125 * x1[0] * x2[0] * x3[0];  // h1 h2 h3 / 8
     const double sig = x1[5] * x2[5] * x3[5];          // sqrt(8 / (h1 h2 h3))
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
+    tm.sync();
+    for (int idx = tm.id; idx < mmm; idx += tm.n) {
       const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / mm;
       s.A[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] * f[interior_node(G, a1, a2, a3, idx)];
     }
-    __syncthreads();
-    interior_forward(I, s.Sr, s.A, s.B, sig);
+    tm.sync();
+    interior_forward(I, s.Sr, s.A, s.B, sig, tm);
     double* Ge = Gsave ? Gsave + e * (int64_t)mmm : nullptr;
-    for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
+    for (int idx = tm.id; idx < mmm; idx += tm.n) {
       const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
       const double v = s.A[idx] * inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
       s.A[idx] = v;
       if (Ge) Ge[idx] = v;
     }
-    __syncthreads();
-    faces_reduce(m, F.ne, s.a0, s.A, s.X);
-    __syncthreads();
+    tm.sync();
+    faces_reduce(m, F.ne, s.a0, s.A, s.X, tm);
+    tm.sync();
     double* Ze = Z + e * 6 * mm;
-    faces_backward(F, s.Sh, s.X, s.Tt, sc, [&](int idx, double v) { Ze[idx] = v; });
+    faces_backward(F, s.Sh, s.X, s.Tt, sc, [&](int idx, double v) { Ze[idx] = v; }, tm);
   }
 }
 
 // u_I = H_II^{-1} (F_I - H_IB uhat) written into the nodal array.  With Gin
 // (the coefficients k_elem_condense stored for the same f) the forward
-// transform of F_I is taken from there instead of being recomputed.
+// transform of F_I is taken from there instead of being recomputed.  cs as
+// for k_elem_condense.
 template <int PC>
 __global__ void __launch_bounds__(512, 1) k_elem_recover(Geo G, Tabs<double> t, const double* __restrict__ f,
                                                        const double* __restrict__ Gin,
                                                        const double* __restrict__ uh, double* __restrict__ un,
-                                                       double* ws, WsPlan wp) {
+                                                       double* ws, WsPlan wp, int cs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = PC ? PC - 1 : G.m, mm = m * m, mmm = mm * m;
-  FdmSmem s = fdm_layout(m, smem_raw, ws, wp);
+  const Team tm = team_of(cs);
+  FdmSmem s = fdm_layout(m, smem_raw, ws, wp, blockIdx.x / cs);
   load_tables(m, t, s.Sh, s.a0, s.lI);
   for (int i = threadIdx.x; i < mm; i += blockDim.x) s.Sr[i] = t.Sref[i];
   const Lines F{m, m / 2, (m + 1) / 2, m, m, 6 * mm};
   const Lines I{m, m / 2, (m + 1) / 2, m, m, mmm};
-  for (int64_t e = blockIdx.x; e < G.nelem; e += gridDim.x) {
+  for (int64_t e = blockIdx.x / cs; e < G.nelem; e += gridDim.x / cs) {
     int a1, a2, a3;
     elem_coords(G, e, &a1, &a2, &a3);
     const ElemScal<double> sc = elem_scalars(t, a1, a2, a3);
@@ -611,39 +675,39 @@ __global__ void __launch_bounds__(512, 1) k_elem_recover(Geo G, Tabs<double> t, 
     const double* x3 = t.hx[2] + 6 * a3;
     const double vol = 0.125 * x1[0] * x2[0] * x3[0];  // h1 h2 h3 / 8
     const double sig = x1[5] * x2[5] * x3[5];          // sqrt(8 / (h1 h2 h3))
-    __syncthreads();
+    tm.sync();
     if (!Gin) {
-      for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
+      for (int idx = tm.id; idx < mmm; idx += tm.n) {
         const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / mm;
         s.A[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] * f[interior_node(G, a1, a2, a3, idx)];
       }
     }
-    for (int idx = threadIdx.x; idx < 6 * mm; idx += blockDim.x) {
+    for (int idx = tm.id; idx < 6 * mm; idx += tm.n) {
       const int fc = idx / mm;
       s.X[idx] = uh[elem_face_base(G, a1, a2, a3, fc) + (idx - fc * mm)];
     }
-    __syncthreads();
-    if (!Gin) interior_forward(I, s.Sr, s.A, s.B, sig);
-    face_pairs(mm, s.X);
-    __syncthreads();
-    faces_forward(F, s.Sh, s.X, s.Tt, sc);
+    tm.sync();
+    if (!Gin) interior_forward(I, s.Sr, s.A, s.B, sig, tm);
+    face_pairs(mm, s.X, tm);
+    tm.sync();
+    faces_forward(F, s.Sh, s.X, s.Tt, sc, tm);
     if (Gin) {
       const double* Ge = Gin + e * (int64_t)mmm;
-      for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
+      for (int idx = tm.id; idx < mmm; idx += tm.n) {
         const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
         s.A[idx] = Ge[idx] - face_expand(m, F.ne, s.a0, s.X, k1, k2, k3) *
                                  inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
       }
     } else {
-      for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x) {
+      for (int idx = tm.id; idx < mmm; idx += tm.n) {
         const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
         s.A[idx] = (s.A[idx] - face_expand(m, F.ne, s.a0, s.X, k1, k2, k3)) *
                    inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
       }
     }
-    __syncthreads();
-    interior_backward(I, s.Sr, s.A, s.B);
-    for (int idx = threadIdx.x; idx < mmm; idx += blockDim.x)
+    tm.sync();
+    interior_backward(I, s.Sr, s.A, s.B, tm);
+    for (int idx = tm.id; idx < mmm; idx += tm.n)
       un[interior_node(G, a1, a2, a3, idx)] = sig * unfold_at(I, 0, s.B, idx);
   }
 }
@@ -667,6 +731,18 @@ LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t cap, int block, int wide
   const int64_t grid = (int64_t)nsm * resident_blocks(c, wide);
   c.grid = (int)(G.nelem < grid ? G.nelem : grid);
   if (c.grid < 1) c.grid = 1;
+  // eigenbasis mode with the eigenspace array W in global memory: two CTAs per element (a
+  // cluster) when halving the work units shortens a partial last wave.  Each CTA keeps its
+  // own tables and face data X (transformed in place), so both must be in shared memory.
+  // Rounds are counted per SM (CTAs sharing an SM share its throughput).
+  if (face_form(G) && c.ws.in_smem[0] && c.ws.in_smem[1] && !c.ws.in_smem[3] && grid >= 2) {
+    const int64_t r1 = (G.nelem + nsm - 1) / nsm, r2 = (2 * G.nelem + nsm - 1) / nsm;
+    if (r2 < 2 * r1) {
+      c.cluster = 2;
+      const int64_t nc = G.nelem < grid / 2 ? G.nelem : grid / 2;
+      c.grid = (int)(2 * nc);
+    }
+  }
   return c;
 }
 
@@ -674,12 +750,12 @@ template <typename T, int NB>
 void launch_elem_schur_nb(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws, const LaunchCfg& c,
                           cudaStream_t st, int pre) {
   switch (G.p) {
-    case 2: k_elem_schur<T, 2, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws, pre); break;
-    case 4: k_elem_schur<T, 4, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws, pre); break;
-    case 8: k_elem_schur<T, 8, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws, pre); break;
-    case 16: k_elem_schur<T, 16, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws, pre); break;
-    case 32: k_elem_schur<T, 32, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws, pre); break;
-    default: k_elem_schur<T, 0, NB><<<c.grid, c.block, c.smem, st>>>(G, t, u, Z, ws, c.ws, pre); break;
+    case 2: launch_clustered(k_elem_schur<T, 2, NB>, c, st, G, t, u, Z, ws, c.ws, pre, c.cluster); break;
+    case 4: launch_clustered(k_elem_schur<T, 4, NB>, c, st, G, t, u, Z, ws, c.ws, pre, c.cluster); break;
+    case 8: launch_clustered(k_elem_schur<T, 8, NB>, c, st, G, t, u, Z, ws, c.ws, pre, c.cluster); break;
+    case 16: launch_clustered(k_elem_schur<T, 16, NB>, c, st, G, t, u, Z, ws, c.ws, pre, c.cluster); break;
+    case 32: launch_clustered(k_elem_schur<T, 32, NB>, c, st, G, t, u, Z, ws, c.ws, pre, c.cluster); break;
+    default: launch_clustered(k_elem_schur<T, 0, NB>, c, st, G, t, u, Z, ws, c.ws, pre, c.cluster); break;
   }
 }
 

@@ -17,19 +17,35 @@ LaunchCfg plan_elem_fdm(const Geo& G, int nsm) {
     c.block = 512;
   }
   // the kernels are built for up to 128 registers per thread (512 resident threads per SM)
-  const int64_t grid = (int64_t)nsm * resident_blocks(c, 1);
-  c.grid = (int)(G.nelem < grid ? G.nelem : grid);
+  const int64_t slots = (int64_t)nsm * resident_blocks(c, 1);
+  c.grid = (int)(G.nelem < slots ? G.nelem : slots);
   if (c.grid < 1) c.grid = 1;
+  // Two CTAs per element (a cluster) when the elements fill the SMs in a partial last wave
+  // that halving the work units shortens (6^3 elements at p = 48: 216 units on 152 SMs take
+  // 2 rounds; 432 half units on 76 clusters take 3 half rounds), and only when every work
+  // array but the tables is in global memory already (the two CTAs share them there; each
+  // keeps its own copy of the tables in shared memory).
+  if (c.ws.in_smem[0] && !c.ws.in_smem[1] && !c.ws.in_smem[2] && !c.ws.in_smem[3] && slots >= 2) {
+    // rounds per SM (CTAs sharing an SM share its throughput)
+    const int64_t r1 = (G.nelem + nsm - 1) / nsm;          // rounds of whole elements
+    const int64_t r2 = (2 * G.nelem + nsm - 1) / nsm;      // rounds of half elements
+    if (r2 < 2 * r1) {
+      c.cluster = 2;
+      const int64_t nc = G.nelem < slots / 2 ? G.nelem : slots / 2;
+      c.grid = (int)(2 * nc);
+    }
+  }
   return c;
 }
+
 
 void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f, double* Z, double* Gsave,
                           double* ws, const LaunchCfg& c, cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
   switch (G.p) {
-    case 16: k_elem_condense<16><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, Gsave, ws, c.ws); break;
-    case 32: k_elem_condense<32><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, Gsave, ws, c.ws); break;
-    default: k_elem_condense<0><<<c.grid, c.block, c.smem, st>>>(G, t, f, Z, Gsave, ws, c.ws); break;
+    case 16: launch_clustered(k_elem_condense<16>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
+    case 32: launch_clustered(k_elem_condense<32>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
+    default: launch_clustered(k_elem_condense<0>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
   }
 }
 
@@ -37,9 +53,9 @@ void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f, c
                          const double* uh, double* un, double* ws, const LaunchCfg& c, cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
   switch (G.p) {
-    case 16: k_elem_recover<16><<<c.grid, c.block, c.smem, st>>>(G, t, f, Gin, uh, un, ws, c.ws); break;
-    case 32: k_elem_recover<32><<<c.grid, c.block, c.smem, st>>>(G, t, f, Gin, uh, un, ws, c.ws); break;
-    default: k_elem_recover<0><<<c.grid, c.block, c.smem, st>>>(G, t, f, Gin, uh, un, ws, c.ws); break;
+    case 16: launch_clustered(k_elem_recover<16>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
+    case 32: launch_clustered(k_elem_recover<32>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
+    default: launch_clustered(k_elem_recover<0>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
   }
 }
 

@@ -362,6 +362,7 @@ struct LaunchCfg {
   int wide = 0;
   int depth = 0;                 // element-block kernel: k3-planes of the eigenspace slab
   int bf16 = 0;                  // tensor-core star kernel: BF16 operands (else TF32)
+  int cluster = 1;               // CTAs per cluster sharing one work item (element kernels: 1 or 2)
   size_t ws_elems() const {
     return (size_t)ws.gstride * (size_t)grid;
   }
@@ -411,6 +412,24 @@ template <typename T>
 __device__ __forceinline__ T* ws_ptr(const WsPlan& w, int i, unsigned char* smem, T* gws) {
   return w.in_smem[i] ? reinterpret_cast<T*>(smem) + w.off[i]
                       : gws + (int64_t)blockIdx.x * w.gstride + w.off[i];
+}
+
+// Launch with clusters of c.cluster CTAs along x (c.cluster = 1: a plain launch).
+template <typename... Exp, typename... Act>
+void launch_clustered(void (*kernel)(Exp...), const LaunchCfg& c, cudaStream_t st, Act&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)c.grid);
+  cfg.blockDim = dim3((unsigned)c.block);
+  cfg.dynamicSmemBytes = c.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)c.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = c.cluster > 1 ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<Act&&>(args)...);
 }
 
 inline int blocks_per_sm(size_t smem) {
