@@ -141,6 +141,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long 
   return false;
 }
 
+// One-dimensional bulk copy (TMA) of `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) from global to this CTA's shared memory, completing on mbar's transaction count.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+      : "memory");
+}
+
+// arrive on mbar expecting `bytes` of transactions in the current phase
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
 // tensor-memory load: thread l of the warp reads lane (quadrant base + l), 16 consecutive columns
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
@@ -211,6 +225,10 @@ namespace {
 constexpr long long kTcWaitCycles = 4000000000LL;
 constexpr int kTcWarps = 16;  // 512 threads
 constexpr int kTcKB = 4;      // k3-planes per block of the x2-contraction sums
+#ifndef SEMMG_TC_MIN_STAR
+#define SEMMG_TC_MIN_STAR 31
+#endif
+constexpr int kTcMinStar = SEMMG_TC_MIN_STAR;  // smallest n_S on the tensor cores
 
 __host__ __device__ __forceinline__ int tc_np(int nS) { return (nS + 15) / 16 * 16; }
 __host__ __device__ __forceinline__ size_t tc_al(size_t b) { return (b + 127) & ~size_t(127); }
@@ -316,6 +334,107 @@ __device__ __forceinline__ int rs_index(int lane) {
 
 __host__ __device__ constexpr int tc_pow2(int n) { return n <= 1 ? 1 : (n <= 2 ? 2 : (n <= 4 ? 4 : 8)); }
 
+// The eigenspace step of one star (see the file comment) on register tiles of NI rows (k2)
+// per warp and NJ 32-lane columns (k1): B1, B2, B3 replace P0, P1, P2 in X.  Rows and columns
+// outside the active ranges carry zeros (s = 0, P = 0, D = 1), so the loops have no branches;
+// only the stores are guarded.  The caller picks the smallest tiles that cover the ranges.
+template <int NI, int NJ>
+__device__ __forceinline__ void tc_eigen(float* X, int np, int ld, int nS, float lam, const float* Lm, const float* Sv,
+                                         float* Yf, const TcRanges& rg, int warp, int lane, int tid) {
+  const int lo1 = rg.lo[0], hi1 = rg.hi[0], lo2 = rg.lo[1], hi2 = rg.hi[1], lo3 = rg.lo[2], hi3 = rg.hi[2];
+  float* P0 = X;
+  float* P1 = X + np * ld;
+  float* P2 = X + 2 * np * ld;
+  const float* s1 = Sv;
+  const float* s2 = Sv + nS;
+  const float* s3 = Sv + 2 * nS;
+  constexpr int R = tc_pow2(NI);
+  int k1v[NJ], k2v[NI];
+  bool ok1[NJ], ok2[NI];
+  float s1r[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    k1v[j] = lo1 + lane + 32 * j;
+    ok1[j] = k1v[j] < hi1;
+    s1r[j] = ok1[j] ? s1[k1v[j]] : 0.0f;
+  }
+  float p2r[NI][NJ], b3[NI][NJ], d12[NI][NJ], s2r[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    k2v[i] = lo2 + warp + kTcWarps * i;
+    ok2[i] = k2v[i] < hi2;
+    s2r[i] = ok2[i] ? s2[k2v[i]] : 0.0f;
+    if (!ok2[i]) k2v[i] = lo2;  // a valid row to read from; its contributions are zero or unused
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const bool ok = ok2[i] && ok1[j];
+      p2r[i][j] = ok ? P2[k2v[i] * ld + k1v[j]] : 0.0f;
+      d12[i][j] = ok ? lam + Lm[k1v[j]] + Lm[nS + k2v[i]] : 1.0f;
+      b3[i][j] = 0.0f;
+    }
+  }
+  const int me = rs_index<R>(lane);  // the row whose B1 this lane receives
+  const bool wr1 = (lane & (32 / R - 1)) == 0 && me < NI;
+  const int w1 = hi1 - lo1;
+  for (int k3b = lo3; k3b < hi3; k3b += kTcKB) {
+    const int nb = hi3 - k3b < kTcKB ? hi3 - k3b : kTcKB;
+    for (int kb = 0; kb < nb; ++kb) {
+      const int k3 = k3b + kb;
+      const float s3k = s3[k3], l3 = Lm[2 * nS + k3];
+      float p1r[NJ], b2[NJ], p0[NI], b1[R];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        p1r[j] = ok1[j] ? P1[k3 * ld + k1v[j]] : 0.0f;
+        b2[j] = 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < NI; ++i) p0[i] = P0[k3 * ld + k2v[i]];
+#pragma unroll
+      for (int i = 0; i < R; ++i) b1[i] = 0.0f;
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          float e = s1r[j] * p0[i];
+          e += s2r[i] * p1r[j];
+          e += s3k * p2r[i][j];
+          const float v = __fdividef(e, d12[i][j] + l3);
+          b1[i] += s1r[j] * v;
+          b2[j] += s2r[i] * v;
+          b3[i][j] += s3k * v;
+        }
+      }
+      const float t1 = rs_reduce<R>(b1, lane);
+      // this warp alone reads P0[k3][k2] of its rows (all read above): B1 takes their place
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+        if (wr1 && me == i && ok2[i]) P0[k3 * ld + k2v[i]] = rg.pa[0] ? t1 : 0.0f;
+#pragma unroll
+      for (int j = 0; j < NJ; ++j)
+        if (ok1[j]) Yf[(warp * kTcKB + kb) * np + k1v[j]] = b2[j];
+    }
+    __syncthreads();
+    // B2 rows of the block: the 16 warps' partial sums in warp order, in place of P1's rows
+    for (int o = tid; o < nb * w1; o += blockDim.x) {
+      const int kb = o / w1, k1 = lo1 + (o - kb * w1);
+      float sum = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kTcWarps; ++w) sum += Yf[(w * kTcKB + kb) * np + k1];
+      P1[(k3b + kb) * ld + k1] = rg.pa[1] ? sum : 0.0f;
+    }
+    __syncthreads();
+  }
+  // B3 in place of P2 (the rows this warp owns and alone has read)
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    if (ok2[i]) {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j)
+        if (ok1[j]) P2[k2v[i] * ld + k1v[j]] = rg.pa[2] ? b3[i][j] : 0.0f;
+    }
+  }
+}
+
 template <typename OP, int PC>
 __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const float* __restrict__ r,
                                                      float* __restrict__ Ob, int* counter, int* err,
@@ -327,6 +446,7 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
   constexpr int NI = PC ? (2 * PC - 1 + kTcWarps - 1) / kTcWarps : 6;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint64_t s_mbar;
+  __shared__ uint64_t s_tbar;  // table copies (TMA)
   __shared__ uint32_t s_tmem;
   __shared__ int s_next, s_abort;
   __shared__ TcRanges s_rg;
@@ -350,6 +470,7 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
   const uint32_t ncols = 3 * np <= 256 ? 256u : 512u;
   if (tid == 0) {
     tc::mbar_init(&s_mbar, 1);
+    tc::mbar_init(&s_tbar, 1);
     s_abort = 0;
   }
   for (int i = tid; i <= m; i += blockDim.x) Wt[i] = t.w1d[i];
@@ -362,7 +483,8 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = s_tmem;
-  uint32_t phase = 0;
+  uint32_t phase = 0, tphase = 0;
+  bool tpending = false;  // table copies in flight (issued, not yet awaited)
   // one tensor-core round: operands written -> products issued -> completion awaited
   auto round = [&](auto issue) -> bool {
     tc::fence_async_smem();
@@ -397,11 +519,31 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
       }
     }
   };
-  auto load_table = [&](S* dst, const S* src, int cls) {
-    const uint4* s4 = reinterpret_cast<const uint4*>(src + (int64_t)cls * tb);
-    uint4* d4 = reinterpret_cast<uint4*>(dst);
-    const int nv = tb * (int)sizeof(S) / 16;
-    for (int i = tid; i < nv; i += blockDim.x) d4[i] = s4[i];
+  // Table copies by TMA: thread 0 issues one bulk copy per table on s_tbar (the slot's
+  // previous products have completed: every caller comes after the round that read it);
+  // tables_ready() waits for them, bounded like the product waits.
+  const uint32_t tbytes = (uint32_t)(tb * sizeof(S));
+  auto load_tables = [&](S* d0, const S* s0, int c0, S* d1, const S* s1, int c1) {
+    if (tid == 0) {
+      tc::mbar_expect_tx(&s_tbar, tbytes * (d1 ? 2u : 1u));
+      tc::bulk_g2s(d0, s0 + (int64_t)c0 * tb, tbytes, &s_tbar);
+      if (d1) tc::bulk_g2s(d1, s1 + (int64_t)c1 * tb, tbytes, &s_tbar);
+    }
+    tpending = true;
+  };
+  // A thread whose wait ran out keeps its copy marked in flight (drained at exit); the
+  // outcome is made uniform over the CTA before anyone issues products on the tables.
+  auto tables_ready = [&]() -> bool {
+    const bool ok = tc::mbar_wait(&s_tbar, tphase, wait_budget);
+    if (ok) {
+      tphase ^= 1u;
+      tpending = false;
+    } else {
+      s_abort = 1;
+      if (lane == 0) atomicExch(err, 1);
+    }
+    __syncthreads();
+    return s_abort == 0;
   };
   // position in the star order (most work first when the level has an order table)
   int64_t it = blockIdx.x;
@@ -418,9 +560,8 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
         Ac[d * nS + i] = t.act[d][(int64_t)c[d] * nS + i];
         Sv[d * nS + i] = t.starS[d][(int64_t)c[d] * n2 + m * nS + i];
       }
-    // forward slow-axis tables: x3 for planes 0 and 1, x2 for plane 2
-    load_table(T0, OP::tabT(t, 2), t.starCls[2][c[2]]);
-    load_table(T1, OP::tabT(t, 1), t.starCls[1][c[1]]);
+    // forward slow-axis tables: x3 for planes 0 and 1, x2 for plane 2 (arriving during the gather)
+    load_tables(T0, OP::tabT(t, 2), t.starCls[2][c[2]], T1, OP::tabT(t, 1), t.starCls[1][c[1]]);
     __syncthreads();
     if (tid < 3) {
       const int d = tid;
@@ -433,12 +574,12 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
     }
     // 1. the planes divided by the multiplicity, as B operands P_dd^T: row n = ja, K index jb
     //    (zero outside the star and in the padding).  The operands are filled in their memory
-    //    order (a warp writes whole core matrices: no bank conflicts), four independent loads in
+    //    order (a warp writes whole core matrices: no bank conflicts), eight independent loads in
     //    flight per thread.
-    for (int base = tid; base < 3 * tb; base += 4 * (int)blockDim.x) {
-      float v[4];
+    for (int base = tid; base < 3 * tb; base += 8 * (int)blockDim.x) {
+      float v[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int idx = base + u * (int)blockDim.x;
         v[u] = 0.0f;
         if (idx < 3 * tb) {
@@ -453,12 +594,13 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int idx = base + u * (int)blockDim.x;
         if (idx < 3 * tb) Xo[idx] = OP::cvt(v[u]);
       }
     }
     // 2. forward, slow axis: W = T(S_b) P^T
+    if (!tables_ready()) break;
     if (!round([&] {
           tc_product<OP>(tmem, 0, T0, Xo, 2 * np, np);
           tc_product<OP>(tmem, 2 * np, T1, Xo + 2 * tb, np, np);
@@ -469,8 +611,9 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
       const int dd = col / np;
       tc_store16<OP>(Xo + dd * tb, row, col - dd * np, v, np);
     });
-    load_table(T0, OP::tabT(t, 0), t.starCls[0][c[0]]);
+    load_tables(T0, OP::tabT(t, 0), t.starCls[0][c[0]], nullptr, nullptr, 0);
     // 3. forward, fast axis: Z_dd = W_dd T(S_a) (plane 0: x2 tables; planes 1, 2: x1 tables)
+    if (!tables_ready()) break;
     if (!round([&] {
           tc_product<OP>(tmem, 0, Xo, T1, np, np);
           tc_product<OP>(tmem, np, Xo + tb, T0, np, np);
@@ -483,111 +626,27 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
 #pragma unroll
       for (int q = 0; q < 16; q += 4) *reinterpret_cast<float4*>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
     });
-    // backward slow-axis tables (x3, x2) load while the eigenspace step runs
-    load_table(T0, OP::tabN(t, 2), t.starCls[2][c[2]]);
-    load_table(T1, OP::tabN(t, 1), t.starCls[1][c[1]]);
+    // backward slow-axis tables (x3, x2) arrive while the eigenspace step runs
+    load_tables(T0, OP::tabN(t, 2), t.starCls[2][c[2]], T1, OP::tabN(t, 1), t.starCls[1][c[1]]);
     __syncthreads();
-    // 4. eigenspace step (see the file comment): B1, B2, B3 replace P0, P1, P2 in X.  Rows and
-    //    columns outside the active ranges carry zeros (s = 0, P = 0, D = 1), so the loops have
-    //    no branches; only the stores are guarded.
+    // 4. eigenspace step (see the file comment): B1, B2, B3 replace P0, P1, P2 in X, built for
+    //    the rows and columns this star's active ranges need (half or all of the register tiles)
     {
       const TcRanges rg = s_rg;
-      const int lo1 = rg.lo[0], hi1 = rg.hi[0], lo2 = rg.lo[1], hi2 = rg.hi[1], lo3 = rg.lo[2], hi3 = rg.hi[2];
-      float* P0 = X;
-      float* P1 = X + np * ld;
-      float* P2 = X + 2 * np * ld;
-      const float* s1 = Sv;
-      const float* s2 = Sv + nS;
-      const float* s3 = Sv + 2 * nS;
-      constexpr int R = tc_pow2(NI);
-      int k1v[NJ], k2v[NI];
-      bool ok1[NJ], ok2[NI];
-      float s1r[NJ];
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        k1v[j] = lo1 + lane + 32 * j;
-        ok1[j] = k1v[j] < hi1;
-        s1r[j] = ok1[j] ? s1[k1v[j]] : 0.0f;
-      }
-      float p2r[NI][NJ], b3[NI][NJ], d12[NI][NJ], s2r[NI];
-#pragma unroll
-      for (int i = 0; i < NI; ++i) {
-        k2v[i] = lo2 + warp + kTcWarps * i;
-        ok2[i] = k2v[i] < hi2;
-        s2r[i] = ok2[i] ? s2[k2v[i]] : 0.0f;
-        if (!ok2[i]) k2v[i] = lo2;  // a valid row to read from; its contributions are zero or unused
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-          const bool ok = ok2[i] && ok1[j];
-          p2r[i][j] = ok ? P2[k2v[i] * ld + k1v[j]] : 0.0f;
-          d12[i][j] = ok ? lam + Lm[k1v[j]] + Lm[nS + k2v[i]] : 1.0f;
-          b3[i][j] = 0.0f;
-        }
-      }
-      const int me = rs_index<R>(lane);  // the row whose B1 this lane receives
-      const bool wr1 = (lane & (32 / R - 1)) == 0 && me < NI;
-      const int w1 = hi1 - lo1;
-      for (int k3b = lo3; k3b < hi3; k3b += kTcKB) {
-        const int nb = hi3 - k3b < kTcKB ? hi3 - k3b : kTcKB;
-        for (int kb = 0; kb < nb; ++kb) {
-          const int k3 = k3b + kb;
-          const float s3k = s3[k3], l3 = Lm[2 * nS + k3];
-          float p1r[NJ], b2[NJ], p0[NI], b1[R];
-#pragma unroll
-          for (int j = 0; j < NJ; ++j) {
-            p1r[j] = ok1[j] ? P1[k3 * ld + k1v[j]] : 0.0f;
-            b2[j] = 0.0f;
-          }
-#pragma unroll
-          for (int i = 0; i < NI; ++i) p0[i] = P0[k3 * ld + k2v[i]];
-#pragma unroll
-          for (int i = 0; i < R; ++i) b1[i] = 0.0f;
-#pragma unroll
-          for (int i = 0; i < NI; ++i) {
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-              float e = s1r[j] * p0[i];
-              e += s2r[i] * p1r[j];
-              e += s3k * p2r[i][j];
-              const float v = __fdividef(e, d12[i][j] + l3);
-              b1[i] += s1r[j] * v;
-              b2[j] += s2r[i] * v;
-              b3[i][j] += s3k * v;
-            }
-          }
-          const float t1 = rs_reduce<R>(b1, lane);
-          // this warp alone reads P0[k3][k2] of its rows (all read above): B1 takes their place
-#pragma unroll
-          for (int i = 0; i < NI; ++i)
-            if (wr1 && me == i && ok2[i]) P0[k3 * ld + k2v[i]] = rg.pa[0] ? t1 : 0.0f;
-#pragma unroll
-          for (int j = 0; j < NJ; ++j)
-            if (ok1[j]) Yf[(warp * kTcKB + kb) * np + k1v[j]] = b2[j];
-        }
-        __syncthreads();
-        // B2 rows of the block: the 16 warps' partial sums in warp order, in place of P1's rows
-        for (int o = tid; o < nb * w1; o += blockDim.x) {
-          const int kb = o / w1, k1 = lo1 + (o - kb * w1);
-          float sum = 0.0f;
-#pragma unroll
-          for (int w = 0; w < kTcWarps; ++w) sum += Yf[(w * kTcKB + kb) * np + k1];
-          P1[(k3b + kb) * ld + k1] = rg.pa[1] ? sum : 0.0f;
-        }
-        __syncthreads();
-      }
-      // B3 in place of P2 (the rows this warp owns and alone has read)
-#pragma unroll
-      for (int i = 0; i < NI; ++i) {
-        if (ok2[i]) {
-#pragma unroll
-          for (int j = 0; j < NJ; ++j)
-            if (ok1[j]) P2[k2v[i] * ld + k1v[j]] = rg.pa[2] ? b3[i][j] : 0.0f;
-        }
-      }
+      const bool fi = rg.hi[1] - rg.lo[1] > kTcWarps * ((NI + 1) / 2);  // k2 rows beyond the half tile
+      const bool fj = rg.hi[0] - rg.lo[0] > 32 * ((NJ + 1) / 2);         // k1 columns beyond the half tile
+      if (fi && fj)
+        tc_eigen<NI, NJ>(X, np, ld, nS, lam, Lm, Sv, Yf, rg, warp, lane, tid);
+      else if (fi)
+        tc_eigen<NI, (NJ + 1) / 2>(X, np, ld, nS, lam, Lm, Sv, Yf, rg, warp, lane, tid);
+      else if (fj)
+        tc_eigen<(NI + 1) / 2, NJ>(X, np, ld, nS, lam, Lm, Sv, Yf, rg, warp, lane, tid);
+      else
+        tc_eigen<(NI + 1) / 2, (NJ + 1) / 2>(X, np, ld, nS, lam, Lm, Sv, Yf, rg, warp, lane, tid);
     }
     // 5. backward, slow axis, one plane at a time: O_dd = N(S_b) B_dd^T with B_dd (rows k_b,
     //    columns k_a in X) staged in Y as the B operand (row n = k_a, K index k_b)
-    bool aborted = false;
+    bool aborted = !tables_ready();
     for (int dd = 0; dd < 3 && !aborted; ++dd) {
       if (dd > 0) __syncthreads();  // the previous round's operand is consumed (round() waited)
       const float* B = X + dd * np * ld;
@@ -605,8 +664,9 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
       const int dd = col / np;
       tc_store16<OP>(Xo + dd * tb, row, col - dd * np, v, np);
     });
-    load_table(T0, OP::tabN(t, 0), t.starCls[0][c[0]]);
+    load_tables(T0, OP::tabN(t, 0), t.starCls[0][c[0]], nullptr, nullptr, 0);
     // 6. backward, fast axis: Y_dd = O_dd N(S_a) (plane 0: x2 tables; planes 1, 2: x1 tables)
+    if (!tables_ready()) break;
     if (!round([&] {
           tc_product<OP>(tmem, 0, Xo, T1, np, np);
           tc_product<OP>(tmem, np, Xo + tb, T0, np, np);
@@ -652,6 +712,7 @@ __global__ void __launch_bounds__(512, 1) k_star_tc(Geo G, Tabs<float> t, const 
     }
   }
   if (s_abort) tc::mbar_wait(&s_mbar, phase ^ 1u, kTcWaitCycles);  // products still in flight
+  if (tpending) tc::mbar_wait(&s_tbar, tphase, kTcWaitCycles);      // table copies still in flight
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, ncols);
@@ -700,7 +761,7 @@ LaunchCfg plan_star_tc(const Geo& G, int nsm, int bf16) {
   LaunchCfg c;
   // 31 <= n_S <= 95 (np <= 96: the stacked products fit N <= 256 and the tensor memory 512
   // columns); below n_S = 31 the CUDA-core kernel is as fast
-  if (G.nS > 95 || G.nS < 31) return c;
+  if (G.nS > 95 || G.nS < kTcMinStar) return c;
   c.smem = tc_smem_bytes(G.nS, bf16);
   if (c.smem > kTcSmemMax) return c;
   c.block = 32 * kTcWarps;
