@@ -54,6 +54,7 @@ FORMS = {"fp64": ("fp64", "mg", "star"), "mixed": ("mixed", "mg", "star"), "mixe
          "eblock_mixed": ("mixed", "mg", "element")}
 MIXED_FORMS = ("mixed", "mixed_tc", "mixed_bf16")  # candidates for the result line's `mixed`
 DETAIL_FORMS = ("kmg_fp64", "kmg_mixed", "kmg_mixed_tc", "mixed_fp32", "mixed_fp32_tc")
+TC_FORMS = ("mixed_tc", "mixed_bf16", "mixed_fp32_tc")  # star on the tensor cores at n_S >= 31
 FP64_NOMINAL_TFLOPS = 1.25  # 2 FP64 FMA / clock / SM x 152 SMs x 2.07 GHz: fallback when the probe fails
 # DRAM bytes (read + write) per k_star<double> launch of the timed FP64 region of the headline
 # workload (all levels, every launch of two steps), from an ncu capture of that region
@@ -248,31 +249,53 @@ def timed_solves(ctx, f, u, steps, flush, stream, host=None):
     return ms, info
 
 
-def roofline(kst, peak, peak_source, steps):
-    """Roofline of the dominant kernel class of a timing pass (kst: class -> totals over `steps` solves)."""
+def roofline(kst, star_peak, peaks, steps, tc=False):
+    """Roofline of the dominant kernel class of a timing pass (kst: class -> totals over `steps` solves).
+
+    star_peak: (TFLOP/s, source) of the precision the form's star kernel runs in; peaks: "fp64" and
+    "hbm" (value, source).  tc: the form runs its star on the tensor cores at the upper levels, where
+    the library keeps no executed-operation count."""
     dom = max(kst, key=lambda k: kst[k]["ms"])
     d = kst[dom]
     total_ms = sum(v["ms"] for v in kst.values())
     launches = sum(v["launches"] for v in kst.values())
-    per_launch_s = d["ms"] / 1e3 / max(1, d["launches"])
+    sec = d["ms"] / 1e3
     out = {"kernel": dom, "share": d["ms"] / total_ms, "launches_per_step": d["launches"] / steps,
-           "ms_per_launch": 1e3 * per_launch_s, "kernel_launches_per_step": launches / steps}
-    if d["xflops"] > 0:
-        achieved = d["xflops"] / (d["ms"] / 1e3) / 1e12
-        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "peak_source": peak_source, "ops_per_launch": d["xflops"] / max(1, d["launches"]),
-                    "paper_count_tflops": d["flops"] / (d["ms"] / 1e3) / 1e12,
-                    "hbm_gbs": d["bytes"] / (d["ms"] / 1e3) / 1e9})
+           "ms_per_launch": 1e3 * sec / max(1, d["launches"]), "kernel_launches_per_step": launches / steps}
+    if d["xflops"] > 0 and not (tc and dom == "star"):
+        achieved = d["xflops"] / sec / 1e12
+        out.update({"bound": "alu", "achieved": achieved, "peak": star_peak[0], "unit": "TFLOP/s",
+                    "frac": achieved / star_peak[0] if star_peak[0] else None, "peak_source": star_peak[1],
+                    "ops_per_launch": d["xflops"] / max(1, d["launches"]),
+                    "paper_count_tflops": d["flops"] / sec / 1e12, "hbm_gbs": d["bytes"] / sec / 1e9})
+    elif d["flops"] > 0:
+        # arithmetic-bound class without an executed-operation count: the paper count only
+        pk = star_peak if dom == "star" else peaks["fp64"]
+        out.update({"bound": "alu", "achieved": None, "peak": pk[0], "unit": "TFLOP/s", "frac": None,
+                    "peak_source": pk[1], "paper_count_tflops": d["flops"] / sec / 1e12,
+                    "note": "no executed-operation count for this kernel class"})
     else:
-        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        out.update({"bound": "hbm", "achieved": achieved, "unit": "GB/s", "peak": None, "frac": None})
+        achieved = d["bytes"] / sec / 1e9
+        out.update({"bound": "hbm", "achieved": achieved, "unit": "GB/s", "peak": peaks["hbm"][0],
+                    "frac": achieved / peaks["hbm"][0] if peaks["hbm"][0] else None, "peak_source": peaks["hbm"][1]})
     return out
 
 
-def kernel_table(kst, steps):
+def measured_hbm():
+    """(GB/s, source): the copy bandwidth measured on this GPU type, else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
+def kernel_table(kst, steps, tc=False):
+    """Per-class event times and rates; tc: the star's executed count covers only its CUDA-core levels."""
     return {k: {"ms_per_step": r4(v["ms"] / steps), "launches_per_step": r4(v["launches"] / steps),
                 "paper_tflops": r4(v["flops"] / (v["ms"] / 1e3) / 1e12) if v["flops"] and v["ms"] else None,
-                "exec_tflops": r4(v["xflops"] / (v["ms"] / 1e3) / 1e12) if v["xflops"] and v["ms"] else None,
+                "exec_tflops": (r4(v["xflops"] / (v["ms"] / 1e3) / 1e12)
+                                if v["xflops"] and v["ms"] and not (tc and k == "star") else None),
                 "hbm_gbs": r4(v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["bytes"] and v["ms"] else None}
             for k, v in kst.items() if v["launches"]}
 
@@ -355,8 +378,8 @@ def run_semmg(args, world, rank, local, pg):
     kst_m = {}
     for form in MIXED_FORMS:
         kst_m[form] = timing_pass(ctx[form], fd, ud, npass)
-        emit(f"kernels_{form}", {"workload": HEADLINE, "solves": npass, "kernels": kernel_table(kst_m[form], npass)},
-             details)
+        emit(f"kernels_{form}", {"workload": HEADLINE, "solves": npass,
+                                 "kernels": kernel_table(kst_m[form], npass, tc=form in TC_FORMS)}, details)
     torch.cuda.synchronize()
 
     t64 = max_over_ranks(pg, t64)
@@ -369,13 +392,15 @@ def run_semmg(args, world, rank, local, pg):
                    "forms": {k: {"value": r4(v), "speedup_vs_fp64": r4(v / value), "iterations": iters[k],
                                  "precision": FORMS[k][0], "solver": FORMS[k][1]}
                              for k, v in [("fp64", value)] + list(vforms.items())}}, details)
-    roof = roofline(kst, fp64_peak, fp64_src, npass)
+    peaks = {"fp64": (fp64_peak, fp64_src), "hbm": measured_hbm()}
+    roof = roofline(kst, peaks["fp64"], peaks, npass)
     h_now = star_source_hash()
     roof["traffic"] = (STAR_TRAFFIC["bytes_per_launch"] if roof["kernel"] == "star" and h_now is not None
                        and h_now == STAR_TRAFFIC["source"] else None)
     emit("roofline", {k: (r4(v) if isinstance(v, float) else v) for k, v in roof.items()}, details)
     for form in MIXED_FORMS:
-        rm = roofline(kst_m[form], fp32_peak or 1.0, "measured (FP32 FMA chains, this run)", npass)
+        rm = roofline(kst_m[form], (fp32_peak, "measured (FP32 FMA chains, this run)"), peaks, npass,
+                      tc=form in TC_FORMS)
         emit(f"roofline_{form}", {k: (r4(v) if isinstance(v, float) else v) for k, v in rm.items()}, details)
     best = max(MIXED_FORMS, key=lambda k: vforms[k])
     for c in ctx.values():

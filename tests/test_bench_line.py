@@ -37,3 +37,43 @@ def test_result_line_has_the_required_keys():
     assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(line["roofline"])
     assert {"value", "unit", "cores", "kind", "sample"} <= set(line["cpu_baseline"])
     assert line["mixed"]["speedup_vs_fp64"] > 1.0
+
+
+def _kst(**classes):
+    base = {"ms": 0.0, "launches": 0, "flops": 0.0, "bytes": 0.0, "xflops": 0.0}
+    return {k: {**base, **v} for k, v in classes.items()}
+
+
+PEAKS = {"fp64": (1.25, "fp64 probe"), "hbm": (6792.4, "copy")}
+
+
+def test_roofline_executed_count_against_the_star_peak():
+    kst = _kst(star=dict(ms=100.0, launches=10, flops=3e12, bytes=1e9, xflops=1e11),
+               vector=dict(ms=1.0, launches=5, bytes=1e9))
+    r = bench.roofline(kst, (1.25, "fp64 probe"), PEAKS, steps=2)
+    assert r["kernel"] == "star" and r["bound"] == "alu"
+    assert abs(r["achieved"] - 1.0) < 1e-12 and abs(r["frac"] - 0.8) < 1e-12
+    assert abs(r["paper_count_tflops"] - 30.0) < 1e-9 and r["launches_per_step"] == 5
+
+
+def test_roofline_without_executed_count_reports_no_fraction():
+    # tensor-core star: the library's count covers the CUDA-core levels only
+    kst = _kst(star=dict(ms=100.0, launches=10, flops=3e12, xflops=1e9))
+    r = bench.roofline(kst, (78.0, "fp32 probe"), PEAKS, steps=1, tc=True)
+    assert r["achieved"] is None and r["frac"] is None and r["peak"] == 78.0
+    # an FP64 element class with only the paper count is measured against the FP64 peak
+    kst = _kst(elem_schur=dict(ms=10.0, launches=3, flops=1e10), star=dict(ms=1.0, launches=1, xflops=1e6))
+    r = bench.roofline(kst, (78.0, "fp32 probe"), PEAKS, steps=1)
+    assert r["kernel"] == "elem_schur" and r["bound"] == "alu" and r["peak"] == 1.25 and r["frac"] is None
+
+
+def test_roofline_data_movement_class_against_measured_hbm():
+    kst = _kst(star_gather=dict(ms=2.0, launches=4, bytes=6.7924e9))
+    r = bench.roofline(kst, (1.25, "fp64 probe"), PEAKS, steps=1)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 3396.2) < 1e-6 and abs(r["frac"] - 0.5) < 1e-12
+
+
+def test_measured_hbm_reads_the_peaks_file():
+    v, src = bench.measured_hbm()
+    assert v > 1000.0 and isinstance(src, str)
