@@ -47,14 +47,16 @@ SWEEP = [4, 8, 16, 32]
 METRIC = "unknowns/s per solve to 1e-10 residual (FP64 vs mixed); smoother HBM GB/s"
 # timed forms: name -> (precision, outer iteration, smoother)
 FORMS = {"fp64": ("fp64", "mg", "star"), "mixed": ("mixed", "mg", "star"), "mixed_tc": ("mixed_tc", "mg", "star"),
-         "mixed_bf16": ("mixed_bf16", "mg", "star"),
+         "mixed_bf16": ("mixed_bf16", "mg", "star"), "mixed_ff_tc": ("mixed_ff_tc", "mg", "star"),
+         "mixed_ff": ("mixed_ff", "mg", "star"), "kmg_mixed_ff_tc": ("mixed_ff_tc", "kmg", "star"),
          "mixed_fp32": ("mixed_fp32", "mg", "star"), "mixed_fp32_tc": ("mixed_fp32_tc", "mg", "star"),
          "kmg_fp64": ("fp64", "kmg", "star"), "kmg_mixed": ("mixed", "kmg", "star"),
          "kmg_mixed_tc": ("mixed_tc", "kmg", "star"), "eblock_fp64": ("fp64", "mg", "element"),
          "eblock_mixed": ("mixed", "mg", "element")}
-MIXED_FORMS = ("mixed", "mixed_tc", "mixed_bf16")  # candidates for the result line's `mixed`
-DETAIL_FORMS = ("kmg_fp64", "kmg_mixed", "kmg_mixed_tc", "mixed_fp32", "mixed_fp32_tc")
-TC_FORMS = ("mixed_tc", "mixed_bf16", "mixed_fp32_tc")  # star on the tensor cores at n_S >= 31
+MIXED_FORMS = ("mixed", "mixed_tc", "mixed_bf16", "mixed_ff_tc")  # candidates for the result line's `mixed`
+DETAIL_FORMS = ("kmg_fp64", "kmg_mixed", "kmg_mixed_tc", "kmg_mixed_ff_tc", "mixed_fp32", "mixed_fp32_tc",
+                "mixed_ff")
+TC_FORMS = ("mixed_tc", "mixed_bf16", "mixed_fp32_tc", "mixed_ff_tc")  # star on the tensor cores at n_S >= 31
 FP64_NOMINAL_TFLOPS = 1.25  # 2 FP64 FMA / clock / SM x 152 SMs x 2.07 GHz: fallback when the probe fails
 # DRAM bytes (read + write) per k_star<double> launch of the timed FP64 region of the headline
 # workload (all levels, every launch of two steps), from an ncu capture of that region

@@ -84,7 +84,8 @@ enum {
 #define SEMMG_MAX_DEGREE 48
 
 /* precision of the V-cycle; the outer iteration (its residual, norms and
- * update), the coarse solve, condensation and recovery are always FP64.
+ * update) and the coarse solve are always FP64, and so are condensation and
+ * recovery except in the solves of the float-float forms.
  *   SEMMG_FP64        everything FP64;
  *   SEMMG_MIXED       FP32 vectors, smoother and transfers in the V-cycle; its
  *                     level residuals F - Hhat u in FP64 arithmetic on the FP32
@@ -96,14 +97,28 @@ enum {
  *   SEMMG_MIXED_FP32_TC  as SEMMG_MIXED_FP32, with the tensor-core smoother of
  *                     SEMMG_MIXED_TC on the levels it covers;
  *   SEMMG_MIXED_BF16  as SEMMG_MIXED_TC with BF16 operands (8-bit significand,
- *                     FP32 accumulation) in the tensor-core transforms. */
+ *                     FP32 accumulation) in the tensor-core transforms;
+ *   SEMMG_MIXED_FF    as SEMMG_MIXED, with the level residuals of the levels
+ *                     with p >= 12 (the face-parallel form of the operator) in
+ *                     float-float arithmetic: every value an unevaluated sum of
+ *                     two FP32 numbers (about 48 significant bits), run on the
+ *                     FP32 pipes; levels with p < 12 as SEMMG_MIXED.  When the
+ *                     finest level has p >= 12, semmg_solve (and a batch) also
+ *                     condenses the right-hand side and recovers the interiors
+ *                     in float-float (relative rounding about 1e-14, four
+ *                     orders below the 1e-10 target); semmg_condense_rhs and
+ *                     semmg_recover stay FP64;
+ *   SEMMG_MIXED_FF_TC as SEMMG_MIXED_FF, with the tensor-core smoother of
+ *                     SEMMG_MIXED_TC. */
 enum {
   SEMMG_FP64 = 0,
   SEMMG_MIXED = 1,
   SEMMG_MIXED_FP32 = 2,
   SEMMG_MIXED_TC = 3,
   SEMMG_MIXED_FP32_TC = 4,
-  SEMMG_MIXED_BF16 = 5
+  SEMMG_MIXED_BF16 = 5,
+  SEMMG_MIXED_FF = 6,
+  SEMMG_MIXED_FF_TC = 7
 };
 /* outer iteration of semmg_solve and of the batched form */
 enum { SEMMG_SOLVER_MG = 0, SEMMG_SOLVER_KMG = 1 };
@@ -137,9 +152,9 @@ typedef struct {
   int p0;          /* coarse degree, 1 <= p0 <= p (default 2, Sec. 4.1) */
   int nu_pre;      /* pre-smoothing steps per level (default 1, Algorithm 3) */
   int nu_post;     /* post-smoothing steps per level (default 1) */
-  int precision;   /* SEMMG_FP64 (default), SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC
-                      or SEMMG_MIXED_BF16 */
-  int max_iter;    /* iteration cap of semmg_solve (default 50) */
+  int precision;   /* SEMMG_FP64 (default), SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC,
+                      SEMMG_MIXED_BF16, SEMMG_MIXED_FF or SEMMG_MIXED_FF_TC */
+  int max_iter;    /* iteration cap of semmg_solve (default 50; 0: condensation and recovery from u_hat = 0 only) */
   int solver;      /* SEMMG_SOLVER_MG (Algorithm 4, default) or SEMMG_SOLVER_KMG (Algorithm 5) */
   int nu_vary;     /* 0 (default): nu_pre / nu_post steps on every level; 1: nu_pre 2^(L-l) and
                       nu_post 2^(L-l) steps on level l (Sec. 4.1, "kvMG" with SEMMG_SOLVER_KMG) */
@@ -201,6 +216,16 @@ int semmg_apply_condensed(semmg_ctx* ctx, int level, const double* u_hat, double
 /* r_hat = f_hat - Hhat u_hat (Sec. 2.3, residual), FP64.  r_hat may alias f_hat. */
 int semmg_residual(semmg_ctx* ctx, int level, const double* f_hat, const double* u_hat,
                    double* r_hat, void* stream);
+
+/* r_hat = f_hat - Hhat u_hat on `level` as the V-cycle of a mixed-precision
+ * context forms it: FP32 vectors (f_hat, u_hat, r_hat: condensed size of the
+ * level), the arithmetic of the context's precision (FP64 for SEMMG_MIXED,
+ * _TC and _BF16; float-float on the levels with p >= 12 for SEMMG_MIXED_FF and
+ * _FF_TC, FP64 below; FP32 for SEMMG_MIXED_FP32 and _FP32_TC), the result
+ * rounded once to FP32.  r_hat may alias f_hat, not u_hat.
+ * SEMMG_ERR_UNSUPPORTED for an FP64 context. */
+int semmg_residual_cycle(semmg_ctx* ctx, int level, const float* f_hat, const float* u_hat, float* r_hat,
+                         void* stream);
 
 /* du_hat = Smoother(r_hat): Algorithm 2 around Algorithm 1 on the stars of all
  * (n1+1)(n2+1)(n3+1) vertices of the level (Sec. 3.2), level >= 1; with
@@ -355,7 +380,7 @@ int semmg_set_launch(semmg_ctx* ctx, int level, int kernel, int dtype, int smem_
  * semmg_smooth_noalloc computes exactly what semmg_smooth computes (du_hat =
  * Smoother(r_hat) on `level`, bitwise the same result) with the same kernels:
  * the CUDA-core star kernel, or for dtype SEMMG_F32 on the levels where the
- * context's precision (SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC, SEMMG_MIXED_BF16) puts the star
+ * context's precision (SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC, SEMMG_MIXED_BF16, SEMMG_MIXED_FF_TC) puts the star
  * transforms on the tensor cores, the tensor-core star kernel.  It calls no
  * cudaMalloc, cudaFree or other allocating routine: the star output buffer and
  * the per-block work arrays come from one array of SEMMG_NOALLOC_SCRATCH_BYTES

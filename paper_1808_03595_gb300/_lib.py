@@ -25,6 +25,7 @@ ERRORS = {
 }
 SEMMG_ERR_NOT_CONVERGED, SEMMG_ERR_NONFINITE, SEMMG_ERR_TIMEOUT, SEMMG_ERR_DIVERGED = -4, -5, -6, -8
 SEMMG_FP64, SEMMG_MIXED, SEMMG_MIXED_FP32, SEMMG_MIXED_TC, SEMMG_MIXED_FP32_TC, SEMMG_MIXED_BF16 = 0, 1, 2, 3, 4, 5
+SEMMG_MIXED_FF, SEMMG_MIXED_FF_TC = 6, 7
 SEMMG_SOLVER_MG, SEMMG_SOLVER_KMG = 0, 1
 SEMMG_SMOOTHER_STAR, SEMMG_SMOOTHER_ELEMENT, SEMMG_SMOOTHER_ELEMENT_MULT = 0, 1, 2
 SEMMG_BC_DIRICHLET, SEMMG_BC_NEUMANN, SEMMG_BC_PERIODIC = 0, 1, 2
@@ -69,6 +70,7 @@ SIGNATURES = {
     "semmg_pack_dirichlet": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "semmg_apply_condensed": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "semmg_residual": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "semmg_residual_cycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "semmg_smooth": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "semmg_restrict": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "semmg_prolong_add": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),

@@ -38,11 +38,12 @@ constexpr double kDivergence = 1e3;
 struct DevLevel {
   Tabs<double> td{};
   Tabs<float> tf{};
+  Tabs<ff> tff{};      // float-float tables (SEMMG_MIXED_FF, _FF_TC; face-parallel levels only)
   void* Fw = nullptr;  // V-cycle vectors in the working precision
   void* Uw = nullptr;
   void* Rw = nullptr;
   LaunchCfg schur64, schur32, star64, star32;
-  LaunchCfg startc;  // tensor-core star smoother (SEMMG_MIXED_TC, _FP32_TC, _BF16), when the level allows it
+  LaunchCfg startc;  // tensor-core star smoother (SEMMG_MIXED_TC, _FP32_TC, _BF16, _FF_TC), when the level allows it
   LaunchCfg eb64, eb32;  // element-centred block smoother (SEMMG_SMOOTHER_ELEMENT)
 };
 
@@ -679,10 +680,21 @@ bool upload_star_order(semmg_ctx* c, int l) {
 
 // V-cycle in FP32 (the mixed forms)
 bool cycle32(const semmg_ctx* c) { return c->opts.precision != SEMMG_FP64; }
-// FP32 V-cycle whose level residuals are formed in FP64
+// FP32 V-cycle whose level residuals are formed in float-float on the face-parallel
+// levels (FP64 on the others)
+bool residff(const semmg_ctx* c) {
+  return c->opts.precision == SEMMG_MIXED_FF || c->opts.precision == SEMMG_MIXED_FF_TC;
+}
+// FP32 V-cycle whose level residuals are formed in FP64 (all levels, or the levels
+// without the float-float form)
 bool resid64(const semmg_ctx* c) {
   return c->opts.precision == SEMMG_MIXED || c->opts.precision == SEMMG_MIXED_TC ||
-         c->opts.precision == SEMMG_MIXED_BF16;
+         c->opts.precision == SEMMG_MIXED_BF16 || residff(c);
+}
+// The star smoother on the tensor cores where a level allows it
+bool tc_form(int precision) {
+  return precision == SEMMG_MIXED_TC || precision == SEMMG_MIXED_FP32_TC || precision == SEMMG_MIXED_BF16 ||
+         precision == SEMMG_MIXED_FF_TC;
 }
 
 // out = F - Hhat u (mode 0) or Hhat u (mode 1) on level l with arithmetic in T
@@ -694,11 +706,17 @@ void apply_op(semmg_ctx* c, int l, const Tabs<T>& tb, const LaunchCfg& cfg, cons
   const double vec = (double)G.size * sizeof(TF), uvec = (double)G.size * sizeof(T);
   const double zb = (double)G.nelem * 6 * G.m * G.m * sizeof(T);
   const double fb = (double)G.oE1 * sizeof(T);
-  if (face_form(G)) {
+  if (face_form(G) || std::is_same<T, ff>::value) {
     {
       Tic t(c, SEMMG_K_ELEM_SCHUR, st);
       launch_face_fwd<T>(G, tb, u, (T*)c->Uts, st);
-      launch_elem_schur<T>(G, tb, (const T*)c->Uts, (T*)c->Zs, (T*)c->wss, cfg, st, 1);
+      // the element terms in the face eigenbasis: float-float streams the eigenspace through
+      // registers (its arithmetic is issue-bound, the stored form memory-bound); FP64 and FP32
+      // keep the stored form, whose FP64 work fits the narrow FP64 pipe as well
+      if constexpr (std::is_same<T, ff>::value)
+        launch_schur_eb<T>(G, tb, (const T*)c->Uts, (T*)c->Zs, plan_schur_eb<T>(G, c->nsm), st);
+      else
+        launch_elem_schur<T>(G, tb, (const T*)c->Uts, (T*)c->Zs, (T*)c->wss, cfg, st, 1);
       t.toc(schur_flops(G), 3 * fb + zb, 2);
     }
     Tic t(c, SEMMG_K_ASSEMBLE, st);
@@ -706,17 +724,19 @@ void apply_op(semmg_ctx* c, int l, const Tabs<T>& tb, const LaunchCfg& cfg, cons
     t.toc(0.0, vec * (mode == 0 ? 2 : 1) + uvec + zb, 2);  // face back transforms, edge and vertex slots
     return;
   }
-  {
-    Tic t(c, SEMMG_K_ELEM_SCHUR, st);
-    launch_elem_schur<T>(G, tb, u, (T*)c->Zs, (T*)c->wss, cfg, st);
-    t.toc(schur_flops(G), zb * 2, G.m > 0 ? 1 : 0);
+  if constexpr (!std::is_same<T, ff>::value) {
+    {
+      Tic t(c, SEMMG_K_ELEM_SCHUR, st);
+      launch_elem_schur<T>(G, tb, u, (T*)c->Zs, (T*)c->wss, cfg, st);
+      t.toc(schur_flops(G), zb * 2, G.m > 0 ? 1 : 0);
+    }
+    Tic t(c, SEMMG_K_ASSEMBLE, st);
+    if constexpr (std::is_same<T, TF>::value)
+      launch_assemble<T>(G, tb, F, u, (T*)c->Zs, out, mode, st);
+    else
+      launch_assemble_mixed(G, tb, F, u, (const double*)c->Zs, out, mode, st);
+    t.toc(0.0, vec * (mode == 0 ? 2 : 1) + uvec + zb);
   }
-  Tic t(c, SEMMG_K_ASSEMBLE, st);
-  if constexpr (std::is_same<T, TF>::value)
-    launch_assemble<T>(G, tb, F, u, (T*)c->Zs, out, mode, st);
-  else
-    launch_assemble_mixed(G, tb, F, u, (const double*)c->Zs, out, mode, st);
-  t.toc(0.0, vec * (mode == 0 ? 2 : 1) + uvec + zb);
 }
 
 // out = F - Hhat u (mode 0) or Hhat u (mode 1) on level l.  FP32 vectors of
@@ -725,6 +745,16 @@ template <typename T>
 void op_residual(semmg_ctx* c, int l, const T* F, const T* u, T* out, int mode, cudaStream_t st) {
   const Geo& G = c->geo[l];
   if constexpr (std::is_same<T, float>::value) {
+    if (residff(c) && face_form(G)) {
+      // u widened to float-float (exactly), then the float-float kernels
+      {
+        Tic t(c, SEMMG_K_VECTOR, st);
+        launch_copy<ff, float>((ff*)c->U64s, u, G.size, st);
+        t.toc(0.0, (double)G.size * 12);
+      }
+      apply_op<ff, float>(c, l, c->dl[l].tff, c->dl[l].schur64, F, (const ff*)c->U64s, out, mode, st);
+      return;
+    }
     if (resid64(c)) {
       // u widened to FP64 once, then the FP64 kernels; F and the result stay FP32
       {
@@ -886,25 +916,39 @@ void correction(semmg_ctx* c, double* u, const double* r, cudaStream_t st) {
 
 // F_hat = F_B - H_BI H_II^{-1} F_I; with `save`, the scaled interior
 // eigen-coefficients of F_I are kept in Gs for recover_impl(..., use_saved).
-void condense_impl(semmg_ctx* c, const double* f, double* fh, bool save, cudaStream_t st) {
+// The solve of a float-float form condenses and recovers in float-float where the finest
+// level has its tables (the face-parallel levels); the public entry points stay FP64.
+bool ff_fdm(const semmg_ctx* c) { return residff(c) && c->dl[c->L()].tff.Sh != nullptr; }
+
+void condense_impl(semmg_ctx* c, const double* f, double* fh, bool save, cudaStream_t st, bool ffok = false) {
   const int L = c->L();
   const Geo& G = c->geo[L];
   const double nn = (double)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
   Tic t(c, SEMMG_K_CONDENSE, st);
-  launch_elem_condense(G, c->dl[L].td, f, (double*)c->Zs, save ? c->Gs : nullptr, (double*)c->wss, c->fdm, st);
+  if (ffok && ff_fdm(c))
+    launch_elem_condense<ff>(G, c->dl[L].tff, f, (double*)c->Zs, save ? (ff*)c->Gs : nullptr, (ff*)c->wss, c->fdm,
+                             st);
+  else
+    launch_elem_condense<double>(G, c->dl[L].td, f, (double*)c->Zs, save ? c->Gs : nullptr, (double*)c->wss,
+                                 c->fdm, st);
   launch_assemble_rhs(G, c->dl[L].td, f, (const double*)c->Zs, fh, st);
   t.toc(G.m > 0 ? fdm_flops(G) : 0.0, 8.0 * (nn + G.size), 2);
 }
 
 // u = (u_hat, H_II^{-1}(F_I - H_IB u_hat)); use_saved: F_I's coefficients from
 // the preceding condense_impl(..., save = true) on the same f.
-void recover_impl(semmg_ctx* c, const double* f, const double* uh, double* u, bool use_saved, cudaStream_t st) {
+void recover_impl(semmg_ctx* c, const double* f, const double* uh, double* u, bool use_saved, cudaStream_t st,
+                  bool ffok = false) {
   const int L = c->L();
   const Geo& G = c->geo[L];
   const double nn = (double)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
   Tic t(c, SEMMG_K_RECOVER, st);
   launch_unpack(G, uh, u, st);
-  launch_elem_recover(G, c->dl[L].td, f, use_saved ? c->Gs : nullptr, uh, u, (double*)c->wss, c->fdm, st);
+  if (ffok && ff_fdm(c))
+    launch_elem_recover<ff>(G, c->dl[L].tff, f, use_saved ? (const ff*)c->Gs : nullptr, uh, u, (ff*)c->wss, c->fdm,
+                            st);
+  else
+    launch_elem_recover<double>(G, c->dl[L].td, f, use_saved ? c->Gs : nullptr, uh, u, (double*)c->wss, c->fdm, st);
   t.toc(G.m > 0 ? fdm_flops(G) : 0.0, 8.0 * (2 * nn + G.size), 2);
 }
 
@@ -1045,7 +1089,7 @@ void build_star_rtab(semmg_ctx* c, const Geo& G, const HostLevel& H, Tabs<double
 int set_limits(semmg_ctx* c) {
   if (g_limits_done) return SEMMG_OK;
   if (set_elem_smem_limits() | set_star_smem_limits() | set_transfer_smem_limits() | set_star_tc_smem_limits() |
-      set_eblock_smem_limits() | set_face_smem_limits())
+      set_eblock_smem_limits() | set_face_smem_limits() | set_ff_smem_limits())
     return fail(c, SEMMG_ERR_CUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
   g_limits_done = 1;
   return SEMMG_OK;
@@ -1134,9 +1178,8 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   if (p < 1 || p > SEMMG_MAX_DEGREE) return SEMMG_ERR_UNSUPPORTED;
   if (o.p0 < 1 || o.p0 > p) return SEMMG_ERR_UNSUPPORTED;
   if (!(lambda >= 0.0) || !std::isfinite(lambda)) return SEMMG_ERR_INVALID_ARG;
-  if (o.nu_pre < 0 || o.nu_post < 0 || o.max_iter < 1) return SEMMG_ERR_INVALID_ARG;
-  if (o.precision != SEMMG_FP64 && o.precision != SEMMG_MIXED && o.precision != SEMMG_MIXED_FP32 &&
-      o.precision != SEMMG_MIXED_TC && o.precision != SEMMG_MIXED_FP32_TC && o.precision != SEMMG_MIXED_BF16)
+  if (o.nu_pre < 0 || o.nu_post < 0 || o.max_iter < 0) return SEMMG_ERR_INVALID_ARG;
+  if (o.precision < SEMMG_FP64 || o.precision > SEMMG_MIXED_FF_TC)
     return SEMMG_ERR_INVALID_ARG;
   if (o.solver != SEMMG_SOLVER_MG && o.solver != SEMMG_SOLVER_KMG) return SEMMG_ERR_INVALID_ARG;
   if (o.nu_vary != 0 && o.nu_vary != 1) return SEMMG_ERR_INVALID_ARG;
@@ -1200,6 +1243,8 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
   for (int l = 0; l < nl; ++l) {
     c->dl[l].td = upload_tabs<double>(c.get(), c->geo[l], c->hl[l], c->h, &ok);
     c->dl[l].tf = upload_tabs<float>(c.get(), c->geo[l], c->hl[l], c->h, &ok);
+    if (residff(c.get()) && face_form(c->geo[l]))
+      c->dl[l].tff = upload_tabs<ff>(c.get(), c->geo[l], c->hl[l], c->h, &ok);
     // 1/D tables of the FP64 star kernel: always when small; up to kMaxStarRtabFp64 entries (GB on
     // stretched meshes, where every vertex line is its own class) for the FP64 V-cycle
     if (l >= 1 && ok && o.smoother == SEMMG_SMOOTHER_STAR)
@@ -1238,9 +1283,7 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
         const int64_t nE = 3 * (int64_t)G.p - 1;
         obs = std::max(obs, (size_t)(G.nelem * 6 * nE * nE));
       }
-      const bool tcform = o.precision == SEMMG_MIXED_TC || o.precision == SEMMG_MIXED_FP32_TC ||
-                          o.precision == SEMMG_MIXED_BF16;
-      if (tcform && o.smoother == SEMMG_SMOOTHER_STAR) {
+      if (tc_form(o.precision) && o.smoother == SEMMG_SMOOTHER_STAR) {
         const bool bf16 = o.precision == SEMMG_MIXED_BF16;
         D.startc = plan_star_tc(G, c->nsm, bf16 ? 1 : 0);
         if (D.startc.ok) {
@@ -1293,7 +1336,8 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     c->Uts = dalloc(c.get(), (size_t)c->geo[nl - 1].oE1 * sizeof(double));
     if (!c->Uts) return SEMMG_ERR_NOMEM;
   }
-  if (o.precision == SEMMG_MIXED || o.precision == SEMMG_MIXED_TC || o.precision == SEMMG_MIXED_BF16) {
+  if (resid64(c.get())) {  // the widened copy of u (FP64, or float-float of the same size)
+    static_assert(sizeof(ff) == sizeof(double), "float-float and FP64 share the widened copy");
     c->U64s = (double*)dalloc(c.get(), nL * sizeof(double));
     if (!c->U64s) return SEMMG_ERR_NOMEM;
   }
@@ -1404,6 +1448,13 @@ int semmg_residual(semmg_ctx* c, int level, const double* f, const double* u, do
   return check_cuda(c, "residual");
 }
 
+int semmg_residual_cycle(semmg_ctx* c, int level, const float* f, const float* u, float* r, void* stream) {
+  if (!valid_level(c, level) || !f || !u || !r || u == r) return SEMMG_ERR_INVALID_ARG;
+  if (!cycle32(c)) return fail(c, SEMMG_ERR_UNSUPPORTED, "residual_cycle: the context's V-cycle is FP64");
+  op_residual<float>(c, level, f, u, r, 0, (cudaStream_t)stream);
+  return check_cuda(c, "residual_cycle");
+}
+
 int semmg_smooth(semmg_ctx* c, int level, int dtype, const void* r, void* du, void* stream) {
   if (!valid_level(c, level) || level < 1 || !r || !du || r == du) return SEMMG_ERR_INVALID_ARG;
   if (dtype == SEMMG_F64)
@@ -1472,7 +1523,7 @@ namespace {
 int solve_impl(semmg_ctx* c, const double* f, const double* g, double* u, double rtol, semmg_info* info,
                cudaStream_t st) {
   cudaMemsetAsync(c->dev_err, 0, sizeof(int), st);  // a wait that ran out in an earlier call is not this one's
-  condense_impl(c, f, c->Fh, true, st);
+  condense_impl(c, f, c->Fh, true, st, true);
   int rc = check_cuda(c, "condense_rhs");
   if (rc) return rc;
   iter_start(c, st, g);
@@ -1494,7 +1545,7 @@ int solve_impl(semmg_ctx* c, const double* f, const double* g, double* u, double
       status = SEMMG_ERR_DIVERGED;
   }
   if (status == SEMMG_OK && rn > rtol * r0) status = SEMMG_ERR_NOT_CONVERGED;
-  recover_impl(c, f, c->Uh, u, true, st);
+  recover_impl(c, f, c->Uh, u, true, st, true);
   rc = check_cuda(c, "recover");
   if (rc) return rc;
   if (info) {
@@ -1619,8 +1670,9 @@ __global__ void k_batch_init(BatchCtl* ctl, const double* dnorm, cudaGraphCondit
   ctl->ressq = r0;
   ctl->iters = 0;
   const bool finite = isfinite(r0);
-  ctl->status = finite ? SEMMG_OK : SEMMG_ERR_NONFINITE;
-  cudaGraphSetConditional(h, (finite && r0 > 0.0 && ctl->maxit > 0) ? 1u : 0u);
+  const bool need = finite && r0 > ctl->rtol * ctl->rtol * r0;  // not yet converged (as semmg_solve tests it)
+  ctl->status = !finite ? SEMMG_ERR_NONFINITE : ((need && ctl->maxit <= 0) ? SEMMG_ERR_NOT_CONVERGED : SEMMG_OK);
+  cudaGraphSetConditional(h, (need && ctl->maxit > 0) ? 1u : 0u);
 }
 
 // after a cycle: continue while ||r||^2 > rtol^2 ||r_0||^2 and below the cycle cap
@@ -1669,7 +1721,7 @@ namespace {
 // Enqueue one solve of context c (device nodal f -> u) into the capturing stream s.
 int capture_solve(semmg_ctx* c, const double* f, const double* gdata, double* u, BatchCtl* ctl, cudaStream_t s,
                   cudaStream_t sb) {
-  condense_impl(c, f, c->Fh, true, s);
+  condense_impl(c, f, c->Fh, true, s, true);
   iter_start(c, s, gdata);
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
@@ -1699,7 +1751,7 @@ int capture_solve(semmg_ctx* c, const double* f, const double* gdata, double* u,
   if (cudaStreamEndCapture(sb, &got) != cudaSuccess) return check_cuda(c, "batch: body end");
   if (cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
     return check_cuda(c, "batch: dependencies");
-  recover_impl(c, f, c->Uh, u, true, s);
+  recover_impl(c, f, c->Uh, u, true, s, true);
   return check_cuda(c, "batch: capture");
 }
 

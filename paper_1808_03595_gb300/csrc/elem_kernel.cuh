@@ -212,7 +212,7 @@ __device__ __forceinline__ void tx_lines_g(const Lines& L, int ax, const T* __re
       const T* sr = S + (even ? L.h + j : j) * n + k0;
 #pragma unroll
       for (int q = 0; q < kG; ++q)
-        if (k0 + q < k1) a[q] += sr[q] * yv;
+        if (k0 + q < k1) a[q] = madd(sr[q], yv, a[q]);
     }
     const T s = sc2 ? sc2[i2] : scale;
 #pragma unroll
@@ -243,7 +243,7 @@ __device__ __forceinline__ void txT_lines_g(const Lines& L, int ax, const T* __r
     for (int k = j0; k < j1; ++k) {
       const T bv = B[base + k * str];
 #pragma unroll
-      for (int q = 0; q < kG; ++q) a[q] += sr[q][k] * bv;
+      for (int q = 0; q < kG; ++q) a[q] = madd(sr[q][k], bv, a[q]);
     }
 #pragma unroll
     for (int q = 0; q < kG; ++q)
@@ -343,10 +343,10 @@ __device__ __forceinline__ void faces_reduce(int m, int ne, const T* a0, const T
     T s0 = 0, s1 = 0;  // two independent partial sums
     int k = k0;
     for (; k + 1 < k1; k += 2) {
-      s0 += a0[k] * w[k * ws];
-      s1 += a0[k + 1] * w[(k + 1) * ws];
+      s0 = madd(a0[k], w[k * ws], s0);
+      s1 = madd(a0[k + 1], w[(k + 1) * ws], s1);
     }
-    if (k < k1) s0 += a0[k] * w[k * ws];
+    if (k < k1) s0 = madd(a0[k], w[k * ws], s0);
     X[idx] = s0 + s1;
   }
 }
@@ -376,10 +376,10 @@ __device__ __forceinline__ void faces_reduce_rows(int m, int ne, const T* a0, co
     T s0 = 0, s1 = 0;
     int k = k0;
     for (; k + 1 < k1; k += 2) {
-      s0 += a0[k] * w[k * ws];
-      s1 += a0[k + 1] * w[(k + 1) * ws];
+      s0 = madd(a0[k], w[k * ws], s0);
+      s1 = madd(a0[k + 1], w[(k + 1) * ws], s1);
     }
-    if (k < k1) s0 += a0[k] * w[k * ws];
+    if (k < k1) s0 = madd(a0[k], w[k * ws], s0);
     X[f * mm + k3 * m + kx] = s0 + s1;
   }
 }
@@ -393,7 +393,7 @@ __device__ __forceinline__ void faces_reduce_slab45(int m, int ne, const T* a0, 
     const int f = idx / mm, r = idx - f * mm;
     const int lo = max(r0, f ? ne : 0), hi = min(r1, f ? m : ne);
     T acc = 0;
-    for (int k3 = lo; k3 < hi; ++k3) acc += a0[k3] * W[(k3 - r0) * mm + r];
+    for (int k3 = lo; k3 < hi; ++k3) acc = madd(a0[k3], W[(k3 - r0) * mm + r], acc);
     P[idx] = acc;
   }
 }
@@ -402,6 +402,13 @@ __device__ __forceinline__ double inv_d(const Tabs<double>& t, const ElemScal<do
                                         double lam, int64_t idx, int k1, int k2, int k3, int64_t n3) {
   if (t.Relem) return t.Relem[sc.cls * n3 + idx];
   return 1.0 / (lam + sc.e[0] * lI[k1] + sc.e[1] * lI[k2] + sc.e[2] * lI[k3]);
+}
+
+// float-float: the table's value, or the refined reciprocal of the sum
+__device__ __forceinline__ ff inv_d(const Tabs<ff>& t, const ElemScal<ff>& sc, const ff* lI, ff lam, int64_t idx,
+                                    int k1, int k2, int k3, int64_t n3) {
+  if (t.Relem) return t.Relem[sc.cls * n3 + idx];
+  return ff_recip(lam + sc.e[0] * lI[k1] + sc.e[1] * lI[k2] + sc.e[2] * lI[k3]);
 }
 
 // FP32 (inside FP64 iterative refinement): approximate reciprocal, no table read
@@ -501,10 +508,10 @@ __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const 
         T s0 = 0, s1 = 0;
         int k = k0;
         for (; k + 1 < k1; k += 2) {
-          s0 += a0[k] * w[k * wst];
-          s1 += a0[k + 1] * w[(k + 1) * wst];
+          s0 = madd(a0[k], w[k * wst], s0);
+          s1 = madd(a0[k + 1], w[(k + 1) * wst], s1);
         }
-        if (k < k1) s0 += a0[k] * w[k * wst];
+        if (k < k1) s0 = madd(a0[k], w[k * wst], s0);
         X[f * mm + r] = s0 + s1;
       }
     }
@@ -517,7 +524,7 @@ __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const 
       for (int r0 = 0; r0 < m; r0 += slab) {
         const int lo = max(r0, flo), hi = min(r0 + slab, fhi);
         T acc = 0;
-        for (int k3 = lo; k3 < hi; ++k3) acc += a0[k3] * W[k3 * mm + r];
+        for (int k3 = lo; k3 < hi; ++k3) acc = madd(a0[k3], W[k3 * mm + r], acc);
         tot = r0 == 0 ? acc : tot + acc;
       }
       X[(4 + f) * mm + r] = tot;
@@ -539,25 +546,26 @@ __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const 
 
 // Interior 3D transforms with the folded reference eigenvectors.
 // forward: A <- scale * (Sref^T (x) Sref^T (x) Sref^T) A, B is scratch.
-__device__ __forceinline__ void interior_forward(const Lines& I, const double* Sr, double* A, double* B, double scale,
-                                                 const Team& tm) {
+template <typename T>
+__device__ __forceinline__ void interior_forward(const Lines& I, const T* Sr, T* A, T* B, T scale, const Team& tm) {
   fold_lines(I, 0, A, B, tm);
   tm.sync();
-  tx_lines_g(I, 0, Sr, B, A, 1.0, (const double*)nullptr, tm);
+  tx_lines_g(I, 0, Sr, B, A, (T)1, (const T*)nullptr, tm);
   tm.sync();
   fold_lines(I, 1, A, B, tm);
   tm.sync();
-  tx_lines_g(I, 1, Sr, B, A, 1.0, (const double*)nullptr, tm);
+  tx_lines_g(I, 1, Sr, B, A, (T)1, (const T*)nullptr, tm);
   tm.sync();
   fold_lines(I, 2, A, B, tm);
   tm.sync();
-  tx_lines_g(I, 2, Sr, B, A, scale, (const double*)nullptr, tm);
+  tx_lines_g(I, 2, Sr, B, A, scale, (const T*)nullptr, tm);
   tm.sync();
 }
 
 // backward along x3 and x2 (natural order in A afterwards), then the x1
 // transposed transform into B; the caller unfolds B along x1.
-__device__ __forceinline__ void interior_backward(const Lines& I, const double* Sr, double* A, double* B, const Team& tm) {
+template <typename T>
+__device__ __forceinline__ void interior_backward(const Lines& I, const T* Sr, T* A, T* B, const Team& tm) {
   txT_lines_g(I, 2, Sr, A, B, tm);
   tm.sync();
   unfold_lines(I, 2, B, A, tm);
@@ -570,19 +578,21 @@ __device__ __forceinline__ void interior_backward(const Lines& I, const double* 
   tm.sync();
 }
 
+template <typename T>
 struct FdmSmem {
-  double *Sh, *Sr, *a0, *lI, *X, *Tt, *A, *B;
+  T *Sh, *Sr, *a0, *lI, *X, *Tt, *A, *B;
 };
 
 // Work regions: 0 tables (Sh, Sref, a0, Lam), 1 X (6 m^2), 2 Tt (6 m^2), 3 A+B (2 m^3).
 // Work arrays of the team: shared memory of this CTA, or the team's slice of the global
 // workspace (slice = the team's index: the CTA, or the cluster, in the grid).
-__device__ FdmSmem fdm_layout(int m, unsigned char* smem, double* ws, const WsPlan& wp, int64_t slice) {
+template <typename T>
+__device__ FdmSmem<T> fdm_layout(int m, unsigned char* smem, T* ws, const WsPlan& wp, int64_t slice) {
   const int mm = m * m;
   auto at = [&](int i) {
-    return wp.in_smem[i] ? reinterpret_cast<double*>(smem) + wp.off[i] : ws + slice * wp.gstride + wp.off[i];
+    return wp.in_smem[i] ? reinterpret_cast<T*>(smem) + wp.off[i] : ws + slice * wp.gstride + wp.off[i];
   };
-  FdmSmem s;
+  FdmSmem<T> s;
   s.Sh = at(0);
   s.Sr = s.Sh + mm;
   s.a0 = s.Sr + mm;
@@ -606,14 +616,15 @@ __device__ __forceinline__ int64_t interior_node(const Geo& G, int a1, int a2, i
 // D^{-1} (S^T x S^T x S^T) F_I of every element are also stored there
 // (m^3 per element), for the recovery of the same solve.  cs = 2: launched in
 // clusters of two CTAs that share each element's work (global work arrays).
-template <int PC>
-__global__ void __launch_bounds__(512, 1) k_elem_condense(Geo G, Tabs<double> t, const double* __restrict__ f,
-                                                        double* __restrict__ Z, double* __restrict__ Gsave,
-                                                        double* ws, WsPlan wp, int cs) {
+// T: the arithmetic (FP64, or float-float); f and Z are FP64, Gsave of type T.
+template <typename T, int PC>
+__global__ void __launch_bounds__(512, 1) k_elem_condense(Geo G, Tabs<T> t, const double* __restrict__ f,
+                                                        double* __restrict__ Z, T* __restrict__ Gsave, T* ws,
+                                                        WsPlan wp, int cs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = PC ? PC - 1 : G.m, mm = m * m, mmm = mm * m;
   const Team tm = team_of(cs);
-  FdmSmem s = fdm_layout(m, smem_raw, ws, wp, blockIdx.x / cs);
+  FdmSmem<T> s = fdm_layout(m, smem_raw, ws, wp, blockIdx.x / cs);
   load_tables(m, t, s.Sh, s.a0, s.lI);
   for (int i = threadIdx.x; i < mm; i += blockDim.x) s.Sr[i] = t.Sref[i];
   const Lines F{m, m / 2, (m + 1) / 2, m, m, 6 * mm};
@@ -621,23 +632,23 @@ __global__ void __launch_bounds__(512, 1) k_elem_condense(Geo G, Tabs<double> t,
   for (int64_t e = blockIdx.x / cs; e < G.nelem; e += gridDim.x / cs) {
     int a1, a2, a3;
     elem_coords(G, e, &a1, &a2, &a3);
-    const ElemScal<double> sc = elem_scalars(t, a1, a2, a3);
-    const double* x1 = t.hx[0] + 6 * a1;
-    const double* x2 = t.hx[1] + 6 * a2;
-    const double* x3 = t.hx[2] + 6 * a3;
-    const double vol = 0.125 * x1[0] * x2[0] * x3[0];  // h1 h2 h3 / 8
-    const double sig = x1[5] * x2[5] * x3[5];          // sqrt(8 / (h1 h2 h3))
+    const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
+    const T* x1 = t.hx[0] + 6 * a1;
+    const T* x2 = t.hx[1] + 6 * a2;
+    const T* x3 = t.hx[2] + 6 * a3;
+    const T vol = (T)0.125 * x1[0] * x2[0] * x3[0];  // h1 h2 h3 / 8
+    const T sig = x1[5] * x2[5] * x3[5];             // sqrt(8 / (h1 h2 h3))
     tm.sync();
     for (int idx = tm.id; idx < mmm; idx += tm.n) {
       const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / mm;
-      s.A[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] * f[interior_node(G, a1, a2, a3, idx)];
+      s.A[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] * (T)f[interior_node(G, a1, a2, a3, idx)];
     }
     tm.sync();
     interior_forward(I, s.Sr, s.A, s.B, sig, tm);
-    double* Ge = Gsave ? Gsave + e * (int64_t)mmm : nullptr;
+    T* Ge = Gsave ? Gsave + e * (int64_t)mmm : nullptr;
     for (int idx = tm.id; idx < mmm; idx += tm.n) {
       const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
-      const double v = s.A[idx] * inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
+      const T v = s.A[idx] * inv_d(t, sc, s.lI, (T)G.lam, idx, k1, k2, k3, mmm);
       s.A[idx] = v;
       if (Ge) Ge[idx] = v;
     }
@@ -645,23 +656,23 @@ __global__ void __launch_bounds__(512, 1) k_elem_condense(Geo G, Tabs<double> t,
     faces_reduce(m, F.ne, s.a0, s.A, s.X, tm);
     tm.sync();
     double* Ze = Z + e * 6 * mm;
-    faces_backward(F, s.Sh, s.X, s.Tt, sc, [&](int idx, double v) { Ze[idx] = v; }, tm);
+    faces_backward(F, s.Sh, s.X, s.Tt, sc, [&](int idx, T v) { Ze[idx] = (double)v; }, tm);
   }
 }
 
 // u_I = H_II^{-1} (F_I - H_IB uhat) written into the nodal array.  With Gin
 // (the coefficients k_elem_condense stored for the same f) the forward
 // transform of F_I is taken from there instead of being recomputed.  cs as
-// for k_elem_condense.
-template <int PC>
-__global__ void __launch_bounds__(512, 1) k_elem_recover(Geo G, Tabs<double> t, const double* __restrict__ f,
-                                                       const double* __restrict__ Gin,
+// for k_elem_condense; T and Gin as there, f, uh and un FP64.
+template <typename T, int PC>
+__global__ void __launch_bounds__(512, 1) k_elem_recover(Geo G, Tabs<T> t, const double* __restrict__ f,
+                                                       const T* __restrict__ Gin,
                                                        const double* __restrict__ uh, double* __restrict__ un,
-                                                       double* ws, WsPlan wp, int cs) {
+                                                       T* ws, WsPlan wp, int cs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = PC ? PC - 1 : G.m, mm = m * m, mmm = mm * m;
   const Team tm = team_of(cs);
-  FdmSmem s = fdm_layout(m, smem_raw, ws, wp, blockIdx.x / cs);
+  FdmSmem<T> s = fdm_layout(m, smem_raw, ws, wp, blockIdx.x / cs);
   load_tables(m, t, s.Sh, s.a0, s.lI);
   for (int i = threadIdx.x; i < mm; i += blockDim.x) s.Sr[i] = t.Sref[i];
   const Lines F{m, m / 2, (m + 1) / 2, m, m, 6 * mm};
@@ -669,22 +680,22 @@ __global__ void __launch_bounds__(512, 1) k_elem_recover(Geo G, Tabs<double> t, 
   for (int64_t e = blockIdx.x / cs; e < G.nelem; e += gridDim.x / cs) {
     int a1, a2, a3;
     elem_coords(G, e, &a1, &a2, &a3);
-    const ElemScal<double> sc = elem_scalars(t, a1, a2, a3);
-    const double* x1 = t.hx[0] + 6 * a1;
-    const double* x2 = t.hx[1] + 6 * a2;
-    const double* x3 = t.hx[2] + 6 * a3;
-    const double vol = 0.125 * x1[0] * x2[0] * x3[0];  // h1 h2 h3 / 8
-    const double sig = x1[5] * x2[5] * x3[5];          // sqrt(8 / (h1 h2 h3))
+    const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
+    const T* x1 = t.hx[0] + 6 * a1;
+    const T* x2 = t.hx[1] + 6 * a2;
+    const T* x3 = t.hx[2] + 6 * a3;
+    const T vol = (T)0.125 * x1[0] * x2[0] * x3[0];  // h1 h2 h3 / 8
+    const T sig = x1[5] * x2[5] * x3[5];             // sqrt(8 / (h1 h2 h3))
     tm.sync();
     if (!Gin) {
       for (int idx = tm.id; idx < mmm; idx += tm.n) {
         const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / mm;
-        s.A[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] * f[interior_node(G, a1, a2, a3, idx)];
+        s.A[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] * (T)f[interior_node(G, a1, a2, a3, idx)];
       }
     }
     for (int idx = tm.id; idx < 6 * mm; idx += tm.n) {
       const int fc = idx / mm;
-      s.X[idx] = uh[elem_face_base(G, a1, a2, a3, fc) + (idx - fc * mm)];
+      s.X[idx] = (T)uh[elem_face_base(G, a1, a2, a3, fc) + (idx - fc * mm)];
     }
     tm.sync();
     if (!Gin) interior_forward(I, s.Sr, s.A, s.B, sig, tm);
@@ -692,23 +703,23 @@ __global__ void __launch_bounds__(512, 1) k_elem_recover(Geo G, Tabs<double> t, 
     tm.sync();
     faces_forward(F, s.Sh, s.X, s.Tt, sc, tm);
     if (Gin) {
-      const double* Ge = Gin + e * (int64_t)mmm;
+      const T* Ge = Gin + e * (int64_t)mmm;
       for (int idx = tm.id; idx < mmm; idx += tm.n) {
         const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
         s.A[idx] = Ge[idx] - face_expand(m, F.ne, s.a0, s.X, k1, k2, k3) *
-                                 inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
+                                 inv_d(t, sc, s.lI, (T)G.lam, idx, k1, k2, k3, mmm);
       }
     } else {
       for (int idx = tm.id; idx < mmm; idx += tm.n) {
         const int k1 = idx % m, k2 = (idx / m) % m, k3 = idx / mm;
         s.A[idx] = (s.A[idx] - face_expand(m, F.ne, s.a0, s.X, k1, k2, k3)) *
-                   inv_d(t, sc, s.lI, G.lam, idx, k1, k2, k3, mmm);
+                   inv_d(t, sc, s.lI, (T)G.lam, idx, k1, k2, k3, mmm);
       }
     }
     tm.sync();
     interior_backward(I, s.Sr, s.A, s.B, tm);
     for (int idx = tm.id; idx < mmm; idx += tm.n)
-      un[interior_node(G, a1, a2, a3, idx)] = sig * unfold_at(I, 0, s.B, idx);
+      un[interior_node(G, a1, a2, a3, idx)] = (double)(sig * unfold_at(I, 0, s.B, idx));
   }
 }
 

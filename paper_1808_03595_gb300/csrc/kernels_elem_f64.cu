@@ -1,6 +1,7 @@
 // FP64 instantiation of the element kernels: condensed operator (FP64 form and
 // the outer residual of the mixed form), right-hand-side condensation and
-// interior recovery.
+// interior recovery (the latter two also in float-float, for the float-float
+// forms).
 #include "elem_kernel.cuh"
 
 namespace semmg {
@@ -39,25 +40,47 @@ LaunchCfg plan_elem_fdm(const Geo& G, int nsm) {
 }
 
 
-void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f, double* Z, double* Gsave,
-                          double* ws, const LaunchCfg& c, cudaStream_t st) {
+template <typename T>
+void launch_elem_condense(const Geo& G, const Tabs<T>& t, const double* f, double* Z, T* Gsave, T* ws,
+                          const LaunchCfg& c, cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
   switch (G.p) {
-    case 16: launch_clustered(k_elem_condense<16>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
-    case 32: launch_clustered(k_elem_condense<32>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
-    default: launch_clustered(k_elem_condense<0>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
+    case 16: launch_clustered(k_elem_condense<T, 16>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
+    case 32: launch_clustered(k_elem_condense<T, 32>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
+    default: launch_clustered(k_elem_condense<T, 0>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
   }
 }
 
-void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f, const double* Gin,
-                         const double* uh, double* un, double* ws, const LaunchCfg& c, cudaStream_t st) {
+template <typename T>
+void launch_elem_recover(const Geo& G, const Tabs<T>& t, const double* f, const T* Gin, const double* uh, double* un,
+                         T* ws, const LaunchCfg& c, cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
   switch (G.p) {
-    case 16: launch_clustered(k_elem_recover<16>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
-    case 32: launch_clustered(k_elem_recover<32>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
-    default: launch_clustered(k_elem_recover<0>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
+    case 16: launch_clustered(k_elem_recover<T, 16>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
+    case 32: launch_clustered(k_elem_recover<T, 32>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
+    default: launch_clustered(k_elem_recover<T, 0>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
   }
 }
+
+template <typename T>
+int fdm_attrs() {
+  int bad = cudaFuncSetAttribute(k_elem_condense<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_condense<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_condense<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_recover<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_recover<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_recover<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return bad;
+}
+
+template void launch_elem_condense<double>(const Geo&, const Tabs<double>&, const double*, double*, double*, double*,
+                                           const LaunchCfg&, cudaStream_t);
+template void launch_elem_recover<double>(const Geo&, const Tabs<double>&, const double*, const double*,
+                                          const double*, double*, double*, const LaunchCfg&, cudaStream_t);
+template void launch_elem_condense<ff>(const Geo&, const Tabs<ff>&, const double*, double*, ff*, ff*,
+                                       const LaunchCfg&, cudaStream_t);
+template void launch_elem_recover<ff>(const Geo&, const Tabs<ff>&, const double*, const ff*, const double*, double*,
+                                      ff*, const LaunchCfg&, cudaStream_t);
 
 template LaunchCfg plan_elem_schur<double>(const Geo&, int, size_t, int, int);
 template void launch_elem_schur<double>(const Geo&, const Tabs<double>&, const double*, double*, double*,
@@ -66,12 +89,7 @@ template void launch_elem_schur<double>(const Geo&, const Tabs<double>&, const d
 int set_elem_smem_limits_f32();
 int set_elem_smem_limits() {
   int bad = schur_attrs<double>() | set_elem_smem_limits_f32();
-  bad |= cudaFuncSetAttribute(k_elem_condense<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_condense<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_condense<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_recover<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_recover<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  bad |= cudaFuncSetAttribute(k_elem_recover<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= fdm_attrs<double>() | fdm_attrs<ff>();
   return bad;
 }
 

@@ -280,5 +280,6 @@ template void launch_copy<double, double>(double*, const double*, int64_t, cudaS
 template void launch_copy<float, double>(float*, const double*, int64_t, cudaStream_t);
 template void launch_copy<double, float>(double*, const float*, int64_t, cudaStream_t);
 template void launch_copy<float, float>(float*, const float*, int64_t, cudaStream_t);
+template void launch_copy<ff, float>(ff*, const float*, int64_t, cudaStream_t);
 
 }  // namespace semmg

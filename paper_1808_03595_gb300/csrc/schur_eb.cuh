@@ -1,0 +1,307 @@
+// Element Schur term in the face eigenbasis, streamed plane by plane (Sec. 2.2).
+//
+// On the levels of the face-parallel operator every face arrives transformed
+// into its in-plane eigenbasis (k_face_fwd).  For one element the Schur term
+// H_BI H_II^{-1} H_IB u on its six faces is then, in the interior eigenbasis
+// k = (k1, k2, k3),
+//   W(k) = D(k)^{-1} (a0[k1] X_{0|1}(k3,k2) + a0[k2] X_{2|3}(k3,k1) + a0[k3] X_{4|5}(k2,k1)),
+//   X'_{0|1}(k3,k2) = sum_k1 a0[k1] W(k),  X'_{2|3}(k3,k1) = sum_k2 a0[k2] W(k),
+//   X'_{4|5}(k2,k1) = sum_k3 a0[k3] W(k),
+// where X_{2d}, X_{2d+1} are alpha_d times the sum and the difference of the two
+// faces normal to axis d, the one used at k being picked by the parity class of
+// k_d (eigenvector columns 0..ne-1 even, ne..m-1 odd), and the sums over k_d run
+// over that class.  The element's face terms are
+//   Z_{2d} = alpha_d (X'_{2d} + X'_{2d+1}),  Z_{2d+1} = alpha_d (X'_{2d} - X'_{2d+1})
+// (elem_kernel.cuh derives the same terms with W stored; here W is never
+// stored: each k3-plane is formed in registers and consumed at once).
+//
+// Thread mapping (512 threads, 16 warps; one element per CTA at a time):
+//  - warp w owns the rows k2 = w + 16 i (i < NI) of every plane; a row's parity
+//    class is uniform over the warp;
+//  - lane l owns NJ column slots: lanes 0..15 the even columns k1 = 16 j + l,
+//    lanes 16..31 the odd columns k1 = ne + 16 j + (l - 16), so all columns of a
+//    lane are of one class.
+// Per plane, the sums over k1 are reduced within each half-warp by one
+// butterfly reduce-scatter over the warp's rows (X'_0 in the lower half, X'_1
+// in the upper); the sums over k2 are per-warp partials in shared memory, added
+// in warp order every KB planes; the sums over k3 accumulate in registers, the
+// even planes first (X'_4), then the odd ones (X'_5).  Every output has a fixed
+// summation order.
+#pragma once
+#include "elem_kernel.cuh"
+
+namespace semmg {
+
+namespace {
+
+constexpr int kEbWarps = 16;  // 512 threads
+constexpr int kEbKB = 4;      // planes per shared-memory round of the k2 sums
+constexpr int kEbSmemMax = 200 * 1024;
+
+__device__ __forceinline__ float eb_shx(float v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ double eb_shx(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ ff eb_shx(ff v, int off) {
+  return ff(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
+}
+
+// Reduce-scatter over the 16 lanes of a half-warp: R values per lane (R a power of
+// two) -> the sum over the half-warp of value rs16_index<R>(lane).  Partners add in
+// either order, which gives the same bits (addition commutes).
+template <int R, typename T>
+__device__ __forceinline__ T rs16_reduce(T* v, int lane) {
+  int off = 8;
+#pragma unroll
+  for (int n = R; n > 1; n >>= 1, off >>= 1) {
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < n / 2; ++k) {
+      const T send = hi ? v[k] : v[k + n / 2];
+      const T keep = hi ? v[k + n / 2] : v[k];
+      v[k] = keep + eb_shx(send, off);
+    }
+  }
+  T t = v[0];
+#pragma unroll
+  for (; off > 0; off >>= 1) t = t + eb_shx(t, off);
+  return t;
+}
+
+template <int R>
+__device__ __forceinline__ int rs16_index(int lane) {
+  int idx = 0, off = 8;
+#pragma unroll
+  for (int n = R; n > 1; n >>= 1, off >>= 1)
+    if (lane & off) idx += n / 2;
+  return idx;
+}
+
+__host__ __device__ constexpr int eb_pow2(int n) { return n <= 1 ? 1 : (n <= 2 ? 2 : (n <= 4 ? 4 : 8)); }
+
+// Shared memory of the kernel, in elements of T: X (6 m^2), Y (k2 partial sums:
+// 16 warps x KB planes x 2 classes x NJ*32 slots), a0 (m), lI (m).
+__host__ __device__ constexpr size_t eb_smem_elems(int m, int nj) {
+  return (size_t)6 * m * m + (size_t)kEbWarps * kEbKB * 2 * nj * 32 + 2 * (size_t)m;
+}
+
+// 1/D at one point: the element class's table, or the sum of the scaled eigenvalues inverted
+__device__ __forceinline__ double eb_inv(double d) { return 1.0 / d; }
+__device__ __forceinline__ float eb_inv(float d) { return __fdividef(1.0f, d); }
+__device__ __forceinline__ ff eb_inv(ff d) { return ff_recip(d); }
+
+// TAB: 1/D from the element class's table (t.Relem), else computed per point; a
+// template parameter so that neither form carries the other's work.
+template <typename T, int NI, int NJ, bool TAB>
+__global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* __restrict__ Ut,
+                                                     T* __restrict__ Z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = G.m, mm = m * m, ne = (m + 1) / 2;
+  const int64_t n3 = (int64_t)mm * m;
+  T* X = reinterpret_cast<T*>(smem_raw);
+  T* Y = X + 6 * mm;
+  T* a0 = Y + kEbWarps * kEbKB * 2 * NJ * 32;
+  T* lI = a0 + m;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, half = lane >> 4, hl = lane & 15;
+  for (int i = tid; i < m; i += blockDim.x) {
+    a0[i] = t.a0[i];
+    lI[i] = t.lamI[i];
+  }
+  const T lam = (T)G.lam;
+  constexpr int R = eb_pow2(NI);
+  const int me = rs16_index<R>(lane);                 // the row whose k1 sum this lane receives
+  const bool wr = (hl & (16 / R - 1)) == 0 && me < NI;  // one writer lane per row and half
+  // columns and rows of this lane (invalid ones point at index 0 and carry zero weights)
+  int k1v[NJ], k2v[NI];
+  bool ok1[NJ], ok2[NI], odd2[NI];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int c = half ? ne + 16 * j + hl : 16 * j + hl;
+    ok1[j] = half ? c < m : c < ne;
+    k1v[j] = ok1[j] ? c : 0;
+  }
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int r = warp + kEbWarps * i;
+    ok2[i] = r < m;
+    odd2[i] = r >= ne;  // uniform over the warp
+    k2v[i] = ok2[i] ? r : 0;
+  }
+  for (int64_t e = blockIdx.x; e < G.nelem; e += gridDim.x) {
+    int a1, a2, a3;
+    elem_coords(G, e, &a1, &a2, &a3);
+    const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
+    const T* Rt = TAB ? t.Relem + sc.cls * n3 : nullptr;
+    __syncthreads();  // X and Y of the previous element are consumed
+    for (int idx = tid; idx < 3 * mm; idx += blockDim.x) {
+      const int d = idx / mm, r = idx - d * mm;
+      const T a = Ut[elem_face_base(G, a1, a2, a3, 2 * d) + r];
+      const T b = Ut[elem_face_base(G, a1, a2, a3, 2 * d + 1) + r];
+      X[(2 * d) * mm + r] = sc.al[d] * (a + b);
+      X[(2 * d + 1) * mm + r] = sc.al[d] * (a - b);
+    }
+    __syncthreads();
+    T a1r[NJ], a2r[NI];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) a1r[j] = ok1[j] ? a0[k1v[j]] : (T)0;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) a2r[i] = ok2[i] ? a0[k2v[i]] : (T)0;
+    T* Ze = Z + e * 6 * mm;
+    const T al0 = sc.al[0], al1 = sc.al[1], al2 = sc.al[2];
+    for (int q3 = 0; q3 < 2; ++q3) {
+      const int lo3 = q3 ? ne : 0, hi3 = q3 ? m : ne;
+      T x45[NI][NJ], b3[NI][NJ];
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          x45[i][j] = (ok2[i] && ok1[j]) ? X[(4 + q3) * mm + k2v[i] * m + k1v[j]] : (T)0;
+          b3[i][j] = (T)0;
+        }
+      for (int k3b = lo3; k3b < hi3; k3b += kEbKB) {
+        const int nb = hi3 - k3b < kEbKB ? hi3 - k3b : kEbKB;
+        for (int kb = 0; kb < nb; ++kb) {
+          const int k3 = k3b + kb;
+          const T a3 = a0[k3];
+          T x01[NI], x23e[NJ], x23o[NJ], b1[R], b2e[NJ], b2o[NJ];
+#pragma unroll
+          for (int i = 0; i < NI; ++i) x01[i] = X[half * mm + k3 * m + k2v[i]];
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            x23e[j] = X[2 * mm + k3 * m + k1v[j]];
+            x23o[j] = X[3 * mm + k3 * m + k1v[j]];
+            b2e[j] = (T)0;
+            b2o[j] = (T)0;
+          }
+#pragma unroll
+          for (int i = 0; i < R; ++i) b1[i] = (T)0;
+#pragma unroll
+          for (int i = 0; i < NI; ++i) {
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+              const bool ok = ok2[i] && ok1[j];
+              const T x23 = odd2[i] ? x23o[j] : x23e[j];
+              T E = a1r[j] * x01[i];
+              E = madd(a2r[i], x23, E);
+              E = madd(a3, x45[i][j], E);
+              // 1/D: the class table, or lam + sum_d (4/h_d^2) Lam[k_d] summed in that order and inverted
+              T rinv;
+              if constexpr (TAB)
+                rinv = Rt[(int64_t)(k3 * m + k2v[i]) * m + k1v[j]];
+              else
+                rinv = eb_inv(lam + sc.e[0] * lI[k1v[j]] + sc.e[1] * lI[k2v[i]] + sc.e[2] * lI[k3]);
+              const T V = ok ? E * rinv : (T)0;
+              b1[i] = madd(a1r[j], V, b1[i]);
+              if (odd2[i])
+                b2o[j] = madd(a2r[i], V, b2o[j]);
+              else
+                b2e[j] = madd(a2r[i], V, b2e[j]);
+              b3[i][j] = madd(a3, V, b3[i][j]);
+            }
+          }
+          // faces 0 / 1 at (k3, k2): the half-warp sums, even class below, odd above
+          const T s1 = rs16_reduce<R>(b1, lane);
+          const T other = eb_shx(s1, 16);
+#pragma unroll
+          for (int i = 0; i < NI; ++i)
+            if (wr && me == i && ok2[i]) {
+              const int r = k3 * m + k2v[i];
+              if (half == 0)
+                Ze[0 * mm + r] = al0 * (s1 + other);
+              else
+                Ze[1 * mm + r] = al0 * (other - s1);
+            }
+          // faces 2 / 3: this warp's partial sums over its rows
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            Y[((warp * kEbKB + kb) * 2 + 0) * (NJ * 32) + j * 32 + lane] = b2e[j];
+            Y[((warp * kEbKB + kb) * 2 + 1) * (NJ * 32) + j * 32 + lane] = b2o[j];
+          }
+        }
+        __syncthreads();
+        // faces 2 / 3 at (k3, k1): the 16 warps' partial sums in warp order
+        for (int o = tid; o < nb * NJ * 32; o += blockDim.x) {
+          const int kb = o / (NJ * 32), s = o - kb * (NJ * 32), j = s >> 5, ln = s & 31;
+          const int c = (ln >> 4) ? ne + 16 * j + (ln & 15) : 16 * j + (ln & 15);
+          const bool okc = (ln >> 4) ? c < m : c < ne;
+          if (!okc) continue;
+          T se = Y[((0 * kEbKB + kb) * 2 + 0) * (NJ * 32) + s];
+          T so = Y[((0 * kEbKB + kb) * 2 + 1) * (NJ * 32) + s];
+#pragma unroll
+          for (int w = 1; w < kEbWarps; ++w) {
+            se = se + Y[((w * kEbKB + kb) * 2 + 0) * (NJ * 32) + s];
+            so = so + Y[((w * kEbKB + kb) * 2 + 1) * (NJ * 32) + s];
+          }
+          const int r = (k3b + kb) * m + c;
+          Ze[2 * mm + r] = al1 * (se + so);
+          Ze[3 * mm + r] = al1 * (se - so);
+        }
+        __syncthreads();
+      }
+      // faces 4 / 5 at (k2, k1): the even planes' sums wait in X_4 (read into registers at
+      // the start and owned by this thread), then both are combined
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          if (!(ok2[i] && ok1[j])) continue;
+          const int r = k2v[i] * m + k1v[j];
+          if (q3 == 0) {
+            X[4 * mm + r] = b3[i][j];
+          } else {
+            const T ev = X[4 * mm + r];
+            Ze[4 * mm + r] = al2 * (ev + b3[i][j]);
+            Ze[5 * mm + r] = al2 * (ev - b3[i][j]);
+          }
+        }
+    }
+  }
+}
+
+}  // namespace
+
+// Launch shape of the streamed eigenbasis Schur kernel for the level (block 512).
+template <typename T>
+LaunchCfg plan_schur_eb(const Geo& G, int nsm) {
+  LaunchCfg c;
+  const int m = G.m, nj = m > 32 ? 2 : 1;
+  c.block = 512;
+  c.smem = eb_smem_elems(m, nj) * sizeof(T);
+  c.ok = m >= 1 && m < SEMMG_MAX_DEGREE && c.smem <= (size_t)kEbSmemMax;
+  // one CTA per SM: the kernel takes 70 to 122 registers a thread (FP32 to FP64 tiles)
+  c.grid = (int)(G.nelem < nsm ? G.nelem : nsm);
+  if (c.grid < 1) c.grid = 1;
+  return c;
+}
+
+template <typename T, bool TAB>
+void launch_schur_eb_tab(const Geo& G, const Tabs<T>& t, const T* Ut, T* Z, const LaunchCfg& c, cudaStream_t st) {
+  if (G.m <= 16)
+    k_schur_eb<T, 1, 1, TAB><<<c.grid, c.block, c.smem, st>>>(G, t, Ut, Z);
+  else if (G.m <= 32)
+    k_schur_eb<T, 2, 1, TAB><<<c.grid, c.block, c.smem, st>>>(G, t, Ut, Z);
+  else
+    k_schur_eb<T, 3, 2, TAB><<<c.grid, c.block, c.smem, st>>>(G, t, Ut, Z);
+}
+
+template <typename T>
+void launch_schur_eb(const Geo& G, const Tabs<T>& t, const T* Ut, T* Z, const LaunchCfg& c, cudaStream_t st) {
+  if (G.m == 0 || G.nelem == 0 || !c.ok) return;
+  if (t.Relem)
+    launch_schur_eb_tab<T, true>(G, t, Ut, Z, c, st);
+  else
+    launch_schur_eb_tab<T, false>(G, t, Ut, Z, c, st);
+}
+
+template <typename T, bool TAB>
+int schur_eb_attrs_tab() {
+  int bad = cudaFuncSetAttribute(k_schur_eb<T, 1, 1, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEbSmemMax);
+  bad |= cudaFuncSetAttribute(k_schur_eb<T, 2, 1, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEbSmemMax);
+  bad |= cudaFuncSetAttribute(k_schur_eb<T, 3, 2, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEbSmemMax);
+  return bad;
+}
+
+template <typename T>
+int schur_eb_attrs() {
+  return schur_eb_attrs_tab<T, true>() | schur_eb_attrs_tab<T, false>();
+}
+
+}  // namespace semmg

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "semmg.h"
+#include "ff.cuh"
 
 namespace semmg {
 
@@ -458,7 +459,7 @@ template <typename T> LaunchCfg plan_elem_schur(const Geo& G, int nsm, size_t ca
 // receives the element terms in the face eigenbasis, for launch_face_bwd_assemble
 template <typename T> void launch_elem_schur(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* ws,
                                              const LaunchCfg& c, cudaStream_t st, int pre = 0);
-// Face-parallel form of the condensed operator (kernels_face.cu), for levels
+// Face-parallel form of the condensed operator (face_kernel.cuh), for levels
 // with face interiors (m >= 1):
 //   launch_face_fwd: Ut[s] = c_f (Sh^T U_f Sh) on every face f (slots of the
 //     face groups, same indexing as u; Ut holds at least G.oE1 values);
@@ -471,13 +472,23 @@ template <typename T, typename TF>
 void launch_face_bwd_assemble(const Geo& G, const Tabs<T>& t, const TF* F, const T* u, const T* Ut, const T* Zh,
                               TF* out, int mode, cudaStream_t st);
 int set_face_smem_limits();
+// Float-float instantiations (kernels_ff.cu): the face-parallel form only (levels with m >= 11).
+int set_ff_smem_limits();
+// Element Schur term in the face eigenbasis with the eigenspace streamed plane by plane
+// (schur_eb.cuh): the float-float element kernel of the face-parallel levels.
+template <typename T> LaunchCfg plan_schur_eb(const Geo& G, int nsm);
+template <typename T> void launch_schur_eb(const Geo& G, const Tabs<T>& t, const T* Ut, T* Z, const LaunchCfg& c,
+                                           cudaStream_t st);
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm);
+// Arithmetic T: double, or ff (float-float); f_nodal, Z, uhat and u_nodal are FP64 either way.
 // Gsave (optional): scaled interior eigen-coefficients D^{-1} S^T F_I per element, m^3 each
-void launch_elem_condense(const Geo& G, const Tabs<double>& t, const double* f_nodal, double* Z, double* Gsave,
-                          double* ws, const LaunchCfg& c, cudaStream_t st);
+template <typename T>
+void launch_elem_condense(const Geo& G, const Tabs<T>& t, const double* f_nodal, double* Z, T* Gsave, T* ws,
+                          const LaunchCfg& c, cudaStream_t st);
 // Gin (optional): the coefficients saved by launch_elem_condense for the same f_nodal
-void launch_elem_recover(const Geo& G, const Tabs<double>& t, const double* f_nodal, const double* Gin,
-                         const double* uhat, double* u_nodal, double* ws, const LaunchCfg& c, cudaStream_t st);
+template <typename T>
+void launch_elem_recover(const Geo& G, const Tabs<T>& t, const double* f_nodal, const T* Gin, const double* uhat,
+                         double* u_nodal, T* ws, const LaunchCfg& c, cudaStream_t st);
 template <typename T> void launch_assemble(const Geo& G, const Tabs<T>& t, const T* F, const T* u,
                                            const T* Z, T* out, int mode, cudaStream_t st);
 // out = F - Hhat u (mode 0) / Hhat u (mode 1) in FP64 arithmetic with FP32 F and out

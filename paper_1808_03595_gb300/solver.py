@@ -55,7 +55,8 @@ class Context:
         opts.nu_post = nu_post
         opts.precision = {"fp64": L.SEMMG_FP64, "mixed": L.SEMMG_MIXED, "mixed_fp32": L.SEMMG_MIXED_FP32,
                           "mixed_tc": L.SEMMG_MIXED_TC, "mixed_fp32_tc": L.SEMMG_MIXED_FP32_TC,
-                          "mixed_bf16": L.SEMMG_MIXED_BF16}[precision]
+                          "mixed_bf16": L.SEMMG_MIXED_BF16, "mixed_ff": L.SEMMG_MIXED_FF,
+                          "mixed_ff_tc": L.SEMMG_MIXED_FF_TC}[precision]
         opts.max_iter = max_iter
         opts.solver = {"mg": L.SEMMG_SOLVER_MG, "kmg": L.SEMMG_SOLVER_KMG}[solver]
         opts.nu_vary = 1 if nu_vary else 0
@@ -149,6 +150,12 @@ class Context:
     def residual(self, level, f, u, out=None):
         out = self._hat(level) if out is None else out
         self._check(self._lib.semmg_residual(self._ctx, level, _ptr(f), _ptr(u), _ptr(out), _stream()))
+        return out
+
+    def residual_cycle(self, level, f, u, out=None):
+        """The V-cycle's level residual f - Hhat u of a mixed context: FP32 vectors, the context's arithmetic."""
+        out = self._hat(level, torch.float32) if out is None else out
+        self._check(self._lib.semmg_residual_cycle(self._ctx, level, _ptr(f), _ptr(u), _ptr(out), _stream()))
         return out
 
     @staticmethod

@@ -121,7 +121,7 @@ def test_tc_krylov_and_batch():
         c.close()
 
 
-@pytest.mark.parametrize("precision", ["mixed_tc", "mixed_bf16"])
+@pytest.mark.parametrize("precision", ["mixed_tc", "mixed_bf16", "mixed_ff_tc"])
 def test_tc_solve_stretched_p48_full_size(precision):
     # the 6^3 stretched workload at p = 48: the finest level's smoother on the tensor cores
     from paper_1808_03595_gb300 import Context
