@@ -124,6 +124,7 @@ struct semmg_ctx {
   void* wss = nullptr;
   size_t ws_bytes = 0;
   LaunchCfg fdm;
+  LaunchCfg fsff;  // float-float condensation and recovery (fdm_stream.cuh), when the form and level allow it
   // FP64 outer iteration
   double* Fh = nullptr;
   double* Uh = nullptr;
@@ -918,7 +919,7 @@ void correction(semmg_ctx* c, double* u, const double* r, cudaStream_t st) {
 // eigen-coefficients of F_I are kept in Gs for recover_impl(..., use_saved).
 // The solve of a float-float form condenses and recovers in float-float where the finest
 // level has its tables (the face-parallel levels); the public entry points stay FP64.
-bool ff_fdm(const semmg_ctx* c) { return residff(c) && c->dl[c->L()].tff.Sh != nullptr; }
+bool ff_fdm(const semmg_ctx* c) { return residff(c) && c->dl[c->L()].tff.Sh != nullptr && c->fsff.ok; }
 
 void condense_impl(semmg_ctx* c, const double* f, double* fh, bool save, cudaStream_t st, bool ffok = false) {
   const int L = c->L();
@@ -926,8 +927,7 @@ void condense_impl(semmg_ctx* c, const double* f, double* fh, bool save, cudaStr
   const double nn = (double)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
   Tic t(c, SEMMG_K_CONDENSE, st);
   if (ffok && ff_fdm(c))
-    launch_elem_condense<ff>(G, c->dl[L].tff, f, (double*)c->Zs, save ? (ff*)c->Gs : nullptr, (ff*)c->wss, c->fdm,
-                             st);
+    launch_fs_condense<ff>(G, c->dl[L].tff, f, (double*)c->Zs, save ? (ff*)c->Gs : nullptr, (ff*)c->wss, c->fsff, st);
   else
     launch_elem_condense<double>(G, c->dl[L].td, f, (double*)c->Zs, save ? c->Gs : nullptr, (double*)c->wss,
                                  c->fdm, st);
@@ -944,9 +944,8 @@ void recover_impl(semmg_ctx* c, const double* f, const double* uh, double* u, bo
   const double nn = (double)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
   Tic t(c, SEMMG_K_RECOVER, st);
   launch_unpack(G, uh, u, st);
-  if (ffok && ff_fdm(c))
-    launch_elem_recover<ff>(G, c->dl[L].tff, f, use_saved ? (const ff*)c->Gs : nullptr, uh, u, (ff*)c->wss, c->fdm,
-                            st);
+  if (ffok && use_saved && ff_fdm(c))
+    launch_fs_recover<ff>(G, c->dl[L].tff, (const ff*)c->Gs, uh, u, (ff*)c->wss, c->fsff, st);
   else
     launch_elem_recover<double>(G, c->dl[L].td, f, use_saved ? c->Gs : nullptr, uh, u, (double*)c->wss, c->fdm, st);
   t.toc(G.m > 0 ? fdm_flops(G) : 0.0, 8.0 * (2 * nn + G.size), 2);
@@ -1299,6 +1298,10 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     }
   }
   c->fdm = plan_elem_fdm(c->geo[nl - 1], c->nsm);
+  if (residff(c.get()) && face_form(c->geo[nl - 1])) {
+    c->fsff = plan_fs<ff>(c->geo[nl - 1], c->nsm);
+    if (c->fsff.ok) wsb = std::max(wsb, c->fsff.ws_elems() * sizeof(ff));
+  }
   for (int l = 0; l < nl; ++l) {
     const DevLevel& D = c->dl[l];
     if (!D.schur64.ok || !D.schur32.ok || (l >= 1 && (!D.star64.ok || !D.star32.ok)))

@@ -204,20 +204,20 @@ __device__ __forceinline__ void tx_lines_g(const Lines& L, int ax, const T* __re
     int base, str, i2, k0, k1, j0, j1, even;
     line_of(L, ax, l, &base, &str, &i2);
     line_block(L, g, &k0, &k1, &j0, &j1, &even);
-    T a[kG];
+    Acc<T> a[kG];
 #pragma unroll
-    for (int q = 0; q < kG; ++q) a[q] = 0;
+    for (int q = 0; q < kG; ++q) a[q] = Acc<T>::zero();
     for (int j = j0; j < j1; ++j) {
       const T yv = Y[base + j * str];
       const T* sr = S + (even ? L.h + j : j) * n + k0;
 #pragma unroll
       for (int q = 0; q < kG; ++q)
-        if (k0 + q < k1) a[q] = madd(sr[q], yv, a[q]);
+        if (k0 + q < k1) a[q].add(sr[q], yv);
     }
     const T s = sc2 ? sc2[i2] : scale;
 #pragma unroll
     for (int q = 0; q < kG; ++q)
-      if (k0 + q < k1) Z[base + (k0 + q) * str] = s * a[q];
+      if (k0 + q < k1) Z[base + (k0 + q) * str] = s * a[q].value();
   }
 }
 
@@ -232,22 +232,22 @@ __device__ __forceinline__ void txT_lines_g(const Lines& L, int ax, const T* __r
     int base, str, i2, k0, k1, j0, j1, even;
     line_of(L, ax, l, &base, &str, &i2);
     line_block(L, g, &k0, &k1, &j0, &j1, &even);
-    T a[kG];
+    Acc<T> a[kG];
     const T* sr[kG];
 #pragma unroll
     for (int q = 0; q < kG; ++q) {
-      a[q] = 0;
+      a[q] = Acc<T>::zero();
       const int jo = min(k0 + q, k1 - 1);
       sr[q] = S + (even ? L.h + jo : jo) * n;
     }
     for (int k = j0; k < j1; ++k) {
       const T bv = B[base + k * str];
 #pragma unroll
-      for (int q = 0; q < kG; ++q) a[q] = madd(sr[q][k], bv, a[q]);
+      for (int q = 0; q < kG; ++q) a[q].add(sr[q][k], bv);
     }
 #pragma unroll
     for (int q = 0; q < kG; ++q)
-      if (k0 + q < k1) Y[base + (k0 + q) * str] = a[q];
+      if (k0 + q < k1) Y[base + (k0 + q) * str] = a[q].value();
   }
 }
 

@@ -83,6 +83,39 @@ template <typename T>
 __device__ __forceinline__ T madd(T a, T b, T c) { return c + a * b; }
 __device__ __forceinline__ ff madd(ff a, ff b, ff c) { return ff_fma(a, b, c); }
 
+// Sums of products in the kernels' long multiply-add chains: for float-float the
+// running sum keeps an exact high word (TwoSum) and gathers every rounding error
+// (the sums' and the products') in one FP32 word, normalised once at the end
+// (the compensated dot product of Ogita, Rump and Oishi); for FP32 and FP64 a
+// plain accumulator that the compiler contracts into FMAs.
+template <typename T>
+struct Acc {
+  T v;
+  __device__ __forceinline__ static Acc zero() { return Acc{(T)0}; }
+  __device__ __forceinline__ void add(T a, T b) { v = v + a * b; }
+  __device__ __forceinline__ T value() const { return v; }
+};
+
+template <>
+struct Acc<ff> {
+  float s, c;
+  __device__ __forceinline__ static Acc zero() { return Acc{0.0f, 0.0f}; }
+  __device__ __forceinline__ void add(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    float t;
+    ff_two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, e));
+  }
+  __device__ __forceinline__ ff value() const {
+    float h, l;
+    ff_two_sum(s, c, h, l);
+    return ff(h, l);
+  }
+};
+
 // 1 / d: the FP32 reciprocal refined by one Newton step in float-float,
 // y + y (1 - d y), which doubles its correct bits
 __device__ __forceinline__ ff ff_recip(ff d) {

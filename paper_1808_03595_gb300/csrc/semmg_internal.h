@@ -474,13 +474,20 @@ void launch_face_bwd_assemble(const Geo& G, const Tabs<T>& t, const TF* F, const
 int set_face_smem_limits();
 // Float-float instantiations (kernels_ff.cu): the face-parallel form only (levels with m >= 11).
 int set_ff_smem_limits();
+// Condensation and recovery with the interior transforms staged through shared memory
+// (fdm_stream.cuh), instantiated for float-float; recovery from the saved coefficients only.
+template <typename T> LaunchCfg plan_fs(const Geo& G, int nsm);
+template <typename T> void launch_fs_condense(const Geo& G, const Tabs<T>& t, const double* f_nodal, double* Z,
+                                              T* Gsave, T* ws, const LaunchCfg& c, cudaStream_t st);
+template <typename T> void launch_fs_recover(const Geo& G, const Tabs<T>& t, const T* Gin, const double* uhat,
+                                             double* u_nodal, T* ws, const LaunchCfg& c, cudaStream_t st);
 // Element Schur term in the face eigenbasis with the eigenspace streamed plane by plane
 // (schur_eb.cuh): the float-float element kernel of the face-parallel levels.
 template <typename T> LaunchCfg plan_schur_eb(const Geo& G, int nsm);
 template <typename T> void launch_schur_eb(const Geo& G, const Tabs<T>& t, const T* Ut, T* Z, const LaunchCfg& c,
                                            cudaStream_t st);
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm);
-// Arithmetic T: double, or ff (float-float); f_nodal, Z, uhat and u_nodal are FP64 either way.
+// Arithmetic T: double (the float-float forms use launch_fs_condense / launch_fs_recover).
 // Gsave (optional): scaled interior eigen-coefficients D^{-1} S^T F_I per element, m^3 each
 template <typename T>
 void launch_elem_condense(const Geo& G, const Tabs<T>& t, const double* f_nodal, double* Z, T* Gsave, T* ws,

@@ -140,8 +140,9 @@ def test_ff_tc_p48_full_size_iterations():
     assert abs(red3["mixed_ff_tc"] / red3["mixed_tc"] - 1.0) < 0.05, red3
 
 
-@pytest.mark.parametrize("p,n", [(16, 3), (33, 2), (48, 2)])
+@pytest.mark.parametrize("p,n", [(16, 3), (33, 2), (48, 2), (16, 6), (24, 5)])
 def test_ff_condense_and_recover(p, n):
+    # 6^3 and 5^3 elements fill the SMs in a partial last round: two CTAs share each element there
     # a solve with no outer iteration condenses f, takes u_hat = 0 and recovers the interiors:
     # u = (0 on the skeleton, H_II^{-1} F_I inside), here in float-float against the FP64 form
     # and the oracle's recovery
