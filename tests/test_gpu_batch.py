@@ -26,7 +26,8 @@ def _case(n, p, lam, seed, precision):
 
 
 CASES = [_case(2, 4, 0.01, 1, "fp64"), _case(3, 7, 5.0, 2, "mixed"), _case(4, 5, 300.0, 3, "fp64"),
-         _case(2, 12, 1.0, 5, "mixed_fp32"), _case(3, 9, 0.0, 4, "fp64")]
+         _case(2, 12, 1.0, 5, "mixed_fp32"), _case(3, 9, 0.0, 4, "fp64"), _case(3, 14, 1.0, 6, "mixed_ff_tc"),
+         _case(2, 16, 2.0, 7, "mixed_ff")]
 
 
 def test_batch_equals_individual_solves_and_relaunches():

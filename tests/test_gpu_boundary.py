@@ -170,7 +170,9 @@ def test_coarse_solve_and_vcycle(mesh_name, bc, p0, lam):
                                                         (("D", "D", "N", "N", "N", "N"), "scc", "mg", "mixed", 8),
                                                         (("N", "D", "N", "D", "D", "N"), "mixed", "kmg", "fp64", 8),
                                                         (NEUMANN, "ccc", "kmg", "fp64", 12),
-                                                        (("N", "D", "N", "D", "D", "N"), "mixed", "mg", "mixed_fp32", 13)])
+                                                        (("N", "D", "N", "D", "D", "N"), "mixed", "mg", "mixed_fp32", 13),
+                                                        (("N", "D", "N", "D", "D", "N"), "mixed", "kmg", "mixed_ff", 13),
+                                                        (NEUMANN, "ccc", "mg", "mixed_ff_tc", 16)])
 def test_solve_manufactured(bc, kind, solver, precision, p):
     # solutions with zero normal derivative on the Neumann faces (see the oracle pins);
     # p >= 12 runs the face-parallel operator
@@ -208,10 +210,11 @@ def test_pure_neumann_needs_positive_lambda():
 
 @pytest.mark.parametrize("bc,kind,solver,precision", [(("P",) * 6, "ccc2", "mg", "fp64"),
                                                       (("P", "P", "D", "D", "D", "D"), "css", "kmg", "mixed"),
-                                                      (("P", "P", "N", "N", "D", "D"), "scs", "mg", "mixed_tc")])
+                                                      (("P", "P", "N", "N", "D", "D"), "scs", "mg", "mixed_tc"),
+                                                      (("P", "P", "N", "N", "D", "D"), "scs", "kmg", "mixed_ff_tc")])
 def test_solve_manufactured_periodic(bc, kind, solver, precision):
     # period-1 trigonometric solutions (see the oracle pins); the nodal result repeats plane 0
-    p = 16 if precision == "mixed_tc" else 8
+    p = 16 if precision in ("mixed_tc", "mixed_ff_tc") else 8
     h = workloads.uniform_widths(3)
     m = dense.Mesh(h, p, 1.0, bc)
     x = workloads.node_coords(h, p)
