@@ -35,8 +35,8 @@ namespace semmg {
 namespace {
 
 constexpr int kEbWarps = 16;  // 512 threads
-constexpr int kEbKB = 4;      // planes per shared-memory round of the k2 sums
-constexpr int kEbSmemMax = 200 * 1024;
+constexpr int kEbKB = 2;      // planes per shared-memory round of the k2 sums
+constexpr int kEbSmemMax = 224 * 1024;
 
 __device__ __forceinline__ float eb_shx(float v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
 __device__ __forceinline__ double eb_shx(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
@@ -78,10 +78,23 @@ __device__ __forceinline__ int rs16_index(int lane) {
 __host__ __device__ constexpr int eb_pow2(int n) { return n <= 1 ? 1 : (n <= 2 ? 2 : (n <= 4 ? 4 : 8)); }
 
 // Shared memory of the kernel, in elements of T: X (6 m^2), Y (k2 partial sums:
-// 16 warps x KB planes x 2 classes x NJ*32 slots), a0 (m), lI (m).
-__host__ __device__ constexpr size_t eb_smem_elems(int m, int nj) {
-  return (size_t)6 * m * m + (size_t)kEbWarps * kEbKB * 2 * nj * 32 + 2 * (size_t)m;
+// 16 warps x KB planes x 2 classes x NJ*32 slots), a0 (m), lI (m), and with the
+// 1/D table the staging of each thread's table values for two planes
+// (2 x NI*NJ slots x 512 threads, thread index fastest).
+__host__ __device__ constexpr size_t eb_smem_elems(int m, int ni, int nj, bool tab) {
+  return (size_t)6 * m * m + (size_t)kEbWarps * kEbKB * 2 * nj * 32 + 2 * (size_t)m +
+         (tab ? (size_t)2 * ni * nj * 512 : 0);
 }
+
+// Asynchronous copy of one 8-byte table value into shared memory (cp.async, sm_80+);
+// copies complete in commit-group order, and a thread reads only its own copies.
+__device__ __forceinline__ void eb_cp8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void eb_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void eb_cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // 1/D at one point: the element class's table, or the sum of the scaled eigenvalues inverted
 __device__ __forceinline__ double eb_inv(double d) { return 1.0 / d; }
@@ -100,6 +113,7 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
   T* Y = X + 6 * mm;
   T* a0 = Y + kEbWarps * kEbKB * 2 * NJ * 32;
   T* lI = a0 + m;
+  T* Rs = lI + m;  // [plane & 1][i NJ + j][thread] (TAB only)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, half = lane >> 4, hl = lane & 15;
   for (int i = tid; i < m; i += blockDim.x) {
     a0[i] = t.a0[i];
@@ -130,6 +144,19 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
     elem_coords(G, e, &a1, &a2, &a3);
     const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
     const T* Rt = TAB ? t.Relem + sc.cls * n3 : nullptr;
+    // stage this thread's table values of plane k3 into buffer k3 & 1 (one commit group per plane)
+    auto stage = [&](int k3) {
+      if constexpr (TAB) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+          for (int j = 0; j < NJ; ++j)
+            if (ok2[i] && ok1[j])
+              eb_cp8(Rs + ((size_t)((k3 & 1) * NI * NJ + i * NJ + j) * blockDim.x + tid),
+                     Rt + ((int64_t)k3 * m + k2v[i]) * m + k1v[j]);
+        eb_cp_commit();
+      }
+    };
     __syncthreads();  // X and Y of the previous element are consumed
     for (int idx = tid; idx < 3 * mm; idx += blockDim.x) {
       const int d = idx / mm, r = idx - d * mm;
@@ -146,6 +173,7 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
     for (int i = 0; i < NI; ++i) a2r[i] = ok2[i] ? a0[k2v[i]] : (T)0;
     T* Ze = Z + e * 6 * mm;
     const T al0 = sc.al[0], al1 = sc.al[1], al2 = sc.al[2];
+    stage(0);
     for (int q3 = 0; q3 < 2; ++q3) {
       const int lo3 = q3 ? ne : 0, hi3 = q3 ? m : ne;
       T x45[NI][NJ], b3[NI][NJ];
@@ -161,6 +189,14 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
         for (int kb = 0; kb < nb; ++kb) {
           const int k3 = k3b + kb;
           const T a3 = a0[k3];
+          if constexpr (TAB) {  // the next plane's values on their way, this plane's in place
+            if (k3 + 1 < m) {
+              stage(k3 + 1);
+              eb_cp_wait<1>();
+            } else {
+              eb_cp_wait<0>();
+            }
+          }
           T x01[NI], x23e[NJ], x23o[NJ], b1[R], b2e[NJ], b2o[NJ];
 #pragma unroll
           for (int i = 0; i < NI; ++i) x01[i] = X[half * mm + k3 * m + k2v[i]];
@@ -185,7 +221,7 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
               // 1/D: the class table, or lam + sum_d (4/h_d^2) Lam[k_d] summed in that order and inverted
               T rinv;
               if constexpr (TAB)
-                rinv = Rt[(int64_t)(k3 * m + k2v[i]) * m + k1v[j]];
+                rinv = Rs[(size_t)((k3 & 1) * NI * NJ + i * NJ + j) * blockDim.x + tid];
               else
                 rinv = eb_inv(lam + sc.e[0] * lI[k1v[j]] + sc.e[1] * lI[k2v[i]] + sc.e[2] * lI[k3]);
               const T V = ok ? E * rinv : (T)0;
@@ -262,9 +298,9 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
 template <typename T>
 LaunchCfg plan_schur_eb(const Geo& G, int nsm) {
   LaunchCfg c;
-  const int m = G.m, nj = m > 32 ? 2 : 1;
+  const int m = G.m, nj = m > 32 ? 2 : 1, ni = m <= 16 ? 1 : (m <= 32 ? 2 : 3);
   c.block = 512;
-  c.smem = eb_smem_elems(m, nj) * sizeof(T);
+  c.smem = eb_smem_elems(m, ni, nj, true) * sizeof(T);  // the table-staging size covers both forms
   c.ok = m >= 1 && m < SEMMG_MAX_DEGREE && c.smem <= (size_t)kEbSmemMax;
   // one CTA per SM: the kernel takes 70 to 122 registers a thread (FP32 to FP64 tiles)
   c.grid = (int)(G.nelem < nsm ? G.nelem : nsm);
