@@ -715,7 +715,7 @@ void apply_op(semmg_ctx* c, int l, const Tabs<T>& tb, const LaunchCfg& cfg, cons
       // registers (its arithmetic is issue-bound, the stored form memory-bound); FP64 and FP32
       // keep the stored form, whose FP64 work fits the narrow FP64 pipe as well
       if constexpr (std::is_same<T, ff>::value)
-        launch_schur_eb<T>(G, tb, (const T*)c->Uts, (T*)c->Zs, plan_schur_eb<T>(G, c->nsm), st);
+        launch_schur_eb<T>(G, tb, (const T*)c->Uts, (T*)c->Zs, (T*)c->wss, plan_schur_eb<T>(G, c->nsm), st);
       else
         launch_elem_schur<T>(G, tb, (const T*)c->Uts, (T*)c->Zs, (T*)c->wss, cfg, st, 1);
       t.toc(schur_flops(G), 3 * fb + zb, 2);
@@ -1267,6 +1267,11 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     DevLevel& D = c->dl[l];
     D.schur64 = plan_elem_schur<double>(G, c->nsm);
     D.schur32 = plan_elem_schur<float>(G, c->nsm);
+    if (residff(c.get()) && face_form(G)) {
+      const LaunchCfg eb = plan_schur_eb<ff>(G, c->nsm);
+      if (!eb.ok) return SEMMG_ERR_UNSUPPORTED;
+      wsb = std::max(wsb, eb.ws_elems() * sizeof(ff));
+    }
     wsb = std::max(wsb, D.schur64.ws_elems() * sizeof(double));
     wsb = std::max(wsb, D.schur32.ws_elems() * sizeof(float));
     zs = std::max(zs, (size_t)(G.nelem * 6 * (int64_t)G.m * G.m));

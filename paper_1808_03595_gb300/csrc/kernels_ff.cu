@@ -23,7 +23,7 @@ int face_ff_attrs() {
 }  // namespace
 
 template LaunchCfg plan_schur_eb<ff>(const Geo&, int);
-template void launch_schur_eb<ff>(const Geo&, const Tabs<ff>&, const ff*, ff*, const LaunchCfg&, cudaStream_t);
+template void launch_schur_eb<ff>(const Geo&, const Tabs<ff>&, const ff*, ff*, ff*, const LaunchCfg&, cudaStream_t);
 template void launch_face_fwd<ff>(const Geo&, const Tabs<ff>&, const ff*, ff*, cudaStream_t);
 template LaunchCfg plan_fs<ff>(const Geo&, int);
 template void launch_fs_condense<ff>(const Geo&, const Tabs<ff>&, const double*, double*, ff*, ff*, const LaunchCfg&,

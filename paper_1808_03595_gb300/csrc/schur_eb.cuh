@@ -15,7 +15,8 @@
 // (elem_kernel.cuh derives the same terms with W stored; here W is never
 // stored: each k3-plane is formed in registers and consumed at once).
 //
-// Thread mapping (512 threads, 16 warps; one element per CTA at a time):
+// Thread mapping (512 threads, 16 warps; one element per CTA, or per cluster of two
+// CTAs that take alternate blocks of planes, at a time):
 //  - warp w owns the rows k2 = w + 16 i (i < NI) of every plane; a row's parity
 //    class is uniform over the warp;
 //  - lane l owns NJ column slots: lanes 0..15 the even columns k1 = 16 j + l,
@@ -104,8 +105,8 @@ __device__ __forceinline__ ff eb_inv(ff d) { return ff_recip(d); }
 // TAB: 1/D from the element class's table (t.Relem), else computed per point; a
 // template parameter so that neither form carries the other's work.
 template <typename T, int NI, int NJ, bool TAB>
-__global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* __restrict__ Ut,
-                                                     T* __restrict__ Z) {
+__global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* __restrict__ Ut, T* __restrict__ Z,
+                                                     T* ws, int cs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = G.m, mm = m * m, ne = (m + 1) / 2;
   const int64_t n3 = (int64_t)mm * m;
@@ -113,8 +114,27 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
   T* Y = X + 6 * mm;
   T* a0 = Y + kEbWarps * kEbKB * 2 * NJ * 32;
   T* lI = a0 + m;
-  T* Rs = lI + m;  // [plane & 1][i NJ + j][thread] (TAB only)
+  T* Rs = lI + m;  // [step & 1][i NJ + j][thread] (TAB only)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, half = lane >> 4, hl = lane & 15;
+  // cs = 2: the two CTAs of a cluster share an element, taking alternate blocks of KB planes of
+  // each parity class; the second CTA's sums over k3 (faces 4, 5) go through ws to the first,
+  // which adds them after its own
+  const Team tm = team_of(cs);
+  const int rank = tm.id / (int)blockDim.x;
+  T* wsT = ws + (int64_t)(blockIdx.x / cs) * 2 * NI * NJ * 512;
+  // this CTA's plane after k3 (k3 < 0: its first plane), or -1
+  auto next_plane = [&](int k3) -> int {
+    if (k3 >= 0) {
+      const int q = k3 >= ne ? 1 : 0, lo = q ? ne : 0, hi = q ? m : ne, off = k3 - lo;
+      if ((off + 1) % kEbKB != 0 && k3 + 1 < hi) return k3 + 1;
+      const int nb = lo + (off / kEbKB + cs) * kEbKB;
+      if (nb < hi) return nb;
+      if (q == 1) return -1;
+    } else if (rank * kEbKB < ne) {
+      return rank * kEbKB;
+    }
+    return ne + rank * kEbKB < m ? ne + rank * kEbKB : -1;
+  };
   for (int i = tid; i < m; i += blockDim.x) {
     a0[i] = t.a0[i];
     lI[i] = t.lamI[i];
@@ -139,25 +159,25 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
     odd2[i] = r >= ne;  // uniform over the warp
     k2v[i] = ok2[i] ? r : 0;
   }
-  for (int64_t e = blockIdx.x; e < G.nelem; e += gridDim.x) {
+  for (int64_t e = blockIdx.x / cs; e < G.nelem; e += gridDim.x / cs) {
     int a1, a2, a3;
     elem_coords(G, e, &a1, &a2, &a3);
     const ElemScal<T> sc = elem_scalars(t, a1, a2, a3);
     const T* Rt = TAB ? t.Relem + sc.cls * n3 : nullptr;
-    // stage this thread's table values of plane k3 into buffer k3 & 1 (one commit group per plane)
-    auto stage = [&](int k3) {
+    // stage this thread's table values of plane k3 into buffer b (one commit group per plane)
+    auto stage = [&](int k3, int b) {
       if constexpr (TAB) {
 #pragma unroll
         for (int i = 0; i < NI; ++i)
 #pragma unroll
           for (int j = 0; j < NJ; ++j)
             if (ok2[i] && ok1[j])
-              eb_cp8(Rs + ((size_t)((k3 & 1) * NI * NJ + i * NJ + j) * blockDim.x + tid),
+              eb_cp8(Rs + ((size_t)(b * NI * NJ + i * NJ + j) * blockDim.x + tid),
                      Rt + ((int64_t)k3 * m + k2v[i]) * m + k1v[j]);
         eb_cp_commit();
       }
     };
-    __syncthreads();  // X and Y of the previous element are consumed
+    tm.sync();  // X and Y of the previous element are consumed, and the team's ws slice
     for (int idx = tid; idx < 3 * mm; idx += blockDim.x) {
       const int d = idx / mm, r = idx - d * mm;
       const T a = Ut[elem_face_base(G, a1, a2, a3, 2 * d) + r];
@@ -173,7 +193,11 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
     for (int i = 0; i < NI; ++i) a2r[i] = ok2[i] ? a0[k2v[i]] : (T)0;
     T* Ze = Z + e * 6 * mm;
     const T al0 = sc.al[0], al1 = sc.al[1], al2 = sc.al[2];
-    stage(0);
+    int step = 0;  // planes this CTA has done in this element (staging buffer step & 1)
+    {
+      const int f = next_plane(-1);
+      if (f >= 0) stage(f, 0);
+    }
     for (int q3 = 0; q3 < 2; ++q3) {
       const int lo3 = q3 ? ne : 0, hi3 = q3 ? m : ne;
       T x45[NI][NJ], b3[NI][NJ];
@@ -184,14 +208,16 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
           x45[i][j] = (ok2[i] && ok1[j]) ? X[(4 + q3) * mm + k2v[i] * m + k1v[j]] : (T)0;
           b3[i][j] = (T)0;
         }
-      for (int k3b = lo3; k3b < hi3; k3b += kEbKB) {
+      for (int k3b = lo3 + rank * kEbKB; k3b < hi3; k3b += cs * kEbKB) {
         const int nb = hi3 - k3b < kEbKB ? hi3 - k3b : kEbKB;
-        for (int kb = 0; kb < nb; ++kb) {
+        for (int kb = 0; kb < nb; ++kb, ++step) {
           const int k3 = k3b + kb;
           const T a3 = a0[k3];
+          const int buf = step & 1;
           if constexpr (TAB) {  // the next plane's values on their way, this plane's in place
-            if (k3 + 1 < m) {
-              stage(k3 + 1);
+            const int nk = next_plane(k3);
+            if (nk >= 0) {
+              stage(nk, buf ^ 1);
               eb_cp_wait<1>();
             } else {
               eb_cp_wait<0>();
@@ -221,7 +247,7 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
               // 1/D: the class table, or lam + sum_d (4/h_d^2) Lam[k_d] summed in that order and inverted
               T rinv;
               if constexpr (TAB)
-                rinv = Rs[(size_t)((k3 & 1) * NI * NJ + i * NJ + j) * blockDim.x + tid];
+                rinv = Rs[(size_t)(buf * NI * NJ + i * NJ + j) * blockDim.x + tid];
               else
                 rinv = eb_inv(lam + sc.e[0] * lI[k1v[j]] + sc.e[1] * lI[k2v[i]] + sc.e[2] * lI[k3]);
               const T V = ok ? E * rinv : (T)0;
@@ -273,21 +299,38 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
         __syncthreads();
       }
       // faces 4 / 5 at (k2, k1): the even planes' sums wait in X_4 (read into registers at
-      // the start and owned by this thread), then both are combined
+      // the start and owned by this thread); with a second CTA its sums come through ws
+      if (cs > 1 && rank == 1) {
 #pragma unroll
-      for (int i = 0; i < NI; ++i)
+        for (int i = 0; i < NI; ++i)
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-          if (!(ok2[i] && ok1[j])) continue;
-          const int r = k2v[i] * m + k1v[j];
-          if (q3 == 0) {
-            X[4 * mm + r] = b3[i][j];
-          } else {
-            const T ev = X[4 * mm + r];
-            Ze[4 * mm + r] = al2 * (ev + b3[i][j]);
-            Ze[5 * mm + r] = al2 * (ev - b3[i][j]);
-          }
+          for (int j = 0; j < NJ; ++j) wsT[(size_t)(q3 * NI * NJ + i * NJ + j) * 512 + tid] = b3[i][j];
+      }
+      if (q3 == 0) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+          for (int j = 0; j < NJ; ++j)
+            if (ok2[i] && ok1[j]) X[4 * mm + k2v[i] * m + k1v[j]] = b3[i][j];
+      } else {
+        tm.sync();  // the second CTA's sums are in ws
+        if (rank == 0) {
+#pragma unroll
+          for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) {
+              if (!(ok2[i] && ok1[j])) continue;
+              const int r = k2v[i] * m + k1v[j];
+              T ev = X[4 * mm + r], od = b3[i][j];
+              if (cs > 1) {
+                ev = ev + wsT[(size_t)(0 * NI * NJ + i * NJ + j) * 512 + tid];
+                od = od + wsT[(size_t)(1 * NI * NJ + i * NJ + j) * 512 + tid];
+              }
+              Ze[4 * mm + r] = al2 * (ev + od);
+              Ze[5 * mm + r] = al2 * (ev - od);
+            }
         }
+      }
     }
   }
 }
@@ -302,29 +345,35 @@ LaunchCfg plan_schur_eb(const Geo& G, int nsm) {
   c.block = 512;
   c.smem = eb_smem_elems(m, ni, nj, true) * sizeof(T);  // the table-staging size covers both forms
   c.ok = m >= 1 && m < SEMMG_MAX_DEGREE && c.smem <= (size_t)kEbSmemMax;
-  // one CTA per SM: the kernel takes 70 to 122 registers a thread (FP32 to FP64 tiles)
-  c.grid = (int)(G.nelem < nsm ? G.nelem : nsm);
+  // one CTA per SM: the kernel takes 70 to 122 registers a thread (FP32 to FP64 tiles); two
+  // per element (a cluster) when halving the work units shortens the rounds per SM
+  const int64_t r1 = (G.nelem + nsm - 1) / nsm, r2 = (2 * G.nelem + nsm - 1) / nsm;
+  c.cluster = (nsm >= 2 && r2 < 2 * r1) ? 2 : 1;
+  const int64_t teams = nsm / c.cluster, nt = G.nelem < teams ? G.nelem : teams;
+  c.grid = (int)((nt < 1 ? 1 : nt) * c.cluster);
+  c.ws.gstride = (int64_t)2 * ni * nj * 512;  // per CTA: covers the team's slice
   if (c.grid < 1) c.grid = 1;
   return c;
 }
 
 template <typename T, bool TAB>
-void launch_schur_eb_tab(const Geo& G, const Tabs<T>& t, const T* Ut, T* Z, const LaunchCfg& c, cudaStream_t st) {
+void launch_schur_eb_tab(const Geo& G, const Tabs<T>& t, const T* Ut, T* Z, T* ws, const LaunchCfg& c,
+                         cudaStream_t st) {
   if (G.m <= 16)
-    k_schur_eb<T, 1, 1, TAB><<<c.grid, c.block, c.smem, st>>>(G, t, Ut, Z);
+    launch_clustered(k_schur_eb<T, 1, 1, TAB>, c, st, G, t, Ut, Z, ws, c.cluster);
   else if (G.m <= 32)
-    k_schur_eb<T, 2, 1, TAB><<<c.grid, c.block, c.smem, st>>>(G, t, Ut, Z);
+    launch_clustered(k_schur_eb<T, 2, 1, TAB>, c, st, G, t, Ut, Z, ws, c.cluster);
   else
-    k_schur_eb<T, 3, 2, TAB><<<c.grid, c.block, c.smem, st>>>(G, t, Ut, Z);
+    launch_clustered(k_schur_eb<T, 3, 2, TAB>, c, st, G, t, Ut, Z, ws, c.cluster);
 }
 
 template <typename T>
-void launch_schur_eb(const Geo& G, const Tabs<T>& t, const T* Ut, T* Z, const LaunchCfg& c, cudaStream_t st) {
+void launch_schur_eb(const Geo& G, const Tabs<T>& t, const T* Ut, T* Z, T* ws, const LaunchCfg& c, cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
   if (t.Relem)
-    launch_schur_eb_tab<T, true>(G, t, Ut, Z, c, st);
+    launch_schur_eb_tab<T, true>(G, t, Ut, Z, ws, c, st);
   else
-    launch_schur_eb_tab<T, false>(G, t, Ut, Z, c, st);
+    launch_schur_eb_tab<T, false>(G, t, Ut, Z, ws, c, st);
 }
 
 template <typename T, bool TAB>

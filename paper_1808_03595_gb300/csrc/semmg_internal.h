@@ -484,8 +484,8 @@ template <typename T> void launch_fs_recover(const Geo& G, const Tabs<T>& t, con
 // Element Schur term in the face eigenbasis with the eigenspace streamed plane by plane
 // (schur_eb.cuh): the float-float element kernel of the face-parallel levels.
 template <typename T> LaunchCfg plan_schur_eb(const Geo& G, int nsm);
-template <typename T> void launch_schur_eb(const Geo& G, const Tabs<T>& t, const T* Ut, T* Z, const LaunchCfg& c,
-                                           cudaStream_t st);
+template <typename T> void launch_schur_eb(const Geo& G, const Tabs<T>& t, const T* Ut, T* Z, T* ws,
+                                           const LaunchCfg& c, cudaStream_t st);
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm);
 // Arithmetic T: double (the float-float forms use launch_fs_condense / launch_fs_recover).
 // Gsave (optional): scaled interior eigen-coefficients D^{-1} S^T F_I per element, m^3 each
