@@ -19,7 +19,7 @@ namespace semmg {
 
 namespace {
 
-constexpr int kFaceThreads = 256;
+constexpr int kFaceThreads = 320;  // upper bound; face_threads picks the launch size
 
 // Ut = c_f Sh^T U_f Sh for nfb consecutive faces per block (face records in t.faces).
 // Shared memory: Sh[m^2], X[nfb m^2], Tt[nfb m^2], cf[nfb].
@@ -172,6 +172,19 @@ __global__ void __launch_bounds__(kFaceThreads) k_face_bwd(Geo G, Tabs<T> t, con
   }
 }
 
+// Threads of a face block: the grouped line transforms of its faces (m lines per face,
+// groups of 4 outputs) in as few rounds of at most kFaceThreads as they need, the
+// rounds filled evenly (m = 47: 564 work items, 2 rounds of 288 threads instead of 3 of
+// 256 with the last one a fifth full).
+inline int face_threads(int m, int nfb) {
+  const int ne = (m + 1) / 2, groups = (ne + 3) / 4 + (m - ne + 3) / 4;
+  const int items = nfb * m * groups;
+  const int rounds = (items + kFaceThreads - 1) / kFaceThreads;
+  const int per = (items + rounds - 1) / rounds;
+  const int t = (per + 31) / 32 * 32;
+  return t < 64 ? 64 : t;
+}
+
 // faces per block: about 1024 face nodes, at most 32 faces
 inline int face_nfb(int m) {
   const int n = 1024 / (m * m);
@@ -199,7 +212,8 @@ void face_fwd_pc(const Geo& G, const Tabs<T>& t, const T* u, T* Ut, cudaStream_t
   const int64_t nF = face_count(G);
   const int nfb = face_nfb(G.m);
   const int64_t blocks = (nF + nfb - 1) / nfb;
-  k_face_fwd<T, PC><<<(unsigned)blocks, kFaceThreads, face_fwd_smem<T>(G.m, nfb), st>>>(G, t, u, Ut, nfb, nF);
+  k_face_fwd<T, PC><<<(unsigned)blocks, face_threads(G.m, nfb), face_fwd_smem<T>(G.m, nfb), st>>>(G, t, u, Ut, nfb,
+                                                                                               nF);
 }
 
 template <typename T, typename TF, int PC>
@@ -209,8 +223,9 @@ void face_bwd_pc(const Geo& G, const Tabs<T>& t, const TF* F, const T* u, const 
   const int nfb = face_nfb(G.m);
   const int64_t fblocks = (nF + nfb - 1) / nfb;
   const int64_t eblocks = (G.size - G.oE1 + kEdgeSlots - 1) / kEdgeSlots;
-  k_face_bwd<T, TF, PC><<<(unsigned)fblocks, kFaceThreads, face_bwd_smem<T>(G.m, nfb), st>>>(G, t, F, u, Ut, Zh, out,
-                                                                                            mode, nfb, nF);
+  const int nt = face_threads(G.m, nfb);
+  k_face_bwd<T, TF, PC><<<(unsigned)fblocks, nt, face_bwd_smem<T>(G.m, nfb), st>>>(G, t, F, u, Ut, Zh, out, mode, nfb,
+                                                                                  nF);
   if (eblocks > 0) k_edge_assemble<T, TF><<<(unsigned)eblocks, 3 * kEdgeSlots, 0, st>>>(G, t, F, u, out, mode);
 }
 
