@@ -303,8 +303,11 @@ int semmg_solve(semmg_ctx* ctx, const double* f_nodal, double* u_nodal, double r
 int semmg_solve_dirichlet(semmg_ctx* ctx, const double* f_nodal, const double* g_nodal, double* u_nodal,
                           double rtol, semmg_info* info, void* stream);
 
-/* semmg_solve with HOST nodal arrays: copies f to the device, solves, copies u
- * back, and synchronises `stream` before returning. */
+/* semmg_solve with HOST nodal arrays: copies f to the device, solves, and
+ * synchronises `stream` before returning.  u goes back by a copy, or, when
+ * u_host is page-locked host memory (cudaHostAlloc / cudaHostRegister), is
+ * written by the unpack and recovery kernels through its device mapping (no
+ * copy after the solve). */
 int semmg_solve_host(semmg_ctx* ctx, const double* f_host, double* u_host, double rtol,
                      semmg_info* info, void* stream);
 

@@ -1593,10 +1593,20 @@ int semmg_solve_host(semmg_ctx* c, const double* f_host, double* u_host, double 
     c->unod = (double*)dalloc(c, nn * sizeof(double));
     if (!c->fnod || !c->unod) return fail(c, SEMMG_ERR_NOMEM, "solve_host: device buffers");
   }
+  // u: a page-locked (registered) host buffer is written by the unpack and recovery kernels
+  // through its device mapping, so the result needs no copy after the solve; any other host
+  // memory gets the copy
+  double* u_map = nullptr;
+  {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, u_host) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+      u_map = (double*)pa.devicePointer;
+    cudaGetLastError();  // an unregistered pointer is not an error here
+  }
   cudaMemcpyAsync(c->fnod, f_host, nn * sizeof(double), cudaMemcpyHostToDevice, st);
-  const int rc = semmg_solve(c, c->fnod, c->unod, rtol, info, stream);
+  const int rc = semmg_solve(c, c->fnod, u_map ? u_map : c->unod, rtol, info, stream);
   if (rc != SEMMG_OK && rc != SEMMG_ERR_NOT_CONVERGED && rc != SEMMG_ERR_NONFINITE) return rc;
-  cudaMemcpyAsync(u_host, c->unod, nn * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (!u_map) cudaMemcpyAsync(u_host, c->unod, nn * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return check_cuda(c, "solve_host");
   return rc;
 }

@@ -109,44 +109,6 @@ __device__ __forceinline__ void fold_lines(const Lines& L, int ax, const T* X, T
   }
 }
 
-// out[k] = scale * sum_i S[i][k] x[i], from folded x.
-template <typename T>
-__device__ __forceinline__ void tx_lines(const Lines& L, int ax, const T* __restrict__ S, const T* Y, T* Z, T scale) {
-  const int str = L.stride(ax), n = L.n;
-  for (int idx = threadIdx.x; idx < L.total; idx += blockDim.x) {
-    const int k = L.pos(idx, ax);
-    const T* y = Y + (idx - k * str);
-    T s = 0;
-    if (k < L.ne) {
-      for (int j = 0; j < L.ne; ++j) s += S[(L.h + j) * n + k] * y[j * str];
-    } else {
-      for (int q = L.ne; q < n; ++q) s += S[q * n + k] * y[q * str];
-    }
-    Z[idx] = scale * s;
-  }
-}
-
-// Transposed transform into folded form: position j < ne gets
-// E_j = sum_{k even} S[h+j][k] b[k], position q >= ne gets O_q = sum_{k odd} S[q][k] b[k].
-template <typename T>
-__device__ __forceinline__ void txT_lines(const Lines& L, int ax, const T* __restrict__ S, const T* B, T* Y) {
-  const int str = L.stride(ax), n = L.n;
-  for (int idx = threadIdx.x; idx < L.total; idx += blockDim.x) {
-    const int j = L.pos(idx, ax);
-    const T* b = B + (idx - j * str);
-    T s = 0;
-    if (j < L.ne) {
-      const T* sr = S + (L.h + j) * n;
-      for (int k = 0; k < L.ne; ++k) s += sr[k] * b[k * str];
-    } else {
-      const T* sr = S + j * n;
-      for (int k = L.ne; k < n; ++k) s += sr[k] * b[k * str];
-    }
-    Y[idx] = s;
-  }
-}
-
-
 // ---- grouped line transforms: each thread computes kG outputs of one line
 // that share the input loads (independent multiply-add chains).
 constexpr int kG = 4;

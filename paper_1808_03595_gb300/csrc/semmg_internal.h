@@ -260,7 +260,7 @@ SEMMG_HD int64_t elem_face_base(const Geo& G, int a1, int a2, int a3, int f) {
 
 // ---------------------------------------------------------------- tables
 // One face of the face groups (F1, F2, F3 in slot order) for the face-parallel
-// form of the operator (kernels_face.cu), built on the host at setup.  The face
+// form of the operator (face_kernel.cuh), built on the host at setup.  The face
 // has normal axis d and in-plane axes a (fast) and b (slow); Md is the
 // assembled normal mass on its plane, cd0 / cdL / cdR the normal stiffness
 // line sum (cd0 u + cdL u(plane below) + cdR u(plane above)).

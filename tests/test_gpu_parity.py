@@ -272,14 +272,20 @@ def test_solve_helmholtz_8x8x8(p):
         assert rel(u, ref) < 1e-8
 
 
-def test_solve_host_matches_device():
-    h, p, lam, f, p0 = workloads.config("helmholtz_8x8x8_p4")
-    with ctx_for(h, p, lam, p0=p0) as c:
+@pytest.mark.parametrize("p,precision", [(4, "fp64"), (16, "fp64"), (16, "mixed_ff_tc")])
+def test_solve_host_matches_device(p, precision):
+    # page-locked u is written through its device mapping, pageable u gets a copy: both as on the device
+    h, p, lam, f, p0 = workloads.config(f"helmholtz_8x8x8_p{p}")
+    with ctx_for(h, p, lam, p0=p0, precision=precision) as c:
         ud, info_d = c.solve(cuda(f))
         fh = torch.as_tensor(f).pin_memory()
         uh = torch.empty_like(fh).pin_memory()
         c.solve_host(fh, uh)
+        fp = torch.as_tensor(f).clone()
+        up = torch.full_like(fp, float("nan"))
+        c.solve_host(fp, up)
     assert np.array_equal(ud.cpu().numpy(), uh.numpy())
+    assert np.array_equal(ud.cpu().numpy(), up.numpy())
 
 
 def test_not_converged_and_nonfinite_status():
