@@ -376,7 +376,7 @@ __device__ __forceinline__ ff inv_d(const Tabs<ff>& t, const ElemScal<ff>& sc, c
 // FP32 (inside FP64 iterative refinement): approximate reciprocal, no table read
 __device__ __forceinline__ float inv_d(const Tabs<float>&, const ElemScal<float>& sc, const float* lI, float lam,
                                        int64_t, int k1, int k2, int k3, int64_t) {
-  return __fdividef(1.0f, lam + sc.e[0] * lI[k1] + sc.e[1] * lI[k2] + sc.e[2] * lI[k3]);
+  return rcp_approx(lam + sc.e[0] * lI[k1] + sc.e[1] * lI[k2] + sc.e[2] * lI[k3]);
 }
 
 template <typename T>

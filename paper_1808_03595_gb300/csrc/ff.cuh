@@ -116,6 +116,15 @@ struct Acc<ff> {
   }
 };
 
+// 1/d by the hardware's approximate reciprocal (PTX rcp.approx.ftz.f32, about one ulp),
+// for the FP32 eigenvalue sums D = lam + sum_d (4/h_d^2) Lam[k_d] > 0 of the FP32 kernels,
+// which lie in the normal range where no special case applies
+__device__ __forceinline__ float rcp_approx(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return r;
+}
+
 // 1 / d: the FP32 reciprocal refined by one Newton step in float-float,
 // y + y (1 - d y), which doubles its correct bits
 __device__ __forceinline__ ff ff_recip(ff d) {

@@ -99,7 +99,7 @@ __device__ __forceinline__ void eb_cp_wait() { asm volatile("cp.async.wait_group
 
 // 1/D at one point: the element class's table, or the sum of the scaled eigenvalues inverted
 __device__ __forceinline__ double eb_inv(double d) { return 1.0 / d; }
-__device__ __forceinline__ float eb_inv(float d) { return __fdividef(1.0f, d); }
+__device__ __forceinline__ float eb_inv(float d) { return rcp_approx(d); }
 __device__ __forceinline__ ff eb_inv(ff d) { return ff_recip(d); }
 
 // TAB: 1/D from the element class's table (t.Relem), else computed per point; a

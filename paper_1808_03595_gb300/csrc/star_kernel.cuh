@@ -41,7 +41,7 @@ namespace {
 // a / b: IEEE division in FP64, the hardware approximate quotient (about 2 ulp)
 // in FP32, where the smoother sits inside FP64 iterative refinement.
 __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
-__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float fast_div(float a, float b) { return a * rcp_approx(b); }
 
 // k3-planes of the eigenspace held at once.
 __host__ __device__ __forceinline__ int slab_thickness(int nS) { return star_slab_thickness(nS); }

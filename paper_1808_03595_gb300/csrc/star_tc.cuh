@@ -398,7 +398,7 @@ __device__ __forceinline__ void tc_eigen(float* X, int np, int ld, int nS, float
           float e = s1r[j] * p0[i];
           e += s2r[i] * p1r[j];
           e += s3k * p2r[i][j];
-          const float v = __fdividef(e, d12[i][j] + l3);
+          const float v = e * rcp_approx(d12[i][j] + l3);
           b1[i] += s1r[j] * v;
           b2[j] += s2r[i] * v;
           b3[i][j] += s3k * v;
