@@ -362,12 +362,12 @@ def run_semmg(args, world, rank, local, pg):
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier(pg)
-    tform, iters = {}, {"fp64": info64.iters}
+    tform, iters, infos = {}, {"fp64": info64.iters}, {"fp64": info64}
     for form in forms[1:]:
         torch.cuda.nvtx.range_push(f"{form}_timed")
         tform[form], inf = timed_solves(ctx[form], fd, ud, K, flush, stream)
         torch.cuda.nvtx.range_pop()
-        iters[form] = inf.iters
+        iters[form], infos[form] = inf.iters, inf
     # end to end through the host-buffer entry point (pinned host f in, u out)
     te2e = float("nan")
     if not args.no_e2e:
@@ -394,7 +394,8 @@ def run_semmg(args, world, rank, local, pg):
     e2e = world * unknowns * K / (te2e / 1e3) if te2e == te2e else None
     emit("forms", {"workload": HEADLINE, "unknowns": unknowns,
                    "forms": {k: {"value": r4(v), "speedup_vs_fp64": r4(v / value), "iterations": iters[k],
-                                 "precision": FORMS[k][0], "solver": FORMS[k][1]}
+                                 "reduction": r4(infos[k].res_final / infos[k].res0), "rho": r4(infos[k].rho),
+                                 "us_per_unknown": r4(1e6 / v), "precision": FORMS[k][0], "solver": FORMS[k][1]}
                              for k, v in [("fp64", value)] + list(vforms.items())}}, details)
     peaks = {"fp64": (fp64_peak, fp64_src), "hbm": measured_hbm()}
     roof = roofline(kst, peaks["fp64"], peaks, npass)
