@@ -137,18 +137,24 @@ __device__ __forceinline__ int line_groups(const Lines& L) {
   return (L.ne + kG - 1) / kG + (L.n - L.ne + kG - 1) / kG;
 }
 
-// Outputs [k0, k1) of group g and the folded input range [j0, j1); even: inputs use row h + j.
-__device__ __forceinline__ void line_block(const Lines& L, int g, int* k0, int* k1, int* j0, int* j1, int* even) {
-  const int ge = (L.ne + kG - 1) / kG;
+// Outputs k0, k0 + ks, k0 + 2 ks, ... below k1 of group g, and the folded input range
+// [j0, j1); even: inputs use row h + j.  The groups of a half interleave (stride ks = the
+// half's number of groups), so the neighbouring groups of a warp read neighbouring entries
+// of S at each step: no shared-memory bank conflicts between them.
+__device__ __forceinline__ void line_block(const Lines& L, int g, int* k0, int* ks, int* k1, int* j0, int* j1,
+                                           int* even) {
+  const int ge = (L.ne + kG - 1) / kG, go = (L.n - L.ne + kG - 1) / kG;
   if (g < ge) {
-    *k0 = g * kG;
-    *k1 = min(*k0 + kG, L.ne);
+    *k0 = g;
+    *ks = ge;
+    *k1 = L.ne;
     *j0 = 0;
     *j1 = L.ne;
     *even = 1;
   } else {
-    *k0 = L.ne + (g - ge) * kG;
-    *k1 = min(*k0 + kG, L.n);
+    *k0 = L.ne + (g - ge);
+    *ks = go;
+    *k1 = L.n;
     *j0 = L.ne;
     *j1 = L.n;
     *even = 0;
@@ -163,9 +169,9 @@ __device__ __forceinline__ void tx_lines_g(const Lines& L, int ax, const T* __re
   const int items = nlines(L) * G;
   for (int it = tm.id; it < items; it += tm.n) {
     const int l = it / G, g = it - l * G;
-    int base, str, i2, k0, k1, j0, j1, even;
+    int base, str, i2, k0, ks, k1, j0, j1, even;
     line_of(L, ax, l, &base, &str, &i2);
-    line_block(L, g, &k0, &k1, &j0, &j1, &even);
+    line_block(L, g, &k0, &ks, &k1, &j0, &j1, &even);
     Acc<T> a[kG];
 #pragma unroll
     for (int q = 0; q < kG; ++q) a[q] = Acc<T>::zero();
@@ -174,12 +180,12 @@ __device__ __forceinline__ void tx_lines_g(const Lines& L, int ax, const T* __re
       const T* sr = S + (even ? L.h + j : j) * n + k0;
 #pragma unroll
       for (int q = 0; q < kG; ++q)
-        if (k0 + q < k1) a[q].add(sr[q], yv);
+        if (k0 + q * ks < k1) a[q].add(sr[q * ks], yv);
     }
     const T s = sc2 ? sc2[i2] : scale;
 #pragma unroll
     for (int q = 0; q < kG; ++q)
-      if (k0 + q < k1) Z[base + (k0 + q) * str] = s * a[q].value();
+      if (k0 + q * ks < k1) Z[base + (k0 + q * ks) * str] = s * a[q].value();
   }
 }
 
@@ -191,15 +197,15 @@ __device__ __forceinline__ void txT_lines_g(const Lines& L, int ax, const T* __r
   const int items = nlines(L) * G;
   for (int it = tm.id; it < items; it += tm.n) {
     const int l = it / G, g = it - l * G;
-    int base, str, i2, k0, k1, j0, j1, even;
+    int base, str, i2, k0, ks, k1, j0, j1, even;
     line_of(L, ax, l, &base, &str, &i2);
-    line_block(L, g, &k0, &k1, &j0, &j1, &even);
+    line_block(L, g, &k0, &ks, &k1, &j0, &j1, &even);
     Acc<T> a[kG];
     const T* sr[kG];
 #pragma unroll
     for (int q = 0; q < kG; ++q) {
       a[q] = Acc<T>::zero();
-      const int jo = min(k0 + q, k1 - 1);
+      const int jo = min(k0 + q * ks, k1 - 1);
       sr[q] = S + (even ? L.h + jo : jo) * n;
     }
     for (int k = j0; k < j1; ++k) {
@@ -209,7 +215,7 @@ __device__ __forceinline__ void txT_lines_g(const Lines& L, int ax, const T* __r
     }
 #pragma unroll
     for (int q = 0; q < kG; ++q)
-      if (k0 + q < k1) Y[base + (k0 + q) * str] = a[q].value();
+      if (k0 + q * ks < k1) Y[base + (k0 + q * ks) * str] = a[q].value();
   }
 }
 
