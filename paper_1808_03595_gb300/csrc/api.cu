@@ -919,15 +919,20 @@ void correction(semmg_ctx* c, double* u, const double* r, cudaStream_t st) {
 // eigen-coefficients of F_I are kept in Gs for recover_impl(..., use_saved).
 // The solve of a float-float form condenses and recovers in float-float where the finest
 // level has its tables (the face-parallel levels); the public entry points stay FP64.
-bool ff_fdm(const semmg_ctx* c) { return residff(c) && c->dl[c->L()].tff.Sh != nullptr && c->fsff.ok; }
+bool ff_fdm(const semmg_ctx* c) { return residff(c) && c->dl[c->L()].tff.Sh != nullptr; }
+// the shared-memory-staged form pays where the stored form's m^3 work arrays live in global memory
+bool ff_staged(const semmg_ctx* c) { return c->fsff.ok && !c->fdm.ws.in_smem[3]; }
 
 void condense_impl(semmg_ctx* c, const double* f, double* fh, bool save, cudaStream_t st, bool ffok = false) {
   const int L = c->L();
   const Geo& G = c->geo[L];
   const double nn = (double)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
   Tic t(c, SEMMG_K_CONDENSE, st);
-  if (ffok && ff_fdm(c))
+  if (ffok && ff_fdm(c) && ff_staged(c))
     launch_fs_condense<ff>(G, c->dl[L].tff, f, (double*)c->Zs, save ? (ff*)c->Gs : nullptr, (ff*)c->wss, c->fsff, st);
+  else if (ffok && ff_fdm(c))
+    launch_elem_condense<ff>(G, c->dl[L].tff, f, (double*)c->Zs, save ? (ff*)c->Gs : nullptr, (ff*)c->wss, c->fdm,
+                             st);
   else
     launch_elem_condense<double>(G, c->dl[L].td, f, (double*)c->Zs, save ? c->Gs : nullptr, (double*)c->wss,
                                  c->fdm, st);
@@ -944,8 +949,10 @@ void recover_impl(semmg_ctx* c, const double* f, const double* uh, double* u, bo
   const double nn = (double)(G.n1 * G.p + 1) * (G.n2 * G.p + 1) * (G.n3 * G.p + 1);
   Tic t(c, SEMMG_K_RECOVER, st);
   launch_unpack(G, uh, u, st);
-  if (ffok && use_saved && ff_fdm(c))
+  if (ffok && use_saved && ff_fdm(c) && ff_staged(c))
     launch_fs_recover<ff>(G, c->dl[L].tff, (const ff*)c->Gs, uh, u, (ff*)c->wss, c->fsff, st);
+  else if (ffok && use_saved && ff_fdm(c))
+    launch_elem_recover<ff>(G, c->dl[L].tff, f, (const ff*)c->Gs, uh, u, (ff*)c->wss, c->fdm, st);
   else
     launch_elem_recover<double>(G, c->dl[L].td, f, use_saved ? c->Gs : nullptr, uh, u, (double*)c->wss, c->fdm, st);
   t.toc(G.m > 0 ? fdm_flops(G) : 0.0, 8.0 * (2 * nn + G.size), 2);
@@ -1303,7 +1310,7 @@ int semmg_setup(const semmg_mesh* mesh, int p, double lambda, const semmg_opts* 
     }
   }
   c->fdm = plan_elem_fdm(c->geo[nl - 1], c->nsm);
-  if (residff(c.get()) && face_form(c->geo[nl - 1])) {
+  if (residff(c.get()) && face_form(c->geo[nl - 1]) && !c->fdm.ws.in_smem[3]) {
     c->fsff = plan_fs<ff>(c->geo[nl - 1], c->nsm);
     if (c->fsff.ok) wsb = std::max(wsb, c->fsff.ws_elems() * sizeof(ff));
   }

@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(kFaceThreads) k_face_bwd(Geo G, Tabs<T> t, con
 // rounds filled evenly (m = 47: 564 work items, 2 rounds of 288 threads instead of 3 of
 // 256 with the last one a fifth full).
 inline int face_threads(int m, int nfb) {
+  if (m < 32) return 256;  // smaller faces fill 256 threads in one or two rounds already
   const int ne = (m + 1) / 2, groups = (ne + 3) / 4 + (m - ne + 3) / 4;
   const int items = nfb * m * groups;
   const int rounds = (items + kFaceThreads - 1) / kFaceThreads;

@@ -1,6 +1,7 @@
 // FP64 instantiation of the element kernels: condensed operator (FP64 form and
 // the outer residual of the mixed form), right-hand-side condensation and
-// interior recovery.
+// interior recovery (the latter two also in float-float, for elements whose work
+// arrays fit in shared memory).
 #include "elem_kernel.cuh"
 
 namespace semmg {
@@ -76,6 +77,10 @@ template void launch_elem_condense<double>(const Geo&, const Tabs<double>&, cons
                                            const LaunchCfg&, cudaStream_t);
 template void launch_elem_recover<double>(const Geo&, const Tabs<double>&, const double*, const double*,
                                           const double*, double*, double*, const LaunchCfg&, cudaStream_t);
+template void launch_elem_condense<ff>(const Geo&, const Tabs<ff>&, const double*, double*, ff*, ff*,
+                                       const LaunchCfg&, cudaStream_t);
+template void launch_elem_recover<ff>(const Geo&, const Tabs<ff>&, const double*, const ff*, const double*, double*,
+                                      ff*, const LaunchCfg&, cudaStream_t);
 
 template LaunchCfg plan_elem_schur<double>(const Geo&, int, size_t, int, int);
 template void launch_elem_schur<double>(const Geo&, const Tabs<double>&, const double*, double*, double*,
@@ -84,7 +89,7 @@ template void launch_elem_schur<double>(const Geo&, const Tabs<double>&, const d
 int set_elem_smem_limits_f32();
 int set_elem_smem_limits() {
   int bad = schur_attrs<double>() | set_elem_smem_limits_f32();
-  bad |= fdm_attrs<double>();
+  bad |= fdm_attrs<double>() | fdm_attrs<ff>();
   return bad;
 }
 

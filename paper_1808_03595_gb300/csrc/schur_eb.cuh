@@ -36,7 +36,9 @@ namespace semmg {
 namespace {
 
 constexpr int kEbWarps = 16;  // 512 threads
-constexpr int kEbKB = 2;      // planes per shared-memory round of the k2 sums
+// planes per shared-memory round of the k2 sums: 4, or 2 with two column slots (whose wider
+// partial-sum rows would not leave room for the table staging)
+__host__ __device__ constexpr int eb_kb(int nj) { return nj > 1 ? 2 : 4; }
 constexpr int kEbSmemMax = 224 * 1024;
 
 __device__ __forceinline__ float eb_shx(float v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
@@ -83,7 +85,7 @@ __host__ __device__ constexpr int eb_pow2(int n) { return n <= 1 ? 1 : (n <= 2 ?
 // 1/D table the staging of each thread's table values for two planes
 // (2 x NI*NJ slots x 512 threads, thread index fastest).
 __host__ __device__ constexpr size_t eb_smem_elems(int m, int ni, int nj, bool tab) {
-  return (size_t)6 * m * m + (size_t)kEbWarps * kEbKB * 2 * nj * 32 + 2 * (size_t)m +
+  return (size_t)6 * m * m + (size_t)kEbWarps * eb_kb(nj) * 2 * nj * 32 + 2 * (size_t)m +
          (tab ? (size_t)2 * ni * nj * 512 : 0);
 }
 
@@ -108,6 +110,7 @@ template <typename T, int NI, int NJ, bool TAB>
 __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* __restrict__ Ut, T* __restrict__ Z,
                                                      T* ws, int cs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kEbKB = eb_kb(NJ);
   const int m = G.m, mm = m * m, ne = (m + 1) / 2;
   const int64_t n3 = (int64_t)mm * m;
   T* X = reinterpret_cast<T*>(smem_raw);
@@ -347,8 +350,9 @@ LaunchCfg plan_schur_eb(const Geo& G, int nsm) {
   c.ok = m >= 1 && m < SEMMG_MAX_DEGREE && c.smem <= (size_t)kEbSmemMax;
   // one CTA per SM: the kernel takes 70 to 122 registers a thread (FP32 to FP64 tiles); two
   // per element (a cluster) when halving the work units shortens the rounds per SM
+  // (elements with m >= 32 only: on smaller ones the split's exchange costs more than it saves)
   const int64_t r1 = (G.nelem + nsm - 1) / nsm, r2 = (2 * G.nelem + nsm - 1) / nsm;
-  c.cluster = (nsm >= 2 && r2 < 2 * r1) ? 2 : 1;
+  c.cluster = (m >= 32 && nsm >= 2 && r2 < 2 * r1) ? 2 : 1;
   const int64_t teams = nsm / c.cluster, nt = G.nelem < teams ? G.nelem : teams;
   c.grid = (int)((nt < 1 ? 1 : nt) * c.cluster);
   c.ws.gstride = (int64_t)2 * ni * nj * 512;  // per CTA: covers the team's slice

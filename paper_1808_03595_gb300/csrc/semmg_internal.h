@@ -487,7 +487,8 @@ template <typename T> LaunchCfg plan_schur_eb(const Geo& G, int nsm);
 template <typename T> void launch_schur_eb(const Geo& G, const Tabs<T>& t, const T* Ut, T* Z, T* ws,
                                            const LaunchCfg& c, cudaStream_t st);
 LaunchCfg plan_elem_fdm(const Geo& G, int nsm);
-// Arithmetic T: double (the float-float forms use launch_fs_condense / launch_fs_recover).
+// Arithmetic T: double, or ff (float-float) where the work arrays fit in shared memory (larger
+// elements take launch_fs_condense / launch_fs_recover).
 // Gsave (optional): scaled interior eigen-coefficients D^{-1} S^T F_I per element, m^3 each
 template <typename T>
 void launch_elem_condense(const Geo& G, const Tabs<T>& t, const double* f_nodal, double* Z, T* Gsave, T* ws,
