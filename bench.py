@@ -58,6 +58,7 @@ DETAIL_FORMS = ("kmg_fp64", "kmg_mixed", "kmg_mixed_tc", "kmg_mixed_ff_tc", "mix
                 "mixed_ff")
 TC_FORMS = ("mixed_tc", "mixed_bf16", "mixed_fp32_tc", "mixed_ff_tc")  # star on the tensor cores at n_S >= 31
 SWEEP_FORMS = ("fp64", "mixed", "mixed_tc", "mixed_ff_tc")  # forms of the 8^3 degree sweep
+FF_PRECISIONS = ("mixed_ff", "mixed_ff_tc")  # level residuals, condensation and recovery in float-float
 BATCH_MIXED = "mixed_ff_tc"  # precision of the batch's mixed graphs
 FP64_NOMINAL_TFLOPS = 1.25  # 2 FP64 FMA / clock / SM x 152 SMs x 2.07 GHz: fallback when the probe fails
 # DRAM bytes (read + write) per k_star<double> launch of the timed FP64 region of the headline
@@ -253,12 +254,14 @@ def timed_solves(ctx, f, u, steps, flush, stream, host=None):
     return ms, info
 
 
-def roofline(kst, star_peak, peaks, steps, tc=False):
+def roofline(kst, star_peak, peaks, steps, tc=False, class_peaks=None):
     """Roofline of the dominant kernel class of a timing pass (kst: class -> totals over `steps` solves).
 
     star_peak: (TFLOP/s, source) of the precision the form's star kernel runs in; peaks: "fp64" and
     "hbm" (value, source).  tc: the form runs its star on the tensor cores at the upper levels, where
-    the library keeps no executed-operation count."""
+    the library keeps no executed-operation count.  class_peaks: class -> ((TFLOP/s, source) or None,
+    note) for the classes whose kernels do not run on the FP64 pipe in this form (None: kernels of
+    several precisions in one class, no single peak)."""
     dom = max(kst, key=lambda k: kst[k]["ms"])
     d = kst[dom]
     total_ms = sum(v["ms"] for v in kst.values())
@@ -274,15 +277,25 @@ def roofline(kst, star_peak, peaks, steps, tc=False):
                     "paper_count_tflops": d["flops"] / sec / 1e12, "hbm_gbs": d["bytes"] / sec / 1e9})
     elif d["flops"] > 0:
         # arithmetic-bound class without an executed-operation count: the paper count only
-        pk = star_peak if dom == "star" else peaks["fp64"]
-        out.update({"bound": "alu", "achieved": None, "peak": pk[0], "unit": "TFLOP/s", "frac": None,
-                    "peak_source": pk[1], "paper_count_tflops": d["flops"] / sec / 1e12,
-                    "note": "no executed-operation count for this kernel class"})
+        pk, note = star_peak if dom == "star" else peaks["fp64"], "no executed-operation count for this kernel class"
+        if class_peaks and dom in class_peaks:
+            pk, why = class_peaks[dom]
+            note = f"{note}; {why}"
+        out.update({"bound": "alu", "achieved": None, "peak": pk[0] if pk else None, "unit": "TFLOP/s",
+                    "frac": None, "peak_source": pk[1] if pk else None,
+                    "paper_count_tflops": d["flops"] / sec / 1e12, "note": note})
     else:
         achieved = d["bytes"] / sec / 1e9
         out.update({"bound": "hbm", "achieved": achieved, "unit": "GB/s", "peak": peaks["hbm"][0],
                     "frac": achieved / peaks["hbm"][0] if peaks["hbm"][0] else None, "peak_source": peaks["hbm"][1]})
     return out
+
+
+def ff_class_peaks(fp32):
+    """Kernel classes of the float-float forms that leave the FP64 pipe (see `roofline`)."""
+    ff = (fp32, "float-float arithmetic on the FP32 pipes")
+    return {"elem_schur": (None, "FP64 outer residual and float-float level residuals in one class"),
+            "condense": ff, "recover": ff}
 
 
 def measured_hbm():
@@ -403,9 +416,10 @@ def run_semmg(args, world, rank, local, pg):
     roof["traffic"] = (STAR_TRAFFIC["bytes_per_launch"] if roof["kernel"] == "star" and h_now is not None
                        and h_now == STAR_TRAFFIC["source"] else None)
     emit("roofline", {k: (r4(v) if isinstance(v, float) else v) for k, v in roof.items()}, details)
+    fp32 = (fp32_peak, "measured (FP32 FMA chains, this run)")
     for form in MIXED_FORMS:
-        rm = roofline(kst_m[form], (fp32_peak, "measured (FP32 FMA chains, this run)"), peaks, npass,
-                      tc=form in TC_FORMS)
+        rm = roofline(kst_m[form], fp32, peaks, npass, tc=form in TC_FORMS,
+                      class_peaks=ff_class_peaks(fp32) if FORMS[form][0] in FF_PRECISIONS else None)
         emit(f"roofline_{form}", {k: (r4(v) if isinstance(v, float) else v) for k, v in rm.items()}, details)
     best = max(MIXED_FORMS, key=lambda k: vforms[k])
     for c in ctx.values():

@@ -67,6 +67,18 @@ def test_roofline_without_executed_count_reports_no_fraction():
     assert r["kernel"] == "elem_schur" and r["bound"] == "alu" and r["peak"] == 1.25 and r["frac"] is None
 
 
+def test_roofline_of_the_float_float_classes():
+    # float-float forms: the element class mixes the FP64 outer residual with float-float level
+    # residuals (no single peak); condensation runs on the FP32 pipes
+    fp32 = (78.0, "fp32 probe")
+    kst = _kst(elem_schur=dict(ms=10.0, launches=3, flops=1e10), star=dict(ms=1.0, launches=1, xflops=1e6))
+    r = bench.roofline(kst, fp32, PEAKS, steps=1, class_peaks=bench.ff_class_peaks(fp32))
+    assert r["peak"] is None and r["frac"] is None and "outer residual" in r["note"]
+    kst = _kst(condense=dict(ms=10.0, launches=1, flops=1e10), star=dict(ms=1.0, launches=1, xflops=1e6))
+    r = bench.roofline(kst, fp32, PEAKS, steps=1, class_peaks=bench.ff_class_peaks(fp32))
+    assert r["kernel"] == "condense" and r["peak"] == 78.0 and "FP32 pipes" in r["note"]
+
+
 def test_roofline_data_movement_class_against_measured_hbm():
     kst = _kst(star_gather=dict(ms=2.0, launches=4, bytes=6.7924e9))
     r = bench.roofline(kst, (1.25, "fp64 probe"), PEAKS, steps=1)
