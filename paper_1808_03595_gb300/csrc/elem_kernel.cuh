@@ -572,11 +572,16 @@ __device__ FdmSmem<T> fdm_layout(int m, unsigned char* smem, T* ws, const WsPlan
   return s;
 }
 
-__device__ __forceinline__ int64_t interior_node(const Geo& G, int a1, int a2, int a3, int idx) {
-  const int m = G.m, p = G.p;
-  const int i1 = idx % m, i2 = (idx / m) % m, i3 = idx / (m * m);
+// nodal index of interior point (i1, i2, i3) of element (a1, a2, a3)
+__device__ __forceinline__ int64_t interior_node3(const Geo& G, int a1, int a2, int a3, int i1, int i2, int i3) {
+  const int p = G.p;
   const int64_t N1 = (int64_t)G.n1 * p + 1, N2 = (int64_t)G.n2 * p + 1;
   return ((int64_t)(a3 * p + i3 + 1) * N2 + (a2 * p + i2 + 1)) * N1 + (a1 * p + i1 + 1);
+}
+
+__device__ __forceinline__ int64_t interior_node(const Geo& G, int a1, int a2, int a3, int idx) {
+  const int m = G.m;
+  return interior_node3(G, a1, a2, a3, idx % m, (idx / m) % m, idx / (m * m));
 }
 
 // Z[e][f] = (H_BI H_II^{-1} F_I) on the faces, F_I = (M f)_I element-local.
@@ -734,6 +739,7 @@ void launch_elem_schur_nb(const Geo& G, const Tabs<T>& t, const T* u, T* Z, T* w
     case 8: launch_clustered(k_elem_schur<T, 8, NB>, c, st, G, t, u, Z, ws, c.ws, pre, c.cluster); break;
     case 16: launch_clustered(k_elem_schur<T, 16, NB>, c, st, G, t, u, Z, ws, c.ws, pre, c.cluster); break;
     case 32: launch_clustered(k_elem_schur<T, 32, NB>, c, st, G, t, u, Z, ws, c.ws, pre, c.cluster); break;
+    case 48: launch_clustered(k_elem_schur<T, 48, NB>, c, st, G, t, u, Z, ws, c.ws, pre, c.cluster); break;
     default: launch_clustered(k_elem_schur<T, 0, NB>, c, st, G, t, u, Z, ws, c.ws, pre, c.cluster); break;
   }
 }
@@ -756,6 +762,7 @@ static int schur_attrs_nb() {
   bad |= cudaFuncSetAttribute(k_elem_schur<T, 8, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_schur<T, 16, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_schur<T, 32, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_schur<T, 48, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return bad;
 }
 

@@ -242,7 +242,7 @@ int face_attrs_pc() {
 template <typename T, typename TF>
 int face_attrs() {
   return face_attrs_pc<T, TF, 0>() | face_attrs_pc<T, TF, 8>() | face_attrs_pc<T, TF, 16>() |
-         face_attrs_pc<T, TF, 32>();
+         face_attrs_pc<T, TF, 32>() | face_attrs_pc<T, TF, 48>();
 }
 
 }  // namespace
@@ -254,6 +254,7 @@ void launch_face_fwd(const Geo& G, const Tabs<T>& t, const T* u, T* Ut, cudaStre
     case 8: face_fwd_pc<T, 8>(G, t, u, Ut, st); break;
     case 16: face_fwd_pc<T, 16>(G, t, u, Ut, st); break;
     case 32: face_fwd_pc<T, 32>(G, t, u, Ut, st); break;
+    case 48: face_fwd_pc<T, 48>(G, t, u, Ut, st); break;
     default: face_fwd_pc<T, 0>(G, t, u, Ut, st); break;
   }
 }
@@ -265,6 +266,7 @@ void launch_face_bwd_assemble(const Geo& G, const Tabs<T>& t, const TF* F, const
     case 8: face_bwd_pc<T, TF, 8>(G, t, F, u, Ut, Zh, out, mode, st); break;
     case 16: face_bwd_pc<T, TF, 16>(G, t, F, u, Ut, Zh, out, mode, st); break;
     case 32: face_bwd_pc<T, TF, 32>(G, t, F, u, Ut, Zh, out, mode, st); break;
+    case 48: face_bwd_pc<T, TF, 48>(G, t, F, u, Ut, Zh, out, mode, st); break;
     default: face_bwd_pc<T, TF, 0>(G, t, F, u, Ut, Zh, out, mode, st); break;
   }
 }

@@ -86,12 +86,13 @@ __device__ __forceinline__ void fs_load_tables(int m, const Tabs<T>& t, const Fs
 
 // Z[e][f] = (H_BI H_II^{-1} F_I) on the faces, F_I = (M f)_I, with the scaled
 // interior eigen-coefficients of every element saved in Gsave when given (as
-// k_elem_condense).
-template <typename T>
+// k_elem_condense).  PC > 0 compiles the kernel for degree PC (constant
+// extents, the same arithmetic in the same order); PC = 0 reads it from G.
+template <typename T, int PC>
 __global__ void __launch_bounds__(512, 1) k_fs_condense(Geo G, Tabs<T> t, const double* __restrict__ f,
                                                       double* __restrict__ Z, T* __restrict__ Gsave, T* ws, int cs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = G.m, mm = m * m, ne = (m + 1) / 2;
+  const int m = PC ? PC - 1 : G.m, mm = m * m, ne = (m + 1) / 2;
   const int64_t mmm = (int64_t)mm * m;
   const FsShape sh = fs_shape(m, sizeof(T));
   const Team tm = team_of(cs);
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(512, 1) k_fs_condense(Geo G, Tabs<T> t, const 
       for (int idx = threadIdx.x; idx < np * mm; idx += blockDim.x) {
         const int i1 = idx % m, i2 = (idx / m) % m, i3 = p0 + idx / mm;
         Pb[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] *
-                  (T)f[interior_node(G, a1, a2, a3, i3 * mm + i2 * m + i1)];
+                  (T)f[interior_node3(G, a1, a2, a3, i1, i2, i3)];
       }
       __syncthreads();
       fold_lines(P, 0, Pb, Qb);
@@ -222,12 +223,13 @@ __global__ void __launch_bounds__(512, 1) k_fs_condense(Geo G, Tabs<T> t, const 
 
 // u_I = H_II^{-1} (F_I - H_IB uhat) into the nodal array, from the coefficients
 // Gin that k_fs_condense saved for the same f (as k_elem_recover with Gin).
-template <typename T>
+// PC as for k_fs_condense.
+template <typename T, int PC>
 __global__ void __launch_bounds__(512, 1) k_fs_recover(Geo G, Tabs<T> t, const T* __restrict__ Gin,
                                                      const double* __restrict__ uh, double* __restrict__ un, T* ws,
                                                      int cs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = G.m, mm = m * m, ne = (m + 1) / 2;
+  const int m = PC ? PC - 1 : G.m, mm = m * m, ne = (m + 1) / 2;
   const int64_t mmm = (int64_t)mm * m;
   const FsShape sh = fs_shape(m, sizeof(T));
   const Team tm = team_of(cs);
@@ -290,8 +292,10 @@ __global__ void __launch_bounds__(512, 1) k_fs_recover(Geo G, Tabs<T> t, const T
       __syncthreads();
       txT_lines_g(P, 0, s.Sr, Pb, Qb);
       __syncthreads();
-      for (int idx = threadIdx.x; idx < np * mm; idx += blockDim.x)
-        un[interior_node(G, a1, a2, a3, p0 * mm + idx)] = (double)(sig * unfold_at(P, 0, Qb, idx));
+      for (int idx = threadIdx.x; idx < np * mm; idx += blockDim.x) {
+        const int i1 = idx % m, i2 = (idx / m) % m, i3 = p0 + idx / mm;
+        un[interior_node3(G, a1, a2, a3, i1, i2, i3)] = (double)(sig * unfold_at(P, 0, Qb, idx));
+      }
     }
   }
 }
@@ -321,21 +325,34 @@ template <typename T>
 void launch_fs_condense(const Geo& G, const Tabs<T>& t, const double* f, double* Z, T* Gsave, T* ws,
                         const LaunchCfg& c, cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
-  launch_clustered(k_fs_condense<T>, c, st, G, t, f, Z, Gsave, ws, c.cluster);
+  switch (G.p) {
+    case 32: launch_clustered(k_fs_condense<T, 32>, c, st, G, t, f, Z, Gsave, ws, c.cluster); break;
+    case 48: launch_clustered(k_fs_condense<T, 48>, c, st, G, t, f, Z, Gsave, ws, c.cluster); break;
+    default: launch_clustered(k_fs_condense<T, 0>, c, st, G, t, f, Z, Gsave, ws, c.cluster); break;
+  }
 }
 
 template <typename T>
 void launch_fs_recover(const Geo& G, const Tabs<T>& t, const T* Gin, const double* uh, double* un, T* ws,
                        const LaunchCfg& c, cudaStream_t st) {
   if (G.m == 0 || G.nelem == 0 || !c.ok) return;
-  launch_clustered(k_fs_recover<T>, c, st, G, t, Gin, uh, un, ws, c.cluster);
+  switch (G.p) {
+    case 32: launch_clustered(k_fs_recover<T, 32>, c, st, G, t, Gin, uh, un, ws, c.cluster); break;
+    case 48: launch_clustered(k_fs_recover<T, 48>, c, st, G, t, Gin, uh, un, ws, c.cluster); break;
+    default: launch_clustered(k_fs_recover<T, 0>, c, st, G, t, Gin, uh, un, ws, c.cluster); break;
+  }
+}
+
+template <typename T, int PC>
+int fs_attrs_pc() {
+  int bad = cudaFuncSetAttribute(k_fs_condense<T, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFsSmemMax);
+  bad |= cudaFuncSetAttribute(k_fs_recover<T, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFsSmemMax);
+  return bad;
 }
 
 template <typename T>
 int fs_attrs() {
-  int bad = cudaFuncSetAttribute(k_fs_condense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFsSmemMax);
-  bad |= cudaFuncSetAttribute(k_fs_recover<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFsSmemMax);
-  return bad;
+  return fs_attrs_pc<T, 0>() | fs_attrs_pc<T, 32>() | fs_attrs_pc<T, 48>();
 }
 
 }  // namespace semmg

@@ -47,6 +47,7 @@ void launch_elem_condense(const Geo& G, const Tabs<T>& t, const double* f, doubl
   switch (G.p) {
     case 16: launch_clustered(k_elem_condense<T, 16>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
     case 32: launch_clustered(k_elem_condense<T, 32>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
+    case 48: launch_clustered(k_elem_condense<T, 48>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
     default: launch_clustered(k_elem_condense<T, 0>, c, st, G, t, f, Z, Gsave, ws, c.ws, c.cluster); break;
   }
 }
@@ -58,6 +59,7 @@ void launch_elem_recover(const Geo& G, const Tabs<T>& t, const double* f, const 
   switch (G.p) {
     case 16: launch_clustered(k_elem_recover<T, 16>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
     case 32: launch_clustered(k_elem_recover<T, 32>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
+    case 48: launch_clustered(k_elem_recover<T, 48>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
     default: launch_clustered(k_elem_recover<T, 0>, c, st, G, t, f, Gin, uh, un, ws, c.ws, c.cluster); break;
   }
 }
@@ -67,9 +69,11 @@ int fdm_attrs() {
   int bad = cudaFuncSetAttribute(k_elem_condense<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_condense<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_condense<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_condense<T, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_recover<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_recover<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   bad |= cudaFuncSetAttribute(k_elem_recover<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  bad |= cudaFuncSetAttribute(k_elem_recover<T, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return bad;
 }
 

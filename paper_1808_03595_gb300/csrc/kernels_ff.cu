@@ -35,7 +35,7 @@ template void launch_face_bwd_assemble<ff, float>(const Geo&, const Tabs<ff>&, c
 
 int set_ff_smem_limits() {
   return schur_eb_attrs<ff>() | fs_attrs<ff>() | face_ff_attrs<0>() | face_ff_attrs<8>() | face_ff_attrs<16>() |
-         face_ff_attrs<32>();
+         face_ff_attrs<32>() | face_ff_attrs<48>();
 }
 
 }  // namespace semmg
