@@ -56,6 +56,10 @@ struct ElemScal {
   T al[3];      // alpha_d alone (faces transformed beforehand, scaled by c_f there)
   T e[3];       // 4 / h_d^2
   int64_t cls;  // width-class triple of the element (for the 1/D table)
+  // sf[d] and al[d] for a run-time axis d, by selection: an indexed read would
+  // place the whole struct in local memory
+  __device__ __forceinline__ T sfd(int d) const { return d == 0 ? sf[0] : (d == 1 ? sf[1] : sf[2]); }
+  __device__ __forceinline__ T ald(int d) const { return d == 0 ? al[0] : (d == 1 ? al[1] : al[2]); }
 };
 
 template <typename T>
@@ -161,27 +165,47 @@ __device__ __forceinline__ void line_block(const Lines& L, int g, int* k0, int* 
   }
 }
 
+// The input loops below run over the odd half's length tc = n - ne for every group, so that
+// all lanes of a warp take the same trip count (known at compile time where n is); the even
+// half's one extra input (n odd) is added after them.  Each output's terms are summed in
+// input order.
+
+// Float-float steps are long (about twelve FP32 operations each), so unrolling them costs
+// little code and removes the loop's own instructions; FP64 and FP32 builds keep the
+// compiler's choice (their 64-register builds would spill).
+template <typename T>
+constexpr bool kTxUnroll = std::is_same<T, ff>::value;
+
 // Z = (scale or sc2[i2]) * forward transform of folded Y along ax.
 template <typename T>
 __device__ __forceinline__ void tx_lines_g(const Lines& L, int ax, const T* __restrict__ S, const T* Y, T* Z,
                                            T scale, const T* sc2, const Team& tm = Team::block()) {
-  const int G = line_groups(L), n = L.n;
+  const int G = line_groups(L), n = L.n, tc = L.n - L.ne;
   const int items = nlines(L) * G;
   for (int it = tm.id; it < items; it += tm.n) {
     const int l = it / G, g = it - l * G;
     int base, str, i2, k0, ks, k1, j0, j1, even;
     line_of(L, ax, l, &base, &str, &i2);
     line_block(L, g, &k0, &ks, &k1, &j0, &j1, &even);
+    const T* yp = Y + base + j0 * str;
+    const T* sp = S + (even ? L.h : L.ne) * n + k0;  // row of input j0
     Acc<T> a[kG];
 #pragma unroll
     for (int q = 0; q < kG; ++q) a[q] = Acc<T>::zero();
-    for (int j = j0; j < j1; ++j) {
-      const T yv = Y[base + j * str];
-      const T* sr = S + (even ? L.h + j : j) * n + k0;
+    auto step = [&](int t) {
+      const T yv = yp[t * str];
+      const T* sr = sp + t * n;
 #pragma unroll
       for (int q = 0; q < kG; ++q)
         if (k0 + q * ks < k1) a[q].add(sr[q * ks], yv);
+    };
+    if constexpr (kTxUnroll<T>) {
+#pragma unroll 4
+      for (int t = 0; t < tc; ++t) step(t);
+    } else {
+      for (int t = 0; t < tc; ++t) step(t);
     }
+    if (j1 - j0 > tc) step(tc);
     const T s = sc2 ? sc2[i2] : scale;
 #pragma unroll
     for (int q = 0; q < kG; ++q)
@@ -193,26 +217,34 @@ __device__ __forceinline__ void tx_lines_g(const Lines& L, int ax, const T* __re
 template <typename T>
 __device__ __forceinline__ void txT_lines_g(const Lines& L, int ax, const T* __restrict__ S, const T* B, T* Y,
                                             const Team& tm = Team::block()) {
-  const int G = line_groups(L), n = L.n;
+  const int G = line_groups(L), n = L.n, tc = L.n - L.ne;
   const int items = nlines(L) * G;
   for (int it = tm.id; it < items; it += tm.n) {
     const int l = it / G, g = it - l * G;
     int base, str, i2, k0, ks, k1, j0, j1, even;
     line_of(L, ax, l, &base, &str, &i2);
     line_block(L, g, &k0, &ks, &k1, &j0, &j1, &even);
+    const T* bp = B + base + j0 * str;
     Acc<T> a[kG];
     const T* sr[kG];
 #pragma unroll
     for (int q = 0; q < kG; ++q) {
       a[q] = Acc<T>::zero();
       const int jo = min(k0 + q * ks, k1 - 1);
-      sr[q] = S + (even ? L.h + jo : jo) * n;
+      sr[q] = S + (even ? L.h + jo : jo) * n + j0;
     }
-    for (int k = j0; k < j1; ++k) {
-      const T bv = B[base + k * str];
+    auto step = [&](int t) {
+      const T bv = bp[t * str];
 #pragma unroll
-      for (int q = 0; q < kG; ++q) a[q].add(sr[q][k], bv);
+      for (int q = 0; q < kG; ++q) a[q].add(sr[q][t], bv);
+    };
+    if constexpr (kTxUnroll<T>) {
+#pragma unroll 4
+      for (int t = 0; t < tc; ++t) step(t);
+    } else {
+      for (int t = 0; t < tc; ++t) step(t);
     }
+    if (j1 - j0 > tc) step(tc);
 #pragma unroll
     for (int q = 0; q < kG; ++q)
       if (k0 + q * ks < k1) Y[base + (k0 + q * ks) * str] = a[q].value();
@@ -254,7 +286,7 @@ template <typename T>
 __device__ __forceinline__ void faces_forward(const Lines& F, const T* Sh, T* X, T* Tt, const ElemScal<T>& sc,
                                               const Team& tm = Team::block()) {
   __shared__ T sc6[6];
-  if (threadIdx.x < 6) sc6[threadIdx.x] = sc.sf[threadIdx.x >> 1];
+  if (threadIdx.x < 6) sc6[threadIdx.x] = sc.sfd(threadIdx.x >> 1);
   fold_lines(F, 0, X, Tt, tm);
   tm.sync();
   tx_lines_g(F, 0, Sh, Tt, X, (T)1, (const T*)nullptr, tm);
@@ -281,8 +313,8 @@ __device__ __forceinline__ void faces_backward(const Lines& F, const T* Sh, T* X
     const int d = idx / mm, r = idx - d * mm;
     const T ye = unfold_at(F, 1, Tt, (2 * d) * mm + r);
     const T yo = unfold_at(F, 1, Tt, (2 * d + 1) * mm + r);
-    store((2 * d) * mm + r, sc.sf[d] * (ye + yo));
-    store((2 * d + 1) * mm + r, sc.sf[d] * (ye - yo));
+    store((2 * d) * mm + r, sc.sfd(d) * (ye + yo));
+    store((2 * d + 1) * mm + r, sc.sfd(d) * (ye - yo));
   }
 }
 
@@ -450,8 +482,8 @@ __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const 
       for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
         const int d = idx / mm, r = idx - d * mm;
         const T a = X[(2 * d) * mm + r], b = X[(2 * d + 1) * mm + r];
-        X[(2 * d) * mm + r] = sc.al[d] * (a + b);
-        X[(2 * d + 1) * mm + r] = sc.al[d] * (a - b);
+        X[(2 * d) * mm + r] = sc.ald(d) * (a + b);
+        X[(2 * d + 1) * mm + r] = sc.ald(d) * (a - b);
       }
       __syncthreads();
     } else {
@@ -503,8 +535,8 @@ __global__ void __launch_bounds__(512, NB) k_elem_schur(Geo G, Tabs<T> t, const 
       for (int idx = threadIdx.x; idx < 3 * nr; idx += blockDim.x) {
         const int d = idx / nr, r = rlo + (idx - d * nr);
         const T xe = X[(2 * d) * mm + r], xo = X[(2 * d + 1) * mm + r];
-        Ze[(2 * d) * mm + r] = sc.al[d] * (xe + xo);
-        Ze[(2 * d + 1) * mm + r] = sc.al[d] * (xe - xo);
+        Ze[(2 * d) * mm + r] = sc.ald(d) * (xe + xo);
+        Ze[(2 * d + 1) * mm + r] = sc.ald(d) * (xe - xo);
       }
     } else {
       faces_backward(F, Sh, X, Tt, sc, [&](int idx, T v) { Ze[idx] = v; });

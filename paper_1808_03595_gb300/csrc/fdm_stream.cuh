@@ -26,7 +26,7 @@ namespace semmg {
 
 namespace {
 
-constexpr size_t kFsSmemMax = 200 * 1024;
+constexpr size_t kFsSmemMax = 224 * 1024;  // one CTA per SM: the planes and tiles take what is left
 
 // Shared memory: Sh (m^2), Sr (m^2), a0 (m), lI (m), then the pass buffers:
 // pass A two plane buffers of NP m^2, pass B two tile buffers of TK m^2 and the

@@ -185,8 +185,8 @@ __global__ void __launch_bounds__(512, 1) k_schur_eb(Geo G, Tabs<T> t, const T* 
       const int d = idx / mm, r = idx - d * mm;
       const T a = Ut[elem_face_base(G, a1, a2, a3, 2 * d) + r];
       const T b = Ut[elem_face_base(G, a1, a2, a3, 2 * d + 1) + r];
-      X[(2 * d) * mm + r] = sc.al[d] * (a + b);
-      X[(2 * d + 1) * mm + r] = sc.al[d] * (a - b);
+      X[(2 * d) * mm + r] = sc.ald(d) * (a + b);
+      X[(2 * d + 1) * mm + r] = sc.ald(d) * (a - b);
     }
     __syncthreads();
     T a1r[NJ], a2r[NI];
