@@ -188,16 +188,27 @@ __device__ __forceinline__ void tx_lines_g(const Lines& L, int ax, const T* __re
     line_of(L, ax, l, &base, &str, &i2);
     line_block(L, g, &k0, &ks, &k1, &j0, &j1, &even);
     const T* yp = Y + base + j0 * str;
-    const T* sp = S + (even ? L.h : L.ne) * n + k0;  // row of input j0
+    const T* sp = S + (even ? L.h : L.ne) * n + k0;  // row of input j0, first output column
+    // column offsets of the outputs; in the float-float build a slot past the group's end
+    // repeats its last column (summed, not stored), so that every step is the same
+    // straight-line code; the other builds skip that slot
+    int kq[kG];
     Acc<T> a[kG];
 #pragma unroll
-    for (int q = 0; q < kG; ++q) a[q] = Acc<T>::zero();
+    for (int q = 0; q < kG; ++q) {
+      a[q] = Acc<T>::zero();
+      kq[q] = kTxUnroll<T> ? min(q * ks, k1 - 1 - k0) : q * ks;
+    }
     auto step = [&](int t) {
       const T yv = yp[t * str];
       const T* sr = sp + t * n;
 #pragma unroll
-      for (int q = 0; q < kG; ++q)
-        if (k0 + q * ks < k1) a[q].add(sr[q * ks], yv);
+      for (int q = 0; q < kG; ++q) {
+        if constexpr (kTxUnroll<T>)
+          a[q].add(sr[kq[q]], yv);
+        else if (k0 + q * ks < k1)
+          a[q].add(sr[q * ks], yv);
+      }
     };
     if constexpr (kTxUnroll<T>) {
 #pragma unroll 4
