@@ -96,6 +96,13 @@ struct Lines {
   }
 };
 
+// The float-float builds of the line operations run as straight-line code: a float-float
+// step is long (about twelve FP32 operations), so unrolling costs little code and removes the
+// loop's own instructions, and selects in place of branches keep a warp's lanes together.
+// FP64 and FP32 builds keep the compiler's choices (their 64-register builds would spill).
+template <typename T>
+constexpr bool kStraight = std::is_same<T, ff>::value;
+
 template <typename T>
 __device__ __forceinline__ void fold_lines(const Lines& L, int ax, const T* X, T* Y, const Team& tm = Team::block()) {
   const int str = L.stride(ax);
@@ -103,7 +110,13 @@ __device__ __forceinline__ void fold_lines(const Lines& L, int ax, const T* X, T
     const int j = L.pos(idx, ax);
     const int base = idx - j * str;
     T v;
-    if (j < L.ne) {
+    if constexpr (kStraight<T>) {
+      // E_j = x[h + j] + x[n-1-h-j] (the middle point alone), O_j = x[j] - x[n-1-j]
+      const bool ev = j < L.ne;
+      const int i = ev ? L.h + j : j, mi = L.n - 1 - i;
+      const T xb = X[base + mi * str];
+      v = X[base + i * str] + (ev ? (i == mi ? T(0) : xb) : -xb);
+    } else if (j < L.ne) {
       const int i = L.h + j, mi = L.n - 1 - i;
       v = (i == mi) ? X[base + i * str] : X[base + i * str] + X[base + mi * str];
     } else {
@@ -170,12 +183,6 @@ __device__ __forceinline__ void line_block(const Lines& L, int g, int* k0, int* 
 // half's one extra input (n odd) is added after them.  Each output's terms are summed in
 // input order.
 
-// Float-float steps are long (about twelve FP32 operations each), so unrolling them costs
-// little code and removes the loop's own instructions; FP64 and FP32 builds keep the
-// compiler's choice (their 64-register builds would spill).
-template <typename T>
-constexpr bool kTxUnroll = std::is_same<T, ff>::value;
-
 // Z = (scale or sc2[i2]) * forward transform of folded Y along ax.
 template <typename T>
 __device__ __forceinline__ void tx_lines_g(const Lines& L, int ax, const T* __restrict__ S, const T* Y, T* Z,
@@ -197,20 +204,20 @@ __device__ __forceinline__ void tx_lines_g(const Lines& L, int ax, const T* __re
 #pragma unroll
     for (int q = 0; q < kG; ++q) {
       a[q] = Acc<T>::zero();
-      kq[q] = kTxUnroll<T> ? min(q * ks, k1 - 1 - k0) : q * ks;
+      kq[q] = kStraight<T> ? min(q * ks, k1 - 1 - k0) : q * ks;
     }
     auto step = [&](int t) {
       const T yv = yp[t * str];
       const T* sr = sp + t * n;
 #pragma unroll
       for (int q = 0; q < kG; ++q) {
-        if constexpr (kTxUnroll<T>)
+        if constexpr (kStraight<T>)
           a[q].add(sr[kq[q]], yv);
         else if (k0 + q * ks < k1)
           a[q].add(sr[q * ks], yv);
       }
     };
-    if constexpr (kTxUnroll<T>) {
+    if constexpr (kStraight<T>) {
 #pragma unroll 4
       for (int t = 0; t < tc; ++t) step(t);
     } else {
@@ -249,7 +256,7 @@ __device__ __forceinline__ void txT_lines_g(const Lines& L, int ax, const T* __r
 #pragma unroll
       for (int q = 0; q < kG; ++q) a[q].add(sr[q][t], bv);
     };
-    if constexpr (kTxUnroll<T>) {
+    if constexpr (kStraight<T>) {
 #pragma unroll 4
       for (int t = 0; t < tc; ++t) step(t);
     } else {
@@ -269,6 +276,12 @@ __device__ __forceinline__ T unfold_at(const Lines& L, int ax, const T* Y, int i
   const int i = L.pos(idx, ax);
   const int base = idx - i * str;
   const int mi = L.n - 1 - i;
+  if constexpr (kStraight<T>) {
+    // u = max(i, mi): E at u - h plus (i > mi) or minus (i < mi) O at u; the middle point E alone
+    const int u = i > mi ? i : mi;
+    const T ob = Y[base + u * str];
+    return Y[base + (u - L.h) * str] + (i == mi ? T(0) : (i > mi ? ob : -ob));
+  }
   if (i == mi) return Y[base + (i - L.h) * str];
   if (i > mi) return Y[base + (i - L.h) * str] + Y[base + i * str];
   return Y[base + (mi - L.h) * str] - Y[base + mi * str];

@@ -118,6 +118,8 @@ __global__ void __launch_bounds__(512, 1) k_fs_condense(Geo G, Tabs<T> t, const 
       T* Pb = s.W;
       T* Qb = s.W + sh.np * mm;
       __syncthreads();  // the previous round's planes are stored
+      // (the staging loops are unrolled so that several global loads are in flight per thread)
+#pragma unroll 4
       for (int idx = threadIdx.x; idx < np * mm; idx += blockDim.x) {
         const int i1 = idx % m, i2 = (idx / m) % m, i3 = p0 + idx / mm;
         Pb[idx] = vol * t.w[i1 + 1] * t.w[i2 + 1] * t.w[i3 + 1] *
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(512, 1) k_fs_condense(Geo G, Tabs<T> t, const 
       const int tk = m - b0 < sh.tk ? m - b0 : sh.tk;
       const Lines Cl{m, m / 2, ne, m, tk, tk * mm};  // C[i3][t][k1], lines along i3
       __syncthreads();  // the previous tile is consumed
+#pragma unroll 4
       for (int idx = threadIdx.x; idx < tk * mm; idx += blockDim.x) {
         const int k1 = idx % m, tt = (idx / m) % tk, i3 = idx / (m * tk);
         C[idx] = s.gA[((int64_t)i3 * m + b0 + tt) * m + k1];
@@ -155,6 +158,7 @@ __global__ void __launch_bounds__(512, 1) k_fs_condense(Geo G, Tabs<T> t, const 
       __syncthreads();
       tx_lines_g(Cl, 2, s.Sr, D, C, sig, (const T*)nullptr);
       __syncthreads();
+#pragma unroll 4
       for (int idx = threadIdx.x; idx < tk * mm; idx += blockDim.x) {
         const int k1 = idx % m, tt = (idx / m) % tk, k3 = idx / (m * tk), k2 = b0 + tt;
         const int64_t gi = ((int64_t)k3 * m + k2) * m + k1;
@@ -261,6 +265,7 @@ __global__ void __launch_bounds__(512, 1) k_fs_recover(Geo G, Tabs<T> t, const T
       const int tk = m - b0 < sh.tk ? m - b0 : sh.tk;
       const Lines Cl{m, m / 2, ne, m, tk, tk * mm};
       __syncthreads();
+#pragma unroll 4
       for (int idx = threadIdx.x; idx < tk * mm; idx += blockDim.x) {
         const int k1 = idx % m, tt = (idx / m) % tk, k3 = idx / (m * tk), k2 = b0 + tt;
         const int64_t gi = ((int64_t)k3 * m + k2) * m + k1;
@@ -284,6 +289,7 @@ __global__ void __launch_bounds__(512, 1) k_fs_recover(Geo G, Tabs<T> t, const T
       T* Pb = s.W;
       T* Qb = s.W + sh.np * mm;
       __syncthreads();
+#pragma unroll 4
       for (int idx = threadIdx.x; idx < np * mm; idx += blockDim.x) Pb[idx] = s.gA[(int64_t)p0 * mm + idx];
       __syncthreads();
       txT_lines_g(P, 1, s.Sr, Pb, Qb);
